@@ -1,0 +1,201 @@
+"""Seeded synthetic lattice problems.
+
+This module only *describes* problems: lattice size, cell grid, strut
+radii, macro-map parameters, boundary conditions and load cases.  It
+holds none of the solver's arithmetic, so that the CPU oracle and the
+CUDA path can both take their inputs from it without sharing any
+method code.
+
+Every random draw comes from ``numpy.random.default_rng(seed)`` in the
+order the draws are listed in each generator.
+
+Conventions (all of them are readings of the paper's silent points):
+
+* Cell ``s = cx + nx*(cy + ny*cz)``; lattice coordinate
+  ``xi = (cx, cy, cz) + eta`` with ``eta`` in the unit reference cell
+  (the cells are images of one reference cell, Sec. 2.2.1, Eq. 6).
+* ``map_kind`` selects an analytic macro map ``x = F(xi)`` standing in
+  for the paper's spline macro geometries (Sec. 4.1, Eq. 51):
+  0 identity; 1 2D bend ``(xi_x, xi_y + a sin(pi xi_x / L))``;
+  2 3D shear+bend ``xi + (g1 xi_z, g2 xi_z, a sin(pi xi_x / L))``;
+  3 3D twist about the x axis through ``(yc, zc)`` by ``tau xi_x / L``,
+  then bend ``a sin(pi xi_x / L)`` along z.
+* ``mask_kind`` selects the ersatz strut material: 0 2D frame plus both
+  diagonals (hard), 1 3D body-centred-cubic diagonals (hard), 2 BCC with
+  a sigmoid transition of width ``mask_width``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Tuple
+
+import numpy as np
+
+MASK_FRAME_DIAG = 0
+MASK_BCC_HARD = 1
+MASK_BCC_SIGMOID = 2
+
+MAP_IDENTITY = 0
+MAP_BEND_2D = 1
+MAP_SHEAR_BEND_3D = 2
+MAP_BEND_TWIST_3D = 3
+
+LOAD_TRACTION = 0
+LOAD_BODY = 1
+
+
+@dataclass
+class Load:
+    """One load case: a unit traction on a lattice face or a body force.
+
+    ``axis``/``side`` name the face (side 0: xi_axis = 0, side 1:
+    xi_axis = n_axis); they are ignored for body forces.  ``direction``
+    is the force per unit physical area (traction) or volume (body).
+    """
+
+    kind: int
+    direction: Tuple[float, ...]
+    axis: int = 0
+    side: int = 1
+
+
+@dataclass
+class LatticeProblem:
+    dim: int
+    cells: Tuple[int, int, int]          # (nx, ny, nz); nz = 1 in 2D
+    elems: int                           # Q1 elements per cell edge
+    r_cell: np.ndarray                   # [N] strut radius per cell
+    mask_kind: int
+    map_kind: int
+    map_params: Tuple[float, ...]        # see module docstring
+    loads: List[Load]
+    clamp_axis: int = 0
+    clamp_side: int = 0
+    nu: float = 0.3
+    E_solid: float = 1.0
+    E_void: float = 1e-3
+    mask_width: float = 0.02
+    n_rb: int = 8                        # principal cells requested
+    tol_rb: float = 1e-10                # greedy stop on max |Delta|_inf (relative)
+    name: str = ""
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n_cells(self) -> int:
+        nx, ny, nz = self.cells
+        return nx * ny * nz
+
+    @property
+    def n_rhs(self) -> int:
+        return len(self.loads)
+
+    def map_params_array(self) -> np.ndarray:
+        p = np.zeros(8)
+        p[: len(self.map_params)] = self.map_params
+        return p
+
+
+def _frame_problem(nx, ny, e, r_cell, a, n_rb, name):
+    return LatticeProblem(
+        dim=2, cells=(nx, ny, 1), elems=e, r_cell=np.asarray(r_cell, float),
+        mask_kind=MASK_FRAME_DIAG, map_kind=MAP_BEND_2D,
+        map_params=(float(a), float(nx)),
+        loads=[Load(LOAD_TRACTION, (0.0, -1.0), axis=0, side=1)],
+        clamp_axis=0, clamp_side=0, n_rb=n_rb, name=name)
+
+
+def lattice_2d(nx=4, ny=4, e=8, a=0.0, r=0.12, n_rb=2, r_grade=0.0,
+               name="lattice_2d") -> LatticeProblem:
+    """Small 2D frame-and-diagonal lattice for tests.
+
+    ``r_grade`` > 0 grades the radius as ``r + r_grade*sin(2 pi x_c / nx)``
+    like the 64x64 workload; ``a`` is the bend amplitude.
+    """
+    xc = (np.arange(nx) + 0.5)
+    r_col = r + r_grade * np.sin(2.0 * np.pi * xc / nx)
+    r_cell = np.tile(r_col, ny)
+    return _frame_problem(nx, ny, e, r_cell, a, n_rb, name)
+
+
+def config1(seed: int = 1) -> LatticeProblem:
+    """2D plane strain, 4x4 cells of 8x8 Q1, r = 0.12, a ~ U[0, 0.5], 2 principal cells."""
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(0.0, 0.5)
+    return _frame_problem(4, 4, 8, np.full(16, 0.12), a, 2, "2d_4x4_e8")
+
+
+def config2(seed: int = 2) -> LatticeProblem:
+    """2D plane strain, 64x64 cells of 16x16 Q1, graded r_s, a ~ U[0, 4], 8 principal cells."""
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(0.0, 4.0)
+    p = lattice_2d(64, 64, 16, a=a, r=0.1, n_rb=8, r_grade=0.05, name="2d_64x64_e16")
+    return p
+
+
+def _bcc(cells, e, r_cell, mask_kind, map_kind, map_params, loads, n_rb, name):
+    return LatticeProblem(
+        dim=3, cells=tuple(cells), elems=e, r_cell=np.asarray(r_cell, float),
+        mask_kind=mask_kind, map_kind=map_kind, map_params=tuple(float(v) for v in map_params),
+        loads=loads, clamp_axis=2, clamp_side=0, n_rb=n_rb, name=name)
+
+
+def _top_tractions():
+    return [Load(LOAD_TRACTION, tuple(float(i == c) for i in range(3)), axis=2, side=1)
+            for c in range(3)]
+
+
+def lattice_3d(nx=2, ny=2, nz=2, e=3, r=0.2, r_spread=0.0, map_kind=MAP_IDENTITY,
+               map_params=(), mask_kind=MASK_BCC_HARD, loads=None, n_rb=4, seed=0,
+               name="lattice_3d") -> LatticeProblem:
+    """Small 3D BCC lattice for tests (radii r +/- r_spread drawn from ``seed``)."""
+    rng = np.random.default_rng(seed)
+    n = nx * ny * nz
+    r_cell = r + r_spread * rng.uniform(-1.0, 1.0, size=n)
+    if loads is None:
+        loads = [Load(LOAD_TRACTION, (0.0, 0.0, -1.0), axis=2, side=1)]
+    return _bcc((nx, ny, nz), e, r_cell, mask_kind, map_kind, map_params, loads, n_rb, name)
+
+
+def config3(seed: int = 3) -> List[LatticeProblem]:
+    """32 independent 3D BCC lattices of uneven size, 3 top tractions each."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(32):
+        nx, ny = (int(v) for v in rng.integers(4, 25, size=2))
+        nz = int(rng.integers(2, 9))
+        r_cell = rng.uniform(0.15, 0.3, size=nx * ny * nz)
+        g1, g2 = rng.uniform(-0.2, 0.2, size=2)
+        a = rng.uniform(0.0, nx / 8.0)
+        out.append(_bcc((nx, ny, nz), 6, r_cell, MASK_BCC_HARD, MAP_SHEAR_BEND_3D,
+                        (a, float(nx), g1, g2), _top_tractions(), 16, f"batch3d_{b}"))
+    return out
+
+
+def config4(seed: int = 4) -> LatticeProblem:
+    """3D 24x24x12 BCC with sigmoid density, identity map, unit downward top traction."""
+    rng = np.random.default_rng(seed)
+    cells = (24, 24, 12)
+    r_cell = rng.uniform(0.15, 0.3, size=24 * 24 * 12)
+    fd_cells = rng.choice(24 * 24 * 12, size=16, replace=False)
+    p = _bcc(cells, 6, r_cell, MASK_BCC_SIGMOID, MAP_IDENTITY, (),
+             [Load(LOAD_TRACTION, (0.0, 0.0, -1.0), axis=2, side=1)], 16, "adjoint_3d_24x24x12")
+    p.extra["fd_cells"] = np.sort(fd_cells)
+    return p
+
+
+def config5(seed: int = 5) -> LatticeProblem:
+    """3D 32x32x16 BCC, radius graded along x, bend+twist map, 6 load cases."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = 32, 32, 16
+    a = rng.uniform(0.0, 4.0)
+    tau = rng.uniform(0.0, np.pi / 8.0)
+    cx = np.arange(nx)
+    r_col = 0.15 + 0.15 * (cx + 0.5) / nx
+    r_cell = np.tile(r_col, ny * nz)
+    loads = _top_tractions() + [Load(LOAD_BODY, tuple(float(i == c) for i in range(3)))
+                                for c in range(3)]
+    return _bcc((nx, ny, nz), 6, r_cell, MASK_BCC_HARD, MAP_BEND_TWIST_3D,
+                (a, float(nx), tau, ny / 2.0, nz / 2.0), loads, 16, "3d_32x32x16")
+
+
+CONFIGS = {1: config1, 2: config2, 3: config3, 4: config4, 5: config5}

@@ -1,0 +1,210 @@
+"""Pins of the oracle's discretisation against closed forms, invariants and brute force."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from paper_2308_11371_gb300 import workloads as W
+from oracle import monolithic
+from oracle.discretization import Lattice, ReferenceCell, macro_map
+
+
+@pytest.mark.parametrize("dim,e,n,ni,nd,npp", [
+    (2, 8, 162, 98, 56, 8),        # 4x4 lattice cell
+    (2, 16, 578, 450, 120, 8),     # 64x64 lattice cell
+    (3, 6, 1029, 375, 630, 24),    # 3D BCC cell
+])
+def test_reference_cell_counts(dim, e, n, ni, nd, npp):
+    ref = ReferenceCell(dim, e)
+    assert (ref.n_dof, ref.n_i, ref.n_d, ref.n_p) == (n, ni, nd, npp)
+    # closed forms: (e+1)^d nodes, (e-1)^d interior nodes, 2^d corners
+    assert ref.n_dof == dim * (e + 1) ** dim
+    assert ref.n_i == dim * (e - 1) ** dim
+    assert ref.n_p == dim * 2 ** dim
+
+
+def test_config1_sizes():
+    lat = Lattice(W.config1())
+    assert (lat.N, lat.L, lat.n_P) == (16, 392, 40)
+    # 2D: interior vertical edges 3*4*7 nodes, horizontal 4*3*7, clamped face 4 cells*7 nodes
+    assert lat.L == 2 * (3 * 4 * 7 + 4 * 3 * 7 + 4 * 7)
+
+
+def _textbook_q1_stiffness(coords, E, nu, dim):
+    """Element stiffness by the textbook Voigt B^T D B in physical space (independent formula)."""
+    from itertools import product
+    g = [0.5 - 0.5 / np.sqrt(3.0), 0.5 + 0.5 / np.sqrt(3.0)]
+    offs = np.array(list(product([0, 1], repeat=dim)))[:, ::-1]
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu)); mu = E / (2 * (1 + nu))
+    if dim == 2:
+        D = np.array([[lam + 2 * mu, lam, 0], [lam, lam + 2 * mu, 0], [0, 0, mu]])
+    else:
+        D = np.zeros((6, 6)); D[:3, :3] = lam; D[range(3), range(3)] += 2 * mu
+        D[3:, 3:] = mu * np.eye(3)
+    nA = len(offs)
+    K = np.zeros((nA * dim, nA * dim))
+    for gp in product(range(2), repeat=dim):
+        t = np.array([g[q] for q in gp])
+        dN = np.zeros((nA, dim))
+        for A in range(nA):
+            vals = [t[k] if offs[A, k] else 1 - t[k] for k in range(dim)]
+            for a in range(dim):
+                dN[A, a] = np.prod([(1 if offs[A, k] else -1) if k == a else vals[k]
+                                    for k in range(dim)])
+        Jt = coords.T @ dN                      # dx/dt
+        dNdx = dN @ np.linalg.inv(Jt)
+        if dim == 2:
+            B = np.zeros((3, 2 * nA))
+            B[0, 0::2] = dNdx[:, 0]; B[1, 1::2] = dNdx[:, 1]
+            B[2, 0::2] = dNdx[:, 1]; B[2, 1::2] = dNdx[:, 0]
+        else:
+            B = np.zeros((6, 3 * nA))
+            for k in range(3):
+                B[k, k::3] = dNdx[:, k]
+            B[3, 1::3] = dNdx[:, 2]; B[3, 2::3] = dNdx[:, 1]
+            B[4, 0::3] = dNdx[:, 2]; B[4, 2::3] = dNdx[:, 0]
+            B[5, 0::3] = dNdx[:, 1]; B[5, 1::3] = dNdx[:, 0]
+        K += B.T @ D @ B * abs(np.linalg.det(Jt)) * 0.5 ** dim
+    return K
+
+
+@pytest.mark.parametrize("prob", [
+    W.lattice_2d(1, 1, 2, a=0.0, r=10.0),
+    W.lattice_3d(1, 1, 1, e=2, r=10.0, map_kind=W.MAP_SHEAR_BEND_3D, map_params=(0.0, 1.0, 0.15, -0.1)),
+])
+def test_pulled_back_stiffness_matches_textbook_voigt(prob):
+    """Eq. 52's pulled-back tensor equals B^T D B in physical space for an affine map."""
+    lat = Lattice(prob)
+    K = lat.stiffness(0).toarray()
+    ref, d = lat.ref, lat.dim
+    for el in range(ref.n_elem):
+        nodes = ref.elem_nodes[el]
+        xi = ref.node_eta[nodes]
+        x, _ = macro_map(prob, xi)
+        Ke = _textbook_q1_stiffness(x, 1.0, prob.nu, d)
+        # compare through the quadratic form on the element's DOF (other elements share nodes):
+        # assemble textbook over all elements instead
+        if el == 0:
+            Kt = np.zeros_like(K)
+        dof = (nodes[:, None] * d + np.arange(d)).ravel()
+        Kt[np.ix_(dof, dof)] += Ke
+    assert np.allclose(K, Kt, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("prob", [
+    W.lattice_2d(2, 2, 4, a=0.0, r=10.0),
+    W.lattice_3d(2, 1, 2, e=2, r=10.0, map_kind=W.MAP_SHEAR_BEND_3D, map_params=(0.0, 2.0, 0.2, 0.1)),
+])
+def test_patch_test_linear_field(prob):
+    """Homogeneous material + affine map: a linear Dirichlet field on the whole boundary is
+    reproduced exactly in the interior (constant stress is in equilibrium)."""
+    lat = Lattice(prob)
+    K, _ = monolithic.assemble_global(lat)
+    d = lat.dim
+    gd, gs = lat.global_node_dims, lat.global_node_strides
+    ijk = np.stack([(np.arange(lat.n_global_nodes) // gs[k]) % gd[k] for k in range(d)], -1)
+    xi = ijk / prob.elems
+    x, _ = macro_map(prob, xi)
+    rng = np.random.default_rng(0)
+    Agrad = rng.standard_normal((d, d)); c0 = rng.standard_normal(d)
+    u_exact = (x @ Agrad.T + c0).ravel()
+    bnd = np.any((ijk == 0) | (ijk == gd - 1), axis=1)
+    fixed = (np.nonzero(bnd)[0][:, None] * d + np.arange(d)).ravel()
+    free = np.setdiff1d(np.arange(K.shape[0]), fixed)
+    rhs = -K[free][:, fixed] @ u_exact[fixed]
+    u_free = spla.spsolve(K[free][:, free].tocsc(), rhs)
+    assert np.abs(u_free - u_exact[free]).max() < 1e-10 * np.abs(u_exact).max()
+
+
+@pytest.mark.parametrize("prob,nrigid", [
+    (W.lattice_2d(1, 1, 4, a=0.0, r=0.12), 3),
+    (W.lattice_3d(1, 1, 1, e=3, r=0.2), 6),
+])
+def test_rigid_body_modes_and_spd_remaining_block(prob, nrigid):
+    """A floating cell has exactly d(d+1)/2 zero-energy modes; K_rr (corners removed) is SPD."""
+    lat = Lattice(prob)
+    K = lat.stiffness_idp(0).toarray()
+    ev = np.linalg.eigvalsh(K)
+    scale = ev.max()
+    assert (np.abs(ev) < 1e-12 * scale).sum() == nrigid
+    # the rigid modes themselves: translations and infinitesimal rotations have zero energy
+    ref, d = lat.ref, lat.dim
+    x, _ = macro_map(prob, ref.node_eta)
+    modes = []
+    for k in range(d):
+        t = np.zeros((ref.n_nodes, d)); t[:, k] = 1.0; modes.append(t.ravel())
+    for a in range(d):
+        for b in range(a + 1, d):
+            r = np.zeros((ref.n_nodes, d)); r[:, a] = -x[:, b]; r[:, b] = x[:, a]
+            modes.append(r.ravel())
+    Kn = lat.stiffness(0).toarray()
+    for m in modes:
+        assert m @ Kn @ m < 1e-12 * scale * (m @ m)
+    nr = ref.n_r
+    assert np.linalg.eigvalsh(K[:nr, :nr]).min() > 1e-10 * scale
+
+
+def test_load_resultants():
+    """Traction resultant = direction x mapped face length; body-force resultant = volume."""
+    p = W.lattice_2d(3, 2, 4, a=0.7)
+    lat = Lattice(p)
+    F = sum(lat.load(s)[0].reshape(-1, 2).sum(0) for s in range(lat.N))
+    # face xi_x = nx maps to x = nx, y = xi_y + a sin(pi) -> straight, length ny
+    assert np.allclose(F, [0.0, -2.0], atol=1e-13)
+    p3 = W.lattice_3d(2, 3, 2, e=2, map_kind=W.MAP_BEND_TWIST_3D,
+                      map_params=(0.5, 2.0, 0.3, 1.5, 1.0),
+                      loads=[W.Load(W.LOAD_BODY, (0.0, 1.0, 0.0))])
+    lat3 = Lattice(p3)
+    F3 = sum(lat3.load(s)[0].reshape(-1, 3).sum(0) for s in range(lat3.N))
+    assert np.allclose(F3, [0.0, 12.0, 0.0], atol=1e-12)     # det J = 1 -> volume 2*3*2
+    p4 = W.lattice_3d(2, 3, 2, e=2, loads=[W.Load(W.LOAD_TRACTION, (0, 0, 1.0), axis=2, side=1)])
+    lat4 = Lattice(p4)
+    F4 = sum(lat4.load(s)[0].reshape(-1, 3).sum(0) for s in range(lat4.N))
+    assert np.allclose(F4, [0.0, 0.0, 6.0], atol=1e-13)
+
+
+@pytest.mark.parametrize("prob", [W.config1(), W.lattice_3d(2, 2, 2, e=2)])
+def test_jump_operator_brute_force(prob):
+    """Every B row couples copies of ONE physical node (or clamps a node); B kills continuous
+    fields off the Dirichlet rows; B has full row rank; A_p^T reproduces corner values."""
+    lat = Lattice(prob)
+    ref, d = lat.ref, lat.dim
+    # brute force: node coordinates of each (cell, dual dof)
+    dual_nodes = ref.dual_nodes
+    coords = lat.cell_ijk[:, None, :] * prob.elems + ref.node_ijk[dual_nodes][None]
+    clamp_val = 0 if prob.clamp_side == 0 else lat.nc[prob.clamp_axis] * prob.elems
+    for row, dirich in zip(lat.rows, lat.row_dirichlet):
+        pts = [tuple(coords[s, j // d]) for (s, j, _) in row]
+        comps = {j % d for (_, j, _) in row}
+        assert len(comps) == 1
+        if dirich:
+            assert len(row) == 1 and pts[0][prob.clamp_axis] == clamp_val
+        else:
+            assert len(row) == 2 and pts[0] == pts[1] and row[0][0] < row[1][0]
+            assert row[0][2] == 1.0 and row[1][2] == -1.0
+    # continuous field: global random field copied to cells
+    rng = np.random.default_rng(1)
+    ug = rng.standard_normal(lat.n_global_nodes * d)
+    uc = monolithic.to_cells(lat, ug[None])[0]          # (N, n_dof) natural
+    ud = uc[:, ref.dof_d]
+    jump = lat.Bd @ ud.ravel()
+    assert np.all(jump[~lat.row_dirichlet] == 0.0)
+    assert np.linalg.matrix_rank(lat.Bd.toarray()) == lat.L
+    # corners
+    uP_full = np.zeros(lat.n_P)
+    # build uP from the global field at free vertices
+    for s in range(lat.N):
+        for k, v in enumerate(lat.cell_corner_vertex[s]):
+            if v >= 0:
+                uP_full[v * d:(v + 1) * d] = uc[s, ref.dof_p[k * d:(k + 1) * d]]
+    up = (lat.Ap.T @ uP_full).reshape(lat.N, ref.n_p)
+    for s in range(lat.N):
+        for k, v in enumerate(lat.cell_corner_vertex[s]):
+            if v >= 0:
+                assert np.array_equal(up[s, k * d:(k + 1) * d], uc[s, ref.dof_p[k * d:(k + 1) * d]])
+
+
+def test_dirichlet_scaling_partition_of_unity_2d():
+    """In 2D every interface row couples exactly two copies, so sum_s B_d D B_d^T = I (Eq. 30)."""
+    lat = Lattice(W.config1())
+    M = (lat.Bd @ lat.Bd.T).toarray() @ np.diag(lat.D)
+    assert np.allclose(M, np.eye(lat.L))
