@@ -1,0 +1,214 @@
+/*
+ * fetidp.h -- C ABI of the GB300 (sm_103a) ROM-based inexact FETI-DP hot path.
+ *
+ * Method: Hirschler, Bouclier, Antolin, Buffa, "Reduced Order Modeling based
+ * Inexact FETI-DP solver for lattice structures" (arXiv 2308.11371).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Ownership   The caller owns every buffer it passes.  A context owns all of
+ *             its device workspace; it is allocated in fetidp_setup and freed
+ *             in fetidp_destroy.  No other entry point allocates device
+ *             memory.
+ * Pointers    Vectors are FP64.  Unless stated otherwise they are DEVICE
+ *             pointers on the device that was current at fetidp_setup.
+ * Streams     All work is enqueued on the stream given to fetidp_setup
+ *             (NULL = legacy default stream).  Entry points that return
+ *             host-visible results (fetidp_solve's info, fetidp_rom_data)
+ *             synchronise that stream; the others are asynchronous.
+ * Errors      Every call returns a fetidp_status and never aborts the process.
+ *             A CUDA error is reported as FETIDP_ECUDA; a non-finite value in
+ *             an input vector is not checked on the hot path.
+ * Layouts     n_rhs load cases ("RHS") are stored RHS-major:
+ *               multiplier vectors   lambda[rhs][L]
+ *               cell vectors         u[rhs][cell][n_dof]  (cell-duplicated,
+ *                                    local node-lexicographic order, x fastest,
+ *                                    displacement components interleaved)
+ *               primal vectors       uP[rhs][n_P]
+ *             Cell s = cx + nx*(cy + ny*cz).  Multiplier rows are ordered by
+ *             global node (lexicographic, x fastest), then by the chain pair,
+ *             then by component; see fetidp_problem for the row definition.
+ */
+#ifndef FETIDP_H
+#define FETIDP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fetidp_ctx fetidp_ctx;
+
+typedef enum {
+  FETIDP_OK = 0,
+  FETIDP_EINVAL = -1,      /* invalid argument or unsupported problem */
+  FETIDP_ENOMEM = -2,      /* device or host allocation failed */
+  FETIDP_ECUDA = -3,       /* a CUDA call failed (message: fetidp_last_error) */
+  FETIDP_ENOTCONV = -4,    /* iteration limit reached before the tolerance */
+  FETIDP_ETIMEOUT = -5,    /* a device-side wait exceeded its budget */
+  FETIDP_ESINGULAR = -6,   /* a principal factorisation or the coarse problem is not SPD */
+  FETIDP_EBREAKDOWN = -7   /* Krylov breakdown (p^T F p <= 0 or non-finite) */
+} fetidp_status;
+
+typedef enum {
+  FETIDP_FP64 = 0,         /* every step in FP64 */
+  FETIDP_MIXED_BF16 = 1    /* grouped principal contractions on tcgen05 in BF16 with FP32
+                              accumulation; Krylov recurrences, reductions, coarse solve,
+                              outer operator in FP64 */
+} fetidp_precision;
+
+/* One lattice problem (Sec. 2.1-2.2.1, Eqs. 1-6).  Host memory; copied at setup.
+ *
+ * Cells are images of one reference cell [0,1]^dim carrying elems^dim Q1
+ * elements (Eq. 6).  Lattice coordinate xi = (cx,cy,cz) + eta, physical
+ * x = F(xi) with the analytic macro map selected by map_kind:
+ *   0 identity
+ *   1 2D bend        x = (xi_x, xi_y + a sin(pi xi_x / L))          params a, L
+ *   2 3D shear+bend  x = xi + (g1 xi_z, g2 xi_z, a sin(pi xi_x / L))  params a, L, g1, g2
+ *   3 3D twist+bend  rotate (xi_y, xi_z) about (yc, zc) by tau xi_x / L, then add
+ *                    a sin(pi xi_x / L) to z                          params a, L, tau, yc, zc
+ * Material: isotropic, Poisson ratio nu (plane strain in 2D); Young's modulus
+ * at each Gauss point from the strut mask in cell-local eta (mask_kind
+ * 0 = 2D frame + diagonals, E_solid where distance <= r_cell[s] else E_void;
+ * 1 = 3D body-centred-cubic diagonals, same rule; 2 = BCC with
+ * E = E_void + (E_solid - E_void) sigmoid((r - dist) / mask_width)).
+ * Dirichlet: all DOF on the face xi_{clamp_axis} = (clamp_side ? n : 0) are 0.
+ * Loads: load_kind[l] = 0 traction of load_dir[l*dim..] per unit physical area
+ * on the face xi_{load_axis[l]} = (load_side[l] ? n : 0); 1 body force per unit
+ * physical volume.
+ * Multipliers (Eq. 14-15, P. 156): non-redundant -- for a non-corner interface
+ * node shared by cells s_1 < ... < s_m, rows u(s_j) - u(s_{j+1}) per component;
+ * every cell copy of a clamped non-corner node gets one row u(s) = 0.
+ * Primal DOF (Eq. 18): cell corners, assembled over free lattice vertices.
+ * ROM (Sec. 4.2, Algorithm 4): at most n_rb principal cells, greedy stops early
+ * when max ||Delta||_inf <= tol_rb.                                                 */
+typedef struct {
+  int dim;                  /* 2 or 3 */
+  int cells[3];             /* nx, ny, nz (nz = 1 in 2D) */
+  int elems;                /* Q1 elements per cell edge (>= 2) */
+  double nu, E_solid, E_void;
+  int mask_kind;
+  double mask_width;
+  const double *r_cell;     /* [N] strut radius per cell */
+  int map_kind;
+  double map_params[8];
+  int clamp_axis, clamp_side;
+  int n_loads;              /* number of load cases = RHS (>= 1) */
+  const int *load_kind;     /* [n_loads] */
+  const int *load_axis;     /* [n_loads] */
+  const int *load_side;     /* [n_loads] */
+  const double *load_dir;   /* [n_loads * dim] */
+  int n_rb;                 /* principal cells requested (>= 1) */
+  double tol_rb;
+} fetidp_problem;
+
+/* Solver options.  fetidp_default_options fills the defaults shown. */
+typedef struct {
+  double tol_outer;         /* FGMRES stop: ||b - A x|| / ||b|| (est.) <= tol_outer (1e-8) */
+  double tol_inner;         /* inner PCG stop: ||r_k|| / ||r_0|| <= tol_inner (1e-11; P. 579) */
+  int max_outer;            /* FGMRES iterations, no restart (50); sizes the Krylov storage */
+  int max_inner;            /* PCG iterations per preconditioner application (1000) */
+  int precision;            /* fetidp_precision (FETIDP_FP64) */
+  int fixed_outer;          /* > 0: run exactly this many outer iterations (iterate-locked) */
+  int fixed_inner;          /* > 0: run exactly this many PCG iterations per application */
+} fetidp_options;
+
+typedef struct {
+  int outer_its;            /* FGMRES iterations (max over RHS) */
+  int inner_its_total;      /* PCG iterations summed over preconditioner applications */
+  int n_rb;                 /* principal cells selected */
+  double rel_residual;      /* max over RHS of the true ||b - A x|| / ||b|| */
+  double t_setup_s, t_solve_s;
+  size_t device_bytes;      /* device workspace held by the context */
+} fetidp_info;
+
+/* Sizes of a context: out[0..11] = N cells, n_dof, n_i, n_d, n_p, n_r per cell,
+ * L multipliers, n_P primal DOF, n_rhs, n_rb selected, n_snap snapshot length,
+ * n_tot = N*n_r + n_P + L (outer Krylov vector length per RHS).             */
+fetidp_status fetidp_sizes(const fetidp_ctx *ctx, long long out[12]);
+
+void fetidp_default_options(fetidp_options *opt);
+
+/* Build the context for one lattice (n_problems must be 1): maps B, A_p, D
+ * (Eqs. 14-18); snapshots of C_hat at every Gauss point (Eq. 52); greedy
+ * principal cells and alpha (Algorithm 4, Eqs. 55-56); principal factorisations
+ * and operators (Eq. 39); pi, delta (Eqs. 40-42); ROM local operators and the
+ * coarse S_PP factorisation (Eq. 43, Sec. 3.2.1).  cuda_stream is a
+ * cudaStream_t (may be NULL).  On success *out owns all workspace.
+ * Errors: EINVAL (bad sizes, n_problems != 1), ENOMEM, ECUDA, ESINGULAR.     */
+fetidp_status fetidp_setup(const fetidp_problem *probs, int n_problems,
+                           const fetidp_options *opt, void *cuda_stream, fetidp_ctx **out);
+
+/* y = F_ring lambda (Eq. 48) for every RHS column: gather B_d^T, grouped
+ * principal contraction with delta, coarse correction through S_PP^{-1},
+ * scatter B_d.  lambda, y: device [n_rhs][L]; may not alias.                */
+fetidp_status fetidp_apply_F(fetidp_ctx *ctx, const double *lambda, double *y);
+
+/* z = M_D_ring^{-1} r (Eq. 49): D-scaled gather, alpha-combined principal
+ * Dirichlet Schur complements, D-scaled scatter.  r, z: device [n_rhs][L].  */
+fetidp_status fetidp_precond(fetidp_ctx *ctx, const double *r, double *z);
+
+/* Solve the saddle-point system of Eq. 16 by right-preconditioned flexible
+ * GMRES with the block preconditioner of Eq. 44 (Algorithms 1-3), x_0 = 0.
+ * u: device [n_rhs][N][n_dof] cell-duplicated displacements (out);
+ * lambda: device [n_rhs][L] multipliers (out), may be NULL.  info (host, may
+ * be NULL) receives iteration counts, residual and timings.
+ * Returns ENOTCONV when max_outer is reached above tol_outer (u still holds
+ * the last iterate), EBREAKDOWN on a Krylov breakdown.                       */
+fetidp_status fetidp_solve(fetidp_ctx *ctx, double *u, double *lambda, fetidp_info *info);
+
+/* Same as fetidp_solve with HOST output buffers (pageable or pinned); copies
+ * the results back inside the call (end-to-end measurement).               */
+fetidp_status fetidp_solve_host(fetidp_ctx *ctx, double *u_host, double *lambda_host,
+                                fetidp_info *info);
+
+/* Gradient of compliance w.r.t. the per-cell radii r_s: for every RHS,
+ * g[rhs][s] = - w_s^T (dK_s / dr_s) u_s with w = u when w == NULL (the
+ * compliance c = f^T u is self-adjoint).  u, w: device [n_rhs][N][n_dof] as
+ * returned by fetidp_solve; g: device [n_rhs][N].  Zero for hard masks.    */
+fetidp_status fetidp_grad(fetidp_ctx *ctx, const double *u, const double *w, double *g);
+
+/* ---- component entry points (the individual steps of the hot path) ---- */
+
+/* x_d = B_d^T lambda for every cell (Eq. 15): x_d device [n_rhs][N][n_d]
+ * (dual DOF in local order), lambda device [n_rhs][L].  Bit-exact.          */
+fetidp_status fetidp_gather_BT(fetidp_ctx *ctx, const double *lambda, double *x_d);
+
+/* z = sum_s B_d^(s) y_d^(s) (Eq. 15): y_d device [n_rhs][N][n_d], z device
+ * [n_rhs][L].  Row-wise, no atomics, bit-exact.                            */
+fetidp_status fetidp_scatter_B(fetidp_ctx *ctx, const double *y_d, double *z);
+
+/* y_s = K_s u_s for every cell (Eq. 5a with Eq. 52), matrix-free from the
+ * Gauss-point field C_hat: u, y device [n_rhs][N][n_dof] (natural order).   */
+fetidp_status fetidp_apply_K(fetidp_ctx *ctx, const double *u, double *y);
+
+/* x = S_PP_ring^{-1} b, the coarse solve of Sec. 3.2.1 (FP64 block cyclic
+ * reduction of the Cholesky-equivalent block factorisation): b, x device
+ * [n_rhs][n_P]; may alias.                                                   */
+fetidp_status fetidp_coarse_solve(fetidp_ctx *ctx, const double *b, double *x);
+
+/* x_r = K_rr_ring^{-ROM} v_r (Eq. 46a-b) for every cell: v, x device
+ * [n_rhs][N][n_r] in local (i, d) order.                                     */
+fetidp_status fetidp_local_rom_solve(fetidp_ctx *ctx, const double *v, double *x);
+
+/* y = A x with A the saddle-point matrix of Eq. 16, and y = P x with P the
+ * preconditioner of Eq. 44 (Algorithm 1).  x, y device [n_rhs][n_tot] laid
+ * out as (u_R [N][n_r] local (i,d) order, u_P [n_P], lambda [L]).           */
+fetidp_status fetidp_apply_A(fetidp_ctx *ctx, const double *x, double *y);
+fetidp_status fetidp_apply_P(fetidp_ctx *ctx, const double *x, double *y);
+
+/* Copy the ROM data to HOST buffers (any may be NULL): sigma [n_rb] principal
+ * cells, alpha / pi / delta [N][n_rb] (Eqs. 38, 41).  Synchronises.          */
+fetidp_status fetidp_rom_data(fetidp_ctx *ctx, int *sigma, double *alpha, double *pi,
+                              double *delta);
+
+void fetidp_destroy(fetidp_ctx *ctx);
+const char *fetidp_status_string(fetidp_status s);
+/* Last error message of this thread (CUDA error text or argument check). */
+const char *fetidp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FETIDP_H */

@@ -1,0 +1,202 @@
+// Internal declarations of the FETI-DP library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/fetidp.h"
+#include "geometry.cuh"
+
+namespace fetidp {
+
+void set_error(const std::string& msg);
+
+#define FD_CUDA(call)                                                        \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess) {                                                 \
+      ::fetidp::set_error(std::string(#call) + ": " + cudaGetErrorString(e_)); \
+      return FETIDP_ECUDA;                                                   \
+    }                                                                        \
+  } while (0)
+
+#define FD_CHECK_LAUNCH()                                                    \
+  do {                                                                       \
+    cudaError_t e_ = cudaGetLastError();                                     \
+    if (e_ != cudaSuccess) {                                                 \
+      ::fetidp::set_error(std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+      return FETIDP_ECUDA;                                                   \
+    }                                                                        \
+  } while (0)
+
+#define FD_TRY(expr)                              \
+  do {                                            \
+    fetidp_status s_ = (expr);                    \
+    if (s_ != FETIDP_OK) return s_;               \
+  } while (0)
+
+// Per-cell vector view: element (rhs, cell, i) at p[rhs*rs + cell*cs + i].
+struct CellVec {
+  double* p;
+  long long rs;   // RHS stride
+  int cs;         // cell stride
+};
+struct CCellVec {
+  const double* p;
+  long long rs;
+  int cs;
+};
+inline CCellVec cview(const CellVec& v) { return {v.p, v.rs, v.cs}; }
+
+// Block cyclic reduction of the block-tridiagonal coarse matrix (slab ordering).
+struct CoarseBCR {
+  int b = 0;                       // block (slab) size in DOF
+  int nb = 0;                      // slabs at level 0
+  int levels = 0;                  // reductions until one block remains
+  std::vector<int> n_at;           // blocks at level l (levels + 1 entries)
+  std::vector<long long> vec_off;  // offset of level l in the per-RHS level vectors
+  long long vec_len = 0;           // per-RHS length of all level vectors
+  // matrices, FP64 row-major b x b; per level l and odd j:
+  //   Ainv_j at mat_off[l][j], U_j (if j+1 < n), U_j^T, V_j, V_j^T
+  std::vector<std::vector<long long>> off_Ainv, off_U, off_UT, off_V, off_VT;
+  long long off_final = 0;         // Ainv of the last remaining block
+  double* mats = nullptr;          // device
+  long long* tables = nullptr;     // device offsets: per level A, U, UT, V, VT arrays of n entries
+  int* perm = nullptr;             // device [nb*b]: slab-ordered position -> primal DOF
+  double* bl = nullptr;            // device [m][vec_len] right-hand sides per level
+  double* xl = nullptr;            // device [m][vec_len] solutions per level
+  size_t mat_bytes = 0;
+};
+
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  Geo geo{};
+  fetidp_options opt{};
+  // sizes
+  int d = 0, e = 0, n = 0, ni = 0, nd = 0, np = 0, nr = 0, ncorner = 0;
+  int nelem = 0, ngp = 0, nc = 0;
+  long long nsnap = 0;
+  long long N = 0, L = 0, nP = 0, ntot = 0;
+  int m = 0;        // RHS
+  int nrb = 0;      // principal cells selected
+  int nV = 0;       // free lattice vertices
+  int clamp_axis = 0, clamp_side = 0;
+  std::vector<int> sigma;
+  std::vector<double> r_cell;
+  double t_setup_s = 0.0;
+  size_t device_bytes = 0;
+  std::vector<void*> allocations;
+
+  // reference-cell tables
+  int* perm = nullptr;        // [2n]: local (i,d,p) index -> natural index node*d + c,
+                              //       then the inverse permutation
+  // lattice maps
+  int* gath = nullptr;        // [N*nd*2] signed (row+1) codes, 0 = none (B_d^T)
+  int* scat = nullptr;        // [L*2] signed (cell*nd + j + 1) codes, 0 = none (B_d)
+  double* Dw = nullptr;       // [L] scaling D
+  int* corner_v = nullptr;    // [N*ncorner] free vertex index or -1 (A_p)
+  int* vert_cells = nullptr;  // [nV*ncorner] (cell*ncorner + k) or -1 (A_p^T gather)
+  double* r_dev = nullptr;    // [N]
+  // snapshots = C_hat at every Gauss point, [N][nsnap]
+  double* snap = nullptr;
+  // ROM coefficients [N][nrb]
+  double* alpha = nullptr;
+  double* pi = nullptr;
+  double* delta = nullptr;
+  // principal operators (FP64)
+  double* Kinv = nullptr;     // [nrb][nr][nr]  K_rr^(sigma_k)^{-1}
+  double* Urp = nullptr;      // [nrb][nr][np]
+  double* UrpT = nullptr;     // [nrb][np][nr]
+  double* Sdd = nullptr;      // [nrb][nd][nd]  = F_dd^{-1}
+  // ROM per-cell operators (assembled, Eq. 43)
+  double* Fdd_c = nullptr;    // [N][nd][nd]
+  double* Sdd_c = nullptr;    // [N][nd][nd]
+  double* Urp_c = nullptr;    // [N][nr][np]
+  double* UrpT_c = nullptr;   // [N][np][nr]
+  // coarse solve
+  CoarseBCR bcr;
+  // right-hand side of Eq. 16: [m][ntot] = (f_R, f_P, d = 0)
+  double* rhs = nullptr;
+  // workspace
+  double* w_cell_a = nullptr;   // [m][N][max(n, nr)]
+  double* w_cell_b = nullptr;   // [m][N][max(n, nr)]
+  double* w_d1 = nullptr;       // [m][N][nd]
+  double* w_d2 = nullptr;       // [m][N][nd]
+  double* w_p1 = nullptr;       // [m][N][np]
+  double* w_P1 = nullptr;       // [m][nP]
+  double* w_P2 = nullptr;       // [m][nP]
+  double* w_zP = nullptr;       // [m][nP]  coarse solution shared by Algorithms 2 and 3
+  double* w_L1 = nullptr;       // [m][L]
+  double* w_R = nullptr;        // [m][N][nrb][nr]  local ROM bases (Eq. 46a)
+  double* w_KR = nullptr;       // [m][N][nrb][nr]  K_s R
+  double* w_tot = nullptr;      // [m][ntot] x 3 (preconditioner scratch)
+  // Krylov storage
+  double* V = nullptr;          // [(max_outer+1)][m][ntot]
+  double* Z = nullptr;          // [max_outer][m][ntot]
+  double* pcg = nullptr;        // [6][m][L]: x, r, z, p, q, right-hand side
+  double* red = nullptr;        // reduction scratch (partials + scalars)
+  unsigned int* red_count = nullptr;
+  double* scal = nullptr;       // device scalars [64][m]
+  double* h_scal = nullptr;     // pinned host mirror
+  int inner_total = 0;
+};
+
+// ---------------------------------------------------------------- allocation
+fetidp_status dalloc(Ctx& c, void** p, size_t bytes);
+template <typename T>
+fetidp_status dalloc_t(Ctx& c, T** p, size_t count) {
+  return dalloc(c, reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+// ---------------------------------------------------------------- kernels (maps, vectors)
+fetidp_status k_gather_BT(Ctx& c, const double* lam, long long lam_rs, const double* scale,
+                          CellVec out_d, int nrhs, double beta);
+fetidp_status k_scatter_B(Ctx& c, CCellVec yd, double* out, long long out_rs, const double* scale,
+                          double alpha, double beta, int nrhs);
+fetidp_status k_primal_assemble(Ctx& c, CCellVec cp, double* out, long long out_rs, double alpha,
+                                double beta, int nrhs);
+fetidp_status k_primal_extract(Ctx& c, const double* uP, long long uP_rs, CellVec cp, int nrhs);
+fetidp_status k_dot(Ctx& c, const double* x, long long xs, const double* y, long long ys,
+                    long long len, int nrhs, double* out);
+fetidp_status k_multi_dot(Ctx& c, const double* Vb, long long vstride, int nv, const double* w,
+                          long long len, int nrhs, double* out);
+fetidp_status k_multi_axpy(Ctx& c, const double* Vb, long long vstride, int nv, const double* coef,
+                           double* w, long long len, int nrhs, double sign);
+fetidp_status k_copy_scale(Ctx& c, const double* x, double* y, long long len, int nrhs,
+                           long long xs, long long ys, const double* s_dev, double s_host);
+
+// ---------------------------------------------------------------- kernels (cell-level compute)
+fetidp_status k_snapshots(Ctx& c);
+fetidp_status k_apply_K(Ctx& c, CCellVec u, CellVec y, int nvec_per_col, int ncols, bool idp,
+                        bool r_only, const double* chat, double chat_scale_dr);
+fetidp_status k_cell_gemv_strided(Ctx& c, const double* mats, long long mstride, int ld, int mrows,
+                                  int mcols, CCellVec x, CellVec y, double alpha, double beta,
+                                  int nrhs);
+fetidp_status k_grouped_gemm(Ctx& c, const double* A, long long a_stride_k, int lda, int M, int K,
+                             CCellVec X, CellVec Y, const double* coef, double alpha, double beta,
+                             int nrhs, bool separate, long long y_k_stride);
+fetidp_status k_grouped_gemm_n(Ctx& c, const double* A, long long a_stride_k, int lda, int M,
+                               int K, int nk, CCellVec X, CellVec Y, const double* coef,
+                               double alpha, double beta, long long ncell, int nrhs, bool separate,
+                               long long y_k_stride);
+fetidp_status k_gram_solve(Ctx& c, const double* R, const double* KR, CCellVec v, CellVec x,
+                           int nrhs);
+fetidp_status k_grad(Ctx& c, const double* u, const double* w, double* g);
+
+// ---------------------------------------------------------------- setup / coarse
+fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_options& o);
+fetidp_status coarse_setup(Ctx& c, const std::vector<double>& Spp_cells);
+fetidp_status coarse_solve(Ctx& c, const double* b, long long b_rs, double* x, long long x_rs,
+                           int nrhs);
+
+// ---------------------------------------------------------------- operators (solver.cu)
+fetidp_status op_apply_F(Ctx& c, const double* lam, long long lam_rs, double* y, long long y_rs);
+fetidp_status op_apply_MD(Ctx& c, const double* r, long long r_rs, double* z, long long z_rs);
+fetidp_status op_apply_A(Ctx& c, const double* x, double* y);
+fetidp_status op_precondition(Ctx& c, const double* x, double* y);
+fetidp_status pcg_solve(Ctx& c, const double* b, long long b_rs, double* x, long long x_rs);
+
+}  // namespace fetidp

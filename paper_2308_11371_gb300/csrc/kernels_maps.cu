@@ -1,0 +1,272 @@
+// Integer-indexed maps of the FETI-DP hot path and FP64 vector kernels.
+//
+// * B_d^T gather and B_d scatter (Eq. 15; used in Eqs. 48-49 and Algorithm 3):
+//   both are written as row-wise gathers over at most two signed terms in a
+//   fixed order, so they are bit-exact and need no atomics.
+// * A_p assembly / extraction of corner values (Eq. 18).
+// * Deterministic FP64 reductions for the Krylov recurrences: a fixed
+//   partition into kRedBlocks blocks, warp-shuffle trees, then the partials
+//   summed in block order by a second kernel.
+#include "common.cuh"
+
+namespace fetidp {
+
+namespace {
+
+constexpr int kRedBlocks = 304;   // 2 x 152 SMs
+constexpr int kRedThreads = 256;
+
+__global__ void gather_BT_kernel(const int* __restrict__ gath, const double* __restrict__ lam,
+                                 long long lam_rs, const double* __restrict__ scale,
+                                 double* __restrict__ out, long long out_rs, int out_cs, int nd,
+                                 long long ncell, int nrhs, double beta) {
+  const long long total = ncell * nd;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total * nrhs;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int rhs = (int)(t / total);
+    const long long cj = t - rhs * total;
+    const long long cell = cj / nd;
+    const int j = (int)(cj - cell * nd);
+    const int c0 = gath[2 * cj], c1 = gath[2 * cj + 1];
+    const double* l = lam + rhs * lam_rs;
+    double v = 0.0;
+    if (c0 != 0) {
+      const int row = (c0 > 0 ? c0 : -c0) - 1;
+      const double x = scale ? scale[row] * l[row] : l[row];
+      v = c0 > 0 ? x : -x;
+    }
+    if (c1 != 0) {
+      const int row = (c1 > 0 ? c1 : -c1) - 1;
+      const double x = scale ? scale[row] * l[row] : l[row];
+      v += c1 > 0 ? x : -x;
+    }
+    double* o = out + rhs * out_rs + cell * out_cs + j;
+    *o = (beta == 0.0) ? v : v + beta * (*o);
+  }
+}
+
+__global__ void scatter_B_kernel(const int* __restrict__ scat, const double* __restrict__ yd,
+                                 long long y_rs, int y_cs, int nd, const double* __restrict__ scale,
+                                 double* __restrict__ out, long long out_rs, long long L,
+                                 double alpha, double beta, int nrhs) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < L * nrhs;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int rhs = (int)(t / L);
+    const long long row = t - rhs * L;
+    const double* y = yd + rhs * y_rs;
+    double v = 0.0;
+    const int c0 = scat[2 * row], c1 = scat[2 * row + 1];
+    if (c0 != 0) {
+      const long long idx = (c0 > 0 ? c0 : -c0) - 1;
+      const long long cell = idx / nd;
+      const double x = y[cell * y_cs + (idx - cell * nd)];
+      v = c0 > 0 ? x : -x;
+    }
+    if (c1 != 0) {
+      const long long idx = (c1 > 0 ? c1 : -c1) - 1;
+      const long long cell = idx / nd;
+      const double x = y[cell * y_cs + (idx - cell * nd)];
+      v += c1 > 0 ? x : -x;
+    }
+    if (scale) v *= scale[row];
+    double* o = out + rhs * out_rs + row;
+    *o = (beta == 0.0) ? alpha * v : alpha * v + beta * (*o);
+  }
+}
+
+__global__ void primal_assemble_kernel(const int* __restrict__ vert_cells, int ncorner, int d,
+                                       const double* __restrict__ cp, long long c_rs, int c_cs,
+                                       double* __restrict__ out, long long out_rs, int nV,
+                                       double alpha, double beta, int nrhs) {
+  const long long total = (long long)nV * d;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total * nrhs;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int rhs = (int)(t / total);
+    const long long vc = t - rhs * total;
+    const int v = (int)(vc / d), comp = (int)(vc - (long long)v * d);
+    double s = 0.0;
+    for (int q = 0; q < ncorner; ++q) {
+      const int code = vert_cells[v * ncorner + q];
+      if (code < 0) continue;
+      const long long cell = code / ncorner;
+      const int k = code - (int)cell * ncorner;
+      s += cp[rhs * c_rs + cell * c_cs + k * d + comp];
+    }
+    double* o = out + rhs * out_rs + vc;
+    *o = (beta == 0.0) ? alpha * s : alpha * s + beta * (*o);
+  }
+}
+
+__global__ void primal_extract_kernel(const int* __restrict__ corner_v, int ncorner, int d,
+                                      const double* __restrict__ uP, long long uP_rs,
+                                      double* __restrict__ cp, long long c_rs, int c_cs,
+                                      long long ncell, int nrhs) {
+  const int npc = ncorner * d;
+  const long long total = ncell * npc;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total * nrhs;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int rhs = (int)(t / total);
+    const long long ck = t - rhs * total;
+    const long long cell = ck / npc;
+    const int q = (int)(ck - cell * npc);
+    const int k = q / d, comp = q - k * d;
+    const int v = corner_v[cell * ncorner + k];
+    cp[rhs * c_rs + cell * c_cs + q] = v >= 0 ? uP[rhs * uP_rs + (long long)v * d + comp] : 0.0;
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+    r = warp_sum(r);
+  }
+  __syncthreads();
+  return r;
+}
+
+// partial[(rhs*nv + i)*kRedBlocks + blk] = sum over this block's fixed slice of V_i . w
+__global__ void multi_dot_partial(const double* __restrict__ Vb, long long vstride, long long vrs,
+                                  const double* __restrict__ w, long long wrs, long long len,
+                                  int nv, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const int i = blockIdx.z, rhs = blockIdx.y, blk = blockIdx.x;
+  const double* v = Vb + i * vstride + rhs * vrs;
+  const double* x = w + rhs * wrs;
+  const long long chunk = (len + kRedBlocks - 1) / kRedBlocks;
+  const long long beg = blk * chunk;
+  const long long end = beg + chunk < len ? beg + chunk : len;
+  double s = 0.0;
+  for (long long t = beg + threadIdx.x; t < end; t += blockDim.x) s += v[t] * x[t];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partial[((long long)rhs * nv + i) * kRedBlocks + blk] = s;
+}
+
+__global__ void reduce_partials(const double* __restrict__ partial, int count,
+                                double* __restrict__ out) {
+  __shared__ double sh[32];
+  const int k = blockIdx.x;
+  double s = 0.0;
+  // fixed assignment of partials to threads, then a fixed tree
+  for (int t = threadIdx.x; t < kRedBlocks; t += blockDim.x) s += partial[(long long)k * kRedBlocks + t];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) out[k] = s;
+  (void)count;
+}
+
+__global__ void multi_axpy_kernel(const double* __restrict__ Vb, long long vstride, long long vrs,
+                                  int nv, const double* __restrict__ coef, double* __restrict__ w,
+                                  long long wrs, long long len, int nrhs, double sign) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len * nrhs;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int rhs = (int)(t / len);
+    const long long q = t - rhs * len;
+    double s = 0.0;
+    for (int i = 0; i < nv; ++i) s += coef[rhs * nv + i] * Vb[i * vstride + rhs * vrs + q];
+    w[rhs * wrs + q] += sign * s;
+  }
+}
+
+__global__ void copy_scale_kernel(const double* __restrict__ x, double* __restrict__ y,
+                                  long long len, int nrhs, long long xs, long long ys,
+                                  const double* __restrict__ s_dev, double s_host) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len * nrhs;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int rhs = (int)(t / len);
+    const long long q = t - rhs * len;
+    const double s = s_dev ? s_dev[rhs] : s_host;
+    y[rhs * ys + q] = s * x[rhs * xs + q];
+  }
+}
+
+inline int grid_for(long long work, int threads = 256) {
+  long long g = (work + threads - 1) / threads;
+  if (g > 152LL * 16) g = 152LL * 16;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+fetidp_status k_gather_BT(Ctx& c, const double* lam, long long lam_rs, const double* scale,
+                          CellVec out, int nrhs, double beta) {
+  const long long work = c.N * c.nd * nrhs;
+  gather_BT_kernel<<<grid_for(work), 256, 0, c.stream>>>(c.gath, lam, lam_rs, scale, out.p, out.rs,
+                                                          out.cs, c.nd, c.N, nrhs, beta);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_scatter_B(Ctx& c, CCellVec yd, double* out, long long out_rs, const double* scale,
+                          double alpha, double beta, int nrhs) {
+  scatter_B_kernel<<<grid_for(c.L * nrhs), 256, 0, c.stream>>>(
+      c.scat, yd.p, yd.rs, yd.cs, c.nd, scale, out, out_rs, c.L, alpha, beta, nrhs);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_primal_assemble(Ctx& c, CCellVec cp, double* out, long long out_rs, double alpha,
+                                double beta, int nrhs) {
+  primal_assemble_kernel<<<grid_for((long long)c.nV * c.d * nrhs), 256, 0, c.stream>>>(
+      c.vert_cells, c.ncorner, c.d, cp.p, cp.rs, cp.cs, out, out_rs, c.nV, alpha, beta, nrhs);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_primal_extract(Ctx& c, const double* uP, long long uP_rs, CellVec cp, int nrhs) {
+  primal_extract_kernel<<<grid_for(c.N * c.np * nrhs), 256, 0, c.stream>>>(
+      c.corner_v, c.ncorner, c.d, uP, uP_rs, cp.p, cp.rs, cp.cs, c.N, nrhs);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+// out[rhs*nv + i] = V_i[rhs] . w[rhs]; V_i at Vb + i*vstride + rhs*len_rs.
+static fetidp_status multi_dot_impl(Ctx& c, const double* Vb, long long vstride, long long vrs,
+                                    int nv, const double* w, long long wrs, long long len,
+                                    int nrhs, double* out) {
+  dim3 grid(kRedBlocks, nrhs, nv);
+  multi_dot_partial<<<grid, kRedThreads, 0, c.stream>>>(Vb, vstride, vrs, w, wrs, len, nv, c.red);
+  FD_CHECK_LAUNCH();
+  reduce_partials<<<nrhs * nv, kRedThreads, 0, c.stream>>>(c.red, nrhs * nv, out);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_dot(Ctx& c, const double* x, long long xs, const double* y, long long ys,
+                    long long len, int nrhs, double* out) {
+  return multi_dot_impl(c, x, 0, xs, 1, y, ys, len, nrhs, out);
+}
+
+fetidp_status k_multi_dot(Ctx& c, const double* Vb, long long vstride, int nv, const double* w,
+                          long long len, int nrhs, double* out) {
+  // Krylov vectors: V_i[rhs] at Vb + i*vstride + rhs*len; w[rhs] at w + rhs*len
+  return multi_dot_impl(c, Vb, vstride, len, nv, w, len, len, nrhs, out);
+}
+
+fetidp_status k_multi_axpy(Ctx& c, const double* Vb, long long vstride, int nv, const double* coef,
+                           double* w, long long len, int nrhs, double sign) {
+  multi_axpy_kernel<<<grid_for(len * nrhs), 256, 0, c.stream>>>(Vb, vstride, len, nv, coef, w, len,
+                                                                 len, nrhs, sign);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_copy_scale(Ctx& c, const double* x, double* y, long long len, int nrhs,
+                           long long xs, long long ys, const double* s_dev, double s_host) {
+  copy_scale_kernel<<<grid_for(len * nrhs), 256, 0, c.stream>>>(x, y, len, nrhs, xs, ys, s_dev,
+                                                                 s_host);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+}  // namespace fetidp

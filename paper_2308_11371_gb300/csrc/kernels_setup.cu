@@ -1,0 +1,246 @@
+// Setup kernels: greedy selection (Algorithm 4), trace tables for the
+// projections of Eq. 42, and assembly of the ROM local operators (Eq. 43).
+//
+// The projections use that K^(s) is linear in C_hat (Eq. 52): every trace
+// tr(U_i^T K^(s) U_j) equals sum over Gauss points and tensor entries of
+// C_hat^(s) times a cell-independent table built from the gradients of the
+// principal columns, so all cells' Gram matrices come out of one GEMM
+// against the snapshot matrix.
+#include "common.cuh"
+
+namespace fetidp {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double bsum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r += sh[k];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ double bmax(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r = fmax(r, sh[k]);
+  __syncthreads();
+  return r;
+}
+
+// out[row] = ||X[row]||_2 (mode 0), ||X[row]||_inf (mode 1), X[row] . z (mode 2)
+__global__ void row_reduce_kernel(const double* __restrict__ X, long long len,
+                                  const double* __restrict__ z, int mode, double* __restrict__ out) {
+  __shared__ double sh[32];
+  const double* x = X + blockIdx.x * len;
+  double acc = 0.0;
+  for (long long t = threadIdx.x; t < len; t += blockDim.x) {
+    const double v = x[t];
+    if (mode == 0) acc += v * v;
+    else if (mode == 1) acc = fmax(acc, fabs(v));
+    else acc += v * z[t];
+  }
+  const double r = (mode == 1) ? bmax(acc, sh) : bsum(acc, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = (mode == 0) ? sqrt(r) : r;
+}
+
+// Delta = A / norm (rows)
+__global__ void row_normalise_kernel(const double* __restrict__ A, const double* __restrict__ nrm,
+                                     double* __restrict__ D, long long len, long long rows) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < rows * len;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long r = t / len;
+    D[t] = A[t] / nrm[r];
+  }
+}
+
+// Delta[row] -= beta[row] * zeta
+__global__ void row_update_kernel(double* __restrict__ D, const double* __restrict__ beta,
+                                  const double* __restrict__ zeta, long long len, long long rows) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < rows * len;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long r = t / len;
+    D[t] -= beta[r] * zeta[t - r * len];
+  }
+}
+
+__global__ void scale_copy_kernel(const double* __restrict__ x, const double* __restrict__ s,
+                                  double* __restrict__ y, long long len) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len;
+       t += (long long)gridDim.x * blockDim.x)
+    y[t] = x[t] / s[0];
+}
+
+// Reference gradients G_ia (xi-derivatives) of column vectors at every Gauss point.
+// Column (k, l): values at local (i,d,p) index li taken from
+//   mode 0: src[k*kstride + l*lstride + li] for li < len_in, 0 otherwise
+//   mode 1: unit vector at local index unit_base + l
+// out[((k*ncol + l)*nelem + el)*ngp + gp][d*d]
+template <int D>
+__global__ void column_gradients_kernel(int e, int n, const int* __restrict__ iperm,
+                                        const double* __restrict__ src, long long kstride,
+                                        long long lstride, int len_in, int mode, int unit_base,
+                                        int nk, int ncol, double inv_h, double* __restrict__ out) {
+  constexpr int NA = 1 << D;
+  const int nelem = e * e * (D == 3 ? e : 1);
+  const long long total = (long long)nk * ncol * nelem * NA;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int gp = (int)(t % NA);
+    long long r = t / NA;
+    const int el = (int)(r % nelem);
+    r /= nelem;
+    const int l = (int)(r % ncol);
+    const int k = (int)(r / ncol);
+    const int ex = el % e, ey = (el / e) % e, ez = el / (e * e);
+    double tq[D];
+    for (int q = 0; q < D; ++q) tq[q] = gauss_t((gp >> q) & 1);
+    double G[D * D];
+    for (int q = 0; q < D * D; ++q) G[q] = 0.0;
+    for (int A = 0; A < NA; ++A) {
+      const int ax = A & 1, ay = (A >> 1) & 1, az = (A >> 2) & 1;
+      const int node = (ex + ax) + (e + 1) * ((ey + ay) + (e + 1) * (D == 3 ? (ez + az) : 0));
+      double dn[D];
+      for (int a = 0; a < D; ++a) {
+        double v = inv_h;
+        for (int q = 0; q < D; ++q) {
+          const int off = (A >> q) & 1;
+          if (q == a) v *= off ? 1.0 : -1.0;
+          else v *= off ? tq[q] : 1.0 - tq[q];
+        }
+        dn[a] = v;
+      }
+      for (int i = 0; i < D; ++i) {
+        const int li = iperm[node * D + i];
+        double uv;
+        if (mode == 0) uv = li < len_in ? src[k * kstride + l * lstride + li] : 0.0;
+        else uv = (li == unit_base + l) ? 1.0 : 0.0;
+        for (int a = 0; a < D; ++a) G[i * D + a] += uv * dn[a];
+      }
+    }
+    (void)n;
+    double* o = out + t * (D * D);
+    for (int q = 0; q < D * D; ++q) o[q] = G[q];
+  }
+}
+
+// Table row (i, j): T[(el*ngp + gp)*nc + c] = wq sum_l [Gi_I Gj_J + (I != J) Gi_J Gj_I]
+__global__ void trace_table_kernel(const double* __restrict__ Gi, const double* __restrict__ Gj,
+                                   int ncol, int nqp, int d, double wq, double* __restrict__ T) {
+  const int dd = d * d;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nqp;
+       t += (long long)gridDim.x * blockDim.x) {
+    double acc[45];
+    const int nc = dd * (dd + 1) / 2;
+    for (int c = 0; c < nc; ++c) acc[c] = 0.0;
+    for (int l = 0; l < ncol; ++l) {
+      const double* gi = Gi + ((long long)l * nqp + t) * dd;
+      const double* gj = Gj + ((long long)l * nqp + t) * dd;
+      int c = 0;
+      for (int I = 0; I < dd; ++I)
+        for (int J = I; J < dd; ++J) {
+          double v = gi[I] * gj[J];
+          if (J != I) v += gi[J] * gj[I];
+          acc[c++] += v;
+        }
+    }
+    for (int c = 0; c < nc; ++c) T[t * nc + c] = wq * acc[c];
+  }
+}
+
+// out[cell][r][c] = sum_k coef[cell][k] src[k*kstride + (r0 + r)*ld + c0 + c]
+__global__ void rom_combine_kernel(const double* __restrict__ src, long long kstride, int ld,
+                                   int r0, int c0, int rows, int cols,
+                                   const double* __restrict__ coef, int nrb, long long ncell,
+                                   double* __restrict__ out, bool transpose) {
+  const long long per = (long long)rows * cols;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ncell * per;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long cell = t / per;
+    const long long q = t - cell * per;
+    const int r = (int)(q / cols), cc = (int)(q - (long long)r * cols);
+    double s = 0.0;
+    for (int k = 0; k < nrb; ++k)
+      s += coef[cell * nrb + k] * src[k * kstride + (long long)(r0 + r) * ld + c0 + cc];
+    if (transpose) out[cell * per + (long long)cc * rows + r] = s;
+    else out[t] = s;
+  }
+}
+
+inline int gridn(long long work) {
+  long long g = (work + kThreads - 1) / kThreads;
+  if (g > 152LL * 32) g = 152LL * 32;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+fetidp_status k_row_reduce(Ctx& c, const double* X, long long rows, long long len, const double* z,
+                           int mode, double* out) {
+  row_reduce_kernel<<<(unsigned)rows, kThreads, 0, c.stream>>>(X, len, z, mode, out);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_row_normalise(Ctx& c, const double* A, const double* nrm, double* D, long long rows,
+                              long long len) {
+  row_normalise_kernel<<<gridn(rows * len), kThreads, 0, c.stream>>>(A, nrm, D, len, rows);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_row_update(Ctx& c, double* D, const double* beta, const double* zeta,
+                           long long rows, long long len) {
+  row_update_kernel<<<gridn(rows * len), kThreads, 0, c.stream>>>(D, beta, zeta, len, rows);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_scale_copy(Ctx& c, const double* x, const double* s, double* y, long long len) {
+  scale_copy_kernel<<<gridn(len), kThreads, 0, c.stream>>>(x, s, y, len);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_column_gradients(Ctx& c, const double* src, long long kstride, long long lstride,
+                                 int len_in, int mode, int unit_base, int nk, int ncol,
+                                 double* out) {
+  const double inv_h = (double)c.e;
+  const long long work = (long long)nk * ncol * c.nelem * c.ngp;
+  if (c.d == 2)
+    column_gradients_kernel<2><<<gridn(work), kThreads, 0, c.stream>>>(
+        c.e, c.n, c.perm + c.n, src, kstride, lstride, len_in, mode, unit_base, nk, ncol, inv_h, out);
+  else
+    column_gradients_kernel<3><<<gridn(work), kThreads, 0, c.stream>>>(
+        c.e, c.n, c.perm + c.n, src, kstride, lstride, len_in, mode, unit_base, nk, ncol, inv_h, out);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_trace_table(Ctx& c, const double* Gi, const double* Gj, int ncol, double* T) {
+  const int nqp = c.nelem * c.ngp;
+  const double wq = pow(0.5 / c.e, c.d);
+  trace_table_kernel<<<gridn(nqp), 128, 0, c.stream>>>(Gi, Gj, ncol, nqp, c.d, wq, T);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_rom_combine(Ctx& c, const double* src, long long kstride, int ld, int r0, int c0,
+                            int rows, int cols, const double* coef, double* out, bool transpose) {
+  rom_combine_kernel<<<gridn(c.N * rows * cols), kThreads, 0, c.stream>>>(
+      src, kstride, ld, r0, c0, rows, cols, coef, c.nrb, c.N, out, transpose);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+}  // namespace fetidp

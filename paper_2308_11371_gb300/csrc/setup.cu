@@ -1,0 +1,618 @@
+// Setup phase of the ROM-based inexact FETI-DP solver.
+//
+// Host C++ builds the integer maps (Eqs. 12-18), the loads (Eq. 5b) and the
+// O(N_rb) principal work (Eq. 39 factorisations); the O(N) work runs on the
+// GPU: snapshots (Eq. 52), the greedy passes of Algorithm 4, the projection
+// traces of Eq. 42 (one GEMM against the snapshot matrix) and the ROM local
+// operators of Eq. 43.
+#include <chrono>
+#include <cstring>
+#include <map>
+
+#include "common.cuh"
+#include "host_linalg.h"
+
+namespace fetidp {
+
+fetidp_status k_row_reduce(Ctx& c, const double* X, long long rows, long long len, const double* z,
+                           int mode, double* out);
+fetidp_status k_row_normalise(Ctx& c, const double* A, const double* nrm, double* D, long long rows,
+                              long long len);
+fetidp_status k_row_update(Ctx& c, double* D, const double* beta, const double* zeta,
+                           long long rows, long long len);
+fetidp_status k_scale_copy(Ctx& c, const double* x, const double* s, double* y, long long len);
+fetidp_status k_column_gradients(Ctx& c, const double* src, long long kstride, long long lstride,
+                                 int len_in, int mode, int unit_base, int nk, int ncol, double* out);
+fetidp_status k_trace_table(Ctx& c, const double* Gi, const double* Gj, int ncol, double* T);
+fetidp_status k_rom_combine(Ctx& c, const double* src, long long kstride, int ld, int r0, int c0,
+                            int rows, int cols, const double* coef, double* out, bool transpose);
+
+namespace {
+
+constexpr double kTieRel = 1e-12;     // greedy argmax ties (lowest cell index wins)
+constexpr double kDropRel = 1e-12;    // pivot drop of the N_rb x N_rb Gram systems
+
+struct RefCell {
+  std::vector<int> perm;        // idp -> natural
+  std::vector<int> iperm;       // natural -> idp
+  std::vector<int> dual_pos;    // node -> position among dual nodes, or -1
+  std::vector<int> corner_pos;  // node -> corner index, or -1
+};
+
+RefCell build_ref(int d, int e, int& ni, int& nd, int& np) {
+  RefCell R;
+  const int nn1 = e + 1;
+  const int nnode = d == 2 ? nn1 * nn1 : nn1 * nn1 * nn1;
+  std::vector<int> cls(nnode);
+  for (int nidx = 0; nidx < nnode; ++nidx) {
+    const int ijk[3] = {nidx % nn1, (nidx / nn1) % nn1, nidx / (nn1 * nn1)};
+    int nb = 0;
+    for (int k = 0; k < d; ++k) nb += (ijk[k] == 0 || ijk[k] == e) ? 1 : 0;
+    cls[nidx] = nb == d ? 2 : (nb > 0 ? 1 : 0);
+  }
+  R.dual_pos.assign(nnode, -1);
+  R.corner_pos.assign(nnode, -1);
+  int cnt[3] = {0, 0, 0};
+  for (int nidx = 0; nidx < nnode; ++nidx) {
+    if (cls[nidx] == 1) R.dual_pos[nidx] = cnt[1];
+    if (cls[nidx] == 2) R.corner_pos[nidx] = cnt[2];
+    cnt[cls[nidx]]++;
+  }
+  for (int cl = 0; cl < 3; ++cl)
+    for (int nidx = 0; nidx < nnode; ++nidx)
+      if (cls[nidx] == cl)
+        for (int comp = 0; comp < d; ++comp) R.perm.push_back(nidx * d + comp);
+  R.iperm.assign(R.perm.size(), 0);
+  for (size_t i = 0; i < R.perm.size(); ++i) R.iperm[R.perm[i]] = (int)i;
+  ni = cnt[0] * d;
+  nd = cnt[1] * d;
+  np = cnt[2] * d;
+  return R;
+}
+
+// Element matrix contributions from C_hat of one cell, assembled densely (natural order).
+void assemble_dense_K(const Ctx& c, const double* chat, std::vector<double>& K) {
+  const int d = c.d, e = c.e, n = c.n, NA = 1 << d;
+  K.assign((size_t)n * n, 0.0);
+  const double h = 1.0 / e, wq = std::pow(0.5 * h, d);
+  const int ni2 = d * d;
+  for (int el = 0; el < c.nelem; ++el) {
+    const int ex = el % e, ey = (el / e) % e, ez = el / (e * e);
+    int nodes[8];
+    for (int A = 0; A < NA; ++A) {
+      const int ax = A & 1, ay = (A >> 1) & 1, az = (A >> 2) & 1;
+      nodes[A] = (ex + ax) + (e + 1) * ((ey + ay) + (e + 1) * (d == 3 ? (ez + az) : 0));
+    }
+    for (int gp = 0; gp < NA; ++gp) {
+      double t[3];
+      for (int k = 0; k < d; ++k) t[k] = gauss_t((gp >> k) & 1);
+      double dN[8][3];
+      for (int A = 0; A < NA; ++A)
+        for (int a = 0; a < d; ++a) {
+          double v = 1.0 / h;
+          for (int k = 0; k < d; ++k) {
+            const int off = (A >> k) & 1;
+            v *= (k == a) ? (off ? 1.0 : -1.0) : (off ? t[k] : 1.0 - t[k]);
+          }
+          dN[A][a] = v;
+        }
+      // full symmetric C from the upper triangle
+      double Cf[9][9];
+      const double* Cu = chat + ((size_t)el * NA + gp) * c.nc;
+      int q = 0;
+      for (int I = 0; I < ni2; ++I)
+        for (int J = I; J < ni2; ++J) {
+          Cf[I][J] = Cu[q];
+          Cf[J][I] = Cu[q];
+          ++q;
+        }
+      for (int A = 0; A < NA; ++A)
+        for (int i = 0; i < d; ++i)
+          for (int B = 0; B < NA; ++B)
+            for (int j = 0; j < d; ++j) {
+              double s = 0.0;
+              for (int a = 0; a < d; ++a)
+                for (int b = 0; b < d; ++b) s += dN[A][a] * Cf[i * d + a][j * d + b] * dN[B][b];
+              K[(size_t)(nodes[A] * d + i) * n + nodes[B] * d + j] += wq * s;
+            }
+    }
+  }
+}
+
+// f^(s) of one load case for one cell (natural order), Eq. 5b.
+void cell_load(const Ctx& c, const fetidp_problem& p, int load, int cx, int cy, int cz,
+               std::vector<double>& f) {
+  const int d = c.d, e = c.e, NA = 1 << d;
+  const double h = 1.0 / e;
+  const double* dir = p.load_dir + (size_t)load * d;
+  const int cc[3] = {cx, cy, cz};
+  std::fill(f.begin(), f.end(), 0.0);
+  if (p.load_kind[load] == 1) {   // body force per unit physical volume
+    for (int el = 0; el < c.nelem; ++el) {
+      const int ec[3] = {el % e, (el / e) % e, el / (e * e)};
+      for (int gp = 0; gp < NA; ++gp) {
+        double eta[3], xi[3], J[3][3];
+        gauss_point(c.geo, cx, cy, cz, ec[0], ec[1], ec[2], gp, eta, xi);
+        macro_jacobian(c.geo, xi, J);
+        double det;
+        if (d == 2) det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        else
+          det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+        const double wq = std::pow(0.5 * h, d) * det;
+        for (int A = 0; A < NA; ++A) {
+          double NAv = 1.0;
+          for (int k = 0; k < d; ++k) {
+            const double tk = gauss_t((gp >> k) & 1);
+            NAv *= ((A >> k) & 1) ? tk : 1.0 - tk;
+          }
+          const int node = (ec[0] + (A & 1)) + (e + 1) * ((ec[1] + ((A >> 1) & 1)) +
+                                                          (e + 1) * (d == 3 ? ec[2] + ((A >> 2) & 1) : 0));
+          for (int i = 0; i < d; ++i) f[(size_t)node * d + i] += wq * NAv * dir[i];
+        }
+      }
+    }
+    return;
+  }
+  const int ax = p.load_axis[load], side = p.load_side[load];
+  if (cc[ax] != (side ? c.geo.nc[ax] - 1 : 0)) return;
+  int tang[2], nt = 0;
+  for (int k = 0; k < d; ++k)
+    if (k != ax) tang[nt++] = k;
+  for (int el = 0; el < c.nelem; ++el) {
+    const int ec[3] = {el % e, (el / e) % e, el / (e * e)};
+    if (ec[ax] != (side ? e - 1 : 0)) continue;
+    for (int fg = 0; fg < (1 << (d - 1)); ++fg) {
+      double t[3] = {0.0, 0.0, 0.0};
+      t[ax] = side ? 1.0 : 0.0;
+      for (int q = 0; q < nt; ++q) t[tang[q]] = gauss_t((fg >> q) & 1);
+      double xi[3] = {0.0, 0.0, 0.0};
+      for (int k = 0; k < d; ++k) xi[k] = cc[k] + (ec[k] + t[k]) * h;
+      double J[3][3];
+      macro_jacobian(c.geo, xi, J);
+      double meas;
+      if (d == 2) {
+        meas = std::sqrt(J[0][tang[0]] * J[0][tang[0]] + J[1][tang[0]] * J[1][tang[0]]);
+      } else {
+        const double a[3] = {J[0][tang[0]], J[1][tang[0]], J[2][tang[0]]};
+        const double b[3] = {J[0][tang[1]], J[1][tang[1]], J[2][tang[1]]};
+        const double cr[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2],
+                              a[0] * b[1] - a[1] * b[0]};
+        meas = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+      }
+      const double wq = std::pow(0.5 * h, d - 1) * meas;
+      for (int A = 0; A < NA; ++A) {
+        if (((A >> ax) & 1) != (side ? 1 : 0)) continue;
+        double NAv = 1.0;
+        for (int k = 0; k < d; ++k) NAv *= ((A >> k) & 1) ? t[k] : 1.0 - t[k];
+        const int node = (ec[0] + (A & 1)) + (e + 1) * ((ec[1] + ((A >> 1) & 1)) +
+                                                        (e + 1) * (d == 3 ? ec[2] + ((A >> 2) & 1) : 0));
+        for (int i = 0; i < d; ++i) f[(size_t)node * d + i] += wq * NAv * dir[i];
+      }
+    }
+  }
+}
+
+template <typename T>
+fetidp_status upload(Ctx& c, T** dst, const std::vector<T>& src) {
+  FD_TRY(dalloc_t(c, dst, src.size() ? src.size() : 1));
+  if (!src.empty())
+    FD_CUDA(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice,
+                            c.stream));
+  return FETIDP_OK;
+}
+
+}  // namespace
+
+fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_options& o) {
+  using namespace host;
+  auto t0 = std::chrono::steady_clock::now();
+  // ---------------------------------------------------------------- validation
+  if (p.dim != 2 && p.dim != 3) { set_error("dim must be 2 or 3"); return FETIDP_EINVAL; }
+  if (p.elems < 2) { set_error("elems must be >= 2"); return FETIDP_EINVAL; }
+  for (int k = 0; k < 3; ++k)
+    if (p.cells[k] < 1 || (p.dim == 2 && k == 2 && p.cells[2] != 1)) {
+      set_error("bad cell counts"); return FETIDP_EINVAL;
+    }
+  if (p.n_loads < 1 || !p.load_kind || !p.load_dir || !p.r_cell) {
+    set_error("missing loads or radii"); return FETIDP_EINVAL;
+  }
+  if (p.n_rb < 1 || p.n_rb > 16) { set_error("n_rb must be in [1, 16]"); return FETIDP_EINVAL; }
+  if (p.clamp_axis < 0 || p.clamp_axis >= p.dim) { set_error("bad clamp axis"); return FETIDP_EINVAL; }
+  if (!(p.nu > -1.0 && p.nu < 0.5)) { set_error("nu out of range"); return FETIDP_EINVAL; }
+  if (p.mask_kind < 0 || p.mask_kind > 2 || (p.dim == 2) != (p.mask_kind == 0)) {
+    set_error("mask kind does not match the dimension"); return FETIDP_EINVAL;
+  }
+  if (o.max_outer < 1 || o.max_inner < 1) { set_error("bad iteration limits"); return FETIDP_EINVAL; }
+  c.opt = o;
+  const int d = p.dim, e = p.elems;
+  Geo& g = c.geo;
+  g.dim = d; g.e = e;
+  for (int k = 0; k < 3; ++k) g.nc[k] = p.cells[k];
+  g.mask_kind = p.mask_kind; g.map_kind = p.map_kind;
+  g.mask_width = p.mask_width; g.E_solid = p.E_solid; g.E_void = p.E_void; g.nu = p.nu;
+  for (int k = 0; k < 8; ++k) g.mp[k] = p.map_params[k];
+  c.d = d; c.e = e;
+  c.clamp_axis = p.clamp_axis; c.clamp_side = p.clamp_side;
+  c.N = (long long)p.cells[0] * p.cells[1] * p.cells[2];
+  c.m = p.n_loads;
+  c.ncorner = 1 << d;
+  c.nelem = d == 2 ? e * e : e * e * e;
+  c.ngp = 1 << d;
+  c.nc = d == 2 ? 10 : 45;
+  c.nsnap = (long long)c.nelem * c.ngp * c.nc;
+  RefCell ref = build_ref(d, e, c.ni, c.nd, c.np);
+  c.n = (int)ref.perm.size();
+  c.nr = c.ni + c.nd;
+  c.r_cell.assign(p.r_cell, p.r_cell + c.N);
+  {
+    std::vector<int> pp(ref.perm);
+    pp.insert(pp.end(), ref.iperm.begin(), ref.iperm.end());
+    FD_TRY(upload(c, &c.perm, pp));
+  }
+  FD_TRY(upload(c, &c.r_dev, c.r_cell));
+
+  // ---------------------------------------------------------------- multipliers (Eqs. 14-15)
+  const int nx = p.cells[0], ny = p.cells[1], nz = p.cells[2];
+  const long long gd[3] = {(long long)nx * e + 1, (long long)ny * e + 1, d == 3 ? (long long)nz * e + 1 : 1};
+  const int nn1 = e + 1;
+  std::vector<int> gath((size_t)c.N * c.nd * 2, 0);
+  std::vector<int> scat;
+  std::vector<double> Dw;
+  const long long clamp_coord = p.clamp_side ? (long long)p.cells[p.clamp_axis] * e : 0;
+  for (long long gz = 0; gz < gd[2]; ++gz)
+    for (long long gy = 0; gy < gd[1]; ++gy)
+      for (long long gx = 0; gx < gd[0]; ++gx) {
+        const long long gc[3] = {gx, gy, gz};
+        int on = 0;
+        for (int k = 0; k < d; ++k) on += (gc[k] % e == 0) ? 1 : 0;
+        if (on == 0 || on == d) continue;   // cell interior or lattice vertex (primal)
+        // owner cells: Cartesian product of candidate cell coordinates
+        int cand[3][2], ncand[3];
+        for (int k = 0; k < 3; ++k) {
+          if (k >= d) { cand[k][0] = 0; ncand[k] = 1; continue; }
+          const int nk = p.cells[k];
+          if (gc[k] % e == 0) {
+            const int q = (int)(gc[k] / e);
+            ncand[k] = 0;
+            if (q - 1 >= 0) cand[k][ncand[k]++] = q - 1;
+            if (q < nk) cand[k][ncand[k]++] = q;
+          } else {
+            cand[k][0] = (int)(gc[k] / e);
+            ncand[k] = 1;
+          }
+        }
+        std::vector<std::pair<long long, int>> own;   // (cell, dual node position)
+        for (int a = 0; a < ncand[0]; ++a)
+          for (int b = 0; b < ncand[1]; ++b)
+            for (int q = 0; q < ncand[2]; ++q) {
+              const int cx = cand[0][a], cy = cand[1][b], cz = cand[2][q];
+              const long long s = cx + (long long)nx * (cy + (long long)ny * cz);
+              const int lx = (int)(gx - (long long)cx * e), ly = (int)(gy - (long long)cy * e);
+              const int lz = d == 3 ? (int)(gz - (long long)cz * e) : 0;
+              const int lnode = lx + nn1 * (ly + nn1 * lz);
+              own.push_back({s, ref.dual_pos[lnode]});
+            }
+        std::sort(own.begin(), own.end());
+        const bool clamped = gc[p.clamp_axis] == clamp_coord;
+        const int mult = (int)own.size();
+        auto add_gath = [&](long long s, int j, int code) {
+          int* gp2 = &gath[((size_t)s * c.nd + j) * 2];
+          if (gp2[0] == 0) gp2[0] = code;
+          else gp2[1] = code;
+        };
+        if (clamped) {
+          for (auto& ow : own)
+            for (int comp = 0; comp < d; ++comp) {
+              const long long row = (long long)Dw.size();
+              const int j = ow.second * d + comp;
+              scat.push_back((int)(ow.first * c.nd + j + 1));
+              scat.push_back(0);
+              Dw.push_back(1.0);
+              add_gath(ow.first, j, (int)(row + 1));
+            }
+        } else {
+          for (int q = 0; q + 1 < mult; ++q)
+            for (int comp = 0; comp < d; ++comp) {
+              const long long row = (long long)Dw.size();
+              const int j1 = own[q].second * d + comp, j2 = own[q + 1].second * d + comp;
+              scat.push_back((int)(own[q].first * c.nd + j1 + 1));
+              scat.push_back(-(int)(own[q + 1].first * c.nd + j2 + 1));
+              Dw.push_back(1.0 / mult);
+              add_gath(own[q].first, j1, (int)(row + 1));
+              add_gath(own[q + 1].first, j2, -(int)(row + 1));
+            }
+        }
+      }
+  c.L = (long long)Dw.size();
+  FD_TRY(upload(c, &c.gath, gath));
+  FD_TRY(upload(c, &c.scat, scat));
+  FD_TRY(upload(c, &c.Dw, Dw));
+
+  // ---------------------------------------------------------------- primal DOF (Eq. 18)
+  const int vd[3] = {nx + 1, ny + 1, d == 3 ? nz + 1 : 1};
+  const long long nvert = (long long)vd[0] * vd[1] * vd[2];
+  const int cvert = p.clamp_side ? vd[p.clamp_axis] - 1 : 0;
+  std::vector<int> vnum(nvert, -1);
+  int nV = 0;
+  for (long long v = 0; v < nvert; ++v) {
+    const int ijk[3] = {(int)(v % vd[0]), (int)((v / vd[0]) % vd[1]), (int)(v / ((long long)vd[0] * vd[1]))};
+    if (ijk[p.clamp_axis] != cvert) vnum[v] = nV++;
+  }
+  c.nV = nV;
+  c.nP = (long long)nV * d;
+  std::vector<int> corner_v((size_t)c.N * c.ncorner), vert_cells((size_t)nV * c.ncorner, -1);
+  std::vector<int> vfill(nV, 0);
+  for (long long s = 0; s < c.N; ++s) {
+    const int cijk[3] = {(int)(s % nx), (int)((s / nx) % ny), (int)(s / ((long long)nx * ny))};
+    for (int k = 0; k < c.ncorner; ++k) {
+      const int o[3] = {k & 1, (k >> 1) & 1, (k >> 2) & 1};
+      long long v = 0, stride = 1;
+      for (int q = 0; q < 3; ++q) {
+        v += (cijk[q] + (q < d ? o[q] : 0)) * stride;
+        stride *= vd[q];
+      }
+      const int vn = vnum[v];
+      corner_v[(size_t)s * c.ncorner + k] = vn;
+      if (vn >= 0) vert_cells[(size_t)vn * c.ncorner + vfill[vn]++] = (int)(s * c.ncorner + k);
+    }
+  }
+  FD_TRY(upload(c, &c.corner_v, corner_v));
+  FD_TRY(upload(c, &c.vert_cells, vert_cells));
+  c.ntot = c.N * c.nr + c.nP + c.L;
+
+  // ---------------------------------------------------------------- loads: rhs = (f_R, f_P, 0)
+  {
+    std::vector<double> rhs((size_t)c.m * c.ntot, 0.0);
+    std::vector<double> f(c.n);
+    for (int l = 0; l < c.m; ++l) {
+      double* rl = rhs.data() + (size_t)l * c.ntot;
+      for (long long s = 0; s < c.N; ++s) {
+        const int cx = (int)(s % nx), cy = (int)((s / nx) % ny), cz = (int)(s / ((long long)nx * ny));
+        cell_load(c, p, l, cx, cy, cz, f);
+        for (int li = 0; li < c.nr; ++li) rl[s * c.nr + li] = f[ref.perm[li]];
+        for (int k = 0; k < c.ncorner; ++k) {
+          const int vn = corner_v[(size_t)s * c.ncorner + k];
+          if (vn < 0) continue;
+          for (int comp = 0; comp < d; ++comp)
+            rl[c.N * c.nr + (size_t)vn * d + comp] += f[ref.perm[c.nr + k * d + comp]];
+        }
+      }
+    }
+    FD_TRY(upload(c, &c.rhs, rhs));
+  }
+
+  // ---------------------------------------------------------------- snapshots (Eq. 52)
+  FD_TRY(dalloc_t(c, &c.snap, (size_t)c.N * c.nsnap));
+  FD_TRY(k_snapshots(c));
+
+  // ---------------------------------------------------------------- Algorithm 4 (greedy)
+  const int nrb_req = p.n_rb;
+  double* Delta = nullptr;
+  double *nrm = nullptr, *vals = nullptr, *beta_d = nullptr, *Z = nullptr, *scal1 = nullptr;
+  FD_CUDA(cudaMalloc(&Delta, sizeof(double) * c.N * c.nsnap));
+  FD_CUDA(cudaMalloc(&nrm, sizeof(double) * c.N));
+  FD_CUDA(cudaMalloc(&vals, sizeof(double) * c.N));
+  FD_CUDA(cudaMalloc(&beta_d, sizeof(double) * c.N * nrb_req));
+  FD_CUDA(cudaMalloc(&Z, sizeof(double) * c.nsnap * nrb_req));
+  FD_CUDA(cudaMalloc(&scal1, sizeof(double)));
+  std::vector<double> h_nrm(c.N), h_inf(c.N);
+  auto free_greedy = [&]() {
+    cudaFree(Delta); cudaFree(nrm); cudaFree(vals); cudaFree(beta_d); cudaFree(Z); cudaFree(scal1);
+  };
+  FD_TRY(k_row_reduce(c, c.snap, c.N, c.nsnap, nullptr, 0, nrm));
+  FD_TRY(k_row_normalise(c, c.snap, nrm, Delta, c.N, c.nsnap));
+  FD_CUDA(cudaMemcpyAsync(h_nrm.data(), nrm, sizeof(double) * c.N, cudaMemcpyDeviceToHost, c.stream));
+  c.sigma.clear();
+  for (int i = 0; i < nrb_req; ++i) {
+    FD_TRY(k_row_reduce(c, Delta, c.N, c.nsnap, nullptr, 1, vals));
+    FD_CUDA(cudaMemcpyAsync(h_inf.data(), vals, sizeof(double) * c.N, cudaMemcpyDeviceToHost, c.stream));
+    FD_CUDA(cudaStreamSynchronize(c.stream));
+    double mx = 0.0;
+    for (long long s = 0; s < c.N; ++s) mx = std::max(mx, h_inf[s]);
+    if (i > 0 && mx <= p.tol_rb) break;   // convergence check on Delta_{i-1}
+    if (mx == 0.0) break;
+    long long sig = -1;
+    for (long long s = 0; s < c.N; ++s)
+      if (h_inf[s] >= mx * (1.0 - kTieRel)) { sig = s; break; }
+    c.sigma.push_back((int)sig);
+    double* zeta = Z + (size_t)i * c.nsnap;
+    FD_TRY(k_row_reduce(c, Delta + (size_t)sig * c.nsnap, 1, c.nsnap, nullptr, 0, scal1));
+    FD_TRY(k_scale_copy(c, Delta + (size_t)sig * c.nsnap, scal1, zeta, c.nsnap));
+    FD_TRY(k_row_reduce(c, Delta, c.N, c.nsnap, zeta, 2, beta_d + (size_t)i * c.N));
+    FD_TRY(k_row_update(c, Delta, beta_d + (size_t)i * c.N, zeta, c.N, c.nsnap));
+  }
+  c.nrb = (int)c.sigma.size();
+  const int nrb = c.nrb;
+  // ---------------------------------------------------------------- alpha (Eq. 56)
+  std::vector<double> h_beta((size_t)nrb * c.N), h_alpha((size_t)c.N * nrb);
+  {
+    // T = Z^T [A^(sigma_1) ... ]: T[i][j] = zeta_i . A^(sigma_j)
+    std::vector<double> T((size_t)nrb * nrb);
+    for (int j = 0; j < nrb; ++j) {
+      FD_TRY(k_row_reduce(c, Z, nrb, c.nsnap, c.snap + (size_t)c.sigma[j] * c.nsnap, 2, vals));
+      std::vector<double> col(nrb);
+      FD_CUDA(cudaMemcpyAsync(col.data(), vals, sizeof(double) * nrb, cudaMemcpyDeviceToHost, c.stream));
+      FD_CUDA(cudaStreamSynchronize(c.stream));
+      for (int i = 0; i < nrb; ++i) T[(size_t)i * nrb + j] = col[i];
+    }
+    FD_CUDA(cudaMemcpyAsync(h_beta.data(), beta_d, sizeof(double) * nrb * c.N, cudaMemcpyDeviceToHost,
+                            c.stream));
+    FD_CUDA(cudaStreamSynchronize(c.stream));
+    // upper-triangular solve per cell: T alpha = ||A^(s)|| beta^(s)
+    for (long long s = 0; s < c.N; ++s) {
+      double* a = h_alpha.data() + (size_t)s * nrb;
+      for (int i = nrb - 1; i >= 0; --i) {
+        double v = h_nrm[s] * h_beta[(size_t)i * c.N + s];
+        for (int j = i + 1; j < nrb; ++j) v -= T[(size_t)i * nrb + j] * a[j];
+        a[i] = v / T[(size_t)i * nrb + i];
+      }
+    }
+  }
+  free_greedy();
+  FD_TRY(upload(c, &c.alpha, h_alpha));
+
+  // ---------------------------------------------------------------- principal operators (Eq. 39)
+  const int n = c.n, nr = c.nr, ni = c.ni, nd = c.nd, np = c.np;
+  std::vector<double> h_snap_p((size_t)nrb * c.nsnap);
+  for (int k = 0; k < nrb; ++k)
+    FD_CUDA(cudaMemcpyAsync(h_snap_p.data() + (size_t)k * c.nsnap, c.snap + (size_t)c.sigma[k] * c.nsnap,
+                            sizeof(double) * c.nsnap, cudaMemcpyDeviceToHost, c.stream));
+  FD_CUDA(cudaStreamSynchronize(c.stream));
+  std::vector<double> hKinv((size_t)nrb * nr * nr), hUrp((size_t)nrb * nr * np),
+      hUrpT((size_t)nrb * np * nr), hSdd((size_t)nrb * nd * nd), hKpp((size_t)nrb * np * np),
+      hKrp((size_t)nrb * nr * np);
+  std::vector<char> fail(nrb, 0);
+  parallel_for(nrb, [&](int k) {
+    std::vector<double> Knat;
+    assemble_dense_K(c, h_snap_p.data() + (size_t)k * c.nsnap, Knat);
+    std::vector<double> Krr((size_t)nr * nr);
+    for (int a = 0; a < nr; ++a)
+      for (int b = 0; b < nr; ++b) Krr[(size_t)a * nr + b] = Knat[(size_t)ref.perm[a] * n + ref.perm[b]];
+    double* Krp = hKrp.data() + (size_t)k * nr * np;
+    for (int a = 0; a < nr; ++a)
+      for (int b = 0; b < np; ++b) Krp[(size_t)a * np + b] = Knat[(size_t)ref.perm[a] * n + ref.perm[nr + b]];
+    double* Kpp = hKpp.data() + (size_t)k * np * np;
+    for (int a = 0; a < np; ++a)
+      for (int b = 0; b < np; ++b) Kpp[(size_t)a * np + b] = Knat[(size_t)ref.perm[nr + a] * n + ref.perm[nr + b]];
+    double* Ki = hKinv.data() + (size_t)k * nr * nr;
+    if (!spd_inverse(nr, Krr.data(), nr, Ki, nr)) { fail[k] = 1; return; }
+    double* U = hUrp.data() + (size_t)k * nr * np;
+    gemm(false, false, nr, np, nr, 1.0, Ki, nr, Krp, np, 0.0, U, np);
+    double* UT = hUrpT.data() + (size_t)k * np * nr;
+    for (int a = 0; a < nr; ++a)
+      for (int b = 0; b < np; ++b) UT[(size_t)b * nr + a] = U[(size_t)a * np + b];
+    // S_dd = F_dd^{-1}, F_dd = T_dr K_rr^{-1} T_rd (Sec. 3.1.1)
+    std::vector<double> F((size_t)nd * nd);
+    for (int a = 0; a < nd; ++a)
+      for (int b = 0; b < nd; ++b) F[(size_t)a * nd + b] = Ki[(size_t)(ni + a) * nr + ni + b];
+    if (!spd_inverse(nd, F.data(), nd, hSdd.data() + (size_t)k * nd * nd, nd)) fail[k] = 1;
+  });
+  for (int k = 0; k < nrb; ++k)
+    if (fail[k]) { set_error("principal K_rr is not positive definite"); return FETIDP_ESINGULAR; }
+  FD_TRY(upload(c, &c.Kinv, hKinv));
+  FD_TRY(upload(c, &c.Urp, hUrp));
+  FD_TRY(upload(c, &c.UrpT, hUrpT));
+  FD_TRY(upload(c, &c.Sdd, hSdd));
+
+  // ---------------------------------------------------------------- projections pi, delta (Eqs. 41-42)
+  std::vector<double> h_pi((size_t)c.N * nrb), h_delta((size_t)c.N * nrb);
+  {
+    const int nqp = c.nelem * c.ngp, dd = d * d;
+    const int npair = nrb * (nrb + 1) / 2;
+    const int ntab = 2 * npair + nrb;
+    double *Gd = nullptr, *Gp = nullptr, *Ge = nullptr, *Tab = nullptr, *Y = nullptr;
+    FD_CUDA(cudaMalloc(&Gd, sizeof(double) * (size_t)nrb * nd * nqp * dd));
+    FD_CUDA(cudaMalloc(&Gp, sizeof(double) * (size_t)nrb * np * nqp * dd));
+    FD_CUDA(cudaMalloc(&Ge, sizeof(double) * (size_t)np * nqp * dd));
+    FD_CUDA(cudaMalloc(&Tab, sizeof(double) * (size_t)ntab * c.nsnap));
+    FD_CUDA(cudaMalloc(&Y, sizeof(double) * (size_t)c.N * ntab));
+    // columns of U_rd^(k) = K_rr^{-1} T_rd: rows ni+l of the symmetric inverse
+    FD_TRY(k_column_gradients(c, c.Kinv + (size_t)ni * nr, (long long)nr * nr, nr, nr, 0, 0, nrb, nd, Gd));
+    // columns of U_rp^(k): rows of U_rp^T
+    FD_TRY(k_column_gradients(c, c.UrpT, (long long)np * nr, nr, nr, 0, 0, nrb, np, Gp));
+    // unit corner vectors e_p (columns of K_rp)
+    FD_TRY(k_column_gradients(c, nullptr, 0, 0, 0, 1, nr, 1, np, Ge));
+    const size_t gstride_d = (size_t)nd * nqp * dd, gstride_p = (size_t)np * nqp * dd;
+    int t = 0;
+    for (int i = 0; i < nrb; ++i)
+      for (int j = i; j < nrb; ++j, ++t)
+        FD_TRY(k_trace_table(c, Gp + i * gstride_p, Gp + j * gstride_p, np, Tab + (size_t)t * c.nsnap));
+    for (int i = 0; i < nrb; ++i, ++t)
+      FD_TRY(k_trace_table(c, Gp + i * gstride_p, Ge, np, Tab + (size_t)t * c.nsnap));
+    for (int i = 0; i < nrb; ++i)
+      for (int j = i; j < nrb; ++j, ++t)
+        FD_TRY(k_trace_table(c, Gd + i * gstride_d, Gd + j * gstride_d, nd, Tab + (size_t)t * c.nsnap));
+    FD_TRY(k_grouped_gemm_n(c, Tab, 0, (int)c.nsnap, ntab, (int)c.nsnap, 1,
+                            CCellVec{c.snap, 0, (int)c.nsnap}, CellVec{Y, 0, ntab}, nullptr, 1.0, 0.0,
+                            c.N, 1, false, 0));
+    std::vector<double> hY((size_t)c.N * ntab);
+    FD_CUDA(cudaMemcpyAsync(hY.data(), Y, sizeof(double) * hY.size(), cudaMemcpyDeviceToHost, c.stream));
+    FD_CUDA(cudaStreamSynchronize(c.stream));
+    cudaFree(Gd); cudaFree(Gp); cudaFree(Ge); cudaFree(Tab); cudaFree(Y);
+    std::vector<double> dvec(nrb, 0.0);
+    for (int k = 0; k < nrb; ++k)
+      for (int l = 0; l < nd; ++l) dvec[k] += hKinv[(size_t)k * nr * nr + (size_t)(ni + l) * nr + ni + l];
+    parallel_for((int)std::min<long long>(c.N, 1 << 30), [&](int s) {
+      const double* y = hY.data() + (size_t)s * ntab;
+      std::vector<double> A((size_t)nrb * nrb), M((size_t)nrb * nrb), b(nrb);
+      int q = 0;
+      for (int i = 0; i < nrb; ++i)
+        for (int j = i; j < nrb; ++j, ++q) { A[(size_t)i * nrb + j] = y[q]; A[(size_t)j * nrb + i] = y[q]; }
+      for (int i = 0; i < nrb; ++i, ++q) b[i] = y[q];
+      for (int i = 0; i < nrb; ++i)
+        for (int j = i; j < nrb; ++j, ++q) { M[(size_t)i * nrb + j] = y[q]; M[(size_t)j * nrb + i] = y[q]; }
+      gram_solve(nrb, A.data(), b.data(), kDropRel, h_pi.data() + (size_t)s * nrb);
+      gram_solve(nrb, M.data(), dvec.data(), kDropRel, h_delta.data() + (size_t)s * nrb);
+    });
+  }
+  FD_TRY(upload(c, &c.pi, h_pi));
+  FD_TRY(upload(c, &c.delta, h_delta));
+
+  // ---------------------------------------------------------------- ROM local operators (Eq. 43)
+  FD_TRY(dalloc_t(c, &c.Fdd_c, (size_t)c.N * nd * nd));
+  FD_TRY(dalloc_t(c, &c.Sdd_c, (size_t)c.N * nd * nd));
+  FD_TRY(dalloc_t(c, &c.Urp_c, (size_t)c.N * nr * np));
+  FD_TRY(dalloc_t(c, &c.UrpT_c, (size_t)c.N * nr * np));
+  FD_TRY(k_rom_combine(c, c.Kinv, (long long)nr * nr, nr, ni, ni, nd, nd, c.delta, c.Fdd_c, false));
+  FD_TRY(k_rom_combine(c, c.Sdd, (long long)nd * nd, nd, 0, 0, nd, nd, c.alpha, c.Sdd_c, false));
+  FD_TRY(k_rom_combine(c, c.Urp, (long long)nr * np, np, 0, 0, nr, np, c.pi, c.Urp_c, false));
+  FD_TRY(k_rom_combine(c, c.Urp, (long long)nr * np, np, 0, 0, nr, np, c.pi, c.UrpT_c, true));
+
+  // ---------------------------------------------------------------- coarse S_PP (Eq. 43, Sec. 3.2.1)
+  {
+    // P_kj = K_rp^(k)T U_rp^(j)
+    std::vector<double> P((size_t)nrb * nrb * np * np);
+    for (int k = 0; k < nrb; ++k)
+      for (int j = 0; j < nrb; ++j)
+        gemm(true, false, np, np, nr, 1.0, hKrp.data() + (size_t)k * nr * np, np,
+             hUrp.data() + (size_t)j * nr * np, np, 0.0, P.data() + ((size_t)k * nrb + j) * np * np, np);
+    std::vector<double> Spp((size_t)c.N * np * np);
+    parallel_for((int)c.N, [&](int s) {
+      const double* a = h_alpha.data() + (size_t)s * nrb;
+      const double* pv = h_pi.data() + (size_t)s * nrb;
+      std::vector<double> X((size_t)np * np, 0.0);
+      for (int k = 0; k < nrb; ++k) {
+        const double* Kpp = hKpp.data() + (size_t)k * np * np;
+        for (int q = 0; q < np * np; ++q) X[q] += a[k] * Kpp[q];
+        for (int j = 0; j < nrb; ++j) {
+          const double* Pk = P.data() + ((size_t)k * nrb + j) * np * np;
+          const double w = a[k] * pv[j];
+          for (int q = 0; q < np * np; ++q) X[q] -= w * Pk[q];
+        }
+      }
+      double* out = Spp.data() + (size_t)s * np * np;
+      for (int r = 0; r < np; ++r)
+        for (int q = 0; q < np; ++q) out[(size_t)r * np + q] = 0.5 * (X[(size_t)r * np + q] + X[(size_t)q * np + r]);
+    });
+    FD_TRY(coarse_setup(c, Spp));
+  }
+
+  // ---------------------------------------------------------------- workspace
+  const size_t m = c.m;
+  const size_t ncell_max = (size_t)c.N * std::max(c.n, c.nr);
+  FD_TRY(dalloc_t(c, &c.w_cell_a, m * ncell_max));
+  FD_TRY(dalloc_t(c, &c.w_cell_b, m * ncell_max));
+  FD_TRY(dalloc_t(c, &c.w_d1, m * c.N * nd));
+  FD_TRY(dalloc_t(c, &c.w_d2, m * c.N * nd));
+  FD_TRY(dalloc_t(c, &c.w_p1, m * c.N * np));
+  FD_TRY(dalloc_t(c, &c.w_P1, m * c.nP + 1));
+  FD_TRY(dalloc_t(c, &c.w_P2, m * c.nP + 1));
+  FD_TRY(dalloc_t(c, &c.w_zP, m * c.nP + 1));
+  FD_TRY(dalloc_t(c, &c.w_L1, m * c.L + 1));
+  FD_TRY(dalloc_t(c, &c.w_R, m * c.N * nrb * nr));
+  FD_TRY(dalloc_t(c, &c.w_KR, m * c.N * nrb * nr));
+  FD_TRY(dalloc_t(c, &c.w_tot, 3 * m * c.ntot));
+  FD_TRY(dalloc_t(c, &c.V, (size_t)(o.max_outer + 1) * m * c.ntot));
+  FD_TRY(dalloc_t(c, &c.Z, (size_t)o.max_outer * m * c.ntot));
+  FD_TRY(dalloc_t(c, &c.pcg, 6 * m * c.L + 1));
+  FD_TRY(dalloc_t(c, &c.red, (size_t)m * (o.max_outer + 2) * 304));
+  FD_TRY(dalloc_t(c, &c.scal, 64 * m + (size_t)m * (o.max_outer + 2) * 2));
+  FD_CUDA(cudaMallocHost(&c.h_scal, sizeof(double) * (64 * m + (size_t)m * (o.max_outer + 2) * 2)));
+  FD_CUDA(cudaStreamSynchronize(c.stream));
+  c.t_setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return FETIDP_OK;
+}
+
+}  // namespace fetidp

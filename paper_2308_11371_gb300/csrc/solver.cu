@@ -1,0 +1,661 @@
+// Operators and Krylov drivers of the ROM-based inexact FETI-DP solver, and
+// the C ABI (include/fetidp.h).
+//
+// * op_apply_F   -- Eq. 48: gather, F_dd_ring, coarse correction, scatter.
+// * op_apply_MD  -- Eq. 49: D-scaled gather, S_dd_ring, D-scaled scatter.
+// * U_apply      -- Algorithm 3 (U_ring v); UT_apply its transpose.
+// * K_rom_inv    -- Algorithm 2 / Eq. 45 with the local ROM solve of Eq. 46.
+// * precondition -- Algorithm 1 (the block preconditioner of Eq. 44).
+// * pcg          -- inner PCG on F_ring preconditioned by M_D_ring (Sec. 3.2.3).
+// * fgmres       -- outer right-preconditioned flexible GMRES on Eq. 16.
+// Every step runs in the kernels of this library; the host only keeps the
+// Krylov scalars (Hessenberg, Givens rotations, convergence decisions).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "common.cuh"
+
+namespace fetidp {
+
+namespace {
+thread_local std::string g_last_error;
+
+constexpr int S_RZ0 = 0, S_RZ1 = 1, S_PQ = 2, S_RR = 3, S_ACT = 4, S_R0 = 5, S_NSLOT = 8;
+
+__global__ void copy_cells_kernel(const double* __restrict__ x, long long x_rs, int x_cs,
+                                  double* __restrict__ y, long long y_rs, int y_cs, int len,
+                                  long long ncell, int nrhs) {
+  const long long per = ncell * len;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < per * nrhs;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int rhs = (int)(t / per);
+    const long long q = t - rhs * per;
+    const long long cell = q / len;
+    const int i = (int)(q - cell * len);
+    y[rhs * y_rs + cell * y_cs + i] = x[rhs * x_rs + cell * x_cs + i];
+  }
+}
+
+__global__ void axpby_kernel(const double* __restrict__ x, long long xs, const double* __restrict__ y,
+                             long long ys, double* __restrict__ out, long long os, double a, double b,
+                             long long len, int nrhs) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len * nrhs;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int rhs = (int)(t / len);
+    const long long q = t - rhs * len;
+    out[rhs * os + q] = a * x[rhs * xs + q] + b * y[rhs * ys + q];
+  }
+}
+
+// out[rhs][cell][perm[li]] = in[rhs][cell][li]
+__global__ void permute_out_kernel(const int* __restrict__ perm, const double* __restrict__ in,
+                                   double* __restrict__ out, int n, long long ncell, int nrhs) {
+  const long long per = ncell * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < per * nrhs;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long cn = t / n;
+    const int li = (int)(t - cn * n);
+    out[cn * n + perm[li]] = in[t];
+  }
+}
+
+// x += alpha p, r -= alpha q with alpha = rz / pq per active RHS
+__global__ void pcg_xr_kernel(double* __restrict__ X, double* __restrict__ R,
+                              const double* __restrict__ P, const double* __restrict__ Q,
+                              const double* __restrict__ scal, int rz_slot, long long L, int nrhs) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < L * nrhs;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int rhs = (int)(t / L);
+    const double act = scal[S_ACT * nrhs + rhs];
+    if (act == 0.0) continue;
+    const double alpha = scal[rz_slot * nrhs + rhs] / scal[S_PQ * nrhs + rhs];
+    X[t] += alpha * P[t];
+    R[t] -= alpha * Q[t];
+  }
+}
+
+// p = z + beta p, beta = rz_new / rz_old per active RHS
+__global__ void pcg_p_kernel(double* __restrict__ P, const double* __restrict__ Zv,
+                             const double* __restrict__ scal, int new_slot, int old_slot, long long L,
+                             int nrhs) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < L * nrhs;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int rhs = (int)(t / L);
+    if (scal[S_ACT * nrhs + rhs] == 0.0) continue;
+    const double beta = scal[new_slot * nrhs + rhs] / scal[old_slot * nrhs + rhs];
+    P[t] = Zv[t] + beta * P[t];
+  }
+}
+
+inline int gridn(long long work) {
+  long long g = (work + 255) / 256;
+  if (g > 152LL * 16) g = 152LL * 16;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+fetidp_status dalloc(Ctx& c, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 8;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? FETIDP_ENOMEM : FETIDP_ECUDA;
+  }
+  c.allocations.push_back(*p);
+  c.device_bytes += bytes;
+  return FETIDP_OK;
+}
+
+namespace {
+
+fetidp_status copy_cells(Ctx& c, CCellVec x, CellVec y, int len, int nrhs) {
+  copy_cells_kernel<<<gridn(c.N * len * nrhs), 256, 0, c.stream>>>(x.p, x.rs, x.cs, y.p, y.rs, y.cs,
+                                                                   len, c.N, nrhs);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status axpby(Ctx& c, const double* x, long long xs, const double* y, long long ys, double* out,
+                    long long os, double a, double b, long long len, int nrhs) {
+  axpby_kernel<<<gridn(len * nrhs), 256, 0, c.stream>>>(x, xs, y, ys, out, os, a, b, len, nrhs);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+// Per-cell operator sub-blocks (FP64 path): y = alpha M x + beta y, M rows x cols with
+// row stride ld and per-cell stride mstride.
+fetidp_status cell_op(Ctx& c, const double* mats, long long mstride, int ld, int rows, int cols,
+                      CCellVec x, CellVec y, double alpha, double beta) {
+  return k_cell_gemv_strided(c, mats, mstride, ld, rows, cols, x, y, alpha, beta, c.m);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ Eq. 48
+fetidp_status op_apply_F(Ctx& c, const double* lam, long long lam_rs, double* y, long long y_rs) {
+  const int m = c.m, nd = c.nd, np = c.np, nr = c.nr, ni = c.ni;
+  CellVec g{c.w_d1, c.N * nd, nd}, yd{c.w_d2, c.N * nd, nd}, cp{c.w_p1, c.N * np, np};
+  FD_TRY(k_gather_BT(c, lam, lam_rs, nullptr, g, m, 0.0));
+  FD_TRY(cell_op(c, c.Fdd_c, (long long)nd * nd, nd, nd, nd, cview(g), yd, 1.0, 0.0));
+  // coarse correction: c_p = (T_dr U_rp_ring)^T g, assembled, S_PP^{-1}, prolonged
+  FD_TRY(cell_op(c, c.UrpT_c + ni, (long long)np * nr, nr, np, nd, cview(g), cp, 1.0, 0.0));
+  FD_TRY(k_primal_assemble(c, cview(cp), c.w_P1, c.nP, 1.0, 0.0, m));
+  FD_TRY(coarse_solve(c, c.w_P1, c.nP, c.w_P2, c.nP, m));
+  FD_TRY(k_primal_extract(c, c.w_P2, c.nP, cp, m));
+  FD_TRY(cell_op(c, c.Urp_c + (size_t)ni * np, (long long)nr * np, np, nd, np, cview(cp), yd, 1.0, 1.0));
+  FD_TRY(k_scatter_B(c, cview(yd), y, y_rs, nullptr, 1.0, 0.0, m));
+  return FETIDP_OK;
+}
+
+// ------------------------------------------------------------------ Eq. 49
+fetidp_status op_apply_MD(Ctx& c, const double* r, long long r_rs, double* z, long long z_rs) {
+  const int m = c.m, nd = c.nd;
+  CellVec g{c.w_d1, c.N * nd, nd}, yd{c.w_d2, c.N * nd, nd};
+  FD_TRY(k_gather_BT(c, r, r_rs, c.Dw, g, m, 0.0));
+  FD_TRY(cell_op(c, c.Sdd_c, (long long)nd * nd, nd, nd, nd, cview(g), yd, 1.0, 0.0));
+  FD_TRY(k_scatter_B(c, cview(yd), z, z_rs, c.Dw, 1.0, 0.0, m));
+  return FETIDP_OK;
+}
+
+namespace {
+
+// Algorithm 3: out_L = U_ring v,  zP (= S_PP^{-1} (v_P - U_RP^T v_R)) kept in c.w_zP.
+fetidp_status U_apply(Ctx& c, CCellVec vR, const double* vP, long long vP_rs, double* out_L,
+                      long long out_rs) {
+  const int m = c.m, nd = c.nd, np = c.np, nr = c.nr, ni = c.ni;
+  CellVec cp{c.w_p1, c.N * np, np}, td{c.w_d1, c.N * nd, nd};
+  FD_TRY(cell_op(c, c.UrpT_c, (long long)np * nr, nr, np, nr, vR, cp, 1.0, 0.0));
+  FD_TRY(k_copy_scale(c, vP, c.w_P1, c.nP, m, vP_rs, c.nP, nullptr, 1.0));
+  FD_TRY(k_primal_assemble(c, cview(cp), c.w_P1, c.nP, -1.0, 1.0, m));
+  FD_TRY(coarse_solve(c, c.w_P1, c.nP, c.w_zP, c.nP, m));
+  // t_d = U_rd_ring^T v_r - T_dr U_rp_ring A_p^T z_P
+  FD_TRY(k_grouped_gemm(c, c.Kinv + (size_t)ni * nr, (long long)nr * nr, nr, nd, nr, vR, td, c.delta,
+                        1.0, 0.0, m, false, 0));
+  FD_TRY(k_primal_extract(c, c.w_zP, c.nP, cp, m));
+  FD_TRY(cell_op(c, c.Urp_c + (size_t)ni * np, (long long)nr * np, np, nd, np, cview(cp), td, -1.0, 1.0));
+  FD_TRY(k_scatter_B(c, cview(td), out_L, out_rs, nullptr, 1.0, 0.0, m));
+  return FETIDP_OK;
+}
+
+// Eq. 46 for every (rhs, cell): x_r = R (R^T K_s R)^{-1} R^T v_r, R = [K_rr^(sigma_k)^{-1} v_r]_k
+fetidp_status local_rom(Ctx& c, CCellVec vR, CellVec xR) {
+  const int m = c.m, nr = c.nr, nrb = c.nrb;
+  CellVec R{c.w_R, c.N * nrb * nr, nrb * nr};
+  FD_TRY(k_grouped_gemm(c, c.Kinv, (long long)nr * nr, nr, nr, nr, vR, R, nullptr, 1.0, 0.0, m, true,
+                        nr));
+  CellVec KR{c.w_KR, c.N * nrb * nr, nrb * nr};
+  FD_TRY(k_apply_K(c, cview(R), KR, nrb, m, true, true, c.snap, 0.0));
+  FD_TRY(k_gram_solve(c, c.w_R, c.w_KR, vR, xR, m));
+  return FETIDP_OK;
+}
+
+}  // namespace
+
+// inner PCG on F_ring y = b (Sec. 3.2.3); x: output [m][L] with row stride x_rs
+fetidp_status pcg_solve(Ctx& c, const double* b, long long b_rs, double* x, long long x_rs) {
+  const int m = c.m;
+  const long long L = c.L, mL = (long long)m * L;
+  double *X = c.pcg, *R = c.pcg + mL, *Zv = c.pcg + 2 * mL, *P = c.pcg + 3 * mL, *Q = c.pcg + 4 * mL;
+  double* sc = c.scal;
+  double* hs = c.h_scal;
+  FD_TRY(k_copy_scale(c, b, R, L, m, b_rs, L, nullptr, 1.0));
+  FD_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * mL, c.stream));
+  FD_TRY(k_dot(c, R, L, R, L, L, m, sc + S_R0 * m));
+  FD_CUDA(cudaMemcpyAsync(hs, sc, sizeof(double) * S_NSLOT * m, cudaMemcpyDeviceToHost, c.stream));
+  FD_CUDA(cudaStreamSynchronize(c.stream));
+  std::vector<double> rr0(m), act(m, 0.0);
+  int nact = 0;
+  for (int r = 0; r < m; ++r) {
+    rr0[r] = hs[S_R0 * m + r];
+    if (!std::isfinite(rr0[r])) { set_error("non-finite PCG right-hand side"); return FETIDP_EBREAKDOWN; }
+    act[r] = rr0[r] > 0.0 ? 1.0 : 0.0;
+    nact += act[r] > 0.0;
+  }
+  if (nact > 0) {
+    FD_CUDA(cudaMemcpyAsync(sc + S_ACT * m, act.data(), sizeof(double) * m, cudaMemcpyHostToDevice, c.stream));
+    FD_TRY(op_apply_MD(c, R, L, Zv, L));
+    FD_CUDA(cudaMemcpyAsync(P, Zv, sizeof(double) * mL, cudaMemcpyDeviceToDevice, c.stream));
+    FD_TRY(k_dot(c, R, L, Zv, L, L, m, sc + S_RZ0 * m));
+  }
+  const int max_it = c.opt.fixed_inner > 0 ? c.opt.fixed_inner : c.opt.max_inner;
+  int cur = S_RZ0, it = 0;
+  while (nact > 0 && it < max_it) {
+    FD_TRY(op_apply_F(c, P, L, Q, L));
+    FD_TRY(k_dot(c, P, L, Q, L, L, m, sc + S_PQ * m));
+    pcg_xr_kernel<<<gridn(mL), 256, 0, c.stream>>>(X, R, P, Q, sc, cur, L, m);
+    FD_CHECK_LAUNCH();
+    FD_TRY(k_dot(c, R, L, R, L, L, m, sc + S_RR * m));
+    FD_CUDA(cudaMemcpyAsync(hs, sc, sizeof(double) * S_NSLOT * m, cudaMemcpyDeviceToHost, c.stream));
+    FD_CUDA(cudaStreamSynchronize(c.stream));
+    ++it;
+    nact = 0;
+    for (int r = 0; r < m; ++r) {
+      if (act[r] == 0.0) continue;
+      const double pq = hs[S_PQ * m + r], rr = hs[S_RR * m + r];
+      if (!(pq > 0.0) || !std::isfinite(rr)) {
+        set_error("PCG breakdown: p^T F p <= 0 or non-finite residual");
+        return FETIDP_EBREAKDOWN;
+      }
+      const double rel = std::sqrt(rr / rr0[r]);
+      if (c.opt.fixed_inner <= 0 && rel <= c.opt.tol_inner) act[r] = 0.0;
+      if (rr == 0.0) act[r] = 0.0;
+      nact += act[r] > 0.0;
+    }
+    if (nact == 0 || it >= max_it) break;
+    FD_CUDA(cudaMemcpyAsync(sc + S_ACT * m, act.data(), sizeof(double) * m, cudaMemcpyHostToDevice, c.stream));
+    FD_TRY(op_apply_MD(c, R, L, Zv, L));
+    const int nxt = cur == S_RZ0 ? S_RZ1 : S_RZ0;
+    FD_TRY(k_dot(c, R, L, Zv, L, L, m, sc + nxt * m));
+    pcg_p_kernel<<<gridn(mL), 256, 0, c.stream>>>(P, Zv, sc, nxt, cur, L, m);
+    FD_CHECK_LAUNCH();
+    cur = nxt;
+  }
+  c.inner_total += it;
+  FD_TRY(k_copy_scale(c, X, x, L, m, L, x_rs, nullptr, 1.0));
+  return FETIDP_OK;
+}
+
+// ------------------------------------------------------------------ Eq. 16 operator
+fetidp_status op_apply_A(Ctx& c, const double* x, double* y) {
+  const int m = c.m, n = c.n, nr = c.nr, ni = c.ni;
+  const long long nt = c.ntot, NR = c.N * nr;
+  CellVec ua{c.w_cell_a, c.N * n, n}, ub{c.w_cell_b, c.N * n, n};
+  FD_TRY(copy_cells(c, CCellVec{x, nt, nr}, ua, nr, m));
+  FD_TRY(k_primal_extract(c, x + NR, nt, CellVec{c.w_cell_a + nr, c.N * n, n}, m));
+  FD_TRY(k_apply_K(c, cview(ua), ub, 1, m, true, false, c.snap, 0.0));
+  FD_TRY(copy_cells(c, cview(ub), CellVec{y, nt, nr}, nr, m));
+  FD_TRY(k_gather_BT(c, x + NR + c.nP, nt, nullptr, CellVec{y + ni, nt, nr}, m, 1.0));
+  FD_TRY(k_primal_assemble(c, CCellVec{c.w_cell_b + nr, c.N * n, n}, y + NR, nt, 1.0, 0.0, m));
+  FD_TRY(k_scatter_B(c, CCellVec{x + ni, nt, nr}, y + NR + c.nP, nt, nullptr, 1.0, 0.0, m));
+  return FETIDP_OK;
+}
+
+// ------------------------------------------------------------------ Algorithm 1 (Eq. 44)
+fetidp_status op_precondition(Ctx& c, const double* x, double* y) {
+  const int m = c.m, nd = c.nd, np = c.np, nr = c.nr, ni = c.ni;
+  const long long nt = c.ntot, NR = c.N * nr;
+  CCellVec vR{x, nt, nr};
+  const double* vP = x + NR;
+  const double* w = x + NR + c.nP;
+  CellVec yR{y, nt, nr};
+  double* yP = y + NR;
+  double* yL = y + NR + c.nP;
+  double* pcg_b = c.pcg + 5LL * m * c.L;
+  // w_bar = w - U_ring v  (Algorithm 3; keeps z_P = x_P of Algorithm 2 in w_zP)
+  FD_TRY(U_apply(c, vR, vP, nt, c.w_L1, c.L));
+  FD_TRY(axpby(c, w, nt, c.w_L1, c.L, pcg_b, c.L, 1.0, -1.0, c.L, m));
+  // y = -F_ring^{-pcg} w_bar
+  FD_TRY(pcg_solve(c, pcg_b, c.L, yL, nt));
+  FD_TRY(k_copy_scale(c, yL, yL, c.L, m, nt, nt, nullptr, -1.0));
+  // x = K_ring^{-ROM} v - U_ring^T y   (Algorithm 2 with Eq. 46)
+  FD_TRY(local_rom(c, vR, yR));
+  CellVec cp{c.w_p1, c.N * np, np};
+  FD_TRY(k_primal_extract(c, c.w_zP, c.nP, cp, m));
+  FD_TRY(cell_op(c, c.Urp_c, (long long)nr * np, np, nr, np, cview(cp), yR, -1.0, 1.0));
+  // U_ring^T y = (U_RD B_R^T y - U_RP z'_P, z'_P), z'_P = S_PP^{-1}(-U_RP^T B_R^T y)
+  CellVec g{c.w_d1, c.N * nd, nd};
+  FD_TRY(k_gather_BT(c, yL, nt, nullptr, g, m, 0.0));
+  FD_TRY(cell_op(c, c.UrpT_c + ni, (long long)np * nr, nr, np, nd, cview(g), cp, 1.0, 0.0));
+  FD_TRY(k_primal_assemble(c, cview(cp), c.w_P1, c.nP, -1.0, 0.0, m));
+  FD_TRY(coarse_solve(c, c.w_P1, c.nP, c.w_P1, c.nP, m));
+  FD_TRY(k_grouped_gemm(c, c.Kinv + ni, (long long)nr * nr, nr, nr, nd, cview(g), yR, c.delta, -1.0,
+                        1.0, m, false, 0));
+  FD_TRY(k_primal_extract(c, c.w_P1, c.nP, cp, m));
+  FD_TRY(cell_op(c, c.Urp_c, (long long)nr * np, np, nr, np, cview(cp), yR, 1.0, 1.0));
+  FD_TRY(axpby(c, c.w_zP, c.nP, c.w_P1, c.nP, yP, nt, 1.0, -1.0, c.nP, m));
+  return FETIDP_OK;
+}
+
+// ------------------------------------------------------------------ outer FGMRES
+struct OuterResult {
+  int its = 0;
+  double rel_res = 0.0;
+  bool converged = false;
+};
+
+fetidp_status fgmres(Ctx& c, double* xout, OuterResult& res) {
+  const int m = c.m, mo = c.opt.max_outer;
+  const long long nt = c.ntot, mnt = (long long)m * nt;
+  double* dots1 = c.scal + 64 * m;
+  double* dots2 = dots1 + (size_t)m * (mo + 2);
+  std::vector<double> hbuf((size_t)m * (mo + 2));
+  // beta = ||b||
+  FD_TRY(k_dot(c, c.rhs, nt, c.rhs, nt, nt, m, dots1));
+  FD_CUDA(cudaMemcpyAsync(hbuf.data(), dots1, sizeof(double) * m, cudaMemcpyDeviceToHost, c.stream));
+  FD_CUDA(cudaStreamSynchronize(c.stream));
+  std::vector<double> beta(m), inv(m);
+  for (int r = 0; r < m; ++r) {
+    beta[r] = std::sqrt(hbuf[r]);
+    inv[r] = beta[r] > 0.0 ? 1.0 / beta[r] : 0.0;
+  }
+  FD_CUDA(cudaMemcpyAsync(dots2, inv.data(), sizeof(double) * m, cudaMemcpyHostToDevice, c.stream));
+  FD_TRY(k_copy_scale(c, c.rhs, c.V, nt, m, nt, nt, dots2, 0.0));
+  std::vector<std::vector<double>> H(m, std::vector<double>((size_t)(mo + 1) * mo, 0.0));
+  std::vector<std::vector<double>> g(m, std::vector<double>(mo + 1, 0.0)), cs(m, std::vector<double>(mo)),
+      sn(m, std::vector<double>(mo));
+  std::vector<int> k_used(m, 0);
+  std::vector<char> active(m, 1);
+  for (int r = 0; r < m; ++r) {
+    g[r][0] = beta[r];
+    if (beta[r] == 0.0) active[r] = 0;
+  }
+  auto Hij = [&](int r, int i, int j) -> double& { return H[r][(size_t)i * mo + j]; };
+  int j = 0;
+  int nact = 0;
+  for (int r = 0; r < m; ++r) nact += active[r];
+  for (j = 0; j < mo && nact > 0; ++j) {
+    double* Vj = c.V + (size_t)j * mnt;
+    double* Zj = c.Z + (size_t)j * mnt;
+    double* w = c.V + (size_t)(j + 1) * mnt;
+    FD_TRY(op_precondition(c, Vj, Zj));
+    FD_TRY(op_apply_A(c, Zj, w));
+    // CGS2
+    FD_TRY(k_multi_dot(c, c.V, mnt, j + 1, w, nt, m, dots1));
+    FD_TRY(k_multi_axpy(c, c.V, mnt, j + 1, dots1, w, nt, m, -1.0));
+    FD_TRY(k_multi_dot(c, c.V, mnt, j + 1, w, nt, m, dots2));
+    FD_TRY(k_multi_axpy(c, c.V, mnt, j + 1, dots2, w, nt, m, -1.0));
+    std::vector<double> h1((size_t)m * (j + 1)), h2((size_t)m * (j + 1));
+    FD_CUDA(cudaMemcpyAsync(h1.data(), dots1, sizeof(double) * h1.size(), cudaMemcpyDeviceToHost, c.stream));
+    FD_CUDA(cudaMemcpyAsync(h2.data(), dots2, sizeof(double) * h2.size(), cudaMemcpyDeviceToHost, c.stream));
+    FD_TRY(k_dot(c, w, nt, w, nt, nt, m, dots1));
+    FD_CUDA(cudaMemcpyAsync(hbuf.data(), dots1, sizeof(double) * m, cudaMemcpyDeviceToHost, c.stream));
+    FD_CUDA(cudaStreamSynchronize(c.stream));
+    for (int r = 0; r < m; ++r) {
+      inv[r] = 0.0;
+      if (!active[r]) continue;
+      const double hn = std::sqrt(hbuf[r]);
+      for (int i = 0; i <= j; ++i) Hij(r, i, j) = h1[(size_t)r * (j + 1) + i] + h2[(size_t)r * (j + 1) + i];
+      Hij(r, j + 1, j) = hn;
+      for (int i = 0; i < j; ++i) {
+        const double a = Hij(r, i, j), b = Hij(r, i + 1, j);
+        Hij(r, i, j) = cs[r][i] * a + sn[r][i] * b;
+        Hij(r, i + 1, j) = -sn[r][i] * a + cs[r][i] * b;
+      }
+      const double rho = std::hypot(Hij(r, j, j), Hij(r, j + 1, j));
+      if (!(rho > 0.0) || !std::isfinite(rho)) {
+        set_error("FGMRES breakdown");
+        return FETIDP_EBREAKDOWN;
+      }
+      cs[r][j] = Hij(r, j, j) / rho;
+      sn[r][j] = Hij(r, j + 1, j) / rho;
+      Hij(r, j, j) = rho;
+      Hij(r, j + 1, j) = 0.0;
+      g[r][j + 1] = -sn[r][j] * g[r][j];
+      g[r][j] = cs[r][j] * g[r][j];
+      k_used[r] = j + 1;
+      const double est = std::fabs(g[r][j + 1]) / beta[r];
+      const bool fixed = c.opt.fixed_outer > 0;
+      if ((!fixed && est <= c.opt.tol_outer) || hn == 0.0 || (fixed && j + 1 >= c.opt.fixed_outer))
+        active[r] = 0;
+      inv[r] = (active[r] && hn > 0.0) ? 1.0 / hn : 0.0;
+    }
+    nact = 0;
+    for (int r = 0; r < m; ++r) nact += active[r];
+    if (nact > 0) {
+      FD_CUDA(cudaMemcpyAsync(dots2, inv.data(), sizeof(double) * m, cudaMemcpyHostToDevice, c.stream));
+      FD_TRY(k_copy_scale(c, w, w, nt, m, nt, nt, dots2, 0.0));
+    }
+  }
+  // x = sum_i y_i Z_i, y from the triangular least-squares system
+  const int kmax = *std::max_element(k_used.begin(), k_used.end());
+  std::vector<double> coef((size_t)m * std::max(kmax, 1), 0.0);
+  for (int r = 0; r < m; ++r) {
+    const int k = k_used[r];
+    std::vector<double> yv(k, 0.0);
+    for (int i = k - 1; i >= 0; --i) {
+      double s = g[r][i];
+      for (int q = i + 1; q < k; ++q) s -= Hij(r, i, q) * yv[q];
+      yv[i] = s / Hij(r, i, i);
+    }
+    for (int i = 0; i < k; ++i) coef[(size_t)r * kmax + i] = yv[i];
+  }
+  FD_CUDA(cudaMemsetAsync(xout, 0, sizeof(double) * mnt, c.stream));
+  if (kmax > 0) {
+    FD_CUDA(cudaMemcpyAsync(dots1, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice, c.stream));
+    FD_TRY(k_multi_axpy(c, c.Z, mnt, kmax, dots1, xout, nt, m, 1.0));
+  }
+  // true residual
+  double* rbuf = c.w_tot + 2 * mnt;
+  FD_TRY(op_apply_A(c, xout, rbuf));
+  FD_TRY(axpby(c, c.rhs, nt, rbuf, nt, rbuf, nt, 1.0, -1.0, nt, m));
+  FD_TRY(k_dot(c, rbuf, nt, rbuf, nt, nt, m, dots1));
+  FD_CUDA(cudaMemcpyAsync(hbuf.data(), dots1, sizeof(double) * m, cudaMemcpyDeviceToHost, c.stream));
+  FD_CUDA(cudaStreamSynchronize(c.stream));
+  res.rel_res = 0.0;
+  res.converged = true;
+  for (int r = 0; r < m; ++r) {
+    const double rr = beta[r] > 0.0 ? std::sqrt(hbuf[r]) / beta[r] : 0.0;
+    res.rel_res = std::max(res.rel_res, rr);
+    const double est = k_used[r] > 0 ? std::fabs(g[r][k_used[r]]) / beta[r] : 0.0;
+    if (c.opt.fixed_outer <= 0 && beta[r] > 0.0 && est > c.opt.tol_outer) res.converged = false;
+  }
+  res.its = kmax;
+  return FETIDP_OK;
+}
+
+// u_out natural [m][N][n] from an outer vector x [m][ntot]
+fetidp_status to_cells_natural(Ctx& c, const double* x, double* u_out) {
+  const int m = c.m, n = c.n, nr = c.nr;
+  CellVec ua{c.w_cell_a, c.N * n, n};
+  FD_TRY(copy_cells(c, CCellVec{x, c.ntot, nr}, ua, nr, m));
+  FD_TRY(k_primal_extract(c, x + c.N * nr, c.ntot, CellVec{c.w_cell_a + nr, c.N * n, n}, m));
+  permute_out_kernel<<<gridn(c.N * n * m), 256, 0, c.stream>>>(c.perm, c.w_cell_a, u_out, n, c.N, m);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+}  // namespace fetidp
+
+// ======================================================================== C ABI
+using namespace fetidp;
+
+struct fetidp_ctx {
+  Ctx c;
+};
+
+static fetidp_status enter(fetidp_ctx* ctx) {
+  if (!ctx) { set_error("null context"); return FETIDP_EINVAL; }
+  cudaError_t e = cudaSetDevice(ctx->c.device);
+  if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return FETIDP_ECUDA; }
+  return FETIDP_OK;
+}
+
+extern "C" {
+
+void fetidp_default_options(fetidp_options* o) {
+  if (!o) return;
+  o->tol_outer = 1e-8;
+  o->tol_inner = 1e-11;
+  o->max_outer = 50;
+  o->max_inner = 1000;
+  o->precision = FETIDP_FP64;
+  o->fixed_outer = 0;
+  o->fixed_inner = 0;
+}
+
+const char* fetidp_status_string(fetidp_status s) {
+  switch (s) {
+    case FETIDP_OK: return "ok";
+    case FETIDP_EINVAL: return "invalid argument";
+    case FETIDP_ENOMEM: return "out of memory";
+    case FETIDP_ECUDA: return "CUDA error";
+    case FETIDP_ENOTCONV: return "not converged";
+    case FETIDP_ETIMEOUT: return "device wait timed out";
+    case FETIDP_ESINGULAR: return "singular (not SPD)";
+    case FETIDP_EBREAKDOWN: return "Krylov breakdown";
+  }
+  return "unknown status";
+}
+
+const char* fetidp_last_error(void) { return g_last_error.c_str(); }
+
+void fetidp_destroy(fetidp_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->c.device);
+  cudaStreamSynchronize(ctx->c.stream);
+  for (void* p : ctx->c.allocations) cudaFree(p);
+  if (ctx->c.h_scal) cudaFreeHost(ctx->c.h_scal);
+  delete ctx;
+}
+
+fetidp_status fetidp_setup(const fetidp_problem* probs, int n_problems, const fetidp_options* opt,
+                           void* cuda_stream, fetidp_ctx** out) {
+  if (!out) { set_error("null output pointer"); return FETIDP_EINVAL; }
+  *out = nullptr;
+  if (!probs || n_problems != 1) {
+    set_error("exactly one problem per context is supported");
+    return FETIDP_EINVAL;
+  }
+  fetidp_options o;
+  fetidp_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision != FETIDP_FP64) {
+    set_error("requested precision is not available in this build");
+    return FETIDP_EINVAL;
+  }
+  fetidp_ctx* ctx = new fetidp_ctx();
+  cudaGetDevice(&ctx->c.device);
+  ctx->c.stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  fetidp_status s = setup_context(ctx->c, probs[0], o);
+  if (s != FETIDP_OK) {
+    fetidp_destroy(ctx);
+    return s;
+  }
+  *out = ctx;
+  return FETIDP_OK;
+}
+
+fetidp_status fetidp_sizes(const fetidp_ctx* ctx, long long o[12]) {
+  if (!ctx || !o) { set_error("null argument"); return FETIDP_EINVAL; }
+  const Ctx& c = ctx->c;
+  o[0] = c.N; o[1] = c.n; o[2] = c.ni; o[3] = c.nd; o[4] = c.np; o[5] = c.nr;
+  o[6] = c.L; o[7] = c.nP; o[8] = c.m; o[9] = c.nrb; o[10] = c.nsnap; o[11] = c.ntot;
+  return FETIDP_OK;
+}
+
+fetidp_status fetidp_apply_F(fetidp_ctx* ctx, const double* lambda, double* y) {
+  FD_TRY(enter(ctx));
+  return op_apply_F(ctx->c, lambda, ctx->c.L, y, ctx->c.L);
+}
+
+fetidp_status fetidp_precond(fetidp_ctx* ctx, const double* r, double* z) {
+  FD_TRY(enter(ctx));
+  return op_apply_MD(ctx->c, r, ctx->c.L, z, ctx->c.L);
+}
+
+fetidp_status fetidp_gather_BT(fetidp_ctx* ctx, const double* lambda, double* x_d) {
+  FD_TRY(enter(ctx));
+  Ctx& c = ctx->c;
+  return k_gather_BT(c, lambda, c.L, nullptr, CellVec{x_d, c.N * c.nd, c.nd}, c.m, 0.0);
+}
+
+fetidp_status fetidp_scatter_B(fetidp_ctx* ctx, const double* y_d, double* z) {
+  FD_TRY(enter(ctx));
+  Ctx& c = ctx->c;
+  return k_scatter_B(c, CCellVec{y_d, c.N * c.nd, c.nd}, z, c.L, nullptr, 1.0, 0.0, c.m);
+}
+
+fetidp_status fetidp_apply_K(fetidp_ctx* ctx, const double* u, double* y) {
+  FD_TRY(enter(ctx));
+  Ctx& c = ctx->c;
+  return k_apply_K(c, CCellVec{u, c.N * c.n, c.n}, CellVec{y, c.N * c.n, c.n}, 1, c.m, false, false,
+                   c.snap, 0.0);
+}
+
+fetidp_status fetidp_coarse_solve(fetidp_ctx* ctx, const double* b, double* x) {
+  FD_TRY(enter(ctx));
+  Ctx& c = ctx->c;
+  return coarse_solve(c, b, c.nP, x, c.nP, c.m);
+}
+
+fetidp_status fetidp_local_rom_solve(fetidp_ctx* ctx, const double* v, double* x) {
+  FD_TRY(enter(ctx));
+  Ctx& c = ctx->c;
+  return local_rom(c, CCellVec{v, c.N * c.nr, c.nr}, CellVec{x, c.N * c.nr, c.nr});
+}
+
+fetidp_status fetidp_apply_A(fetidp_ctx* ctx, const double* x, double* y) {
+  FD_TRY(enter(ctx));
+  return op_apply_A(ctx->c, x, y);
+}
+
+fetidp_status fetidp_apply_P(fetidp_ctx* ctx, const double* x, double* y) {
+  FD_TRY(enter(ctx));
+  return op_precondition(ctx->c, x, y);
+}
+
+fetidp_status fetidp_rom_data(fetidp_ctx* ctx, int* sigma, double* alpha, double* pi, double* delta) {
+  FD_TRY(enter(ctx));
+  Ctx& c = ctx->c;
+  if (sigma) std::memcpy(sigma, c.sigma.data(), sizeof(int) * c.nrb);
+  const size_t bytes = sizeof(double) * c.N * c.nrb;
+  if (alpha) FD_CUDA(cudaMemcpyAsync(alpha, c.alpha, bytes, cudaMemcpyDeviceToHost, c.stream));
+  if (pi) FD_CUDA(cudaMemcpyAsync(pi, c.pi, bytes, cudaMemcpyDeviceToHost, c.stream));
+  if (delta) FD_CUDA(cudaMemcpyAsync(delta, c.delta, bytes, cudaMemcpyDeviceToHost, c.stream));
+  FD_CUDA(cudaStreamSynchronize(c.stream));
+  return FETIDP_OK;
+}
+
+static fetidp_status solve_common(fetidp_ctx* ctx, fetidp_info* info, OuterResult& r) {
+  Ctx& c = ctx->c;
+  auto t0 = std::chrono::steady_clock::now();
+  c.inner_total = 0;
+  FD_TRY(fgmres(c, c.w_tot, r));
+  FD_CUDA(cudaStreamSynchronize(c.stream));
+  if (info) {
+    info->outer_its = r.its;
+    info->inner_its_total = c.inner_total;
+    info->n_rb = c.nrb;
+    info->rel_residual = r.rel_res;
+    info->t_setup_s = c.t_setup_s;
+    info->t_solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    info->device_bytes = c.device_bytes;
+  }
+  return FETIDP_OK;
+}
+
+fetidp_status fetidp_solve(fetidp_ctx* ctx, double* u, double* lambda, fetidp_info* info) {
+  FD_TRY(enter(ctx));
+  Ctx& c = ctx->c;
+  OuterResult r;
+  FD_TRY(solve_common(ctx, info, r));
+  if (u) FD_TRY(to_cells_natural(c, c.w_tot, u));
+  if (lambda)
+    FD_TRY(k_copy_scale(c, c.w_tot + c.N * c.nr + c.nP, lambda, c.L, c.m, c.ntot, c.L, nullptr, 1.0));
+  FD_CUDA(cudaStreamSynchronize(c.stream));
+  return r.converged ? FETIDP_OK : FETIDP_ENOTCONV;
+}
+
+fetidp_status fetidp_solve_host(fetidp_ctx* ctx, double* u_host, double* lambda_host,
+                                fetidp_info* info) {
+  FD_TRY(enter(ctx));
+  Ctx& c = ctx->c;
+  OuterResult r;
+  FD_TRY(solve_common(ctx, info, r));
+  if (u_host) {
+    FD_TRY(to_cells_natural(c, c.w_tot, c.w_cell_b));
+    FD_CUDA(cudaMemcpyAsync(u_host, c.w_cell_b, sizeof(double) * c.m * c.N * c.n,
+                            cudaMemcpyDeviceToHost, c.stream));
+  }
+  if (lambda_host)
+    for (int q = 0; q < c.m; ++q)
+      FD_CUDA(cudaMemcpyAsync(lambda_host + (size_t)q * c.L, c.w_tot + (size_t)q * c.ntot + c.N * c.nr + c.nP,
+                              sizeof(double) * c.L, cudaMemcpyDeviceToHost, c.stream));
+  FD_CUDA(cudaStreamSynchronize(c.stream));
+  return r.converged ? FETIDP_OK : FETIDP_ENOTCONV;
+}
+
+fetidp_status fetidp_grad(fetidp_ctx* ctx, const double* u, const double* w, double* g) {
+  FD_TRY(enter(ctx));
+  Ctx& c = ctx->c;
+  return k_grad(c, u, w ? w : u, g);
+}
+
+}  // extern "C"

@@ -1,0 +1,66 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol include/fetidp.h declares
+(no compute call: this runs without a GPU)."""
+import os
+import re
+
+import pytest
+
+from paper_2308_11371_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "fetidp.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fetidp_[A-Za-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return binding.load()
+
+
+def test_header_declares_the_hot_path_entry_points():
+    syms = declared_symbols()
+    for s in ("fetidp_setup", "fetidp_apply_F", "fetidp_precond", "fetidp_solve", "fetidp_grad",
+              "fetidp_destroy"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [s for s in declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    assert set(declared_symbols()) <= set(binding.SYMBOLS)
+
+
+def test_default_options_and_status_strings(lib):
+    o = binding.default_options()
+    assert o.tol_outer == 1e-8 and o.tol_inner == 1e-11 and o.precision == binding.FETIDP_FP64
+    assert lib.fetidp_status_string(-4) == b"not converged"
+    assert lib.fetidp_status_string(0) == b"ok"
+
+
+def test_problem_struct_marshalling():
+    from paper_2308_11371_gb300 import workloads as W
+    p = W.config5()
+    s, keep = binding.make_problem_struct(p)
+    assert (s.dim, list(s.cells), s.elems, s.n_loads, s.n_rb) == (3, [32, 32, 16], 6, 6, 16)
+    assert s.load_kind[3] == W.LOAD_BODY and s.load_dir[3 * 3 + 0] == 1.0
+    assert abs(s.r_cell[0] - p.r_cell[0]) == 0.0
+
+
+def test_setup_rejects_bad_input_without_gpu(lib):
+    """Argument checks run before any CUDA call."""
+    import ctypes
+    from paper_2308_11371_gb300 import workloads as W
+    p = W.config1()
+    p.n_rb = 0
+    s, keep = binding.make_problem_struct(p)
+    h = ctypes.c_void_p()
+    st = lib.fetidp_setup(ctypes.byref(s), 2, None, None, ctypes.byref(h))
+    assert st == -1 and not h.value
