@@ -99,15 +99,17 @@ typedef struct {
   const int *load_axis;     /* [n_loads] */
   const int *load_side;     /* [n_loads] */
   const double *load_dir;   /* [n_loads * dim] */
-  int n_rb;                 /* principal cells requested (>= 1) */
+  int n_rb;                 /* principal cells requested (1..64) */
   double tol_rb;
 } fetidp_problem;
 
 /* Solver options.  fetidp_default_options fills the defaults shown. */
 typedef struct {
-  double tol_outer;         /* FGMRES stop: ||b - A x|| / ||b|| (est.) <= tol_outer (1e-8) */
+  double tol_outer;         /* stop when the TRUE ||b - A x|| / ||b|| <= tol_outer (1e-8) */
   double tol_inner;         /* inner PCG stop: ||r_k|| / ||r_0|| <= tol_inner (1e-11; P. 579) */
-  int max_outer;            /* FGMRES iterations, no restart (50); sizes the Krylov storage */
+  int max_outer;            /* FGMRES iterations per cycle (50); sizes the Krylov storage.
+                               A cycle restarts from the current iterate while the true
+                               residual is above tol_outer (at most 8 cycles)            */
   int max_inner;            /* PCG iterations per preconditioner application (1000) */
   int precision;            /* fetidp_precision (FETIDP_FP64) */
   int fixed_outer;          /* > 0: run exactly this many outer iterations (iterate-locked) */
@@ -150,7 +152,8 @@ fetidp_status fetidp_apply_F(fetidp_ctx *ctx, const double *lambda, double *y);
 fetidp_status fetidp_precond(fetidp_ctx *ctx, const double *r, double *z);
 
 /* Solve the saddle-point system of Eq. 16 by right-preconditioned flexible
- * GMRES with the block preconditioner of Eq. 44 (Algorithms 1-3), x_0 = 0.
+ * GMRES with the block preconditioner of Eq. 44 (Algorithms 1-3), x_0 = 0,
+ * restarted from the current iterate while the true residual is above tol.
  * u: device [n_rhs][N][n_dof] cell-duplicated displacements (out);
  * lambda: device [n_rhs][L] multipliers (out), may be NULL.  info (host, may
  * be NULL) receives iteration counts, residual and timings.
@@ -202,6 +205,39 @@ fetidp_status fetidp_apply_P(fetidp_ctx *ctx, const double *x, double *y);
  * cells, alpha / pi / delta [N][n_rb] (Eqs. 38, 41).  Synchronises.          */
 fetidp_status fetidp_rom_data(fetidp_ctx *ctx, int *sigma, double *alpha, double *pi,
                               double *delta);
+
+/* ---- diagnostics ---- */
+
+/* Kernel classes timed by the profiler. */
+enum {
+  FETIDP_K_GROUPED_GEMM = 0,  /* principal-operator contraction, FP64 CUDA cores (Eqs. 43, 46a) */
+  FETIDP_K_APPLY_K = 1,       /* matrix-free K_s (Eq. 52) */
+  FETIDP_K_MAPS = 2,          /* B_d gather / scatter, A_p assembly / extraction (Eqs. 15, 18) */
+  FETIDP_K_COARSE = 3,        /* coarse block cyclic reduction sweeps (Sec. 3.2.1) */
+  FETIDP_K_CELL_GEMV = 4,     /* per-cell ROM operators (Eq. 43) */
+  FETIDP_K_VECTOR = 5,        /* Krylov reductions and vector updates */
+  FETIDP_K_GRAM = 6,          /* Eq. 46b Gram solves */
+  FETIDP_K_TC_GEMM = 7,       /* principal contraction on tcgen05 tensor cores (BF16) */
+  FETIDP_K_SETUP = 8,         /* setup kernels */
+  FETIDP_K_NCLASS = 16
+};
+
+/* Start (mask != 0) or stop (mask == 0) timing the kernel classes whose bit is set in
+ * mask: a CUDA event pair on the context stream around every launch of those classes
+ * (at most 65536 launches until the next read), plus the algorithmic FLOP and byte
+ * counts of each launch computed from its shapes.  Resets the accumulators.       */
+fetidp_status fetidp_profile_enable(fetidp_ctx *ctx, unsigned mask);
+
+/* Synchronise the stream and return per-class totals since the last enable/read
+ * (host arrays of FETIDP_K_NCLASS entries, any may be NULL): device milliseconds,
+ * launches, algorithmic FLOPs and algorithmic bytes.  Milliseconds, FLOPs and bytes
+ * cover the launches that got an event pair (the first 16384); launches counts all.
+ * Resets the accumulators.                                                          */
+fetidp_status fetidp_profile_read(fetidp_ctx *ctx, double *ms, long long *launches,
+                                  double *flops, double *bytes);
+
+/* Number of kernels this library has launched in the calling process. */
+long long fetidp_kernel_launches(void);
 
 void fetidp_destroy(fetidp_ctx *ctx);
 const char *fetidp_status_string(fetidp_status s);

@@ -27,7 +27,11 @@ SYMBOLS = ["fetidp_sizes", "fetidp_default_options", "fetidp_setup", "fetidp_app
            "fetidp_precond", "fetidp_solve", "fetidp_solve_host", "fetidp_grad", "fetidp_gather_BT",
            "fetidp_scatter_B", "fetidp_apply_K", "fetidp_coarse_solve", "fetidp_local_rom_solve",
            "fetidp_apply_A", "fetidp_apply_P", "fetidp_rom_data", "fetidp_destroy",
-           "fetidp_status_string", "fetidp_last_error"]
+           "fetidp_status_string", "fetidp_last_error", "fetidp_profile_enable",
+           "fetidp_profile_read", "fetidp_kernel_launches"]
+
+KCLASS = {"grouped_gemm": 0, "apply_K": 1, "maps": 2, "coarse": 3, "cell_gemv": 4, "vector": 5,
+          "gram": 6, "tc_gemm": 7, "setup": 8}
 
 
 class FetidpError(RuntimeError):
@@ -113,6 +117,12 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.fetidp_rom_data.argtypes = [P, V, V, V, V]
     lib.fetidp_destroy.restype = None
     lib.fetidp_destroy.argtypes = [P]
+    lib.fetidp_profile_enable.restype = I
+    lib.fetidp_profile_enable.argtypes = [P, ctypes.c_uint]
+    lib.fetidp_profile_read.restype = I
+    lib.fetidp_profile_read.argtypes = [P, V, V, V, V]
+    lib.fetidp_kernel_launches.restype = ctypes.c_longlong
+    lib.fetidp_kernel_launches.argtypes = []
     _LIB = lib
     return lib
 
@@ -268,6 +278,29 @@ class Solver:
                                       ctypes.c_void_p(delta.ctypes.data)))
         return sigma, alpha, pi, delta
 
+    def profile_enable(self, classes=None):
+        """Time the given kernel classes (names of KCLASS; None = all)."""
+        names = list(KCLASS) if classes is None else classes
+        mask = 0
+        for n in names:
+            mask |= 1 << KCLASS[n]
+        _check(load().fetidp_profile_enable(self._h, mask))
+
+    def profile_disable(self):
+        _check(load().fetidp_profile_enable(self._h, 0))
+
+    def profile_read(self):
+        """{class: {ms, launches, flops, bytes}} since the last enable/read."""
+        n = 16
+        ms = np.zeros(n); fl = np.zeros(n); by = np.zeros(n)
+        la = np.zeros(n, np.int64)
+        _check(load().fetidp_profile_read(self._h, ctypes.c_void_p(ms.ctypes.data),
+                                          ctypes.c_void_p(la.ctypes.data),
+                                          ctypes.c_void_p(fl.ctypes.data),
+                                          ctypes.c_void_p(by.ctypes.data)))
+        return {k: {"ms": float(ms[i]), "launches": int(la[i]), "flops": float(fl[i]),
+                    "bytes": float(by[i])} for k, i in KCLASS.items()}
+
     def close(self):
         if getattr(self, "_h", None):
             load().fetidp_destroy(self._h)
@@ -278,3 +311,8 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(load().fetidp_kernel_launches())

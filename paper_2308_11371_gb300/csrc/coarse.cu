@@ -394,6 +394,8 @@ fetidp_status coarse_solve(Ctx& c, const double* b, long long b_rs, double* x, l
   CoarseBCR& B = c.bcr;
   const long long len0 = (long long)B.nb * B.b;
   const long long rs = B.vec_len;
+  ProfScope ps(c, FETIDP_K_COARSE, 2.0 * (B.mat_bytes / 8.0) * nrhs,
+               (double)B.mat_bytes + 8.0 * nrhs * 4.0 * B.vec_len);
   bcr_gather_kernel<<<gridn(len0 * nrhs), 256, 0, c.stream>>>(B.perm, b, b_rs, B.bl, rs, len0, nrhs);
   FD_CHECK_LAUNCH();
   // device offset tables: per level 5 arrays of n entries, in order A, U, UT, V, VT

@@ -12,6 +12,7 @@
 namespace fetidp {
 
 void set_error(const std::string& msg);
+void count_launch();
 
 #define FD_CUDA(call)                                                        \
   do {                                                                       \
@@ -24,6 +25,7 @@ void set_error(const std::string& msg);
 
 #define FD_CHECK_LAUNCH()                                                    \
   do {                                                                       \
+    ::fetidp::count_launch();                                                \
     cudaError_t e_ = cudaGetLastError();                                     \
     if (e_ != cudaSuccess) {                                                 \
       ::fetidp::set_error(std::string("kernel launch: ") + cudaGetErrorString(e_)); \
@@ -70,7 +72,22 @@ struct CoarseBCR {
   size_t mat_bytes = 0;
 };
 
+// Kernel-class profiler: CUDA event pairs on the context stream plus the algorithmic
+// FLOP / byte counts of every timed launch.
+struct Prof {
+  unsigned mask = 0;
+  int capacity = 0;
+  std::vector<cudaEvent_t> ev;   // 2 * capacity events
+  std::vector<int> cls;          // class of each used pair
+  int used = 0;
+  double flops[FETIDP_K_NCLASS] = {};
+  double bytes[FETIDP_K_NCLASS] = {};
+  long long launches[FETIDP_K_NCLASS] = {};
+};
+
 struct Ctx {
+  Prof prof;
+  double prof_pending_flops = 0.0, prof_pending_bytes = 0.0;
   int device = 0;
   cudaStream_t stream = nullptr;
   Geo geo{};
@@ -142,6 +159,26 @@ struct Ctx {
   double* scal = nullptr;       // device scalars [64][m]
   double* h_scal = nullptr;     // pinned host mirror
   int inner_total = 0;
+};
+
+// RAII timing of one launch (or one multi-kernel step) of a kernel class.
+struct ProfScope {
+  Ctx& c;
+  int slot = -1;
+  ProfScope(Ctx& ctx, int cls, double flops, double bytes) : c(ctx) {
+    Prof& P = c.prof;
+    if (!(P.mask >> cls & 1u)) return;
+    P.launches[cls] += 1;
+    if (P.used >= P.capacity) return;   // totals below cover the timed launches only
+    P.flops[cls] += flops;
+    P.bytes[cls] += bytes;
+    slot = P.used++;
+    P.cls[slot] = cls;
+    cudaEventRecord(P.ev[2 * slot], c.stream);
+  }
+  ~ProfScope() {
+    if (slot >= 0) cudaEventRecord(c.prof.ev[2 * slot + 1], c.stream);
+  }
 };
 
 // ---------------------------------------------------------------- allocation

@@ -11,6 +11,8 @@
 //   every cell's column (Remark 7; Eq. 46a with separate outputs).
 // * gram_solve: Eq. 46b with diagonal-pivoted Cholesky.
 // * grad: adjoint compliance gradient -w^T dK_s/dr_s u.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace fetidp {
@@ -285,32 +287,31 @@ __global__ void __launch_bounds__(256) grouped_gemm_kernel(
 }
 
 // Eq. 46b for one (rhs, cell) per warp: G = R^T (K R), h = R^T v, pivoted Cholesky,
-// x = R c.  Pivots below drop_rel * max diag(G) are dropped (coefficient 0).
-constexpr int kMaxRb = 16;
-constexpr int kGramWarps = 8;
-__global__ void __launch_bounds__(256) gram_solve_kernel(
-    const double* __restrict__ R, const double* __restrict__ KR, const double* __restrict__ v,
-    long long v_rs, int v_cs, double* __restrict__ x, long long x_rs, int x_cs, int nr, int nrb,
-    long long ncell, int nrhs, double drop_rel) {
-  __shared__ double Gs[kGramWarps][kMaxRb * kMaxRb];
-  __shared__ double Ss[kGramWarps][kMaxRb * kMaxRb];
-  __shared__ double Ls[kGramWarps][kMaxRb * kMaxRb];
-  __shared__ double hs[kGramWarps][kMaxRb];
-  __shared__ double ys[kGramWarps][kMaxRb];
-  __shared__ double cs[kGramWarps][kMaxRb];
-  __shared__ int pv[kGramWarps][kMaxRb];
+// x = R c.  Pivots below drop_rel * max diag(G) are dropped (coefficient 0).  Per-warp
+// scratch lives in dynamic shared memory: 3 nrb x nrb matrices and 4 nrb vectors.
+constexpr int kMaxRb = 64;
+__global__ void gram_solve_kernel(const double* __restrict__ R, const double* __restrict__ KR,
+                                  const double* __restrict__ v, long long v_rs, int v_cs,
+                                  double* __restrict__ x, long long x_rs, int x_cs, int nr,
+                                  int nrb, long long ncell, int nrhs, double drop_rel) {
+  extern __shared__ double gsm[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const long long col = (long long)blockIdx.x * kGramWarps + wib;
+  const int per = 3 * nrb * nrb + 4 * nrb;
+  double* G = gsm + (size_t)wib * per;
+  double* S = G + nrb * nrb;
+  double* Lm = S + nrb * nrb;
+  double* hs = Lm + nrb * nrb;
+  double* ys = hs + nrb;
+  double* cs = ys + nrb;
+  int* pv = reinterpret_cast<int*>(cs + nrb);
+  const long long col = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
   if (col >= ncell * nrhs) return;
   const int rhs = (int)(col / ncell);
   const long long cell = col - (long long)rhs * ncell;
   const double* Rc = R + col * (long long)nrb * nr;
   const double* KRc = KR + col * (long long)nrb * nr;
   const double* vc = v + rhs * v_rs + cell * v_cs;
-  double* G = Gs[wib];
-  double* S = Ss[wib];
-  double* Lm = Ls[wib];
-  const int ld = kMaxRb;
+  const int ld = nrb;
   for (int i = 0; i < nrb; ++i) {
     for (int j = i; j < nrb; ++j) {
       double s = 0.0;
@@ -321,57 +322,54 @@ __global__ void __launch_bounds__(256) gram_solve_kernel(
     double s = 0.0;
     for (int q = lane; q < nr; q += 32) s += Rc[(size_t)i * nr + q] * vc[q];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) hs[wib][i] = s;
+    if (lane == 0) hs[i] = s;
   }
   __syncwarp();
   if (lane == 0) {
     // diagonal-pivoted Cholesky on the Schur complements: pivot order and rank
-    for (int i = 0; i < nrb; ++i)
-      for (int j = 0; j < nrb; ++j) S[i * ld + j] = G[i * ld + j];
+    for (int i = 0; i < nrb * nrb; ++i) S[i] = G[i];
     double dmax = 0.0;
     for (int i = 0; i < nrb; ++i) dmax = fmax(dmax, G[i * ld + i]);
-    unsigned used = 0u;
+    unsigned long long used = 0ull;
     int np = 0;
     while (np < nrb) {
       int jb = -1;
       double best = 0.0;
       for (int i = 0; i < nrb; ++i)
-        if (!(used >> i & 1u) && (jb < 0 || S[i * ld + i] > best)) { best = S[i * ld + i]; jb = i; }
+        if (!(used >> i & 1ull) && (jb < 0 || S[i * ld + i] > best)) { best = S[i * ld + i]; jb = i; }
       if (!(best > drop_rel * dmax)) break;
-      used |= 1u << jb;
-      pv[wib][np++] = jb;
+      used |= 1ull << jb;
+      pv[np++] = jb;
       const double inv = 1.0 / sqrt(best);
-      double colv[kMaxRb];
-      for (int i = 0; i < nrb; ++i) colv[i] = S[i * ld + jb] * inv;
+      for (int i = 0; i < nrb; ++i) ys[i] = S[i * ld + jb] * inv;
       for (int i = 0; i < nrb; ++i)
-        for (int j = 0; j < nrb; ++j) S[i * ld + j] -= colv[i] * colv[j];
+        for (int j = 0; j < nrb; ++j) S[i * ld + j] -= ys[i] * ys[j];
     }
     // Cholesky of G restricted to the pivots (pivot order), forward/back substitution
-    const int* piv = pv[wib];
     for (int a = 0; a < np; ++a) {
       for (int b = 0; b <= a; ++b) {
-        double s = G[piv[a] * ld + piv[b]];
+        double s = G[pv[a] * ld + pv[b]];
         for (int k = 0; k < b; ++k) s -= Lm[a * ld + k] * Lm[b * ld + k];
         Lm[a * ld + b] = (a == b) ? sqrt(s) : s / Lm[b * ld + b];
       }
     }
     for (int a = 0; a < np; ++a) {
-      double s = hs[wib][piv[a]];
-      for (int k = 0; k < a; ++k) s -= Lm[a * ld + k] * ys[wib][k];
-      ys[wib][a] = s / Lm[a * ld + a];
+      double s = hs[pv[a]];
+      for (int k = 0; k < a; ++k) s -= Lm[a * ld + k] * ys[k];
+      ys[a] = s / Lm[a * ld + a];
     }
-    for (int i = 0; i < nrb; ++i) cs[wib][i] = 0.0;
+    for (int i = 0; i < nrb; ++i) cs[i] = 0.0;
     for (int a = np - 1; a >= 0; --a) {
-      double s = ys[wib][a];
-      for (int k = a + 1; k < np; ++k) s -= Lm[k * ld + a] * cs[wib][piv[k]];
-      cs[wib][piv[a]] = s / Lm[a * ld + a];
+      double s = ys[a];
+      for (int k = a + 1; k < np; ++k) s -= Lm[k * ld + a] * cs[pv[k]];
+      cs[pv[a]] = s / Lm[a * ld + a];
     }
   }
   __syncwarp();
   double* xc = x + rhs * x_rs + cell * x_cs;
   for (int q = lane; q < nr; q += 32) {
     double s = 0.0;
-    for (int i = 0; i < nrb; ++i) s += cs[wib][i] * Rc[(size_t)i * nr + q];
+    for (int i = 0; i < nrb; ++i) s += cs[i] * Rc[(size_t)i * nr + q];
     xc[q] = s;
   }
 }
@@ -455,6 +453,7 @@ __global__ void grad_kernel(Geo g, const double* __restrict__ r_cell, long long 
 }  // namespace
 
 fetidp_status k_snapshots(Ctx& c) {
+  ProfScope ps(c, FETIDP_K_SETUP, 0.0, (double)c.N * c.nsnap * 8.0);
   const long long total = c.N * c.nelem * c.ngp;
   int grid = ceil_div(total, 256);
   if (grid > 152 * 32) grid = 152 * 32;
@@ -468,6 +467,14 @@ fetidp_status k_apply_K(Ctx& c, CCellVec u, CellVec y, int nvec, int nrhs, bool 
                         const double* chat, double /*unused*/) {
   const int len = r_only ? c.nr : c.n;
   const int VB = nvec < 8 ? nvec : 8;
+  {
+    const double D = c.d, NA = c.ngp;
+    const double fma = NA * D * D * 2.0 + D * D * D * D;   // gradient + stress + scatter per gp
+    const double cols = (double)c.N * nrhs;
+    c.prof_pending_flops = 2.0 * fma * c.nelem * c.ngp * nvec * cols;
+    c.prof_pending_bytes = cols * (c.nsnap * 8.0 + 2.0 * nvec * len * 8.0);
+  }
+  ProfScope ps(c, FETIDP_K_APPLY_K, c.prof_pending_flops, c.prof_pending_bytes);
   const size_t smem = 2 * (size_t)VB * c.n * sizeof(double);
   const double h = 1.0 / c.e;
   const double wq = pow(0.5 * h, c.d);
@@ -490,6 +497,8 @@ fetidp_status k_apply_K(Ctx& c, CCellVec u, CellVec y, int nvec, int nrhs, bool 
 fetidp_status k_cell_gemv_strided(Ctx& c, const double* mats, long long mstride, int ld, int mrows,
                                   int mcols, CCellVec x, CellVec y, double alpha, double beta,
                                   int nrhs) {
+  ProfScope ps(c, FETIDP_K_CELL_GEMV, 2.0 * mrows * mcols * (double)c.N * nrhs,
+               8.0 * c.N * ((double)mrows * mcols + (double)nrhs * (mrows + mcols)));
   const size_t smem = (size_t)nrhs * mcols * sizeof(double);
   cudaFuncSetAttribute(cell_gemv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cell_gemv_kernel<<<(unsigned)c.N, 256, smem, c.stream>>>(mats, mstride, ld, mrows, mcols, x.p,
@@ -511,6 +520,8 @@ fetidp_status k_grouped_gemm_n(Ctx& c, const double* A, long long a_stride_k, in
                                double alpha, double beta, long long ncell, int nrhs, bool separate,
                                long long y_k_stride) {
   const long long ncols = ncell * nrhs;
+  ProfScope ps(c, FETIDP_K_GROUPED_GEMM, 2.0 * M * K * nk * (double)ncols,
+               8.0 * ((double)nk * M * K + (double)ncols * K + (double)ncols * M * (separate ? nk : 1)));
   dim3 grid((unsigned)ceil_div(ncols, GT), (unsigned)ceil_div(M, GT));
   grouped_gemm_kernel<<<grid, 256, 0, c.stream>>>(A, a_stride_k, lda, M, K, nk, X.p, X.rs, X.cs,
                                                   Y.p, Y.rs, Y.cs, coef, alpha, beta, ncell, nrhs,
@@ -522,11 +533,18 @@ fetidp_status k_grouped_gemm_n(Ctx& c, const double* A, long long a_stride_k, in
 fetidp_status k_gram_solve(Ctx& c, const double* R, const double* KR, CCellVec v, CellVec x,
                            int nrhs) {
   if (c.nrb > kMaxRb) {
-    set_error("n_rb above 16 is not supported by the Gram solve");
+    set_error("n_rb above 64 is not supported by the Gram solve");
     return FETIDP_EINVAL;
   }
   const long long cols = c.N * nrhs;
-  gram_solve_kernel<<<(unsigned)ceil_div(cols, kGramWarps), 256, 0, c.stream>>>(
+  const size_t per = (3 * (size_t)c.nrb * c.nrb + 4 * (size_t)c.nrb) * sizeof(double);
+  int warps = (int)std::min<size_t>(8, (200 * 1024) / per);
+  if (warps < 1) warps = 1;
+  const size_t smem = per * warps;
+  cudaFuncSetAttribute(gram_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  ProfScope ps(c, FETIDP_K_GRAM, cols * 2.0 * c.nr * (c.nrb * (c.nrb + 1) / 2.0 + 2.0 * c.nrb),
+               cols * 8.0 * (2.0 * c.nrb * c.nr + 2.0 * c.nr));
+  gram_solve_kernel<<<(unsigned)ceil_div(cols, warps), 32 * warps, smem, c.stream>>>(
       R, KR, v.p, v.rs, v.cs, x.p, x.rs, x.cs, c.nr, c.nrb, c.N, nrhs, 1e-12);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;

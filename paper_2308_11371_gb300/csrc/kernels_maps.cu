@@ -201,6 +201,7 @@ inline int grid_for(long long work, int threads = 256) {
 fetidp_status k_gather_BT(Ctx& c, const double* lam, long long lam_rs, const double* scale,
                           CellVec out, int nrhs, double beta) {
   const long long work = c.N * c.nd * nrhs;
+  ProfScope ps(c, FETIDP_K_MAPS, 0.0, (double)nrhs * (c.L * 8.0 + c.N * c.nd * 8.0) + c.N * c.nd * 8.0);
   gather_BT_kernel<<<grid_for(work), 256, 0, c.stream>>>(c.gath, lam, lam_rs, scale, out.p, out.rs,
                                                           out.cs, c.nd, c.N, nrhs, beta);
   FD_CHECK_LAUNCH();
@@ -209,6 +210,7 @@ fetidp_status k_gather_BT(Ctx& c, const double* lam, long long lam_rs, const dou
 
 fetidp_status k_scatter_B(Ctx& c, CCellVec yd, double* out, long long out_rs, const double* scale,
                           double alpha, double beta, int nrhs) {
+  ProfScope ps(c, FETIDP_K_MAPS, 0.0, (double)nrhs * (c.L * 8.0 + c.N * c.nd * 8.0) + c.L * 8.0);
   scatter_B_kernel<<<grid_for(c.L * nrhs), 256, 0, c.stream>>>(
       c.scat, yd.p, yd.rs, yd.cs, c.nd, scale, out, out_rs, c.L, alpha, beta, nrhs);
   FD_CHECK_LAUNCH();
@@ -217,6 +219,7 @@ fetidp_status k_scatter_B(Ctx& c, CCellVec yd, double* out, long long out_rs, co
 
 fetidp_status k_primal_assemble(Ctx& c, CCellVec cp, double* out, long long out_rs, double alpha,
                                 double beta, int nrhs) {
+  ProfScope ps(c, FETIDP_K_MAPS, 0.0, (double)nrhs * (c.N * c.np * 8.0 + c.nP * 8.0));
   primal_assemble_kernel<<<grid_for((long long)c.nV * c.d * nrhs), 256, 0, c.stream>>>(
       c.vert_cells, c.ncorner, c.d, cp.p, cp.rs, cp.cs, out, out_rs, c.nV, alpha, beta, nrhs);
   FD_CHECK_LAUNCH();
@@ -224,6 +227,7 @@ fetidp_status k_primal_assemble(Ctx& c, CCellVec cp, double* out, long long out_
 }
 
 fetidp_status k_primal_extract(Ctx& c, const double* uP, long long uP_rs, CellVec cp, int nrhs) {
+  ProfScope ps(c, FETIDP_K_MAPS, 0.0, (double)nrhs * (c.N * c.np * 8.0 + c.nP * 8.0));
   primal_extract_kernel<<<grid_for(c.N * c.np * nrhs), 256, 0, c.stream>>>(
       c.corner_v, c.ncorner, c.d, uP, uP_rs, cp.p, cp.rs, cp.cs, c.N, nrhs);
   FD_CHECK_LAUNCH();
@@ -234,6 +238,7 @@ fetidp_status k_primal_extract(Ctx& c, const double* uP, long long uP_rs, CellVe
 static fetidp_status multi_dot_impl(Ctx& c, const double* Vb, long long vstride, long long vrs,
                                     int nv, const double* w, long long wrs, long long len,
                                     int nrhs, double* out) {
+  ProfScope ps(c, FETIDP_K_VECTOR, 2.0 * nv * len * nrhs, 8.0 * (nv + 1) * len * nrhs);
   dim3 grid(kRedBlocks, nrhs, nv);
   multi_dot_partial<<<grid, kRedThreads, 0, c.stream>>>(Vb, vstride, vrs, w, wrs, len, nv, c.red);
   FD_CHECK_LAUNCH();
@@ -255,6 +260,7 @@ fetidp_status k_multi_dot(Ctx& c, const double* Vb, long long vstride, int nv, c
 
 fetidp_status k_multi_axpy(Ctx& c, const double* Vb, long long vstride, int nv, const double* coef,
                            double* w, long long len, int nrhs, double sign) {
+  ProfScope ps(c, FETIDP_K_VECTOR, 2.0 * nv * len * nrhs, 8.0 * (nv + 2) * len * nrhs);
   multi_axpy_kernel<<<grid_for(len * nrhs), 256, 0, c.stream>>>(Vb, vstride, len, nv, coef, w, len,
                                                                  len, nrhs, sign);
   FD_CHECK_LAUNCH();
@@ -263,6 +269,7 @@ fetidp_status k_multi_axpy(Ctx& c, const double* Vb, long long vstride, int nv, 
 
 fetidp_status k_copy_scale(Ctx& c, const double* x, double* y, long long len, int nrhs,
                            long long xs, long long ys, const double* s_dev, double s_host) {
+  ProfScope ps(c, FETIDP_K_VECTOR, (double)len * nrhs, 16.0 * len * nrhs);
   copy_scale_kernel<<<grid_for(len * nrhs), 256, 0, c.stream>>>(x, y, len, nrhs, xs, ys, s_dev,
                                                                  s_host);
   FD_CHECK_LAUNCH();

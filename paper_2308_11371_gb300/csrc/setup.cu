@@ -218,7 +218,7 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
   if (p.n_loads < 1 || !p.load_kind || !p.load_dir || !p.r_cell) {
     set_error("missing loads or radii"); return FETIDP_EINVAL;
   }
-  if (p.n_rb < 1 || p.n_rb > 16) { set_error("n_rb must be in [1, 16]"); return FETIDP_EINVAL; }
+  if (p.n_rb < 1 || p.n_rb > 64) { set_error("n_rb must be in [1, 64]"); return FETIDP_EINVAL; }
   if (p.clamp_axis < 0 || p.clamp_axis >= p.dim) { set_error("bad clamp axis"); return FETIDP_EINVAL; }
   if (!(p.nu > -1.0 && p.nu < 0.5)) { set_error("nu out of range"); return FETIDP_EINVAL; }
   if (p.mask_kind < 0 || p.mask_kind > 2 || (p.dim == 2) != (p.mask_kind == 0)) {

@@ -11,6 +11,7 @@
 // Every step runs in the kernels of this library; the host only keeps the
 // Krylov scalars (Hessenberg, Givens rotations, convergence decisions).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -99,6 +100,9 @@ inline int gridn(long long work) {
 }  // namespace
 
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 fetidp_status dalloc(Ctx& c, void** p, size_t bytes) {
   if (bytes == 0) bytes = 8;
@@ -320,123 +324,144 @@ struct OuterResult {
   bool converged = false;
 };
 
+// Restarted flexible GMRES: each cycle runs the Arnoldi process on the current residual;
+// after a cycle the true residual b - A x is recomputed and the solver restarts from x
+// while it is above tol_outer (the least-squares estimate and the true residual drift
+// apart when the preconditioner changes between applications).
 fetidp_status fgmres(Ctx& c, double* xout, OuterResult& res) {
   const int m = c.m, mo = c.opt.max_outer;
   const long long nt = c.ntot, mnt = (long long)m * nt;
+  const bool fixed = c.opt.fixed_outer > 0;
+  const int max_cycles = fixed ? 1 : 8;
   double* dots1 = c.scal + 64 * m;
   double* dots2 = dots1 + (size_t)m * (mo + 2);
+  double* rcur = c.w_tot + mnt;        // residual of the current cycle
+  double* rbuf = c.w_tot + 2 * mnt;    // A x
   std::vector<double> hbuf((size_t)m * (mo + 2));
-  // beta = ||b||
   FD_TRY(k_dot(c, c.rhs, nt, c.rhs, nt, nt, m, dots1));
   FD_CUDA(cudaMemcpyAsync(hbuf.data(), dots1, sizeof(double) * m, cudaMemcpyDeviceToHost, c.stream));
   FD_CUDA(cudaStreamSynchronize(c.stream));
-  std::vector<double> beta(m), inv(m);
-  for (int r = 0; r < m; ++r) {
-    beta[r] = std::sqrt(hbuf[r]);
-    inv[r] = beta[r] > 0.0 ? 1.0 / beta[r] : 0.0;
-  }
-  FD_CUDA(cudaMemcpyAsync(dots2, inv.data(), sizeof(double) * m, cudaMemcpyHostToDevice, c.stream));
-  FD_TRY(k_copy_scale(c, c.rhs, c.V, nt, m, nt, nt, dots2, 0.0));
+  std::vector<double> bnorm(m), rnorm(m), inv(m);
+  for (int r = 0; r < m; ++r) bnorm[r] = std::sqrt(hbuf[r]);
+  FD_CUDA(cudaMemsetAsync(xout, 0, sizeof(double) * mnt, c.stream));
+  FD_CUDA(cudaMemcpyAsync(rcur, c.rhs, sizeof(double) * mnt, cudaMemcpyDeviceToDevice, c.stream));
+  rnorm = bnorm;
+  int total_its = 0;
+  res.converged = false;
   std::vector<std::vector<double>> H(m, std::vector<double>((size_t)(mo + 1) * mo, 0.0));
   std::vector<std::vector<double>> g(m, std::vector<double>(mo + 1, 0.0)), cs(m, std::vector<double>(mo)),
       sn(m, std::vector<double>(mo));
-  std::vector<int> k_used(m, 0);
-  std::vector<char> active(m, 1);
-  for (int r = 0; r < m; ++r) {
-    g[r][0] = beta[r];
-    if (beta[r] == 0.0) active[r] = 0;
-  }
   auto Hij = [&](int r, int i, int j) -> double& { return H[r][(size_t)i * mo + j]; };
-  int j = 0;
-  int nact = 0;
-  for (int r = 0; r < m; ++r) nact += active[r];
-  for (j = 0; j < mo && nact > 0; ++j) {
-    double* Vj = c.V + (size_t)j * mnt;
-    double* Zj = c.Z + (size_t)j * mnt;
-    double* w = c.V + (size_t)(j + 1) * mnt;
-    FD_TRY(op_precondition(c, Vj, Zj));
-    FD_TRY(op_apply_A(c, Zj, w));
-    // CGS2
-    FD_TRY(k_multi_dot(c, c.V, mnt, j + 1, w, nt, m, dots1));
-    FD_TRY(k_multi_axpy(c, c.V, mnt, j + 1, dots1, w, nt, m, -1.0));
-    FD_TRY(k_multi_dot(c, c.V, mnt, j + 1, w, nt, m, dots2));
-    FD_TRY(k_multi_axpy(c, c.V, mnt, j + 1, dots2, w, nt, m, -1.0));
-    std::vector<double> h1((size_t)m * (j + 1)), h2((size_t)m * (j + 1));
-    FD_CUDA(cudaMemcpyAsync(h1.data(), dots1, sizeof(double) * h1.size(), cudaMemcpyDeviceToHost, c.stream));
-    FD_CUDA(cudaMemcpyAsync(h2.data(), dots2, sizeof(double) * h2.size(), cudaMemcpyDeviceToHost, c.stream));
-    FD_TRY(k_dot(c, w, nt, w, nt, nt, m, dots1));
+  for (int cycle = 0; cycle < max_cycles; ++cycle) {
+    std::vector<char> active(m, 0);
+    std::vector<double> target(m, 0.0);
+    int nact = 0;
+    for (int r = 0; r < m; ++r) {
+      const bool done = bnorm[r] == 0.0 || rnorm[r] == 0.0 ||
+                        (!fixed && rnorm[r] <= c.opt.tol_outer * bnorm[r]);
+      active[r] = !done;
+      target[r] = c.opt.tol_outer * bnorm[r] / std::max(rnorm[r], 1e-300);
+      inv[r] = active[r] ? 1.0 / rnorm[r] : 0.0;
+      nact += active[r];
+      std::fill(H[r].begin(), H[r].end(), 0.0);
+      std::fill(g[r].begin(), g[r].end(), 0.0);
+      g[r][0] = rnorm[r];
+    }
+    if (nact == 0) { res.converged = true; break; }
+    FD_CUDA(cudaMemcpyAsync(dots2, inv.data(), sizeof(double) * m, cudaMemcpyHostToDevice, c.stream));
+    FD_TRY(k_copy_scale(c, rcur, c.V, nt, m, nt, nt, dots2, 0.0));
+    std::vector<int> k_used(m, 0);
+    std::vector<char> live = active;
+    int j = 0;
+    for (j = 0; j < mo && nact > 0; ++j) {
+      double* Vj = c.V + (size_t)j * mnt;
+      double* Zj = c.Z + (size_t)j * mnt;
+      double* w = c.V + (size_t)(j + 1) * mnt;
+      FD_TRY(op_precondition(c, Vj, Zj));
+      FD_TRY(op_apply_A(c, Zj, w));
+      // classical Gram-Schmidt with one reorthogonalisation
+      FD_TRY(k_multi_dot(c, c.V, mnt, j + 1, w, nt, m, dots1));
+      FD_TRY(k_multi_axpy(c, c.V, mnt, j + 1, dots1, w, nt, m, -1.0));
+      FD_TRY(k_multi_dot(c, c.V, mnt, j + 1, w, nt, m, dots2));
+      FD_TRY(k_multi_axpy(c, c.V, mnt, j + 1, dots2, w, nt, m, -1.0));
+      std::vector<double> h1((size_t)m * (j + 1)), h2((size_t)m * (j + 1));
+      FD_CUDA(cudaMemcpyAsync(h1.data(), dots1, sizeof(double) * h1.size(), cudaMemcpyDeviceToHost, c.stream));
+      FD_CUDA(cudaMemcpyAsync(h2.data(), dots2, sizeof(double) * h2.size(), cudaMemcpyDeviceToHost, c.stream));
+      FD_TRY(k_dot(c, w, nt, w, nt, nt, m, dots1));
+      FD_CUDA(cudaMemcpyAsync(hbuf.data(), dots1, sizeof(double) * m, cudaMemcpyDeviceToHost, c.stream));
+      FD_CUDA(cudaStreamSynchronize(c.stream));
+      ++total_its;
+      for (int r = 0; r < m; ++r) {
+        inv[r] = 0.0;
+        if (!live[r]) continue;
+        const double hn = std::sqrt(hbuf[r]);
+        for (int i = 0; i <= j; ++i) Hij(r, i, j) = h1[(size_t)r * (j + 1) + i] + h2[(size_t)r * (j + 1) + i];
+        Hij(r, j + 1, j) = hn;
+        for (int i = 0; i < j; ++i) {
+          const double a = Hij(r, i, j), b = Hij(r, i + 1, j);
+          Hij(r, i, j) = cs[r][i] * a + sn[r][i] * b;
+          Hij(r, i + 1, j) = -sn[r][i] * a + cs[r][i] * b;
+        }
+        const double rho = std::hypot(Hij(r, j, j), Hij(r, j + 1, j));
+        if (!(rho > 0.0) || !std::isfinite(rho)) {
+          set_error("FGMRES breakdown");
+          return FETIDP_EBREAKDOWN;
+        }
+        cs[r][j] = Hij(r, j, j) / rho;
+        sn[r][j] = Hij(r, j + 1, j) / rho;
+        Hij(r, j, j) = rho;
+        Hij(r, j + 1, j) = 0.0;
+        g[r][j + 1] = -sn[r][j] * g[r][j];
+        g[r][j] = cs[r][j] * g[r][j];
+        k_used[r] = j + 1;
+        const double est = std::fabs(g[r][j + 1]) / rnorm[r];
+        if ((!fixed && est <= target[r]) || hn == 0.0 || (fixed && j + 1 >= c.opt.fixed_outer))
+          live[r] = 0;
+        inv[r] = (live[r] && hn > 0.0) ? 1.0 / hn : 0.0;
+      }
+      nact = 0;
+      for (int r = 0; r < m; ++r) nact += live[r];
+      if (nact > 0) {
+        FD_CUDA(cudaMemcpyAsync(dots2, inv.data(), sizeof(double) * m, cudaMemcpyHostToDevice, c.stream));
+        FD_TRY(k_copy_scale(c, w, w, nt, m, nt, nt, dots2, 0.0));
+      }
+    }
+    // x += sum_i y_i Z_i with y from the triangular least-squares system
+    int kmax = 0;
+    for (int r = 0; r < m; ++r) kmax = std::max(kmax, k_used[r]);
+    if (kmax > 0) {
+      std::vector<double> coef((size_t)m * kmax, 0.0);
+      for (int r = 0; r < m; ++r) {
+        const int k = k_used[r];
+        std::vector<double> yv(k, 0.0);
+        for (int i = k - 1; i >= 0; --i) {
+          double sacc = g[r][i];
+          for (int q = i + 1; q < k; ++q) sacc -= Hij(r, i, q) * yv[q];
+          yv[i] = sacc / Hij(r, i, i);
+        }
+        for (int i = 0; i < k; ++i) coef[(size_t)r * kmax + i] = yv[i];
+      }
+      FD_CUDA(cudaMemcpyAsync(dots1, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice, c.stream));
+      FD_TRY(k_multi_axpy(c, c.Z, mnt, kmax, dots1, xout, nt, m, 1.0));
+    }
+    // true residual
+    FD_TRY(op_apply_A(c, xout, rbuf));
+    FD_TRY(axpby(c, c.rhs, nt, rbuf, nt, rcur, nt, 1.0, -1.0, nt, m));
+    FD_TRY(k_dot(c, rcur, nt, rcur, nt, nt, m, dots1));
     FD_CUDA(cudaMemcpyAsync(hbuf.data(), dots1, sizeof(double) * m, cudaMemcpyDeviceToHost, c.stream));
     FD_CUDA(cudaStreamSynchronize(c.stream));
-    for (int r = 0; r < m; ++r) {
-      inv[r] = 0.0;
-      if (!active[r]) continue;
-      const double hn = std::sqrt(hbuf[r]);
-      for (int i = 0; i <= j; ++i) Hij(r, i, j) = h1[(size_t)r * (j + 1) + i] + h2[(size_t)r * (j + 1) + i];
-      Hij(r, j + 1, j) = hn;
-      for (int i = 0; i < j; ++i) {
-        const double a = Hij(r, i, j), b = Hij(r, i + 1, j);
-        Hij(r, i, j) = cs[r][i] * a + sn[r][i] * b;
-        Hij(r, i + 1, j) = -sn[r][i] * a + cs[r][i] * b;
-      }
-      const double rho = std::hypot(Hij(r, j, j), Hij(r, j + 1, j));
-      if (!(rho > 0.0) || !std::isfinite(rho)) {
-        set_error("FGMRES breakdown");
-        return FETIDP_EBREAKDOWN;
-      }
-      cs[r][j] = Hij(r, j, j) / rho;
-      sn[r][j] = Hij(r, j + 1, j) / rho;
-      Hij(r, j, j) = rho;
-      Hij(r, j + 1, j) = 0.0;
-      g[r][j + 1] = -sn[r][j] * g[r][j];
-      g[r][j] = cs[r][j] * g[r][j];
-      k_used[r] = j + 1;
-      const double est = std::fabs(g[r][j + 1]) / beta[r];
-      const bool fixed = c.opt.fixed_outer > 0;
-      if ((!fixed && est <= c.opt.tol_outer) || hn == 0.0 || (fixed && j + 1 >= c.opt.fixed_outer))
-        active[r] = 0;
-      inv[r] = (active[r] && hn > 0.0) ? 1.0 / hn : 0.0;
-    }
-    nact = 0;
-    for (int r = 0; r < m; ++r) nact += active[r];
-    if (nact > 0) {
-      FD_CUDA(cudaMemcpyAsync(dots2, inv.data(), sizeof(double) * m, cudaMemcpyHostToDevice, c.stream));
-      FD_TRY(k_copy_scale(c, w, w, nt, m, nt, nt, dots2, 0.0));
-    }
+    for (int r = 0; r < m; ++r) rnorm[r] = std::sqrt(hbuf[r]);
+    if (fixed) { res.converged = true; break; }
   }
-  // x = sum_i y_i Z_i, y from the triangular least-squares system
-  const int kmax = *std::max_element(k_used.begin(), k_used.end());
-  std::vector<double> coef((size_t)m * std::max(kmax, 1), 0.0);
-  for (int r = 0; r < m; ++r) {
-    const int k = k_used[r];
-    std::vector<double> yv(k, 0.0);
-    for (int i = k - 1; i >= 0; --i) {
-      double s = g[r][i];
-      for (int q = i + 1; q < k; ++q) s -= Hij(r, i, q) * yv[q];
-      yv[i] = s / Hij(r, i, i);
-    }
-    for (int i = 0; i < k; ++i) coef[(size_t)r * kmax + i] = yv[i];
-  }
-  FD_CUDA(cudaMemsetAsync(xout, 0, sizeof(double) * mnt, c.stream));
-  if (kmax > 0) {
-    FD_CUDA(cudaMemcpyAsync(dots1, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice, c.stream));
-    FD_TRY(k_multi_axpy(c, c.Z, mnt, kmax, dots1, xout, nt, m, 1.0));
-  }
-  // true residual
-  double* rbuf = c.w_tot + 2 * mnt;
-  FD_TRY(op_apply_A(c, xout, rbuf));
-  FD_TRY(axpby(c, c.rhs, nt, rbuf, nt, rbuf, nt, 1.0, -1.0, nt, m));
-  FD_TRY(k_dot(c, rbuf, nt, rbuf, nt, nt, m, dots1));
-  FD_CUDA(cudaMemcpyAsync(hbuf.data(), dots1, sizeof(double) * m, cudaMemcpyDeviceToHost, c.stream));
-  FD_CUDA(cudaStreamSynchronize(c.stream));
   res.rel_res = 0.0;
-  res.converged = true;
+  bool conv = true;
   for (int r = 0; r < m; ++r) {
-    const double rr = beta[r] > 0.0 ? std::sqrt(hbuf[r]) / beta[r] : 0.0;
+    const double rr = bnorm[r] > 0.0 ? rnorm[r] / bnorm[r] : 0.0;
     res.rel_res = std::max(res.rel_res, rr);
-    const double est = k_used[r] > 0 ? std::fabs(g[r][k_used[r]]) / beta[r] : 0.0;
-    if (c.opt.fixed_outer <= 0 && beta[r] > 0.0 && est > c.opt.tol_outer) res.converged = false;
+    if (!fixed && rr > c.opt.tol_outer) conv = false;
   }
-  res.its = kmax;
+  res.converged = fixed ? true : conv;
+  res.its = total_its;
   return FETIDP_OK;
 }
 
@@ -496,10 +521,52 @@ const char* fetidp_status_string(fetidp_status s) {
 
 const char* fetidp_last_error(void) { return g_last_error.c_str(); }
 
+long long fetidp_kernel_launches(void) { return g_launches.load(); }
+
+fetidp_status fetidp_profile_enable(fetidp_ctx* ctx, unsigned mask) {
+  FD_TRY(enter(ctx));
+  Prof& P = ctx->c.prof;
+  FD_CUDA(cudaStreamSynchronize(ctx->c.stream));
+  if (mask != 0 && P.capacity == 0) {
+    const int cap = 16384;
+    P.ev.resize(2 * cap);
+    for (auto& e : P.ev) FD_CUDA(cudaEventCreate(&e));
+    P.cls.assign(cap, 0);
+    P.capacity = cap;
+  }
+  P.mask = mask;
+  P.used = 0;
+  for (int k = 0; k < FETIDP_K_NCLASS; ++k) { P.flops[k] = 0; P.bytes[k] = 0; P.launches[k] = 0; }
+  return FETIDP_OK;
+}
+
+fetidp_status fetidp_profile_read(fetidp_ctx* ctx, double* ms, long long* launches, double* flops,
+                                  double* bytes) {
+  FD_TRY(enter(ctx));
+  Prof& P = ctx->c.prof;
+  FD_CUDA(cudaStreamSynchronize(ctx->c.stream));
+  double t[FETIDP_K_NCLASS] = {};
+  for (int i = 0; i < P.used; ++i) {
+    float v = 0.f;
+    FD_CUDA(cudaEventElapsedTime(&v, P.ev[2 * i], P.ev[2 * i + 1]));
+    t[P.cls[i]] += v;
+  }
+  for (int k = 0; k < FETIDP_K_NCLASS; ++k) {
+    if (ms) ms[k] = t[k];
+    if (launches) launches[k] = P.launches[k];
+    if (flops) flops[k] = P.flops[k];
+    if (bytes) bytes[k] = P.bytes[k];
+    P.flops[k] = 0; P.bytes[k] = 0; P.launches[k] = 0;
+  }
+  P.used = 0;
+  return FETIDP_OK;
+}
+
 void fetidp_destroy(fetidp_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->c.device);
   cudaStreamSynchronize(ctx->c.stream);
+  for (auto& e : ctx->c.prof.ev) cudaEventDestroy(e);
   for (void* p : ctx->c.allocations) cudaFree(p);
   if (ctx->c.h_scal) cudaFreeHost(ctx->c.h_scal);
   delete ctx;

@@ -124,11 +124,20 @@ def config1(seed: int = 1) -> LatticeProblem:
     return _frame_problem(4, 4, 8, np.full(16, 0.12), a, 2, "2d_4x4_e8")
 
 
-def config2(seed: int = 2) -> LatticeProblem:
-    """2D plane strain, 64x64 cells of 16x16 Q1, graded r_s, a ~ U[0, 4], 8 principal cells."""
+# Principal cells used when the 64x64 lattice is solved to rel. residual 1e-8.  With the
+# hard strut mask and the column-graded radius the Gauss-point tensor jumps between solid
+# and void as r_s changes, so 8 principal cells cannot represent the 64 distinct columns:
+# the outer solver stagnates (measured on the oracle and on the GPU).  32 principal cells
+# converge in a few outer iterations, following the paper's advice to grow the reduced
+# basis until the global iterations are few (Sec. 5.1.2, Fig. 9).
+CONFIG2_SOLVE_N_RB = 32
+
+
+def config2(seed: int = 2, n_rb: int = 8) -> LatticeProblem:
+    """2D plane strain, 64x64 cells of 16x16 Q1, graded r_s, a ~ U[0, 4], n_rb principal cells."""
     rng = np.random.default_rng(seed)
     a = rng.uniform(0.0, 4.0)
-    p = lattice_2d(64, 64, 16, a=a, r=0.1, n_rb=8, r_grade=0.05, name="2d_64x64_e16")
+    p = lattice_2d(64, 64, 16, a=a, r=0.1, n_rb=n_rb, r_grade=0.05, name="2d_64x64_e16")
     return p
 
 
