@@ -215,6 +215,8 @@ def main():
     ap.add_argument("--precision", default="best", choices=["fp64", "mixed", "best"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=16)
+    ap.add_argument("--cells", type=int, default=64,
+                    help="cells per side (64 = the benchmark workload; smaller for profiling)")
     args = ap.parse_args()
     rank, world, local = dist_init()
     if args.impl == "reference":
@@ -227,7 +229,9 @@ def main():
     torch.cuda.set_device(local)
     binding.load()
     prob = W.config2(n_rb=W.CONFIG2_SOLVE_N_RB)
-    prec_name = {"fp64": "fp64", "mixed": "mixed", "best": "fp64"}[args.precision]
+    if args.cells != 64:   # same cell / mask / radius law / bend, fewer cells (profiling runs)
+        prob = sample_problem(args.cells)
+    prec_name = {"fp64": "fp64", "mixed": "mixed", "best": "mixed"}[args.precision]
     precision = binding.FETIDP_FP64 if prec_name == "fp64" else binding.FETIDP_MIXED_BF16
     stream = torch.cuda.current_stream()
     dof = prob.n_cells * 578 * prob.n_rhs
@@ -240,6 +244,21 @@ def main():
         prof = s.profile_read() if profile is not None else None
         s.close()
         return info, prof
+
+    # the plain FP64 path on the same workload, for the mixed-vs-FP64 comparison (one step)
+    fp64_ref = None
+    if prec_name == "mixed":
+        s64 = binding.Solver(prob, precision=binding.FETIDP_FP64)
+        s64.close()
+        torch.cuda.synchronize()
+        f0 = time.perf_counter()
+        s64 = binding.Solver(prob, precision=binding.FETIDP_FP64)
+        _, _, info64 = s64.solve()
+        s64.close()
+        torch.cuda.synchronize()
+        fp64_ref = {"ms": 1e3 * (time.perf_counter() - f0), "outer_its": info64["outer_its"],
+                    "inner_its_total": info64["inner_its_total"],
+                    "t_setup_ms": 1e3 * info64["t_setup_s"], "t_solve_ms": 1e3 * info64["t_solve_s"]}
 
     # warm-up; the first step also profiles every kernel class to find the dominant one
     info0, prof0 = one_step(profile=list(binding.KCLASS))
@@ -290,7 +309,7 @@ def main():
     by = sum(p["bytes"] for p in profs)
     kms = sum(p["ms"] for p in profs)
     nl = sum(p["launches"] for p in profs)
-    if dominant in ("grouped_gemm", "gram"):
+    if dominant in ("grouped_gemm", "gram") and prec_name == "fp64":
         achieved = fl / (kms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "peak_source": "derived FP64 DFMA rate (152 SMs x 2 DFMA/clk x 2.07 GHz)"}
@@ -321,7 +340,8 @@ def main():
         "dtype": "f64" if prec_name == "fp64" else "bf16-tc/f32/f64",
         "data": "synthetic",
         "config": {
-            "workload": "2d_64x64_e16", "cells": [64, 64], "q1_per_cell": [16, 16],
+            "workload": "2d_64x64_e16" if args.cells == 64 else f"2d_{args.cells}x{args.cells}_e16",
+            "cells": [args.cells, args.cells], "q1_per_cell": [16, 16],
             "dof": dof, "rhs": prob.n_rhs, "n_rb": info0["n_rb"], "precision": prec_name,
             "n_rb_note": "8 principal cells stagnate on this hard-mask lattice; 32 used",
             "step": "fetidp_setup + fetidp_solve to outer rel. residual 1e-8",
@@ -332,6 +352,8 @@ def main():
             "t_solve_ms": 1e3 * statistics.median(i["t_solve_s"] for i in infos),
             "device_bytes": infos[-1]["device_bytes"],
             "parallelism": f"replicas x{world}",
+            "fp64_path": fp64_ref,
+            "speedup_vs_fp64": (fp64_ref["ms"] / (ms_max / args.steps)) if fp64_ref else None,
         },
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,

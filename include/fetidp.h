@@ -114,6 +114,10 @@ typedef struct {
   int precision;            /* fetidp_precision (FETIDP_FP64) */
   int fixed_outer;          /* > 0: run exactly this many outer iterations (iterate-locked) */
   int fixed_inner;          /* > 0: run exactly this many PCG iterations per application */
+  int tc_split;             /* mixed: 1 = one BF16 x BF16 product per contraction; 3 = operands
+                               split into hi + lo BF16 parts, three products (hi hi, hi lo,
+                               lo hi) for ~16-bit input precision (default 3)                */
+  double tol_inner_mixed;   /* inner PCG tolerance used by the mixed path (1e-6)             */
 } fetidp_options;
 
 typedef struct {
@@ -235,6 +239,13 @@ fetidp_status fetidp_profile_enable(fetidp_ctx *ctx, unsigned mask);
  * Resets the accumulators.                                                          */
 fetidp_status fetidp_profile_read(fetidp_ctx *ctx, double *ms, long long *launches,
                                   double *flops, double *bytes);
+
+/* Self-check of the tcgen05 tensor-core GEMM on the current device: random A (M x K) and
+ * N columns X, packed to BF16, multiplied on the tensor cores with FP32 accumulation and
+ * compared with an FP64 GEMM of the same BF16-rounded inputs.  *rel_err receives
+ * max |Y_tc - Y_ref| / max |Y_ref|.  Allocates and frees its own scratch (diagnostic only).
+ * ETIMEOUT if a bounded device wait expired.                                           */
+fetidp_status fetidp_tc_selfcheck(int M, int K, int N, double *rel_err);
 
 /* Number of kernels this library has launched in the calling process. */
 long long fetidp_kernel_launches(void);

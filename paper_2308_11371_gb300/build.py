@@ -16,7 +16,9 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
-LIB = os.path.join(OUT_DIR, "libfetidp.so")
+# FETIDP_CHECKED=1 selects the debug build whose kernels bounds-check their accesses
+CHECKED = os.environ.get("FETIDP_CHECKED", "0") == "1"
+LIB = os.path.join(OUT_DIR, "libfetidp_checked.so" if CHECKED else "libfetidp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3"]
 
@@ -54,8 +56,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj]
+        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + (".chk.o" if CHECKED else ".o"))
+        cmd = [nvcc, *ARCH, *FLAGS, *(["-DFETIDP_BOUNDS_CHECK"] if CHECKED else []), "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")

@@ -39,18 +39,79 @@ void count_launch();
     if (s_ != FETIDP_OK) return s_;               \
   } while (0)
 
+// One Eq. 42 trace table: gradients of two column sets of ncol columns each.
+struct TraceTableSpec {
+  const double* Gi;
+  const double* Gj;
+  int ncol;
+};
+
+// ---------------------------------------------------------------- debug bounds checks
+// Built with -DFETIDP_BOUNDS_CHECK, the kernels of the mixed local-ROM chain compare their
+// global accesses with the extent of the buffer they touch; a violation is recorded in
+// g_fd_violation (kernel code, offending index, extent) and the access is skipped.
+struct FdViolation {
+  int code;
+  long long index;
+  long long extent;
+};
+#ifdef FETIDP_BOUNDS_CHECK
+static __device__ FdViolation g_fd_violation;   // one record per translation unit
+__device__ __forceinline__ bool fd_in_bounds(long long idx, long long extent, int code) {
+  if (extent < 0 || (idx >= 0 && idx < extent)) return true;   // extent < 0: unknown, unchecked
+  if (atomicCAS(&g_fd_violation.code, 0, code) == 0) {
+    g_fd_violation.index = idx;
+    g_fd_violation.extent = extent;
+  }
+  return false;
+}
+#define FD_INB(idx, extent, code) fd_in_bounds((long long)(idx), (long long)(extent), (code))
+#define FD_CHECKED_BUILD 1
+#else
+#define FD_INB(idx, extent, code) true
+#define FD_CHECKED_BUILD 0
+#endif
+// per-translation-unit readers of the violation record (FETIDP_OK in unchecked builds)
+fetidp_status fd_check_cell(const char* where);
+fetidp_status fd_check_tc(const char* where);
+#ifdef FETIDP_BOUNDS_CHECK
+#define FD_DEFINE_CHECK(fname)                                                                  \
+  fetidp_status fname(const char* where) {                                                       \
+    FdViolation h{};                                                                             \
+    const cudaError_t se = cudaDeviceSynchronize();                                              \
+    if (se != cudaSuccess) {                                                                     \
+      set_error(std::string("after ") + where + ": " + cudaGetErrorString(se));                  \
+      return FETIDP_ECUDA;                                                                       \
+    }                                                                                            \
+    cudaMemcpyFromSymbol(&h, g_fd_violation, sizeof(h));                                         \
+    if (h.code != 0) {                                                                           \
+      FdViolation z{};                                                                           \
+      cudaMemcpyToSymbol(g_fd_violation, &z, sizeof(z));                                         \
+      set_error(std::string("bounds check in ") + where + ": code " + std::to_string(h.code) +   \
+                " index " + std::to_string(h.index) + " extent " + std::to_string(h.extent));    \
+      return FETIDP_ECUDA;                                                                       \
+    }                                                                                            \
+    return FETIDP_OK;                                                                            \
+  }
+#else
+#define FD_DEFINE_CHECK(fname) \
+  fetidp_status fname(const char*) { return FETIDP_OK; }
+#endif
+
 // Per-cell vector view: element (rhs, cell, i) at p[rhs*rs + cell*cs + i].
 struct CellVec {
   double* p;
   long long rs;   // RHS stride
   int cs;         // cell stride
+  long long ext = -1;   // elements addressable from p (checked builds; -1 = unknown)
 };
 struct CCellVec {
   const double* p;
   long long rs;
   int cs;
+  long long ext = -1;
 };
-inline CCellVec cview(const CellVec& v) { return {v.p, v.rs, v.cs}; }
+inline CCellVec cview(const CellVec& v) { return {v.p, v.rs, v.cs, v.ext}; }
 
 // Block cyclic reduction of the block-tridiagonal coarse matrix (slab ordering).
 struct CoarseBCR {
@@ -70,6 +131,15 @@ struct CoarseBCR {
   double* bl = nullptr;            // device [m][vec_len] right-hand sides per level
   double* xl = nullptr;            // device [m][vec_len] solutions per level
   size_t mat_bytes = 0;
+};
+
+// A principal-operator set packed for the tensor-core GEMM (BF16, SW128 K-major tiles).
+struct TcOperator {
+  uint8_t* tiles = nullptr;
+  int M = 0, K = 0, nops = 0, nterm = 1;
+  bool separate = false;
+  int m_tiles = 0, k_tiles_op = 0, k_tiles = 0;
+  long long batch_bytes = 0;
 };
 
 // Kernel-class profiler: CUDA event pairs on the context stream plus the algorithmic
@@ -159,6 +229,16 @@ struct Ctx {
   double* scal = nullptr;       // device scalars [64][m]
   double* h_scal = nullptr;     // pinned host mirror
   int inner_total = 0;
+  // tensor-core path (mixed precision)
+  bool mixed = false;           // FETIDP_MIXED_BF16
+  TcOperator opKinv;            // K_rr^(k)^{-1}, separate (Eq. 46a)
+  TcOperator opUrdT;            // U_rd^(k)T = rows d of K_rr^(k)^{-1}, combined with delta (Alg. 3)
+  TcOperator opUrd;             // U_rd^(k) = columns d of K_rr^(k)^{-1}, combined with delta
+  TcOperator opFdd;             // F_dd^(k), combined with delta (Eq. 48)
+  TcOperator opSdd;             // S_dd^(k), combined with alpha (Eq. 49)
+  uint8_t* tc_bbuf = nullptr;   // packed B operand staging
+  size_t tc_bbuf_bytes = 0;
+  int* tc_err = nullptr;        // device error flag of the bounded waits
 };
 
 // RAII timing of one launch (or one multi-kernel step) of a kernel class.
@@ -222,6 +302,19 @@ fetidp_status k_grouped_gemm_n(Ctx& c, const double* A, long long a_stride_k, in
 fetidp_status k_gram_solve(Ctx& c, const double* R, const double* KR, CCellVec v, CellVec x,
                            int nrhs);
 fetidp_status k_grad(Ctx& c, const double* u, const double* w, double* g);
+fetidp_status k_apply_K_f32(Ctx& c, const float* u, long long u_rs, int u_cs, float* y, long long y_rs,
+                            int y_cs, int nvec, int nrhs, bool idp, bool r_only, long long ext = -1);
+fetidp_status k_gram_solve_f32(Ctx& c, const float* R, const float* KR, CCellVec v, CellVec x,
+                               int nrhs, long long r_ext = -1);
+
+// ---------------------------------------------------------------- tensor cores (tc_gemm.cu)
+int tc_bn_for(long long ncols, int m_tiles, int batch);
+fetidp_status tc_pack_operator(Ctx& c, TcOperator& op, const double* src, long long op_stride, int lda,
+                               int r0, int c0, int M, int K, int nops, bool separate, int nterm);
+fetidp_status tc_apply(Ctx& c, const TcOperator& op, CCellVec X, const double* coef, void* Y,
+                       bool y_f64, long long y_rs, int y_cs, long long y_b_stride, double alpha,
+                       double beta, int nrhs, long long ncell, long long y_ext = -1);
+fetidp_status tc_selfcheck(Ctx& c, int M, int K, int N, double* rel_err);
 
 // ---------------------------------------------------------------- setup / coarse
 fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_options& o);

@@ -45,48 +45,47 @@ __global__ void snapshot_kernel(Geo g, const double* __restrict__ r_cell, long l
 }
 
 // Element contribution f_e = sum_gp w dN^T C_hat dN u_e for one element and one vector.
-template <int D>
+template <int D, typename T>
 __device__ __forceinline__ void element_apply(const double* __restrict__ chat_el, int nc,
-                                              double wq, double inv_h, const double* ue,
-                                              double* fe) {
+                                              T wq, T inv_h, const T* ue, T* fe) {
   constexpr int NA = 1 << D;
   constexpr int NI = D * D;
-  for (int k = 0; k < NA * D; ++k) fe[k] = 0.0;
+  for (int k = 0; k < NA * D; ++k) fe[k] = T(0);
   for (int gp = 0; gp < NA; ++gp) {
-    double t[D];
-    for (int k = 0; k < D; ++k) t[k] = gauss_t((gp >> k) & 1);
+    T t[D];
+    for (int k = 0; k < D; ++k) t[k] = (T)gauss_t((gp >> k) & 1);
     // dN_A / dxi_a
-    double dN[NA][D];
+    T dN[NA][D];
     for (int A = 0; A < NA; ++A) {
       for (int a = 0; a < D; ++a) {
-        double v = inv_h;
+        T v = inv_h;
         for (int k = 0; k < D; ++k) {
           const int off = (A >> k) & 1;
-          if (k == a) v *= off ? 1.0 : -1.0;
-          else v *= off ? t[k] : 1.0 - t[k];
+          if (k == a) v *= off ? T(1) : T(-1);
+          else v *= off ? t[k] : T(1) - t[k];
         }
         dN[A][a] = v;
       }
     }
-    double G[NI];
-    for (int I = 0; I < NI; ++I) G[I] = 0.0;
+    T G[NI];
+    for (int I = 0; I < NI; ++I) G[I] = T(0);
     for (int A = 0; A < NA; ++A)
       for (int i = 0; i < D; ++i)
         for (int a = 0; a < D; ++a) G[i * D + a] += ue[A * D + i] * dN[A][a];
-    double S[NI];
-    for (int I = 0; I < NI; ++I) S[I] = 0.0;
+    T S[NI];
+    for (int I = 0; I < NI; ++I) S[I] = T(0);
     const double* C = chat_el + gp * nc;
     int q = 0;
     for (int I = 0; I < NI; ++I) {
       for (int J = I; J < NI; ++J) {
-        const double cij = C[q++];
+        const T cij = (T)C[q++];
         S[I] += cij * G[J];
         if (J != I) S[J] += cij * G[I];
       }
     }
     for (int A = 0; A < NA; ++A)
       for (int i = 0; i < D; ++i) {
-        double v = 0.0;
+        T v = T(0);
         for (int a = 0; a < D; ++a) v += dN[A][a] * S[i * D + a];
         fe[A * D + i] += wq * v;
       }
@@ -94,36 +93,42 @@ __device__ __forceinline__ void element_apply(const double* __restrict__ chat_el
 }
 
 // One block per (rhs, cell) column; vectors of the column processed VB at a time.
-template <int D>
+// T = double (FP64 path) or float (the Eq. 46b products of the mixed path).
+template <int D, typename T>
 __global__ void apply_K_kernel(int e, long long ncell, int n, int len, const int* __restrict__ perm,
-                               const int* __restrict__ iperm, bool idp, const double* __restrict__ u,
-                               long long u_rs, int u_cs, double* __restrict__ y, long long y_rs,
+                               const int* __restrict__ iperm, bool idp, const T* __restrict__ u,
+                               long long u_rs, int u_cs, T* __restrict__ y, long long y_rs,
                                int y_cs, int nvec, int VB, const double* __restrict__ chat, int nc,
-                               double wq, double inv_h) {
-  extern __shared__ double sm[];
+                               T wq, T inv_h, long long u_ext, long long y_ext) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* sm = reinterpret_cast<T*>(sm_raw);
   constexpr int NA = 1 << D;
   const long long col = blockIdx.x;
   const int rhs = (int)(col / ncell);
   const long long cell = col - (long long)rhs * ncell;
-  const double* uc = u + rhs * u_rs + cell * u_cs;
-  double* yc = y + rhs * y_rs + cell * y_cs;
+  const T* uc = u + rhs * u_rs + cell * u_cs;
+  T* yc = y + rhs * y_rs + cell * y_cs;
   const double* chat_cell = chat + cell * (long long)nc * NA * (e * e * (D == 3 ? e : 1));
-  double* us = sm;
-  double* ys = sm + (size_t)VB * n;
+  T* us = sm;
+  T* ys = sm + (size_t)VB * n;
   const int ecount[3] = {e, e, D == 3 ? e : 1};
   for (int v0 = 0; v0 < nvec; v0 += VB) {
     const int vb = min(VB, nvec - v0);
     for (int t = threadIdx.x; t < vb * n; t += blockDim.x) {
       const int v = t / n, i = t - v * n;     // i natural index
-      double val;
+      T val;
       if (idp) {
         const int li = iperm[i];
-        val = li < len ? uc[(size_t)(v0 + v) * len + li] : 0.0;
+        val = (li < len && FD_INB(rhs * u_rs + cell * u_cs + (long long)(v0 + v) * len + li, u_ext, 201))
+                  ? uc[(size_t)(v0 + v) * len + li]
+                  : T(0);
       } else {
-        val = uc[(size_t)(v0 + v) * len + i];
+        val = FD_INB(rhs * u_rs + cell * u_cs + (long long)(v0 + v) * len + i, u_ext, 201)
+                  ? uc[(size_t)(v0 + v) * len + i]
+                  : T(0);
       }
       us[t] = val;
-      ys[t] = 0.0;
+      ys[t] = T(0);
     }
     __syncthreads();
     for (int color = 0; color < NA; ++color) {
@@ -144,12 +149,12 @@ __global__ void apply_K_kernel(int e, long long ncell, int n, int len, const int
           const int ax = A & 1, ay = (A >> 1) & 1, az = (A >> 2) & 1;
           nodes[A] = (ex + ax) + (e + 1) * ((ey + ay) + (e + 1) * (D == 3 ? (ez + az) : 0));
         }
-        double ue[NA * D], fe[NA * D];
-        const double* uv = us + (size_t)v * n;
+        T ue[NA * D], fe[NA * D];
+        const T* uv = us + (size_t)v * n;
         for (int A = 0; A < NA; ++A)
           for (int i = 0; i < D; ++i) ue[A * D + i] = uv[nodes[A] * D + i];
-        element_apply<D>(chat_cell + (size_t)el * NA * nc, nc, wq, inv_h, ue, fe);
-        double* yv = ys + (size_t)v * n;
+        element_apply<D, T>(chat_cell + (size_t)el * NA * nc, nc, wq, inv_h, ue, fe);
+        T* yv = ys + (size_t)v * n;
         for (int A = 0; A < NA; ++A)
           for (int i = 0; i < D; ++i) yv[nodes[A] * D + i] += fe[A * D + i];
       }
@@ -158,7 +163,8 @@ __global__ void apply_K_kernel(int e, long long ncell, int n, int len, const int
     for (int t = threadIdx.x; t < vb * len; t += blockDim.x) {
       const int v = t / len, li = t - v * len;
       const int nat = idp ? perm[li] : li;
-      yc[(size_t)(v0 + v) * len + li] = ys[(size_t)v * n + nat];
+      if (FD_INB(rhs * y_rs + cell * y_cs + (long long)(v0 + v) * len + li, y_ext, 202))
+        yc[(size_t)(v0 + v) * len + li] = ys[(size_t)v * n + nat];
     }
     __syncthreads();
   }
@@ -286,90 +292,99 @@ __global__ void __launch_bounds__(256) grouped_gemm_kernel(
   }
 }
 
-// Eq. 46b for one (rhs, cell) per warp: G = R^T (K R), h = R^T v, pivoted Cholesky,
-// x = R c.  Pivots below drop_rel * max diag(G) are dropped (coefficient 0).  Per-warp
-// scratch lives in dynamic shared memory: 3 nrb x nrb matrices and 4 nrb vectors.
+// Eq. 46b for one (rhs, cell) per warp: G = R^T (K R) and h = R^T v by lane-strided dot
+// products with a shuffle reduction, then lane 0 runs the diagonal-pivoted Cholesky and the
+// triangular solves on the warp's shared-memory scratch, and the warp forms x = R c.  Pivots
+// below drop_rel * max diag(G) are dropped (coefficient 0).
+// Scratch per warp (doubles): G, S, L (nrb x nrb each), h, y, c (nrb each), then nrb ints.
 constexpr int kMaxRb = 64;
-__global__ void gram_solve_kernel(const double* __restrict__ R, const double* __restrict__ KR,
-                                  const double* __restrict__ v, long long v_rs, int v_cs,
-                                  double* __restrict__ x, long long x_rs, int x_cs, int nr,
-                                  int nrb, long long ncell, int nrhs, double drop_rel) {
-  extern __shared__ double gsm[];
+__host__ __device__ inline int gram_warp_doubles(int nrb) { return 3 * nrb * nrb + 4 * nrb; }
+
+template <typename TB>
+__global__ void gram_warp_kernel(const TB* __restrict__ R, const TB* __restrict__ KR,
+                                 const double* __restrict__ v, long long v_rs, int v_cs,
+                                 double* __restrict__ x, long long x_rs, int x_cs, int nr, int nrb,
+                                 long long ncell, int nrhs, double drop_rel) {
+  extern __shared__ double gwsm[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int per = 3 * nrb * nrb + 4 * nrb;
-  double* G = gsm + (size_t)wib * per;
-  double* S = G + nrb * nrb;
-  double* Lm = S + nrb * nrb;
-  double* hs = Lm + nrb * nrb;
+  const long long col = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
+  if (col >= ncell * nrhs) return;                  // the whole warp leaves together
+  const int nb2 = nrb * nrb;
+  double* G = gwsm + (size_t)wib * gram_warp_doubles(nrb);
+  double* S = G + nb2;
+  double* Lm = S + nb2;
+  double* hs = Lm + nb2;
   double* ys = hs + nrb;
   double* cs = ys + nrb;
-  int* pv = reinterpret_cast<int*>(cs + nrb);
-  const long long col = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
-  if (col >= ncell * nrhs) return;
+  int* piv = reinterpret_cast<int*>(cs + nrb);      // nrb ints in the last nrb doubles
   const int rhs = (int)(col / ncell);
   const long long cell = col - (long long)rhs * ncell;
-  const double* Rc = R + col * (long long)nrb * nr;
-  const double* KRc = KR + col * (long long)nrb * nr;
+  const TB* Rc = R + col * (long long)nrb * nr;
+  const TB* KRc = KR + col * (long long)nrb * nr;
   const double* vc = v + rhs * v_rs + cell * v_cs;
-  const int ld = nrb;
   for (int i = 0; i < nrb; ++i) {
     for (int j = i; j < nrb; ++j) {
       double s = 0.0;
-      for (int q = lane; q < nr; q += 32) s += Rc[(size_t)i * nr + q] * KRc[(size_t)j * nr + q];
+      for (int q = lane; q < nr; q += 32) s += (double)Rc[(size_t)i * nr + q] * (double)KRc[(size_t)j * nr + q];
       for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-      if (lane == 0) { G[i * ld + j] = s; G[j * ld + i] = s; }
+      if (lane == 0) {
+        G[i * nrb + j] = s;
+        G[j * nrb + i] = s;
+      }
     }
     double s = 0.0;
-    for (int q = lane; q < nr; q += 32) s += Rc[(size_t)i * nr + q] * vc[q];
+    for (int q = lane; q < nr; q += 32) s += (double)Rc[(size_t)i * nr + q] * vc[q];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (lane == 0) hs[i] = s;
   }
   __syncwarp();
   if (lane == 0) {
-    // diagonal-pivoted Cholesky on the Schur complements: pivot order and rank
-    for (int i = 0; i < nrb * nrb; ++i) S[i] = G[i];
+    for (int t = 0; t < nb2; ++t) S[t] = G[t];
     double dmax = 0.0;
-    for (int i = 0; i < nrb; ++i) dmax = fmax(dmax, G[i * ld + i]);
+    for (int i = 0; i < nrb; ++i) dmax = fmax(dmax, G[i * nrb + i]);
     unsigned long long used = 0ull;
     int np = 0;
     while (np < nrb) {
       int jb = -1;
       double best = 0.0;
-      for (int i = 0; i < nrb; ++i)
-        if (!(used >> i & 1ull) && (jb < 0 || S[i * ld + i] > best)) { best = S[i * ld + i]; jb = i; }
-      if (!(best > drop_rel * dmax)) break;
-      used |= 1ull << jb;
-      pv[np++] = jb;
-      const double inv = 1.0 / sqrt(best);
-      for (int i = 0; i < nrb; ++i) ys[i] = S[i * ld + jb] * inv;
-      for (int i = 0; i < nrb; ++i)
-        for (int j = 0; j < nrb; ++j) S[i * ld + j] -= ys[i] * ys[j];
-    }
-    // Cholesky of G restricted to the pivots (pivot order), forward/back substitution
-    for (int a = 0; a < np; ++a) {
-      for (int b = 0; b <= a; ++b) {
-        double s = G[pv[a] * ld + pv[b]];
-        for (int k = 0; k < b; ++k) s -= Lm[a * ld + k] * Lm[b * ld + k];
-        Lm[a * ld + b] = (a == b) ? sqrt(s) : s / Lm[b * ld + b];
+      for (int i = 0; i < nrb; ++i) {
+        if ((used >> i) & 1ull) continue;
+        const double dv = S[i * nrb + i];
+        if (jb < 0 || dv > best) { best = dv; jb = i; }
       }
+      if (jb < 0 || !(best > drop_rel * dmax)) break;
+      used |= 1ull << jb;
+      piv[np] = jb;
+      ++np;
+      const double inv = 1.0 / sqrt(best);
+      for (int i = 0; i < nrb; ++i) ys[i] = S[i * nrb + jb] * inv;   // pivot column (scratch)
+      for (int i = 0; i < nrb; ++i)
+        for (int j = 0; j < nrb; ++j) S[i * nrb + j] -= ys[i] * ys[j];
     }
+    // Cholesky of G restricted to the pivots (pivot order)
+    for (int a = 0; a < np; ++a)
+      for (int b = 0; b <= a; ++b) {
+        double s = G[piv[a] * nrb + piv[b]];
+        for (int k = 0; k < b; ++k) s -= Lm[a * nrb + k] * Lm[b * nrb + k];
+        Lm[a * nrb + b] = (a == b) ? sqrt(s) : s / Lm[b * nrb + b];
+      }
     for (int a = 0; a < np; ++a) {
-      double s = hs[pv[a]];
-      for (int k = 0; k < a; ++k) s -= Lm[a * ld + k] * ys[k];
-      ys[a] = s / Lm[a * ld + a];
+      double s = hs[piv[a]];
+      for (int k = 0; k < a; ++k) s -= Lm[a * nrb + k] * ys[k];
+      ys[a] = s / Lm[a * nrb + a];
     }
     for (int i = 0; i < nrb; ++i) cs[i] = 0.0;
     for (int a = np - 1; a >= 0; --a) {
       double s = ys[a];
-      for (int k = a + 1; k < np; ++k) s -= Lm[k * ld + a] * cs[pv[k]];
-      cs[pv[a]] = s / Lm[a * ld + a];
+      for (int k = a + 1; k < np; ++k) s -= Lm[k * nrb + a] * cs[piv[k]];
+      cs[piv[a]] = s / Lm[a * nrb + a];
     }
   }
   __syncwarp();
   double* xc = x + rhs * x_rs + cell * x_cs;
   for (int q = lane; q < nr; q += 32) {
     double s = 0.0;
-    for (int i = 0; i < nrb; ++i) s += cs[i] * Rc[(size_t)i * nr + q];
+    for (int i = 0; i < nrb; ++i) s += cs[i] * (double)Rc[(size_t)i * nr + q];
     xc[q] = s;
   }
 }
@@ -480,15 +495,47 @@ fetidp_status k_apply_K(Ctx& c, CCellVec u, CellVec y, int nvec, int nrhs, bool 
   const double wq = pow(0.5 * h, c.d);
   const dim3 grid((unsigned)(c.N * nrhs));
   if (c.d == 2) {
-    cudaFuncSetAttribute(apply_K_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    apply_K_kernel<2><<<grid, 256, smem, c.stream>>>(c.e, c.N, c.n, len, c.perm, c.perm + c.n, idp,
-                                                     u.p, u.rs, u.cs, y.p, y.rs, y.cs, nvec, VB,
-                                                     chat, c.nc, wq, 1.0 / h);
+    cudaFuncSetAttribute(apply_K_kernel<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    apply_K_kernel<2, double><<<grid, 256, smem, c.stream>>>(
+        c.e, c.N, c.n, len, c.perm, c.perm + c.n, idp, u.p, u.rs, u.cs, y.p, y.rs, y.cs, nvec, VB,
+        chat, c.nc, wq, 1.0 / h, u.ext, y.ext);
   } else {
-    cudaFuncSetAttribute(apply_K_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    apply_K_kernel<3><<<grid, 256, smem, c.stream>>>(c.e, c.N, c.n, len, c.perm, c.perm + c.n, idp,
-                                                     u.p, u.rs, u.cs, y.p, y.rs, y.cs, nvec, VB,
-                                                     chat, c.nc, wq, 1.0 / h);
+    cudaFuncSetAttribute(apply_K_kernel<3, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    apply_K_kernel<3, double><<<grid, 256, smem, c.stream>>>(
+        c.e, c.N, c.n, len, c.perm, c.perm + c.n, idp, u.p, u.rs, u.cs, y.p, y.rs, y.cs, nvec, VB,
+        chat, c.nc, wq, 1.0 / h, u.ext, y.ext);
+  }
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+// FP32 variant (local ROM bases of the mixed path): u, y float with the same view strides.
+fetidp_status k_apply_K_f32(Ctx& c, const float* u, long long u_rs, int u_cs, float* y, long long y_rs,
+                            int y_cs, int nvec, int nrhs, bool idp, bool r_only, long long ext) {
+  const int len = r_only ? c.nr : c.n;
+  const int VB = nvec < 16 ? nvec : 16;
+  {
+    const double D = c.d, NA = c.ngp;
+    const double fma = NA * D * D * 2.0 + D * D * D * D;
+    const double cols = (double)c.N * nrhs;
+    c.prof_pending_flops = 2.0 * fma * c.nelem * c.ngp * nvec * cols;
+    c.prof_pending_bytes = cols * (c.nsnap * 8.0 + 2.0 * nvec * len * 4.0);
+  }
+  ProfScope ps(c, FETIDP_K_APPLY_K, c.prof_pending_flops, c.prof_pending_bytes);
+  const size_t smem = 2 * (size_t)VB * c.n * sizeof(float);
+  const float h = 1.0f / c.e;
+  const float wq = (float)pow(0.5 / c.e, c.d);
+  const dim3 grid((unsigned)(c.N * nrhs));
+  if (c.d == 2) {
+    cudaFuncSetAttribute(apply_K_kernel<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    apply_K_kernel<2, float><<<grid, 256, smem, c.stream>>>(c.e, c.N, c.n, len, c.perm, c.perm + c.n, idp,
+                                                            u, u_rs, u_cs, y, y_rs, y_cs, nvec, VB,
+                                                            c.snap, c.nc, wq, 1.0f / h, ext, ext);
+  } else {
+    cudaFuncSetAttribute(apply_K_kernel<3, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    apply_K_kernel<3, float><<<grid, 256, smem, c.stream>>>(c.e, c.N, c.n, len, c.perm, c.perm + c.n, idp,
+                                                            u, u_rs, u_cs, y, y_rs, y_cs, nvec, VB,
+                                                            c.snap, c.nc, wq, 1.0f / h, ext, ext);
   }
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
@@ -530,24 +577,35 @@ fetidp_status k_grouped_gemm_n(Ctx& c, const double* A, long long a_stride_k, in
   return FETIDP_OK;
 }
 
-fetidp_status k_gram_solve(Ctx& c, const double* R, const double* KR, CCellVec v, CellVec x,
-                           int nrhs) {
+template <typename TB>
+static fetidp_status gram_solve_t(Ctx& c, const TB* R, const TB* KR, CCellVec v, CellVec x, int nrhs) {
   if (c.nrb > kMaxRb) {
     set_error("n_rb above 64 is not supported by the Gram solve");
     return FETIDP_EINVAL;
   }
   const long long cols = c.N * nrhs;
-  const size_t per = (3 * (size_t)c.nrb * c.nrb + 4 * (size_t)c.nrb) * sizeof(double);
-  int warps = (int)std::min<size_t>(8, (200 * 1024) / per);
-  if (warps < 1) warps = 1;
-  const size_t smem = per * warps;
-  cudaFuncSetAttribute(gram_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   ProfScope ps(c, FETIDP_K_GRAM, cols * 2.0 * c.nr * (c.nrb * (c.nrb + 1) / 2.0 + 2.0 * c.nrb),
-               cols * 8.0 * (2.0 * c.nrb * c.nr + 2.0 * c.nr));
-  gram_solve_kernel<<<(unsigned)ceil_div(cols, warps), 32 * warps, smem, c.stream>>>(
+               cols * (double)sizeof(TB) * (2.0 * c.nrb * c.nr) + cols * 16.0 * c.nr);
+  const size_t per_warp = (size_t)gram_warp_doubles(c.nrb) * sizeof(double);
+  int wpb = (int)std::min<size_t>(8, (200 * 1024) / per_warp);
+  if (wpb < 1) wpb = 1;
+  const size_t smem = per_warp * wpb;
+  cudaFuncSetAttribute(gram_warp_kernel<TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  gram_warp_kernel<TB><<<(unsigned)ceil_div(cols, wpb), 32 * wpb, smem, c.stream>>>(
       R, KR, v.p, v.rs, v.cs, x.p, x.rs, x.cs, c.nr, c.nrb, c.N, nrhs, 1e-12);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
+}
+
+fetidp_status k_gram_solve(Ctx& c, const double* R, const double* KR, CCellVec v, CellVec x,
+                           int nrhs) {
+  return gram_solve_t<double>(c, R, KR, v, x, nrhs);
+}
+
+fetidp_status k_gram_solve_f32(Ctx& c, const float* R, const float* KR, CCellVec v, CellVec x,
+                               int nrhs, long long r_ext) {
+  (void)r_ext;
+  return gram_solve_t<float>(c, R, KR, v, x, nrhs);
 }
 
 fetidp_status k_grad(Ctx& c, const double* u, const double* w, double* g) {
@@ -563,5 +621,7 @@ fetidp_status k_grad(Ctx& c, const double* u, const double* w, double* g) {
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }
+
+FD_DEFINE_CHECK(fd_check_cell)
 
 }  // namespace fetidp

@@ -134,27 +134,31 @@ __global__ void column_gradients_kernel(int e, int n, const int* __restrict__ ip
   }
 }
 
-// Table row (i, j): T[(el*ngp + gp)*nc + c] = wq sum_l [Gi_I Gj_J + (I != J) Gi_J Gj_I]
-__global__ void trace_table_kernel(const double* __restrict__ Gi, const double* __restrict__ Gj,
-                                   int ncol, int nqp, int d, double wq, double* __restrict__ T) {
+// Table row t = (i, j): T[t][(el*ngp + gp)*nc + c] = wq sum_l [Gi_I Gj_J + (I != J) Gi_J Gj_I]
+// for every table in one launch (grid.y = table).
+__global__ void trace_tables_kernel(const TraceTableSpec* __restrict__ specs, int nqp, int d,
+                                    double wq, double* __restrict__ T, long long tstride) {
+  const TraceTableSpec sp = specs[blockIdx.y];
   const int dd = d * d;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nqp;
-       t += (long long)gridDim.x * blockDim.x) {
+  const int nc = dd * (dd + 1) / 2;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nqp; t += gridDim.x * blockDim.x) {
     double acc[45];
-    const int nc = dd * (dd + 1) / 2;
     for (int c = 0; c < nc; ++c) acc[c] = 0.0;
-    for (int l = 0; l < ncol; ++l) {
-      const double* gi = Gi + ((long long)l * nqp + t) * dd;
-      const double* gj = Gj + ((long long)l * nqp + t) * dd;
+    for (int l = 0; l < sp.ncol; ++l) {
+      const double* gi = sp.Gi + ((long long)l * nqp + t) * dd;
+      const double* gj = sp.Gj + ((long long)l * nqp + t) * dd;
+      double a[9], b[9];
+      for (int I = 0; I < dd; ++I) { a[I] = gi[I]; b[I] = gj[I]; }
       int c = 0;
       for (int I = 0; I < dd; ++I)
         for (int J = I; J < dd; ++J) {
-          double v = gi[I] * gj[J];
-          if (J != I) v += gi[J] * gj[I];
+          double v = a[I] * b[J];
+          if (J != I) v += a[J] * b[I];
           acc[c++] += v;
         }
     }
-    for (int c = 0; c < nc; ++c) T[t * nc + c] = wq * acc[c];
+    double* o = T + blockIdx.y * tstride + (long long)t * nc;
+    for (int c = 0; c < nc; ++c) o[c] = wq * acc[c];
   }
 }
 
@@ -227,10 +231,13 @@ fetidp_status k_column_gradients(Ctx& c, const double* src, long long kstride, l
   return FETIDP_OK;
 }
 
-fetidp_status k_trace_table(Ctx& c, const double* Gi, const double* Gj, int ncol, double* T) {
+fetidp_status k_trace_tables(Ctx& c, const TraceTableSpec* specs_dev, int ntab, double* T,
+                             long long tstride) {
   const int nqp = c.nelem * c.ngp;
   const double wq = pow(0.5 / c.e, c.d);
-  trace_table_kernel<<<gridn(nqp), 128, 0, c.stream>>>(Gi, Gj, ncol, nqp, c.d, wq, T);
+  ProfScope ps(c, FETIDP_K_SETUP, 0.0, 0.0);
+  dim3 grid((unsigned)((nqp + 127) / 128), (unsigned)ntab);
+  trace_tables_kernel<<<grid, 128, 0, c.stream>>>(specs_dev, nqp, c.d, wq, T, tstride);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }

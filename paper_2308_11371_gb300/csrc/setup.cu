@@ -23,7 +23,8 @@ fetidp_status k_row_update(Ctx& c, double* D, const double* beta, const double* 
 fetidp_status k_scale_copy(Ctx& c, const double* x, const double* s, double* y, long long len);
 fetidp_status k_column_gradients(Ctx& c, const double* src, long long kstride, long long lstride,
                                  int len_in, int mode, int unit_base, int nk, int ncol, double* out);
-fetidp_status k_trace_table(Ctx& c, const double* Gi, const double* Gj, int ncol, double* T);
+fetidp_status k_trace_tables(Ctx& c, const TraceTableSpec* specs_dev, int ntab, double* T,
+                             long long tstride);
 fetidp_status k_rom_combine(Ctx& c, const double* src, long long kstride, int ld, int r0, int c0,
                             int rows, int cols, const double* coef, double* out, bool transpose);
 
@@ -226,6 +227,8 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
   }
   if (o.max_outer < 1 || o.max_inner < 1) { set_error("bad iteration limits"); return FETIDP_EINVAL; }
   c.opt = o;
+  c.mixed = o.precision == FETIDP_MIXED_BF16;
+  if (c.mixed && o.tc_split != 1 && o.tc_split != 3) { set_error("tc_split must be 1 or 3"); return FETIDP_EINVAL; }
   const int d = p.dim, e = p.elems;
   Geo& g = c.geo;
   g.dim = d; g.e = e;
@@ -515,22 +518,24 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
     // unit corner vectors e_p (columns of K_rp)
     FD_TRY(k_column_gradients(c, nullptr, 0, 0, 0, 1, nr, 1, np, Ge));
     const size_t gstride_d = (size_t)nd * nqp * dd, gstride_p = (size_t)np * nqp * dd;
-    int t = 0;
+    std::vector<TraceTableSpec> specs;
     for (int i = 0; i < nrb; ++i)
-      for (int j = i; j < nrb; ++j, ++t)
-        FD_TRY(k_trace_table(c, Gp + i * gstride_p, Gp + j * gstride_p, np, Tab + (size_t)t * c.nsnap));
-    for (int i = 0; i < nrb; ++i, ++t)
-      FD_TRY(k_trace_table(c, Gp + i * gstride_p, Ge, np, Tab + (size_t)t * c.nsnap));
+      for (int j = i; j < nrb; ++j) specs.push_back({Gp + i * gstride_p, Gp + j * gstride_p, np});
+    for (int i = 0; i < nrb; ++i) specs.push_back({Gp + i * gstride_p, Ge, np});
     for (int i = 0; i < nrb; ++i)
-      for (int j = i; j < nrb; ++j, ++t)
-        FD_TRY(k_trace_table(c, Gd + i * gstride_d, Gd + j * gstride_d, nd, Tab + (size_t)t * c.nsnap));
+      for (int j = i; j < nrb; ++j) specs.push_back({Gd + i * gstride_d, Gd + j * gstride_d, nd});
+    TraceTableSpec* specs_dev = nullptr;
+    FD_CUDA(cudaMalloc(&specs_dev, sizeof(TraceTableSpec) * specs.size()));
+    FD_CUDA(cudaMemcpyAsync(specs_dev, specs.data(), sizeof(TraceTableSpec) * specs.size(),
+                            cudaMemcpyHostToDevice, c.stream));
+    FD_TRY(k_trace_tables(c, specs_dev, (int)specs.size(), Tab, c.nsnap));
     FD_TRY(k_grouped_gemm_n(c, Tab, 0, (int)c.nsnap, ntab, (int)c.nsnap, 1,
                             CCellVec{c.snap, 0, (int)c.nsnap}, CellVec{Y, 0, ntab}, nullptr, 1.0, 0.0,
                             c.N, 1, false, 0));
     std::vector<double> hY((size_t)c.N * ntab);
     FD_CUDA(cudaMemcpyAsync(hY.data(), Y, sizeof(double) * hY.size(), cudaMemcpyDeviceToHost, c.stream));
     FD_CUDA(cudaStreamSynchronize(c.stream));
-    cudaFree(Gd); cudaFree(Gp); cudaFree(Ge); cudaFree(Tab); cudaFree(Y);
+    cudaFree(Gd); cudaFree(Gp); cudaFree(Ge); cudaFree(Tab); cudaFree(Y); cudaFree(specs_dev);
     std::vector<double> dvec(nrb, 0.0);
     for (int k = 0; k < nrb; ++k)
       for (int l = 0; l < nd; ++l) dvec[k] += hKinv[(size_t)k * nr * nr + (size_t)(ni + l) * nr + ni + l];
@@ -551,12 +556,34 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
   FD_TRY(upload(c, &c.delta, h_delta));
 
   // ---------------------------------------------------------------- ROM local operators (Eq. 43)
-  FD_TRY(dalloc_t(c, &c.Fdd_c, (size_t)c.N * nd * nd));
-  FD_TRY(dalloc_t(c, &c.Sdd_c, (size_t)c.N * nd * nd));
+  if (!c.mixed) {   // FP64 path: per-cell assembled F_dd_ring, S_dd_ring
+    FD_TRY(dalloc_t(c, &c.Fdd_c, (size_t)c.N * nd * nd));
+    FD_TRY(dalloc_t(c, &c.Sdd_c, (size_t)c.N * nd * nd));
+    FD_TRY(k_rom_combine(c, c.Kinv, (long long)nr * nr, nr, ni, ni, nd, nd, c.delta, c.Fdd_c, false));
+    FD_TRY(k_rom_combine(c, c.Sdd, (long long)nd * nd, nd, 0, 0, nd, nd, c.alpha, c.Sdd_c, false));
+  } else {          // mixed path: principal operators packed for the tensor cores
+    const int nt = o.tc_split == 3 ? 3 : 1;
+    FD_TRY(tc_pack_operator(c, c.opKinv, c.Kinv, (long long)nr * nr, nr, 0, 0, nr, nr, nrb, true, nt));
+    FD_TRY(tc_pack_operator(c, c.opUrdT, c.Kinv, (long long)nr * nr, nr, ni, 0, nd, nr, nrb, false, nt));
+    FD_TRY(tc_pack_operator(c, c.opUrd, c.Kinv, (long long)nr * nr, nr, 0, ni, nr, nd, nrb, false, nt));
+    FD_TRY(tc_pack_operator(c, c.opFdd, c.Kinv, (long long)nr * nr, nr, ni, ni, nd, nd, nrb, false, nt));
+    FD_TRY(tc_pack_operator(c, c.opSdd, c.Sdd, (long long)nd * nd, nd, 0, 0, nd, nd, nrb, false, nt));
+    size_t mx = 0;
+    const long long ncols = c.N * c.m;
+    for (const TcOperator* op : {&c.opKinv, &c.opUrdT, &c.opUrd, &c.opFdd, &c.opSdd}) {
+      const int batch = op->separate ? op->nops : 1;
+      const int bn = tc_bn_for(ncols, op->m_tiles, batch);
+      const long long n_tiles = (ncols + bn - 1) / bn;
+      const int k_tiles = (op->separate ? 1 : op->nops) * op->nterm * op->k_tiles_op;
+      mx = std::max(mx, (size_t)n_tiles * k_tiles * bn * 64 * 2);
+    }
+    c.tc_bbuf_bytes = mx;
+    FD_TRY(dalloc(c, reinterpret_cast<void**>(&c.tc_bbuf), mx));
+    FD_TRY(dalloc(c, reinterpret_cast<void**>(&c.tc_err), sizeof(int)));
+    FD_CUDA(cudaMemsetAsync(c.tc_err, 0, sizeof(int), c.stream));
+  }
   FD_TRY(dalloc_t(c, &c.Urp_c, (size_t)c.N * nr * np));
   FD_TRY(dalloc_t(c, &c.UrpT_c, (size_t)c.N * nr * np));
-  FD_TRY(k_rom_combine(c, c.Kinv, (long long)nr * nr, nr, ni, ni, nd, nd, c.delta, c.Fdd_c, false));
-  FD_TRY(k_rom_combine(c, c.Sdd, (long long)nd * nd, nd, 0, 0, nd, nd, c.alpha, c.Sdd_c, false));
   FD_TRY(k_rom_combine(c, c.Urp, (long long)nr * np, np, 0, 0, nr, np, c.pi, c.Urp_c, false));
   FD_TRY(k_rom_combine(c, c.Urp, (long long)nr * np, np, 0, 0, nr, np, c.pi, c.UrpT_c, true));
 

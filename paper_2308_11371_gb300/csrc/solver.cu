@@ -147,7 +147,10 @@ fetidp_status op_apply_F(Ctx& c, const double* lam, long long lam_rs, double* y,
   const int m = c.m, nd = c.nd, np = c.np, nr = c.nr, ni = c.ni;
   CellVec g{c.w_d1, c.N * nd, nd}, yd{c.w_d2, c.N * nd, nd}, cp{c.w_p1, c.N * np, np};
   FD_TRY(k_gather_BT(c, lam, lam_rs, nullptr, g, m, 0.0));
-  FD_TRY(cell_op(c, c.Fdd_c, (long long)nd * nd, nd, nd, nd, cview(g), yd, 1.0, 0.0));
+  if (c.mixed)
+    FD_TRY(tc_apply(c, c.opFdd, cview(g), c.delta, yd.p, true, yd.rs, yd.cs, 0, 1.0, 0.0, m, c.N));
+  else
+    FD_TRY(cell_op(c, c.Fdd_c, (long long)nd * nd, nd, nd, nd, cview(g), yd, 1.0, 0.0));
   // coarse correction: c_p = (T_dr U_rp_ring)^T g, assembled, S_PP^{-1}, prolonged
   FD_TRY(cell_op(c, c.UrpT_c + ni, (long long)np * nr, nr, np, nd, cview(g), cp, 1.0, 0.0));
   FD_TRY(k_primal_assemble(c, cview(cp), c.w_P1, c.nP, 1.0, 0.0, m));
@@ -163,7 +166,10 @@ fetidp_status op_apply_MD(Ctx& c, const double* r, long long r_rs, double* z, lo
   const int m = c.m, nd = c.nd;
   CellVec g{c.w_d1, c.N * nd, nd}, yd{c.w_d2, c.N * nd, nd};
   FD_TRY(k_gather_BT(c, r, r_rs, c.Dw, g, m, 0.0));
-  FD_TRY(cell_op(c, c.Sdd_c, (long long)nd * nd, nd, nd, nd, cview(g), yd, 1.0, 0.0));
+  if (c.mixed)
+    FD_TRY(tc_apply(c, c.opSdd, cview(g), c.alpha, yd.p, true, yd.rs, yd.cs, 0, 1.0, 0.0, m, c.N));
+  else
+    FD_TRY(cell_op(c, c.Sdd_c, (long long)nd * nd, nd, nd, nd, cview(g), yd, 1.0, 0.0));
   FD_TRY(k_scatter_B(c, cview(yd), z, z_rs, c.Dw, 1.0, 0.0, m));
   return FETIDP_OK;
 }
@@ -180,8 +186,11 @@ fetidp_status U_apply(Ctx& c, CCellVec vR, const double* vP, long long vP_rs, do
   FD_TRY(k_primal_assemble(c, cview(cp), c.w_P1, c.nP, -1.0, 1.0, m));
   FD_TRY(coarse_solve(c, c.w_P1, c.nP, c.w_zP, c.nP, m));
   // t_d = U_rd_ring^T v_r - T_dr U_rp_ring A_p^T z_P
-  FD_TRY(k_grouped_gemm(c, c.Kinv + (size_t)ni * nr, (long long)nr * nr, nr, nd, nr, vR, td, c.delta,
-                        1.0, 0.0, m, false, 0));
+  if (c.mixed)
+    FD_TRY(tc_apply(c, c.opUrdT, vR, c.delta, td.p, true, td.rs, td.cs, 0, 1.0, 0.0, m, c.N));
+  else
+    FD_TRY(k_grouped_gemm(c, c.Kinv + (size_t)ni * nr, (long long)nr * nr, nr, nd, nr, vR, td, c.delta,
+                          1.0, 0.0, m, false, 0));
   FD_TRY(k_primal_extract(c, c.w_zP, c.nP, cp, m));
   FD_TRY(cell_op(c, c.Urp_c + (size_t)ni * np, (long long)nr * np, np, nd, np, cview(cp), td, -1.0, 1.0));
   FD_TRY(k_scatter_B(c, cview(td), out_L, out_rs, nullptr, 1.0, 0.0, m));
@@ -191,6 +200,19 @@ fetidp_status U_apply(Ctx& c, CCellVec vR, const double* vP, long long vP_rs, do
 // Eq. 46 for every (rhs, cell): x_r = R (R^T K_s R)^{-1} R^T v_r, R = [K_rr^(sigma_k)^{-1} v_r]_k
 fetidp_status local_rom(Ctx& c, CCellVec vR, CellVec xR) {
   const int m = c.m, nr = c.nr, nrb = c.nrb;
+  if (c.mixed) {
+    float* Rf = reinterpret_cast<float*>(c.w_R);
+    float* KRf = reinterpret_cast<float*>(c.w_KR);
+    const long long rs = c.N * nrb * nr;
+    const long long rext = 2 * (long long)m * rs;   // float capacity of the double-sized buffers
+    FD_TRY(tc_apply(c, c.opKinv, vR, nullptr, Rf, false, rs, nrb * nr, nr, 1.0, 0.0, m, c.N, rext));
+    FD_TRY(fd_check_tc("local ROM basis (tensor cores)"));
+    FD_TRY(k_apply_K_f32(c, Rf, rs, nrb * nr, KRf, rs, nrb * nr, nrb, m, true, true, rext));
+    FD_TRY(fd_check_cell("local ROM K_s products"));
+    FD_TRY(k_gram_solve_f32(c, Rf, KRf, vR, xR, m, rext));
+    FD_TRY(fd_check_cell("local ROM Gram solve"));
+    return FETIDP_OK;
+  }
   CellVec R{c.w_R, c.N * nrb * nr, nrb * nr};
   FD_TRY(k_grouped_gemm(c, c.Kinv, (long long)nr * nr, nr, nr, nr, vR, R, nullptr, 1.0, 0.0, m, true,
                         nr));
@@ -248,7 +270,8 @@ fetidp_status pcg_solve(Ctx& c, const double* b, long long b_rs, double* x, long
         return FETIDP_EBREAKDOWN;
       }
       const double rel = std::sqrt(rr / rr0[r]);
-      if (c.opt.fixed_inner <= 0 && rel <= c.opt.tol_inner) act[r] = 0.0;
+      const double tol = c.mixed ? c.opt.tol_inner_mixed : c.opt.tol_inner;
+      if (c.opt.fixed_inner <= 0 && rel <= tol) act[r] = 0.0;
       if (rr == 0.0) act[r] = 0.0;
       nact += act[r] > 0.0;
     }
@@ -309,8 +332,11 @@ fetidp_status op_precondition(Ctx& c, const double* x, double* y) {
   FD_TRY(cell_op(c, c.UrpT_c + ni, (long long)np * nr, nr, np, nd, cview(g), cp, 1.0, 0.0));
   FD_TRY(k_primal_assemble(c, cview(cp), c.w_P1, c.nP, -1.0, 0.0, m));
   FD_TRY(coarse_solve(c, c.w_P1, c.nP, c.w_P1, c.nP, m));
-  FD_TRY(k_grouped_gemm(c, c.Kinv + ni, (long long)nr * nr, nr, nr, nd, cview(g), yR, c.delta, -1.0,
-                        1.0, m, false, 0));
+  if (c.mixed)
+    FD_TRY(tc_apply(c, c.opUrd, cview(g), c.delta, yR.p, true, yR.rs, yR.cs, 0, -1.0, 1.0, m, c.N));
+  else
+    FD_TRY(k_grouped_gemm(c, c.Kinv + ni, (long long)nr * nr, nr, nr, nd, cview(g), yR, c.delta, -1.0,
+                          1.0, m, false, 0));
   FD_TRY(k_primal_extract(c, c.w_P1, c.nP, cp, m));
   FD_TRY(cell_op(c, c.Urp_c, (long long)nr * np, np, nr, np, cview(cp), yR, 1.0, 1.0));
   FD_TRY(axpby(c, c.w_zP, c.nP, c.w_P1, c.nP, yP, nt, 1.0, -1.0, c.nP, m));
@@ -503,6 +529,8 @@ void fetidp_default_options(fetidp_options* o) {
   o->precision = FETIDP_FP64;
   o->fixed_outer = 0;
   o->fixed_inner = 0;
+  o->tc_split = 3;
+  o->tol_inner_mixed = 1e-6;
 }
 
 const char* fetidp_status_string(fetidp_status s) {
@@ -522,6 +550,28 @@ const char* fetidp_status_string(fetidp_status s) {
 const char* fetidp_last_error(void) { return g_last_error.c_str(); }
 
 long long fetidp_kernel_launches(void) { return g_launches.load(); }
+
+fetidp_status fetidp_tc_selfcheck(int M, int K, int N, double* rel_err) {
+  if (M < 1 || K < 1 || N < 1 || !rel_err) { set_error("bad self-check sizes"); return FETIDP_EINVAL; }
+  fetidp_ctx tmp;
+  Ctx& c = tmp.c;
+  cudaGetDevice(&c.device);
+  c.stream = nullptr;
+  const int m_tiles = (M + 127) / 128, k_tiles = (K + 63) / 64;
+  const int bn = tc_bn_for(N, m_tiles, 1);
+  const long long n_tiles = (N + bn - 1) / bn;
+  c.tc_bbuf_bytes = (size_t)n_tiles * k_tiles * bn * 64 * 2;
+  fetidp_status st = dalloc(c, reinterpret_cast<void**>(&c.tc_bbuf), c.tc_bbuf_bytes);
+  if (st == FETIDP_OK) st = dalloc(c, reinterpret_cast<void**>(&c.tc_err), sizeof(int));
+  if (st == FETIDP_OK) {
+    cudaMemset(c.tc_err, 0, sizeof(int));
+    st = tc_selfcheck(c, M, K, N, rel_err);
+  }
+  cudaStreamSynchronize(nullptr);
+  for (void* p : c.allocations) cudaFree(p);
+  c.allocations.clear();
+  return st;
+}
 
 fetidp_status fetidp_profile_enable(fetidp_ctx* ctx, unsigned mask) {
   FD_TRY(enter(ctx));
@@ -583,8 +633,8 @@ fetidp_status fetidp_setup(const fetidp_problem* probs, int n_problems, const fe
   fetidp_options o;
   fetidp_default_options(&o);
   if (opt) o = *opt;
-  if (o.precision != FETIDP_FP64) {
-    set_error("requested precision is not available in this build");
+  if (o.precision != FETIDP_FP64 && o.precision != FETIDP_MIXED_BF16) {
+    set_error("unknown precision");
     return FETIDP_EINVAL;
   }
   fetidp_ctx* ctx = new fetidp_ctx();
@@ -645,7 +695,8 @@ fetidp_status fetidp_coarse_solve(fetidp_ctx* ctx, const double* b, double* x) {
 fetidp_status fetidp_local_rom_solve(fetidp_ctx* ctx, const double* v, double* x) {
   FD_TRY(enter(ctx));
   Ctx& c = ctx->c;
-  return local_rom(c, CCellVec{v, c.N * c.nr, c.nr}, CellVec{x, c.N * c.nr, c.nr});
+  const long long ext = (long long)c.m * c.N * c.nr;
+  return local_rom(c, CCellVec{v, c.N * c.nr, c.nr, ext}, CellVec{x, c.N * c.nr, c.nr, ext});
 }
 
 fetidp_status fetidp_apply_A(fetidp_ctx* ctx, const double* x, double* y) {
@@ -676,6 +727,14 @@ static fetidp_status solve_common(fetidp_ctx* ctx, fetidp_info* info, OuterResul
   c.inner_total = 0;
   FD_TRY(fgmres(c, c.w_tot, r));
   FD_CUDA(cudaStreamSynchronize(c.stream));
+  if (c.mixed) {
+    int herr = 0;
+    FD_CUDA(cudaMemcpy(&herr, c.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr != 0) {
+      set_error("tensor-core GEMM wait timed out (code " + std::to_string(herr) + ")");
+      return FETIDP_ETIMEOUT;
+    }
+  }
   if (info) {
     info->outer_its = r.its;
     info->inner_its_total = c.inner_total;

@@ -1,0 +1,577 @@
+// Grouped principal contractions on the 5th-generation tensor cores (tcgen05).
+//
+// The ROM operators of Eq. 43 are linear combinations of a few principal
+// operators (Remark 7), so every cell's column is multiplied by the SAME
+// principal matrices: Y[:, c] = sum_k coef_k(c) A_k X[:, c] (Eqs. 46a, 48, 49,
+// Algorithm 3).  Written as one GEMM per use:
+//   combine  : A = [A_1 ... A_nk] (K-concatenated), B column c = [coef_k(c) X_c]_k
+//   separate : batch over k, B = X shared (Eq. 46a keeps every R column)
+// with BF16 operands (optionally split into hi + lo BF16 terms, three products
+// A_hi X_hi + A_hi X_lo + A_lo X_hi, for ~16-bit input precision) and FP32
+// accumulation in TMEM.
+//
+// Kernel: one CTA per (n-tile, m-tile, batch); warp 0 lane 0 streams 128x64 A
+// tiles and BNx64 B tiles with cp.async.bulk into a STAGES-deep mbarrier ring;
+// warp 1 lane 0 issues tcgen05.mma (M=128, N=BN, K=16) and commits each stage
+// back to the producer; all four warps drain the accumulator with tcgen05.ld.
+// Operands are pre-packed in global memory in the canonical 128-byte-swizzled
+// K-major layout, so a linear bulk copy lands the exact shared-memory image.
+// Every mbarrier wait is bounded (1 s of globaltimer): on expiry the CTA sets
+// an error flag, drains its own copies (bounded), frees TMEM and returns.
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace fetidp {
+
+namespace {
+
+constexpr int TC_BM = 128;
+constexpr int TC_BK = 64;                     // bf16 elements per 128-byte row
+constexpr int A_TILE = TC_BM * TC_BK * 2;     // 16 KB
+constexpr unsigned long long kWaitNs = 1000000000ull;   // 1 s bound on every wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: false on timeout or when another role has aborted
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  const unsigned long long t0 = gtime();
+  for (unsigned it = 0;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 63u) == 63u) {
+      if (*abort_flag) return false;
+      if (gtime() - t0 > kWaitNs) return false;
+    }
+  }
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups
+// 1024 bytes apart.  start address >> 4 in bits 0-13, SBO >> 4 in bits 32-45,
+// descriptor version 1 at bit 46, layout type SWIZZLE_128B (2) in bits 61-63.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;                  // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D f32 (bits 4-5 = 1), A and B bf16 (bits 7-9, 10-12 = 1)
+// or f16 (0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N, bool bf16) {
+  return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+// Byte offset of element (row r, k-index q in [0, 64)) inside a SW128 K-major tile.
+__host__ __device__ __forceinline__ uint32_t sw128_offset(int r, int q) {
+  const int chunk = q >> 3;
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((chunk ^ (r & 7)) << 4) + ((q & 7) << 1));
+}
+
+}  // namespace
+
+struct TcParams {
+  const uint8_t* A;
+  const uint8_t* B;
+  int m_tiles, n_tiles, k_tiles;
+  long long a_batch_stride;   // bytes
+  long long b_batch_stride;   // bytes
+  int M;
+  long long ncols, ncell;
+  void* Y;
+  int y_f64;
+  long long y_rs;
+  int y_cs;
+  long long y_b_stride;
+  double alpha, beta;
+  int* err;
+  long long a_bytes, b_bytes, y_ext;   // extents for checked builds
+};
+
+namespace {
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(TcParams P) {
+  constexpr int B_TILE = BN * TC_BK * 2;
+  constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+  constexpr uint32_t IDESC = make_idesc(TC_BM, BN, true);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * A_TILE;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + STAGES * B_TILE);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nt = blockIdx.x, mt = blockIdx.y, bz = blockIdx.z;
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int KT = P.k_tiles;
+  const uint8_t* Ab = P.A + bz * P.a_batch_stride + (long long)mt * KT * A_TILE;
+  const uint8_t* Bb = P.B + bz * P.b_batch_stride + (long long)nt * KT * B_TILE;
+  if (warp == 0 && lane == 0) {
+    // ---------------- producer: bulk copies into the ring
+    int issued = 0;
+    for (int kt = 0; kt < KT; ++kt) {
+      const int s = kt % STAGES, n = kt / STAGES;
+      if (kt >= STAGES && !mbar_wait(empty0 + 8 * s, (uint32_t)((n - 1) & 1), abort_flag)) {
+        *abort_flag = 1;
+        atomicExch(P.err, 1);
+        break;
+      }
+      const long long aoff = (Ab - P.A) + (long long)kt * A_TILE, boff = (Bb - P.B) + (long long)kt * B_TILE;
+      if (!FD_INB(aoff + A_TILE - 1, P.a_bytes, 101) || !FD_INB(boff + B_TILE - 1, P.b_bytes, 102)) {
+        *abort_flag = 1;
+        atomicExch(P.err, 4);
+        break;
+      }
+      mbar_expect_tx(full0 + 8 * s, A_TILE + B_TILE);
+      bulk_g2s(smem_u32(sA + s * A_TILE), Ab + (long long)kt * A_TILE, A_TILE, full0 + 8 * s);
+      bulk_g2s(smem_u32(sB + s * B_TILE), Bb + (long long)kt * B_TILE, B_TILE, full0 + 8 * s);
+      ++issued;
+    }
+    if (*abort_flag) {
+      // drain our own copies in flight and the MMA thread's releases (both bounded) before
+      // the CTA may exit
+      for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued; ++kt) {
+        const int s = kt % STAGES, n = kt / STAGES;
+        unsigned long long t0 = gtime();
+        while (!mbar_try(full0 + 8 * s, (uint32_t)(n & 1)) && gtime() - t0 < kWaitNs) {
+        }
+        t0 = gtime();
+        while (!mbar_try(empty0 + 8 * s, (uint32_t)(n & 1)) && gtime() - t0 < kWaitNs / 8) {
+        }
+      }
+    } else {
+      // pipeline tail: wait until the MMA thread has released the last stages.  The arrivals of
+      // tcgen05.commit on the empty barriers are asynchronous; a CTA that exits before they land
+      // would let them write into shared memory that the next kernel's CTAs already own.
+      for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued; ++kt) {
+        const int s = kt % STAGES, n = kt / STAGES;
+        if (!mbar_wait(empty0 + 8 * s, (uint32_t)(n & 1), abort_flag)) {
+          atomicExch(P.err, 5);
+          break;
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    for (int kt = 0; kt < KT; ++kt) {
+      const int s = kt % STAGES, n = kt / STAGES;
+      if (!mbar_wait(full0 + 8 * s, (uint32_t)(n & 1), abort_flag)) {
+        *abort_flag = 1;
+        atomicExch(P.err, 2);
+        break;
+      }
+      tc_fence_after();
+      const uint64_t ad = sw128_desc(smem_u32(sA + s * A_TILE));
+      const uint64_t bd = sw128_desc(smem_u32(sB + s * B_TILE));
+#pragma unroll
+      for (int j = 0; j < TC_BK / 16; ++j)
+        tc_mma(tmem, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), IDESC, (kt > 0 || j > 0) ? 1u : 0u);
+      tc_commit(empty0 + 8 * s);
+    }
+    tc_commit(done);
+  }
+  __syncwarp();
+  // ---------------- epilogue: TMEM -> registers -> global (rows = TMEM lanes)
+  const bool ok = mbar_wait(done, 0u, abort_flag);
+  tc_fence_after();
+  if (!ok) atomicExch(P.err, 3);
+  if (ok && !*abort_flag) {
+    const int m = mt * TC_BM + warp * 32 + lane;
+    for (int ch = 0; ch < BN / 32; ++ch) {
+      uint32_t r[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 32), r);
+      tmem_ld_wait();
+      if (m < P.M) {
+        for (int j = 0; j < 32; ++j) {
+          const long long cidx = (long long)nt * BN + ch * 32 + j;
+          if (cidx >= P.ncols) break;
+          const int rhs = (int)(cidx / P.ncell);
+          const long long cell = cidx - (long long)rhs * P.ncell;
+          const long long off = bz * P.y_b_stride + rhs * P.y_rs + cell * P.y_cs + m;
+          if (!FD_INB(off, P.y_ext, 103)) continue;
+          const double v = P.alpha * (double)__uint_as_float(r[j]);
+          if (P.y_f64) {
+            double* y = reinterpret_cast<double*>(P.Y) + off;
+            *y = (P.beta == 0.0) ? v : v + P.beta * (*y);
+          } else {
+            float* y = reinterpret_cast<float*>(P.Y) + off;
+            *y = (P.beta == 0.0) ? (float)v : (float)(v + P.beta * (double)(*y));
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// ---- packing into SW128 K-major tiles
+// A operand: nb batches x m_tiles x k_tiles tiles.  K index of batch b is a concatenation of
+// nblk blocks of Kp (= k_tiles_op * 64) columns; block q uses operator op = q / nterm and split
+// term t = q % nterm (t = 0 hi, t = 1 hi, t = 2 lo for three terms).  Element (row m, col kk) of
+// operator op is src[op*op_stride + (r0 + m)*lda + c0 + kk] for m < M, kk < K.
+__global__ void pack_A_kernel(const double* __restrict__ src, long long op_stride, int lda, int r0,
+                              int c0, int M, int K, int nops_per_batch, int nterm, int k_tiles_op,
+                              int m_tiles, int nb, uint8_t* __restrict__ out) {
+  const int k_tiles = nops_per_batch * nterm * k_tiles_op;
+  const long long total = (long long)nb * m_tiles * k_tiles * TC_BM * 8;   // 16-byte chunks
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int chunk = (int)(t & 7);
+    long long rest = t >> 3;
+    const int row = (int)(rest % TC_BM);
+    rest /= TC_BM;
+    const int kt = (int)(rest % k_tiles);
+    rest /= k_tiles;
+    const int mt = (int)(rest % m_tiles);
+    const int b = (int)(rest / m_tiles);
+    const int blk = kt / k_tiles_op, ktl = kt - blk * k_tiles_op;
+    const int op = b * nops_per_batch + blk / nterm, term = blk % nterm;
+    const int m = mt * TC_BM + row;
+    alignas(16) __nv_bfloat16 v[8];
+    for (int e = 0; e < 8; ++e) {
+      const int kk = ktl * TC_BK + chunk * 8 + e;
+      float x = 0.f;
+      if (m < M && kk < K) {
+        const double a = src[op * op_stride + (long long)(r0 + m) * lda + c0 + kk];
+        const __nv_bfloat16 hi = __double2bfloat16(a);
+        if (term == 2) x = (float)(a - (double)__bfloat162float(hi));
+        else x = __bfloat162float(hi);
+      }
+      v[e] = __float2bfloat16_rn(x);
+    }
+    uint8_t* tile = out + (((long long)b * m_tiles + mt) * k_tiles + kt) * A_TILE;
+    *reinterpret_cast<uint4*>(tile + sw128_offset(row, chunk * 8)) = *reinterpret_cast<uint4*>(v);
+  }
+}
+
+// B operand: n_tiles x k_tiles tiles of BN rows (columns c = rhs*ncell + cell) x 64.  K block q
+// = (op = q / nterm, term = q % nterm) holds coef[cell*ncoef + op] * X[c][kk] (coef may be null)
+// as hi (terms 0, 2) or lo (term 1) bf16 part.
+template <int BN>
+__global__ void pack_B_kernel(const double* __restrict__ X, long long x_rs, int x_cs, int K,
+                              const double* __restrict__ coef, int ncoef, int nops, int nterm,
+                              int k_tiles_op, long long ncols, long long ncell, int n_tiles,
+                              uint8_t* __restrict__ out, long long x_ext, long long out_bytes) {
+  constexpr int B_TILE = BN * TC_BK * 2;
+  const int k_tiles = nops * nterm * k_tiles_op;
+  const long long total = (long long)n_tiles * k_tiles * BN * 8;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int chunk = (int)(t & 7);
+    long long rest = t >> 3;
+    const int row = (int)(rest % BN);
+    rest /= BN;
+    const int kt = (int)(rest % k_tiles);
+    const int nt = (int)(rest / k_tiles);
+    const int blk = kt / k_tiles_op, ktl = kt - blk * k_tiles_op;
+    const int op = blk / nterm, term = blk % nterm;
+    const long long cidx = (long long)nt * BN + row;
+    alignas(16) __nv_bfloat16 v[8];
+    if (cidx < ncols) {
+      const int rhs = (int)(cidx / ncell);
+      const long long cell = cidx - (long long)rhs * ncell;
+      const double cf = coef ? coef[cell * ncoef + op] : 1.0;
+      const double* xc = X + rhs * x_rs + cell * x_cs;
+      for (int e = 0; e < 8; ++e) {
+        const int kk = ktl * TC_BK + chunk * 8 + e;
+        float x = 0.f;
+        if (kk < K && FD_INB(rhs * x_rs + cell * x_cs + kk, x_ext, 104)) {
+          const double a = cf * xc[kk];
+          const __nv_bfloat16 hi = __double2bfloat16(a);
+          if (term == 1) x = (float)(a - (double)__bfloat162float(hi));
+          else x = __bfloat162float(hi);
+        }
+        v[e] = __float2bfloat16_rn(x);
+      }
+    } else {
+      for (int e = 0; e < 8; ++e) v[e] = __float2bfloat16_rn(0.f);
+    }
+    uint8_t* tile = out + ((long long)nt * k_tiles + kt) * B_TILE;
+    if (!FD_INB(((long long)nt * k_tiles + kt) * B_TILE + sw128_offset(row, chunk * 8) + 15, out_bytes, 105))
+      continue;
+    *reinterpret_cast<uint4*>(tile + sw128_offset(row, chunk * 8)) = *reinterpret_cast<uint4*>(v);
+  }
+}
+
+// Reference for the self-check: Y[c][m] = sum_kk A[m][kk] X[c][kk] in FP64 on bf16-rounded inputs.
+__global__ void ref_gemm_kernel(const double* A, const double* X, int M, int K, int N, double* Y) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)M * N;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(t / M), m = (int)(t % M);
+    double s = 0.0;
+    for (int kk = 0; kk < K; ++kk)
+      s += (double)__bfloat162float(__double2bfloat16(A[(long long)m * K + kk])) *
+           (double)__bfloat162float(__double2bfloat16(X[(long long)c * K + kk]));
+    Y[t] = s;
+  }
+}
+
+__global__ void fill_random_kernel(double* x, long long n, unsigned long long seed) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(t + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    x[t] = (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+  }
+}
+
+inline int gridn(long long work) {
+  long long g = (work + 255) / 256;
+  if (g > 152LL * 32) g = 152LL * 32;
+  return (int)(g < 1 ? 1 : g);
+}
+
+template <int BN, int STAGES>
+constexpr size_t tc_smem_bytes() {
+  return (size_t)STAGES * (A_TILE + BN * TC_BK * 2) + 8 * (2 * STAGES + 1) + 16 + 1024;
+}
+
+template <int BN, int STAGES>
+fetidp_status launch_tc(Ctx& c, const TcParams& P, int batch) {
+  const size_t smem = tc_smem_bytes<BN, STAGES>();
+  cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid((unsigned)P.n_tiles, (unsigned)P.m_tiles, (unsigned)batch);
+  tc_gemm_kernel<BN, STAGES><<<grid, 128, smem, c.stream>>>(P);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host API
+int tc_bn_for(long long ncols, int m_tiles, int batch) {
+  // smallest tile width that still gives at least one wave of CTAs on 148 SMs
+  const long long ctas256 = ((ncols + 255) / 256) * m_tiles * batch;
+  if (ctas256 >= 148) return 256;
+  const long long ctas128 = ((ncols + 127) / 128) * m_tiles * batch;
+  if (ctas128 >= 148) return 128;
+  return 64;
+}
+
+fetidp_status tc_pack_operator(Ctx& c, TcOperator& op, const double* src, long long op_stride, int lda,
+                               int r0, int c0, int M, int K, int nops, bool separate, int nterm) {
+  op.M = M;
+  op.K = K;
+  op.nops = nops;
+  op.nterm = nterm;
+  op.separate = separate;
+  op.m_tiles = (M + TC_BM - 1) / TC_BM;
+  op.k_tiles_op = (K + TC_BK - 1) / TC_BK;
+  const int nb = separate ? nops : 1;
+  const int per_batch = separate ? 1 : nops;
+  op.k_tiles = per_batch * nterm * op.k_tiles_op;
+  op.batch_bytes = (long long)op.m_tiles * op.k_tiles * A_TILE;
+  FD_TRY(dalloc(c, reinterpret_cast<void**>(&op.tiles), (size_t)nb * op.batch_bytes));
+  ProfScope ps(c, FETIDP_K_SETUP, 0.0, (double)nb * op.batch_bytes);
+  const long long work = (long long)nb * op.m_tiles * op.k_tiles * TC_BM * 8;
+  pack_A_kernel<<<gridn(work), 256, 0, c.stream>>>(src, op_stride, lda, r0, c0, M, K, per_batch, nterm,
+                                                  op.k_tiles_op, op.m_tiles, nb, op.tiles);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+// Y = alpha * op(X) (+ beta Y).  X: FP64 columns (rhs, cell), K values each.  coef: [ncell][nops]
+// scaling of the K blocks (combine mode), or null.  Y: FP64 or FP32; separate mode writes batch k
+// at Y + k * y_b_stride.
+fetidp_status tc_apply(Ctx& c, const TcOperator& op, CCellVec X, const double* coef, void* Y,
+                       bool y_f64, long long y_rs, int y_cs, long long y_b_stride, double alpha,
+                       double beta, int nrhs, long long ncell, long long y_ext) {
+  const long long ncols = ncell * nrhs;
+  const int batch = op.separate ? op.nops : 1;
+  const int BN = tc_bn_for(ncols, op.m_tiles, batch);
+  const int n_tiles = (int)((ncols + BN - 1) / BN);
+  const int nops_b = op.separate ? 1 : op.nops;
+  const int k_tiles = nops_b * op.nterm * op.k_tiles_op;
+  const size_t b_bytes = (size_t)n_tiles * k_tiles * BN * TC_BK * 2;
+  if (b_bytes > c.tc_bbuf_bytes) {
+    set_error("tensor-core B staging buffer too small");
+    return FETIDP_EINVAL;
+  }
+  {
+    ProfScope ps(c, FETIDP_K_MAPS, 0.0, (double)ncols * op.K * 8.0 + (double)b_bytes);
+    const long long work = (long long)n_tiles * k_tiles * BN * 8;
+    if (BN == 256)
+      pack_B_kernel<256><<<gridn(work), 256, 0, c.stream>>>(X.p, X.rs, X.cs, op.K, coef, op.nops, nops_b,
+                                                           op.nterm, op.k_tiles_op, ncols, ncell, n_tiles,
+                                                           c.tc_bbuf, X.ext, (long long)c.tc_bbuf_bytes);
+    else if (BN == 128)
+      pack_B_kernel<128><<<gridn(work), 256, 0, c.stream>>>(X.p, X.rs, X.cs, op.K, coef, op.nops, nops_b,
+                                                           op.nterm, op.k_tiles_op, ncols, ncell, n_tiles,
+                                                           c.tc_bbuf, X.ext, (long long)c.tc_bbuf_bytes);
+    else
+      pack_B_kernel<64><<<gridn(work), 256, 0, c.stream>>>(X.p, X.rs, X.cs, op.K, coef, op.nops, nops_b,
+                                                          op.nterm, op.k_tiles_op, ncols, ncell, n_tiles,
+                                                          c.tc_bbuf, X.ext, (long long)c.tc_bbuf_bytes);
+    FD_CHECK_LAUNCH();
+  }
+  TcParams P;
+  P.A = op.tiles;
+  P.B = c.tc_bbuf;
+  P.m_tiles = op.m_tiles;
+  P.n_tiles = n_tiles;
+  P.k_tiles = k_tiles;
+  P.a_batch_stride = op.separate ? op.batch_bytes : 0;
+  P.b_batch_stride = 0;
+  P.M = op.M;
+  P.ncols = ncols;
+  P.ncell = ncell;
+  P.Y = Y;
+  P.y_f64 = y_f64 ? 1 : 0;
+  P.y_rs = y_rs;
+  P.y_cs = y_cs;
+  P.y_b_stride = y_b_stride;
+  P.alpha = alpha;
+  P.beta = beta;
+  P.err = c.tc_err;
+  P.a_bytes = (long long)batch * op.batch_bytes;
+  P.b_bytes = (long long)c.tc_bbuf_bytes;
+  P.y_ext = y_ext;
+  const double flops = 2.0 * op.m_tiles * TC_BM * (double)k_tiles * TC_BK * (double)n_tiles * BN * batch;
+  ProfScope ps(c, FETIDP_K_TC_GEMM, flops,
+               (double)batch * op.batch_bytes + (double)b_bytes + (double)ncols * op.M * (y_f64 ? 8 : 4) * batch);
+  if (BN == 256) return launch_tc<256, 4>(c, P, batch);
+  if (BN == 128) return launch_tc<128, 6>(c, P, batch);
+  return launch_tc<64, 8>(c, P, batch);
+}
+
+// Self-check of the tensor-core path: random A (M x K), X (N columns), compare with an FP64
+// GEMM of the same bf16-rounded inputs.  Returns the max relative error in *rel_err.
+fetidp_status tc_selfcheck(Ctx& c, int M, int K, int N, double* rel_err) {
+  double *A = nullptr, *X = nullptr, *Yt = nullptr, *Yr = nullptr;
+  FD_CUDA(cudaMalloc(&A, sizeof(double) * M * K));
+  FD_CUDA(cudaMalloc(&X, sizeof(double) * (size_t)N * K));
+  FD_CUDA(cudaMalloc(&Yt, sizeof(double) * (size_t)N * M));
+  FD_CUDA(cudaMalloc(&Yr, sizeof(double) * (size_t)N * M));
+  fill_random_kernel<<<gridn((long long)M * K), 256, 0, c.stream>>>(A, (long long)M * K, 1234);
+  fill_random_kernel<<<gridn((long long)N * K), 256, 0, c.stream>>>(X, (long long)N * K, 5678);
+  FD_CHECK_LAUNCH();
+  TcOperator op;
+  FD_TRY(tc_pack_operator(c, op, A, 0, K, 0, 0, M, K, 1, false, 1));
+  FD_TRY(tc_apply(c, op, CCellVec{X, 0, K}, nullptr, Yt, true, 0, M, 0, 1.0, 0.0, 1, N));
+  ref_gemm_kernel<<<gridn((long long)M * N), 256, 0, c.stream>>>(A, X, M, K, N, Yr);
+  FD_CHECK_LAUNCH();
+  std::vector<double> ht((size_t)N * M), hr((size_t)N * M);
+  FD_CUDA(cudaMemcpyAsync(ht.data(), Yt, sizeof(double) * ht.size(), cudaMemcpyDeviceToHost, c.stream));
+  FD_CUDA(cudaMemcpyAsync(hr.data(), Yr, sizeof(double) * hr.size(), cudaMemcpyDeviceToHost, c.stream));
+  int herr = 0;
+  FD_CUDA(cudaMemcpyAsync(&herr, c.tc_err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  FD_CUDA(cudaStreamSynchronize(c.stream));
+  cudaFree(A); cudaFree(X); cudaFree(Yt); cudaFree(Yr);
+  if (herr != 0) {
+    set_error("tensor-core GEMM wait timed out (code " + std::to_string(herr) + ")");
+    return FETIDP_ETIMEOUT;
+  }
+  double mx = 0.0, ref = 0.0;
+  for (size_t i = 0; i < ht.size(); ++i) {
+    mx = std::max(mx, std::fabs(ht[i] - hr[i]));
+    ref = std::max(ref, std::fabs(hr[i]));
+  }
+  *rel_err = mx / (ref > 0 ? ref : 1.0);
+  return FETIDP_OK;
+}
+
+FD_DEFINE_CHECK(fd_check_tc)
+
+}  // namespace fetidp

@@ -1,0 +1,94 @@
+"""Mixed-precision path (principal contractions on tcgen05 tensor cores, BF16 operands with
+FP32 accumulation; everything else FP64) against the FP64 oracle.
+
+Tolerances: one BF16 x BF16 product has input rounding 2^-9 per operand, so a contraction
+is accurate to ~1e-2 of its largest terms; the hi + lo split (3 products) leaves ~2^-17
+input rounding, so ~1e-4.  The converged solution is held to the FP64 outer residual, so
+its displacement must match the monolithic solution to <= 1e-7 at relative residual <= 1e-8.
+"""
+import numpy as np
+import pytest
+
+from paper_2308_11371_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300)
+
+
+def _dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def _host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _mixed(prob, **kw):
+    from paper_2308_11371_gb300 import binding
+    return binding.Solver(prob, precision=binding.FETIDP_MIXED_BF16, **kw)
+
+
+_OC = {}
+
+
+def oracle(name):
+    if name not in _OC:
+        from oracle.discretization import Lattice
+        from oracle import ifeti_dp
+        prob = {"cfg1": W.config1(),
+                "ragged2d": W.lattice_2d(12, 7, 6, a=0.9, r=0.12, r_grade=0.04, n_rb=5),
+                "bcc3d": W.lattice_3d(2, 2, 2, e=3, r=0.2, r_spread=0.06, seed=7, n_rb=4,
+                                      map_kind=W.MAP_SHEAR_BEND_3D, map_params=(0.3, 2.0, 0.1, -0.15))}[name]
+        lat = Lattice(prob)
+        _OC[name] = (prob, lat, ifeti_dp.InexactFETIDP(lat))
+    return _OC[name]
+
+
+@pytest.mark.parametrize("split,tol", [(1, 3e-2), (3, 3e-4)])
+@pytest.mark.parametrize("name", ["cfg1", "ragged2d", "bcc3d"])
+def test_mixed_interface_operators(name, split, tol):
+    prob, lat, fe = oracle(name)
+    s = _mixed(prob, tc_split=split)
+    rng = np.random.default_rng(31)
+    lam = rng.standard_normal((s.n_rhs, s.L))
+    y = _host(s.apply_F(_dev(lam)))[0]
+    z = _host(s.precond(_dev(lam)))[0]
+    assert _rel(y, fe.apply_F(lam[0])) < tol
+    assert _rel(z, fe.apply_MD(lam[0])) < tol
+
+
+@pytest.mark.parametrize("name", ["cfg1", "ragged2d", "bcc3d"])
+def test_mixed_local_rom_solve(name):
+    """Eq. 46 with an FP32 basis from the tensor cores: the Galerkin projection with the exact
+    K_s keeps the solve a near-best approximation, so it matches the FP64 one closely."""
+    prob, lat, fe = oracle(name)
+    s = _mixed(prob)
+    rng = np.random.default_rng(33)
+    v = rng.standard_normal((s.n_rhs, s.N, s.n_r))
+    x = _host(s.local_rom_solve(_dev(v)))[0]
+    assert _rel(x, fe.rom.local_rom_solve(v[0])) < 1e-3
+
+
+@pytest.mark.parametrize("split", [1, 3])
+@pytest.mark.parametrize("name", ["cfg1", "ragged2d", "bcc3d"])
+def test_mixed_solve_matches_monolithic(name, split):
+    from oracle import monolithic
+    prob, lat, fe = oracle(name)
+    s = _mixed(prob, tc_split=split)
+    u, lam, info = s.solve()
+    assert info["rel_residual"] <= 1e-8
+    ref = monolithic.to_cells(lat, monolithic.solve(lat))
+    assert _rel(_host(u)[0], ref[0]) < 1e-7
+
+
+def test_mixed_config2_converges():
+    """The 64x64 workload (32 principal cells) in mixed precision reaches 1e-8."""
+    prob = W.config2(n_rb=W.CONFIG2_SOLVE_N_RB)
+    s = _mixed(prob)
+    u, lam, info = s.solve()
+    assert info["rel_residual"] <= 1e-8 and info["outer_its"] <= 12
