@@ -247,6 +247,11 @@ fetidp_status fetidp_profile_read(fetidp_ctx *ctx, double *ms, long long *launch
  * ETIMEOUT if a bounded device wait expired.                                           */
 fetidp_status fetidp_tc_selfcheck(int M, int K, int N, double *rel_err);
 
+/* Self-check of the fused combine kernel: nops random operators of M0 + M1 rows, rows below M0
+ * combined with one random coefficient set and the others with a second set, random N
+ * columns X; compared with FP64 on the same BF16-rounded inputs.  Diagnostic only.        */
+fetidp_status fetidp_tc_comb_selfcheck(int M0, int M1, int K, int N, int nops, double *rel_err);
+
 /* Number of kernels this library has launched in the calling process. */
 long long fetidp_kernel_launches(void);
 

@@ -28,7 +28,8 @@ SYMBOLS = ["fetidp_sizes", "fetidp_default_options", "fetidp_setup", "fetidp_app
            "fetidp_scatter_B", "fetidp_apply_K", "fetidp_coarse_solve", "fetidp_local_rom_solve",
            "fetidp_apply_A", "fetidp_apply_P", "fetidp_rom_data", "fetidp_destroy",
            "fetidp_status_string", "fetidp_last_error", "fetidp_profile_enable",
-           "fetidp_profile_read", "fetidp_kernel_launches", "fetidp_tc_selfcheck"]
+           "fetidp_profile_read", "fetidp_kernel_launches", "fetidp_tc_selfcheck",
+           "fetidp_tc_comb_selfcheck"]
 
 KCLASS = {"grouped_gemm": 0, "apply_K": 1, "maps": 2, "coarse": 3, "cell_gemv": 4, "vector": 5,
           "gram": 6, "tc_gemm": 7, "setup": 8}
@@ -122,6 +123,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.fetidp_profile_enable.argtypes = [P, ctypes.c_uint]
     lib.fetidp_profile_read.restype = I
     lib.fetidp_profile_read.argtypes = [P, V, V, V, V]
+    lib.fetidp_tc_comb_selfcheck.restype = I
+    lib.fetidp_tc_comb_selfcheck.argtypes = [I, I, I, I, I, ctypes.POINTER(ctypes.c_double)]
     lib.fetidp_tc_selfcheck.restype = I
     lib.fetidp_tc_selfcheck.argtypes = [I, I, I, ctypes.POINTER(ctypes.c_double)]
     lib.fetidp_kernel_launches.restype = ctypes.c_longlong
@@ -325,4 +328,11 @@ def tc_selfcheck(M: int, K: int, N: int) -> float:
     """Max relative error of the tcgen05 GEMM against FP64 on the same BF16 inputs."""
     err = ctypes.c_double()
     _check(load().fetidp_tc_selfcheck(M, K, N, ctypes.byref(err)))
+    return err.value
+
+
+def tc_comb_selfcheck(M0: int, M1: int, K: int, N: int, nops: int) -> float:
+    """Max relative error of the fused combine kernel against FP64 on the same BF16 inputs."""
+    err = ctypes.c_double()
+    _check(load().fetidp_tc_comb_selfcheck(M0, M1, K, N, nops, ctypes.byref(err)))
     return err.value

@@ -68,7 +68,7 @@ __device__ __forceinline__ bool fd_in_bounds(long long idx, long long extent, in
 #define FD_INB(idx, extent, code) fd_in_bounds((long long)(idx), (long long)(extent), (code))
 #define FD_CHECKED_BUILD 1
 #else
-#define FD_INB(idx, extent, code) true
+#define FD_INB(idx, extent, code) ((void)(idx), (void)(extent), true)
 #define FD_CHECKED_BUILD 0
 #endif
 // per-translation-unit readers of the violation record (FETIDP_OK in unchecked builds)
@@ -140,6 +140,14 @@ struct TcOperator {
   bool separate = false;
   int m_tiles = 0, k_tiles_op = 0, k_tiles = 0;
   long long batch_bytes = 0;
+};
+
+// Principal-operator set for the fused combine kernel (operator tiles with hi/lo parts; rows
+// [0, msplit) combined with coef0, the rest with coef1).
+struct TcComb {
+  uint8_t* tiles = nullptr;
+  int M = 0, msplit = 0, K = 0, nops = 0, nA = 1, nX = 1, m_tiles = 0, kto = 0;
+  long long bytes = 0;
 };
 
 // Kernel-class profiler: CUDA event pairs on the context stream plus the algorithmic
@@ -232,10 +240,10 @@ struct Ctx {
   // tensor-core path (mixed precision)
   bool mixed = false;           // FETIDP_MIXED_BF16
   TcOperator opKinv;            // K_rr^(k)^{-1}, separate (Eq. 46a)
-  TcOperator opUrdT;            // U_rd^(k)T = rows d of K_rr^(k)^{-1}, combined with delta (Alg. 3)
-  TcOperator opUrd;             // U_rd^(k) = columns d of K_rr^(k)^{-1}, combined with delta
-  TcOperator opFdd;             // F_dd^(k), combined with delta (Eq. 48)
-  TcOperator opSdd;             // S_dd^(k), combined with alpha (Eq. 49)
+  TcComb cFdd;                  // F_dd^(k) combined with delta (Eq. 48)
+  TcComb cSdd;                  // S_dd^(k) combined with alpha (Eq. 49)
+  TcComb cUrdT;                 // U_rd^(k)T combined with delta (Algorithm 3)
+  TcComb cUrd;                  // U_rd^(k) combined with delta (transpose of Algorithm 3)
   uint8_t* tc_bbuf = nullptr;   // packed B operand staging
   size_t tc_bbuf_bytes = 0;
   int* tc_err = nullptr;        // device error flag of the bounded waits
@@ -315,6 +323,17 @@ fetidp_status tc_apply(Ctx& c, const TcOperator& op, CCellVec X, const double* c
                        bool y_f64, long long y_rs, int y_cs, long long y_b_stride, double alpha,
                        double beta, int nrhs, long long ncell, long long y_ext = -1);
 fetidp_status tc_selfcheck(Ctx& c, int M, int K, int N, double* rel_err);
+void tc_free_operator(Ctx& c, TcOperator& op);
+int tc_comb_bn(long long ncols, int m_tiles);
+bool tc_comb_fits(int K, int split, long long ncols, int m_tiles);
+fetidp_status tc_comb_pack(Ctx& c, TcComb& op, const double* src0, long long st0, int lda0, int r00, int c00,
+                           int M0, const double* src1, long long st1, int lda1, int r01, int c01, int M1,
+                           int K, int nops, int split);
+size_t tc_comb_staging_bytes(const TcComb& op, long long ncols);
+fetidp_status tc_comb_selfcheck(Ctx& c, int M0, int M1, int K, int N, int nops, double* rel_err);
+fetidp_status tc_comb_apply(Ctx& c, const TcComb& op, CCellVec X, const double* coef0, const double* coef1,
+                            void* Y, bool y_f64, long long y_rs, int y_cs, double alpha, double beta, int nrhs,
+                            long long ncell);
 
 // ---------------------------------------------------------------- setup / coarse
 fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_options& o);

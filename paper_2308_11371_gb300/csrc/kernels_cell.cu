@@ -296,9 +296,14 @@ __global__ void __launch_bounds__(256) grouped_gemm_kernel(
 // products with a shuffle reduction, then lane 0 runs the diagonal-pivoted Cholesky and the
 // triangular solves on the warp's shared-memory scratch, and the warp forms x = R c.  Pivots
 // below drop_rel * max diag(G) are dropped (coefficient 0).
-// Scratch per warp (doubles): G, S, L (nrb x nrb each), h, y, c (nrb each), then nrb ints.
+// Scratch per warp (doubles): G, S, L (nrb x nrb each), h, y, c, pivot column (nrb each),
+// nrb ints (pivot order), 2 scalars (current pivot, its Schur diagonal), then two staging
+// tiles of R and K R (nrb x 32 values of the basis type each, counted in doubles).
 constexpr int kMaxRb = 64;
-__host__ __device__ inline int gram_warp_doubles(int nrb) { return 3 * nrb * nrb + 4 * nrb; }
+constexpr int kGramChunk = 32;
+__host__ __device__ inline int gram_warp_doubles(int nrb, int tb_bytes) {
+  return 3 * nrb * nrb + 5 * nrb + 2 + (2 * nrb * kGramChunk * tb_bytes + 7) / 8;
+}
 
 template <typename TB>
 __global__ void gram_warp_kernel(const TB* __restrict__ R, const TB* __restrict__ KR,
@@ -310,41 +315,71 @@ __global__ void gram_warp_kernel(const TB* __restrict__ R, const TB* __restrict_
   const long long col = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
   if (col >= ncell * nrhs) return;                  // the whole warp leaves together
   const int nb2 = nrb * nrb;
-  double* G = gwsm + (size_t)wib * gram_warp_doubles(nrb);
+  double* G = gwsm + (size_t)wib * gram_warp_doubles(nrb, (int)sizeof(TB));
   double* S = G + nb2;
   double* Lm = S + nb2;
   double* hs = Lm + nb2;
   double* ys = hs + nrb;
   double* cs = ys + nrb;
-  int* piv = reinterpret_cast<int*>(cs + nrb);      // nrb ints in the last nrb doubles
+  double* colv = cs + nrb;
+  int* piv = reinterpret_cast<int*>(colv + nrb);    // nrb ints in the next nrb doubles
+  double* sc = colv + 2 * nrb;                      // [0] pivot index, [1] its Schur diagonal
+  TB* Rt = reinterpret_cast<TB*>(sc + 2);           // nrb x kGramChunk
+  TB* Kt = Rt + nrb * kGramChunk;                   // nrb x kGramChunk
   const int rhs = (int)(col / ncell);
   const long long cell = col - (long long)rhs * ncell;
   const TB* Rc = R + col * (long long)nrb * nr;
   const TB* KRc = KR + col * (long long)nrb * nr;
   const double* vc = v + rhs * v_rs + cell * v_cs;
-  for (int i = 0; i < nrb; ++i) {
-    for (int j = i; j < nrb; ++j) {
-      double s = 0.0;
-      for (int q = lane; q < nr; q += 32) s += (double)Rc[(size_t)i * nr + q] * (double)KRc[(size_t)j * nr + q];
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-      if (lane == 0) {
-        G[i * nrb + j] = s;
-        G[j * nrb + i] = s;
-      }
+  // G (upper triangle, row-major pair index p) and h: each lane owns pairs p = lane + 32 t and
+  // h[lane + 32 t]; chunks of 32 entries of every basis vector are staged in shared memory
+  // (coalesced loads), products in the basis type, chunk sums accumulated in FP64.
+  const int npair = nrb * (nrb + 1) / 2;
+  for (int p = lane; p < npair; p += 32) {
+    int i = 0, rem = p;
+    while (rem >= nrb - i) { rem -= nrb - i; ++i; }
+    G[i * nrb + i + rem] = 0.0;
+  }
+  for (int i = lane; i < nrb; i += 32) hs[i] = 0.0;
+  for (int q0 = 0; q0 < nr; q0 += kGramChunk) {
+    const int qn = min(kGramChunk, nr - q0);
+    __syncwarp();
+    for (int i = 0; i < nrb; ++i) {
+      Rt[i * kGramChunk + lane] = lane < qn ? Rc[(size_t)i * nr + q0 + lane] : TB(0);
+      Kt[i * kGramChunk + lane] = lane < qn ? KRc[(size_t)i * nr + q0 + lane] : TB(0);
     }
-    double s = 0.0;
-    for (int q = lane; q < nr; q += 32) s += (double)Rc[(size_t)i * nr + q] * vc[q];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) hs[i] = s;
+    const double vq = lane < qn ? vc[q0 + lane] : 0.0;
+    __syncwarp();
+    for (int p = lane; p < npair; p += 32) {
+      int i = 0, rem = p;
+      while (rem >= nrb - i) { rem -= nrb - i; ++i; }
+      const int j = i + rem;
+      TB acc = TB(0);
+      for (int q = 0; q < kGramChunk; ++q) acc += Rt[i * kGramChunk + q] * Kt[j * kGramChunk + q];
+      G[i * nrb + j] += (double)acc;
+    }
+    for (int i = 0; i < nrb; ++i) {          // h_i += sum_q R_iq v_q (warp reduction)
+      double s = (double)Rt[i * kGramChunk + lane] * vq;
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if (lane == 0) hs[i] += s;
+    }
   }
   __syncwarp();
-  if (lane == 0) {
-    for (int t = 0; t < nb2; ++t) S[t] = G[t];
-    double dmax = 0.0;
-    for (int i = 0; i < nrb; ++i) dmax = fmax(dmax, G[i * nrb + i]);
-    unsigned long long used = 0ull;
-    int np = 0;
-    while (np < nrb) {
+  for (int p = lane; p < npair; p += 32) {    // mirror the upper triangle
+    int i = 0, rem = p;
+    while (rem >= nrb - i) { rem -= nrb - i; ++i; }
+    G[(i + rem) * nrb + i] = G[i * nrb + i + rem];
+  }
+  __syncwarp();
+  for (int t = lane; t < nb2; t += 32) S[t] = G[t];
+  double dmax = 0.0;
+  for (int i = 0; i < nrb; ++i) dmax = fmax(dmax, G[i * nrb + i]);
+  unsigned long long used = 0ull;                   // identical in every lane
+  int np = 0;
+  __syncwarp();
+  while (np < nrb) {
+    if (lane == 0) {
+      // largest remaining Schur diagonal, lowest index on ties
       int jb = -1;
       double best = 0.0;
       for (int i = 0; i < nrb; ++i) {
@@ -352,15 +387,24 @@ __global__ void gram_warp_kernel(const TB* __restrict__ R, const TB* __restrict_
         const double dv = S[i * nrb + i];
         if (jb < 0 || dv > best) { best = dv; jb = i; }
       }
-      if (jb < 0 || !(best > drop_rel * dmax)) break;
-      used |= 1ull << jb;
-      piv[np] = jb;
-      ++np;
-      const double inv = 1.0 / sqrt(best);
-      for (int i = 0; i < nrb; ++i) ys[i] = S[i * nrb + jb] * inv;   // pivot column (scratch)
-      for (int i = 0; i < nrb; ++i)
-        for (int j = 0; j < nrb; ++j) S[i * nrb + j] -= ys[i] * ys[j];
+      sc[0] = (double)jb;
+      sc[1] = best;
     }
+    __syncwarp();
+    const int jb = (int)sc[0];
+    const double best = sc[1];
+    if (jb < 0 || jb >= nrb || !(best > drop_rel * dmax)) break;   // uniform across the warp
+    used |= 1ull << jb;
+    if (lane == 0) piv[np] = jb;
+    ++np;
+    const double inv = 1.0 / sqrt(best);
+    for (int i = lane; i < nrb; i += 32) colv[i] = S[i * nrb + jb] * inv;
+    __syncwarp();
+    for (int i = lane; i < nrb; i += 32)             // each lane owns rows i
+      for (int j = 0; j < nrb; ++j) S[i * nrb + j] -= colv[i] * colv[j];
+    __syncwarp();
+  }
+  if (lane == 0) {
     // Cholesky of G restricted to the pivots (pivot order)
     for (int a = 0; a < np; ++a)
       for (int b = 0; b <= a; ++b) {
@@ -586,7 +630,7 @@ static fetidp_status gram_solve_t(Ctx& c, const TB* R, const TB* KR, CCellVec v,
   const long long cols = c.N * nrhs;
   ProfScope ps(c, FETIDP_K_GRAM, cols * 2.0 * c.nr * (c.nrb * (c.nrb + 1) / 2.0 + 2.0 * c.nrb),
                cols * (double)sizeof(TB) * (2.0 * c.nrb * c.nr) + cols * 16.0 * c.nr);
-  const size_t per_warp = (size_t)gram_warp_doubles(c.nrb) * sizeof(double);
+  const size_t per_warp = (size_t)gram_warp_doubles(c.nrb, (int)sizeof(TB)) * sizeof(double);
   int wpb = (int)std::min<size_t>(8, (200 * 1024) / per_warp);
   if (wpb < 1) wpb = 1;
   const size_t smem = per_warp * wpb;

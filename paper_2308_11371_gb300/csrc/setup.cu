@@ -6,6 +6,8 @@
 // traces of Eq. 42 (one GEMM against the snapshot matrix) and the ROM local
 // operators of Eq. 43.
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 
@@ -209,6 +211,17 @@ fetidp_status upload(Ctx& c, T** dst, const std::vector<T>& src) {
 fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_options& o) {
   using namespace host;
   auto t0 = std::chrono::steady_clock::now();
+  // FETIDP_VERBOSE=1: synchronise after each phase and print its wall time to stderr
+  const bool verbose = std::getenv("FETIDP_VERBOSE") != nullptr;
+  auto tp = t0;
+  auto phase = [&](const char* name) {
+    if (!verbose) return;
+    cudaStreamSynchronize(c.stream);
+    const auto now = std::chrono::steady_clock::now();
+    std::fprintf(stderr, "[fetidp setup] %-28s %8.2f ms\n", name,
+                 std::chrono::duration<double, std::milli>(now - tp).count());
+    tp = now;
+  };
   // ---------------------------------------------------------------- validation
   if (p.dim != 2 && p.dim != 3) { set_error("dim must be 2 or 3"); return FETIDP_EINVAL; }
   if (p.elems < 2) { set_error("elems must be >= 2"); return FETIDP_EINVAL; }
@@ -255,6 +268,7 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
     FD_TRY(upload(c, &c.perm, pp));
   }
   FD_TRY(upload(c, &c.r_dev, c.r_cell));
+  phase("reference tables");
 
   // ---------------------------------------------------------------- multipliers (Eqs. 14-15)
   const int nx = p.cells[0], ny = p.cells[1], nz = p.cells[2];
@@ -332,6 +346,7 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
   FD_TRY(upload(c, &c.gath, gath));
   FD_TRY(upload(c, &c.scat, scat));
   FD_TRY(upload(c, &c.Dw, Dw));
+  phase("multiplier maps");
 
   // ---------------------------------------------------------------- primal DOF (Eq. 18)
   const int vd[3] = {nx + 1, ny + 1, d == 3 ? nz + 1 : 1};
@@ -385,10 +400,12 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
     }
     FD_TRY(upload(c, &c.rhs, rhs));
   }
+  phase("primal maps + loads");
 
   // ---------------------------------------------------------------- snapshots (Eq. 52)
   FD_TRY(dalloc_t(c, &c.snap, (size_t)c.N * c.nsnap));
   FD_TRY(k_snapshots(c));
+  phase("snapshots");
 
   // ---------------------------------------------------------------- Algorithm 4 (greedy)
   const int nrb_req = p.n_rb;
@@ -455,6 +472,7 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
   }
   free_greedy();
   FD_TRY(upload(c, &c.alpha, h_alpha));
+  phase("greedy + alpha");
 
   // ---------------------------------------------------------------- principal operators (Eq. 39)
   const int n = c.n, nr = c.nr, ni = c.ni, nd = c.nd, np = c.np;
@@ -498,6 +516,7 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
   FD_TRY(upload(c, &c.Urp, hUrp));
   FD_TRY(upload(c, &c.UrpT, hUrpT));
   FD_TRY(upload(c, &c.Sdd, hSdd));
+  phase("principal factorisations");
 
   // ---------------------------------------------------------------- projections pi, delta (Eqs. 41-42)
   std::vector<double> h_pi((size_t)c.N * nrb), h_delta((size_t)c.N * nrb);
@@ -529,9 +548,11 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
     FD_CUDA(cudaMemcpyAsync(specs_dev, specs.data(), sizeof(TraceTableSpec) * specs.size(),
                             cudaMemcpyHostToDevice, c.stream));
     FD_TRY(k_trace_tables(c, specs_dev, (int)specs.size(), Tab, c.nsnap));
-    FD_TRY(k_grouped_gemm_n(c, Tab, 0, (int)c.nsnap, ntab, (int)c.nsnap, 1,
-                            CCellVec{c.snap, 0, (int)c.nsnap}, CellVec{Y, 0, ntab}, nullptr, 1.0, 0.0,
-                            c.N, 1, false, 0));
+    // Both trace systems of Eq. 42 are Gram matrices of nearly dependent principal fields; their
+    // pivoted solves decide which directions to drop at 1e-12 of the largest pivot, so the traces
+    // are always taken in FP64 (a BF16-split contraction changes those decisions).
+    FD_TRY(k_grouped_gemm_n(c, Tab, 0, (int)c.nsnap, ntab, (int)c.nsnap, 1, CCellVec{c.snap, 0, (int)c.nsnap},
+                            CellVec{Y, 0, ntab}, nullptr, 1.0, 0.0, c.N, 1, false, 0));
     std::vector<double> hY((size_t)c.N * ntab);
     FD_CUDA(cudaMemcpyAsync(hY.data(), Y, sizeof(double) * hY.size(), cudaMemcpyDeviceToHost, c.stream));
     FD_CUDA(cudaStreamSynchronize(c.stream));
@@ -554,6 +575,7 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
   }
   FD_TRY(upload(c, &c.pi, h_pi));
   FD_TRY(upload(c, &c.delta, h_delta));
+  phase("projections pi, delta");
 
   // ---------------------------------------------------------------- ROM local operators (Eq. 43)
   if (!c.mixed) {   // FP64 path: per-cell assembled F_dd_ring, S_dd_ring
@@ -562,24 +584,33 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
     FD_TRY(k_rom_combine(c, c.Kinv, (long long)nr * nr, nr, ni, ni, nd, nd, c.delta, c.Fdd_c, false));
     FD_TRY(k_rom_combine(c, c.Sdd, (long long)nd * nd, nd, 0, 0, nd, nd, c.alpha, c.Sdd_c, false));
   } else {          // mixed path: principal operators packed for the tensor cores
-    const int nt = o.tc_split == 3 ? 3 : 1;
-    FD_TRY(tc_pack_operator(c, c.opKinv, c.Kinv, (long long)nr * nr, nr, 0, 0, nr, nr, nrb, true, nt));
-    FD_TRY(tc_pack_operator(c, c.opUrdT, c.Kinv, (long long)nr * nr, nr, ni, 0, nd, nr, nrb, false, nt));
-    FD_TRY(tc_pack_operator(c, c.opUrd, c.Kinv, (long long)nr * nr, nr, 0, ni, nr, nd, nrb, false, nt));
-    FD_TRY(tc_pack_operator(c, c.opFdd, c.Kinv, (long long)nr * nr, nr, ni, ni, nd, nd, nrb, false, nt));
-    FD_TRY(tc_pack_operator(c, c.opSdd, c.Sdd, (long long)nd * nd, nd, 0, 0, nd, nd, nrb, false, nt));
-    size_t mx = 0;
+    const int split = o.tc_split == 3 ? 3 : 1;
     const long long ncols = c.N * c.m;
-    for (const TcOperator* op : {&c.opKinv, &c.opUrdT, &c.opUrd, &c.opFdd, &c.opSdd}) {
-      const int batch = op->separate ? op->nops : 1;
-      const int bn = tc_bn_for(ncols, op->m_tiles, batch);
+    FD_TRY(tc_pack_operator(c, c.opKinv, c.Kinv, (long long)nr * nr, nr, 0, 0, nr, nr, nrb, true, split));
+    FD_TRY(tc_comb_pack(c, c.cFdd, c.Kinv, (long long)nr * nr, nr, ni, ni, nd, nullptr, 0, 0, 0, 0, 0, nd, nrb,
+                        split));
+    FD_TRY(tc_comb_pack(c, c.cSdd, c.Sdd, (long long)nd * nd, nd, 0, 0, nd, nullptr, 0, 0, 0, 0, 0, nd, nrb, split));
+    FD_TRY(tc_comb_pack(c, c.cUrdT, c.Kinv, (long long)nr * nr, nr, ni, 0, nd, nullptr, 0, 0, 0, 0, 0, nr, nrb,
+                        split));
+    FD_TRY(tc_comb_pack(c, c.cUrd, c.Kinv, (long long)nr * nr, nr, 0, ni, nr, nullptr, 0, 0, 0, 0, 0, nd, nrb,
+                        split));
+    for (const TcComb* cb : {&c.cFdd, &c.cSdd, &c.cUrdT, &c.cUrd})
+      if (!tc_comb_fits(cb->K, split, ncols, cb->m_tiles)) {
+        set_error("combine kernel does not fit this cell size");
+        return FETIDP_EINVAL;
+      }
+    size_t mx = 0;
+    {
+      const TcOperator* op = &c.opKinv;
+      const int bn = tc_bn_for(ncols, op->m_tiles, op->nops);
       const long long n_tiles = (ncols + bn - 1) / bn;
-      const int k_tiles = (op->separate ? 1 : op->nops) * op->nterm * op->k_tiles_op;
-      mx = std::max(mx, (size_t)n_tiles * k_tiles * bn * 64 * 2);
+      mx = (size_t)n_tiles * op->k_tiles * bn * 64 * 2;
     }
+    for (const TcComb* cb : {&c.cFdd, &c.cSdd, &c.cUrdT, &c.cUrd})
+      mx = std::max(mx, tc_comb_staging_bytes(*cb, ncols));
     c.tc_bbuf_bytes = mx;
     FD_TRY(dalloc(c, reinterpret_cast<void**>(&c.tc_bbuf), mx));
-    FD_TRY(dalloc(c, reinterpret_cast<void**>(&c.tc_err), sizeof(int)));
+    if (!c.tc_err) FD_TRY(dalloc(c, reinterpret_cast<void**>(&c.tc_err), sizeof(int)));
     FD_CUDA(cudaMemsetAsync(c.tc_err, 0, sizeof(int), c.stream));
   }
   FD_TRY(dalloc_t(c, &c.Urp_c, (size_t)c.N * nr * np));
@@ -613,7 +644,9 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
       for (int r = 0; r < np; ++r)
         for (int q = 0; q < np; ++q) out[(size_t)r * np + q] = 0.5 * (X[(size_t)r * np + q] + X[(size_t)q * np + r]);
     });
+    phase("S_pp per cell");
     FD_TRY(coarse_setup(c, Spp));
+    phase("coarse factorisation");
   }
 
   // ---------------------------------------------------------------- workspace
@@ -638,6 +671,7 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
   FD_TRY(dalloc_t(c, &c.scal, 64 * m + (size_t)m * (o.max_outer + 2) * 2));
   FD_CUDA(cudaMallocHost(&c.h_scal, sizeof(double) * (64 * m + (size_t)m * (o.max_outer + 2) * 2)));
   FD_CUDA(cudaStreamSynchronize(c.stream));
+  phase("workspace");
   c.t_setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return FETIDP_OK;
 }

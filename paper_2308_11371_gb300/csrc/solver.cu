@@ -148,7 +148,7 @@ fetidp_status op_apply_F(Ctx& c, const double* lam, long long lam_rs, double* y,
   CellVec g{c.w_d1, c.N * nd, nd}, yd{c.w_d2, c.N * nd, nd}, cp{c.w_p1, c.N * np, np};
   FD_TRY(k_gather_BT(c, lam, lam_rs, nullptr, g, m, 0.0));
   if (c.mixed)
-    FD_TRY(tc_apply(c, c.opFdd, cview(g), c.delta, yd.p, true, yd.rs, yd.cs, 0, 1.0, 0.0, m, c.N));
+    FD_TRY(tc_comb_apply(c, c.cFdd, cview(g), c.delta, c.delta, yd.p, true, yd.rs, yd.cs, 1.0, 0.0, m, c.N));
   else
     FD_TRY(cell_op(c, c.Fdd_c, (long long)nd * nd, nd, nd, nd, cview(g), yd, 1.0, 0.0));
   // coarse correction: c_p = (T_dr U_rp_ring)^T g, assembled, S_PP^{-1}, prolonged
@@ -167,7 +167,7 @@ fetidp_status op_apply_MD(Ctx& c, const double* r, long long r_rs, double* z, lo
   CellVec g{c.w_d1, c.N * nd, nd}, yd{c.w_d2, c.N * nd, nd};
   FD_TRY(k_gather_BT(c, r, r_rs, c.Dw, g, m, 0.0));
   if (c.mixed)
-    FD_TRY(tc_apply(c, c.opSdd, cview(g), c.alpha, yd.p, true, yd.rs, yd.cs, 0, 1.0, 0.0, m, c.N));
+    FD_TRY(tc_comb_apply(c, c.cSdd, cview(g), c.alpha, c.alpha, yd.p, true, yd.rs, yd.cs, 1.0, 0.0, m, c.N));
   else
     FD_TRY(cell_op(c, c.Sdd_c, (long long)nd * nd, nd, nd, nd, cview(g), yd, 1.0, 0.0));
   FD_TRY(k_scatter_B(c, cview(yd), z, z_rs, c.Dw, 1.0, 0.0, m));
@@ -187,7 +187,7 @@ fetidp_status U_apply(Ctx& c, CCellVec vR, const double* vP, long long vP_rs, do
   FD_TRY(coarse_solve(c, c.w_P1, c.nP, c.w_zP, c.nP, m));
   // t_d = U_rd_ring^T v_r - T_dr U_rp_ring A_p^T z_P
   if (c.mixed)
-    FD_TRY(tc_apply(c, c.opUrdT, vR, c.delta, td.p, true, td.rs, td.cs, 0, 1.0, 0.0, m, c.N));
+    FD_TRY(tc_comb_apply(c, c.cUrdT, vR, c.delta, c.delta, td.p, true, td.rs, td.cs, 1.0, 0.0, m, c.N));
   else
     FD_TRY(k_grouped_gemm(c, c.Kinv + (size_t)ni * nr, (long long)nr * nr, nr, nd, nr, vR, td, c.delta,
                           1.0, 0.0, m, false, 0));
@@ -333,7 +333,7 @@ fetidp_status op_precondition(Ctx& c, const double* x, double* y) {
   FD_TRY(k_primal_assemble(c, cview(cp), c.w_P1, c.nP, -1.0, 0.0, m));
   FD_TRY(coarse_solve(c, c.w_P1, c.nP, c.w_P1, c.nP, m));
   if (c.mixed)
-    FD_TRY(tc_apply(c, c.opUrd, cview(g), c.delta, yR.p, true, yR.rs, yR.cs, 0, -1.0, 1.0, m, c.N));
+    FD_TRY(tc_comb_apply(c, c.cUrd, cview(g), c.delta, c.delta, yR.p, true, yR.rs, yR.cs, -1.0, 1.0, m, c.N));
   else
     FD_TRY(k_grouped_gemm(c, c.Kinv + ni, (long long)nr * nr, nr, nr, nd, cview(g), yR, c.delta, -1.0,
                           1.0, m, false, 0));
@@ -550,6 +550,26 @@ const char* fetidp_status_string(fetidp_status s) {
 const char* fetidp_last_error(void) { return g_last_error.c_str(); }
 
 long long fetidp_kernel_launches(void) { return g_launches.load(); }
+
+fetidp_status fetidp_tc_comb_selfcheck(int M0, int M1, int K, int N, int nops, double* rel_err) {
+  if (M0 < 1 || M1 < 0 || K < 1 || N < 1 || nops < 1 || !rel_err) {
+    set_error("bad self-check sizes");
+    return FETIDP_EINVAL;
+  }
+  fetidp_ctx tmp;
+  Ctx& c = tmp.c;
+  cudaGetDevice(&c.device);
+  c.stream = nullptr;
+  fetidp_status st = dalloc(c, reinterpret_cast<void**>(&c.tc_err), sizeof(int));
+  if (st == FETIDP_OK) {
+    cudaMemset(c.tc_err, 0, sizeof(int));
+    st = tc_comb_selfcheck(c, M0, M1, K, N, nops, rel_err);
+  }
+  cudaStreamSynchronize(nullptr);
+  for (void* p : c.allocations) cudaFree(p);
+  c.allocations.clear();
+  return st;
+}
 
 fetidp_status fetidp_tc_selfcheck(int M, int K, int N, double* rel_err) {
   if (M < 1 || K < 1 || N < 1 || !rel_err) { set_error("bad self-check sizes"); return FETIDP_EINVAL; }

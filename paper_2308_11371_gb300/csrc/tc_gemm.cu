@@ -440,6 +440,304 @@ fetidp_status launch_tc(Ctx& c, const TcParams& P, int batch) {
 
 }  // namespace
 
+// ---------------------------------------------------------------- fused combine kernel
+// Y[:, c] = sum_k coef_k(c, row) (A_k X)[:, c] without materialising scaled copies of X:
+// X is packed once (hi [+ lo] BF16 parts) and stays resident in shared memory; the operators
+// A_k stream through a TMA ring; the MMAs of operator k accumulate in TMEM buffer k & 1; four
+// epilogue warps add coef * accumulator into FP32 registers while the MMA warp fills the other
+// buffer.  Rows below msplit use coef0, the others coef1 (stacked operator sets).
+// Warps 0-3 epilogue (TMEM lane quadrants), warp 4 producer, warp 5 MMA issuer.
+struct TcCombParams {
+  const uint8_t* A;
+  const uint8_t* B;
+  int m_tiles, n_tiles, kto, nops, nA, nX, astages;
+  int M, msplit;
+  long long ncols, ncell;
+  const double* coef0;
+  const double* coef1;
+  void* Y;
+  int y_f64;
+  long long y_rs;
+  int y_cs;
+  double alpha, beta;
+  int* err;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
+}
+
+template <int BN>
+__global__ void __launch_bounds__(192, 1) tc_comb_kernel(TcCombParams P) {
+  constexpr int B_TILE = BN * TC_BK * 2;
+  constexpr uint32_t TMEM_COLS = 2 * BN < 32 ? 32 : 2 * BN;
+  constexpr uint32_t IDESC = make_idesc(TC_BM, BN, true);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int KX = P.kto * P.nX;
+  const int S = P.astages;
+  uint8_t* sB = smem;
+  uint8_t* sA = sB + (size_t)KX * B_TILE;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + (size_t)S * A_TILE);
+  // bars: aFull[8], aEmpty[8], bFull, accFull[2], accEmpty[2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 21);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const uint32_t aFull = smem_u32(bars), aEmpty = smem_u32(bars + 8), bFull = smem_u32(bars + 16);
+  const uint32_t accFull = smem_u32(bars + 17), accEmpty = smem_u32(bars + 19);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nt = blockIdx.x, mt = blockIdx.y;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 8; ++s) {
+      mbar_init(aFull + 8 * s, 1);
+      mbar_init(aEmpty + 8 * s, 1);
+    }
+    mbar_init(bFull, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accFull + 8 * b, 1);
+      mbar_init(accEmpty + 8 * b, 128);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int per_op = P.kto * P.nA;
+  const int total = P.nops * per_op;
+  if (warp == 4) {
+    if (lane == 0) {
+      // resident X tiles, then the operator ring
+      const uint8_t* Bb = P.B + (long long)nt * KX * B_TILE;
+      mbar_expect_tx(bFull, (uint32_t)(KX * B_TILE));
+      for (int t = 0; t < KX; ++t)
+        bulk_g2s(smem_u32(sB + (size_t)t * B_TILE), Bb + (long long)t * B_TILE, B_TILE, bFull);
+      int issued = 0;
+      for (int i = 0; i < total; ++i) {
+        const int s = i % S, n = i / S;
+        if (i >= S && !mbar_wait(aEmpty + 8 * s, (uint32_t)((n - 1) & 1), abort_flag)) {
+          *abort_flag = 1;
+          atomicExch(P.err, 11);
+          break;
+        }
+        const int k = i / per_op, rem = i - k * per_op;   // rem = kt * nA + part
+        const uint8_t* src = P.A + (((long long)k * P.m_tiles + mt) * per_op + rem) * A_TILE;
+        mbar_expect_tx(aFull + 8 * s, A_TILE);
+        bulk_g2s(smem_u32(sA + (size_t)s * A_TILE), src, A_TILE, aFull + 8 * s);
+        ++issued;
+      }
+      // tail: every stage released (and, on abort, every copy landed) before the CTA may exit
+      for (int i = (issued > S ? issued - S : 0); i < issued; ++i) {
+        const int s = i % S, n = i / S;
+        unsigned long long t0 = gtime();
+        while (!mbar_try(aFull + 8 * s, (uint32_t)(n & 1)) && gtime() - t0 < kWaitNs) {
+        }
+        t0 = gtime();
+        while (!mbar_try(aEmpty + 8 * s, (uint32_t)(n & 1)) && gtime() - t0 < kWaitNs) {
+        }
+      }
+      {
+        const unsigned long long t0 = gtime();
+        while (!mbar_try(bFull, 0u) && gtime() - t0 < kWaitNs) {
+        }
+      }
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      bool ok = mbar_wait(bFull, 0u, abort_flag);
+      if (!ok) { *abort_flag = 1; atomicExch(P.err, 12); }
+      int i = 0;
+      for (int k = 0; ok && k < P.nops; ++k) {
+        const int b = k & 1;
+        if (k >= 2 && !mbar_wait(accEmpty + 8 * b, (uint32_t)(((k >> 1) - 1) & 1), abort_flag)) {
+          *abort_flag = 1;
+          atomicExch(P.err, 13);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        bool first = true;
+        const uint32_t dst = tmem + (uint32_t)(b * BN);
+        for (int kt = 0; ok && kt < P.kto; ++kt) {
+          for (int part = 0; part < P.nA; ++part, ++i) {
+            const int s = i % S, n = i / S;
+            if (!mbar_wait(aFull + 8 * s, (uint32_t)(n & 1), abort_flag)) {
+              *abort_flag = 1;
+              atomicExch(P.err, 14);
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint64_t ad = sw128_desc(smem_u32(sA + (size_t)s * A_TILE));
+            // A hi pairs with X hi (and X lo when split); A lo pairs with X hi
+            const int nxp = (part == 0) ? P.nX : 1;
+            for (int xp = 0; xp < nxp; ++xp) {
+              const uint64_t bd = sw128_desc(smem_u32(sB + (size_t)(kt * P.nX + xp) * B_TILE));
+#pragma unroll
+              for (int j = 0; j < TC_BK / 16; ++j) {
+                tc_mma(dst, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), IDESC, first ? 0u : 1u);
+                first = false;
+              }
+            }
+            tc_commit(aEmpty + 8 * s);
+          }
+        }
+        if (ok) tc_commit(accFull + 8 * b);
+      }
+    }
+  } else {
+    // ---------------- epilogue warps 0-3: one row per thread
+    const int m = mt * TC_BM + warp * 32 + lane;
+    const double* coef = (m < P.msplit) ? P.coef0 : P.coef1;
+    float acc[BN];
+#pragma unroll
+    for (int j = 0; j < BN; ++j) acc[j] = 0.f;
+    bool ok = true;
+    for (int k = 0; k < P.nops; ++k) {
+      const int b = k & 1;
+      if (!mbar_wait(accFull + 8 * b, (uint32_t)((k >> 1) & 1), abort_flag)) {
+        *abort_flag = 1;
+        atomicExch(P.err, 15);
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+#pragma unroll
+      for (int ch = 0; ch < BN / 32; ++ch) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * BN + ch * 32), r);
+        tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const long long cidx = (long long)nt * BN + ch * 32 + j;
+          float cf = 1.f;
+          if (coef != nullptr) {
+            cf = 0.f;
+            if (cidx < P.ncols) {
+              const long long cell = cidx % P.ncell;
+              cf = (float)coef[cell * P.nops + k];
+            }
+          }
+          acc[ch * 32 + j] += cf * __uint_as_float(r[j]);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(accEmpty + 8 * b);
+    }
+    if (ok && !*abort_flag && m < P.M) {
+#pragma unroll
+      for (int j = 0; j < BN; ++j) {
+        const long long cidx = (long long)nt * BN + j;
+        if (cidx < P.ncols) {
+          const int rhs = (int)(cidx / P.ncell);
+          const long long cell = cidx - (long long)rhs * P.ncell;
+          const long long off = rhs * P.y_rs + cell * P.y_cs + m;
+          const double v = P.alpha * (double)acc[j];
+          if (P.y_f64) {
+            double* y = reinterpret_cast<double*>(P.Y) + off;
+            *y = (P.beta == 0.0) ? v : v + P.beta * (*y);
+          } else {
+            float* y = reinterpret_cast<float*>(P.Y) + off;
+            *y = (P.beta == 0.0) ? (float)v : (float)(v + P.beta * (double)(*y));
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// Operator tiles for the combine kernel: tile ((op * m_tiles + mt) * kto + kt) * nA + part, part 0
+// the bf16 value, part 1 the bf16 rounding remainder.  Rows [0, M0) come from src0, rows
+// [M0, M0 + M1) from src1 (same K): element (m, kk) of op = srcX[op*strideX + (r0X + m)*ldaX + c0X + kk].
+__global__ void pack_comb_A_kernel(const double* __restrict__ src0, long long st0, int lda0, int r00,
+                                   int c00, int M0, const double* __restrict__ src1, long long st1,
+                                   int lda1, int r01, int c01, int M1, int K, int nops, int nA, int kto,
+                                   int m_tiles, uint8_t* __restrict__ out) {
+  const long long total = (long long)nops * m_tiles * kto * nA * TC_BM * 8;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int chunk = (int)(t & 7);
+    long long rest = t >> 3;
+    const int row = (int)(rest % TC_BM);
+    rest /= TC_BM;
+    const int part = (int)(rest % nA);
+    rest /= nA;
+    const int kt = (int)(rest % kto);
+    rest /= kto;
+    const int mt = (int)(rest % m_tiles);
+    const int op = (int)(rest / m_tiles);
+    const int m = mt * TC_BM + row;
+    alignas(16) __nv_bfloat16 v[8];
+    for (int e = 0; e < 8; ++e) {
+      const int kk = kt * TC_BK + chunk * 8 + e;
+      float x = 0.f;
+      if (kk < K && m < M0 + M1) {
+        const double a = (m < M0) ? src0[op * st0 + (long long)(r00 + m) * lda0 + c00 + kk]
+                                  : src1[op * st1 + (long long)(r01 + m - M0) * lda1 + c01 + kk];
+        const __nv_bfloat16 hi = __double2bfloat16(a);
+        x = (part == 1) ? (float)(a - (double)__bfloat162float(hi)) : __bfloat162float(hi);
+      }
+      v[e] = __float2bfloat16_rn(x);
+    }
+    uint8_t* tile = out + ((((long long)op * m_tiles + mt) * kto + kt) * nA + part) * A_TILE;
+    *reinterpret_cast<uint4*>(tile + sw128_offset(row, chunk * 8)) = *reinterpret_cast<uint4*>(v);
+  }
+}
+
+// X tiles for the combine kernel: tile (nt * kto + kt) * nX + part of BN columns.
+template <int BN>
+__global__ void pack_comb_X_kernel(const double* __restrict__ X, long long x_rs, int x_cs, int K, int nX,
+                                   int kto, long long ncols, long long ncell, int n_tiles,
+                                   uint8_t* __restrict__ out) {
+  constexpr int B_TILE = BN * TC_BK * 2;
+  const long long total = (long long)n_tiles * kto * nX * BN * 8;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int chunk = (int)(t & 7);
+    long long rest = t >> 3;
+    const int row = (int)(rest % BN);
+    rest /= BN;
+    const int part = (int)(rest % nX);
+    rest /= nX;
+    const int kt = (int)(rest % kto);
+    const int nt = (int)(rest / kto);
+    const long long cidx = (long long)nt * BN + row;
+    alignas(16) __nv_bfloat16 v[8];
+    if (cidx < ncols) {
+      const int rhs = (int)(cidx / ncell);
+      const long long cell = cidx - (long long)rhs * ncell;
+      const double* xc = X + rhs * x_rs + cell * x_cs;
+      for (int e = 0; e < 8; ++e) {
+        const int kk = kt * TC_BK + chunk * 8 + e;
+        float x = 0.f;
+        if (kk < K) {
+          const double a = xc[kk];
+          const __nv_bfloat16 hi = __double2bfloat16(a);
+          x = (part == 1) ? (float)(a - (double)__bfloat162float(hi)) : __bfloat162float(hi);
+        }
+        v[e] = __float2bfloat16_rn(x);
+      }
+    } else {
+      for (int e = 0; e < 8; ++e) v[e] = __float2bfloat16_rn(0.f);
+    }
+    uint8_t* tile = out + (((long long)nt * kto + kt) * nX + part) * B_TILE;
+    *reinterpret_cast<uint4*>(tile + sw128_offset(row, chunk * 8)) = *reinterpret_cast<uint4*>(v);
+  }
+}
+
+template <int BN>
+size_t comb_smem_bytes(int kto, int nX, int astages) {
+  return (size_t)kto * nX * BN * TC_BK * 2 + (size_t)astages * A_TILE + 8 * 21 + 16 + 1024;
+}
+
 // ---------------------------------------------------------------- host API
 int tc_bn_for(long long ncols, int m_tiles, int batch) {
   // smallest tile width that still gives at least one wave of CTAs on 148 SMs
@@ -470,6 +768,19 @@ fetidp_status tc_pack_operator(Ctx& c, TcOperator& op, const double* src, long l
                                                   op.k_tiles_op, op.m_tiles, nb, op.tiles);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
+}
+
+void tc_free_operator(Ctx& c, TcOperator& op) {
+  if (!op.tiles) return;
+  cudaStreamSynchronize(c.stream);
+  for (auto it = c.allocations.begin(); it != c.allocations.end(); ++it)
+    if (*it == op.tiles) {
+      c.allocations.erase(it);
+      break;
+    }
+  c.device_bytes -= (size_t)(op.separate ? op.nops : 1) * op.batch_bytes;
+  cudaFree(op.tiles);
+  op.tiles = nullptr;
 }
 
 // Y = alpha * op(X) (+ beta Y).  X: FP64 columns (rhs, cell), K values each.  coef: [ncell][nops]
@@ -561,6 +872,183 @@ fetidp_status tc_selfcheck(Ctx& c, int M, int K, int N, double* rel_err) {
   cudaFree(A); cudaFree(X); cudaFree(Yt); cudaFree(Yr);
   if (herr != 0) {
     set_error("tensor-core GEMM wait timed out (code " + std::to_string(herr) + ")");
+    return FETIDP_ETIMEOUT;
+  }
+  double mx = 0.0, ref = 0.0;
+  for (size_t i = 0; i < ht.size(); ++i) {
+    mx = std::max(mx, std::fabs(ht[i] - hr[i]));
+    ref = std::max(ref, std::fabs(hr[i]));
+  }
+  *rel_err = mx / (ref > 0 ? ref : 1.0);
+  return FETIDP_OK;
+}
+
+
+// ---------------------------------------------------------------- combine kernel host side
+int tc_comb_bn(long long ncols, int m_tiles) {
+  if (((ncols + 127) / 128) * m_tiles >= 148) return 128;
+  if (((ncols + 63) / 64) * m_tiles >= 148) return 64;
+  return 32;
+}
+
+static int comb_stages(int bn, int kto, int nX) {
+  const size_t budget = 220 * 1024;
+  const size_t b = (size_t)kto * nX * bn * TC_BK * 2 + 8 * 21 + 16 + 1024;
+  if (b >= budget) return 0;
+  int st = (int)((budget - b) / A_TILE);
+  if (st > 8) st = 8;
+  return st;
+}
+
+bool tc_comb_fits(int K, int split, long long ncols, int m_tiles) {
+  const int kto = (K + TC_BK - 1) / TC_BK;
+  const int bn = tc_comb_bn(ncols, m_tiles);
+  return comb_stages(bn, kto, split == 3 ? 2 : 1) >= 2;
+}
+
+fetidp_status tc_comb_pack(Ctx& c, TcComb& op, const double* src0, long long st0, int lda0, int r00, int c00,
+                           int M0, const double* src1, long long st1, int lda1, int r01, int c01, int M1,
+                           int K, int nops, int split) {
+  op.M = M0 + M1;
+  op.msplit = M0;
+  op.K = K;
+  op.nops = nops;
+  op.nA = split == 3 ? 2 : 1;
+  op.nX = split == 3 ? 2 : 1;
+  op.m_tiles = (op.M + TC_BM - 1) / TC_BM;
+  op.kto = (K + TC_BK - 1) / TC_BK;
+  op.bytes = (long long)nops * op.m_tiles * op.kto * op.nA * A_TILE;
+  FD_TRY(dalloc(c, reinterpret_cast<void**>(&op.tiles), (size_t)op.bytes));
+  ProfScope ps(c, FETIDP_K_SETUP, 0.0, (double)op.bytes);
+  const long long work = (long long)nops * op.m_tiles * op.kto * op.nA * TC_BM * 8;
+  pack_comb_A_kernel<<<gridn(work), 256, 0, c.stream>>>(src0, st0, lda0, r00, c00, M0, src1, st1, lda1, r01, c01,
+                                                       M1, K, nops, op.nA, op.kto, op.m_tiles, op.tiles);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+size_t tc_comb_staging_bytes(const TcComb& op, long long ncols) {
+  const int bn = tc_comb_bn(ncols, op.m_tiles);
+  const long long n_tiles = (ncols + bn - 1) / bn;
+  return (size_t)n_tiles * op.kto * op.nX * bn * TC_BK * 2;
+}
+
+template <int BN>
+static fetidp_status comb_launch(Ctx& c, const TcComb& op, const TcCombParams& P0, CCellVec X, long long ncols,
+                                 long long ncell) {
+  TcCombParams P = P0;
+  const int n_tiles = (int)((ncols + BN - 1) / BN);
+  P.n_tiles = n_tiles;
+  const size_t b_bytes = (size_t)n_tiles * op.kto * op.nX * BN * TC_BK * 2;
+  if (b_bytes > c.tc_bbuf_bytes) {
+    set_error("tensor-core X staging buffer too small");
+    return FETIDP_EINVAL;
+  }
+  P.astages = comb_stages(BN, op.kto, op.nX);
+  if (P.astages < 2) {
+    set_error("combine kernel: operand K too large for shared memory");
+    return FETIDP_EINVAL;
+  }
+  {
+    ProfScope ps(c, FETIDP_K_MAPS, 0.0, (double)ncols * op.K * 8.0 + (double)b_bytes);
+    const long long work = (long long)n_tiles * op.kto * op.nX * BN * 8;
+    pack_comb_X_kernel<BN><<<gridn(work), 256, 0, c.stream>>>(X.p, X.rs, X.cs, op.K, op.nX, op.kto, ncols,
+                                                              ncell, n_tiles, c.tc_bbuf);
+    FD_CHECK_LAUNCH();
+  }
+  const double flops = 2.0 * op.m_tiles * TC_BM * (double)op.kto * TC_BK * op.nops *
+                       (op.nA == 2 ? 3.0 : 1.0) * (double)n_tiles * BN;
+  ProfScope ps(c, FETIDP_K_TC_GEMM, flops,
+               (double)op.bytes + (double)b_bytes + (double)ncols * op.M * (P.y_f64 ? 8 : 4));
+  const size_t smem = comb_smem_bytes<BN>(op.kto, op.nX, P.astages);
+  cudaFuncSetAttribute(tc_comb_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid((unsigned)n_tiles, (unsigned)op.m_tiles, 1);
+  tc_comb_kernel<BN><<<grid, 192, smem, c.stream>>>(P);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status tc_comb_apply(Ctx& c, const TcComb& op, CCellVec X, const double* coef0, const double* coef1,
+                            void* Y, bool y_f64, long long y_rs, int y_cs, double alpha, double beta, int nrhs,
+                            long long ncell) {
+  const long long ncols = ncell * nrhs;
+  TcCombParams P{};
+  P.A = op.tiles;
+  P.B = c.tc_bbuf;
+  P.m_tiles = op.m_tiles;
+  P.kto = op.kto;
+  P.nops = op.nops;
+  P.nA = op.nA;
+  P.nX = op.nX;
+  P.M = op.M;
+  P.msplit = op.msplit;
+  P.ncols = ncols;
+  P.ncell = ncell;
+  P.coef0 = coef0;
+  P.coef1 = coef1;
+  P.Y = Y;
+  P.y_f64 = y_f64 ? 1 : 0;
+  P.y_rs = y_rs;
+  P.y_cs = y_cs;
+  P.alpha = alpha;
+  P.beta = beta;
+  P.err = c.tc_err;
+  const int bn = tc_comb_bn(ncols, op.m_tiles);
+  if (bn == 128) return comb_launch<128>(c, op, P, X, ncols, ncell);
+  if (bn == 64) return comb_launch<64>(c, op, P, X, ncols, ncell);
+  return comb_launch<32>(c, op, P, X, ncols, ncell);
+}
+
+// Reference for the combine self-check: Y[c][m] = sum_k coef_sel[c][k] sum_kk bf16(A_k[m][kk]) bf16(X[c][kk])
+__global__ void ref_comb_kernel(const double* A, const double* X, const double* coef0, const double* coef1,
+                                int M, int msplit, int K, int N, int nops, double* Y) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)M * N;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(t / M), m = (int)(t % M);
+    const double* cf = (m < msplit) ? coef0 : coef1;
+    double s = 0.0;
+    for (int k = 0; k < nops; ++k) {
+      double d = 0.0;
+      for (int kk = 0; kk < K; ++kk)
+        d += (double)__bfloat162float(__double2bfloat16(A[((long long)k * M + m) * K + kk])) *
+             (double)__bfloat162float(__double2bfloat16(X[(long long)c * K + kk]));
+      s += cf[(long long)c * nops + k] * d;
+    }
+    Y[t] = s;
+  }
+}
+
+fetidp_status tc_comb_selfcheck(Ctx& c, int M0, int M1, int K, int N, int nops, double* rel_err) {
+  const int M = M0 + M1;
+  double *A = nullptr, *X = nullptr, *C0 = nullptr, *C1 = nullptr, *Yt = nullptr, *Yr = nullptr;
+  FD_CUDA(cudaMalloc(&A, sizeof(double) * (size_t)nops * M * K));
+  FD_CUDA(cudaMalloc(&X, sizeof(double) * (size_t)N * K));
+  FD_CUDA(cudaMalloc(&C0, sizeof(double) * (size_t)N * nops));
+  FD_CUDA(cudaMalloc(&C1, sizeof(double) * (size_t)N * nops));
+  FD_CUDA(cudaMalloc(&Yt, sizeof(double) * (size_t)N * M));
+  FD_CUDA(cudaMalloc(&Yr, sizeof(double) * (size_t)N * M));
+  fill_random_kernel<<<gridn((long long)nops * M * K), 256, 0, c.stream>>>(A, (long long)nops * M * K, 11);
+  fill_random_kernel<<<gridn((long long)N * K), 256, 0, c.stream>>>(X, (long long)N * K, 12);
+  fill_random_kernel<<<gridn((long long)N * nops), 256, 0, c.stream>>>(C0, (long long)N * nops, 13);
+  fill_random_kernel<<<gridn((long long)N * nops), 256, 0, c.stream>>>(C1, (long long)N * nops, 14);
+  FD_CHECK_LAUNCH();
+  TcComb op;
+  // rows [0, M0) of each operator from the first M0 rows, rows [M0, M) from the rest (same array)
+  FD_TRY(tc_comb_pack(c, op, A, (long long)M * K, K, 0, 0, M0, A, (long long)M * K, K, M0, 0, M1, K, nops, 1));
+  c.tc_bbuf_bytes = tc_comb_staging_bytes(op, N);
+  FD_TRY(dalloc(c, reinterpret_cast<void**>(&c.tc_bbuf), c.tc_bbuf_bytes));
+  FD_TRY(tc_comb_apply(c, op, CCellVec{X, 0, K}, C0, C1, Yt, true, 0, M, 1.0, 0.0, 1, N));
+  ref_comb_kernel<<<gridn((long long)M * N), 256, 0, c.stream>>>(A, X, C0, C1, M, M0, K, N, nops, Yr);
+  FD_CHECK_LAUNCH();
+  std::vector<double> ht((size_t)N * M), hr((size_t)N * M);
+  FD_CUDA(cudaMemcpyAsync(ht.data(), Yt, sizeof(double) * ht.size(), cudaMemcpyDeviceToHost, c.stream));
+  FD_CUDA(cudaMemcpyAsync(hr.data(), Yr, sizeof(double) * hr.size(), cudaMemcpyDeviceToHost, c.stream));
+  int herr = 0;
+  FD_CUDA(cudaMemcpyAsync(&herr, c.tc_err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  FD_CUDA(cudaStreamSynchronize(c.stream));
+  cudaFree(A); cudaFree(X); cudaFree(C0); cudaFree(C1); cudaFree(Yt); cudaFree(Yr);
+  if (herr != 0) {
+    set_error("combine kernel wait timed out (code " + std::to_string(herr) + ")");
     return FETIDP_ETIMEOUT;
   }
   double mx = 0.0, ref = 0.0;

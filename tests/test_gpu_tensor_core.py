@@ -19,3 +19,17 @@ def test_tc_gemm_matches_fp64_on_bf16_inputs(M, K, N):
     assert torch.cuda.is_available()
     err = binding.tc_selfcheck(M, K, N)
     assert err < 1e-4, err
+
+
+@pytest.mark.parametrize("M0,M1,K,N,nops", [
+    (120, 8, 120, 4096, 32),    # F_dd stacked with (T_dr U_rp)^T, 32-wide tiles, 2 buffers x 16 ops
+    (56, 8, 56, 16, 2),         # tiny ragged case
+    (570, 0, 120, 4096, 8),     # U_rd: 5 row tiles, 128-wide column tiles
+    (120, 8, 570, 300, 5),      # long K resident in shared memory, ragged columns
+])
+def test_tc_combine_matches_fp64_on_bf16_inputs(M0, M1, K, N, nops):
+    import torch
+    from paper_2308_11371_gb300 import binding
+    assert torch.cuda.is_available()
+    err = binding.tc_comb_selfcheck(M0, M1, K, N, nops)
+    assert err < 1e-4, err
