@@ -252,6 +252,41 @@ fetidp_status fetidp_tc_selfcheck(int M, int K, int N, double *rel_err);
  * columns X; compared with FP64 on the same BF16-rounded inputs.  Diagnostic only.        */
 fetidp_status fetidp_tc_comb_selfcheck(int M0, int M1, int K, int N, int nops, double *rel_err);
 
+/* Size in bytes of the static device scratch behind fetidp_tc_selfcheck_static (4 MiB). */
+#define FETIDP_TC_STATIC_SCRATCH_BYTES 4194304
+
+/* Allocation-free variant of fetidp_tc_selfcheck.  The paper has no counterpart: this is a
+ * health probe of the tensor-core path for callers that must not allocate device memory.
+ *
+ * Who cannot allocate, and why: a process whose device memory is held by a caching allocator
+ * (PyTorch's, for one) can see a raw cudaMalloc fail while the cache still has room, and
+ * cudaFree waits for the whole device, so a probe that frees stalls every stream other host
+ * threads have queued work on.  A long-running solver or serving process that wants to check
+ * its tensor cores between jobs is such a caller.
+ *
+ * Computes exactly what fetidp_tc_selfcheck(M, K, N, rel_err) computes (same seeded inputs,
+ * same kernels; *rel_err = max |Y_tc - Y_ref| / max |Y_ref|), but every buffer (A, X, both
+ * outputs, packed tiles, staging, error flag, result slot) is carved from one fixed device array
+ * of FETIDP_TC_STATIC_SCRATCH_BYTES bytes inside this library.  No cudaMalloc / cudaFree or
+ * other allocating routine is called; the error flag and result slot are cleared on the stream
+ * at the start of each call, and every other buffer is fully written before it is read.
+ *
+ * M, K, N >= 1.  The scratch needed is about 8 (M K + N K + 2 N M) bytes plus the packed BF16
+ * tiles; a shape that does not fit returns FETIDP_EINVAL with the required and available
+ * byte counts in fetidp_last_error(), before any CUDA call.
+ * stream: a cudaStream_t, or NULL for the legacy default stream; the call returns after that
+ * stream has finished the probe.  rel_err: host pointer.
+ *
+ * Setup: the first call on each device looks the scratch address up with cudaGetSymbolAddress
+ * (this may load the library's device code on that device), with that device current, and keeps
+ * it; later calls reuse it.  Make the first call on a device before any stream capture begins.
+ *
+ * Concurrency: all callers on a device share the one scratch array.  Calls that overlap in time
+ * (from two host threads, or on two streams with no ordering between them) race on it and may
+ * return wrong results; the caller must serialise them.
+ * Errors: EINVAL (sizes, or scratch too small), ECUDA, ETIMEOUT (a bounded device wait expired). */
+fetidp_status fetidp_tc_selfcheck_static(int M, int K, int N, double *rel_err, void *stream);
+
 /* Number of kernels this library has launched in the calling process. */
 long long fetidp_kernel_launches(void);
 

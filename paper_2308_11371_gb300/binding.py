@@ -29,7 +29,7 @@ SYMBOLS = ["fetidp_sizes", "fetidp_default_options", "fetidp_setup", "fetidp_app
            "fetidp_apply_A", "fetidp_apply_P", "fetidp_rom_data", "fetidp_destroy",
            "fetidp_status_string", "fetidp_last_error", "fetidp_profile_enable",
            "fetidp_profile_read", "fetidp_kernel_launches", "fetidp_tc_selfcheck",
-           "fetidp_tc_comb_selfcheck"]
+           "fetidp_tc_comb_selfcheck", "fetidp_tc_selfcheck_static"]
 
 KCLASS = {"grouped_gemm": 0, "apply_K": 1, "maps": 2, "coarse": 3, "cell_gemv": 4, "vector": 5,
           "gram": 6, "tc_gemm": 7, "setup": 8}
@@ -127,6 +127,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.fetidp_tc_comb_selfcheck.argtypes = [I, I, I, I, I, ctypes.POINTER(ctypes.c_double)]
     lib.fetidp_tc_selfcheck.restype = I
     lib.fetidp_tc_selfcheck.argtypes = [I, I, I, ctypes.POINTER(ctypes.c_double)]
+    lib.fetidp_tc_selfcheck_static.restype = I
+    lib.fetidp_tc_selfcheck_static.argtypes = [I, I, I, ctypes.POINTER(ctypes.c_double), V]
     lib.fetidp_kernel_launches.restype = ctypes.c_longlong
     lib.fetidp_kernel_launches.argtypes = []
     _LIB = lib
@@ -335,4 +337,17 @@ def tc_comb_selfcheck(M0: int, M1: int, K: int, N: int, nops: int) -> float:
     """Max relative error of the fused combine kernel against FP64 on the same BF16 inputs."""
     err = ctypes.c_double()
     _check(load().fetidp_tc_comb_selfcheck(M0, M1, K, N, nops, ctypes.byref(err)))
+    return err.value
+
+
+# Size of the static device scratch of tc_selfcheck_static (FETIDP_TC_STATIC_SCRATCH_BYTES).
+TC_STATIC_SCRATCH_BYTES = 4194304
+
+
+def tc_selfcheck_static(M: int, K: int, N: int, stream: int = 0) -> float:
+    """tc_selfcheck without any device allocation: all buffers live in the library's fixed
+    4 MiB device scratch (shapes that do not fit raise EINVAL).  stream: raw cudaStream_t
+    handle, 0 for the legacy default stream.  Calls that overlap in time race on the scratch."""
+    err = ctypes.c_double()
+    _check(load().fetidp_tc_selfcheck_static(M, K, N, ctypes.byref(err), ctypes.c_void_p(stream or None)))
     return err.value

@@ -323,6 +323,8 @@ fetidp_status tc_apply(Ctx& c, const TcOperator& op, CCellVec X, const double* c
                        bool y_f64, long long y_rs, int y_cs, long long y_b_stride, double alpha,
                        double beta, int nrhs, long long ncell, long long y_ext = -1);
 fetidp_status tc_selfcheck(Ctx& c, int M, int K, int N, double* rel_err);
+fetidp_status tc_selfcheck_static(Ctx& c, int M, int K, int N, double* rel_err);
+size_t tc_selfcheck_static_bytes(int M, int K, int N);
 void tc_free_operator(Ctx& c, TcOperator& op);
 int tc_comb_bn(long long ncols, int m_tiles);
 bool tc_comb_fits(int K, int split, long long ncols, int m_tiles);

@@ -593,6 +593,23 @@ fetidp_status fetidp_tc_selfcheck(int M, int K, int N, double* rel_err) {
   return st;
 }
 
+fetidp_status fetidp_tc_selfcheck_static(int M, int K, int N, double* rel_err, void* stream) {
+  if (M < 1 || K < 1 || N < 1 || !rel_err) { set_error("bad self-check sizes"); return FETIDP_EINVAL; }
+  // the size check needs no device: an oversized request fails before any CUDA call
+  const size_t need = tc_selfcheck_static_bytes(M, K, N);
+  if (need > (size_t)FETIDP_TC_STATIC_SCRATCH_BYTES) {
+    set_error("tensor-core probe M=" + std::to_string(M) + " K=" + std::to_string(K) + " N=" +
+              std::to_string(N) + " needs " + std::to_string(need) + " bytes of scratch; the static scratch holds " +
+              std::to_string((size_t)FETIDP_TC_STATIC_SCRATCH_BYTES) + " (fetidp_tc_selfcheck takes any size)");
+    return FETIDP_EINVAL;
+  }
+  fetidp_ctx tmp;
+  Ctx& c = tmp.c;
+  FD_CUDA(cudaGetDevice(&c.device));
+  c.stream = static_cast<cudaStream_t>(stream);
+  return tc_selfcheck_static(c, M, K, N, rel_err);
+}
+
 fetidp_status fetidp_profile_enable(fetidp_ctx* ctx, unsigned mask) {
   FD_TRY(enter(ctx));
   Prof& P = ctx->c.prof;

@@ -21,6 +21,7 @@
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -1057,6 +1058,158 @@ fetidp_status tc_comb_selfcheck(Ctx& c, int M0, int M1, int K, int N, int nops, 
     ref = std::max(ref, std::fabs(hr[i]));
   }
   *rel_err = mx / (ref > 0 ? ref : 1.0);
+  return FETIDP_OK;
+}
+
+// ---------------------------------------------------------------- allocation-free self-check
+// Scratch of fetidp_tc_selfcheck_static: a fixed array in this library's device image, so the
+// probe calls no cudaMalloc / cudaFree.  Its address is looked up once per device.
+static __device__ __align__(256) unsigned char g_tc_static_scratch[FETIDP_TC_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+struct TcCheckSlot {   // results of one probe, written on the device
+  double diff;         // max |Y_tc - Y_ref| (+inf if Y_tc holds a non-finite value)
+  double ref;          // max |Y_ref|
+  int err;             // tensor-core wait / bounds status: must be zero before the GEMM runs
+  int pad;
+};
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_addr[kStaticMaxDevices] = {};
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Byte offsets of the probe's buffers inside the static scratch.
+struct StaticLayout {
+  size_t A, X, Yt, Yr, tiles, bbuf, slot, total;
+  size_t bbuf_bytes;
+  int m_tiles, k_tiles, bn;
+};
+
+StaticLayout static_layout(int M, int K, int N) {
+  StaticLayout L{};
+  L.m_tiles = (M + TC_BM - 1) / TC_BM;
+  L.k_tiles = (K + TC_BK - 1) / TC_BK;
+  L.bn = tc_bn_for(N, L.m_tiles, 1);
+  const size_t n_tiles = ((size_t)N + L.bn - 1) / L.bn;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t o = off; off += round256(bytes); return o; };
+  L.A = take((size_t)M * K * sizeof(double));
+  L.X = take((size_t)N * K * sizeof(double));
+  L.Yt = take((size_t)N * M * sizeof(double));
+  L.Yr = take((size_t)N * M * sizeof(double));
+  L.tiles = take((size_t)L.m_tiles * L.k_tiles * A_TILE);
+  L.bbuf_bytes = n_tiles * L.k_tiles * L.bn * TC_BK * 2;
+  L.bbuf = take(L.bbuf_bytes);
+  L.slot = take(sizeof(TcCheckSlot));
+  L.total = off;
+  return L;
+}
+
+__device__ __forceinline__ void absmax_warp(double& d, double& r) {
+  for (int o = 16; o > 0; o >>= 1) {
+    d = fmax(d, __shfl_xor_sync(0xffffffffu, d, o));
+    r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+  }
+}
+
+// One block: max |a - b| and max |b|.  A maximum is exact in any order, so the result is
+// deterministic; a non-finite difference turns into +inf, which no later fmax undoes.
+__global__ void __launch_bounds__(1024) absmax_pair_kernel(const double* a, const double* b, long long n,
+                                                         TcCheckSlot* out) {
+  __shared__ double sd[32], sr[32];
+  double d = 0.0, r = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    const double v = fabs(a[i] - b[i]);
+    d = isfinite(v) ? fmax(d, v) : INFINITY;
+    r = fmax(r, fabs(b[i]));
+  }
+  absmax_warp(d, r);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { sd[w] = d; sr[w] = r; }
+  __syncthreads();
+  if (w == 0) {
+    const int nw = (int)(blockDim.x >> 5);
+    d = l < nw ? sd[l] : 0.0;
+    r = l < nw ? sr[l] : 0.0;
+    absmax_warp(d, r);
+    if (l == 0) { out->diff = d; out->ref = r; }
+  }
+}
+
+}  // namespace
+
+size_t tc_selfcheck_static_bytes(int M, int K, int N) { return static_layout(M, K, N).total; }
+
+// Address of the static scratch on the current device; the first call on a device looks it up.
+fetidp_status tc_static_scratch(uint8_t** p) {
+  int dev = 0;
+  FD_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kStaticMaxDevices) {
+    set_error("device ordinal beyond the static-scratch table");
+    return FETIDP_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* a = nullptr;
+    FD_CUDA(cudaGetSymbolAddress(&a, g_tc_static_scratch));
+    g_static_addr[dev] = a;
+  }
+  *p = static_cast<uint8_t*>(g_static_addr[dev]);
+  return FETIDP_OK;
+}
+
+// The probe of tc_selfcheck (same seeds, same kernels) with every buffer carved from the static
+// scratch.  The caller has checked tc_selfcheck_static_bytes against the scratch size.
+fetidp_status tc_selfcheck_static(Ctx& c, int M, int K, int N, double* rel_err) {
+  const StaticLayout L = static_layout(M, K, N);
+  if (L.total > (size_t)FETIDP_TC_STATIC_SCRATCH_BYTES) {
+    set_error("tensor-core probe does not fit the static scratch");
+    return FETIDP_EINVAL;
+  }
+  uint8_t* base = nullptr;
+  FD_TRY(tc_static_scratch(&base));
+  double* A = reinterpret_cast<double*>(base + L.A);
+  double* X = reinterpret_cast<double*>(base + L.X);
+  double* Yt = reinterpret_cast<double*>(base + L.Yt);
+  double* Yr = reinterpret_cast<double*>(base + L.Yr);
+  TcCheckSlot* slot = reinterpret_cast<TcCheckSlot*>(base + L.slot);
+  FD_CUDA(cudaMemsetAsync(slot, 0, sizeof(TcCheckSlot), c.stream));
+  c.tc_err = &slot->err;
+  c.tc_bbuf = base + L.bbuf;
+  c.tc_bbuf_bytes = L.bbuf_bytes;
+  fill_random_kernel<<<gridn((long long)M * K), 256, 0, c.stream>>>(A, (long long)M * K, 1234);
+  fill_random_kernel<<<gridn((long long)N * K), 256, 0, c.stream>>>(X, (long long)N * K, 5678);
+  FD_CHECK_LAUNCH();
+  TcOperator op;
+  op.M = M;
+  op.K = K;
+  op.nops = 1;
+  op.nterm = 1;
+  op.separate = false;
+  op.m_tiles = L.m_tiles;
+  op.k_tiles_op = L.k_tiles;
+  op.k_tiles = L.k_tiles;
+  op.batch_bytes = (long long)L.m_tiles * L.k_tiles * A_TILE;
+  op.tiles = base + L.tiles;
+  pack_A_kernel<<<gridn((long long)L.m_tiles * L.k_tiles * TC_BM * 8), 256, 0, c.stream>>>(
+      A, 0, K, 0, 0, M, K, 1, 1, L.k_tiles, L.m_tiles, 1, op.tiles);
+  FD_CHECK_LAUNCH();
+  FD_TRY(tc_apply(c, op, CCellVec{X, 0, K}, nullptr, Yt, true, 0, M, 0, 1.0, 0.0, 1, N));
+  ref_gemm_kernel<<<gridn((long long)M * N), 256, 0, c.stream>>>(A, X, M, K, N, Yr);
+  FD_CHECK_LAUNCH();
+  absmax_pair_kernel<<<1, 1024, 0, c.stream>>>(Yt, Yr, (long long)M * N, slot);
+  FD_CHECK_LAUNCH();
+  TcCheckSlot h{};
+  FD_CUDA(cudaMemcpyAsync(&h, slot, sizeof(h), cudaMemcpyDeviceToHost, c.stream));
+  FD_CUDA(cudaStreamSynchronize(c.stream));
+  if (h.err != 0) {
+    set_error("tensor-core GEMM wait timed out or left its bounds (code " + std::to_string(h.err) + ")");
+    return FETIDP_ETIMEOUT;
+  }
+  *rel_err = h.diff / (h.ref > 0 ? h.ref : 1.0);
   return FETIDP_OK;
 }
 
