@@ -327,7 +327,7 @@ fetidp_status tc_selfcheck_static(Ctx& c, int M, int K, int N, double* rel_err);
 size_t tc_selfcheck_static_bytes(int M, int K, int N);
 void tc_free_operator(Ctx& c, TcOperator& op);
 int tc_comb_bn(long long ncols, int m_tiles);
-bool tc_comb_fits(int K, int split, long long ncols, int m_tiles);
+bool tc_comb_fits(int K, int split, long long ncols, int m_tiles, int nops, bool two_sets);
 fetidp_status tc_comb_pack(Ctx& c, TcComb& op, const double* src0, long long st0, int lda0, int r00, int c00,
                            int M0, const double* src1, long long st1, int lda1, int r01, int c01, int M1,
                            int K, int nops, int split);

@@ -170,6 +170,181 @@ __global__ void apply_K_kernel(int e, long long ncell, int n, int len, const int
   }
 }
 
+// Index of entry (I, J) of a symmetric d^2 x d^2 matrix kept as its upper triangle, row-major.
+__device__ __forceinline__ int sym_index(int I, int J, int NI) {
+  if (I > J) { const int t = I; I = J; J = t; }
+  return I * NI - I * (I - 1) / 2 + (J - I);
+}
+
+// Multi-vector K_s application in FP32 (the Eq. 46b products K_s R of the mixed path).  One
+// block per (rhs, cell); for each colour group (elements that share no node) the Gauss-point
+// C_hat of its elements is staged in shared memory (coalesced), every element matrix
+// K_e = sum_gp w B^T C_hat B is formed once (one thread per element row) and applied to all
+// vectors of the chunk, one thread per (element, vector).  Vectors are stored dof-major with a
+// padded stride, so the threads of an element read consecutive words and every K_e entry is a
+// broadcast.  Global vectors are read and written in local order through the staged
+// permutation, so no load depends on another.
+constexpr int kMultiThreads = 512;
+// padded strides (in floats) of the staged element data: odd / 4-mod-32 so that the threads of
+// neighbouring elements hit different banks; K_e rows stay 16-byte aligned
+__host__ __device__ constexpr int multi_ke_stride(int D) { return (D == 2 ? 64 : 576) + 4; }
+__host__ __device__ constexpr int multi_c_stride(int D) { return (D == 2 ? 4 * 16 : 8 * 81) + 1; }
+template <int D>
+__global__ void __launch_bounds__(kMultiThreads) apply_K_multi_kernel(
+    int e, long long ncell, int n, int len, const int* __restrict__ perm, bool idp,
+    const float* __restrict__ u, long long u_rs, int u_cs, float* __restrict__ y, long long y_rs, int y_cs,
+    int nvec, int VB, const double* __restrict__ chat, int nc, float wq, float inv_h, int nelc_max,
+    long long u_ext, long long y_ext) {
+  constexpr int NA = 1 << D;
+  constexpr int ND = NA * D;
+  constexpr int NI = D * D;
+  constexpr int KES = multi_ke_stride(D);
+  constexpr int CS = multi_c_stride(D);
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int VBp = VB + 1;
+  float* us = reinterpret_cast<float*>(sm_raw);        // [n][VBp]
+  float* ys = us + (size_t)n * VBp;                     // [n][VBp]
+  float* Ke = ys + (size_t)n * VBp;                     // [nelc_max][KES], rows of ND
+  Ke = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(Ke) + 15) & ~uintptr_t(15));
+  float* Cs = Ke + (size_t)nelc_max * KES;              // [nelc_max][CS]: per gp the full NI x NI C_hat
+  float* dNs = Cs + (size_t)nelc_max * CS;              // [NA gp][NA][D] shape-function gradients
+  int* perm_s = reinterpret_cast<int*>(dNs + NA * NA * D);   // [n] local -> natural
+  const long long col = blockIdx.x;
+  const int rhs = (int)(col / ncell);
+  const long long cell = col - (long long)rhs * ncell;
+  const float* uc = u + rhs * u_rs + cell * u_cs;
+  float* yc = y + rhs * y_rs + cell * y_cs;
+  const int nel = e * e * (D == 3 ? e : 1);
+  const int cpe = NA * nc;                              // C_hat values per element (upper triangles)
+  const double* chat_cell = chat + cell * (long long)cpe * nel;
+  const int ecount[3] = {e, e, D == 3 ? e : 1};
+  for (int li = threadIdx.x; li < n; li += blockDim.x) perm_s[li] = idp ? perm[li] : li;
+  for (int t = threadIdx.x; t < NA * NA * D; t += blockDim.x) {
+    const int gp = t / (NA * D), B = (t / D) % NA, a = t % D;
+    float v = inv_h;
+    for (int k = 0; k < D; ++k) {
+      const int off = (B >> k) & 1;
+      const float tk = (float)gauss_t((gp >> k) & 1);
+      if (k == a) v *= off ? 1.f : -1.f;
+      else v *= off ? tk : 1.f - tk;
+    }
+    dNs[t] = v;
+  }
+  __syncthreads();
+  for (int v0 = 0; v0 < nvec; v0 += VB) {
+    const int vb = min(VB, nvec - v0);
+#pragma unroll 4
+    for (int t = threadIdx.x; t < vb * len; t += blockDim.x) {
+      const int v = t / len, li = t - v * len;
+      float val = 0.f;
+      if (FD_INB(rhs * u_rs + cell * u_cs + (long long)(v0 + v) * len + li, u_ext, 203))
+        val = uc[(size_t)(v0 + v) * len + li];
+      us[(size_t)perm_s[li] * VBp + v] = val;
+    }
+    for (int t = threadIdx.x; t < vb * (n - len); t += blockDim.x) {   // dofs outside the vector
+      const int v = t / (n - len), r = t - v * (n - len);
+      us[(size_t)perm_s[len + r] * VBp + v] = 0.f;
+    }
+    for (int t = threadIdx.x; t < n * VBp; t += blockDim.x) ys[t] = 0.f;
+    for (int color = 0; color < NA; ++color) {
+      int cnt[3], par[3];
+      int nelc = 1;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        par[k] = (k < D) ? ((color >> k) & 1) : 0;
+        cnt[k] = (k < D) ? (ecount[k] - par[k] + 1) / 2 : 1;
+        nelc *= cnt[k];
+      }
+      __syncthreads();   // previous colour's K_e and C_hat no longer read
+      // C_hat of the colour's elements, unpacked to the full symmetric NI x NI matrix per gp
+      for (int t = threadIdx.x; t < nelc * NA * NI * NI; t += blockDim.x) {
+        const int q = t / (NA * NI * NI), r = t - q * (NA * NI * NI);
+        const int gp = r / (NI * NI), I = (r / NI) % NI, J = r % NI;
+        const int qx = q % cnt[0], qy = (q / cnt[0]) % cnt[1], qz = q / (cnt[0] * cnt[1]);
+        const int el = (par[0] + 2 * qx) + e * ((par[1] + 2 * qy) + e * (par[2] + 2 * qz));
+        Cs[(size_t)q * CS + r] = (float)chat_cell[(size_t)el * cpe + gp * nc + sym_index(I, J, NI)];
+      }
+      __syncthreads();
+      // element matrices of this colour, one row (A, i) per thread
+      for (int t = threadIdx.x; t < nelc * ND; t += blockDim.x) {
+        const int q = t / ND, row = t - q * ND;
+        const int A = row / D, i = row - A * D;
+        const float* Cq = Cs + (size_t)q * CS;
+        float krow[ND];
+#pragma unroll
+        for (int k = 0; k < ND; ++k) krow[k] = 0.f;
+        for (int gp = 0; gp < NA; ++gp) {
+          const float* dn = dNs + gp * NA * D;
+          const float* Cg = Cq + gp * NI * NI + i * D * NI;   // rows (i, a)
+          float w[D][D];   // w[j][b] = sum_a dN_A[a] C[(i,a),(j,b)]
+#pragma unroll
+          for (int j = 0; j < D; ++j)
+#pragma unroll
+            for (int b = 0; b < D; ++b) {
+              float sacc = 0.f;
+#pragma unroll
+              for (int a = 0; a < D; ++a) sacc += dn[A * D + a] * Cg[a * NI + j * D + b];
+              w[j][b] = sacc;
+            }
+#pragma unroll
+          for (int B = 0; B < NA; ++B)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+              float sacc = 0.f;
+#pragma unroll
+              for (int b = 0; b < D; ++b) sacc += w[j][b] * dn[B * D + b];
+              krow[B * D + j] += wq * sacc;
+            }
+        }
+        float* kr = Ke + (size_t)q * KES + row * ND;
+#pragma unroll
+        for (int k = 0; k < ND; k += 4)
+          *reinterpret_cast<float4*>(kr + k) = make_float4(krow[k], krow[k + 1], krow[k + 2], krow[k + 3]);
+      }
+      __syncthreads();
+      // apply to every vector of the chunk
+      for (int t = threadIdx.x; t < nelc * vb; t += blockDim.x) {
+        const int q = t / vb, v = t - q * vb;
+        const int qx = q % cnt[0], qy = (q / cnt[0]) % cnt[1], qz = q / (cnt[0] * cnt[1]);
+        const int ex = par[0] + 2 * qx, ey = par[1] + 2 * qy, ez = par[2] + 2 * qz;
+        int dof0[NA];
+#pragma unroll
+        for (int B = 0; B < NA; ++B) {
+          const int bx = B & 1, by = (B >> 1) & 1, bz = (B >> 2) & 1;
+          dof0[B] = D * ((ex + bx) + (e + 1) * ((ey + by) + (e + 1) * (D == 3 ? (ez + bz) : 0)));
+        }
+        float ue[ND];
+#pragma unroll
+        for (int B = 0; B < NA; ++B)
+#pragma unroll
+          for (int j = 0; j < D; ++j) ue[B * D + j] = us[(size_t)(dof0[B] + j) * VBp + v];
+        const float* kq = Ke + (size_t)q * KES;
+#pragma unroll
+        for (int A = 0; A < NA; ++A)
+#pragma unroll
+          for (int i = 0; i < D; ++i) {
+            const float* kr = kq + (A * D + i) * ND;
+            float sacc = 0.f;
+#pragma unroll
+            for (int k = 0; k < ND; k += 4) {
+              const float4 k4 = *reinterpret_cast<const float4*>(kr + k);
+              sacc += k4.x * ue[k] + k4.y * ue[k + 1] + k4.z * ue[k + 2] + k4.w * ue[k + 3];
+            }
+            ys[(size_t)(dof0[A] + i) * VBp + v] += sacc;
+          }
+      }
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int t = threadIdx.x; t < vb * len; t += blockDim.x) {
+      const int v = t / len, li = t - v * len;
+      if (FD_INB(rhs * y_rs + cell * y_cs + (long long)(v0 + v) * len + li, y_ext, 204))
+        yc[(size_t)(v0 + v) * len + li] = ys[(size_t)perm_s[li] * VBp + v];
+    }
+    __syncthreads();
+  }
+}
+
 // Per-cell dense operators: y[rhs,cell] = alpha M_cell x[rhs,cell] + beta y, M_cell at
 // mats + cell*mstride with row stride ld (sub-blocks of the per-cell ROM operators).
 constexpr int kMaxRhsGemv = 8;
@@ -201,6 +376,41 @@ __global__ void cell_gemv_kernel(const double* __restrict__ mats, long long mstr
         if (lane == 0) {
           double* dst = y + (r0 + r) * y_rs + cell * y_cs + row;
           *dst = (beta == 0.0) ? alpha * s : alpha * s + beta * (*dst);
+        }
+      }
+    }
+  }
+}
+
+// Narrow per-cell operators (at most 32 columns, e.g. the n_r x n_p prolongations): one thread
+// per (cell, row), so consecutive threads read consecutive rows; x entries are shared by the
+// threads of a cell (cache broadcast).
+__global__ void cell_gemv_narrow_kernel(const double* __restrict__ mats, long long mstride, int ld,
+                                        int mrows, int mcols, const double* __restrict__ x, long long x_rs,
+                                        int x_cs, double* __restrict__ y, long long y_rs, int y_cs,
+                                        double alpha, double beta, int nrhs, long long ncell) {
+  const long long total = ncell * mrows;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long cell = t / mrows;
+    const int row = (int)(t - cell * mrows);
+    const double* Mr = mats + cell * mstride + (long long)row * ld;
+    for (int r0 = 0; r0 < nrhs; r0 += kMaxRhsGemv) {
+      const int rb = min(kMaxRhsGemv, nrhs - r0);
+      double acc[kMaxRhsGemv];
+#pragma unroll
+      for (int r = 0; r < kMaxRhsGemv; ++r) acc[r] = 0.0;
+      for (int q = 0; q < mcols; ++q) {
+        const double mv = Mr[q];
+#pragma unroll
+        for (int r = 0; r < kMaxRhsGemv; ++r)
+          if (r < rb) acc[r] += mv * x[(r0 + r) * x_rs + cell * x_cs + q];
+      }
+#pragma unroll
+      for (int r = 0; r < kMaxRhsGemv; ++r) {
+        if (r < rb) {
+          double* dst = y + (r0 + r) * y_rs + cell * y_cs + row;
+          *dst = (beta == 0.0) ? alpha * acc[r] : alpha * acc[r] + beta * (*dst);
         }
       }
     }
@@ -292,17 +502,54 @@ __global__ void __launch_bounds__(256) grouped_gemm_kernel(
   }
 }
 
-// Eq. 46b for one (rhs, cell) per warp: G = R^T (K R) and h = R^T v by lane-strided dot
-// products with a shuffle reduction, then lane 0 runs the diagonal-pivoted Cholesky and the
-// triangular solves on the warp's shared-memory scratch, and the warp forms x = R c.  Pivots
-// below drop_rel * max diag(G) are dropped (coefficient 0).
-// Scratch per warp (doubles): G, S, L (nrb x nrb each), h, y, c, pivot column (nrb each),
-// nrb ints (pivot order), 2 scalars (current pivot, its Schur diagonal), then two staging
-// tiles of R and K R (nrb x 32 values of the basis type each, counted in doubles).
+// Eq. 46b for one (rhs, cell) per warp.
+//  1. G = R^T (K R) and h = R^T v.  G is formed in 32 x 32 blocks (upper blocks only, then
+//     mirrored): lane r owns row r of the block.  Chunks of 32 entries of the basis vectors are
+//     staged in shared memory, the R rows with a padded stride (each lane reads its own row,
+//     conflict-free) and the K R chunk transposed with 16-byte rows (all lanes read the same
+//     address: broadcast, four values per load).  Products in the basis type, chunk sums in FP64.
+//  2. Diagonal-pivoted Cholesky, right-looking: each step takes the largest remaining Schur
+//     diagonal (lowest index on ties), stops when it is not above drop_rel * max diag(G), stores
+//     the scaled pivot column as the next column of L and applies the rank-1 update (lanes own
+//     matrix columns, so the row-major updates are conflict-free).
+//  3. L y = h(piv), L^T c(piv) = y (column-oriented, lane-parallel), c = 0 off the pivots,
+//     and x = R c.
+// Scratch per warp (doubles): S and L (nrb x (nrb + 1) each), h, y, c, pivot column (nrb
+// each), nrb pivot ints (in nrb doubles), 2 scalars, the v chunk (32), then the two staging
+// tiles (32 x 33 and 32 x 36 values of the basis type), padded to an even count.
 constexpr int kMaxRb = 64;
-constexpr int kGramChunk = 32;
+constexpr int kGramQ = 32;     // basis-vector entries per staged chunk
+constexpr int kGramRld = 33;   // row stride of the staged R rows
+constexpr int kGramKld = 36;   // row stride of the staged, transposed K R chunk (16-byte rows)
 __host__ __device__ inline int gram_warp_doubles(int nrb, int tb_bytes) {
-  return 3 * nrb * nrb + 5 * nrb + 2 + (2 * nrb * kGramChunk * tb_bytes + 7) / 8;
+  const int ld = nrb + 1;
+  const int fixed = 2 * nrb * ld + 5 * nrb + 2 + kGramQ;
+  const int head = fixed + (fixed & 1);   // the staging tiles start 16-byte aligned
+  const int tiles = (kGramQ * (kGramRld + kGramKld) * tb_bytes + 7) / 8;
+  const int tot = head + tiles;
+  return tot + (tot & 1);
+}
+
+__device__ __forceinline__ void load4(const float* p, float (&o)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&o)[4]) {
+  const double2 t0 = *reinterpret_cast<const double2*>(p);
+  const double2 t1 = *reinterpret_cast<const double2*>(p + 2);
+  o[0] = t0.x; o[1] = t0.y; o[2] = t1.x; o[3] = t1.y;
+}
+
+// s + c += x with Neumaier's compensation (c collects the rounding error of every addition)
+template <typename T>
+__device__ __forceinline__ void neumaier_add(T& s, T& c, T x) {
+  if (sizeof(T) == 8) {   // FP64 sums need no compensation at these lengths
+    s += x;
+    return;
+  }
+  const T t = s + x;
+  c += (fabs(s) >= fabs(x)) ? ((s - t) + x) : ((x - t) + s);
+  s = t;
 }
 
 template <typename TB>
@@ -314,122 +561,148 @@ __global__ void gram_warp_kernel(const TB* __restrict__ R, const TB* __restrict_
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long col = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
   if (col >= ncell * nrhs) return;                  // the whole warp leaves together
-  const int nb2 = nrb * nrb;
-  double* G = gwsm + (size_t)wib * gram_warp_doubles(nrb, (int)sizeof(TB));
-  double* S = G + nb2;
-  double* Lm = S + nb2;
-  double* hs = Lm + nb2;
+  const int ld = nrb + 1;
+  double* S = gwsm + (size_t)wib * gram_warp_doubles(nrb, (int)sizeof(TB));
+  double* Lc = S + nrb * ld;                        // column a of L at Lc[a * ld + i]
+  double* hs = Lc + nrb * ld;
   double* ys = hs + nrb;
   double* cs = ys + nrb;
   double* colv = cs + nrb;
-  int* piv = reinterpret_cast<int*>(colv + nrb);    // nrb ints in the next nrb doubles
-  double* sc = colv + 2 * nrb;                      // [0] pivot index, [1] its Schur diagonal
-  TB* Rt = reinterpret_cast<TB*>(sc + 2);           // nrb x kGramChunk
-  TB* Kt = Rt + nrb * kGramChunk;                   // nrb x kGramChunk
+  int* piv = reinterpret_cast<int*>(colv + nrb);
+  double* sc = colv + 2 * nrb;
+  double* vq = sc + 2;
+  const int fixed = 2 * nrb * ld + 5 * nrb + 2 + kGramQ;
+  TB* Rt = reinterpret_cast<TB*>(S + fixed + (fixed & 1));   // [32][kGramRld]
+  TB* Kt = Rt + kGramQ * kGramRld;                            // [32 q][kGramKld]
   const int rhs = (int)(col / ncell);
   const long long cell = col - (long long)rhs * ncell;
   const TB* Rc = R + col * (long long)nrb * nr;
   const TB* KRc = KR + col * (long long)nrb * nr;
   const double* vc = v + rhs * v_rs + cell * v_cs;
-  // G (upper triangle, row-major pair index p) and h: each lane owns pairs p = lane + 32 t and
-  // h[lane + 32 t]; chunks of 32 entries of every basis vector are staged in shared memory
-  // (coalesced loads), products in the basis type, chunk sums accumulated in FP64.
-  const int npair = nrb * (nrb + 1) / 2;
-  for (int p = lane; p < npair; p += 32) {
-    int i = 0, rem = p;
-    while (rem >= nrb - i) { rem -= nrb - i; ++i; }
-    G[i * nrb + i + rem] = 0.0;
-  }
-  for (int i = lane; i < nrb; i += 32) hs[i] = 0.0;
-  for (int q0 = 0; q0 < nr; q0 += kGramChunk) {
-    const int qn = min(kGramChunk, nr - q0);
-    __syncwarp();
-    for (int i = 0; i < nrb; ++i) {
-      Rt[i * kGramChunk + lane] = lane < qn ? Rc[(size_t)i * nr + q0 + lane] : TB(0);
-      Kt[i * kGramChunk + lane] = lane < qn ? KRc[(size_t)i * nr + q0 + lane] : TB(0);
-    }
-    const double vq = lane < qn ? vc[q0 + lane] : 0.0;
-    __syncwarp();
-    for (int p = lane; p < npair; p += 32) {
-      int i = 0, rem = p;
-      while (rem >= nrb - i) { rem -= nrb - i; ++i; }
-      const int j = i + rem;
-      TB acc = TB(0);
-      for (int q = 0; q < kGramChunk; ++q) acc += Rt[i * kGramChunk + q] * Kt[j * kGramChunk + q];
-      G[i * nrb + j] += (double)acc;
-    }
-    for (int i = 0; i < nrb; ++i) {          // h_i += sum_q R_iq v_q (warp reduction)
-      double s = (double)Rt[i * kGramChunk + lane] * vq;
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-      if (lane == 0) hs[i] += s;
+
+  // ---- 1. G (upper blocks) and h
+  for (int ib = 0; ib < nrb; ib += 32) {
+    const int ni = min(32, nrb - ib);
+    for (int jb = ib; jb < nrb; jb += 32) {
+      const int nj = min(32, nrb - jb);
+      const bool diag = (jb == ib);
+      // chunk sums in the basis type, accumulated over chunks with Neumaier compensation (as
+      // accurate as FP64 chunk sums, with no FP64 pipe work in the FP32 path)
+      TB gacc[32], gcmp[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) { gacc[j] = TB(0); gcmp[j] = TB(0); }
+      TB hacc = TB(0), hcmp = TB(0);
+      for (int q0 = 0; q0 < nr; q0 += kGramQ) {
+        const int qn = min(kGramQ, nr - q0);
+        __syncwarp();
+        for (int r = 0; r < ni; ++r)
+          Rt[r * kGramRld + lane] = lane < qn ? Rc[(size_t)(ib + r) * nr + q0 + lane] : TB(0);
+        for (int r = 0; r < 32; ++r)
+          Kt[lane * kGramKld + r] = (lane < qn && r < nj) ? KRc[(size_t)(jb + r) * nr + q0 + lane] : TB(0);
+        if (diag) vq[lane] = lane < qn ? vc[q0 + lane] : 0.0;
+        __syncwarp();
+        if (lane < ni) {
+          TB acc[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) acc[j] = TB(0);
+#pragma unroll 2
+          for (int q = 0; q < kGramQ; ++q) {
+            const TB rq = Rt[lane * kGramRld + q];
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+              TB k4[4];
+              load4(Kt + q * kGramKld + j, k4);
+              acc[j] += rq * k4[0];
+              acc[j + 1] += rq * k4[1];
+              acc[j + 2] += rq * k4[2];
+              acc[j + 3] += rq * k4[3];
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) neumaier_add(gacc[j], gcmp[j], acc[j]);
+          if (diag) {
+            TB hsum = TB(0);
+            for (int q = 0; q < kGramQ; ++q) hsum += Rt[lane * kGramRld + q] * (TB)vq[q];
+            neumaier_add(hacc, hcmp, hsum);
+          }
+        }
+      }
+      if (lane < ni) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (j < nj && (!diag || j >= lane)) S[(ib + lane) * ld + jb + j] = (double)gacc[j] + (double)gcmp[j];
+        if (diag) hs[ib + lane] = (double)hacc + (double)hcmp;
+      }
     }
   }
   __syncwarp();
-  for (int p = lane; p < npair; p += 32) {    // mirror the upper triangle
-    int i = 0, rem = p;
-    while (rem >= nrb - i) { rem -= nrb - i; ++i; }
-    G[(i + rem) * nrb + i] = G[i * nrb + i + rem];
+  for (int t = lane; t < nrb * nrb; t += 32) {      // mirror the upper triangle
+    const int i = t / nrb, j = t - (t / nrb) * nrb;
+    if (i > j) S[i * ld + j] = S[j * ld + i];
   }
   __syncwarp();
-  for (int t = lane; t < nb2; t += 32) S[t] = G[t];
+
+  // ---- 2. pivoted Cholesky
   double dmax = 0.0;
-  for (int i = 0; i < nrb; ++i) dmax = fmax(dmax, G[i * nrb + i]);
+  for (int i = 0; i < nrb; ++i) dmax = fmax(dmax, S[i * ld + i]);
   unsigned long long used = 0ull;                   // identical in every lane
   int np = 0;
-  __syncwarp();
   while (np < nrb) {
-    if (lane == 0) {
-      // largest remaining Schur diagonal, lowest index on ties
-      int jb = -1;
-      double best = 0.0;
-      for (int i = 0; i < nrb; ++i) {
-        if ((used >> i) & 1ull) continue;
-        const double dv = S[i * nrb + i];
-        if (jb < 0 || dv > best) { best = dv; jb = i; }
-      }
-      sc[0] = (double)jb;
-      sc[1] = best;
+    // largest remaining Schur diagonal, lowest index on ties (lane-parallel, then a warp argmax)
+    int jb = -1;
+    double best = 0.0;
+    for (int i = lane; i < nrb; i += 32) {
+      if ((used >> i) & 1ull) continue;
+      const double dv = S[i * ld + i];
+      if (jb < 0 || dv > best) { best = dv; jb = i; }
     }
-    __syncwarp();
-    const int jb = (int)sc[0];
-    const double best = sc[1];
-    if (jb < 0 || jb >= nrb || !(best > drop_rel * dmax)) break;   // uniform across the warp
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oj = __shfl_xor_sync(0xffffffffu, jb, o);
+      if (oj >= 0 && (jb < 0 || ob > best || (ob == best && oj < jb))) { best = ob; jb = oj; }
+    }
+    if (jb < 0 || !(best > drop_rel * dmax)) break;   // uniform across the warp
     used |= 1ull << jb;
     if (lane == 0) piv[np] = jb;
-    ++np;
     const double inv = 1.0 / sqrt(best);
-    for (int i = lane; i < nrb; i += 32) colv[i] = S[i * nrb + jb] * inv;
+    for (int i = lane; i < nrb; i += 32) {
+      const double cv = S[i * ld + jb] * inv;
+      colv[i] = cv;
+      Lc[np * ld + i] = cv;
+    }
     __syncwarp();
-    for (int i = lane; i < nrb; i += 32)             // each lane owns rows i
-      for (int j = 0; j < nrb; ++j) S[i * nrb + j] -= colv[i] * colv[j];
+    for (int i = 0; i < nrb; ++i) {                    // lanes own columns j
+      const double ci = colv[i];
+      for (int j = lane; j < nrb; j += 32) S[i * ld + j] -= ci * colv[j];
+    }
+    ++np;
     __syncwarp();
   }
-  if (lane == 0) {
-    // Cholesky of G restricted to the pivots (pivot order)
-    for (int a = 0; a < np; ++a)
-      for (int b = 0; b <= a; ++b) {
-        double s = G[piv[a] * nrb + piv[b]];
-        for (int k = 0; k < b; ++k) s -= Lm[a * nrb + k] * Lm[b * nrb + k];
-        Lm[a * nrb + b] = (a == b) ? sqrt(s) : s / Lm[b * nrb + b];
-      }
-    for (int a = 0; a < np; ++a) {
-      double s = hs[piv[a]];
-      for (int k = 0; k < a; ++k) s -= Lm[a * nrb + k] * ys[k];
-      ys[a] = s / Lm[a * nrb + a];
-    }
-    for (int i = 0; i < nrb; ++i) cs[i] = 0.0;
-    for (int a = np - 1; a >= 0; --a) {
-      double s = ys[a];
-      for (int k = a + 1; k < np; ++k) s -= Lm[k * nrb + a] * cs[piv[k]];
-      cs[piv[a]] = s / Lm[a * nrb + a];
-    }
-  }
+
+  // ---- 3. L y = h(piv), L^T c(piv) = y, x = R c
+  for (int i = lane; i < nrb; i += 32) { ys[i] = hs[i]; cs[i] = 0.0; }
   __syncwarp();
+  for (int a = 0; a < np; ++a) {                       // forward: column a of L
+    const int pa = piv[a];
+    const double ya = ys[pa] / Lc[a * ld + pa];
+    __syncwarp();
+    for (int r = a + 1 + lane; r < np; r += 32) ys[piv[r]] -= Lc[a * ld + piv[r]] * ya;
+    if (lane == 0) colv[a] = ya;                       // y in pivot order
+    __syncwarp();
+  }
+  for (int a = np - 1; a >= 0; --a) {                  // backward: row a of L^T = column a of L
+    const int pa = piv[a];
+    const double ca = colv[a] / Lc[a * ld + pa];
+    __syncwarp();
+    for (int r = lane; r < a; r += 32) colv[r] -= Lc[r * ld + pa] * ca;
+    if (lane == 0) cs[pa] = ca;
+    __syncwarp();
+  }
   double* xc = x + rhs * x_rs + cell * x_cs;
   for (int q = lane; q < nr; q += 32) {
-    double s = 0.0;
-    for (int i = 0; i < nrb; ++i) s += cs[i] * (double)Rc[(size_t)i * nr + q];
-    xc[q] = s;
+    TB sx = TB(0);
+    for (int i = 0; i < nrb; ++i) sx += (TB)cs[i] * Rc[(size_t)i * nr + q];
+    xc[q] = (double)sx;
   }
 }
 
@@ -557,29 +830,46 @@ fetidp_status k_apply_K(Ctx& c, CCellVec u, CellVec y, int nvec, int nrhs, bool 
 fetidp_status k_apply_K_f32(Ctx& c, const float* u, long long u_rs, int u_cs, float* y, long long y_rs,
                             int y_cs, int nvec, int nrhs, bool idp, bool r_only, long long ext) {
   const int len = r_only ? c.nr : c.n;
-  const int VB = nvec < 16 ? nvec : 16;
+  const int NA = 1 << c.d, ND = NA * c.d;
+  const int half = (c.e + 1) / 2;
+  const int nelc_max = half * half * (c.d == 3 ? half : 1);
+  const int kes = c.d == 2 ? multi_ke_stride(2) : multi_ke_stride(3);
+  const int cst = c.d == 2 ? multi_c_stride(2) : multi_c_stride(3);
+  const size_t fixed = (size_t)nelc_max * (kes + cst) * sizeof(float) + 16 + (size_t)NA * NA * c.d * sizeof(float) +
+                       (size_t)c.n * sizeof(int);
+  // vectors per chunk: as many as fit beside one colour's element data (<= 32)
+  auto bytes = [&](int vb) { return fixed + 2 * (size_t)c.n * (vb + 1) * sizeof(float); };
+  const size_t budget = 220 * 1024;
+  int VB = (int)std::min<long long>(32, nvec);
+  while (VB > 1 && bytes(VB) > budget) --VB;
+  if (bytes(VB) > budget) {
+    set_error("multi-vector K_s: cell too large for shared memory");
+    return FETIDP_EINVAL;
+  }
   {
-    const double D = c.d, NA = c.ngp;
-    const double fma = NA * D * D * 2.0 + D * D * D * D;
+    // algorithmic work: every element matrix once per chunk (ND rows x NA Gauss points x
+    // (D^3 + ND D) FMA) plus one K_e product (ND^2 FMA) per element and vector
     const double cols = (double)c.N * nrhs;
-    c.prof_pending_flops = 2.0 * fma * c.nelem * c.ngp * nvec * cols;
-    c.prof_pending_bytes = cols * (c.nsnap * 8.0 + 2.0 * nvec * len * 4.0);
+    const double chunks = (double)((nvec + VB - 1) / VB);
+    const double form = (double)ND * NA * (c.d * c.d * c.d + ND * c.d);
+    c.prof_pending_flops = 2.0 * cols * c.nelem * (chunks * form + (double)nvec * ND * ND);
+    c.prof_pending_bytes = cols * (chunks * c.nsnap * 8.0 + 2.0 * nvec * len * 4.0);
   }
   ProfScope ps(c, FETIDP_K_APPLY_K, c.prof_pending_flops, c.prof_pending_bytes);
-  const size_t smem = 2 * (size_t)VB * c.n * sizeof(float);
+  const size_t smem = bytes(VB);
   const float h = 1.0f / c.e;
   const float wq = (float)pow(0.5 / c.e, c.d);
   const dim3 grid((unsigned)(c.N * nrhs));
   if (c.d == 2) {
-    cudaFuncSetAttribute(apply_K_kernel<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    apply_K_kernel<2, float><<<grid, 256, smem, c.stream>>>(c.e, c.N, c.n, len, c.perm, c.perm + c.n, idp,
-                                                            u, u_rs, u_cs, y, y_rs, y_cs, nvec, VB,
-                                                            c.snap, c.nc, wq, 1.0f / h, ext, ext);
+    cudaFuncSetAttribute(apply_K_multi_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    apply_K_multi_kernel<2><<<grid, kMultiThreads, smem, c.stream>>>(
+        c.e, c.N, c.n, len, c.perm, idp, u, u_rs, u_cs, y, y_rs, y_cs, nvec, VB, c.snap, c.nc, wq, 1.0f / h,
+        nelc_max, ext, ext);
   } else {
-    cudaFuncSetAttribute(apply_K_kernel<3, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    apply_K_kernel<3, float><<<grid, 256, smem, c.stream>>>(c.e, c.N, c.n, len, c.perm, c.perm + c.n, idp,
-                                                            u, u_rs, u_cs, y, y_rs, y_cs, nvec, VB,
-                                                            c.snap, c.nc, wq, 1.0f / h, ext, ext);
+    cudaFuncSetAttribute(apply_K_multi_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    apply_K_multi_kernel<3><<<grid, kMultiThreads, smem, c.stream>>>(
+        c.e, c.N, c.n, len, c.perm, idp, u, u_rs, u_cs, y, y_rs, y_cs, nvec, VB, c.snap, c.nc, wq, 1.0f / h,
+        nelc_max, ext, ext);
   }
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
@@ -590,6 +880,15 @@ fetidp_status k_cell_gemv_strided(Ctx& c, const double* mats, long long mstride,
                                   int nrhs) {
   ProfScope ps(c, FETIDP_K_CELL_GEMV, 2.0 * mrows * mcols * (double)c.N * nrhs,
                8.0 * c.N * ((double)mrows * mcols + (double)nrhs * (mrows + mcols)));
+  if (mcols <= 32) {
+    const long long total = c.N * mrows;
+    long long grid = (total + 255) / 256;
+    if (grid > 152LL * 16) grid = 152LL * 16;
+    cell_gemv_narrow_kernel<<<(unsigned)grid, 256, 0, c.stream>>>(mats, mstride, ld, mrows, mcols, x.p, x.rs,
+                                                                 x.cs, y.p, y.rs, y.cs, alpha, beta, nrhs, c.N);
+    FD_CHECK_LAUNCH();
+    return FETIDP_OK;
+  }
   const size_t smem = (size_t)nrhs * mcols * sizeof(double);
   cudaFuncSetAttribute(cell_gemv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cell_gemv_kernel<<<(unsigned)c.N, 256, smem, c.stream>>>(mats, mstride, ld, mrows, mcols, x.p,

@@ -595,7 +595,7 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
     FD_TRY(tc_comb_pack(c, c.cUrd, c.Kinv, (long long)nr * nr, nr, 0, ni, nr, nullptr, 0, 0, 0, 0, 0, nd, nrb,
                         split));
     for (const TcComb* cb : {&c.cFdd, &c.cSdd, &c.cUrdT, &c.cUrd})
-      if (!tc_comb_fits(cb->K, split, ncols, cb->m_tiles)) {
+      if (!tc_comb_fits(cb->K, split, ncols, cb->m_tiles, cb->nops, cb->msplit < cb->M)) {
         set_error("combine kernel does not fit this cell size");
         return FETIDP_EINVAL;
       }

@@ -483,10 +483,23 @@ __global__ void __launch_bounds__(192, 1) tc_comb_kernel(TcCombParams P) {
   // bars: aFull[8], aEmpty[8], bFull, accFull[2], accEmpty[2]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 21);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* sCoef = reinterpret_cast<float*>(bars + 24);   // [set][op][column], FP32
   const uint32_t aFull = smem_u32(bars), aEmpty = smem_u32(bars + 8), bFull = smem_u32(bars + 16);
   const uint32_t accFull = smem_u32(bars + 17), accEmpty = smem_u32(bars + 19);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nt = blockIdx.x, mt = blockIdx.y;
+  // the tile's combination coefficients, once: 1 without coefficients, 0 past the last column
+  const int csets = P.msplit < P.M ? 2 : 1;
+  for (int t = threadIdx.x; t < csets * P.nops * BN; t += blockDim.x) {
+    const int set = t / (P.nops * BN);
+    const int rem = t - set * P.nops * BN;
+    const int j = rem / P.nops, k = rem - j * P.nops;   // op fastest: coalesced coefficient reads
+    const long long cidx = (long long)nt * BN + j;
+    const double* cp = set ? P.coef1 : P.coef0;
+    float v = 0.f;
+    if (cidx < P.ncols) v = cp ? (float)cp[(cidx % P.ncell) * P.nops + k] : 1.f;
+    sCoef[(set * P.nops + k) * BN + j] = v;
+  }
   if (threadIdx.x == 0) {
     for (int s = 0; s < 8; ++s) {
       mbar_init(aFull + 8 * s, 1);
@@ -593,7 +606,7 @@ __global__ void __launch_bounds__(192, 1) tc_comb_kernel(TcCombParams P) {
   } else {
     // ---------------- epilogue warps 0-3: one row per thread
     const int m = mt * TC_BM + warp * 32 + lane;
-    const double* coef = (m < P.msplit) ? P.coef0 : P.coef1;
+    const float* cset = (m < P.msplit || csets == 1) ? sCoef : sCoef + P.nops * BN;
     float acc[BN];
 #pragma unroll
     for (int j = 0; j < BN; ++j) acc[j] = 0.f;
@@ -612,18 +625,14 @@ __global__ void __launch_bounds__(192, 1) tc_comb_kernel(TcCombParams P) {
         uint32_t r[32];
         tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * BN + ch * 32), r);
         tmem_ld_wait();
+        const float* ck = cset + k * BN + ch * 32;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const long long cidx = (long long)nt * BN + ch * 32 + j;
-          float cf = 1.f;
-          if (coef != nullptr) {
-            cf = 0.f;
-            if (cidx < P.ncols) {
-              const long long cell = cidx % P.ncell;
-              cf = (float)coef[cell * P.nops + k];
-            }
-          }
-          acc[ch * 32 + j] += cf * __uint_as_float(r[j]);
+        for (int j = 0; j < 32; j += 4) {
+          const float4 c4 = *reinterpret_cast<const float4*>(ck + j);   // broadcast
+          acc[ch * 32 + j] += c4.x * __uint_as_float(r[j]);
+          acc[ch * 32 + j + 1] += c4.y * __uint_as_float(r[j + 1]);
+          acc[ch * 32 + j + 2] += c4.z * __uint_as_float(r[j + 2]);
+          acc[ch * 32 + j + 3] += c4.w * __uint_as_float(r[j + 3]);
         }
       }
       tc_fence_before();
@@ -735,8 +744,8 @@ __global__ void pack_comb_X_kernel(const double* __restrict__ X, long long x_rs,
 }
 
 template <int BN>
-size_t comb_smem_bytes(int kto, int nX, int astages) {
-  return (size_t)kto * nX * BN * TC_BK * 2 + (size_t)astages * A_TILE + 8 * 21 + 16 + 1024;
+size_t comb_smem_bytes(int kto, int nX, int astages, size_t coef_bytes) {
+  return (size_t)kto * nX * BN * TC_BK * 2 + (size_t)astages * A_TILE + 8 * 24 + coef_bytes + 1024;
 }
 
 // ---------------------------------------------------------------- host API
@@ -840,7 +849,8 @@ fetidp_status tc_apply(Ctx& c, const TcOperator& op, CCellVec X, const double* c
   P.a_bytes = (long long)batch * op.batch_bytes;
   P.b_bytes = (long long)c.tc_bbuf_bytes;
   P.y_ext = y_ext;
-  const double flops = 2.0 * op.m_tiles * TC_BM * (double)k_tiles * TC_BK * (double)n_tiles * BN * batch;
+  // algorithmic flops: one M x K product per operator and column (no padding, no split products)
+  const double flops = 2.0 * op.M * (double)op.K * op.nops * (double)ncols;
   ProfScope ps(c, FETIDP_K_TC_GEMM, flops,
                (double)batch * op.batch_bytes + (double)b_bytes + (double)ncols * op.M * (y_f64 ? 8 : 4) * batch);
   if (BN == 256) return launch_tc<256, 4>(c, P, batch);
@@ -892,19 +902,24 @@ int tc_comb_bn(long long ncols, int m_tiles) {
   return 32;
 }
 
-static int comb_stages(int bn, int kto, int nX) {
+// shared bytes of the staged combination coefficients (one or two FP32 sets of nops x bn)
+static size_t comb_coef_bytes(int bn, int nops, bool two_sets) {
+  return (size_t)(two_sets ? 2 : 1) * nops * bn * sizeof(float);
+}
+
+static int comb_stages(int bn, int kto, int nX, size_t coef_bytes) {
   const size_t budget = 220 * 1024;
-  const size_t b = (size_t)kto * nX * bn * TC_BK * 2 + 8 * 21 + 16 + 1024;
+  const size_t b = (size_t)kto * nX * bn * TC_BK * 2 + 8 * 24 + coef_bytes + 1024;
   if (b >= budget) return 0;
   int st = (int)((budget - b) / A_TILE);
   if (st > 8) st = 8;
   return st;
 }
 
-bool tc_comb_fits(int K, int split, long long ncols, int m_tiles) {
+bool tc_comb_fits(int K, int split, long long ncols, int m_tiles, int nops, bool two_sets) {
   const int kto = (K + TC_BK - 1) / TC_BK;
   const int bn = tc_comb_bn(ncols, m_tiles);
-  return comb_stages(bn, kto, split == 3 ? 2 : 1) >= 2;
+  return comb_stages(bn, kto, split == 3 ? 2 : 1, comb_coef_bytes(bn, nops, two_sets)) >= 2;
 }
 
 fetidp_status tc_comb_pack(Ctx& c, TcComb& op, const double* src0, long long st0, int lda0, int r00, int c00,
@@ -945,7 +960,8 @@ static fetidp_status comb_launch(Ctx& c, const TcComb& op, const TcCombParams& P
     set_error("tensor-core X staging buffer too small");
     return FETIDP_EINVAL;
   }
-  P.astages = comb_stages(BN, op.kto, op.nX);
+  const size_t coef_bytes = comb_coef_bytes(BN, op.nops, op.msplit < op.M);
+  P.astages = comb_stages(BN, op.kto, op.nX, coef_bytes);
   if (P.astages < 2) {
     set_error("combine kernel: operand K too large for shared memory");
     return FETIDP_EINVAL;
@@ -957,11 +973,12 @@ static fetidp_status comb_launch(Ctx& c, const TcComb& op, const TcCombParams& P
                                                               ncell, n_tiles, c.tc_bbuf);
     FD_CHECK_LAUNCH();
   }
-  const double flops = 2.0 * op.m_tiles * TC_BM * (double)op.kto * TC_BK * op.nops *
-                       (op.nA == 2 ? 3.0 : 1.0) * (double)n_tiles * BN;
+  // algorithmic flops: one M x K product per principal operator and column (no tile padding,
+  // no hi / lo split products)
+  const double flops = 2.0 * op.M * (double)op.K * op.nops * (double)ncols;
   ProfScope ps(c, FETIDP_K_TC_GEMM, flops,
                (double)op.bytes + (double)b_bytes + (double)ncols * op.M * (P.y_f64 ? 8 : 4));
-  const size_t smem = comb_smem_bytes<BN>(op.kto, op.nX, P.astages);
+  const size_t smem = comb_smem_bytes<BN>(op.kto, op.nX, P.astages, coef_bytes);
   cudaFuncSetAttribute(tc_comb_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid((unsigned)n_tiles, (unsigned)op.m_tiles, 1);
   tc_comb_kernel<BN><<<grid, 192, smem, c.stream>>>(P);
