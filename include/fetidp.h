@@ -118,6 +118,11 @@ typedef struct {
                                split into hi + lo BF16 parts, three products (hi hi, hi lo,
                                lo hi) for ~16-bit input precision (default 3)                */
   double tol_inner_mixed;   /* inner PCG tolerance used by the mixed path (1e-6)             */
+  double gram_drop_mixed;   /* mixed path, Eq. 46b: pivots of the FP32 Gram matrix whose Schur
+                               diagonal is not above this fraction of its largest diagonal are
+                               dropped (1e-9; the FP64 path drops below 1e-12).  The Gram data
+                               carry ~1e-5 relative noise (BF16 split products, FP32 K_s), so
+                               Schur diagonals below ~1e-10 are noise                        */
 } fetidp_options;
 
 typedef struct {

@@ -61,7 +61,7 @@ class Options(ctypes.Structure):
                 ("max_outer", ctypes.c_int), ("max_inner", ctypes.c_int),
                 ("precision", ctypes.c_int), ("fixed_outer", ctypes.c_int),
                 ("fixed_inner", ctypes.c_int), ("tc_split", ctypes.c_int),
-                ("tol_inner_mixed", ctypes.c_double)]
+                ("tol_inner_mixed", ctypes.c_double), ("gram_drop_mixed", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):

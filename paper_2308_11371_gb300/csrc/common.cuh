@@ -295,6 +295,16 @@ fetidp_status k_copy_scale(Ctx& c, const double* x, double* y, long long len, in
 
 // ---------------------------------------------------------------- kernels (cell-level compute)
 fetidp_status k_snapshots(Ctx& c);
+// dense batched setup kernels (principal blocks, SPD inverses by sweeps)
+fetidp_status k_assemble_principal(Ctx& c, const int* sigma_dev, int nrb, double* Krr, double* Krp, double* Kpp);
+fetidp_status k_spd_inverse_batched(Ctx& c, double* A, long long stride, int n, int lda, int batch, double* work,
+                                    int* status);
+fetidp_status k_batched_gemm_nn(Ctx& c, const double* A, long long sa, int lda, const double* B, long long sb,
+                                int ldb, double* C, long long sc, int ldc, int M, int N, int K, int batch);
+fetidp_status k_batched_block_copy(Ctx& c, const double* in, long long si, int ldi, int r0, int c0, double* out,
+                                   long long so, int ldo, int M, int N, int batch, bool transpose);
+fetidp_status k_batched_diag_sum(Ctx& c, const double* A, long long stride, int lda, int r0, int m, int batch,
+                                 double* out);
 fetidp_status k_apply_K(Ctx& c, CCellVec u, CellVec y, int nvec_per_col, int ncols, bool idp,
                         bool r_only, const double* chat, double chat_scale_dr);
 fetidp_status k_cell_gemv_strided(Ctx& c, const double* mats, long long mstride, int ld, int mrows,

@@ -1,0 +1,291 @@
+// Dense batched FP64 kernels of the setup phase: the principal cells' stiffness blocks
+// K_rr, K_rp, K_pp (Eq. 39) assembled from their Gauss-point C_hat, the principal inverses
+// K_rr^{-1} and S_dd = F_dd^{-1} (Sec. 3.1.1) by the symmetric sweep operator, and the products
+// U_rp = K_rr^{-1} K_rp.
+//
+// Sweep operator on a symmetric matrix, pivot k (a = A_kk > 0 while A is positive definite):
+//   A_kk <- -1/a,   A_ik <- A_ik / a (i != k),   A_ij <- A_ij - A_ik A_kj / a (i, j != k).
+// Sweeping every index gives -A^{-1}.  Only the upper triangle is updated; one launch per pivot
+// updates all matrices of the batch.  The old pivot column (= row, by symmetry) and 1/a are read
+// from a buffer that the previous launch filled with the next pivot's column, so no thread reads
+// an entry another thread of the same launch writes.
+#include <cmath>
+
+#include "common.cuh"
+
+namespace fetidp {
+namespace {
+
+inline int grid_for(long long work, int threads) {
+  long long g = (work + threads - 1) / threads;
+  if (g > 152LL * 64) g = 152LL * 64;
+  return (int)(g < 1 ? 1 : g);
+}
+
+// Element matrices of the principal cells scattered into K_rr, K_rp, K_pp (local order).
+// One thread per (principal, element, row (A, i)).
+template <int D>
+__global__ void assemble_principal_kernel(const double* __restrict__ snap, const int* __restrict__ sigma,
+                                          long long nsnap, int nrb, int e, int nc, int n, int nr,
+                                          const int* __restrict__ iperm, double wq, double inv_h,
+                                          double* __restrict__ Krr, double* __restrict__ Krp,
+                                          double* __restrict__ Kpp) {
+  constexpr int NA = 1 << D;
+  constexpr int ND = NA * D;
+  constexpr int NI = D * D;
+  const int nel = e * e * (D == 3 ? e : 1);
+  const int np = n - nr;
+  const long long total = (long long)nrb * nel * ND;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(t / ((long long)nel * ND));
+    const int r = (int)(t - (long long)k * nel * ND);
+    const int el = r / ND, row = r - el * ND;
+    const int A = row / D, i = row - A * D;
+    const int ex = el % e, ey = (el / e) % e, ez = el / (e * e);
+    const double* Cel = snap + (long long)sigma[k] * nsnap + (long long)el * NA * nc;
+    double krow[ND];
+#pragma unroll
+    for (int q = 0; q < ND; ++q) krow[q] = 0.0;
+    for (int gp = 0; gp < NA; ++gp) {
+      double dN[NA][D];
+#pragma unroll
+      for (int B = 0; B < NA; ++B)
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          double v = inv_h;
+#pragma unroll
+          for (int kk = 0; kk < D; ++kk) {
+            const int off = (B >> kk) & 1;
+            const double tk = gauss_t((gp >> kk) & 1);
+            v *= (kk == a) ? (off ? 1.0 : -1.0) : (off ? tk : 1.0 - tk);
+          }
+          dN[B][a] = v;
+        }
+      const double* C = Cel + gp * nc;
+      double w[D][D];   // w[j][b] = sum_a dN_A[a] C[(i,a),(j,b)]
+#pragma unroll
+      for (int j = 0; j < D; ++j)
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+          double s = 0.0;
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            int I = i * D + a, J = j * D + b;
+            if (I > J) { const int tmp = I; I = J; J = tmp; }
+            s += dN[A][a] * C[I * NI - I * (I - 1) / 2 + (J - I)];
+          }
+          w[j][b] = s;
+        }
+#pragma unroll
+      for (int B = 0; B < NA; ++B)
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          double s = 0.0;
+#pragma unroll
+          for (int b = 0; b < D; ++b) s += w[j][b] * dN[B][b];
+          krow[B * D + j] += wq * s;
+        }
+    }
+    int nodes[NA];
+#pragma unroll
+    for (int B = 0; B < NA; ++B) {
+      const int bx = B & 1, by = (B >> 1) & 1, bz = (B >> 2) & 1;
+      nodes[B] = (ex + bx) + (e + 1) * ((ey + by) + (e + 1) * (D == 3 ? (ez + bz) : 0));
+    }
+    const int la = iperm[nodes[A] * D + i];
+#pragma unroll
+    for (int B = 0; B < NA; ++B)
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const int lb = iperm[nodes[B] * D + j];
+        const double v = krow[B * D + j];
+        if (la < nr) {
+          if (lb < nr) atomicAdd(Krr + ((long long)k * nr + la) * nr + lb, v);
+          else atomicAdd(Krp + ((long long)k * nr + la) * np + (lb - nr), v);
+        } else if (lb >= nr) {
+          atomicAdd(Kpp + ((long long)k * np + (la - nr)) * np + (lb - nr), v);
+        }
+      }
+  }
+}
+
+// Pivot column 0 and 1/A_00 of every matrix (start of the sweep).
+__global__ void sweep_init_kernel(const double* __restrict__ A, long long stride, int n, int lda, int batch,
+                                  double* __restrict__ col, int* __restrict__ status) {
+  const long long total = (long long)batch * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / n), i = (int)(t - (long long)b * n);
+    const double v = A[b * stride + i];   // row 0 = column 0
+    col[(long long)b * (n + 1) + i] = v;
+    if (i == 0) {
+      if (!(v > 0.0)) atomicExch(status, 1);
+      col[(long long)b * (n + 1) + n] = 1.0 / v;
+    }
+  }
+}
+
+// One sweep step on the upper triangles; each thread updates 4 consecutive entries of a row.
+__global__ void sweep_step_kernel(double* __restrict__ A, long long stride, int n, int lda, int batch, int k,
+                                  const double* __restrict__ cin, double* __restrict__ cout,
+                                  int* __restrict__ status) {
+  const int nq = (n + 3) / 4;
+  const long long total = (long long)batch * n * nq;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / ((long long)n * nq));
+    const int r = (int)(t - (long long)b * n * nq);
+    const int i = r / nq, j0 = 4 * (r - (r / nq) * nq);
+    if (j0 + 3 < i) continue;                       // wholly below the diagonal
+    const double* ci = cin + (long long)b * (n + 1);
+    const double inv = ci[n];
+    const double cii = ci[i] * inv;
+    double* Ar = A + b * stride + (long long)i * lda;
+    double* co = cout + (long long)b * (n + 1);
+    for (int j = j0; j < j0 + 4 && j < n; ++j) {
+      if (j < i) continue;
+      double v;
+      if (i == k) v = (j == k) ? -inv : ci[j] * inv;
+      else if (j == k) v = cii;
+      else v = fma(-cii, ci[j], Ar[j]);
+      Ar[j] = v;
+      if (k + 1 < n) {
+        if (j == k + 1) co[i] = v;                  // entries (i, k+1), i <= k+1
+        if (i == k + 1) {                           // entries (k+1, j), j >= k+1
+          co[j] = v;
+          if (j == k + 1) {
+            if (!(v > 0.0)) atomicExch(status, 1);
+            co[n] = 1.0 / v;
+          }
+        }
+      }
+    }
+  }
+}
+
+// -A (upper) -> A^{-1} in both triangles.
+__global__ void sweep_finish_kernel(double* __restrict__ A, long long stride, int n, int lda, int batch) {
+  const long long total = (long long)batch * n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / ((long long)n * n));
+    const int r = (int)(t - (long long)b * n * n);
+    const int i = r / n, j = r - (r / n) * n;
+    if (j < i) continue;
+    double* Ab = A + b * stride;
+    const double v = -Ab[(long long)i * lda + j];
+    Ab[(long long)i * lda + j] = v;
+    Ab[(long long)j * lda + i] = v;
+  }
+}
+
+// C_b = A_b B_b (A: M x K row-major lda, B: K x N row-major ldb), one thread per output entry.
+__global__ void batched_gemm_nn_kernel(const double* __restrict__ A, long long sa, int lda,
+                                       const double* __restrict__ B, long long sb, int ldb, double* __restrict__ C,
+                                       long long sc, int ldc, int M, int N, int K, int batch) {
+  const long long total = (long long)batch * M * N;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / ((long long)M * N));
+    const int r = (int)(t - (long long)b * M * N);
+    const int i = r / N, j = r - (r / N) * N;
+    const double* Ar = A + b * sa + (long long)i * lda;
+    const double* Bc = B + b * sb + j;
+    double s = 0.0;
+    for (int q = 0; q < K; ++q) s = fma(Ar[q], Bc[(long long)q * ldb], s);
+    C[b * sc + (long long)i * ldc + j] = s;
+  }
+}
+
+// Out_b = (In_b block rows [r0, r0+M), cols [c0, c0+N)), optionally transposed.
+__global__ void batched_block_copy_kernel(const double* __restrict__ in, long long si, int ldi, int r0, int c0,
+                                          double* __restrict__ out, long long so, int ldo, int M, int N,
+                                          int batch, bool transpose) {
+  const long long total = (long long)batch * M * N;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / ((long long)M * N));
+    const int r = (int)(t - (long long)b * M * N);
+    const int i = r / N, j = r - (r / N) * N;
+    const double v = in[b * si + (long long)(r0 + i) * ldi + c0 + j];
+    if (transpose) out[b * so + (long long)j * ldo + i] = v;
+    else out[b * so + (long long)i * ldo + j] = v;
+  }
+}
+
+// out[b] = sum_l A_b[r0 + l][r0 + l], l < m (one warp per matrix).
+__global__ void batched_diag_sum_kernel(const double* __restrict__ A, long long stride, int lda, int r0, int m,
+                                        int batch, double* __restrict__ out) {
+  const int w = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (w >= batch) return;
+  double s = 0.0;
+  for (int l = lane; l < m; l += 32) s += A[w * stride + (long long)(r0 + l) * lda + r0 + l];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) out[w] = s;
+}
+
+}  // namespace
+
+fetidp_status k_assemble_principal(Ctx& c, const int* sigma_dev, int nrb, double* Krr, double* Krp, double* Kpp) {
+  const int np = c.n - c.nr;
+  ProfScope ps(c, FETIDP_K_SETUP, 0.0, (double)nrb * c.nsnap * 8.0);
+  FD_CUDA(cudaMemsetAsync(Krr, 0, sizeof(double) * (size_t)nrb * c.nr * c.nr, c.stream));
+  FD_CUDA(cudaMemsetAsync(Krp, 0, sizeof(double) * (size_t)nrb * c.nr * np, c.stream));
+  FD_CUDA(cudaMemsetAsync(Kpp, 0, sizeof(double) * (size_t)nrb * np * np, c.stream));
+  const double h = 1.0 / c.e, wq = std::pow(0.5 * h, c.d);
+  const int NA = 1 << c.d;
+  const long long work = (long long)nrb * c.nelem * NA * c.d;
+  if (c.d == 2)
+    assemble_principal_kernel<2><<<grid_for(work, 128), 128, 0, c.stream>>>(
+        c.snap, sigma_dev, c.nsnap, nrb, c.e, c.nc, c.n, c.nr, c.perm + c.n, wq, 1.0 / h, Krr, Krp, Kpp);
+  else
+    assemble_principal_kernel<3><<<grid_for(work, 128), 128, 0, c.stream>>>(
+        c.snap, sigma_dev, c.nsnap, nrb, c.e, c.nc, c.n, c.nr, c.perm + c.n, wq, 1.0 / h, Krr, Krp, Kpp);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_spd_inverse_batched(Ctx& c, double* A, long long stride, int n, int lda, int batch, double* work,
+                                    int* status) {
+  ProfScope ps(c, FETIDP_K_SETUP, 2.0 * batch * (double)n * n * n / 2.0, 16.0 * batch * (double)n * n * n / 2.0);
+  double* cbuf[2] = {work, work + (size_t)batch * (n + 1)};
+  sweep_init_kernel<<<grid_for((long long)batch * n, 256), 256, 0, c.stream>>>(A, stride, n, lda, batch, cbuf[0],
+                                                                               status);
+  FD_CHECK_LAUNCH();
+  const long long steps_work = (long long)batch * n * ((n + 3) / 4);
+  const int g = grid_for(steps_work, 256);
+  for (int k = 0; k < n; ++k) {
+    sweep_step_kernel<<<g, 256, 0, c.stream>>>(A, stride, n, lda, batch, k, cbuf[k & 1], cbuf[(k + 1) & 1], status);
+    FD_CHECK_LAUNCH();
+  }
+  sweep_finish_kernel<<<grid_for((long long)batch * n * n, 256), 256, 0, c.stream>>>(A, stride, n, lda, batch);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_batched_gemm_nn(Ctx& c, const double* A, long long sa, int lda, const double* B, long long sb,
+                                int ldb, double* C, long long sc, int ldc, int M, int N, int K, int batch) {
+  ProfScope ps(c, FETIDP_K_SETUP, 2.0 * batch * (double)M * N * K, 8.0 * batch * ((double)M * K + (double)M * N));
+  batched_gemm_nn_kernel<<<grid_for((long long)batch * M * N, 128), 128, 0, c.stream>>>(A, sa, lda, B, sb, ldb, C,
+                                                                                        sc, ldc, M, N, K, batch);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_batched_block_copy(Ctx& c, const double* in, long long si, int ldi, int r0, int c0, double* out,
+                                   long long so, int ldo, int M, int N, int batch, bool transpose) {
+  batched_block_copy_kernel<<<grid_for((long long)batch * M * N, 256), 256, 0, c.stream>>>(
+      in, si, ldi, r0, c0, out, so, ldo, M, N, batch, transpose);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_batched_diag_sum(Ctx& c, const double* A, long long stride, int lda, int r0, int m, int batch,
+                                 double* out) {
+  batched_diag_sum_kernel<<<(batch * 32 + 255) / 256, 256, 0, c.stream>>>(A, stride, lda, r0, m, batch, out);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+}  // namespace fetidp

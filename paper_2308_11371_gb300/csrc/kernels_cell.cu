@@ -921,7 +921,8 @@ fetidp_status k_grouped_gemm_n(Ctx& c, const double* A, long long a_stride_k, in
 }
 
 template <typename TB>
-static fetidp_status gram_solve_t(Ctx& c, const TB* R, const TB* KR, CCellVec v, CellVec x, int nrhs) {
+static fetidp_status gram_solve_t(Ctx& c, const TB* R, const TB* KR, CCellVec v, CellVec x, int nrhs,
+                                  double drop_rel) {
   if (c.nrb > kMaxRb) {
     set_error("n_rb above 64 is not supported by the Gram solve");
     return FETIDP_EINVAL;
@@ -935,20 +936,20 @@ static fetidp_status gram_solve_t(Ctx& c, const TB* R, const TB* KR, CCellVec v,
   const size_t smem = per_warp * wpb;
   cudaFuncSetAttribute(gram_warp_kernel<TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   gram_warp_kernel<TB><<<(unsigned)ceil_div(cols, wpb), 32 * wpb, smem, c.stream>>>(
-      R, KR, v.p, v.rs, v.cs, x.p, x.rs, x.cs, c.nr, c.nrb, c.N, nrhs, 1e-12);
+      R, KR, v.p, v.rs, v.cs, x.p, x.rs, x.cs, c.nr, c.nrb, c.N, nrhs, drop_rel);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }
 
 fetidp_status k_gram_solve(Ctx& c, const double* R, const double* KR, CCellVec v, CellVec x,
                            int nrhs) {
-  return gram_solve_t<double>(c, R, KR, v, x, nrhs);
+  return gram_solve_t<double>(c, R, KR, v, x, nrhs, 1e-12);
 }
 
 fetidp_status k_gram_solve_f32(Ctx& c, const float* R, const float* KR, CCellVec v, CellVec x,
                                int nrhs, long long r_ext) {
   (void)r_ext;
-  return gram_solve_t<float>(c, R, KR, v, x, nrhs);
+  return gram_solve_t<float>(c, R, KR, v, x, nrhs, c.opt.gram_drop_mixed);
 }
 
 fetidp_status k_grad(Ctx& c, const double* u, const double* w, double* g) {

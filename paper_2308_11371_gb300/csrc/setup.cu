@@ -73,55 +73,6 @@ RefCell build_ref(int d, int e, int& ni, int& nd, int& np) {
   return R;
 }
 
-// Element matrix contributions from C_hat of one cell, assembled densely (natural order).
-void assemble_dense_K(const Ctx& c, const double* chat, std::vector<double>& K) {
-  const int d = c.d, e = c.e, n = c.n, NA = 1 << d;
-  K.assign((size_t)n * n, 0.0);
-  const double h = 1.0 / e, wq = std::pow(0.5 * h, d);
-  const int ni2 = d * d;
-  for (int el = 0; el < c.nelem; ++el) {
-    const int ex = el % e, ey = (el / e) % e, ez = el / (e * e);
-    int nodes[8];
-    for (int A = 0; A < NA; ++A) {
-      const int ax = A & 1, ay = (A >> 1) & 1, az = (A >> 2) & 1;
-      nodes[A] = (ex + ax) + (e + 1) * ((ey + ay) + (e + 1) * (d == 3 ? (ez + az) : 0));
-    }
-    for (int gp = 0; gp < NA; ++gp) {
-      double t[3];
-      for (int k = 0; k < d; ++k) t[k] = gauss_t((gp >> k) & 1);
-      double dN[8][3];
-      for (int A = 0; A < NA; ++A)
-        for (int a = 0; a < d; ++a) {
-          double v = 1.0 / h;
-          for (int k = 0; k < d; ++k) {
-            const int off = (A >> k) & 1;
-            v *= (k == a) ? (off ? 1.0 : -1.0) : (off ? t[k] : 1.0 - t[k]);
-          }
-          dN[A][a] = v;
-        }
-      // full symmetric C from the upper triangle
-      double Cf[9][9];
-      const double* Cu = chat + ((size_t)el * NA + gp) * c.nc;
-      int q = 0;
-      for (int I = 0; I < ni2; ++I)
-        for (int J = I; J < ni2; ++J) {
-          Cf[I][J] = Cu[q];
-          Cf[J][I] = Cu[q];
-          ++q;
-        }
-      for (int A = 0; A < NA; ++A)
-        for (int i = 0; i < d; ++i)
-          for (int B = 0; B < NA; ++B)
-            for (int j = 0; j < d; ++j) {
-              double s = 0.0;
-              for (int a = 0; a < d; ++a)
-                for (int b = 0; b < d; ++b) s += dN[A][a] * Cf[i * d + a][j * d + b] * dN[B][b];
-              K[(size_t)(nodes[A] * d + i) * n + nodes[B] * d + j] += wq * s;
-            }
-    }
-  }
-}
-
 // f^(s) of one load case for one cell (natural order), Eq. 5b.
 void cell_load(const Ctx& c, const fetidp_problem& p, int load, int cx, int cy, int cz,
                std::vector<double>& f) {
@@ -242,6 +193,10 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
   c.opt = o;
   c.mixed = o.precision == FETIDP_MIXED_BF16;
   if (c.mixed && o.tc_split != 1 && o.tc_split != 3) { set_error("tc_split must be 1 or 3"); return FETIDP_EINVAL; }
+  if (!(o.gram_drop_mixed >= 0.0 && o.gram_drop_mixed < 1.0)) {
+    set_error("gram_drop_mixed must lie in [0, 1)");
+    return FETIDP_EINVAL;
+  }
   const int d = p.dim, e = p.elems;
   Geo& g = c.geo;
   g.dim = d; g.e = e;
@@ -475,47 +430,47 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
   phase("greedy + alpha");
 
   // ---------------------------------------------------------------- principal operators (Eq. 39)
-  const int n = c.n, nr = c.nr, ni = c.ni, nd = c.nd, np = c.np;
-  std::vector<double> h_snap_p((size_t)nrb * c.nsnap);
-  for (int k = 0; k < nrb; ++k)
-    FD_CUDA(cudaMemcpyAsync(h_snap_p.data() + (size_t)k * c.nsnap, c.snap + (size_t)c.sigma[k] * c.nsnap,
-                            sizeof(double) * c.nsnap, cudaMemcpyDeviceToHost, c.stream));
-  FD_CUDA(cudaStreamSynchronize(c.stream));
-  std::vector<double> hKinv((size_t)nrb * nr * nr), hUrp((size_t)nrb * nr * np),
-      hUrpT((size_t)nrb * np * nr), hSdd((size_t)nrb * nd * nd), hKpp((size_t)nrb * np * np),
-      hKrp((size_t)nrb * nr * np);
-  std::vector<char> fail(nrb, 0);
-  parallel_for(nrb, [&](int k) {
-    std::vector<double> Knat;
-    assemble_dense_K(c, h_snap_p.data() + (size_t)k * c.nsnap, Knat);
-    std::vector<double> Krr((size_t)nr * nr);
-    for (int a = 0; a < nr; ++a)
-      for (int b = 0; b < nr; ++b) Krr[(size_t)a * nr + b] = Knat[(size_t)ref.perm[a] * n + ref.perm[b]];
-    double* Krp = hKrp.data() + (size_t)k * nr * np;
-    for (int a = 0; a < nr; ++a)
-      for (int b = 0; b < np; ++b) Krp[(size_t)a * np + b] = Knat[(size_t)ref.perm[a] * n + ref.perm[nr + b]];
-    double* Kpp = hKpp.data() + (size_t)k * np * np;
-    for (int a = 0; a < np; ++a)
-      for (int b = 0; b < np; ++b) Kpp[(size_t)a * np + b] = Knat[(size_t)ref.perm[nr + a] * n + ref.perm[nr + b]];
-    double* Ki = hKinv.data() + (size_t)k * nr * nr;
-    if (!spd_inverse(nr, Krr.data(), nr, Ki, nr)) { fail[k] = 1; return; }
-    double* U = hUrp.data() + (size_t)k * nr * np;
-    gemm(false, false, nr, np, nr, 1.0, Ki, nr, Krp, np, 0.0, U, np);
-    double* UT = hUrpT.data() + (size_t)k * np * nr;
-    for (int a = 0; a < nr; ++a)
-      for (int b = 0; b < np; ++b) UT[(size_t)b * nr + a] = U[(size_t)a * np + b];
-    // S_dd = F_dd^{-1}, F_dd = T_dr K_rr^{-1} T_rd (Sec. 3.1.1)
-    std::vector<double> F((size_t)nd * nd);
-    for (int a = 0; a < nd; ++a)
-      for (int b = 0; b < nd; ++b) F[(size_t)a * nd + b] = Ki[(size_t)(ni + a) * nr + ni + b];
-    if (!spd_inverse(nd, F.data(), nd, hSdd.data() + (size_t)k * nd * nd, nd)) fail[k] = 1;
-  });
-  for (int k = 0; k < nrb; ++k)
-    if (fail[k]) { set_error("principal K_rr is not positive definite"); return FETIDP_ESINGULAR; }
-  FD_TRY(upload(c, &c.Kinv, hKinv));
-  FD_TRY(upload(c, &c.Urp, hUrp));
-  FD_TRY(upload(c, &c.UrpT, hUrpT));
-  FD_TRY(upload(c, &c.Sdd, hSdd));
+  const int nr = c.nr, ni = c.ni, nd = c.nd, np = c.np;
+  // All on the device: the principal K blocks assembled from their C_hat snapshots, K_rr^{-1} and
+  // S_dd = F_dd^{-1} (F_dd = T_dr K_rr^{-1} T_rd, Sec. 3.1.1) by batched sweeps, U_rp = K_rr^{-1} K_rp.
+  std::vector<double> hUrp((size_t)nrb * nr * np), hKpp((size_t)nrb * np * np), hKrp((size_t)nrb * nr * np),
+      dvec(nrb, 0.0);
+  {
+    FD_TRY(dalloc_t(c, &c.Kinv, (size_t)nrb * nr * nr));
+    FD_TRY(dalloc_t(c, &c.Urp, (size_t)nrb * nr * np));
+    FD_TRY(dalloc_t(c, &c.UrpT, (size_t)nrb * np * nr));
+    FD_TRY(dalloc_t(c, &c.Sdd, (size_t)nrb * nd * nd));
+    int* sigma_dev = nullptr;
+    int* st_dev = nullptr;
+    double *Krp_d = nullptr, *Kpp_d = nullptr, *work = nullptr, *dvec_d = nullptr;
+    FD_CUDA(cudaMalloc(&sigma_dev, sizeof(int) * nrb));
+    FD_CUDA(cudaMalloc(&st_dev, sizeof(int)));
+    FD_CUDA(cudaMalloc(&Krp_d, sizeof(double) * (size_t)nrb * nr * np));
+    FD_CUDA(cudaMalloc(&Kpp_d, sizeof(double) * (size_t)nrb * np * np));
+    FD_CUDA(cudaMalloc(&work, sizeof(double) * 2 * (size_t)nrb * (nr + 1)));
+    FD_CUDA(cudaMalloc(&dvec_d, sizeof(double) * nrb));
+    FD_CUDA(cudaMemcpyAsync(sigma_dev, c.sigma.data(), sizeof(int) * nrb, cudaMemcpyHostToDevice, c.stream));
+    FD_CUDA(cudaMemsetAsync(st_dev, 0, sizeof(int), c.stream));
+    FD_TRY(k_assemble_principal(c, sigma_dev, nrb, c.Kinv, Krp_d, Kpp_d));
+    FD_TRY(k_spd_inverse_batched(c, c.Kinv, (long long)nr * nr, nr, nr, nrb, work, st_dev));
+    FD_TRY(k_batched_gemm_nn(c, c.Kinv, (long long)nr * nr, nr, Krp_d, (long long)nr * np, np, c.Urp,
+                             (long long)nr * np, np, nr, np, nr, nrb));
+    FD_TRY(k_batched_block_copy(c, c.Urp, (long long)nr * np, np, 0, 0, c.UrpT, (long long)np * nr, nr, nr, np,
+                                nrb, true));
+    FD_TRY(k_batched_diag_sum(c, c.Kinv, (long long)nr * nr, nr, ni, nd, nrb, dvec_d));
+    FD_TRY(k_batched_block_copy(c, c.Kinv, (long long)nr * nr, nr, ni, ni, c.Sdd, (long long)nd * nd, nd, nd, nd,
+                                nrb, false));
+    FD_TRY(k_spd_inverse_batched(c, c.Sdd, (long long)nd * nd, nd, nd, nrb, work, st_dev));
+    int hst = 0;
+    FD_CUDA(cudaMemcpyAsync(hUrp.data(), c.Urp, sizeof(double) * hUrp.size(), cudaMemcpyDeviceToHost, c.stream));
+    FD_CUDA(cudaMemcpyAsync(hKrp.data(), Krp_d, sizeof(double) * hKrp.size(), cudaMemcpyDeviceToHost, c.stream));
+    FD_CUDA(cudaMemcpyAsync(hKpp.data(), Kpp_d, sizeof(double) * hKpp.size(), cudaMemcpyDeviceToHost, c.stream));
+    FD_CUDA(cudaMemcpyAsync(dvec.data(), dvec_d, sizeof(double) * nrb, cudaMemcpyDeviceToHost, c.stream));
+    FD_CUDA(cudaMemcpyAsync(&hst, st_dev, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    FD_CUDA(cudaStreamSynchronize(c.stream));
+    cudaFree(sigma_dev); cudaFree(st_dev); cudaFree(Krp_d); cudaFree(Kpp_d); cudaFree(work); cudaFree(dvec_d);
+    if (hst != 0) { set_error("principal K_rr is not positive definite"); return FETIDP_ESINGULAR; }
+  }
   phase("principal factorisations");
 
   // ---------------------------------------------------------------- projections pi, delta (Eqs. 41-42)
@@ -557,9 +512,6 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
     FD_CUDA(cudaMemcpyAsync(hY.data(), Y, sizeof(double) * hY.size(), cudaMemcpyDeviceToHost, c.stream));
     FD_CUDA(cudaStreamSynchronize(c.stream));
     cudaFree(Gd); cudaFree(Gp); cudaFree(Ge); cudaFree(Tab); cudaFree(Y); cudaFree(specs_dev);
-    std::vector<double> dvec(nrb, 0.0);
-    for (int k = 0; k < nrb; ++k)
-      for (int l = 0; l < nd; ++l) dvec[k] += hKinv[(size_t)k * nr * nr + (size_t)(ni + l) * nr + ni + l];
     parallel_for((int)std::min<long long>(c.N, 1 << 30), [&](int s) {
       const double* y = hY.data() + (size_t)s * ntab;
       std::vector<double> A((size_t)nrb * nrb), M((size_t)nrb * nrb), b(nrb);

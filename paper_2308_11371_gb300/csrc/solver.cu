@@ -531,6 +531,7 @@ void fetidp_default_options(fetidp_options* o) {
   o->fixed_inner = 0;
   o->tc_split = 3;
   o->tol_inner_mixed = 1e-6;
+  o->gram_drop_mixed = 1e-9;
 }
 
 const char* fetidp_status_string(fetidp_status s) {

@@ -41,6 +41,7 @@ def test_binding_covers_every_declared_symbol():
 def test_default_options_and_status_strings(lib):
     o = binding.default_options()
     assert o.tol_outer == 1e-8 and o.tol_inner == 1e-11 and o.precision == binding.FETIDP_FP64
+    assert o.tol_inner_mixed == 1e-6 and o.gram_drop_mixed == 1e-9 and o.tc_split == 3
     assert lib.fetidp_status_string(-4) == b"not converged"
     assert lib.fetidp_status_string(0) == b"ok"
 
