@@ -303,6 +303,8 @@ fetidp_status k_batched_gemm_nn(Ctx& c, const double* A, long long sa, int lda, 
                                 int ldb, double* C, long long sc, int ldc, int M, int N, int K, int batch);
 fetidp_status k_batched_block_copy(Ctx& c, const double* in, long long si, int ldi, int r0, int c0, double* out,
                                    long long so, int ldo, int M, int N, int batch, bool transpose);
+fetidp_status k_df_gemm(Ctx& c, const double* A, int lda, int M, int K, const double* X, int x_cs, long long ncols,
+                        double* Y, int y_cs);
 fetidp_status k_batched_diag_sum(Ctx& c, const double* A, long long stride, int lda, int r0, int m, int batch,
                                  double* out);
 fetidp_status k_apply_K(Ctx& c, CCellVec u, CellVec y, int nvec_per_col, int ncols, bool idp,

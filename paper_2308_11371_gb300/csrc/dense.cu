@@ -225,6 +225,75 @@ __global__ void batched_diag_sum_kernel(const double* __restrict__ A, long long 
   if (lane == 0) out[w] = s;
 }
 
+// Y[cell][m] = sum_k A[m][k] X[cell][k] in double-float arithmetic on the FP32 pipe (GB300
+// issues FP32 at ~60x its FP64 rate).  Each FP64 operand is split into hi + lo floats (48
+// significant bits); a product is hi*hi, made exact by an FMA residual, plus the cross terms;
+// the sum is kept as an unevaluated pair (s, c) with TwoSum on the leading part.  Relative error
+// ~K * 2^-46 of the largest term, against K * 2^-53 for FP64.  64 x 64 output tile per block,
+// 4 x 4 per thread, K chunks of 16.
+constexpr int DF_T = 64, DF_K = 16;
+__global__ void __launch_bounds__(256) df_gemm_kernel(const double* __restrict__ A, int lda, int M, int K,
+                                                      const double* __restrict__ X, int x_cs, long long ncols,
+                                                      double* __restrict__ Y, int y_cs) {
+  __shared__ float Ah[DF_K][DF_T + 1], Al[DF_K][DF_T + 1];
+  __shared__ float Xh[DF_K][DF_T + 1], Xl[DF_K][DF_T + 1];
+  const long long col0 = (long long)blockIdx.x * DF_T;
+  const int m0 = blockIdx.y * DF_T;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float sh[4][4], sl[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { sh[i][j] = 0.f; sl[i][j] = 0.f; }
+  for (int k0 = 0; k0 < K; k0 += DF_K) {
+    for (int t = threadIdx.x; t < DF_K * DF_T; t += 256) {
+      const int r = t / DF_K, q = t - r * DF_K;   // q fastest: coalesced rows of A and X
+      const int gm = m0 + r, gk = k0 + q;
+      const double av = (gm < M && gk < K) ? A[(size_t)gm * lda + gk] : 0.0;
+      const float ah = (float)av;
+      Ah[q][r] = ah;
+      Al[q][r] = (float)(av - (double)ah);
+      const long long gc = col0 + r;
+      const double xv = (gc < ncols && gk < K) ? X[gc * x_cs + gk] : 0.0;
+      const float xh = (float)xv;
+      Xh[q][r] = xh;
+      Xl[q][r] = (float)(xv - (double)xh);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int q = 0; q < DF_K; ++q) {
+      float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) { ah[i] = Ah[q][ty + 16 * i]; al[i] = Al[q][ty + 16 * i]; }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) { bh[j] = Xh[q][tx + 16 * j]; bl[j] = Xl[q][tx + 16 * j]; }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float p = ah[i] * bh[j];
+          const float e = fmaf(ah[i], bh[j], -p) + fmaf(ah[i], bl[j], al[i] * bh[j]);
+          const float t = sh[i][j] + p;            // TwoSum(sh, p)
+          const float bv = t - sh[i][j];
+          const float err = (sh[i][j] - (t - bv)) + (p - bv);
+          sh[i][j] = t;
+          sl[i][j] += err + e;
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const long long gc = col0 + tx + 16 * j;
+    if (gc >= ncols) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int gm = m0 + ty + 16 * i;
+      if (gm < M) Y[gc * y_cs + gm] = (double)sh[i][j] + (double)sl[i][j];
+    }
+  }
+}
+
 }  // namespace
 
 fetidp_status k_assemble_principal(Ctx& c, const int* sigma_dev, int nrb, double* Krr, double* Krp, double* Kpp) {
@@ -284,6 +353,15 @@ fetidp_status k_batched_block_copy(Ctx& c, const double* in, long long si, int l
 fetidp_status k_batched_diag_sum(Ctx& c, const double* A, long long stride, int lda, int r0, int m, int batch,
                                  double* out) {
   batched_diag_sum_kernel<<<(batch * 32 + 255) / 256, 256, 0, c.stream>>>(A, stride, lda, r0, m, batch, out);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_df_gemm(Ctx& c, const double* A, int lda, int M, int K, const double* X, int x_cs, long long ncols,
+                        double* Y, int y_cs) {
+  ProfScope ps(c, FETIDP_K_SETUP, 2.0 * M * (double)K * ncols, 8.0 * ((double)M * K + (double)ncols * (K + M)));
+  const dim3 grid((unsigned)((ncols + DF_T - 1) / DF_T), (unsigned)((M + DF_T - 1) / DF_T));
+  df_gemm_kernel<<<grid, 256, 0, c.stream>>>(A, lda, M, K, X, x_cs, ncols, Y, y_cs);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }

@@ -504,10 +504,15 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
                             cudaMemcpyHostToDevice, c.stream));
     FD_TRY(k_trace_tables(c, specs_dev, (int)specs.size(), Tab, c.nsnap));
     // Both trace systems of Eq. 42 are Gram matrices of nearly dependent principal fields; their
-    // pivoted solves decide which directions to drop at 1e-12 of the largest pivot, so the traces
-    // are always taken in FP64 (a BF16-split contraction changes those decisions).
-    FD_TRY(k_grouped_gemm_n(c, Tab, 0, (int)c.nsnap, ntab, (int)c.nsnap, 1, CCellVec{c.snap, 0, (int)c.nsnap},
-                            CellVec{Y, 0, ntab}, nullptr, 1.0, 0.0, c.N, 1, false, 0));
+    // pivoted solves decide which directions to drop at 1e-12 of the largest pivot and amplify
+    // trace errors by ~1e5, so a BF16-split contraction is far too coarse.  The FP64 path takes
+    // the traces in FP64; the mixed path (whose operators carry ~1e-5 BF16 error) in double-float
+    // arithmetic on the FP32 pipe (~1e-13).
+    if (c.mixed)
+      FD_TRY(k_df_gemm(c, Tab, (int)c.nsnap, ntab, (int)c.nsnap, c.snap, (int)c.nsnap, c.N, Y, ntab));
+    else
+      FD_TRY(k_grouped_gemm_n(c, Tab, 0, (int)c.nsnap, ntab, (int)c.nsnap, 1, CCellVec{c.snap, 0, (int)c.nsnap},
+                              CellVec{Y, 0, ntab}, nullptr, 1.0, 0.0, c.N, 1, false, 0));
     std::vector<double> hY((size_t)c.N * ntab);
     FD_CUDA(cudaMemcpyAsync(hY.data(), Y, sizeof(double) * hY.size(), cudaMemcpyDeviceToHost, c.stream));
     FD_CUDA(cudaStreamSynchronize(c.stream));

@@ -448,6 +448,8 @@ fetidp_status launch_tc(Ctx& c, const TcParams& P, int batch) {
 // epilogue warps add coef * accumulator into FP32 registers while the MMA warp fills the other
 // buffer.  Rows below msplit use coef0, the others coef1 (stacked operator sets).
 // Warps 0-3 epilogue (TMEM lane quadrants), warp 4 producer, warp 5 MMA issuer.
+constexpr int kCombStages = 12;                   // deepest operator-tile ring
+constexpr int kCombBars = 2 * kCombStages + 8;    // barrier slots (8 bytes) before the coefficients
 struct TcCombParams {
   const uint8_t* A;
   const uint8_t* B;
@@ -480,12 +482,13 @@ __global__ void __launch_bounds__(192, 1) tc_comb_kernel(TcCombParams P) {
   uint8_t* sB = smem;
   uint8_t* sA = sB + (size_t)KX * B_TILE;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sA + (size_t)S * A_TILE);
-  // bars: aFull[8], aEmpty[8], bFull, accFull[2], accEmpty[2]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 21);
+  // bars: aFull[kCombStages], aEmpty[kCombStages], bFull, accFull[2], accEmpty[2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kCombStages + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  float* sCoef = reinterpret_cast<float*>(bars + 24);   // [set][op][column], FP32
-  const uint32_t aFull = smem_u32(bars), aEmpty = smem_u32(bars + 8), bFull = smem_u32(bars + 16);
-  const uint32_t accFull = smem_u32(bars + 17), accEmpty = smem_u32(bars + 19);
+  float* sCoef = reinterpret_cast<float*>(bars + kCombBars);   // [set][op][column], FP32
+  const uint32_t aFull = smem_u32(bars), aEmpty = smem_u32(bars + kCombStages);
+  const uint32_t bFull = smem_u32(bars + 2 * kCombStages);
+  const uint32_t accFull = smem_u32(bars + 2 * kCombStages + 1), accEmpty = smem_u32(bars + 2 * kCombStages + 3);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nt = blockIdx.x, mt = blockIdx.y;
   // the tile's combination coefficients, once: 1 without coefficients, 0 past the last column
@@ -501,7 +504,7 @@ __global__ void __launch_bounds__(192, 1) tc_comb_kernel(TcCombParams P) {
     sCoef[(set * P.nops + k) * BN + j] = v;
   }
   if (threadIdx.x == 0) {
-    for (int s = 0; s < 8; ++s) {
+    for (int s = 0; s < kCombStages; ++s) {
       mbar_init(aFull + 8 * s, 1);
       mbar_init(aEmpty + 8 * s, 1);
     }
@@ -745,7 +748,7 @@ __global__ void pack_comb_X_kernel(const double* __restrict__ X, long long x_rs,
 
 template <int BN>
 size_t comb_smem_bytes(int kto, int nX, int astages, size_t coef_bytes) {
-  return (size_t)kto * nX * BN * TC_BK * 2 + (size_t)astages * A_TILE + 8 * 24 + coef_bytes + 1024;
+  return (size_t)kto * nX * BN * TC_BK * 2 + (size_t)astages * A_TILE + 8 * kCombBars + coef_bytes + 1024;
 }
 
 // ---------------------------------------------------------------- host API
@@ -909,10 +912,10 @@ static size_t comb_coef_bytes(int bn, int nops, bool two_sets) {
 
 static int comb_stages(int bn, int kto, int nX, size_t coef_bytes) {
   const size_t budget = 220 * 1024;
-  const size_t b = (size_t)kto * nX * bn * TC_BK * 2 + 8 * 24 + coef_bytes + 1024;
+  const size_t b = (size_t)kto * nX * bn * TC_BK * 2 + 8 * kCombBars + coef_bytes + 1024;
   if (b >= budget) return 0;
   int st = (int)((budget - b) / A_TILE);
-  if (st > 8) st = 8;
+  if (st > kCombStages) st = kCombStages;
   return st;
 }
 
