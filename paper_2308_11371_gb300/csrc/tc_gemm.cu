@@ -202,6 +202,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(TcParams P) {
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const int KT = P.k_tiles;
+  const int rot = (int)(((long long)nt + mt + (long long)P.m_tiles * bz) % KT);
   const uint8_t* Ab = P.A + bz * P.a_batch_stride + (long long)mt * KT * A_TILE;
   const uint8_t* Bb = P.B + bz * P.b_batch_stride + (long long)nt * KT * B_TILE;
   if (warp == 0 && lane == 0) {
@@ -214,15 +215,19 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(TcParams P) {
         atomicExch(P.err, 1);
         break;
       }
-      const long long aoff = (Ab - P.A) + (long long)kt * A_TILE, boff = (Bb - P.B) + (long long)kt * B_TILE;
+      // k tiles in rotated order: CTAs that share A tiles (same row tile and operator) differ
+      // in nt, CTAs that share B tiles differ in (mt, bz); the rotation keeps them off the
+      // same L2 lines at the same time (the accumulation order only changes rounding)
+      const int kr = (kt + rot) % KT;
+      const long long aoff = (Ab - P.A) + (long long)kr * A_TILE, boff = (Bb - P.B) + (long long)kr * B_TILE;
       if (!FD_INB(aoff + A_TILE - 1, P.a_bytes, 101) || !FD_INB(boff + B_TILE - 1, P.b_bytes, 102)) {
         *abort_flag = 1;
         atomicExch(P.err, 4);
         break;
       }
       mbar_expect_tx(full0 + 8 * s, A_TILE + B_TILE);
-      bulk_g2s(smem_u32(sA + s * A_TILE), Ab + (long long)kt * A_TILE, A_TILE, full0 + 8 * s);
-      bulk_g2s(smem_u32(sB + s * B_TILE), Bb + (long long)kt * B_TILE, B_TILE, full0 + 8 * s);
+      bulk_g2s(smem_u32(sA + s * A_TILE), Ab + (long long)kr * A_TILE, A_TILE, full0 + 8 * s);
+      bulk_g2s(smem_u32(sB + s * B_TILE), Bb + (long long)kr * B_TILE, B_TILE, full0 + 8 * s);
       ++issued;
     }
     if (*abort_flag) {
@@ -453,7 +458,7 @@ constexpr int kCombBars = 2 * kCombStages + 8;    // barrier slots (8 bytes) bef
 struct TcCombParams {
   const uint8_t* A;
   const uint8_t* B;
-  int m_tiles, n_tiles, kto, nops, nA, nX, astages;
+  int m_tiles, n_tiles, kto, nops, nA, nX, astages, tps;   // tps: operator tiles per ring stage
   int M, msplit;
   long long ncols, ncell;
   const double* coef0;
@@ -481,7 +486,7 @@ __global__ void __launch_bounds__(192, 1) tc_comb_kernel(TcCombParams P) {
   const int S = P.astages;
   uint8_t* sB = smem;
   uint8_t* sA = sB + (size_t)KX * B_TILE;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + (size_t)S * A_TILE);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + (size_t)S * P.tps * A_TILE);
   // bars: aFull[kCombStages], aEmpty[kCombStages], bFull, accFull[2], accEmpty[2]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kCombStages + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -525,31 +530,39 @@ __global__ void __launch_bounds__(192, 1) tc_comb_kernel(TcCombParams P) {
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const int per_op = P.kto * P.nA;
-  const int total = P.nops * per_op;
+  const int tps = P.tps, cpo = (per_op + tps - 1) / tps, nchunk = P.nops * cpo;
+  const size_t stage_bytes = (size_t)tps * A_TILE;
+  // Every column tile streams all operators.  Tile nt starts at operator nt mod nops, so at any
+  // moment the CTAs read different operator tiles, spread over all L2 slices, instead of all
+  // hitting the few slices that hold one tile.
+  const int rot = nt % P.nops;
   if (warp == 4) {
     if (lane == 0) {
-      // resident X tiles, then the operator ring
+      // resident X tiles (one copy), then the operator ring.  A stage holds tps consecutive
+      // tiles of one operator and arrives with one bulk copy: the copy rate per SM grows with
+      // the bytes per copy, not with the number of copies in flight.
       const uint8_t* Bb = P.B + (long long)nt * KX * B_TILE;
       mbar_expect_tx(bFull, (uint32_t)(KX * B_TILE));
-      for (int t = 0; t < KX; ++t)
-        bulk_g2s(smem_u32(sB + (size_t)t * B_TILE), Bb + (long long)t * B_TILE, B_TILE, bFull);
+      bulk_g2s(smem_u32(sB), Bb, (uint32_t)(KX * B_TILE), bFull);
       int issued = 0;
-      for (int i = 0; i < total; ++i) {
-        const int s = i % S, n = i / S;
-        if (i >= S && !mbar_wait(aEmpty + 8 * s, (uint32_t)((n - 1) & 1), abort_flag)) {
+      for (int c = 0; c < nchunk; ++c) {
+        const int s = c % S, n = c / S;
+        if (c >= S && !mbar_wait(aEmpty + 8 * s, (uint32_t)((n - 1) & 1), abort_flag)) {
           *abort_flag = 1;
           atomicExch(P.err, 11);
           break;
         }
-        const int k = i / per_op, rem = i - k * per_op;   // rem = kt * nA + part
-        const uint8_t* src = P.A + (((long long)k * P.m_tiles + mt) * per_op + rem) * A_TILE;
-        mbar_expect_tx(aFull + 8 * s, A_TILE);
-        bulk_g2s(smem_u32(sA + (size_t)s * A_TILE), src, A_TILE, aFull + 8 * s);
+        const int kk = c / cpo, r0 = (c - kk * cpo) * tps;   // tiles [r0, r0 + ntl) of the op
+        const int ntl = min(tps, per_op - r0);
+        const int k = (kk + rot) % P.nops;                    // operator of this step
+        const uint8_t* src = P.A + (((long long)k * P.m_tiles + mt) * per_op + r0) * A_TILE;
+        mbar_expect_tx(aFull + 8 * s, (uint32_t)(ntl * A_TILE));
+        bulk_g2s(smem_u32(sA + (size_t)s * stage_bytes), src, (uint32_t)(ntl * A_TILE), aFull + 8 * s);
         ++issued;
       }
       // tail: every stage released (and, on abort, every copy landed) before the CTA may exit
-      for (int i = (issued > S ? issued - S : 0); i < issued; ++i) {
-        const int s = i % S, n = i / S;
+      for (int c = (issued > S ? issued - S : 0); c < issued; ++c) {
+        const int s = c % S, n = c / S;
         unsigned long long t0 = gtime();
         while (!mbar_try(aFull + 8 * s, (uint32_t)(n & 1)) && gtime() - t0 < kWaitNs) {
         }
@@ -567,7 +580,7 @@ __global__ void __launch_bounds__(192, 1) tc_comb_kernel(TcCombParams P) {
     if (lane == 0) {
       bool ok = mbar_wait(bFull, 0u, abort_flag);
       if (!ok) { *abort_flag = 1; atomicExch(P.err, 12); }
-      int i = 0;
+      int c = 0;
       for (int k = 0; ok && k < P.nops; ++k) {
         const int b = k & 1;
         if (k >= 2 && !mbar_wait(accEmpty + 8 * b, (uint32_t)(((k >> 1) - 1) & 1), abort_flag)) {
@@ -579,17 +592,19 @@ __global__ void __launch_bounds__(192, 1) tc_comb_kernel(TcCombParams P) {
         tc_fence_after();
         bool first = true;
         const uint32_t dst = tmem + (uint32_t)(b * BN);
-        for (int kt = 0; ok && kt < P.kto; ++kt) {
-          for (int part = 0; part < P.nA; ++part, ++i) {
-            const int s = i % S, n = i / S;
-            if (!mbar_wait(aFull + 8 * s, (uint32_t)(n & 1), abort_flag)) {
-              *abort_flag = 1;
-              atomicExch(P.err, 14);
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-            const uint64_t ad = sw128_desc(smem_u32(sA + (size_t)s * A_TILE));
+        for (int cc = 0; ok && cc < cpo; ++cc, ++c) {
+          const int s = c % S, n = c / S;
+          if (!mbar_wait(aFull + 8 * s, (uint32_t)(n & 1), abort_flag)) {
+            *abort_flag = 1;
+            atomicExch(P.err, 14);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int r0 = cc * tps, ntl = min(tps, per_op - r0);
+          for (int t = 0; t < ntl; ++t) {
+            const int rem = r0 + t, kt = rem / P.nA, part = rem - kt * P.nA;
+            const uint64_t ad = sw128_desc(smem_u32(sA + (size_t)s * stage_bytes + (size_t)t * A_TILE));
             // A hi pairs with X hi (and X lo when split); A lo pairs with X hi
             const int nxp = (part == 0) ? P.nX : 1;
             for (int xp = 0; xp < nxp; ++xp) {
@@ -600,8 +615,8 @@ __global__ void __launch_bounds__(192, 1) tc_comb_kernel(TcCombParams P) {
                 first = false;
               }
             }
-            tc_commit(aEmpty + 8 * s);
           }
+          tc_commit(aEmpty + 8 * s);
         }
         if (ok) tc_commit(accFull + 8 * b);
       }
@@ -614,9 +629,10 @@ __global__ void __launch_bounds__(192, 1) tc_comb_kernel(TcCombParams P) {
 #pragma unroll
     for (int j = 0; j < BN; ++j) acc[j] = 0.f;
     bool ok = true;
-    for (int k = 0; k < P.nops; ++k) {
-      const int b = k & 1;
-      if (!mbar_wait(accFull + 8 * b, (uint32_t)((k >> 1) & 1), abort_flag)) {
+    for (int kk = 0; kk < P.nops; ++kk) {
+      const int b = kk & 1;
+      const int k = (kk + rot) % P.nops;
+      if (!mbar_wait(accFull + 8 * b, (uint32_t)((kk >> 1) & 1), abort_flag)) {
         *abort_flag = 1;
         atomicExch(P.err, 15);
         ok = false;
@@ -747,8 +763,8 @@ __global__ void pack_comb_X_kernel(const double* __restrict__ X, long long x_rs,
 }
 
 template <int BN>
-size_t comb_smem_bytes(int kto, int nX, int astages, size_t coef_bytes) {
-  return (size_t)kto * nX * BN * TC_BK * 2 + (size_t)astages * A_TILE + 8 * kCombBars + coef_bytes + 1024;
+size_t comb_smem_bytes(int kto, int nX, int astages, int tps, size_t coef_bytes) {
+  return (size_t)kto * nX * BN * TC_BK * 2 + (size_t)astages * tps * A_TILE + 8 * kCombBars + coef_bytes + 1024;
 }
 
 // ---------------------------------------------------------------- host API
@@ -910,19 +926,30 @@ static size_t comb_coef_bytes(int bn, int nops, bool two_sets) {
   return (size_t)(two_sets ? 2 : 1) * nops * bn * sizeof(float);
 }
 
-static int comb_stages(int bn, int kto, int nX, size_t coef_bytes) {
+// Operator ring of the combine kernel: tiles per stage (as many of one operator's per_op tiles
+// as allow two stages) and the number of stages; stages = 0 when two stages of one tile do not fit.
+static void comb_ring(int bn, int kto, int nX, int per_op, size_t coef_bytes, int* stages, int* tps) {
   const size_t budget = 220 * 1024;
   const size_t b = (size_t)kto * nX * bn * TC_BK * 2 + 8 * kCombBars + coef_bytes + 1024;
-  if (b >= budget) return 0;
-  int st = (int)((budget - b) / A_TILE);
+  *stages = 0;
+  *tps = 1;
+  if (b + 2 * (size_t)A_TILE > budget) return;
+  const size_t avail = budget - b;
+  int t = (int)std::min<size_t>((size_t)per_op, avail / (2 * (size_t)A_TILE));
+  if (t < 1) t = 1;
+  int st = (int)(avail / ((size_t)t * A_TILE));
   if (st > kCombStages) st = kCombStages;
-  return st;
+  *tps = t;
+  *stages = st;
 }
 
 bool tc_comb_fits(int K, int split, long long ncols, int m_tiles, int nops, bool two_sets) {
   const int kto = (K + TC_BK - 1) / TC_BK;
   const int bn = tc_comb_bn(ncols, m_tiles);
-  return comb_stages(bn, kto, split == 3 ? 2 : 1, comb_coef_bytes(bn, nops, two_sets)) >= 2;
+  const int nA = split == 3 ? 2 : 1;
+  int st = 0, tps = 1;
+  comb_ring(bn, kto, nA, kto * nA, comb_coef_bytes(bn, nops, two_sets), &st, &tps);
+  return st >= 2;
 }
 
 fetidp_status tc_comb_pack(Ctx& c, TcComb& op, const double* src0, long long st0, int lda0, int r00, int c00,
@@ -964,7 +991,7 @@ static fetidp_status comb_launch(Ctx& c, const TcComb& op, const TcCombParams& P
     return FETIDP_EINVAL;
   }
   const size_t coef_bytes = comb_coef_bytes(BN, op.nops, op.msplit < op.M);
-  P.astages = comb_stages(BN, op.kto, op.nX, coef_bytes);
+  comb_ring(BN, op.kto, op.nX, op.kto * op.nA, coef_bytes, &P.astages, &P.tps);
   if (P.astages < 2) {
     set_error("combine kernel: operand K too large for shared memory");
     return FETIDP_EINVAL;
@@ -981,7 +1008,7 @@ static fetidp_status comb_launch(Ctx& c, const TcComb& op, const TcCombParams& P
   const double flops = 2.0 * op.M * (double)op.K * op.nops * (double)ncols;
   ProfScope ps(c, FETIDP_K_TC_GEMM, flops,
                (double)op.bytes + (double)b_bytes + (double)ncols * op.M * (P.y_f64 ? 8 : 4));
-  const size_t smem = comb_smem_bytes<BN>(op.kto, op.nX, P.astages, coef_bytes);
+  const size_t smem = comb_smem_bytes<BN>(op.kto, op.nX, P.astages, P.tps, coef_bytes);
   cudaFuncSetAttribute(tc_comb_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid((unsigned)n_tiles, (unsigned)op.m_tiles, 1);
   tc_comb_kernel<BN><<<grid, 192, smem, c.stream>>>(P);
