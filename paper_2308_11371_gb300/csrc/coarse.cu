@@ -177,8 +177,7 @@ inline unsigned grid_exact(long long threads_total, int threads = 256) {
 
 }  // namespace
 
-fetidp_status coarse_setup(Ctx& c, const std::vector<double>& Spp_cells) {
-  using namespace host;
+fetidp_status coarse_setup(Ctx& c, const double* Spp_dev) {
   const int d = c.d;
   CoarseBCR& B = c.bcr;
   // ---- slab axis: longest vertex axis, ties -> highest axis index
@@ -230,131 +229,98 @@ fetidp_status coarse_setup(Ctx& c, const std::vector<double>& Spp_cells) {
     for (int comp = 0; comp < d; ++comp)
       perm[(size_t)vslab[v] * b + vpos[v] * d + comp] = vnum[v] * d + comp;
   }
-  // ---- assemble diagonal blocks A_i and couplings C_i = S(slab i, slab i+1)
-  const size_t bb = (size_t)b * b;
-  std::vector<std::vector<double>> A(nb, std::vector<double>(bb, 0.0));
-  std::vector<std::vector<double>> C(nb > 1 ? nb - 1 : 0, std::vector<double>(bb, 0.0));
-  const int nck = c.ncorner, npc = c.np;
-  for (long long s = 0; s < c.N; ++s) {
-    const int cijk[3] = {(int)(s % c.geo.nc[0]), (int)((s / c.geo.nc[0]) % c.geo.nc[1]),
-                         (int)(s / ((long long)c.geo.nc[0] * c.geo.nc[1]))};
-    long long vid[8];
-    for (int k = 0; k < nck; ++k) {
-      const int o[3] = {k & 1, (k >> 1) & 1, (k >> 2) & 1};
-      long long v = 0, stride = 1;
-      for (int q = 0; q < 3; ++q) {
-        const int coord = cijk[q] + (q < d ? o[q] : 0);
-        v += coord * stride;
-        stride *= vd[q];
-      }
-      vid[k] = v;
-    }
-    const double* S = Spp_cells.data() + (size_t)s * npc * npc;
-    for (int k1 = 0; k1 < nck; ++k1) {
-      if (vnum[vid[k1]] < 0) continue;
-      for (int k2 = 0; k2 < nck; ++k2) {
-        if (vnum[vid[k2]] < 0) continue;
-        const int s1 = vslab[vid[k1]], s2 = vslab[vid[k2]];
-        for (int c1 = 0; c1 < d; ++c1)
-          for (int c2 = 0; c2 < d; ++c2) {
-            const double val = S[(size_t)(k1 * d + c1) * npc + k2 * d + c2];
-            const int r = vpos[vid[k1]] * d + c1, q = vpos[vid[k2]] * d + c2;
-            if (s1 == s2) A[s1][(size_t)r * b + q] += val;
-            else if (s2 == s1 + 1) C[s1][(size_t)r * b + q] += val;
-          }
-      }
-    }
-  }
-  // ---- block cyclic reduction, host FP64
-  struct Lvl {
-    int n;
-    std::vector<long long> oA, oU, oUT, oV, oVT;
-  };
-  std::vector<Lvl> lv;
-  std::vector<double> pool;   // matrices appended here
-  auto push = [&](const std::vector<double>& M) {
-    const long long off = (long long)pool.size();
-    pool.insert(pool.end(), M.begin(), M.end());
-    return off;
-  };
-  int n = nb;
-  bool ok = true;
-  std::vector<std::vector<double>> Acur = std::move(A), Ccur = std::move(C);
-  while (n > 1) {
-    Lvl L;
-    L.n = n;
-    L.oA.assign(n, -1); L.oU.assign(n, -1); L.oUT.assign(n, -1); L.oV.assign(n, -1); L.oVT.assign(n, -1);
-    std::vector<std::vector<double>> Ainv(n), U(n), V(n);
-    std::vector<char> fail(n, 0);
-    parallel_for(n / 2, [&](int q) {
-      const int j = 2 * q + 1;
-      Ainv[j].assign(bb, 0.0);
-      if (!spd_inverse(b, Acur[j].data(), b, Ainv[j].data(), b)) { fail[j] = 1; return; }
-      V[j].assign(bb, 0.0);   // V_j = Ainv_j C_{j-1}^T
-      gemm(false, true, b, b, b, 1.0, Ainv[j].data(), b, Ccur[j - 1].data(), b, 0.0, V[j].data(), b);
-      if (j + 1 < n) {        // U_j = Ainv_j C_j
-        U[j].assign(bb, 0.0);
-        gemm(false, false, b, b, b, 1.0, Ainv[j].data(), b, Ccur[j].data(), b, 0.0, U[j].data(), b);
-      }
-    });
-    for (int j = 1; j < n; j += 2) ok = ok && !fail[j];
-    if (!ok) break;
-    const int nn = (n + 1) / 2;
-    std::vector<std::vector<double>> An(nn), Cn(nn > 1 ? nn - 1 : 0);
-    parallel_for(nn, [&](int q) {
-      const int i = 2 * q;
-      An[q] = Acur[i];
-      if (i - 1 >= 0)   // - C_{i-1}^T U_{i-1}
-        gemm(true, false, b, b, b, -1.0, Ccur[i - 1].data(), b, U[i - 1].data(), b, 1.0, An[q].data(), b);
-      if (i + 1 < n)    // - C_i V_{i+1}
-        gemm(false, false, b, b, b, -1.0, Ccur[i].data(), b, V[i + 1].data(), b, 1.0, An[q].data(), b);
-      if (i + 2 < n) {  // C'_q = - C_i U_{i+1}
-        Cn[q].assign(bb, 0.0);
-        gemm(false, false, b, b, b, -1.0, Ccur[i].data(), b, U[i + 1].data(), b, 0.0, Cn[q].data(), b);
-      }
-    });
-    // symmetrise the reduced diagonal blocks against rounding drift
-    for (int q = 0; q < nn; ++q)
-      for (int r = 0; r < b; ++r)
-        for (int s2 = r + 1; s2 < b; ++s2) {
-          const double avg = 0.5 * (An[q][(size_t)r * b + s2] + An[q][(size_t)s2 * b + r]);
-          An[q][(size_t)r * b + s2] = avg;
-          An[q][(size_t)s2 * b + r] = avg;
-        }
+  // ---- level structure and the device pool: per level l with n_l blocks, regions
+  //      A (Ainv at odd slots after the level), U, U^T, V, V^T of n_l blocks each; the reduced
+  //      block of the last level (then its inverse) follows.
+  const long long bb = (long long)b * b;
+  std::vector<int> nl;
+  for (int n = nb; n > 1; n = (n + 1) / 2) nl.push_back(n);
+  const int levels = (int)nl.size();
+  std::vector<long long> base(levels + 1, 0);
+  for (int l = 0; l < levels; ++l) base[l + 1] = base[l] + 5LL * nl[l] * bb;
+  const long long pool = base[levels] + bb;
+  FD_TRY(dalloc_t(c, &B.mats, (size_t)pool));
+  B.mat_bytes = (size_t)pool * sizeof(double);
+  double* P = B.mats;
+  double *Cbuf[2] = {nullptr, nullptr}, *work = nullptr;
+  int *vslab_d = nullptr, *vpos_d = nullptr, *st_d = nullptr;
+  const long long cmax = nb > 1 ? (long long)(nb - 1) * bb : bb;
+  FD_CUDA(cudaMalloc(&Cbuf[0], sizeof(double) * cmax));
+  FD_CUDA(cudaMalloc(&Cbuf[1], sizeof(double) * cmax));
+  FD_CUDA(cudaMalloc(&work, sizeof(double) * 2 * (size_t)(nb / 2 + 1) * (b + 1)));
+  FD_CUDA(cudaMalloc(&vslab_d, sizeof(int) * nvert));
+  FD_CUDA(cudaMalloc(&vpos_d, sizeof(int) * nvert));
+  FD_CUDA(cudaMalloc(&st_d, sizeof(int)));
+  FD_CUDA(cudaMemcpyAsync(vslab_d, vslab.data(), sizeof(int) * nvert, cudaMemcpyHostToDevice, c.stream));
+  FD_CUDA(cudaMemcpyAsync(vpos_d, vpos.data(), sizeof(int) * nvert, cudaMemcpyHostToDevice, c.stream));
+  FD_CUDA(cudaMemsetAsync(st_d, 0, sizeof(int), c.stream));
+  FD_CUDA(cudaMemsetAsync(P, 0, sizeof(double) * (size_t)nb * bb, c.stream));
+  FD_CUDA(cudaMemsetAsync(Cbuf[0], 0, sizeof(double) * cmax, c.stream));
+  // ---- diagonal blocks A_i and couplings C_i = S(slab i, slab i+1) from the per-cell S_pp
+  FD_TRY(k_coarse_assemble(c, Spp_dev, vslab_d, vpos_d, b, P + base[0], Cbuf[0]));
+  // ---- block cyclic reduction on the device
+  B.off_Ainv.assign(levels, {}); B.off_U.assign(levels, {}); B.off_UT.assign(levels, {});
+  B.off_V.assign(levels, {}); B.off_VT.assign(levels, {});
+  fetidp_status st = FETIDP_OK;
+  for (int l = 0; l < levels && st == FETIDP_OK; ++l) {
+    const int n = nl[l], nn = (n + 1) / 2;
+    double* Al = P + base[l];
+    double* Ul = Al + n * bb;
+    double* UTl = Al + 2 * n * bb;
+    double* Vl = Al + 3 * n * bb;
+    double* VTl = Al + 4 * n * bb;
+    double* An = P + base[l + 1];
+    double* Cl = Cbuf[l & 1];
+    double* Cn = Cbuf[(l + 1) & 1];
+    const int nodd = n / 2, nu = (n - 1) / 2;
+    // Ainv_j (odd j) in place; V_j = Ainv_j C_{j-1}^T; U_j = Ainv_j C_j (j + 1 < n)
+    st = k_spd_inverse_batched(c, Al + bb, 2 * bb, b, b, nodd, work, st_d);
+    if (st == FETIDP_OK)
+      st = k_batched_gemm(c, false, true, b, b, b, 1.0, Al + bb, 2 * bb, b, Cl, 2 * bb, b, 0.0, Vl + bb, 2 * bb, b, nodd);
+    if (st == FETIDP_OK)
+      st = k_batched_gemm(c, false, false, b, b, b, 1.0, Al + bb, 2 * bb, b, Cl + bb, 2 * bb, b, 0.0, Ul + bb, 2 * bb,
+                          b, nu);
+    if (st == FETIDP_OK)
+      st = k_batched_block_copy(c, Vl + bb, 2 * bb, b, 0, 0, VTl + bb, 2 * bb, b, b, b, nodd, true);
+    if (st == FETIDP_OK)
+      st = k_batched_block_copy(c, Ul + bb, 2 * bb, b, 0, 0, UTl + bb, 2 * bb, b, b, b, nu, true);
+    // A'_q = A_2q - C_{2q-1}^T U_{2q-1} - C_2q V_{2q+1};  C'_q = - C_2q U_{2q+1}
+    if (st == FETIDP_OK) st = k_batched_block_copy(c, Al, 2 * bb, b, 0, 0, An, bb, b, b, b, nn, false);
+    if (st == FETIDP_OK)
+      st = k_batched_gemm(c, true, false, b, b, b, -1.0, Cl + bb, 2 * bb, b, Ul + bb, 2 * bb, b, 1.0, An + bb, bb, b,
+                          nn - 1);
+    if (st == FETIDP_OK)
+      st = k_batched_gemm(c, false, false, b, b, b, -1.0, Cl, 2 * bb, b, Vl + bb, 2 * bb, b, 1.0, An, bb, b, nodd);
+    if (st == FETIDP_OK && nn > 1)
+      st = k_batched_gemm(c, false, false, b, b, b, -1.0, Cl, 2 * bb, b, Ul + bb, 2 * bb, b, 0.0, Cn, bb, b, nu);
+    if (st == FETIDP_OK) st = k_batched_symmetrize(c, An, bb, b, b, nn);   // against rounding drift
+    std::vector<long long> oA(n, -1), oU(n, -1), oUT(n, -1), oV(n, -1), oVT(n, -1);
     for (int j = 1; j < n; j += 2) {
-      L.oA[j] = push(Ainv[j]);
-      L.oV[j] = push(V[j]);
-      std::vector<double> T(bb);
-      for (int r = 0; r < b; ++r)
-        for (int s2 = 0; s2 < b; ++s2) T[(size_t)s2 * b + r] = V[j][(size_t)r * b + s2];
-      L.oVT[j] = push(T);
+      oA[j] = base[l] + j * bb;
+      oV[j] = base[l] + 3 * n * bb + j * bb;
+      oVT[j] = base[l] + 4 * n * bb + j * bb;
       if (j + 1 < n) {
-        L.oU[j] = push(U[j]);
-        for (int r = 0; r < b; ++r)
-          for (int s2 = 0; s2 < b; ++s2) T[(size_t)s2 * b + r] = U[j][(size_t)r * b + s2];
-        L.oUT[j] = push(T);
+        oU[j] = base[l] + n * bb + j * bb;
+        oUT[j] = base[l] + 2 * n * bb + j * bb;
       }
     }
-    lv.push_back(std::move(L));
-    Acur = std::move(An);
-    Ccur = std::move(Cn);
-    n = nn;
+    B.off_Ainv[l] = oA; B.off_U[l] = oU; B.off_UT[l] = oUT; B.off_V[l] = oV; B.off_VT[l] = oVT;
   }
-  if (!ok) {
+  if (st == FETIDP_OK) st = k_spd_inverse_batched(c, P + base[levels], bb, b, b, 1, work, st_d);
+  int hst = 0;
+  if (st == FETIDP_OK) {
+    FD_CUDA(cudaMemcpyAsync(&hst, st_d, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    FD_CUDA(cudaStreamSynchronize(c.stream));
+  }
+  cudaFree(Cbuf[0]); cudaFree(Cbuf[1]); cudaFree(work); cudaFree(vslab_d); cudaFree(vpos_d); cudaFree(st_d);
+  FD_TRY(st);
+  if (hst != 0) {
     set_error("coarse S_PP is not positive definite");
     return FETIDP_ESINGULAR;
   }
-  {
-    std::vector<double> Af(bb);
-    if (!spd_inverse(b, Acur[0].data(), b, Af.data(), b)) {
-      set_error("coarse S_PP is not positive definite");
-      return FETIDP_ESINGULAR;
-    }
-    B.off_final = push(Af);
-  }
-  B.levels = (int)lv.size();
-  B.n_at.clear();
-  for (auto& L : lv) B.n_at.push_back(L.n);
+  B.off_final = base[levels];
+  B.levels = levels;
+  B.n_at.assign(nl.begin(), nl.end());
   B.n_at.push_back(1);
   B.vec_off.assign(B.levels + 1, 0);
   long long acc = 0;
@@ -363,29 +329,19 @@ fetidp_status coarse_setup(Ctx& c, const std::vector<double>& Spp_cells) {
     acc += (long long)B.n_at[l] * b;
   }
   B.vec_len = acc;
-  // offset tables appended after the matrices as raw long longs (device side)
+  // offset tables (device): per level the A, U, UT, V, VT arrays of n entries
   std::vector<long long> tab;
-  B.off_Ainv.assign(B.levels, {}); B.off_U.assign(B.levels, {}); B.off_UT.assign(B.levels, {});
-  B.off_V.assign(B.levels, {}); B.off_VT.assign(B.levels, {});
-  for (int l = 0; l < B.levels; ++l) {
-    B.off_Ainv[l] = lv[l].oA; B.off_U[l] = lv[l].oU; B.off_UT[l] = lv[l].oUT;
-    B.off_V[l] = lv[l].oV; B.off_VT[l] = lv[l].oVT;
-    for (auto* v : {&lv[l].oA, &lv[l].oU, &lv[l].oUT, &lv[l].oV, &lv[l].oVT})
+  for (int l = 0; l < B.levels; ++l)
+    for (auto* v : {&B.off_Ainv[l], &B.off_U[l], &B.off_UT[l], &B.off_V[l], &B.off_VT[l]})
       tab.insert(tab.end(), v->begin(), v->end());
-  }
-  B.mat_bytes = pool.size() * sizeof(double);
-  FD_TRY(dalloc_t(c, &B.mats, pool.size()));
-  FD_CUDA(cudaMemcpyAsync(B.mats, pool.data(), B.mat_bytes, cudaMemcpyHostToDevice, c.stream));
   FD_TRY(dalloc_t(c, &B.tables, tab.size() + 1));
   if (!tab.empty())
-    FD_CUDA(cudaMemcpyAsync(B.tables, tab.data(), tab.size() * sizeof(long long),
-                            cudaMemcpyHostToDevice, c.stream));
+    FD_CUDA(cudaMemcpyAsync(B.tables, tab.data(), tab.size() * sizeof(long long), cudaMemcpyHostToDevice, c.stream));
   FD_TRY(dalloc_t(c, &B.perm, perm.size()));
-  FD_CUDA(cudaMemcpyAsync(B.perm, perm.data(), perm.size() * sizeof(int), cudaMemcpyHostToDevice,
-                          c.stream));
+  FD_CUDA(cudaMemcpyAsync(B.perm, perm.data(), perm.size() * sizeof(int), cudaMemcpyHostToDevice, c.stream));
   FD_TRY(dalloc_t(c, &B.bl, (size_t)c.m * B.vec_len));
   FD_TRY(dalloc_t(c, &B.xl, (size_t)c.m * B.vec_len));
-  FD_CUDA(cudaStreamSynchronize(c.stream));   // host pool / tables go out of scope
+  FD_CUDA(cudaStreamSynchronize(c.stream));   // host tables go out of scope
   return FETIDP_OK;
 }
 

@@ -305,6 +305,13 @@ fetidp_status k_batched_block_copy(Ctx& c, const double* in, long long si, int l
                                    long long so, int ldo, int M, int N, int batch, bool transpose);
 fetidp_status k_df_gemm(Ctx& c, const double* A, int lda, int M, int K, const double* X, int x_cs, long long ncols,
                         double* Y, int y_cs);
+fetidp_status k_batched_gemm(Ctx& c, bool ta, bool tb, int M, int N, int K, double alpha, const double* A,
+                             long long sa, int lda, const double* B, long long sb, int ldb, double beta, double* C,
+                             long long sc, int ldc, int batch);
+fetidp_status k_batched_symmetrize(Ctx& c, double* A, long long stride, int n, int lda, int batch);
+fetidp_status k_spp_cells(Ctx& c, const double* Kpp, const double* P, double* out);
+fetidp_status k_coarse_assemble(Ctx& c, const double* Spp, const int* vslab, const int* vpos, int b, double* A,
+                                double* C);
 fetidp_status k_batched_diag_sum(Ctx& c, const double* A, long long stride, int lda, int r0, int m, int batch,
                                  double* out);
 fetidp_status k_apply_K(Ctx& c, CCellVec u, CellVec y, int nvec_per_col, int ncols, bool idp,
@@ -351,7 +358,7 @@ fetidp_status tc_comb_apply(Ctx& c, const TcComb& op, CCellVec X, const double* 
 
 // ---------------------------------------------------------------- setup / coarse
 fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_options& o);
-fetidp_status coarse_setup(Ctx& c, const std::vector<double>& Spp_cells);
+fetidp_status coarse_setup(Ctx& c, const double* Spp_dev);   // per-cell S_pp_ring on the device
 fetidp_status coarse_solve(Ctx& c, const double* b, long long b_rs, double* x, long long x_rs,
                            int nrhs);
 

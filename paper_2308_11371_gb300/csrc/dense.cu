@@ -225,6 +225,147 @@ __global__ void batched_diag_sum_kernel(const double* __restrict__ A, long long 
   if (lane == 0) out[w] = s;
 }
 
+// C_b = alpha op(A_b) op(B_b) + beta C_b, op = identity or transpose, row-major operands.
+// 32 x 32 output tile per block, 2 x 2 per thread, K chunks of 16 staged in shared memory.
+constexpr int BG_T = 32, BG_K = 16;
+__global__ void __launch_bounds__(256) batched_gemm_kernel(bool ta, bool tb, int M, int N, int K, double alpha,
+                                                           const double* __restrict__ A, long long sa, int lda,
+                                                           const double* __restrict__ B, long long sb, int ldb,
+                                                           double beta, double* __restrict__ C, long long sc, int ldc) {
+  __shared__ double As[BG_K][BG_T + 1];
+  __shared__ double Bs[BG_K][BG_T + 1];
+  const int bz = blockIdx.z;
+  const double* Ab = A + bz * sa;
+  const double* Bb = B + bz * sb;
+  double* Cb = C + bz * sc;
+  const int m0 = blockIdx.y * BG_T, n0 = blockIdx.x * BG_T;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int k0 = 0; k0 < K; k0 += BG_K) {
+    for (int t = threadIdx.x; t < BG_K * BG_T; t += 256) {
+      // op(A)[m][k]: m = m0 + r, k = k0 + q
+      {
+        int r, q;
+        if (ta) { q = t / BG_T; r = t - q * BG_T; }   // A[k][m]: m fastest
+        else { r = t / BG_K; q = t - r * BG_K; }      // A[m][k]: k fastest
+        const int gm = m0 + r, gk = k0 + q;
+        double v = 0.0;
+        if (gm < M && gk < K) v = ta ? Ab[(long long)gk * lda + gm] : Ab[(long long)gm * lda + gk];
+        As[q][r] = v;
+      }
+      // op(B)[k][n]: n = n0 + r
+      {
+        int r, q;
+        if (tb) { r = t / BG_K; q = t - r * BG_K; }   // B[n][k]: k fastest
+        else { q = t / BG_T; r = t - q * BG_T; }      // B[k][n]: n fastest
+        const int gn = n0 + r, gk = k0 + q;
+        double v = 0.0;
+        if (gn < N && gk < K) v = tb ? Bb[(long long)gn * ldb + gk] : Bb[(long long)gk * ldb + gn];
+        Bs[q][r] = v;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < BG_K; ++q) {
+      const double a0 = As[q][ty], a1 = As[q][ty + 16];
+      const double b0 = Bs[q][tx], b1 = Bs[q][tx + 16];
+      acc[0][0] = fma(a0, b0, acc[0][0]);
+      acc[0][1] = fma(a0, b1, acc[0][1]);
+      acc[1][0] = fma(a1, b0, acc[1][0]);
+      acc[1][1] = fma(a1, b1, acc[1][1]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
+      if (gm < M && gn < N) {
+        double* cp = Cb + (long long)gm * ldc + gn;
+        *cp = (beta == 0.0) ? alpha * acc[i][j] : fma(alpha, acc[i][j], beta * (*cp));
+      }
+    }
+}
+
+// A_b <- (A_b + A_b^T) / 2.
+__global__ void batched_symmetrize_kernel(double* __restrict__ A, long long stride, int n, int lda, int batch) {
+  const long long total = (long long)batch * n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / ((long long)n * n));
+    const int r = (int)(t - (long long)b * n * n);
+    const int i = r / n, j = r - (r / n) * n;
+    if (j <= i) continue;
+    double* Ab = A + b * stride;
+    const double v = 0.5 * (Ab[(long long)i * lda + j] + Ab[(long long)j * lda + i]);
+    Ab[(long long)i * lda + j] = v;
+    Ab[(long long)j * lda + i] = v;
+  }
+}
+
+// Per-cell S_pp_ring (Eq. 43): sym( sum_k alpha_k K_pp^(k) - sum_{k,j} alpha_k pi_j P_kj ),
+// P_kj = K_rp^(k)T U_rp^(j).  One thread per (cell, r <= q).
+__global__ void spp_cells_kernel(const double* __restrict__ alpha, const double* __restrict__ pi,
+                                 const double* __restrict__ Kpp, const double* __restrict__ P, int nrb, int np,
+                                 long long ncell, double* __restrict__ out) {
+  const int npp = np * np;
+  const long long total = ncell * npp;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long s = t / npp;
+    const int rq = (int)(t - s * npp), r = rq / np, q = rq - (rq / np) * np;
+    if (q < r) continue;
+    const double* a = alpha + s * nrb;
+    const double* p = pi + s * nrb;
+    double x_rq = 0.0, x_qr = 0.0;
+    for (int k = 0; k < nrb; ++k) {
+      const double ak = a[k];
+      double w_rq = Kpp[(long long)k * npp + r * np + q], w_qr = Kpp[(long long)k * npp + q * np + r];
+      const double* Pk = P + (long long)k * nrb * npp;
+      for (int j = 0; j < nrb; ++j) {
+        w_rq -= p[j] * Pk[(long long)j * npp + r * np + q];
+        w_qr -= p[j] * Pk[(long long)j * npp + q * np + r];
+      }
+      x_rq += ak * w_rq;
+      x_qr += ak * w_qr;
+    }
+    const double v = 0.5 * (x_rq + x_qr);
+    out[s * npp + r * np + q] = v;
+    out[s * npp + q * np + r] = v;
+  }
+}
+
+// Slab blocks of S_PP from the per-cell S_pp_ring: diagonal blocks A_i (slab i) and couplings
+// C_i = S(slab i, slab i + 1).  One thread per (cell, corner k1, corner k2).
+__global__ void coarse_assemble_kernel(const double* __restrict__ Spp, long long ncell, int d, int nck, int np,
+                                       int ncx, int ncy, int vdx, int vdy, const int* __restrict__ vslab,
+                                       const int* __restrict__ vpos, int b, double* __restrict__ A,
+                                       double* __restrict__ C) {
+  const long long total = ncell * nck * nck;
+  const long long bb = (long long)b * b;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long s = t / (nck * nck);
+    const int kk = (int)(t - s * nck * nck), k1 = kk / nck, k2 = kk - (kk / nck) * nck;
+    const int cx = (int)(s % ncx), cy = (int)((s / ncx) % ncy), cz = (int)(s / ((long long)ncx * ncy));
+    const long long v1 = (cx + (k1 & 1)) + (long long)vdx * ((cy + ((k1 >> 1) & 1)) + (long long)vdy * (cz + (d == 3 ? ((k1 >> 2) & 1) : 0)));
+    const long long v2 = (cx + (k2 & 1)) + (long long)vdx * ((cy + ((k2 >> 1) & 1)) + (long long)vdy * (cz + (d == 3 ? ((k2 >> 2) & 1) : 0)));
+    const int s1 = vslab[v1], s2 = vslab[v2];
+    if (s1 < 0 || s2 < 0) continue;                 // clamped vertex
+    double* dst;
+    if (s1 == s2) dst = A + s1 * bb;
+    else if (s2 == s1 + 1) dst = C + s1 * bb;
+    else continue;
+    const double* S = Spp + s * (long long)np * np;
+    for (int c1 = 0; c1 < d; ++c1)
+      for (int c2 = 0; c2 < d; ++c2) {
+        const int r = vpos[v1] * d + c1, q = vpos[v2] * d + c2;
+        atomicAdd(dst + (long long)r * b + q, S[(k1 * d + c1) * np + k2 * d + c2]);
+      }
+  }
+}
+
 // Y[cell][m] = sum_k A[m][k] X[cell][k] in double-float arithmetic on the FP32 pipe (GB300
 // issues FP32 at ~60x its FP64 rate).  Each FP64 operand is split into hi + lo floats (48
 // significant bits); a product is hi*hi, made exact by an FMA residual, plus the cross terms;
@@ -362,6 +503,41 @@ fetidp_status k_df_gemm(Ctx& c, const double* A, int lda, int M, int K, const do
   ProfScope ps(c, FETIDP_K_SETUP, 2.0 * M * (double)K * ncols, 8.0 * ((double)M * K + (double)ncols * (K + M)));
   const dim3 grid((unsigned)((ncols + DF_T - 1) / DF_T), (unsigned)((M + DF_T - 1) / DF_T));
   df_gemm_kernel<<<grid, 256, 0, c.stream>>>(A, lda, M, K, X, x_cs, ncols, Y, y_cs);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_batched_gemm(Ctx& c, bool ta, bool tb, int M, int N, int K, double alpha, const double* A,
+                             long long sa, int lda, const double* B, long long sb, int ldb, double beta, double* C,
+                             long long sc, int ldc, int batch) {
+  if (batch <= 0) return FETIDP_OK;
+  ProfScope ps(c, FETIDP_K_SETUP, 2.0 * batch * (double)M * N * K, 8.0 * batch * ((double)M * K + (double)K * N));
+  const dim3 grid((unsigned)((N + BG_T - 1) / BG_T), (unsigned)((M + BG_T - 1) / BG_T), (unsigned)batch);
+  batched_gemm_kernel<<<grid, 256, 0, c.stream>>>(ta, tb, M, N, K, alpha, A, sa, lda, B, sb, ldb, beta, C, sc, ldc);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_batched_symmetrize(Ctx& c, double* A, long long stride, int n, int lda, int batch) {
+  if (batch <= 0) return FETIDP_OK;
+  batched_symmetrize_kernel<<<grid_for((long long)batch * n * n, 256), 256, 0, c.stream>>>(A, stride, n, lda, batch);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_spp_cells(Ctx& c, const double* Kpp, const double* P, double* out) {
+  const int np = c.np;
+  spp_cells_kernel<<<grid_for(c.N * np * np, 256), 256, 0, c.stream>>>(c.alpha, c.pi, Kpp, P, c.nrb, np, c.N, out);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_coarse_assemble(Ctx& c, const double* Spp, const int* vslab, const int* vpos, int b, double* A,
+                                double* C) {
+  const int nck = 1 << c.d;
+  const int vdx = c.geo.nc[0] + 1, vdy = c.geo.nc[1] + 1;
+  coarse_assemble_kernel<<<grid_for(c.N * nck * nck, 256), 256, 0, c.stream>>>(
+      Spp, c.N, c.d, nck, c.np, c.geo.nc[0], c.geo.nc[1], vdx, vdy, vslab, vpos, b, A, C);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }

@@ -433,8 +433,8 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
   const int nr = c.nr, ni = c.ni, nd = c.nd, np = c.np;
   // All on the device: the principal K blocks assembled from their C_hat snapshots, K_rr^{-1} and
   // S_dd = F_dd^{-1} (F_dd = T_dr K_rr^{-1} T_rd, Sec. 3.1.1) by batched sweeps, U_rp = K_rr^{-1} K_rp.
-  std::vector<double> hUrp((size_t)nrb * nr * np), hKpp((size_t)nrb * np * np), hKrp((size_t)nrb * nr * np),
-      dvec(nrb, 0.0);
+  std::vector<double> dvec(nrb, 0.0);
+  double *Krp_d = nullptr, *Kpp_d = nullptr;   // principal K_rp, K_pp: kept for S_pp_ring (Eq. 43)
   {
     FD_TRY(dalloc_t(c, &c.Kinv, (size_t)nrb * nr * nr));
     FD_TRY(dalloc_t(c, &c.Urp, (size_t)nrb * nr * np));
@@ -442,7 +442,7 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
     FD_TRY(dalloc_t(c, &c.Sdd, (size_t)nrb * nd * nd));
     int* sigma_dev = nullptr;
     int* st_dev = nullptr;
-    double *Krp_d = nullptr, *Kpp_d = nullptr, *work = nullptr, *dvec_d = nullptr;
+    double *work = nullptr, *dvec_d = nullptr;
     FD_CUDA(cudaMalloc(&sigma_dev, sizeof(int) * nrb));
     FD_CUDA(cudaMalloc(&st_dev, sizeof(int)));
     FD_CUDA(cudaMalloc(&Krp_d, sizeof(double) * (size_t)nrb * nr * np));
@@ -462,14 +462,15 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
                                 nrb, false));
     FD_TRY(k_spd_inverse_batched(c, c.Sdd, (long long)nd * nd, nd, nd, nrb, work, st_dev));
     int hst = 0;
-    FD_CUDA(cudaMemcpyAsync(hUrp.data(), c.Urp, sizeof(double) * hUrp.size(), cudaMemcpyDeviceToHost, c.stream));
-    FD_CUDA(cudaMemcpyAsync(hKrp.data(), Krp_d, sizeof(double) * hKrp.size(), cudaMemcpyDeviceToHost, c.stream));
-    FD_CUDA(cudaMemcpyAsync(hKpp.data(), Kpp_d, sizeof(double) * hKpp.size(), cudaMemcpyDeviceToHost, c.stream));
     FD_CUDA(cudaMemcpyAsync(dvec.data(), dvec_d, sizeof(double) * nrb, cudaMemcpyDeviceToHost, c.stream));
     FD_CUDA(cudaMemcpyAsync(&hst, st_dev, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     FD_CUDA(cudaStreamSynchronize(c.stream));
-    cudaFree(sigma_dev); cudaFree(st_dev); cudaFree(Krp_d); cudaFree(Kpp_d); cudaFree(work); cudaFree(dvec_d);
-    if (hst != 0) { set_error("principal K_rr is not positive definite"); return FETIDP_ESINGULAR; }
+    cudaFree(sigma_dev); cudaFree(st_dev); cudaFree(work); cudaFree(dvec_d);
+    if (hst != 0) {
+      cudaFree(Krp_d); cudaFree(Kpp_d);
+      set_error("principal K_rr is not positive definite");
+      return FETIDP_ESINGULAR;
+    }
   }
   phase("principal factorisations");
 
@@ -577,32 +578,23 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
 
   // ---------------------------------------------------------------- coarse S_PP (Eq. 43, Sec. 3.2.1)
   {
-    // P_kj = K_rp^(k)T U_rp^(j)
-    std::vector<double> P((size_t)nrb * nrb * np * np);
-    for (int k = 0; k < nrb; ++k)
-      for (int j = 0; j < nrb; ++j)
-        gemm(true, false, np, np, nr, 1.0, hKrp.data() + (size_t)k * nr * np, np,
-             hUrp.data() + (size_t)j * nr * np, np, 0.0, P.data() + ((size_t)k * nrb + j) * np * np, np);
-    std::vector<double> Spp((size_t)c.N * np * np);
-    parallel_for((int)c.N, [&](int s) {
-      const double* a = h_alpha.data() + (size_t)s * nrb;
-      const double* pv = h_pi.data() + (size_t)s * nrb;
-      std::vector<double> X((size_t)np * np, 0.0);
-      for (int k = 0; k < nrb; ++k) {
-        const double* Kpp = hKpp.data() + (size_t)k * np * np;
-        for (int q = 0; q < np * np; ++q) X[q] += a[k] * Kpp[q];
-        for (int j = 0; j < nrb; ++j) {
-          const double* Pk = P.data() + ((size_t)k * nrb + j) * np * np;
-          const double w = a[k] * pv[j];
-          for (int q = 0; q < np * np; ++q) X[q] -= w * Pk[q];
-        }
-      }
-      double* out = Spp.data() + (size_t)s * np * np;
-      for (int r = 0; r < np; ++r)
-        for (int q = 0; q < np; ++q) out[(size_t)r * np + q] = 0.5 * (X[(size_t)r * np + q] + X[(size_t)q * np + r]);
-    });
-    phase("S_pp per cell");
-    FD_TRY(coarse_setup(c, Spp));
+    // P_kj = K_rp^(k)T U_rp^(j), then per cell S_pp_ring = sym(K_pp_ring - K_rp_ring^T U_rp_ring)
+    double *Pkj = nullptr, *Spp = nullptr;
+    fetidp_status st = FETIDP_OK;
+    if (cudaMalloc(&Pkj, sizeof(double) * (size_t)nrb * nrb * np * np) != cudaSuccess ||
+        cudaMalloc(&Spp, sizeof(double) * (size_t)c.N * np * np) != cudaSuccess) {
+      set_error("cudaMalloc failed for the coarse setup");
+      st = FETIDP_ENOMEM;
+    }
+    for (int k = 0; k < nrb && st == FETIDP_OK; ++k)
+      st = k_batched_gemm(c, true, false, np, np, nr, 1.0, Krp_d + (size_t)k * nr * np, 0, np, c.Urp, (long long)nr * np,
+                          np, 0.0, Pkj + (size_t)k * nrb * np * np, (long long)np * np, np, nrb);
+    if (st == FETIDP_OK) st = k_spp_cells(c, Kpp_d, Pkj, Spp);
+    if (st == FETIDP_OK) phase("S_pp per cell");
+    if (st == FETIDP_OK) st = coarse_setup(c, Spp);
+    cudaStreamSynchronize(c.stream);
+    cudaFree(Pkj); cudaFree(Spp); cudaFree(Krp_d); cudaFree(Kpp_d);
+    FD_TRY(st);
     phase("coarse factorisation");
   }
 
