@@ -245,12 +245,12 @@ fetidp_status coarse_setup(Ctx& c, const double* Spp_dev) {
   double *Cbuf[2] = {nullptr, nullptr}, *work = nullptr;
   int *vslab_d = nullptr, *vpos_d = nullptr, *st_d = nullptr;
   const long long cmax = nb > 1 ? (long long)(nb - 1) * bb : bb;
-  FD_CUDA(cudaMalloc(&Cbuf[0], sizeof(double) * cmax));
-  FD_CUDA(cudaMalloc(&Cbuf[1], sizeof(double) * cmax));
-  FD_CUDA(cudaMalloc(&work, sizeof(double) * 2 * (size_t)(nb / 2 + 1) * (b + 1)));
-  FD_CUDA(cudaMalloc(&vslab_d, sizeof(int) * nvert));
-  FD_CUDA(cudaMalloc(&vpos_d, sizeof(int) * nvert));
-  FD_CUDA(cudaMalloc(&st_d, sizeof(int)));
+  FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Cbuf[0]), sizeof(double) * cmax));
+  FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Cbuf[1]), sizeof(double) * cmax));
+  FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&work), sizeof(double) * 2 * (size_t)(nb / 2 + 1) * (b + 1)));
+  FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&vslab_d), sizeof(int) * nvert));
+  FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&vpos_d), sizeof(int) * nvert));
+  FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&st_d), sizeof(int)));
   FD_CUDA(cudaMemcpyAsync(vslab_d, vslab.data(), sizeof(int) * nvert, cudaMemcpyHostToDevice, c.stream));
   FD_CUDA(cudaMemcpyAsync(vpos_d, vpos.data(), sizeof(int) * nvert, cudaMemcpyHostToDevice, c.stream));
   FD_CUDA(cudaMemsetAsync(st_d, 0, sizeof(int), c.stream));
@@ -312,7 +312,7 @@ fetidp_status coarse_setup(Ctx& c, const double* Spp_dev) {
     FD_CUDA(cudaMemcpyAsync(&hst, st_d, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     FD_CUDA(cudaStreamSynchronize(c.stream));
   }
-  cudaFree(Cbuf[0]); cudaFree(Cbuf[1]); cudaFree(work); cudaFree(vslab_d); cudaFree(vpos_d); cudaFree(st_d);
+  tmp_free(c, Cbuf[0]); tmp_free(c, Cbuf[1]); tmp_free(c, work); tmp_free(c, vslab_d); tmp_free(c, vpos_d); tmp_free(c, st_d);
   FD_TRY(st);
   if (hst != 0) {
     set_error("coarse S_PP is not positive definite");

@@ -12,6 +12,10 @@
 namespace fetidp {
 
 void set_error(const std::string& msg);
+struct Ctx;
+// stream-ordered temporaries of the setup phase (not tracked by the context)
+fetidp_status tmp_alloc(Ctx& c, void** p, size_t bytes);
+void tmp_free(Ctx& c, void* p);
 void count_launch();
 
 #define FD_CUDA(call)                                                        \
@@ -295,6 +299,20 @@ fetidp_status k_copy_scale(Ctx& c, const double* x, double* y, long long len, in
 
 // ---------------------------------------------------------------- kernels (cell-level compute)
 fetidp_status k_snapshots(Ctx& c);
+// Device state of the greedy loop (Algorithm 4): selected cells and a stop flag.
+constexpr int kMaxRbGreedy = 64;
+struct GreedyState {
+  int stop;
+  int count;
+  int sigma[kMaxRbGreedy];
+};
+fetidp_status k_greedy_step(Ctx& c, double* D, const double* zeta, long long rows, long long len, double* beta,
+                            double* inf, const GreedyState* st, int i);
+fetidp_status k_greedy_select(Ctx& c, const double* inf, long long n, int i, double tol_rb, double tie,
+                              GreedyState* st);
+fetidp_status k_greedy_zeta(Ctx& c, const double* D, long long len, int i, const GreedyState* st, double* zeta);
+fetidp_status k_greedy_alpha(Ctx& c, const double* Z, const double* nrm, const double* beta, int nrb,
+                             const GreedyState* st, double* T, double* alpha);
 // dense batched setup kernels (principal blocks, SPD inverses by sweeps)
 fetidp_status k_assemble_principal(Ctx& c, const int* sigma_dev, int nrb, double* Krr, double* Krp, double* Kpp);
 fetidp_status k_spd_inverse_batched(Ctx& c, double* A, long long stride, int n, int lda, int batch, double* work,
@@ -312,6 +330,8 @@ fetidp_status k_batched_symmetrize(Ctx& c, double* A, long long stride, int n, i
 fetidp_status k_spp_cells(Ctx& c, const double* Kpp, const double* P, double* out);
 fetidp_status k_coarse_assemble(Ctx& c, const double* Spp, const int* vslab, const int* vpos, int b, double* A,
                                 double* C);
+fetidp_status k_gram_direct(Ctx& c, const double* Y, int ntab, const double* dvec, double* pi, double* delta,
+                           double drop_rel);
 fetidp_status k_batched_diag_sum(Ctx& c, const double* A, long long stride, int lda, int r0, int m, int batch,
                                  double* out);
 fetidp_status k_apply_K(Ctx& c, CCellVec u, CellVec y, int nvec_per_col, int ncols, bool idp,

@@ -540,6 +540,70 @@ __device__ __forceinline__ void load4(const double* p, double (&o)[4]) {
   o[0] = t0.x; o[1] = t0.y; o[2] = t1.x; o[3] = t1.y;
 }
 
+// Diagonal-pivoted Cholesky solve of one symmetric nrb x nrb system by one warp, on the warp's
+// shared scratch (row stride ld = nrb + 1): S holds G (overwritten), hs the right-hand side; the
+// coefficients land in cs (0 off the pivots).  Each step takes the largest remaining Schur
+// diagonal (lowest index on ties) and stops when it is not above drop_rel * max diag(G); the
+// scaled pivot column is the next column of L and the rank-1 update runs with lanes over columns.
+// Then L y = h(piv), L^T c(piv) = y, column-oriented and lane-parallel.
+__device__ void warp_pivoted_gram_solve(double* S, double* Lc, const double* hs, double* ys, double* cs,
+                                        double* colv, int* piv, int nrb, int ld, double drop_rel, int lane) {
+  double dmax = 0.0;
+  for (int i = 0; i < nrb; ++i) dmax = fmax(dmax, S[i * ld + i]);
+  unsigned long long used = 0ull;                   // identical in every lane
+  int np = 0;
+  while (np < nrb) {
+    // largest remaining Schur diagonal, lowest index on ties (lane-parallel, then a warp argmax)
+    int jb = -1;
+    double best = 0.0;
+    for (int i = lane; i < nrb; i += 32) {
+      if ((used >> i) & 1ull) continue;
+      const double dv = S[i * ld + i];
+      if (jb < 0 || dv > best) { best = dv; jb = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oj = __shfl_xor_sync(0xffffffffu, jb, o);
+      if (oj >= 0 && (jb < 0 || ob > best || (ob == best && oj < jb))) { best = ob; jb = oj; }
+    }
+    if (jb < 0 || !(best > drop_rel * dmax)) break;   // uniform across the warp
+    used |= 1ull << jb;
+    if (lane == 0) piv[np] = jb;
+    const double inv = 1.0 / sqrt(best);
+    for (int i = lane; i < nrb; i += 32) {
+      const double cv = S[i * ld + jb] * inv;
+      colv[i] = cv;
+      Lc[np * ld + i] = cv;
+    }
+    __syncwarp();
+    for (int i = 0; i < nrb; ++i) {                    // lanes own columns j
+      const double ci = colv[i];
+      for (int j = lane; j < nrb; j += 32) S[i * ld + j] -= ci * colv[j];
+    }
+    ++np;
+    __syncwarp();
+  }
+
+  for (int i = lane; i < nrb; i += 32) { ys[i] = hs[i]; cs[i] = 0.0; }
+  __syncwarp();
+  for (int a = 0; a < np; ++a) {                       // forward: column a of L
+    const int pa = piv[a];
+    const double ya = ys[pa] / Lc[a * ld + pa];
+    __syncwarp();
+    for (int r = a + 1 + lane; r < np; r += 32) ys[piv[r]] -= Lc[a * ld + piv[r]] * ya;
+    if (lane == 0) colv[a] = ya;                       // y in pivot order
+    __syncwarp();
+  }
+  for (int a = np - 1; a >= 0; --a) {                  // backward: row a of L^T = column a of L
+    const int pa = piv[a];
+    const double ca = colv[a] / Lc[a * ld + pa];
+    __syncwarp();
+    for (int r = lane; r < a; r += 32) colv[r] -= Lc[r * ld + pa] * ca;
+    if (lane == 0) cs[pa] = ca;
+    __syncwarp();
+  }
+}
+
 // s + c += x with Neumaier's compensation (c collects the rounding error of every addition)
 template <typename T>
 __device__ __forceinline__ void neumaier_add(T& s, T& c, T x) {
@@ -642,68 +706,53 @@ __global__ void gram_warp_kernel(const TB* __restrict__ R, const TB* __restrict_
   }
   __syncwarp();
 
-  // ---- 2. pivoted Cholesky
-  double dmax = 0.0;
-  for (int i = 0; i < nrb; ++i) dmax = fmax(dmax, S[i * ld + i]);
-  unsigned long long used = 0ull;                   // identical in every lane
-  int np = 0;
-  while (np < nrb) {
-    // largest remaining Schur diagonal, lowest index on ties (lane-parallel, then a warp argmax)
-    int jb = -1;
-    double best = 0.0;
-    for (int i = lane; i < nrb; i += 32) {
-      if ((used >> i) & 1ull) continue;
-      const double dv = S[i * ld + i];
-      if (jb < 0 || dv > best) { best = dv; jb = i; }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oj = __shfl_xor_sync(0xffffffffu, jb, o);
-      if (oj >= 0 && (jb < 0 || ob > best || (ob == best && oj < jb))) { best = ob; jb = oj; }
-    }
-    if (jb < 0 || !(best > drop_rel * dmax)) break;   // uniform across the warp
-    used |= 1ull << jb;
-    if (lane == 0) piv[np] = jb;
-    const double inv = 1.0 / sqrt(best);
-    for (int i = lane; i < nrb; i += 32) {
-      const double cv = S[i * ld + jb] * inv;
-      colv[i] = cv;
-      Lc[np * ld + i] = cv;
-    }
-    __syncwarp();
-    for (int i = 0; i < nrb; ++i) {                    // lanes own columns j
-      const double ci = colv[i];
-      for (int j = lane; j < nrb; j += 32) S[i * ld + j] -= ci * colv[j];
-    }
-    ++np;
-    __syncwarp();
-  }
-
-  // ---- 3. L y = h(piv), L^T c(piv) = y, x = R c
-  for (int i = lane; i < nrb; i += 32) { ys[i] = hs[i]; cs[i] = 0.0; }
+  warp_pivoted_gram_solve(S, Lc, hs, ys, cs, colv, piv, nrb, ld, drop_rel, lane);
   __syncwarp();
-  for (int a = 0; a < np; ++a) {                       // forward: column a of L
-    const int pa = piv[a];
-    const double ya = ys[pa] / Lc[a * ld + pa];
-    __syncwarp();
-    for (int r = a + 1 + lane; r < np; r += 32) ys[piv[r]] -= Lc[a * ld + piv[r]] * ya;
-    if (lane == 0) colv[a] = ya;                       // y in pivot order
-    __syncwarp();
-  }
-  for (int a = np - 1; a >= 0; --a) {                  // backward: row a of L^T = column a of L
-    const int pa = piv[a];
-    const double ca = colv[a] / Lc[a * ld + pa];
-    __syncwarp();
-    for (int r = lane; r < a; r += 32) colv[r] -= Lc[r * ld + pa] * ca;
-    if (lane == 0) cs[pa] = ca;
-    __syncwarp();
-  }
   double* xc = x + rhs * x_rs + cell * x_cs;
   for (int q = lane; q < nr; q += 32) {
     TB sx = TB(0);
     for (int i = 0; i < nrb; ++i) sx += (TB)cs[i] * Rc[(size_t)i * nr + q];
     xc[q] = (double)sx;
   }
+}
+
+// The two Eq. 42 systems of every cell from its traces Y[cell] = [A upper (npair), b (nrb),
+// M upper (npair)]: pi solves A pi = b, delta solves M delta = dvec (shared right-hand side).
+// One warp per (cell, system); same pivoted solve as Eq. 46b.
+__global__ void gram_direct_kernel(const double* __restrict__ Y, int ntab, int nrb,
+                                   const double* __restrict__ dvec, double* __restrict__ pi,
+                                   double* __restrict__ delta, long long ncell, double drop_rel) {
+  extern __shared__ double gdsm[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const long long task = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
+  if (task >= 2 * ncell) return;                    // the whole warp leaves together
+  const long long cell = task >> 1;
+  const int sys = (int)(task & 1);                  // 0: pi, 1: delta
+  const int ld = nrb + 1;
+  const int per = 2 * nrb * ld + 6 * nrb;
+  double* S = gdsm + (size_t)wib * (per + (per & 1));
+  double* Lc = S + nrb * ld;
+  double* hs = Lc + nrb * ld;
+  double* ys = hs + nrb;
+  double* cs = ys + nrb;
+  double* colv = cs + nrb;
+  int* piv = reinterpret_cast<int*>(colv + nrb);
+  const int npair = nrb * (nrb + 1) / 2;
+  const double* y = Y + cell * ntab;
+  const double* g = y + (sys == 0 ? 0 : npair + nrb);
+  for (int p = lane; p < npair; p += 32) {
+    int i = 0, rem = p;
+    while (rem >= nrb - i) { rem -= nrb - i; ++i; }
+    const int j = i + rem;
+    S[i * ld + j] = g[p];
+    S[j * ld + i] = g[p];
+  }
+  for (int i = lane; i < nrb; i += 32) hs[i] = (sys == 0) ? y[npair + i] : dvec[i];
+  __syncwarp();
+  warp_pivoted_gram_solve(S, Lc, hs, ys, cs, colv, piv, nrb, ld, drop_rel, lane);
+  __syncwarp();
+  double* out = (sys == 0 ? pi : delta) + cell * nrb;
+  for (int i = lane; i < nrb; i += 32) out[i] = cs[i];
 }
 
 // g[rhs][cell] = - sum_e sum_gp w G(w)^T dC_hat/dr G(u), one block per (rhs, cell).
@@ -967,5 +1016,20 @@ fetidp_status k_grad(Ctx& c, const double* u, const double* w, double* g) {
 }
 
 FD_DEFINE_CHECK(fd_check_cell)
+
+fetidp_status k_gram_direct(Ctx& c, const double* Y, int ntab, const double* dvec, double* pi, double* delta,
+                           double drop_rel) {
+  const int nrb = c.nrb, ld = nrb + 1;
+  const int per = 2 * nrb * ld + 6 * nrb;
+  const size_t per_warp = (size_t)(per + (per & 1)) * sizeof(double);
+  int wpb = (int)std::min<size_t>(8, (200 * 1024) / per_warp);
+  if (wpb < 1) wpb = 1;
+  const size_t smem = per_warp * wpb;
+  cudaFuncSetAttribute(gram_direct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  gram_direct_kernel<<<(unsigned)ceil_div(2 * c.N, wpb), 32 * wpb, smem, c.stream>>>(Y, ntab, nrb, dvec, pi, delta,
+                                                                                      c.N, drop_rel);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
 
 }  // namespace fetidp

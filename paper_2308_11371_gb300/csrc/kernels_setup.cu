@@ -74,6 +74,116 @@ __global__ void row_update_kernel(double* __restrict__ D, const double* __restri
   }
 }
 
+// Selection of step i of Algorithm 4 (one block): the largest infinity norm of the current
+// residual snapshots; the selected cell is the lowest index within relative `tie` of it.  Stops
+// (and every later kernel of the loop returns at once) when the maximum is not above tol_rb
+// (from the second step on) or is zero.
+__global__ void greedy_select_kernel(const double* __restrict__ inf, long long n, int i, double tol_rb, double tie,
+                                     GreedyState* __restrict__ st) {
+  __shared__ double sh[32];
+  __shared__ double smx;
+  __shared__ long long sidx[32];
+  if (st->stop) return;                             // uniform across the block
+  double mx = 0.0;
+  for (long long t = threadIdx.x; t < n; t += blockDim.x) mx = fmax(mx, inf[t]);
+  const double m = bmax(mx, sh);
+  if (threadIdx.x == 0) smx = m;
+  __syncthreads();
+  const double M = smx;
+  if ((i > 0 && M <= tol_rb) || M == 0.0) {
+    if (threadIdx.x == 0) st->stop = 1;
+    return;
+  }
+  long long best = n;
+  for (long long t = threadIdx.x; t < n; t += blockDim.x)
+    if (inf[t] >= M * (1.0 - tie)) { best = t; break; }
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long ob = __shfl_down_sync(0xffffffffu, best, o);
+    best = ob < best ? ob : best;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sidx[w] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) best = sidx[k] < best ? sidx[k] : best;
+    st->sigma[i] = (int)best;
+    st->count = i + 1;
+  }
+}
+
+// zeta_i = Delta[sigma_i] / ||Delta[sigma_i]||_2 (one block).
+__global__ void greedy_zeta_kernel(const double* __restrict__ D, long long len, int i,
+                                   const GreedyState* __restrict__ st, double* __restrict__ zeta) {
+  __shared__ double sh[32];
+  __shared__ double snrm;
+  if (st->count <= i) return;
+  const double* x = D + (long long)st->sigma[i] * len;
+  double acc = 0.0;
+  for (long long t = threadIdx.x; t < len; t += blockDim.x) acc += x[t] * x[t];
+  const double r = bsum(acc, sh);
+  if (threadIdx.x == 0) snrm = sqrt(r);
+  __syncthreads();
+  const double nrm = snrm;
+  for (long long t = threadIdx.x; t < len; t += blockDim.x) zeta[t] = x[t] / nrm;
+}
+
+// T[i][j] = zeta_i . A^(sigma_j) (the change of basis of Eq. 56), one block per (i, j).
+__global__ void greedy_T_kernel(const double* __restrict__ Z, const double* __restrict__ snap, long long len, int nrb,
+                                const GreedyState* __restrict__ st, double* __restrict__ T) {
+  __shared__ double sh[32];
+  const int i = blockIdx.x / nrb, j = blockIdx.x - (blockIdx.x / nrb) * nrb;
+  const double* z = Z + (long long)i * len;
+  const double* a = snap + (long long)st->sigma[j] * len;
+  double acc = 0.0;
+  for (long long t = threadIdx.x; t < len; t += blockDim.x) acc += z[t] * a[t];
+  const double r = bsum(acc, sh);
+  if (threadIdx.x == 0) T[i * nrb + j] = r;
+}
+
+// alpha^(s) from T alpha = ||A^(s)|| beta^(s), T upper triangular (Eq. 56); one thread per cell.
+__global__ void greedy_alpha_kernel(const double* __restrict__ T, const double* __restrict__ nrm,
+                                    const double* __restrict__ beta, long long ncell, int nrb,
+                                    double* __restrict__ alpha) {
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < ncell;
+       s += (long long)gridDim.x * blockDim.x) {
+    double* a = alpha + s * nrb;
+    for (int i = nrb - 1; i >= 0; --i) {
+      double v = nrm[s] * beta[(long long)i * ncell + s];
+      for (int j = i + 1; j < nrb; ++j) v -= T[i * nrb + j] * a[j];
+      a[i] = v / T[i * nrb + i];
+    }
+  }
+}
+
+// One greedy step of Algorithm 4 for every row, fused: beta = Delta[row] . zeta,
+// Delta[row] -= beta zeta, and the infinity norm of the updated row (the next step's
+// selection).  One block per row; the second pass re-reads the row from L2.
+__global__ void greedy_step_kernel(double* __restrict__ D, const double* __restrict__ zeta, long long len,
+                                   double* __restrict__ beta_out, double* __restrict__ inf_out,
+                                   const GreedyState* __restrict__ st, int i) {
+  __shared__ double sh[32];
+  __shared__ double sbeta;
+  if (st->count <= i) return;                       // the greedy stopped before step i
+  double* x = D + blockIdx.x * len;
+  double acc = 0.0;
+  for (long long t = threadIdx.x; t < len; t += blockDim.x) acc += x[t] * zeta[t];
+  const double beta = bsum(acc, sh);
+  if (threadIdx.x == 0) sbeta = beta;
+  __syncthreads();
+  const double bt = sbeta;
+  double mx = 0.0;
+  for (long long t = threadIdx.x; t < len; t += blockDim.x) {
+    const double v = x[t] - bt * zeta[t];
+    x[t] = v;
+    mx = fmax(mx, fabs(v));
+  }
+  const double m = bmax(mx, sh);
+  if (threadIdx.x == 0) {
+    beta_out[blockIdx.x] = bt;
+    inf_out[blockIdx.x] = m;
+  }
+}
+
 __global__ void scale_copy_kernel(const double* __restrict__ x, const double* __restrict__ s,
                                   double* __restrict__ y, long long len) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len;
@@ -206,6 +316,35 @@ fetidp_status k_row_normalise(Ctx& c, const double* A, const double* nrm, double
 fetidp_status k_row_update(Ctx& c, double* D, const double* beta, const double* zeta,
                            long long rows, long long len) {
   row_update_kernel<<<gridn(rows * len), kThreads, 0, c.stream>>>(D, beta, zeta, len, rows);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_greedy_step(Ctx& c, double* D, const double* zeta, long long rows, long long len, double* beta,
+                            double* inf, const GreedyState* st, int i) {
+  greedy_step_kernel<<<(unsigned)rows, kThreads, 0, c.stream>>>(D, zeta, len, beta, inf, st, i);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_greedy_select(Ctx& c, const double* inf, long long n, int i, double tol_rb, double tie,
+                              GreedyState* st) {
+  greedy_select_kernel<<<1, 1024, 0, c.stream>>>(inf, n, i, tol_rb, tie, st);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_greedy_zeta(Ctx& c, const double* D, long long len, int i, const GreedyState* st, double* zeta) {
+  greedy_zeta_kernel<<<1, 1024, 0, c.stream>>>(D, len, i, st, zeta);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_greedy_alpha(Ctx& c, const double* Z, const double* nrm, const double* beta, int nrb,
+                             const GreedyState* st, double* T, double* alpha) {
+  greedy_T_kernel<<<(unsigned)(nrb * nrb), kThreads, 0, c.stream>>>(Z, c.snap, c.nsnap, nrb, st, T);
+  FD_CHECK_LAUNCH();
+  greedy_alpha_kernel<<<gridn(c.N), kThreads, 0, c.stream>>>(T, nrm, beta, c.N, nrb, alpha);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }

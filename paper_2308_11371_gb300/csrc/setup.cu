@@ -232,6 +232,12 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
   std::vector<int> gath((size_t)c.N * c.nd * 2, 0);
   std::vector<int> scat;
   std::vector<double> Dw;
+  {
+    // about one multiplier per dual DOF of every cell and component (upper bound for reserve)
+    const size_t est = (size_t)c.N * c.nd;
+    scat.reserve(2 * est);
+    Dw.reserve(est);
+  }
   const long long clamp_coord = p.clamp_side ? (long long)p.cells[p.clamp_axis] * e : 0;
   for (long long gz = 0; gz < gd[2]; ++gz)
     for (long long gy = 0; gy < gd[1]; ++gy)
@@ -255,7 +261,8 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
             ncand[k] = 1;
           }
         }
-        std::vector<std::pair<long long, int>> own;   // (cell, dual node position)
+        std::pair<long long, int> own[8];   // (cell, dual node position), sorted by cell
+        int mult = 0;
         for (int a = 0; a < ncand[0]; ++a)
           for (int b = 0; b < ncand[1]; ++b)
             for (int q = 0; q < ncand[2]; ++q) {
@@ -264,19 +271,20 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
               const int lx = (int)(gx - (long long)cx * e), ly = (int)(gy - (long long)cy * e);
               const int lz = d == 3 ? (int)(gz - (long long)cz * e) : 0;
               const int lnode = lx + nn1 * (ly + nn1 * lz);
-              own.push_back({s, ref.dual_pos[lnode]});
+              int pos = mult++;
+              while (pos > 0 && own[pos - 1].first > s) { own[pos] = own[pos - 1]; --pos; }
+              own[pos] = {s, ref.dual_pos[lnode]};
             }
-        std::sort(own.begin(), own.end());
         const bool clamped = gc[p.clamp_axis] == clamp_coord;
-        const int mult = (int)own.size();
         auto add_gath = [&](long long s, int j, int code) {
           int* gp2 = &gath[((size_t)s * c.nd + j) * 2];
           if (gp2[0] == 0) gp2[0] = code;
           else gp2[1] = code;
         };
         if (clamped) {
-          for (auto& ow : own)
+          for (int q = 0; q < mult; ++q)
             for (int comp = 0; comp < d; ++comp) {
+              const auto& ow = own[q];
               const long long row = (long long)Dw.size();
               const int j = ow.second * d + comp;
               scat.push_back((int)(ow.first * c.nd + j + 1));
@@ -363,70 +371,45 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
   phase("snapshots");
 
   // ---------------------------------------------------------------- Algorithm 4 (greedy)
+  // The whole loop is enqueued without host round trips: each step selects on the device (or
+  // sets the stop flag, after which the remaining kernels return at once); sigma is read back
+  // once at the end.
   const int nrb_req = p.n_rb;
-  double* Delta = nullptr;
-  double *nrm = nullptr, *vals = nullptr, *beta_d = nullptr, *Z = nullptr, *scal1 = nullptr;
-  FD_CUDA(cudaMalloc(&Delta, sizeof(double) * c.N * c.nsnap));
-  FD_CUDA(cudaMalloc(&nrm, sizeof(double) * c.N));
-  FD_CUDA(cudaMalloc(&vals, sizeof(double) * c.N));
-  FD_CUDA(cudaMalloc(&beta_d, sizeof(double) * c.N * nrb_req));
-  FD_CUDA(cudaMalloc(&Z, sizeof(double) * c.nsnap * nrb_req));
-  FD_CUDA(cudaMalloc(&scal1, sizeof(double)));
-  std::vector<double> h_nrm(c.N), h_inf(c.N);
+  if (nrb_req > kMaxRbGreedy) { set_error("n_rb above 64 is not supported"); return FETIDP_EINVAL; }
+  double *Delta = nullptr, *nrm = nullptr, *vals = nullptr, *beta_d = nullptr, *Z = nullptr, *T = nullptr;
+  GreedyState* gst = nullptr;
+  FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Delta), sizeof(double) * c.N * c.nsnap));
+  FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&nrm), sizeof(double) * c.N));
+  FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&vals), sizeof(double) * c.N));
+  FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&beta_d), sizeof(double) * c.N * nrb_req));
+  FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Z), sizeof(double) * c.nsnap * nrb_req));
+  FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&T), sizeof(double) * nrb_req * nrb_req));
+  FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&gst), sizeof(GreedyState)));
   auto free_greedy = [&]() {
-    cudaFree(Delta); cudaFree(nrm); cudaFree(vals); cudaFree(beta_d); cudaFree(Z); cudaFree(scal1);
+    tmp_free(c, Delta); tmp_free(c, nrm); tmp_free(c, vals); tmp_free(c, beta_d); tmp_free(c, Z); tmp_free(c, T); tmp_free(c, gst);
   };
+  FD_CUDA(cudaMemsetAsync(gst, 0, sizeof(GreedyState), c.stream));
   FD_TRY(k_row_reduce(c, c.snap, c.N, c.nsnap, nullptr, 0, nrm));
   FD_TRY(k_row_normalise(c, c.snap, nrm, Delta, c.N, c.nsnap));
-  FD_CUDA(cudaMemcpyAsync(h_nrm.data(), nrm, sizeof(double) * c.N, cudaMemcpyDeviceToHost, c.stream));
-  c.sigma.clear();
+  FD_TRY(k_row_reduce(c, Delta, c.N, c.nsnap, nullptr, 1, vals));
   for (int i = 0; i < nrb_req; ++i) {
-    FD_TRY(k_row_reduce(c, Delta, c.N, c.nsnap, nullptr, 1, vals));
-    FD_CUDA(cudaMemcpyAsync(h_inf.data(), vals, sizeof(double) * c.N, cudaMemcpyDeviceToHost, c.stream));
-    FD_CUDA(cudaStreamSynchronize(c.stream));
-    double mx = 0.0;
-    for (long long s = 0; s < c.N; ++s) mx = std::max(mx, h_inf[s]);
-    if (i > 0 && mx <= p.tol_rb) break;   // convergence check on Delta_{i-1}
-    if (mx == 0.0) break;
-    long long sig = -1;
-    for (long long s = 0; s < c.N; ++s)
-      if (h_inf[s] >= mx * (1.0 - kTieRel)) { sig = s; break; }
-    c.sigma.push_back((int)sig);
     double* zeta = Z + (size_t)i * c.nsnap;
-    FD_TRY(k_row_reduce(c, Delta + (size_t)sig * c.nsnap, 1, c.nsnap, nullptr, 0, scal1));
-    FD_TRY(k_scale_copy(c, Delta + (size_t)sig * c.nsnap, scal1, zeta, c.nsnap));
-    FD_TRY(k_row_reduce(c, Delta, c.N, c.nsnap, zeta, 2, beta_d + (size_t)i * c.N));
-    FD_TRY(k_row_update(c, Delta, beta_d + (size_t)i * c.N, zeta, c.N, c.nsnap));
+    FD_TRY(k_greedy_select(c, vals, c.N, i, p.tol_rb, kTieRel, gst));
+    FD_TRY(k_greedy_zeta(c, Delta, c.nsnap, i, gst, zeta));
+    // beta_i = Delta . zeta_i, Delta -= beta_i zeta_i, and the next infinity norms, in one pass
+    FD_TRY(k_greedy_step(c, Delta, zeta, c.N, c.nsnap, beta_d + (size_t)i * c.N, vals, gst, i));
   }
-  c.nrb = (int)c.sigma.size();
+  GreedyState hst{};
+  FD_CUDA(cudaMemcpyAsync(&hst, gst, sizeof(GreedyState), cudaMemcpyDeviceToHost, c.stream));
+  FD_CUDA(cudaStreamSynchronize(c.stream));
+  c.sigma.assign(hst.sigma, hst.sigma + hst.count);
+  c.nrb = hst.count;
   const int nrb = c.nrb;
   // ---------------------------------------------------------------- alpha (Eq. 56)
-  std::vector<double> h_beta((size_t)nrb * c.N), h_alpha((size_t)c.N * nrb);
-  {
-    // T = Z^T [A^(sigma_1) ... ]: T[i][j] = zeta_i . A^(sigma_j)
-    std::vector<double> T((size_t)nrb * nrb);
-    for (int j = 0; j < nrb; ++j) {
-      FD_TRY(k_row_reduce(c, Z, nrb, c.nsnap, c.snap + (size_t)c.sigma[j] * c.nsnap, 2, vals));
-      std::vector<double> col(nrb);
-      FD_CUDA(cudaMemcpyAsync(col.data(), vals, sizeof(double) * nrb, cudaMemcpyDeviceToHost, c.stream));
-      FD_CUDA(cudaStreamSynchronize(c.stream));
-      for (int i = 0; i < nrb; ++i) T[(size_t)i * nrb + j] = col[i];
-    }
-    FD_CUDA(cudaMemcpyAsync(h_beta.data(), beta_d, sizeof(double) * nrb * c.N, cudaMemcpyDeviceToHost,
-                            c.stream));
-    FD_CUDA(cudaStreamSynchronize(c.stream));
-    // upper-triangular solve per cell: T alpha = ||A^(s)|| beta^(s)
-    for (long long s = 0; s < c.N; ++s) {
-      double* a = h_alpha.data() + (size_t)s * nrb;
-      for (int i = nrb - 1; i >= 0; --i) {
-        double v = h_nrm[s] * h_beta[(size_t)i * c.N + s];
-        for (int j = i + 1; j < nrb; ++j) v -= T[(size_t)i * nrb + j] * a[j];
-        a[i] = v / T[(size_t)i * nrb + i];
-      }
-    }
-  }
+  FD_TRY(dalloc_t(c, &c.alpha, (size_t)c.N * nrb));
+  FD_TRY(k_greedy_alpha(c, Z, nrm, beta_d, nrb, gst, T, c.alpha));
+  FD_CUDA(cudaStreamSynchronize(c.stream));
   free_greedy();
-  FD_TRY(upload(c, &c.alpha, h_alpha));
   phase("greedy + alpha");
 
   // ---------------------------------------------------------------- principal operators (Eq. 39)
@@ -443,16 +426,18 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
     int* sigma_dev = nullptr;
     int* st_dev = nullptr;
     double *work = nullptr, *dvec_d = nullptr;
-    FD_CUDA(cudaMalloc(&sigma_dev, sizeof(int) * nrb));
-    FD_CUDA(cudaMalloc(&st_dev, sizeof(int)));
-    FD_CUDA(cudaMalloc(&Krp_d, sizeof(double) * (size_t)nrb * nr * np));
-    FD_CUDA(cudaMalloc(&Kpp_d, sizeof(double) * (size_t)nrb * np * np));
-    FD_CUDA(cudaMalloc(&work, sizeof(double) * 2 * (size_t)nrb * (nr + 1)));
-    FD_CUDA(cudaMalloc(&dvec_d, sizeof(double) * nrb));
+    FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&sigma_dev), sizeof(int) * nrb));
+    FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&st_dev), sizeof(int)));
+    FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Krp_d), sizeof(double) * (size_t)nrb * nr * np));
+    FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Kpp_d), sizeof(double) * (size_t)nrb * np * np));
+    FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&work), sizeof(double) * 2 * (size_t)nrb * (nr + 1)));
+    FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&dvec_d), sizeof(double) * nrb));
     FD_CUDA(cudaMemcpyAsync(sigma_dev, c.sigma.data(), sizeof(int) * nrb, cudaMemcpyHostToDevice, c.stream));
     FD_CUDA(cudaMemsetAsync(st_dev, 0, sizeof(int), c.stream));
     FD_TRY(k_assemble_principal(c, sigma_dev, nrb, c.Kinv, Krp_d, Kpp_d));
+    phase("  principal assembly");
     FD_TRY(k_spd_inverse_batched(c, c.Kinv, (long long)nr * nr, nr, nr, nrb, work, st_dev));
+    phase("  principal K_rr inverse");
     FD_TRY(k_batched_gemm_nn(c, c.Kinv, (long long)nr * nr, nr, Krp_d, (long long)nr * np, np, c.Urp,
                              (long long)nr * np, np, nr, np, nr, nrb));
     FD_TRY(k_batched_block_copy(c, c.Urp, (long long)nr * np, np, 0, 0, c.UrpT, (long long)np * nr, nr, nr, np,
@@ -465,9 +450,9 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
     FD_CUDA(cudaMemcpyAsync(dvec.data(), dvec_d, sizeof(double) * nrb, cudaMemcpyDeviceToHost, c.stream));
     FD_CUDA(cudaMemcpyAsync(&hst, st_dev, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     FD_CUDA(cudaStreamSynchronize(c.stream));
-    cudaFree(sigma_dev); cudaFree(st_dev); cudaFree(work); cudaFree(dvec_d);
+    tmp_free(c, sigma_dev); tmp_free(c, st_dev); tmp_free(c, work); tmp_free(c, dvec_d);
     if (hst != 0) {
-      cudaFree(Krp_d); cudaFree(Kpp_d);
+      tmp_free(c, Krp_d); tmp_free(c, Kpp_d);
       set_error("principal K_rr is not positive definite");
       return FETIDP_ESINGULAR;
     }
@@ -475,17 +460,16 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
   phase("principal factorisations");
 
   // ---------------------------------------------------------------- projections pi, delta (Eqs. 41-42)
-  std::vector<double> h_pi((size_t)c.N * nrb), h_delta((size_t)c.N * nrb);
   {
     const int nqp = c.nelem * c.ngp, dd = d * d;
     const int npair = nrb * (nrb + 1) / 2;
     const int ntab = 2 * npair + nrb;
     double *Gd = nullptr, *Gp = nullptr, *Ge = nullptr, *Tab = nullptr, *Y = nullptr;
-    FD_CUDA(cudaMalloc(&Gd, sizeof(double) * (size_t)nrb * nd * nqp * dd));
-    FD_CUDA(cudaMalloc(&Gp, sizeof(double) * (size_t)nrb * np * nqp * dd));
-    FD_CUDA(cudaMalloc(&Ge, sizeof(double) * (size_t)np * nqp * dd));
-    FD_CUDA(cudaMalloc(&Tab, sizeof(double) * (size_t)ntab * c.nsnap));
-    FD_CUDA(cudaMalloc(&Y, sizeof(double) * (size_t)c.N * ntab));
+    FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Gd), sizeof(double) * (size_t)nrb * nd * nqp * dd));
+    FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Gp), sizeof(double) * (size_t)nrb * np * nqp * dd));
+    FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Ge), sizeof(double) * (size_t)np * nqp * dd));
+    FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Tab), sizeof(double) * (size_t)ntab * c.nsnap));
+    FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Y), sizeof(double) * (size_t)c.N * ntab));
     // columns of U_rd^(k) = K_rr^{-1} T_rd: rows ni+l of the symmetric inverse
     FD_TRY(k_column_gradients(c, c.Kinv + (size_t)ni * nr, (long long)nr * nr, nr, nr, 0, 0, nrb, nd, Gd));
     // columns of U_rp^(k): rows of U_rp^T
@@ -500,10 +484,11 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
     for (int i = 0; i < nrb; ++i)
       for (int j = i; j < nrb; ++j) specs.push_back({Gd + i * gstride_d, Gd + j * gstride_d, nd});
     TraceTableSpec* specs_dev = nullptr;
-    FD_CUDA(cudaMalloc(&specs_dev, sizeof(TraceTableSpec) * specs.size()));
+    FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&specs_dev), sizeof(TraceTableSpec) * specs.size()));
     FD_CUDA(cudaMemcpyAsync(specs_dev, specs.data(), sizeof(TraceTableSpec) * specs.size(),
                             cudaMemcpyHostToDevice, c.stream));
     FD_TRY(k_trace_tables(c, specs_dev, (int)specs.size(), Tab, c.nsnap));
+    phase("  gradients + trace tables");
     // Both trace systems of Eq. 42 are Gram matrices of nearly dependent principal fields; their
     // pivoted solves decide which directions to drop at 1e-12 of the largest pivot and amplify
     // trace errors by ~1e5, so a BF16-split contraction is far too coarse.  The FP64 path takes
@@ -514,25 +499,17 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
     else
       FD_TRY(k_grouped_gemm_n(c, Tab, 0, (int)c.nsnap, ntab, (int)c.nsnap, 1, CCellVec{c.snap, 0, (int)c.nsnap},
                               CellVec{Y, 0, ntab}, nullptr, 1.0, 0.0, c.N, 1, false, 0));
-    std::vector<double> hY((size_t)c.N * ntab);
-    FD_CUDA(cudaMemcpyAsync(hY.data(), Y, sizeof(double) * hY.size(), cudaMemcpyDeviceToHost, c.stream));
+    phase("  trace contraction");
+    // the two Gram systems of every cell, solved on the device (one warp per system)
+    double* dvec_d = nullptr;
+    FD_TRY(dalloc_t(c, &c.pi, (size_t)c.N * nrb));
+    FD_TRY(dalloc_t(c, &c.delta, (size_t)c.N * nrb));
+    FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&dvec_d), sizeof(double) * nrb));
+    FD_CUDA(cudaMemcpyAsync(dvec_d, dvec.data(), sizeof(double) * nrb, cudaMemcpyHostToDevice, c.stream));
+    FD_TRY(k_gram_direct(c, Y, ntab, dvec_d, c.pi, c.delta, kDropRel));
     FD_CUDA(cudaStreamSynchronize(c.stream));
-    cudaFree(Gd); cudaFree(Gp); cudaFree(Ge); cudaFree(Tab); cudaFree(Y); cudaFree(specs_dev);
-    parallel_for((int)std::min<long long>(c.N, 1 << 30), [&](int s) {
-      const double* y = hY.data() + (size_t)s * ntab;
-      std::vector<double> A((size_t)nrb * nrb), M((size_t)nrb * nrb), b(nrb);
-      int q = 0;
-      for (int i = 0; i < nrb; ++i)
-        for (int j = i; j < nrb; ++j, ++q) { A[(size_t)i * nrb + j] = y[q]; A[(size_t)j * nrb + i] = y[q]; }
-      for (int i = 0; i < nrb; ++i, ++q) b[i] = y[q];
-      for (int i = 0; i < nrb; ++i)
-        for (int j = i; j < nrb; ++j, ++q) { M[(size_t)i * nrb + j] = y[q]; M[(size_t)j * nrb + i] = y[q]; }
-      gram_solve(nrb, A.data(), b.data(), kDropRel, h_pi.data() + (size_t)s * nrb);
-      gram_solve(nrb, M.data(), dvec.data(), kDropRel, h_delta.data() + (size_t)s * nrb);
-    });
+    tmp_free(c, Gd); tmp_free(c, Gp); tmp_free(c, Ge); tmp_free(c, Tab); tmp_free(c, Y); tmp_free(c, specs_dev); tmp_free(c, dvec_d);
   }
-  FD_TRY(upload(c, &c.pi, h_pi));
-  FD_TRY(upload(c, &c.delta, h_delta));
   phase("projections pi, delta");
 
   // ---------------------------------------------------------------- ROM local operators (Eq. 43)
@@ -576,16 +553,15 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
   FD_TRY(k_rom_combine(c, c.Urp, (long long)nr * np, np, 0, 0, nr, np, c.pi, c.Urp_c, false));
   FD_TRY(k_rom_combine(c, c.Urp, (long long)nr * np, np, 0, 0, nr, np, c.pi, c.UrpT_c, true));
 
+  phase("ROM operators / packing");
+
   // ---------------------------------------------------------------- coarse S_PP (Eq. 43, Sec. 3.2.1)
   {
     // P_kj = K_rp^(k)T U_rp^(j), then per cell S_pp_ring = sym(K_pp_ring - K_rp_ring^T U_rp_ring)
     double *Pkj = nullptr, *Spp = nullptr;
     fetidp_status st = FETIDP_OK;
-    if (cudaMalloc(&Pkj, sizeof(double) * (size_t)nrb * nrb * np * np) != cudaSuccess ||
-        cudaMalloc(&Spp, sizeof(double) * (size_t)c.N * np * np) != cudaSuccess) {
-      set_error("cudaMalloc failed for the coarse setup");
-      st = FETIDP_ENOMEM;
-    }
+    st = tmp_alloc(c, reinterpret_cast<void**>(&Pkj), sizeof(double) * (size_t)nrb * nrb * np * np);
+    if (st == FETIDP_OK) st = tmp_alloc(c, reinterpret_cast<void**>(&Spp), sizeof(double) * (size_t)c.N * np * np);
     for (int k = 0; k < nrb && st == FETIDP_OK; ++k)
       st = k_batched_gemm(c, true, false, np, np, nr, 1.0, Krp_d + (size_t)k * nr * np, 0, np, c.Urp, (long long)nr * np,
                           np, 0.0, Pkj + (size_t)k * nrb * np * np, (long long)np * np, np, nrb);
@@ -593,7 +569,7 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
     if (st == FETIDP_OK) phase("S_pp per cell");
     if (st == FETIDP_OK) st = coarse_setup(c, Spp);
     cudaStreamSynchronize(c.stream);
-    cudaFree(Pkj); cudaFree(Spp); cudaFree(Krp_d); cudaFree(Kpp_d);
+    tmp_free(c, Pkj); tmp_free(c, Spp); tmp_free(c, Krp_d); tmp_free(c, Kpp_d);
     FD_TRY(st);
     phase("coarse factorisation");
   }

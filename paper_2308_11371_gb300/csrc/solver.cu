@@ -15,6 +15,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "common.cuh"
@@ -104,12 +105,46 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-fetidp_status dalloc(Ctx& c, void** p, size_t bytes) {
+// Device memory comes from the device's stream-ordered pool, whose release threshold is raised
+// once per device: freed blocks stay in the pool, so a context set up after another reuses its
+// memory without the device-wide synchronisation of cudaMalloc / cudaFree.
+static std::mutex g_pool_mu;
+static bool g_pool_ready[64];
+static void ensure_pool(int dev) {
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (dev < 0 || dev >= 64 || g_pool_ready[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  g_pool_ready[dev] = true;
+}
+
+fetidp_status tmp_alloc(Ctx& c, void** p, size_t bytes) {
   if (bytes == 0) bytes = 8;
-  cudaError_t e = cudaMalloc(p, bytes);
+  ensure_pool(c.device);
+  cudaError_t e = cudaMallocAsync(p, bytes, c.stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    *p = nullptr;
+    set_error(std::string("cudaMallocAsync(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? FETIDP_ENOMEM : FETIDP_ECUDA;
+  }
+  return FETIDP_OK;
+}
+
+void tmp_free(Ctx& c, void* p) {
+  if (p) cudaFreeAsync(p, c.stream);
+}
+
+fetidp_status dalloc(Ctx& c, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 8;
+  ensure_pool(c.device);
+  cudaError_t e = cudaMallocAsync(p, bytes, c.stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error(std::string("cudaMallocAsync(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? FETIDP_ENOMEM : FETIDP_ECUDA;
   }
   c.allocations.push_back(*p);
@@ -566,8 +601,8 @@ fetidp_status fetidp_tc_comb_selfcheck(int M0, int M1, int K, int N, int nops, d
     cudaMemset(c.tc_err, 0, sizeof(int));
     st = tc_comb_selfcheck(c, M0, M1, K, N, nops, rel_err);
   }
+  for (void* p : c.allocations) cudaFreeAsync(p, c.stream);
   cudaStreamSynchronize(nullptr);
-  for (void* p : c.allocations) cudaFree(p);
   c.allocations.clear();
   return st;
 }
@@ -588,8 +623,8 @@ fetidp_status fetidp_tc_selfcheck(int M, int K, int N, double* rel_err) {
     cudaMemset(c.tc_err, 0, sizeof(int));
     st = tc_selfcheck(c, M, K, N, rel_err);
   }
+  for (void* p : c.allocations) cudaFreeAsync(p, c.stream);
   cudaStreamSynchronize(nullptr);
-  for (void* p : c.allocations) cudaFree(p);
   c.allocations.clear();
   return st;
 }
@@ -655,7 +690,8 @@ void fetidp_destroy(fetidp_ctx* ctx) {
   cudaSetDevice(ctx->c.device);
   cudaStreamSynchronize(ctx->c.stream);
   for (auto& e : ctx->c.prof.ev) cudaEventDestroy(e);
-  for (void* p : ctx->c.allocations) cudaFree(p);
+  for (void* p : ctx->c.allocations) cudaFreeAsync(p, ctx->c.stream);
+  cudaStreamSynchronize(ctx->c.stream);
   if (ctx->c.h_scal) cudaFreeHost(ctx->c.h_scal);
   delete ctx;
 }

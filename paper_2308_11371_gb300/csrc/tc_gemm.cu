@@ -808,7 +808,7 @@ void tc_free_operator(Ctx& c, TcOperator& op) {
       break;
     }
   c.device_bytes -= (size_t)(op.separate ? op.nops : 1) * op.batch_bytes;
-  cudaFree(op.tiles);
+  cudaFreeAsync(op.tiles, c.stream);
   op.tiles = nullptr;
 }
 
