@@ -175,6 +175,11 @@ fetidp_status fetidp_solve(fetidp_ctx *ctx, double *u, double *lambda, fetidp_in
 fetidp_status fetidp_solve_host(fetidp_ctx *ctx, double *u_host, double *lambda_host,
                                 fetidp_info *info);
 
+/* Compliance c[l] = sum_s f_l^(s)T u_l^(s) per load case (the objective whose gradient
+ * fetidp_grad returns).  u: device, cell-duplicated natural order [rhs][cell][n_dof] as written by
+ * fetidp_solve; c: n_rhs doubles, host or device.  Deterministic reduction order. */
+fetidp_status fetidp_compliance(fetidp_ctx *ctx, const double *u, double *c);
+
 /* Gradient of compliance w.r.t. the per-cell radii r_s: for every RHS,
  * g[rhs][s] = - w_s^T (dK_s / dr_s) u_s with w = u when w == NULL (the
  * compliance c = f^T u is self-adjoint).  u, w: device [n_rhs][N][n_dof] as

@@ -29,7 +29,8 @@ SYMBOLS = ["fetidp_sizes", "fetidp_default_options", "fetidp_setup", "fetidp_app
            "fetidp_apply_A", "fetidp_apply_P", "fetidp_rom_data", "fetidp_destroy",
            "fetidp_status_string", "fetidp_last_error", "fetidp_profile_enable",
            "fetidp_profile_read", "fetidp_kernel_launches", "fetidp_tc_selfcheck",
-           "fetidp_tc_comb_selfcheck", "fetidp_tc_selfcheck_static"]
+           "fetidp_tc_comb_selfcheck", "fetidp_tc_selfcheck_static",
+           "fetidp_compliance"]
 
 KCLASS = {"grouped_gemm": 0, "apply_K": 1, "maps": 2, "coarse": 3, "cell_gemv": 4, "vector": 5,
           "gram": 6, "tc_gemm": 7, "setup": 8}
@@ -115,6 +116,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.fetidp_solve_host.argtypes = [P, V, V, ctypes.POINTER(Info)]
     lib.fetidp_grad.restype = I
     lib.fetidp_grad.argtypes = [P, V, V, V]
+    lib.fetidp_compliance.restype = I
+    lib.fetidp_compliance.argtypes = [P, V, V]
     lib.fetidp_rom_data.restype = I
     lib.fetidp_rom_data.argtypes = [P, V, V, V, V]
     lib.fetidp_destroy.restype = None
@@ -275,6 +278,12 @@ class Solver:
         wp = ctypes.c_void_p(_ptr(w)) if w is not None else ctypes.c_void_p(None)
         _check(load().fetidp_grad(self._h, ctypes.c_void_p(_ptr(u)), wp, ctypes.c_void_p(_ptr(o))))
         return o
+
+    def compliance(self, u):
+        """c[l] = sum_s f_l^(s) . u_l^(s) per load case (host numpy array)."""
+        c = np.zeros(self.n_rhs)
+        _check(load().fetidp_compliance(self._h, ctypes.c_void_p(_ptr(u)), ctypes.c_void_p(c.ctypes.data)))
+        return c
 
     def rom_data(self):
         k, N = self.n_rb, self.N

@@ -13,6 +13,8 @@ namespace fetidp {
 
 void set_error(const std::string& msg);
 struct Ctx;
+// blocks of the deterministic two-stage reductions (2 x 152 SMs)
+constexpr int kReductionBlocks = 304;
 // stream-ordered temporaries of the setup phase (not tracked by the context)
 fetidp_status tmp_alloc(Ctx& c, void** p, size_t bytes);
 void tmp_free(Ctx& c, void* p);
@@ -219,6 +221,7 @@ struct Ctx {
   CoarseBCR bcr;
   // right-hand side of Eq. 16: [m][ntot] = (f_R, f_P, d = 0)
   double* rhs = nullptr;
+  double* rhs_p_cells = nullptr;   // [m][N][n_p] each cell's own corner loads (local corner order)
   // workspace
   double* w_cell_a = nullptr;   // [m][N][max(n, nr)]
   double* w_cell_b = nullptr;   // [m][N][max(n, nr)]
@@ -299,6 +302,8 @@ fetidp_status k_copy_scale(Ctx& c, const double* x, double* y, long long len, in
 
 // ---------------------------------------------------------------- kernels (cell-level compute)
 fetidp_status k_snapshots(Ctx& c);
+// c[l] = sum_s f_l^(s) . u_l^(s) (u natural cell order); partial: [m][kRedBlocks] scratch
+fetidp_status k_compliance(Ctx& c, const double* u, double* out, double* partial);
 // Device state of the greedy loop (Algorithm 4): selected cells and a stop flag.
 constexpr int kMaxRbGreedy = 64;
 struct GreedyState {
@@ -365,7 +370,7 @@ fetidp_status tc_selfcheck(Ctx& c, int M, int K, int N, double* rel_err);
 fetidp_status tc_selfcheck_static(Ctx& c, int M, int K, int N, double* rel_err);
 size_t tc_selfcheck_static_bytes(int M, int K, int N);
 void tc_free_operator(Ctx& c, TcOperator& op);
-int tc_comb_bn(long long ncols, int m_tiles);
+int tc_comb_bn(long long ncols, int m_tiles, int kto, int nX, int nops, bool two_sets);
 bool tc_comb_fits(int K, int split, long long ncols, int m_tiles, int nops, bool two_sets);
 fetidp_status tc_comb_pack(Ctx& c, TcComb& op, const double* src0, long long st0, int lda0, int r00, int c00,
                            int M0, const double* src1, long long st1, int lda1, int r01, int c01, int M1,

@@ -22,14 +22,16 @@ inline int grid_for(long long work, int threads) {
   return (int)(g < 1 ? 1 : g);
 }
 
-// Element matrices of the principal cells scattered into K_rr, K_rp, K_pp (local order).
-// One thread per (principal, element, row (A, i)).
+// Element matrices of the principal cells added into K_rr, K_rp, K_pp (local order), one colour
+// of elements per launch: elements of a colour (same index parities) share no node, so no two
+// threads of a launch touch the same entry and the sums run in a fixed order (deterministic).
+// One thread per (principal, element, row (A, i)); elements of other colours return.
 template <int D>
 __global__ void assemble_principal_kernel(const double* __restrict__ snap, const int* __restrict__ sigma,
                                           long long nsnap, int nrb, int e, int nc, int n, int nr,
                                           const int* __restrict__ iperm, double wq, double inv_h,
                                           double* __restrict__ Krr, double* __restrict__ Krp,
-                                          double* __restrict__ Kpp) {
+                                          double* __restrict__ Kpp, int color) {
   constexpr int NA = 1 << D;
   constexpr int ND = NA * D;
   constexpr int NI = D * D;
@@ -43,6 +45,7 @@ __global__ void assemble_principal_kernel(const double* __restrict__ snap, const
     const int el = r / ND, row = r - el * ND;
     const int A = row / D, i = row - A * D;
     const int ex = el % e, ey = (el / e) % e, ez = el / (e * e);
+    if ((ex & 1) + 2 * (ey & 1) + 4 * (ez & 1) != color) continue;
     const double* Cel = snap + (long long)sigma[k] * nsnap + (long long)el * NA * nc;
     double krow[ND];
 #pragma unroll
@@ -101,10 +104,10 @@ __global__ void assemble_principal_kernel(const double* __restrict__ snap, const
         const int lb = iperm[nodes[B] * D + j];
         const double v = krow[B * D + j];
         if (la < nr) {
-          if (lb < nr) atomicAdd(Krr + ((long long)k * nr + la) * nr + lb, v);
-          else atomicAdd(Krp + ((long long)k * nr + la) * np + (lb - nr), v);
+          if (lb < nr) Krr[((long long)k * nr + la) * nr + lb] += v;
+          else Krp[((long long)k * nr + la) * np + (lb - nr)] += v;
         } else if (lb >= nr) {
-          atomicAdd(Kpp + ((long long)k * np + (la - nr)) * np + (lb - nr), v);
+          Kpp[((long long)k * np + (la - nr)) * np + (lb - nr)] += v;
         }
       }
   }
@@ -337,11 +340,13 @@ __global__ void spp_cells_kernel(const double* __restrict__ alpha, const double*
 }
 
 // Slab blocks of S_PP from the per-cell S_pp_ring: diagonal blocks A_i (slab i) and couplings
-// C_i = S(slab i, slab i + 1).  One thread per (cell, corner k1, corner k2).
+// C_i = S(slab i, slab i + 1).  One colour of cells per launch (cells of a colour share no vertex:
+// no two threads add into the same entry; fixed colour order, deterministic sums).  One thread per
+// (cell, corner k1, corner k2); cells of other colours return.
 __global__ void coarse_assemble_kernel(const double* __restrict__ Spp, long long ncell, int d, int nck, int np,
                                        int ncx, int ncy, int vdx, int vdy, const int* __restrict__ vslab,
                                        const int* __restrict__ vpos, int b, double* __restrict__ A,
-                                       double* __restrict__ C) {
+                                       double* __restrict__ C, int color) {
   const long long total = ncell * nck * nck;
   const long long bb = (long long)b * b;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
@@ -349,6 +354,7 @@ __global__ void coarse_assemble_kernel(const double* __restrict__ Spp, long long
     const long long s = t / (nck * nck);
     const int kk = (int)(t - s * nck * nck), k1 = kk / nck, k2 = kk - (kk / nck) * nck;
     const int cx = (int)(s % ncx), cy = (int)((s / ncx) % ncy), cz = (int)(s / ((long long)ncx * ncy));
+    if ((cx & 1) + 2 * (cy & 1) + 4 * (cz & 1) != color) continue;
     const long long v1 = (cx + (k1 & 1)) + (long long)vdx * ((cy + ((k1 >> 1) & 1)) + (long long)vdy * (cz + (d == 3 ? ((k1 >> 2) & 1) : 0)));
     const long long v2 = (cx + (k2 & 1)) + (long long)vdx * ((cy + ((k2 >> 1) & 1)) + (long long)vdy * (cz + (d == 3 ? ((k2 >> 2) & 1) : 0)));
     const int s1 = vslab[v1], s2 = vslab[v2];
@@ -361,7 +367,7 @@ __global__ void coarse_assemble_kernel(const double* __restrict__ Spp, long long
     for (int c1 = 0; c1 < d; ++c1)
       for (int c2 = 0; c2 < d; ++c2) {
         const int r = vpos[v1] * d + c1, q = vpos[v2] * d + c2;
-        atomicAdd(dst + (long long)r * b + q, S[(k1 * d + c1) * np + k2 * d + c2]);
+        dst[(long long)r * b + q] += S[(k1 * d + c1) * np + k2 * d + c2];
       }
   }
 }
@@ -446,13 +452,15 @@ fetidp_status k_assemble_principal(Ctx& c, const int* sigma_dev, int nrb, double
   const double h = 1.0 / c.e, wq = std::pow(0.5 * h, c.d);
   const int NA = 1 << c.d;
   const long long work = (long long)nrb * c.nelem * NA * c.d;
-  if (c.d == 2)
-    assemble_principal_kernel<2><<<grid_for(work, 128), 128, 0, c.stream>>>(
-        c.snap, sigma_dev, c.nsnap, nrb, c.e, c.nc, c.n, c.nr, c.perm + c.n, wq, 1.0 / h, Krr, Krp, Kpp);
-  else
-    assemble_principal_kernel<3><<<grid_for(work, 128), 128, 0, c.stream>>>(
-        c.snap, sigma_dev, c.nsnap, nrb, c.e, c.nc, c.n, c.nr, c.perm + c.n, wq, 1.0 / h, Krr, Krp, Kpp);
-  FD_CHECK_LAUNCH();
+  for (int color = 0; color < NA; ++color) {
+    if (c.d == 2)
+      assemble_principal_kernel<2><<<grid_for(work, 128), 128, 0, c.stream>>>(
+          c.snap, sigma_dev, c.nsnap, nrb, c.e, c.nc, c.n, c.nr, c.perm + c.n, wq, 1.0 / h, Krr, Krp, Kpp, color);
+    else
+      assemble_principal_kernel<3><<<grid_for(work, 128), 128, 0, c.stream>>>(
+          c.snap, sigma_dev, c.nsnap, nrb, c.e, c.nc, c.n, c.nr, c.perm + c.n, wq, 1.0 / h, Krr, Krp, Kpp, color);
+    FD_CHECK_LAUNCH();
+  }
   return FETIDP_OK;
 }
 
@@ -536,9 +544,11 @@ fetidp_status k_coarse_assemble(Ctx& c, const double* Spp, const int* vslab, con
                                 double* C) {
   const int nck = 1 << c.d;
   const int vdx = c.geo.nc[0] + 1, vdy = c.geo.nc[1] + 1;
-  coarse_assemble_kernel<<<grid_for(c.N * nck * nck, 256), 256, 0, c.stream>>>(
-      Spp, c.N, c.d, nck, c.np, c.geo.nc[0], c.geo.nc[1], vdx, vdy, vslab, vpos, b, A, C);
-  FD_CHECK_LAUNCH();
+  for (int color = 0; color < nck; ++color) {
+    coarse_assemble_kernel<<<grid_for(c.N * nck * nck, 256), 256, 0, c.stream>>>(
+        Spp, c.N, c.d, nck, c.np, c.geo.nc[0], c.geo.nc[1], vdx, vdy, vslab, vpos, b, A, C, color);
+    FD_CHECK_LAUNCH();
+  }
   return FETIDP_OK;
 }
 

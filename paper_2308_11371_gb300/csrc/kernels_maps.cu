@@ -13,7 +13,7 @@ namespace fetidp {
 
 namespace {
 
-constexpr int kRedBlocks = 304;   // 2 x 152 SMs
+constexpr int kRedBlocks = kReductionBlocks;
 constexpr int kRedThreads = 256;
 
 __global__ void gather_BT_kernel(const int* __restrict__ gath, const double* __restrict__ lam,
@@ -164,6 +164,32 @@ __global__ void reduce_partials(const double* __restrict__ partial, int count,
   (void)count;
 }
 
+// Compliance partial sums: sum over (cell, local dof) of f . u for one load case, with f the
+// remaining-DOF part of the outer right-hand side and the cells' own corner loads, and u in
+// natural cell order.  Fixed chunk per block, fixed tree in the block (deterministic).
+__global__ void compliance_partial(const double* __restrict__ rhs, long long ntot, const double* __restrict__ fp,
+                                   const double* __restrict__ u, const int* __restrict__ perm, int n, int nr,
+                                   long long ncell, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const int rhs_i = blockIdx.y, blk = blockIdx.x;
+  const long long len = ncell * n;
+  const long long chunk = (len + kRedBlocks - 1) / kRedBlocks;
+  const long long beg = blk * chunk;
+  const long long end = beg + chunk < len ? beg + chunk : len;
+  const double* fr = rhs + rhs_i * ntot;
+  const double* fq = fp + rhs_i * ncell * (n - nr);
+  const double* uc = u + rhs_i * len;
+  double acc = 0.0;
+  for (long long t = beg + threadIdx.x; t < end; t += blockDim.x) {
+    const long long s = t / n;
+    const int li = (int)(t - s * n);
+    const double f = li < nr ? fr[s * nr + li] : fq[s * (n - nr) + (li - nr)];
+    acc += f * uc[s * n + perm[li]];
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[(long long)rhs_i * kRedBlocks + blk] = acc;
+}
+
 __global__ void multi_axpy_kernel(const double* __restrict__ Vb, long long vstride, long long vrs,
                                   int nv, const double* __restrict__ coef, double* __restrict__ w,
                                   long long wrs, long long len, int nrhs, double sign) {
@@ -263,6 +289,15 @@ fetidp_status k_multi_axpy(Ctx& c, const double* Vb, long long vstride, int nv, 
   ProfScope ps(c, FETIDP_K_VECTOR, 2.0 * nv * len * nrhs, 8.0 * (nv + 2) * len * nrhs);
   multi_axpy_kernel<<<grid_for(len * nrhs), 256, 0, c.stream>>>(Vb, vstride, len, nv, coef, w, len,
                                                                  len, nrhs, sign);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_compliance(Ctx& c, const double* u, double* out, double* partial) {
+  compliance_partial<<<dim3(kRedBlocks, c.m), 256, 0, c.stream>>>(c.rhs, c.ntot, c.rhs_p_cells, u, c.perm, c.n, c.nr,
+                                                                 c.N, partial);
+  FD_CHECK_LAUNCH();
+  reduce_partials<<<c.m, 256, 0, c.stream>>>(partial, kRedBlocks, out);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }

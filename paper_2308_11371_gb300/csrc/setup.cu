@@ -345,7 +345,7 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
 
   // ---------------------------------------------------------------- loads: rhs = (f_R, f_P, 0)
   {
-    std::vector<double> rhs((size_t)c.m * c.ntot, 0.0);
+    std::vector<double> rhs((size_t)c.m * c.ntot, 0.0), fpc((size_t)c.m * c.N * c.np, 0.0);
     std::vector<double> f(c.n);
     for (int l = 0; l < c.m; ++l) {
       double* rl = rhs.data() + (size_t)l * c.ntot;
@@ -353,6 +353,7 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
         const int cx = (int)(s % nx), cy = (int)((s / nx) % ny), cz = (int)(s / ((long long)nx * ny));
         cell_load(c, p, l, cx, cy, cz, f);
         for (int li = 0; li < c.nr; ++li) rl[s * c.nr + li] = f[ref.perm[li]];
+        for (int q = 0; q < c.np; ++q) fpc[((size_t)l * c.N + s) * c.np + q] = f[ref.perm[c.nr + q]];
         for (int k = 0; k < c.ncorner; ++k) {
           const int vn = corner_v[(size_t)s * c.ncorner + k];
           if (vn < 0) continue;
@@ -362,6 +363,7 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
       }
     }
     FD_TRY(upload(c, &c.rhs, rhs));
+    FD_TRY(upload(c, &c.rhs_p_cells, fpc));
   }
   phase("primal maps + loads");
 

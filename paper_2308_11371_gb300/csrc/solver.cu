@@ -852,6 +852,18 @@ fetidp_status fetidp_solve_host(fetidp_ctx* ctx, double* u_host, double* lambda_
   return r.converged ? FETIDP_OK : FETIDP_ENOTCONV;
 }
 
+fetidp_status fetidp_compliance(fetidp_ctx* ctx, const double* u, double* c_out) {
+  FD_TRY(enter(ctx));
+  Ctx& c = ctx->c;
+  if (!u || !c_out) { set_error("null pointer"); return FETIDP_EINVAL; }
+  // scratch: the partial sums and the results live in the reduction workspace
+  FD_TRY(k_compliance(c, u, c.red + (size_t)c.m * kReductionBlocks, c.red));
+  FD_CUDA(cudaMemcpyAsync(c_out, c.red + (size_t)c.m * kReductionBlocks, sizeof(double) * c.m, cudaMemcpyDefault,
+                          c.stream));
+  FD_CUDA(cudaStreamSynchronize(c.stream));
+  return FETIDP_OK;
+}
+
 fetidp_status fetidp_grad(fetidp_ctx* ctx, const double* u, const double* w, double* g) {
   FD_TRY(enter(ctx));
   Ctx& c = ctx->c;

@@ -915,12 +915,6 @@ fetidp_status tc_selfcheck(Ctx& c, int M, int K, int N, double* rel_err) {
 
 
 // ---------------------------------------------------------------- combine kernel host side
-int tc_comb_bn(long long ncols, int m_tiles) {
-  if (((ncols + 127) / 128) * m_tiles >= 148) return 128;
-  if (((ncols + 63) / 64) * m_tiles >= 148) return 64;
-  return 32;
-}
-
 // shared bytes of the staged combination coefficients (one or two FP32 sets of nops x bn)
 static size_t comb_coef_bytes(int bn, int nops, bool two_sets) {
   return (size_t)(two_sets ? 2 : 1) * nops * bn * sizeof(float);
@@ -943,10 +937,24 @@ static void comb_ring(int bn, int kto, int nX, int per_op, size_t coef_bytes, in
   *stages = st;
 }
 
+// Column-tile width of the combine kernel: the widest of 128 / 64 / 32 that still gives a full
+// wave of CTAs, narrowed while the resident x tiles leave no room for two ring stages (long K).
+int tc_comb_bn(long long ncols, int m_tiles, int kto, int nX, int nops, bool two_sets) {
+  int bn = 32;
+  if (((ncols + 127) / 128) * m_tiles >= 148) bn = 128;
+  else if (((ncols + 63) / 64) * m_tiles >= 148) bn = 64;
+  for (; bn > 32; bn /= 2) {
+    int st = 0, tps = 1;
+    comb_ring(bn, kto, nX, kto * nX, comb_coef_bytes(bn, nops, two_sets), &st, &tps);
+    if (st >= 2) break;
+  }
+  return bn;
+}
+
 bool tc_comb_fits(int K, int split, long long ncols, int m_tiles, int nops, bool two_sets) {
   const int kto = (K + TC_BK - 1) / TC_BK;
-  const int bn = tc_comb_bn(ncols, m_tiles);
   const int nA = split == 3 ? 2 : 1;
+  const int bn = tc_comb_bn(ncols, m_tiles, kto, nA, nops, two_sets);
   int st = 0, tps = 1;
   comb_ring(bn, kto, nA, kto * nA, comb_coef_bytes(bn, nops, two_sets), &st, &tps);
   return st >= 2;
@@ -974,7 +982,7 @@ fetidp_status tc_comb_pack(Ctx& c, TcComb& op, const double* src0, long long st0
 }
 
 size_t tc_comb_staging_bytes(const TcComb& op, long long ncols) {
-  const int bn = tc_comb_bn(ncols, op.m_tiles);
+  const int bn = tc_comb_bn(ncols, op.m_tiles, op.kto, op.nX, op.nops, op.msplit < op.M);
   const long long n_tiles = (ncols + bn - 1) / bn;
   return (size_t)n_tiles * op.kto * op.nX * bn * TC_BK * 2;
 }
@@ -1041,7 +1049,7 @@ fetidp_status tc_comb_apply(Ctx& c, const TcComb& op, CCellVec X, const double* 
   P.alpha = alpha;
   P.beta = beta;
   P.err = c.tc_err;
-  const int bn = tc_comb_bn(ncols, op.m_tiles);
+  const int bn = tc_comb_bn(ncols, op.m_tiles, op.kto, op.nX, op.nops, op.msplit < op.M);
   if (bn == 128) return comb_launch<128>(c, op, P, X, ncols, ncell);
   if (bn == 64) return comb_launch<64>(c, op, P, X, ncols, ncell);
   return comb_launch<32>(c, op, P, X, ncols, ncell);
