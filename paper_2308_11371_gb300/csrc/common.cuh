@@ -312,10 +312,11 @@ struct GreedyState {
   int sigma[kMaxRbGreedy];
 };
 fetidp_status k_greedy_step(Ctx& c, double* D, const double* zeta, long long rows, long long len, double* beta,
-                            double* inf, const GreedyState* st, int i);
+                            double* inf, double* sq, const GreedyState* st, int i);
 fetidp_status k_greedy_select(Ctx& c, const double* inf, long long n, int i, double tol_rb, double tie,
                               GreedyState* st);
-fetidp_status k_greedy_zeta(Ctx& c, const double* D, long long len, int i, const GreedyState* st, double* zeta);
+fetidp_status k_greedy_zeta(Ctx& c, const double* D, const double* sq, long long len, int i, const GreedyState* st,
+                            double* zeta);
 fetidp_status k_greedy_alpha(Ctx& c, const double* Z, const double* nrm, const double* beta, int nrb,
                              const GreedyState* st, double* T, double* alpha);
 // dense batched setup kernels (principal blocks, SPD inverses by sweeps)
@@ -332,6 +333,7 @@ fetidp_status k_batched_gemm(Ctx& c, bool ta, bool tb, int M, int N, int K, doub
                              long long sa, int lda, const double* B, long long sb, int ldb, double beta, double* C,
                              long long sc, int ldc, int batch);
 fetidp_status k_batched_symmetrize(Ctx& c, double* A, long long stride, int n, int lda, int batch);
+fetidp_status k_principal_pairs(Ctx& c, const double* Krp, double* P);   // P_kj = K_rp^(k)T U_rp^(j)
 fetidp_status k_spp_cells(Ctx& c, const double* Kpp, const double* P, double* out);
 fetidp_status k_coarse_assemble(Ctx& c, const double* Spp, const int* vslab, const int* vpos, int b, double* A,
                                 double* C);

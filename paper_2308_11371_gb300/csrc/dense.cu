@@ -307,6 +307,24 @@ __global__ void batched_symmetrize_kernel(double* __restrict__ A, long long stri
   }
 }
 
+// P_kj = K_rp^(k)T U_rp^(j) for all principal pairs (n_p x n_p each, contraction over n_r), one
+// thread per (k, j, r, q).
+__global__ void principal_pairs_kernel(const double* __restrict__ Krp, const double* __restrict__ Urp, int nrb,
+                                       int nr, int np, double* __restrict__ P) {
+  const long long total = (long long)nrb * nrb * np * np;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(t % np), r = (int)((t / np) % np);
+    const long long kj = t / ((long long)np * np);
+    const int j = (int)(kj % nrb), k = (int)(kj / nrb);
+    const double* a = Krp + (long long)k * nr * np + r;
+    const double* b = Urp + (long long)j * nr * np + q;
+    double s = 0.0;
+    for (int i = 0; i < nr; ++i) s = fma(a[(long long)i * np], b[(long long)i * np], s);
+    P[t] = s;
+  }
+}
+
 // Per-cell S_pp_ring (Eq. 43): sym( sum_k alpha_k K_pp^(k) - sum_{k,j} alpha_k pi_j P_kj ),
 // P_kj = K_rp^(k)T U_rp^(j).  One thread per (cell, r <= q).
 __global__ void spp_cells_kernel(const double* __restrict__ alpha, const double* __restrict__ pi,
@@ -549,6 +567,13 @@ fetidp_status k_coarse_assemble(Ctx& c, const double* Spp, const int* vslab, con
         Spp, c.N, c.d, nck, c.np, c.geo.nc[0], c.geo.nc[1], vdx, vdy, vslab, vpos, b, A, C, color);
     FD_CHECK_LAUNCH();
   }
+  return FETIDP_OK;
+}
+
+fetidp_status k_principal_pairs(Ctx& c, const double* Krp, double* P) {
+  const long long total = (long long)c.nrb * c.nrb * c.np * c.np;
+  principal_pairs_kernel<<<grid_for(total, 128), 128, 0, c.stream>>>(Krp, c.Urp, c.nrb, c.nr, c.np, P);
+  FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }
 

@@ -382,6 +382,38 @@ __global__ void cell_gemv_kernel(const double* __restrict__ mats, long long mstr
   }
 }
 
+// Narrow per-cell operators with a compile-time column count MC (n_p: 8 in 2D, 24 in 3D): one
+// thread per (cell, row); the row's MC entries arrive as 16-byte loads issued before any use, so
+// each thread waits for memory once.  Rows must be 16-byte aligned (ld and the base even).
+template <int MC>
+__global__ void cell_gemv_narrow_fixed(const double* __restrict__ mats, long long mstride, int ld, int mrows,
+                                       const double* __restrict__ x, long long x_rs, int x_cs,
+                                       double* __restrict__ y, long long y_rs, int y_cs, double alpha,
+                                       double beta, int nrhs, long long ncell) {
+  const long long total = ncell * mrows;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long cell = t / mrows;
+    const int row = (int)(t - cell * mrows);
+    const double2* Mr = reinterpret_cast<const double2*>(mats + cell * mstride + (long long)row * ld);
+    double mv[MC];
+#pragma unroll
+    for (int q = 0; q < MC / 2; ++q) {
+      const double2 v = Mr[q];
+      mv[2 * q] = v.x;
+      mv[2 * q + 1] = v.y;
+    }
+    for (int r = 0; r < nrhs; ++r) {
+      const double* xc = x + r * x_rs + cell * x_cs;
+      double acc = 0.0;
+#pragma unroll
+      for (int q = 0; q < MC; ++q) acc = fma(mv[q], xc[q], acc);
+      double* dst = y + r * y_rs + cell * y_cs + row;
+      *dst = (beta == 0.0) ? alpha * acc : alpha * acc + beta * (*dst);
+    }
+  }
+}
+
 // Narrow per-cell operators (at most 32 columns, e.g. the n_r x n_p prolongations): one thread
 // per (cell, row), so consecutive threads read consecutive rows; x entries are shared by the
 // threads of a cell (cache broadcast).
@@ -929,6 +961,20 @@ fetidp_status k_cell_gemv_strided(Ctx& c, const double* mats, long long mstride,
                                   int nrhs) {
   ProfScope ps(c, FETIDP_K_CELL_GEMV, 2.0 * mrows * mcols * (double)c.N * nrhs,
                8.0 * c.N * ((double)mrows * mcols + (double)nrhs * (mrows + mcols)));
+  const bool aligned16 = (ld % 2 == 0) && (mstride % 2 == 0) && ((reinterpret_cast<uintptr_t>(mats) & 15) == 0);
+  if ((mcols == 8 || mcols == 24) && aligned16) {
+    const long long total = c.N * mrows;
+    long long grid = (total + 255) / 256;
+    if (grid > 152LL * 32) grid = 152LL * 32;
+    if (mcols == 8)
+      cell_gemv_narrow_fixed<8><<<(unsigned)grid, 256, 0, c.stream>>>(mats, mstride, ld, mrows, x.p, x.rs, x.cs, y.p,
+                                                                     y.rs, y.cs, alpha, beta, nrhs, c.N);
+    else
+      cell_gemv_narrow_fixed<24><<<(unsigned)grid, 256, 0, c.stream>>>(mats, mstride, ld, mrows, x.p, x.rs, x.cs,
+                                                                      y.p, y.rs, y.cs, alpha, beta, nrhs, c.N);
+    FD_CHECK_LAUNCH();
+    return FETIDP_OK;
+  }
   if (mcols <= 32) {
     const long long total = c.N * mrows;
     long long grid = (total + 255) / 256;

@@ -38,7 +38,7 @@ __device__ __forceinline__ double bmax(double v, double* sh) {
   return r;
 }
 
-// out[row] = ||X[row]||_2 (mode 0), ||X[row]||_inf (mode 1), X[row] . z (mode 2)
+// out[row] = ||X[row]||_2 (mode 0), ||X[row]||_inf (mode 1), X[row] . z (mode 2), ||X[row]||_2^2 (mode 3)
 __global__ void row_reduce_kernel(const double* __restrict__ X, long long len,
                                   const double* __restrict__ z, int mode, double* __restrict__ out) {
   __shared__ double sh[32];
@@ -46,7 +46,7 @@ __global__ void row_reduce_kernel(const double* __restrict__ X, long long len,
   double acc = 0.0;
   for (long long t = threadIdx.x; t < len; t += blockDim.x) {
     const double v = x[t];
-    if (mode == 0) acc += v * v;
+    if (mode == 0 || mode == 3) acc += v * v;
     else if (mode == 1) acc = fmax(acc, fabs(v));
     else acc += v * z[t];
   }
@@ -111,20 +111,16 @@ __global__ void greedy_select_kernel(const double* __restrict__ inf, long long n
   }
 }
 
-// zeta_i = Delta[sigma_i] / ||Delta[sigma_i]||_2 (one block).
-__global__ void greedy_zeta_kernel(const double* __restrict__ D, long long len, int i,
+// zeta_i = Delta[sigma_i] / ||Delta[sigma_i]||_2, the squared norm taken from the previous step
+// (grid-stride over the row).
+__global__ void greedy_zeta_kernel(const double* __restrict__ D, const double* __restrict__ sq, long long len, int i,
                                    const GreedyState* __restrict__ st, double* __restrict__ zeta) {
-  __shared__ double sh[32];
-  __shared__ double snrm;
   if (st->count <= i) return;
-  const double* x = D + (long long)st->sigma[i] * len;
-  double acc = 0.0;
-  for (long long t = threadIdx.x; t < len; t += blockDim.x) acc += x[t] * x[t];
-  const double r = bsum(acc, sh);
-  if (threadIdx.x == 0) snrm = sqrt(r);
-  __syncthreads();
-  const double nrm = snrm;
-  for (long long t = threadIdx.x; t < len; t += blockDim.x) zeta[t] = x[t] / nrm;
+  const int sig = st->sigma[i];
+  const double* x = D + (long long)sig * len;
+  const double nrm = sqrt(sq[sig]);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len; t += (long long)gridDim.x * blockDim.x)
+    zeta[t] = x[t] / nrm;
 }
 
 // T[i][j] = zeta_i . A^(sigma_j) (the change of basis of Eq. 56), one block per (i, j).
@@ -160,27 +156,32 @@ __global__ void greedy_alpha_kernel(const double* __restrict__ T, const double* 
 // selection).  One block per row; the second pass re-reads the row from L2.
 __global__ void greedy_step_kernel(double* __restrict__ D, const double* __restrict__ zeta, long long len,
                                    double* __restrict__ beta_out, double* __restrict__ inf_out,
-                                   const GreedyState* __restrict__ st, int i) {
+                                   double* __restrict__ sq_out, const GreedyState* __restrict__ st, int i) {
   __shared__ double sh[32];
   __shared__ double sbeta;
   if (st->count <= i) return;                       // the greedy stopped before step i
   double* x = D + blockIdx.x * len;
   double acc = 0.0;
+#pragma unroll 4
   for (long long t = threadIdx.x; t < len; t += blockDim.x) acc += x[t] * zeta[t];
   const double beta = bsum(acc, sh);
   if (threadIdx.x == 0) sbeta = beta;
   __syncthreads();
   const double bt = sbeta;
-  double mx = 0.0;
+  double mx = 0.0, sq = 0.0;
+#pragma unroll 4
   for (long long t = threadIdx.x; t < len; t += blockDim.x) {
     const double v = x[t] - bt * zeta[t];
     x[t] = v;
     mx = fmax(mx, fabs(v));
+    sq += v * v;
   }
   const double m = bmax(mx, sh);
+  const double q = bsum(sq, sh);
   if (threadIdx.x == 0) {
     beta_out[blockIdx.x] = bt;
     inf_out[blockIdx.x] = m;
+    sq_out[blockIdx.x] = q;
   }
 }
 
@@ -321,8 +322,8 @@ fetidp_status k_row_update(Ctx& c, double* D, const double* beta, const double* 
 }
 
 fetidp_status k_greedy_step(Ctx& c, double* D, const double* zeta, long long rows, long long len, double* beta,
-                            double* inf, const GreedyState* st, int i) {
-  greedy_step_kernel<<<(unsigned)rows, kThreads, 0, c.stream>>>(D, zeta, len, beta, inf, st, i);
+                            double* inf, double* sq, const GreedyState* st, int i) {
+  greedy_step_kernel<<<(unsigned)rows, kThreads, 0, c.stream>>>(D, zeta, len, beta, inf, sq, st, i);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }
@@ -334,8 +335,9 @@ fetidp_status k_greedy_select(Ctx& c, const double* inf, long long n, int i, dou
   return FETIDP_OK;
 }
 
-fetidp_status k_greedy_zeta(Ctx& c, const double* D, long long len, int i, const GreedyState* st, double* zeta) {
-  greedy_zeta_kernel<<<1, 1024, 0, c.stream>>>(D, len, i, st, zeta);
+fetidp_status k_greedy_zeta(Ctx& c, const double* D, const double* sq, long long len, int i, const GreedyState* st,
+                            double* zeta) {
+  greedy_zeta_kernel<<<gridn(len), kThreads, 0, c.stream>>>(D, sq, len, i, st, zeta);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }

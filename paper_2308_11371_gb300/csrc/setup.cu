@@ -379,27 +379,30 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
   const int nrb_req = p.n_rb;
   if (nrb_req > kMaxRbGreedy) { set_error("n_rb above 64 is not supported"); return FETIDP_EINVAL; }
   double *Delta = nullptr, *nrm = nullptr, *vals = nullptr, *beta_d = nullptr, *Z = nullptr, *T = nullptr;
+  double* sq = nullptr;   // squared 2-norms of the residual rows
   GreedyState* gst = nullptr;
   FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Delta), sizeof(double) * c.N * c.nsnap));
   FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&nrm), sizeof(double) * c.N));
   FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&vals), sizeof(double) * c.N));
+  FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&sq), sizeof(double) * c.N));
   FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&beta_d), sizeof(double) * c.N * nrb_req));
   FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Z), sizeof(double) * c.nsnap * nrb_req));
   FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&T), sizeof(double) * nrb_req * nrb_req));
   FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&gst), sizeof(GreedyState)));
   auto free_greedy = [&]() {
-    tmp_free(c, Delta); tmp_free(c, nrm); tmp_free(c, vals); tmp_free(c, beta_d); tmp_free(c, Z); tmp_free(c, T); tmp_free(c, gst);
+    tmp_free(c, Delta); tmp_free(c, nrm); tmp_free(c, vals); tmp_free(c, sq); tmp_free(c, beta_d); tmp_free(c, Z); tmp_free(c, T); tmp_free(c, gst);
   };
   FD_CUDA(cudaMemsetAsync(gst, 0, sizeof(GreedyState), c.stream));
   FD_TRY(k_row_reduce(c, c.snap, c.N, c.nsnap, nullptr, 0, nrm));
   FD_TRY(k_row_normalise(c, c.snap, nrm, Delta, c.N, c.nsnap));
   FD_TRY(k_row_reduce(c, Delta, c.N, c.nsnap, nullptr, 1, vals));
+  FD_TRY(k_row_reduce(c, Delta, c.N, c.nsnap, nullptr, 3, sq));   // squared 2-norms
   for (int i = 0; i < nrb_req; ++i) {
     double* zeta = Z + (size_t)i * c.nsnap;
     FD_TRY(k_greedy_select(c, vals, c.N, i, p.tol_rb, kTieRel, gst));
-    FD_TRY(k_greedy_zeta(c, Delta, c.nsnap, i, gst, zeta));
-    // beta_i = Delta . zeta_i, Delta -= beta_i zeta_i, and the next infinity norms, in one pass
-    FD_TRY(k_greedy_step(c, Delta, zeta, c.N, c.nsnap, beta_d + (size_t)i * c.N, vals, gst, i));
+    FD_TRY(k_greedy_zeta(c, Delta, sq, c.nsnap, i, gst, zeta));
+    // beta_i = Delta . zeta_i, Delta -= beta_i zeta_i, the next infinity and squared 2-norms, one pass
+    FD_TRY(k_greedy_step(c, Delta, zeta, c.N, c.nsnap, beta_d + (size_t)i * c.N, vals, sq, gst, i));
   }
   GreedyState hst{};
   FD_CUDA(cudaMemcpyAsync(&hst, gst, sizeof(GreedyState), cudaMemcpyDeviceToHost, c.stream));
@@ -564,9 +567,7 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
     fetidp_status st = FETIDP_OK;
     st = tmp_alloc(c, reinterpret_cast<void**>(&Pkj), sizeof(double) * (size_t)nrb * nrb * np * np);
     if (st == FETIDP_OK) st = tmp_alloc(c, reinterpret_cast<void**>(&Spp), sizeof(double) * (size_t)c.N * np * np);
-    for (int k = 0; k < nrb && st == FETIDP_OK; ++k)
-      st = k_batched_gemm(c, true, false, np, np, nr, 1.0, Krp_d + (size_t)k * nr * np, 0, np, c.Urp, (long long)nr * np,
-                          np, 0.0, Pkj + (size_t)k * nrb * np * np, (long long)np * np, np, nrb);
+    if (st == FETIDP_OK) st = k_principal_pairs(c, Krp_d, Pkj);
     if (st == FETIDP_OK) st = k_spp_cells(c, Kpp_d, Pkj, Spp);
     if (st == FETIDP_OK) phase("S_pp per cell");
     if (st == FETIDP_OK) st = coarse_setup(c, Spp);
