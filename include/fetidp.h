@@ -129,7 +129,8 @@ typedef struct {
   int outer_its;            /* FGMRES iterations (max over RHS) */
   int inner_its_total;      /* PCG iterations summed over preconditioner applications */
   int n_rb;                 /* principal cells selected */
-  double rel_residual;      /* max over RHS of the true ||b - A x|| / ||b|| */
+  double rel_residual;      /* max over RHS of the true ||b - A x|| / ||b|| (a batch: divided by
+                               min over lattices of ||b_lattice||, which bounds the worst lattice) */
   double t_setup_s, t_solve_s;
   size_t device_bytes;      /* device workspace held by the context */
 } fetidp_info;
@@ -141,13 +142,26 @@ fetidp_status fetidp_sizes(const fetidp_ctx *ctx, long long out[12]);
 
 void fetidp_default_options(fetidp_options *opt);
 
-/* Build the context for one lattice (n_problems must be 1): maps B, A_p, D
- * (Eqs. 14-18); snapshots of C_hat at every Gauss point (Eq. 52); greedy
- * principal cells and alpha (Algorithm 4, Eqs. 55-56); principal factorisations
- * and operators (Eq. 39); pi, delta (Eqs. 40-42); ROM local operators and the
- * coarse S_PP factorisation (Eq. 43, Sec. 3.2.1).  cuda_stream is a
- * cudaStream_t (may be NULL).  On success *out owns all workspace.
- * Errors: EINVAL (bad sizes, n_problems != 1), ENOMEM, ECUDA, ESINGULAR.     */
+/* Where each lattice of a batch sits: cell0[b], L0[b], P0[b] (b = 0..B) are the first cell,
+ * multiplier row and primal DOF of lattice b, and [B] the totals (N, L, n_P).  Arrays of B + 1
+ * entries (host memory), any may be NULL; B = n_problems of fetidp_setup. */
+fetidp_status fetidp_batch_layout(const fetidp_ctx *ctx, long long *cell0, long long *L0, long long *P0);
+
+/* Build the context for n_problems >= 1 lattices: maps B, A_p, D (Eqs. 14-18);
+ * snapshots of C_hat at every Gauss point (Eq. 52); greedy principal cells and
+ * alpha (Algorithm 4, Eqs. 55-56); principal factorisations and operators
+ * (Eq. 39); pi, delta (Eqs. 40-42); ROM local operators and the coarse S_PP
+ * factorisation (Eq. 43, Sec. 3.2.1).  cuda_stream is a cudaStream_t (may be
+ * NULL).  On success *out owns all workspace.
+ * Batch (n_problems > 1): the lattices are solved together as one block-diagonal
+ * system.  They share the reference cell (dim, elems), the material law and mask
+ * and the number of load cases; sizes, radii, macro maps, clamped faces and loads
+ * are their own.  One reduced basis is selected from the snapshots of all cells
+ * (n_rb, tol_rb of probs[0]); the principal operators serve every lattice.  Cells,
+ * multipliers and primal DOF of the lattices follow each other in the context's
+ * vectors (fetidp_batch_layout).  The outer solve stops when every lattice's
+ * relative residual is <= tol_outer.
+ * Errors: EINVAL (bad sizes, incompatible lattices), ENOMEM, ECUDA, ESINGULAR. */
 fetidp_status fetidp_setup(const fetidp_problem *probs, int n_problems,
                            const fetidp_options *opt, void *cuda_stream, fetidp_ctx **out);
 

@@ -30,7 +30,7 @@ SYMBOLS = ["fetidp_sizes", "fetidp_default_options", "fetidp_setup", "fetidp_app
            "fetidp_status_string", "fetidp_last_error", "fetidp_profile_enable",
            "fetidp_profile_read", "fetidp_kernel_launches", "fetidp_tc_selfcheck",
            "fetidp_tc_comb_selfcheck", "fetidp_tc_selfcheck_static",
-           "fetidp_compliance"]
+           "fetidp_compliance", "fetidp_batch_layout"]
 
 KCLASS = {"grouped_gemm": 0, "apply_K": 1, "maps": 2, "coarse": 3, "cell_gemv": 4, "vector": 5,
           "gram": 6, "tc_gemm": 7, "setup": 8}
@@ -118,6 +118,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.fetidp_grad.argtypes = [P, V, V, V]
     lib.fetidp_compliance.restype = I
     lib.fetidp_compliance.argtypes = [P, V, V]
+    lib.fetidp_batch_layout.restype = I
+    lib.fetidp_batch_layout.argtypes = [P, V, V, V]
     lib.fetidp_rom_data.restype = I
     lib.fetidp_rom_data.argtypes = [P, V, V, V, V]
     lib.fetidp_destroy.restype = None
@@ -192,18 +194,26 @@ def _ptr(t) -> int:
 class Solver:
     """One FETI-DP context on the current CUDA device and torch's current stream."""
 
-    def __init__(self, problem: LatticeProblem, precision: int = FETIDP_FP64, stream=None, **opts):
+    def __init__(self, problem, precision: int = FETIDP_FP64, stream=None, **opts):
+        """``problem``: one LatticeProblem, or a list of them solved together as a batch."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("CUDA is not available; the FETI-DP library has no CPU path")
         lib = load()
+        probs = list(problem) if isinstance(problem, (list, tuple)) else [problem]
         self.problem = problem
+        self.n_lattices = len(probs)
         self.options = default_options(precision=precision, **opts)
         st = stream if stream is not None else torch.cuda.current_stream()
         self.stream = st
-        s, self._keep = make_problem_struct(problem)
+        arr = (Problem * len(probs))()
+        self._keep = []
+        for i, q in enumerate(probs):
+            s, keep = make_problem_struct(q)
+            arr[i] = s
+            self._keep.append(keep)
         h = ctypes.c_void_p()
-        _check(lib.fetidp_setup(ctypes.byref(s), 1, ctypes.byref(self.options),
+        _check(lib.fetidp_setup(arr, len(probs), ctypes.byref(self.options),
                                 ctypes.c_void_p(st.cuda_stream), ctypes.byref(h)))
         self._h = h
         sz = (ctypes.c_longlong * 12)()
@@ -284,6 +294,15 @@ class Solver:
         c = np.zeros(self.n_rhs)
         _check(load().fetidp_compliance(self._h, ctypes.c_void_p(_ptr(u)), ctypes.c_void_p(c.ctypes.data)))
         return c
+
+    def batch_layout(self):
+        """(cell0, L0, P0): first cell, multiplier row and primal DOF of every lattice, then the
+        totals (numpy arrays of n_lattices + 1 entries)."""
+        B = self.n_lattices
+        cell0, L0, P0 = (np.zeros(B + 1, np.int64) for _ in range(3))
+        _check(load().fetidp_batch_layout(self._h, ctypes.c_void_p(cell0.ctypes.data),
+                                          ctypes.c_void_p(L0.ctypes.data), ctypes.c_void_p(P0.ctypes.data)))
+        return cell0, L0, P0
 
     def rom_data(self):
         k, N = self.n_rb, self.N

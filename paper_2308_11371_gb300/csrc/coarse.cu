@@ -25,7 +25,8 @@ __global__ void bcr_gather_kernel(const int* __restrict__ perm, const double* __
        t += (long long)gridDim.x * blockDim.x) {
     const int rhs = (int)(t / len);
     const long long q = t - rhs * len;
-    bl[rhs * bl_rs + q] = b[rhs * b_rs + perm[q]];
+    const int pq = perm[q];   // < 0: padding position of a smaller lattice's slab
+    bl[rhs * bl_rs + q] = pq >= 0 ? b[rhs * b_rs + pq] : 0.0;
   }
 }
 
@@ -36,7 +37,18 @@ __global__ void bcr_scatter_kernel(const int* __restrict__ perm, const double* _
        t += (long long)gridDim.x * blockDim.x) {
     const int rhs = (int)(t / len);
     const long long q = t - rhs * len;
-    x[rhs * x_rs + perm[q]] = xl[rhs * xl_rs + q];
+    const int pq = perm[q];
+    if (pq >= 0) x[rhs * x_rs + pq] = xl[rhs * xl_rs + q];
+  }
+}
+
+// Identity on the padding positions of every slab block (positions past the slab's own size).
+__global__ void bcr_pad_identity_kernel(double* __restrict__ A, long long bb, int b, const int* __restrict__ real,
+                                        int nslab) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)nslab * b;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int sl = (int)(t / b), p = (int)(t - (long long)sl * b);
+    if (p >= real[sl]) A[sl * bb + (long long)p * b + p] = 1.0;
   }
 }
 
@@ -180,55 +192,63 @@ inline unsigned grid_exact(long long threads_total, int threads = 256) {
 fetidp_status coarse_setup(Ctx& c, const double* Spp_dev) {
   const int d = c.d;
   CoarseBCR& B = c.bcr;
-  // ---- slab axis: longest vertex axis, ties -> highest axis index
-  int vd[3] = {1, 1, 1};
-  for (int k = 0; k < d; ++k) vd[k] = c.geo.nc[k] + 1;
-  int ax = 0;
-  for (int k = 1; k < d; ++k)
-    if (vd[k] >= vd[ax]) ax = k;
-  const int ca = c.clamp_axis, cs = c.clamp_side;
-  const int clamp_val = cs == 0 ? 0 : vd[ca] - 1;
-  // free vertex numbering (lexicographic, x fastest) must match setup's
-  const long long nvert = (long long)vd[0] * vd[1] * vd[2];
-  std::vector<int> vnum(nvert, -1);
-  {
-    int q = 0;
+  // ---- slabs of every lattice (the vertex planes normal to its longest axis, ties -> highest
+  //      axis; a fully clamped plane is skipped), concatenated lattice after lattice.  The coarse
+  //      matrix is block-diagonal over lattices, so the chains of slab blocks simply follow each
+  //      other with zero coupling; slabs are padded to the largest size with identity.
+  struct SlabMap {
+    std::vector<int> vslab, vpos;   // per local vertex: global slab, position in it (-1: clamped)
+  };
+  std::vector<SlabMap> maps(c.lat.size());
+  std::vector<int> slab_real;       // DOF per slab (before padding)
+  std::vector<std::vector<int>> slab_dofs;   // per slab: global primal DOF at each position
+  int nb = 0, bmax = 0;
+  for (size_t bl = 0; bl < c.lat.size(); ++bl) {
+    const LatticeSpan& ls = c.lat[bl];
+    int vd[3] = {1, 1, 1};
+    for (int k = 0; k < d; ++k) vd[k] = ls.geo.nc[k] + 1;
+    int ax = 0;
+    for (int k = 1; k < d; ++k)
+      if (vd[k] >= vd[ax]) ax = k;
+    const int ca = ls.clamp_axis, cs = ls.clamp_side;
+    const int clamp_val = cs == 0 ? 0 : vd[ca] - 1;
+    const long long nvert = (long long)vd[0] * vd[1] * vd[2];
+    std::vector<int> vnum(nvert, -1);
+    {
+      int q = 0;   // free vertex numbering (lexicographic, x fastest) as in setup, then + V0
+      for (long long v = 0; v < nvert; ++v) {
+        const int ijk[3] = {(int)(v % vd[0]), (int)((v / vd[0]) % vd[1]), (int)(v / ((long long)vd[0] * vd[1]))};
+        if (ijk[ca] != clamp_val) vnum[v] = (int)ls.V0 + q++;
+      }
+    }
+    std::vector<int> slab_of(vd[ax], -1);
+    const int nb0 = nb;
+    for (int sl = 0; sl < vd[ax]; ++sl) {
+      if (ax == ca && sl == clamp_val) continue;
+      slab_of[sl] = nb++;
+    }
+    slab_real.resize(nb, 0);
+    slab_dofs.resize(nb);
+    SlabMap& mp = maps[bl];
+    mp.vslab.assign(nvert, -1);
+    mp.vpos.assign(nvert, -1);
     for (long long v = 0; v < nvert; ++v) {
+      if (vnum[v] < 0) continue;
       const int ijk[3] = {(int)(v % vd[0]), (int)((v / vd[0]) % vd[1]), (int)(v / ((long long)vd[0] * vd[1]))};
-      if (ijk[ca] != clamp_val) vnum[v] = q++;
+      const int sl = slab_of[ijk[ax]];
+      mp.vslab[v] = sl;
+      mp.vpos[v] = slab_real[sl] / d;
+      for (int comp = 0; comp < d; ++comp) slab_dofs[sl].push_back(vnum[v] * d + comp);
+      slab_real[sl] += d;
     }
+    for (int sl = nb0; sl < nb; ++sl) bmax = std::max(bmax, slab_real[sl]);
   }
-  // slabs along ax (skipping a fully clamped slab), position of each free vertex in its slab
-  std::vector<int> slab_of(vd[ax], -1);
-  int nb = 0;
-  for (int s = 0; s < vd[ax]; ++s) {
-    if (ax == ca && s == clamp_val) continue;
-    slab_of[s] = nb++;
-  }
-  std::vector<int> vslab(nvert, -1), vpos(nvert, -1);
-  std::vector<int> count(nb, 0);
-  for (long long v = 0; v < nvert; ++v) {
-    if (vnum[v] < 0) continue;
-    const int ijk[3] = {(int)(v % vd[0]), (int)((v / vd[0]) % vd[1]), (int)(v / ((long long)vd[0] * vd[1]))};
-    const int sl = slab_of[ijk[ax]];
-    vslab[v] = sl;
-    vpos[v] = count[sl]++;
-  }
-  const int bv = count[0];
-  for (int s = 1; s < nb; ++s)
-    if (count[s] != bv) {
-      set_error("coarse: unequal slab sizes");
-      return FETIDP_EINVAL;
-    }
-  const int b = bv * d;
+  const int b = bmax;
   B.b = b;
   B.nb = nb;
-  std::vector<int> perm((size_t)nb * b);
-  for (long long v = 0; v < nvert; ++v) {
-    if (vnum[v] < 0) continue;
-    for (int comp = 0; comp < d; ++comp)
-      perm[(size_t)vslab[v] * b + vpos[v] * d + comp] = vnum[v] * d + comp;
-  }
+  std::vector<int> perm((size_t)nb * b, -1);
+  for (int sl = 0; sl < nb; ++sl)
+    for (size_t q = 0; q < slab_dofs[sl].size(); ++q) perm[(size_t)sl * b + q] = slab_dofs[sl][q];
   // ---- level structure and the device pool: per level l with n_l blocks, regions
   //      A (Ainv at odd slots after the level), U, U^T, V, V^T of n_l blocks each; the reduced
   //      block of the last level (then its inverse) follows.
@@ -248,16 +268,31 @@ fetidp_status coarse_setup(Ctx& c, const double* Spp_dev) {
   FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Cbuf[0]), sizeof(double) * cmax));
   FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Cbuf[1]), sizeof(double) * cmax));
   FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&work), sizeof(double) * 2 * (size_t)(nb / 2 + 1) * (b + 1)));
-  FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&vslab_d), sizeof(int) * nvert));
-  FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&vpos_d), sizeof(int) * nvert));
+  size_t nvert_all = 0;
+  for (const SlabMap& mp : maps) nvert_all += mp.vslab.size();
+  FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&vslab_d), sizeof(int) * nvert_all));
+  FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&vpos_d), sizeof(int) * nvert_all));
+  int* real_d = nullptr;
+  FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&real_d), sizeof(int) * nb));
   FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&st_d), sizeof(int)));
-  FD_CUDA(cudaMemcpyAsync(vslab_d, vslab.data(), sizeof(int) * nvert, cudaMemcpyHostToDevice, c.stream));
-  FD_CUDA(cudaMemcpyAsync(vpos_d, vpos.data(), sizeof(int) * nvert, cudaMemcpyHostToDevice, c.stream));
+  std::vector<size_t> voff(maps.size() + 1, 0);
+  for (size_t bl = 0; bl < maps.size(); ++bl) {
+    FD_CUDA(cudaMemcpyAsync(vslab_d + voff[bl], maps[bl].vslab.data(), sizeof(int) * maps[bl].vslab.size(),
+                            cudaMemcpyHostToDevice, c.stream));
+    FD_CUDA(cudaMemcpyAsync(vpos_d + voff[bl], maps[bl].vpos.data(), sizeof(int) * maps[bl].vpos.size(),
+                            cudaMemcpyHostToDevice, c.stream));
+    voff[bl + 1] = voff[bl] + maps[bl].vslab.size();
+  }
+  FD_CUDA(cudaMemcpyAsync(real_d, slab_real.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, c.stream));
   FD_CUDA(cudaMemsetAsync(st_d, 0, sizeof(int), c.stream));
   FD_CUDA(cudaMemsetAsync(P, 0, sizeof(double) * (size_t)nb * bb, c.stream));
   FD_CUDA(cudaMemsetAsync(Cbuf[0], 0, sizeof(double) * cmax, c.stream));
   // ---- diagonal blocks A_i and couplings C_i = S(slab i, slab i+1) from the per-cell S_pp
-  FD_TRY(k_coarse_assemble(c, Spp_dev, vslab_d, vpos_d, b, P + base[0], Cbuf[0]));
+  for (size_t bl = 0; bl < maps.size(); ++bl)
+    FD_TRY(k_coarse_assemble(c, c.lat[bl], Spp_dev + c.lat[bl].cell0 * c.np * c.np, vslab_d + voff[bl],
+                             vpos_d + voff[bl], b, P + base[0], Cbuf[0]));
+  bcr_pad_identity_kernel<<<gridn((long long)nb * b), 256, 0, c.stream>>>(P + base[0], bb, b, real_d, nb);
+  FD_CHECK_LAUNCH();
   // ---- block cyclic reduction on the device
   B.off_Ainv.assign(levels, {}); B.off_U.assign(levels, {}); B.off_UT.assign(levels, {});
   B.off_V.assign(levels, {}); B.off_VT.assign(levels, {});
@@ -312,7 +347,7 @@ fetidp_status coarse_setup(Ctx& c, const double* Spp_dev) {
     FD_CUDA(cudaMemcpyAsync(&hst, st_d, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     FD_CUDA(cudaStreamSynchronize(c.stream));
   }
-  tmp_free(c, Cbuf[0]); tmp_free(c, Cbuf[1]); tmp_free(c, work); tmp_free(c, vslab_d); tmp_free(c, vpos_d); tmp_free(c, st_d);
+  tmp_free(c, Cbuf[0]); tmp_free(c, Cbuf[1]); tmp_free(c, work); tmp_free(c, vslab_d); tmp_free(c, vpos_d); tmp_free(c, real_d); tmp_free(c, st_d);
   FD_TRY(st);
   if (hst != 0) {
     set_error("coarse S_PP is not positive definite");

@@ -169,6 +169,16 @@ struct Prof {
   long long launches[FETIDP_K_NCLASS] = {};
 };
 
+// One lattice of a batch: its geometry and where its cells, multipliers and free vertices sit in
+// the concatenated vectors of the context.
+struct LatticeSpan {
+  Geo geo{};
+  long long cell0 = 0, ncell = 0;   // cells [cell0, cell0 + ncell)
+  long long L0 = 0, nL = 0;         // multiplier rows
+  long long V0 = 0, nV = 0;         // free vertices (primal DOF = vertex * d + component)
+  int clamp_axis = 0, clamp_side = 0;
+};
+
 struct Ctx {
   Prof prof;
   double prof_pending_flops = 0.0, prof_pending_bytes = 0.0;
@@ -183,8 +193,12 @@ struct Ctx {
   long long N = 0, L = 0, nP = 0, ntot = 0;
   int m = 0;        // RHS
   int nrb = 0;      // principal cells selected
-  int nV = 0;       // free lattice vertices
+  int nV = 0;       // free lattice vertices (all lattices)
   int clamp_axis = 0, clamp_side = 0;
+  std::vector<LatticeSpan> lat;   // the lattices of the context (one unless batched)
+  // per RHS: min over lattices of ||f_b|| / ||f||; the outer solve targets tol * this so that
+  // every lattice meets tol relative to its own load
+  std::vector<double> tol_scale;
   std::vector<int> sigma;
   std::vector<double> r_cell;
   double t_setup_s = 0.0;
@@ -335,8 +349,9 @@ fetidp_status k_batched_gemm(Ctx& c, bool ta, bool tb, int M, int N, int K, doub
 fetidp_status k_batched_symmetrize(Ctx& c, double* A, long long stride, int n, int lda, int batch);
 fetidp_status k_principal_pairs(Ctx& c, const double* Krp, double* P);   // P_kj = K_rp^(k)T U_rp^(j)
 fetidp_status k_spp_cells(Ctx& c, const double* Kpp, const double* P, double* out);
-fetidp_status k_coarse_assemble(Ctx& c, const double* Spp, const int* vslab, const int* vpos, int b, double* A,
-                                double* C);
+struct LatticeSpan;
+fetidp_status k_coarse_assemble(Ctx& c, const LatticeSpan& ls, const double* Spp, const int* vslab, const int* vpos,
+                                int b, double* A, double* C);
 fetidp_status k_gram_direct(Ctx& c, const double* Y, int ntab, const double* dvec, double* pi, double* delta,
                            double drop_rel);
 fetidp_status k_batched_diag_sum(Ctx& c, const double* A, long long stride, int lda, int r0, int m, int batch,
@@ -384,7 +399,7 @@ fetidp_status tc_comb_apply(Ctx& c, const TcComb& op, CCellVec X, const double* 
                             long long ncell);
 
 // ---------------------------------------------------------------- setup / coarse
-fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_options& o);
+fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, const fetidp_options& o);
 fetidp_status coarse_setup(Ctx& c, const double* Spp_dev);   // per-cell S_pp_ring on the device
 fetidp_status coarse_solve(Ctx& c, const double* b, long long b_rs, double* x, long long x_rs,
                            int nrhs);

@@ -558,13 +558,13 @@ fetidp_status k_spp_cells(Ctx& c, const double* Kpp, const double* P, double* ou
   return FETIDP_OK;
 }
 
-fetidp_status k_coarse_assemble(Ctx& c, const double* Spp, const int* vslab, const int* vpos, int b, double* A,
-                                double* C) {
+fetidp_status k_coarse_assemble(Ctx& c, const LatticeSpan& ls, const double* Spp, const int* vslab, const int* vpos,
+                                int b, double* A, double* C) {
   const int nck = 1 << c.d;
-  const int vdx = c.geo.nc[0] + 1, vdy = c.geo.nc[1] + 1;
+  const int vdx = ls.geo.nc[0] + 1, vdy = ls.geo.nc[1] + 1;
   for (int color = 0; color < nck; ++color) {
-    coarse_assemble_kernel<<<grid_for(c.N * nck * nck, 256), 256, 0, c.stream>>>(
-        Spp, c.N, c.d, nck, c.np, c.geo.nc[0], c.geo.nc[1], vdx, vdy, vslab, vpos, b, A, C, color);
+    coarse_assemble_kernel<<<grid_for(ls.ncell * nck * nck, 256), 256, 0, c.stream>>>(
+        Spp, ls.ncell, c.d, nck, c.np, ls.geo.nc[0], ls.geo.nc[1], vdx, vdy, vslab, vpos, b, A, C, color);
     FD_CHECK_LAUNCH();
   }
   return FETIDP_OK;

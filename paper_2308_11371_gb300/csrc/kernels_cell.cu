@@ -790,16 +790,16 @@ __global__ void gram_direct_kernel(const double* __restrict__ Y, int ntab, int n
 // g[rhs][cell] = - sum_e sum_gp w G(w)^T dC_hat/dr G(u), one block per (rhs, cell).
 template <int D>
 __global__ void grad_kernel(Geo g, const double* __restrict__ r_cell, long long ncell, int n,
-                            const double* __restrict__ u, const double* __restrict__ w,
-                            double* __restrict__ out, double wq, double inv_h) {
+                            const double* __restrict__ u, const double* __restrict__ w, long long u_rs,
+                            double* __restrict__ out, long long out_rs, double wq, double inv_h) {
   extern __shared__ double sm[];
   constexpr int NA = 1 << D;
   constexpr int NI = D * D;
   const long long col = blockIdx.x;
   const int rhs = (int)(col / ncell);
-  const long long cell = col - (long long)rhs * ncell;
-  const double* uc = u + col * n;
-  const double* wc = w + col * n;
+  const long long cell = col - (long long)rhs * ncell;   // cell within this launch's lattice
+  const double* uc = u + rhs * u_rs + cell * n;
+  const double* wc = w + rhs * u_rs + cell * n;
   double* us = sm;
   double* ws = sm + n;
   for (int t = threadIdx.x; t < n; t += blockDim.x) { us[t] = uc[t]; ws[t] = wc[t]; }
@@ -859,7 +859,7 @@ __global__ void grad_kernel(Geo g, const double* __restrict__ r_cell, long long 
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k];
-    out[col] = -s;
+    out[rhs * out_rs + cell] = -s;
   }
 }
 
@@ -870,8 +870,11 @@ fetidp_status k_snapshots(Ctx& c) {
   const long long total = c.N * c.nelem * c.ngp;
   int grid = ceil_div(total, 256);
   if (grid > 152 * 32) grid = 152 * 32;
-  snapshot_kernel<<<grid, 256, 0, c.stream>>>(c.geo, c.r_dev, c.N, c.nelem, c.ngp, c.nc, c.snap);
-  FD_CHECK_LAUNCH();
+  for (const LatticeSpan& ls : c.lat) {   // one launch per lattice: its own geometry and radii
+    snapshot_kernel<<<grid, 256, 0, c.stream>>>(ls.geo, c.r_dev + ls.cell0, ls.ncell, c.nelem, c.ngp, c.nc,
+                                                c.snap + ls.cell0 * c.nsnap);
+    FD_CHECK_LAUNCH();
+  }
   return FETIDP_OK;
 }
 
@@ -1051,11 +1054,16 @@ fetidp_status k_grad(Ctx& c, const double* u, const double* w, double* g) {
   const double h = 1.0 / c.e;
   const double wq = pow(0.5 * h, c.d);
   const size_t smem = 2 * (size_t)c.n * sizeof(double);
-  const dim3 grid((unsigned)(c.N * c.m));
-  if (c.d == 2) {
-    grad_kernel<2><<<grid, 256, smem, c.stream>>>(c.geo, c.r_dev, c.N, c.n, u, w, g, wq, 1.0 / h);
-  } else {
-    grad_kernel<3><<<grid, 256, smem, c.stream>>>(c.geo, c.r_dev, c.N, c.n, u, w, g, wq, 1.0 / h);
+  for (const LatticeSpan& ls : c.lat) {   // one launch per lattice: its own geometry and radii
+    const dim3 grid((unsigned)(ls.ncell * c.m));
+    const long long off = ls.cell0 * c.n;
+    if (c.d == 2)
+      grad_kernel<2><<<grid, 256, smem, c.stream>>>(ls.geo, c.r_dev + ls.cell0, ls.ncell, c.n, u + off, w + off,
+                                                    c.N * c.n, g + ls.cell0, c.N, wq, 1.0 / h);
+    else
+      grad_kernel<3><<<grid, 256, smem, c.stream>>>(ls.geo, c.r_dev + ls.cell0, ls.ncell, c.n, u + off, w + off,
+                                                    c.N * c.n, g + ls.cell0, c.N, wq, 1.0 / h);
+    FD_CHECK_LAUNCH();
   }
   FD_CHECK_LAUNCH();
   return FETIDP_OK;

@@ -159,7 +159,7 @@ fetidp_status upload(Ctx& c, T** dst, const std::vector<T>& src) {
 
 }  // namespace
 
-fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_options& o) {
+fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, const fetidp_options& o) {
   using namespace host;
   auto t0 = std::chrono::steady_clock::now();
   // FETIDP_VERBOSE=1: synchronise after each phase and print its wall time to stderr
@@ -174,20 +174,34 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
     tp = now;
   };
   // ---------------------------------------------------------------- validation
-  if (p.dim != 2 && p.dim != 3) { set_error("dim must be 2 or 3"); return FETIDP_EINVAL; }
-  if (p.elems < 2) { set_error("elems must be >= 2"); return FETIDP_EINVAL; }
-  for (int k = 0; k < 3; ++k)
-    if (p.cells[k] < 1 || (p.dim == 2 && k == 2 && p.cells[2] != 1)) {
-      set_error("bad cell counts"); return FETIDP_EINVAL;
+  // A batch shares the reference cell (dim, elems), the material law and mask, the load count
+  // and the reduced basis (n_rb, tol_rb of the first lattice); sizes, radii, macro maps, clamped
+  // faces and load cases are per lattice.
+  if (nprob < 1 || !probs) { set_error("no lattice"); return FETIDP_EINVAL; }
+  const fetidp_problem& p = probs[0];
+  for (int bl = 0; bl < nprob; ++bl) {
+    const fetidp_problem& q = probs[bl];
+    if (q.dim != 2 && q.dim != 3) { set_error("dim must be 2 or 3"); return FETIDP_EINVAL; }
+    if (q.elems < 2) { set_error("elems must be >= 2"); return FETIDP_EINVAL; }
+    for (int k = 0; k < 3; ++k)
+      if (q.cells[k] < 1 || (q.dim == 2 && k == 2 && q.cells[2] != 1)) {
+        set_error("bad cell counts"); return FETIDP_EINVAL;
+      }
+    if (q.n_loads < 1 || !q.load_kind || !q.load_dir || !q.r_cell) {
+      set_error("missing loads or radii"); return FETIDP_EINVAL;
     }
-  if (p.n_loads < 1 || !p.load_kind || !p.load_dir || !p.r_cell) {
-    set_error("missing loads or radii"); return FETIDP_EINVAL;
-  }
-  if (p.n_rb < 1 || p.n_rb > 64) { set_error("n_rb must be in [1, 64]"); return FETIDP_EINVAL; }
-  if (p.clamp_axis < 0 || p.clamp_axis >= p.dim) { set_error("bad clamp axis"); return FETIDP_EINVAL; }
-  if (!(p.nu > -1.0 && p.nu < 0.5)) { set_error("nu out of range"); return FETIDP_EINVAL; }
-  if (p.mask_kind < 0 || p.mask_kind > 2 || (p.dim == 2) != (p.mask_kind == 0)) {
-    set_error("mask kind does not match the dimension"); return FETIDP_EINVAL;
+    if (q.n_rb < 1 || q.n_rb > 64) { set_error("n_rb must be in [1, 64]"); return FETIDP_EINVAL; }
+    if (q.clamp_axis < 0 || q.clamp_axis >= q.dim) { set_error("bad clamp axis"); return FETIDP_EINVAL; }
+    if (!(q.nu > -1.0 && q.nu < 0.5)) { set_error("nu out of range"); return FETIDP_EINVAL; }
+    if (q.mask_kind < 0 || q.mask_kind > 2 || (q.dim == 2) != (q.mask_kind == 0)) {
+      set_error("mask kind does not match the dimension"); return FETIDP_EINVAL;
+    }
+    if (q.dim != p.dim || q.elems != p.elems || q.mask_kind != p.mask_kind || q.nu != p.nu ||
+        q.E_solid != p.E_solid || q.E_void != p.E_void || q.mask_width != p.mask_width ||
+        q.n_loads != p.n_loads) {
+      set_error("lattices of a batch must share dim, elems, material, mask and the number of loads");
+      return FETIDP_EINVAL;
+    }
   }
   if (o.max_outer < 1 || o.max_inner < 1) { set_error("bad iteration limits"); return FETIDP_EINVAL; }
   c.opt = o;
@@ -198,15 +212,26 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
     return FETIDP_EINVAL;
   }
   const int d = p.dim, e = p.elems;
-  Geo& g = c.geo;
-  g.dim = d; g.e = e;
-  for (int k = 0; k < 3; ++k) g.nc[k] = p.cells[k];
-  g.mask_kind = p.mask_kind; g.map_kind = p.map_kind;
-  g.mask_width = p.mask_width; g.E_solid = p.E_solid; g.E_void = p.E_void; g.nu = p.nu;
-  for (int k = 0; k < 8; ++k) g.mp[k] = p.map_params[k];
+  c.lat.assign(nprob, LatticeSpan{});
+  c.N = 0;
+  for (int bl = 0; bl < nprob; ++bl) {
+    const fetidp_problem& q = probs[bl];
+    LatticeSpan& ls = c.lat[bl];
+    Geo& g = ls.geo;
+    g.dim = d; g.e = e;
+    for (int k = 0; k < 3; ++k) g.nc[k] = q.cells[k];
+    g.mask_kind = q.mask_kind; g.map_kind = q.map_kind;
+    g.mask_width = q.mask_width; g.E_solid = q.E_solid; g.E_void = q.E_void; g.nu = q.nu;
+    for (int k = 0; k < 8; ++k) g.mp[k] = q.map_params[k];
+    ls.cell0 = c.N;
+    ls.ncell = (long long)q.cells[0] * q.cells[1] * q.cells[2];
+    ls.clamp_axis = q.clamp_axis;
+    ls.clamp_side = q.clamp_side;
+    c.N += ls.ncell;
+  }
+  c.geo = c.lat[0].geo;
   c.d = d; c.e = e;
   c.clamp_axis = p.clamp_axis; c.clamp_side = p.clamp_side;
-  c.N = (long long)p.cells[0] * p.cells[1] * p.cells[2];
   c.m = p.n_loads;
   c.ncorner = 1 << d;
   c.nelem = d == 2 ? e * e : e * e * e;
@@ -216,7 +241,8 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
   RefCell ref = build_ref(d, e, c.ni, c.nd, c.np);
   c.n = (int)ref.perm.size();
   c.nr = c.ni + c.nd;
-  c.r_cell.assign(p.r_cell, p.r_cell + c.N);
+  c.r_cell.clear();
+  for (int bl = 0; bl < nprob; ++bl) c.r_cell.insert(c.r_cell.end(), probs[bl].r_cell, probs[bl].r_cell + c.lat[bl].ncell);
   {
     std::vector<int> pp(ref.perm);
     pp.insert(pp.end(), ref.iperm.begin(), ref.iperm.end());
@@ -226,8 +252,6 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
   phase("reference tables");
 
   // ---------------------------------------------------------------- multipliers (Eqs. 14-15)
-  const int nx = p.cells[0], ny = p.cells[1], nz = p.cells[2];
-  const long long gd[3] = {(long long)nx * e + 1, (long long)ny * e + 1, d == 3 ? (long long)nz * e + 1 : 1};
   const int nn1 = e + 1;
   std::vector<int> gath((size_t)c.N * c.nd * 2, 0);
   std::vector<int> scat;
@@ -238,7 +262,13 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
     scat.reserve(2 * est);
     Dw.reserve(est);
   }
-  const long long clamp_coord = p.clamp_side ? (long long)p.cells[p.clamp_axis] * e : 0;
+  for (int bl = 0; bl < nprob; ++bl) {
+  const fetidp_problem& pl = probs[bl];
+  const long long cell0 = c.lat[bl].cell0;
+  c.lat[bl].L0 = (long long)Dw.size();
+  const int nx = pl.cells[0], ny = pl.cells[1], nz = pl.cells[2];
+  const long long gd[3] = {(long long)nx * e + 1, (long long)ny * e + 1, d == 3 ? (long long)nz * e + 1 : 1};
+  const long long clamp_coord = pl.clamp_side ? (long long)pl.cells[pl.clamp_axis] * e : 0;
   for (long long gz = 0; gz < gd[2]; ++gz)
     for (long long gy = 0; gy < gd[1]; ++gy)
       for (long long gx = 0; gx < gd[0]; ++gx) {
@@ -250,7 +280,7 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
         int cand[3][2], ncand[3];
         for (int k = 0; k < 3; ++k) {
           if (k >= d) { cand[k][0] = 0; ncand[k] = 1; continue; }
-          const int nk = p.cells[k];
+          const int nk = pl.cells[k];
           if (gc[k] % e == 0) {
             const int q = (int)(gc[k] / e);
             ncand[k] = 0;
@@ -267,7 +297,7 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
           for (int b = 0; b < ncand[1]; ++b)
             for (int q = 0; q < ncand[2]; ++q) {
               const int cx = cand[0][a], cy = cand[1][b], cz = cand[2][q];
-              const long long s = cx + (long long)nx * (cy + (long long)ny * cz);
+              const long long s = cell0 + cx + (long long)nx * (cy + (long long)ny * cz);
               const int lx = (int)(gx - (long long)cx * e), ly = (int)(gy - (long long)cy * e);
               const int lz = d == 3 ? (int)(gz - (long long)cz * e) : 0;
               const int lnode = lx + nn1 * (ly + nn1 * lz);
@@ -275,7 +305,7 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
               while (pos > 0 && own[pos - 1].first > s) { own[pos] = own[pos - 1]; --pos; }
               own[pos] = {s, ref.dual_pos[lnode]};
             }
-        const bool clamped = gc[p.clamp_axis] == clamp_coord;
+        const bool clamped = gc[pl.clamp_axis] == clamp_coord;
         auto add_gath = [&](long long s, int j, int code) {
           int* gp2 = &gath[((size_t)s * c.nd + j) * 2];
           if (gp2[0] == 0) gp2[0] = code;
@@ -305,6 +335,8 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
             }
         }
       }
+  c.lat[bl].nL = (long long)Dw.size() - c.lat[bl].L0;
+  }
   c.L = (long long)Dw.size();
   FD_TRY(upload(c, &c.gath, gath));
   FD_TRY(upload(c, &c.scat, scat));
@@ -312,33 +344,45 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
   phase("multiplier maps");
 
   // ---------------------------------------------------------------- primal DOF (Eq. 18)
-  const int vd[3] = {nx + 1, ny + 1, d == 3 ? nz + 1 : 1};
-  const long long nvert = (long long)vd[0] * vd[1] * vd[2];
-  const int cvert = p.clamp_side ? vd[p.clamp_axis] - 1 : 0;
-  std::vector<int> vnum(nvert, -1);
+  // free vertices numbered lattice by lattice, lexicographic (x fastest) inside each lattice
+  std::vector<int> corner_v((size_t)c.N * c.ncorner);
+  std::vector<int> vert_cells;
   int nV = 0;
-  for (long long v = 0; v < nvert; ++v) {
-    const int ijk[3] = {(int)(v % vd[0]), (int)((v / vd[0]) % vd[1]), (int)(v / ((long long)vd[0] * vd[1]))};
-    if (ijk[p.clamp_axis] != cvert) vnum[v] = nV++;
+  for (int bl = 0; bl < nprob; ++bl) {
+    const fetidp_problem& pl = probs[bl];
+    const long long cell0 = c.lat[bl].cell0;
+    const int nx = pl.cells[0], ny = pl.cells[1], nz = pl.cells[2];
+    const int vd[3] = {nx + 1, ny + 1, d == 3 ? nz + 1 : 1};
+    const long long nvert = (long long)vd[0] * vd[1] * vd[2];
+    const int cvert = pl.clamp_side ? vd[pl.clamp_axis] - 1 : 0;
+    std::vector<int> vnum(nvert, -1);
+    const int V0 = nV;
+    for (long long v = 0; v < nvert; ++v) {
+      const int ijk[3] = {(int)(v % vd[0]), (int)((v / vd[0]) % vd[1]), (int)(v / ((long long)vd[0] * vd[1]))};
+      if (ijk[pl.clamp_axis] != cvert) vnum[v] = nV++;
+    }
+    c.lat[bl].V0 = V0;
+    c.lat[bl].nV = nV - V0;
+    vert_cells.resize((size_t)nV * c.ncorner, -1);
+    std::vector<int> vfill(nV - V0, 0);
+    for (long long sl = 0; sl < c.lat[bl].ncell; ++sl) {
+      const long long s = cell0 + sl;
+      const int cijk[3] = {(int)(sl % nx), (int)((sl / nx) % ny), (int)(sl / ((long long)nx * ny))};
+      for (int k = 0; k < c.ncorner; ++k) {
+        const int o[3] = {k & 1, (k >> 1) & 1, (k >> 2) & 1};
+        long long v = 0, stride = 1;
+        for (int q = 0; q < 3; ++q) {
+          v += (cijk[q] + (q < d ? o[q] : 0)) * stride;
+          stride *= vd[q];
+        }
+        const int vn = vnum[v];
+        corner_v[(size_t)s * c.ncorner + k] = vn;
+        if (vn >= 0) vert_cells[(size_t)vn * c.ncorner + vfill[vn - V0]++] = (int)(s * c.ncorner + k);
+      }
+    }
   }
   c.nV = nV;
   c.nP = (long long)nV * d;
-  std::vector<int> corner_v((size_t)c.N * c.ncorner), vert_cells((size_t)nV * c.ncorner, -1);
-  std::vector<int> vfill(nV, 0);
-  for (long long s = 0; s < c.N; ++s) {
-    const int cijk[3] = {(int)(s % nx), (int)((s / nx) % ny), (int)(s / ((long long)nx * ny))};
-    for (int k = 0; k < c.ncorner; ++k) {
-      const int o[3] = {k & 1, (k >> 1) & 1, (k >> 2) & 1};
-      long long v = 0, stride = 1;
-      for (int q = 0; q < 3; ++q) {
-        v += (cijk[q] + (q < d ? o[q] : 0)) * stride;
-        stride *= vd[q];
-      }
-      const int vn = vnum[v];
-      corner_v[(size_t)s * c.ncorner + k] = vn;
-      if (vn >= 0) vert_cells[(size_t)vn * c.ncorner + vfill[vn]++] = (int)(s * c.ncorner + k);
-    }
-  }
   FD_TRY(upload(c, &c.corner_v, corner_v));
   FD_TRY(upload(c, &c.vert_cells, vert_cells));
   c.ntot = c.N * c.nr + c.nP + c.L;
@@ -350,8 +394,14 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
     for (int l = 0; l < c.m; ++l) {
       double* rl = rhs.data() + (size_t)l * c.ntot;
       for (long long s = 0; s < c.N; ++s) {
-        const int cx = (int)(s % nx), cy = (int)((s / nx) % ny), cz = (int)(s / ((long long)nx * ny));
-        cell_load(c, p, l, cx, cy, cz, f);
+        int bl = 0;
+        while (bl + 1 < nprob && s >= c.lat[bl + 1].cell0) ++bl;
+        const fetidp_problem& pl = probs[bl];
+        const long long sl = s - c.lat[bl].cell0;
+        const int nx = pl.cells[0], ny = pl.cells[1];
+        const int cx = (int)(sl % nx), cy = (int)((sl / nx) % ny), cz = (int)(sl / ((long long)nx * ny));
+        c.geo = c.lat[bl].geo;
+        cell_load(c, pl, l, cx, cy, cz, f);
         for (int li = 0; li < c.nr; ++li) rl[s * c.nr + li] = f[ref.perm[li]];
         for (int q = 0; q < c.np; ++q) fpc[((size_t)l * c.N + s) * c.np + q] = f[ref.perm[c.nr + q]];
         for (int k = 0; k < c.ncorner; ++k) {
@@ -362,8 +412,27 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem& p, const fetidp_option
         }
       }
     }
+    c.geo = c.lat[0].geo;
     FD_TRY(upload(c, &c.rhs, rhs));
     FD_TRY(upload(c, &c.rhs_p_cells, fpc));
+    // per RHS: min over lattices of ||f_b|| / ||f|| (f_b: the lattice's remaining and primal loads)
+    c.tol_scale.assign(c.m, 1.0);
+    if (nprob > 1)
+      for (int l = 0; l < c.m; ++l) {
+        const double* rl = rhs.data() + (size_t)l * c.ntot;
+        double all = 0.0, mn = -1.0;
+        std::vector<double> nb(nprob, 0.0);
+        for (int bl = 0; bl < nprob; ++bl) {
+          for (long long t = c.lat[bl].cell0 * c.nr; t < (c.lat[bl].cell0 + c.lat[bl].ncell) * c.nr; ++t)
+            nb[bl] += rl[t] * rl[t];
+          for (long long t = c.N * c.nr + c.lat[bl].V0 * d; t < c.N * c.nr + (c.lat[bl].V0 + c.lat[bl].nV) * d; ++t)
+            nb[bl] += rl[t] * rl[t];
+          all += nb[bl];
+        }
+        for (int bl = 0; bl < nprob; ++bl)
+          if (nb[bl] > 0.0 && (mn < 0.0 || nb[bl] < mn)) mn = nb[bl];
+        c.tol_scale[l] = (all > 0.0 && mn > 0.0) ? std::sqrt(mn / all) : 1.0;
+      }
   }
   phase("primal maps + loads");
 

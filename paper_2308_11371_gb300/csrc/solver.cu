@@ -418,10 +418,12 @@ fetidp_status fgmres(Ctx& c, double* xout, OuterResult& res) {
     std::vector<double> target(m, 0.0);
     int nact = 0;
     for (int r = 0; r < m; ++r) {
-      const bool done = bnorm[r] == 0.0 || rnorm[r] == 0.0 ||
-                        (!fixed && rnorm[r] <= c.opt.tol_outer * bnorm[r]);
+      // batch: every lattice b must reach tol against its own load; ||r|| <= tol min_b ||f_b||
+      // guarantees ||r_b|| <= tol ||f_b|| for all b (tol_scale = min_b ||f_b|| / ||f||, 1 alone)
+      const double tol_r = c.opt.tol_outer * c.tol_scale[r];
+      const bool done = bnorm[r] == 0.0 || rnorm[r] == 0.0 || (!fixed && rnorm[r] <= tol_r * bnorm[r]);
       active[r] = !done;
-      target[r] = c.opt.tol_outer * bnorm[r] / std::max(rnorm[r], 1e-300);
+      target[r] = tol_r * bnorm[r] / std::max(rnorm[r], 1e-300);
       inv[r] = active[r] ? 1.0 / rnorm[r] : 0.0;
       nact += active[r];
       std::fill(H[r].begin(), H[r].end(), 0.0);
@@ -517,7 +519,9 @@ fetidp_status fgmres(Ctx& c, double* xout, OuterResult& res) {
   res.rel_res = 0.0;
   bool conv = true;
   for (int r = 0; r < m; ++r) {
-    const double rr = bnorm[r] > 0.0 ? rnorm[r] / bnorm[r] : 0.0;
+    // ||r|| / min_b ||f_b||: the combined relative residual alone, an upper bound of the worst
+    // lattice's relative residual in a batch
+    const double rr = bnorm[r] > 0.0 ? rnorm[r] / (bnorm[r] * c.tol_scale[r]) : 0.0;
     res.rel_res = std::max(res.rel_res, rr);
     if (!fixed && rr > c.opt.tol_outer) conv = false;
   }
@@ -700,8 +704,8 @@ fetidp_status fetidp_setup(const fetidp_problem* probs, int n_problems, const fe
                            void* cuda_stream, fetidp_ctx** out) {
   if (!out) { set_error("null output pointer"); return FETIDP_EINVAL; }
   *out = nullptr;
-  if (!probs || n_problems != 1) {
-    set_error("exactly one problem per context is supported");
+  if (!probs || n_problems < 1) {
+    set_error("at least one problem per context");
     return FETIDP_EINVAL;
   }
   fetidp_options o;
@@ -714,12 +718,25 @@ fetidp_status fetidp_setup(const fetidp_problem* probs, int n_problems, const fe
   fetidp_ctx* ctx = new fetidp_ctx();
   cudaGetDevice(&ctx->c.device);
   ctx->c.stream = reinterpret_cast<cudaStream_t>(cuda_stream);
-  fetidp_status s = setup_context(ctx->c, probs[0], o);
+  fetidp_status s = setup_context(ctx->c, probs, n_problems, o);
   if (s != FETIDP_OK) {
     fetidp_destroy(ctx);
     return s;
   }
   *out = ctx;
+  return FETIDP_OK;
+}
+
+fetidp_status fetidp_batch_layout(const fetidp_ctx* ctx, long long* cell0, long long* L0, long long* P0) {
+  if (!ctx) { set_error("null argument"); return FETIDP_EINVAL; }
+  const Ctx& c = ctx->c;
+  const size_t B = c.lat.size();
+  for (size_t b = 0; b <= B; ++b) {
+    const bool end = b == B;
+    if (cell0) cell0[b] = end ? c.N : c.lat[b].cell0;
+    if (L0) L0[b] = end ? c.L : c.lat[b].L0;
+    if (P0) P0[b] = end ? c.nP : c.lat[b].V0 * c.d;
+  }
   return FETIDP_OK;
 }
 
