@@ -196,6 +196,11 @@ struct Ctx {
   int nV = 0;       // free lattice vertices (all lattices)
   int clamp_axis = 0, clamp_side = 0;
   std::vector<LatticeSpan> lat;   // the lattices of the context (one unless batched)
+  cudaGraphExec_t pcg_graph = nullptr;   // two inner PCG iterations, captured on first use
+  long long pcg_graph_kernels = 0;       // kernels in that graph
+  bool pcg_graph_failed = false;         // capture not possible: iterations run one by one
+  cudaStream_t ws = nullptr;             // the context's own stream for graph capture and replay
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   // per RHS: min over lattices of ||f_b|| / ||f||; the outer solve targets tol * this so that
   // every lattice meets tol relative to its own load
   std::vector<double> tol_scale;

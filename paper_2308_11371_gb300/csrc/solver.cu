@@ -25,7 +25,8 @@ namespace fetidp {
 namespace {
 thread_local std::string g_last_error;
 
-constexpr int S_RZ0 = 0, S_RZ1 = 1, S_PQ = 2, S_RR = 3, S_ACT = 4, S_R0 = 5, S_NSLOT = 8;
+constexpr int S_RZ0 = 0, S_RZ1 = 1, S_PQ = 2, S_RR = 3, S_ACT = 4, S_R0 = 5, S_ERR = 6, S_ITS = 7,
+              S_NSLOT = 8;
 
 __global__ void copy_cells_kernel(const double* __restrict__ x, long long x_rs, int x_cs,
                                   double* __restrict__ y, long long y_rs, int y_cs, int len,
@@ -77,6 +78,22 @@ __global__ void pcg_xr_kernel(double* __restrict__ X, double* __restrict__ R,
     X[t] += alpha * P[t];
     R[t] -= alpha * Q[t];
   }
+}
+
+// Convergence test of one PCG iteration on the device (one thread per RHS): counts the iteration,
+// flags a breakdown (p^T F p <= 0 or a non-finite residual) and clears the RHS's active flag when
+// ||r|| / ||r_0|| <= tol or r = 0.  Lets whole iterations run without a host round trip.
+__global__ void pcg_check_kernel(double* __restrict__ scal, int nrhs, double tol) {
+  const int r = threadIdx.x;
+  if (r >= nrhs || scal[S_ACT * nrhs + r] == 0.0) return;
+  const double pq = scal[S_PQ * nrhs + r], rr = scal[S_RR * nrhs + r];
+  scal[S_ITS * nrhs + r] += 1.0;
+  if (!(pq > 0.0) || !isfinite(rr)) {
+    scal[S_ERR * nrhs + r] = 1.0;
+    scal[S_ACT * nrhs + r] = 0.0;
+    return;
+  }
+  if (sqrt(rr / scal[S_R0 * nrhs + r]) <= tol || rr == 0.0) scal[S_ACT * nrhs + r] = 0.0;
 }
 
 // p = z + beta p, beta = rz_new / rz_old per active RHS
@@ -287,6 +304,100 @@ fetidp_status pcg_solve(Ctx& c, const double* b, long long b_rs, double* x, long
   }
   const int max_it = c.opt.fixed_inner > 0 ? c.opt.fixed_inner : c.opt.max_inner;
   int cur = S_RZ0, it = 0;
+  // Graph path (no fixed iteration count, no profiling): two iterations (one per rho slot) are
+  // captured once per context and replayed; the convergence test runs on the device and the host
+  // reads the flags once per replay.  A replay may run one iteration past convergence: the
+  // converged right-hand sides are frozen (their x, r, p do not change), only time is spent.
+  const bool graph_ok = nact > 0 && c.opt.fixed_inner <= 0 && c.prof.mask == 0 && !c.pcg_graph_failed;
+  // The graph runs on the context's own non-blocking stream (capture is not possible on the
+  // legacy default stream), ordered after and before the caller's stream by events.
+  struct StreamSwap {
+    Ctx& c;
+    cudaStream_t user;
+    bool on = false;
+    ~StreamSwap() {
+      if (!on) return;
+      cudaEventRecord(c.ev_out, c.ws);
+      cudaStreamWaitEvent(user, c.ev_out, 0);
+      c.stream = user;
+    }
+  } swap{c, c.stream};
+  if (graph_ok) {
+    if (!c.ws) {
+      FD_CUDA(cudaStreamCreateWithFlags(&c.ws, cudaStreamNonBlocking));
+      FD_CUDA(cudaEventCreateWithFlags(&c.ev_in, cudaEventDisableTiming));
+      FD_CUDA(cudaEventCreateWithFlags(&c.ev_out, cudaEventDisableTiming));
+    }
+    FD_CUDA(cudaEventRecord(c.ev_in, c.stream));
+    FD_CUDA(cudaStreamWaitEvent(c.ws, c.ev_in, 0));
+    c.stream = c.ws;
+    swap.on = true;
+  }
+  if (graph_ok) {
+    const double tol = c.mixed ? c.opt.tol_inner_mixed : c.opt.tol_inner;
+    if (!c.pcg_graph) {
+      const long long l0 = g_launches.load();
+      FD_CUDA(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
+      fetidp_status cap = FETIDP_OK;
+      for (int half = 0; half < 2 && cap == FETIDP_OK; ++half) {
+        const int rz = half == 0 ? S_RZ0 : S_RZ1, rzn = half == 0 ? S_RZ1 : S_RZ0;
+        cap = op_apply_F(c, P, L, Q, L);
+        if (cap == FETIDP_OK) cap = k_dot(c, P, L, Q, L, L, m, sc + S_PQ * m);
+        if (cap == FETIDP_OK) {
+          pcg_xr_kernel<<<gridn(mL), 256, 0, c.stream>>>(X, R, P, Q, sc, rz, L, m);
+          count_launch();
+          cap = k_dot(c, R, L, R, L, L, m, sc + S_RR * m);
+        }
+        if (cap == FETIDP_OK) {
+          pcg_check_kernel<<<1, 32, 0, c.stream>>>(sc, m, tol);
+          count_launch();
+          cap = op_apply_MD(c, R, L, Zv, L);
+        }
+        if (cap == FETIDP_OK) cap = k_dot(c, R, L, Zv, L, L, m, sc + rzn * m);
+        if (cap == FETIDP_OK) {
+          pcg_p_kernel<<<gridn(mL), 256, 0, c.stream>>>(P, Zv, sc, rzn, rz, L, m);
+          count_launch();
+        }
+      }
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(c.stream, &graph);
+      // captured kernels have not run: they are counted when the graph is replayed
+      c.pcg_graph_kernels = g_launches.load() - l0;
+      g_launches.fetch_sub(c.pcg_graph_kernels);
+      cudaError_t ie = cudaErrorUnknown;
+      if (cap == FETIDP_OK && ce == cudaSuccess) ie = cudaGraphInstantiate(&c.pcg_graph, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (ie != cudaSuccess) {   // capture not possible here: run the iterations one by one
+        cudaGetLastError();
+        c.pcg_graph = nullptr;
+        c.pcg_graph_failed = true;
+      }
+    }
+  }
+  if (graph_ok && c.pcg_graph) {
+    // counters and error flags start at zero, active flags are set above
+    FD_CUDA(cudaMemsetAsync(sc + S_ERR * m, 0, sizeof(double) * 2 * m, c.stream));
+    while (true) {
+      FD_CUDA(cudaGraphLaunch(c.pcg_graph, c.stream));
+      g_launches.fetch_add(c.pcg_graph_kernels);
+      FD_CUDA(cudaMemcpyAsync(hs, sc, sizeof(double) * S_NSLOT * m, cudaMemcpyDeviceToHost, c.stream));
+      FD_CUDA(cudaStreamSynchronize(c.stream));
+      nact = 0;
+      it = 0;
+      for (int r = 0; r < m; ++r) {
+        if (hs[S_ERR * m + r] != 0.0) {
+          set_error("PCG breakdown: p^T F p <= 0 or non-finite residual");
+          return FETIDP_EBREAKDOWN;
+        }
+        nact += hs[S_ACT * m + r] != 0.0;
+        it = std::max(it, (int)hs[S_ITS * m + r]);
+      }
+      if (nact == 0 || it >= max_it) break;
+    }
+    c.inner_total += it;
+    FD_TRY(k_copy_scale(c, X, x, L, m, L, x_rs, nullptr, 1.0));
+    return FETIDP_OK;
+  }
   while (nact > 0 && it < max_it) {
     FD_TRY(op_apply_F(c, P, L, Q, L));
     FD_TRY(k_dot(c, P, L, Q, L, L, m, sc + S_PQ * m));
@@ -694,6 +805,13 @@ void fetidp_destroy(fetidp_ctx* ctx) {
   cudaSetDevice(ctx->c.device);
   cudaStreamSynchronize(ctx->c.stream);
   for (auto& e : ctx->c.prof.ev) cudaEventDestroy(e);
+  if (ctx->c.pcg_graph) cudaGraphExecDestroy(ctx->c.pcg_graph);
+  if (ctx->c.ws) {
+    cudaStreamSynchronize(ctx->c.ws);
+    cudaStreamDestroy(ctx->c.ws);
+    cudaEventDestroy(ctx->c.ev_in);
+    cudaEventDestroy(ctx->c.ev_out);
+  }
   for (void* p : ctx->c.allocations) cudaFreeAsync(p, ctx->c.stream);
   cudaStreamSynchronize(ctx->c.stream);
   if (ctx->c.h_scal) cudaFreeHost(ctx->c.h_scal);
