@@ -123,6 +123,9 @@ typedef struct {
                                dropped (1e-9; the FP64 path drops below 1e-12).  The Gram data
                                carry ~1e-5 relative noise (BF16 split products, FP32 K_s), so
                                Schur diagonals below ~1e-10 are noise                        */
+  unsigned profile_mask;    /* kernel classes (bit k = fetidp_kernel_class k) timed from the
+                               start of fetidp_setup, as fetidp_profile_enable does from the
+                               call on; read with fetidp_profile_read (0)                     */
 } fetidp_options;
 
 typedef struct {
@@ -246,7 +249,10 @@ enum {
   FETIDP_K_VECTOR = 5,        /* Krylov reductions and vector updates */
   FETIDP_K_GRAM = 6,          /* Eq. 46b Gram solves */
   FETIDP_K_TC_GEMM = 7,       /* principal contraction on tcgen05 tensor cores (BF16) */
-  FETIDP_K_SETUP = 8,         /* setup kernels */
+  FETIDP_K_SETUP = 8,         /* setup kernels not in the classes below */
+  FETIDP_K_SWEEP = 9,         /* setup: blocked sweep SPD inverses (K_rr, S_dd, coarse blocks) */
+  FETIDP_K_TRACES = 10,       /* setup: Eq. 42 snapshot traces (FP64 or double-float GEMM) */
+  FETIDP_K_GREEDY = 11,       /* setup: Algorithm 4 greedy steps */
   FETIDP_K_NCLASS = 16
 };
 

@@ -33,7 +33,7 @@ SYMBOLS = ["fetidp_sizes", "fetidp_default_options", "fetidp_setup", "fetidp_app
            "fetidp_compliance", "fetidp_batch_layout"]
 
 KCLASS = {"grouped_gemm": 0, "apply_K": 1, "maps": 2, "coarse": 3, "cell_gemv": 4, "vector": 5,
-          "gram": 6, "tc_gemm": 7, "setup": 8}
+          "gram": 6, "tc_gemm": 7, "setup": 8, "sweep": 9, "traces": 10, "greedy": 11}
 
 
 class FetidpError(RuntimeError):
@@ -62,7 +62,8 @@ class Options(ctypes.Structure):
                 ("max_outer", ctypes.c_int), ("max_inner", ctypes.c_int),
                 ("precision", ctypes.c_int), ("fixed_outer", ctypes.c_int),
                 ("fixed_inner", ctypes.c_int), ("tc_split", ctypes.c_int),
-                ("tol_inner_mixed", ctypes.c_double), ("gram_drop_mixed", ctypes.c_double)]
+                ("tol_inner_mixed", ctypes.c_double), ("gram_drop_mixed", ctypes.c_double),
+                ("profile_mask", ctypes.c_uint)]
 
 
 class Info(ctypes.Structure):
@@ -146,7 +147,18 @@ def _check(status: int):
         raise FetidpError(status, msg)
 
 
+def class_mask(names) -> int:
+    """Bit mask of the kernel classes named (KCLASS keys; None = all)."""
+    mask = 0
+    for n in (list(KCLASS) if names is None else names):
+        mask |= 1 << KCLASS[n]
+    return mask
+
+
 def default_options(**kw) -> Options:
+    """Library defaults with the given fields replaced; ``profile=[classes]`` sets profile_mask."""
+    if "profile" in kw:
+        kw["profile_mask"] = class_mask(kw.pop("profile"))
     o = Options()
     load().fetidp_default_options(ctypes.byref(o))
     for k, v in kw.items():
@@ -316,11 +328,7 @@ class Solver:
 
     def profile_enable(self, classes=None):
         """Time the given kernel classes (names of KCLASS; None = all)."""
-        names = list(KCLASS) if classes is None else classes
-        mask = 0
-        for n in names:
-            mask |= 1 << KCLASS[n]
-        _check(load().fetidp_profile_enable(self._h, mask))
+        _check(load().fetidp_profile_enable(self._h, class_mask(classes)))
 
     def profile_disable(self):
         _check(load().fetidp_profile_enable(self._h, 0))

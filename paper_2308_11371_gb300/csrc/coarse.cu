@@ -262,12 +262,11 @@ fetidp_status coarse_setup(Ctx& c, const double* Spp_dev) {
   FD_TRY(dalloc_t(c, &B.mats, (size_t)pool));
   B.mat_bytes = (size_t)pool * sizeof(double);
   double* P = B.mats;
-  double *Cbuf[2] = {nullptr, nullptr}, *work = nullptr;
+  double* Cbuf[2] = {nullptr, nullptr};
   int *vslab_d = nullptr, *vpos_d = nullptr, *st_d = nullptr;
   const long long cmax = nb > 1 ? (long long)(nb - 1) * bb : bb;
   FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Cbuf[0]), sizeof(double) * cmax));
   FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Cbuf[1]), sizeof(double) * cmax));
-  FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&work), sizeof(double) * 2 * (size_t)(nb / 2 + 1) * (b + 1)));
   size_t nvert_all = 0;
   for (const SlabMap& mp : maps) nvert_all += mp.vslab.size();
   FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&vslab_d), sizeof(int) * nvert_all));
@@ -309,7 +308,7 @@ fetidp_status coarse_setup(Ctx& c, const double* Spp_dev) {
     double* Cn = Cbuf[(l + 1) & 1];
     const int nodd = n / 2, nu = (n - 1) / 2;
     // Ainv_j (odd j) in place; V_j = Ainv_j C_{j-1}^T; U_j = Ainv_j C_j (j + 1 < n)
-    st = k_spd_inverse_batched(c, Al + bb, 2 * bb, b, b, nodd, work, st_d);
+    st = k_spd_inverse_batched(c, Al + bb, 2 * bb, b, b, nodd, st_d);
     if (st == FETIDP_OK)
       st = k_batched_gemm(c, false, true, b, b, b, 1.0, Al + bb, 2 * bb, b, Cl, 2 * bb, b, 0.0, Vl + bb, 2 * bb, b, nodd);
     if (st == FETIDP_OK)
@@ -341,13 +340,13 @@ fetidp_status coarse_setup(Ctx& c, const double* Spp_dev) {
     }
     B.off_Ainv[l] = oA; B.off_U[l] = oU; B.off_UT[l] = oUT; B.off_V[l] = oV; B.off_VT[l] = oVT;
   }
-  if (st == FETIDP_OK) st = k_spd_inverse_batched(c, P + base[levels], bb, b, b, 1, work, st_d);
+  if (st == FETIDP_OK) st = k_spd_inverse_batched(c, P + base[levels], bb, b, b, 1, st_d);
   int hst = 0;
   if (st == FETIDP_OK) {
     FD_CUDA(cudaMemcpyAsync(&hst, st_d, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     FD_CUDA(cudaStreamSynchronize(c.stream));
   }
-  tmp_free(c, Cbuf[0]); tmp_free(c, Cbuf[1]); tmp_free(c, work); tmp_free(c, vslab_d); tmp_free(c, vpos_d); tmp_free(c, real_d); tmp_free(c, st_d);
+  tmp_free(c, Cbuf[0]); tmp_free(c, Cbuf[1]); tmp_free(c, vslab_d); tmp_free(c, vpos_d); tmp_free(c, real_d); tmp_free(c, st_d);
   FD_TRY(st);
   if (hst != 0) {
     set_error("coarse S_PP is not positive definite");

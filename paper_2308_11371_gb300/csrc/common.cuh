@@ -167,6 +167,13 @@ struct Prof {
   double flops[FETIDP_K_NCLASS] = {};
   double bytes[FETIDP_K_NCLASS] = {};
   long long launches[FETIDP_K_NCLASS] = {};
+  double ms[FETIDP_K_NCLASS] = {};   // time of launches inside replayed graphs (read per replay)
+  // Launches captured into a graph: their event pair is recorded by the graph's own event nodes
+  // on every replay; the host adds their time after each replay.
+  struct Captured { int cls; double flops, bytes; cudaEvent_t e0, e1; };
+  bool capturing = false;
+  std::vector<Captured> captured;
+  std::vector<cudaEvent_t> gev;   // events for captured launches, created before a capture
 };
 
 // One lattice of a batch: its geometry and where its cells, multipliers and free vertices sit in
@@ -199,6 +206,7 @@ struct Ctx {
   cudaGraphExec_t pcg_graph = nullptr;   // two inner PCG iterations, captured on first use
   long long pcg_graph_kernels = 0;       // kernels in that graph
   bool pcg_graph_failed = false;         // capture not possible: iterations run one by one
+  unsigned pcg_graph_mask = 0;           // profiled kernel classes when the graph was captured
   cudaStream_t ws = nullptr;             // the context's own stream for graph capture and replay
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   // per RHS: min over lattices of ||f_b|| / ||f||; the outer solve targets tol * this so that
@@ -276,14 +284,26 @@ struct Ctx {
 };
 
 // RAII timing of one launch (or one multi-kernel step) of a kernel class.
+bool prof_grow(Ctx& c);
+cudaEvent_t event_take(int dev);
+void event_give(int dev, cudaEvent_t e);
+
 struct ProfScope {
   Ctx& c;
-  int slot = -1;
+  int slot = -1, gslot = -1;
   ProfScope(Ctx& ctx, int cls, double flops, double bytes) : c(ctx) {
     Prof& P = c.prof;
     if (!(P.mask >> cls & 1u)) return;
+    if (P.capturing) {   // becomes a pair of event nodes of the graph being captured
+      const size_t k = 2 * P.captured.size();
+      if (k + 2 > P.gev.size()) return;
+      gslot = (int)P.captured.size();
+      P.captured.push_back({cls, flops, bytes, P.gev[k], P.gev[k + 1]});
+      cudaEventRecordWithFlags(P.gev[k], c.stream, cudaEventRecordExternal);
+      return;
+    }
     P.launches[cls] += 1;
-    if (P.used >= P.capacity) return;   // totals below cover the timed launches only
+    if (P.used >= P.capacity && !prof_grow(c)) return;   // totals below cover the timed launches only
     P.flops[cls] += flops;
     P.bytes[cls] += bytes;
     slot = P.used++;
@@ -292,6 +312,7 @@ struct ProfScope {
   }
   ~ProfScope() {
     if (slot >= 0) cudaEventRecord(c.prof.ev[2 * slot + 1], c.stream);
+    if (gslot >= 0) cudaEventRecordWithFlags(c.prof.captured[gslot].e1, c.stream, cudaEventRecordExternal);
   }
 };
 
@@ -340,8 +361,7 @@ fetidp_status k_greedy_alpha(Ctx& c, const double* Z, const double* nrm, const d
                              const GreedyState* st, double* T, double* alpha);
 // dense batched setup kernels (principal blocks, SPD inverses by sweeps)
 fetidp_status k_assemble_principal(Ctx& c, const int* sigma_dev, int nrb, double* Krr, double* Krp, double* Kpp);
-fetidp_status k_spd_inverse_batched(Ctx& c, double* A, long long stride, int n, int lda, int batch, double* work,
-                                    int* status);
+fetidp_status k_spd_inverse_batched(Ctx& c, double* A, long long stride, int n, int lda, int batch, int* status);
 fetidp_status k_batched_gemm_nn(Ctx& c, const double* A, long long sa, int lda, const double* B, long long sb,
                                 int ldb, double* C, long long sc, int ldc, int M, int N, int K, int batch);
 fetidp_status k_batched_block_copy(Ctx& c, const double* in, long long si, int ldi, int r0, int c0, double* out,
@@ -372,7 +392,7 @@ fetidp_status k_grouped_gemm(Ctx& c, const double* A, long long a_stride_k, int 
 fetidp_status k_grouped_gemm_n(Ctx& c, const double* A, long long a_stride_k, int lda, int M,
                                int K, int nk, CCellVec X, CellVec Y, const double* coef,
                                double alpha, double beta, long long ncell, int nrhs, bool separate,
-                               long long y_k_stride);
+                               long long y_k_stride, int prof_class = FETIDP_K_GROUPED_GEMM);
 fetidp_status k_gram_solve(Ctx& c, const double* R, const double* KR, CCellVec v, CellVec x,
                            int nrhs);
 fetidp_status k_grad(Ctx& c, const double* u, const double* w, double* g);

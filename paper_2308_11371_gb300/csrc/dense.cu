@@ -5,10 +5,9 @@
 //
 // Sweep operator on a symmetric matrix, pivot k (a = A_kk > 0 while A is positive definite):
 //   A_kk <- -1/a,   A_ik <- A_ik / a (i != k),   A_ij <- A_ij - A_ik A_kj / a (i, j != k).
-// Sweeping every index gives -A^{-1}.  Only the upper triangle is updated; one launch per pivot
-// updates all matrices of the batch.  The old pivot column (= row, by symmetry) and 1/a are read
-// from a buffer that the previous launch filled with the next pivot's column, so no thread reads
-// an entry another thread of the same launch writes.
+// Sweeping every index gives -A^{-1}.  Only the upper triangle is updated, a panel of 32 pivots
+// at a time (the block form below), for all matrices of the batch per launch.
+#include <climits>
 #include <cmath>
 
 #include "common.cuh"
@@ -113,56 +112,143 @@ __global__ void assemble_principal_kernel(const double* __restrict__ snap, const
   }
 }
 
-// Pivot column 0 and 1/A_00 of every matrix (start of the sweep).
-__global__ void sweep_init_kernel(const double* __restrict__ A, long long stride, int n, int lda, int batch,
-                                  double* __restrict__ col, int* __restrict__ status) {
-  const long long total = (long long)batch * n;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(t / n), i = (int)(t - (long long)b * n);
-    const double v = A[b * stride + i];   // row 0 = column 0
-    col[(long long)b * (n + 1) + i] = v;
-    if (i == 0) {
-      if (!(v > 0.0)) atomicExch(status, 1);
-      col[(long long)b * (n + 1) + n] = 1.0 / v;
+// Blocked sweep: sweeping the pivots of a panel P = [k0, k0 + nb) one by one equals the block
+// form (Goodnight's SWP on an index set)
+//   A_PP <- -A_PP^{-1},   A_iP <- A_iP A_PP^{-1},   A_ij <- A_ij - A_iP A_PP^{-1} A_Pj   (i, j not in P),
+// and sweeps of disjoint sets compose.  A_PP is the current (Schur complement) block, positive
+// definite while A is.  Each panel is one launch of sweep_panel_kernel (A_PP^{-1} in shared memory
+// and W = V A_PP^{-1} for the panel column V = A_:P) and one of sweep_update_kernel (the rank-nb
+// update of the upper triangle, 64 x 64 tiles): 2 launches per 32 pivots instead of 32.
+constexpr int kSwNb = 32;     // panel width
+constexpr int kSwRows = 64;   // rows per panel-kernel block and update tile edge
+
+// grid: (row blocks of 64) x batch; 256 threads.
+__global__ void __launch_bounds__(256) sweep_panel_kernel(const double* __restrict__ A, long long stride, int n,
+                                                          int lda, int k0, int nb, int nrb_rows,
+                                                          double* __restrict__ V, double* __restrict__ W,
+                                                          double* __restrict__ Sinv, int* __restrict__ status) {
+  __shared__ double S[kSwNb][kSwNb + 1];
+  __shared__ double Vs[kSwRows][kSwNb + 1];
+  const int rb = blockIdx.x % nrb_rows;
+  const long long b = blockIdx.x / nrb_rows;
+  const int tid = threadIdx.x;
+  const double* Ab = A + b * stride;
+  // the panel block, both triangles from the upper one
+  for (int t = tid; t < nb * nb; t += blockDim.x) {
+    const int r = t / nb, q = t - (t / nb) * nb;
+    S[r][q] = r <= q ? Ab[(long long)(k0 + r) * lda + k0 + q] : Ab[(long long)(k0 + q) * lda + k0 + r];
+  }
+  __syncthreads();
+  // sweep of the nb x nb block: S <- -A_PP^{-1}
+  bool bad = false;
+  for (int p = 0; p < nb; ++p) {
+    const double a = S[p][p];
+    bad |= !(a > 0.0);
+    const double inv = 1.0 / a;
+    double nv[(kSwNb * kSwNb + 255) / 256];
+    int cnt = 0;
+    for (int t = tid; t < nb * nb; t += blockDim.x, ++cnt) {
+      const int r = t / nb, q = t - (t / nb) * nb;
+      double v;
+      if (r == p && q == p) v = -inv;
+      else if (r == p) v = S[p][q] * inv;
+      else if (q == p) v = S[r][p] * inv;
+      else v = fma(-S[r][p] * inv, S[p][q], S[r][q]);
+      nv[cnt] = v;
+    }
+    __syncthreads();
+    cnt = 0;
+    for (int t = tid; t < nb * nb; t += blockDim.x, ++cnt) S[t / nb][t - (t / nb) * nb] = nv[cnt];
+    __syncthreads();
+  }
+  if (bad && rb == 0 && tid == 0) atomicExch(status, 1);
+  // V rows of this block: V_i = A_iP (zero for i in P, unused there)
+  const int i0 = rb * kSwRows;
+  if (i0 + kSwRows <= k0) {   // rows above the panel: A[i][k0 + p], contiguous in p
+    for (int t = tid; t < kSwRows * nb; t += blockDim.x) {
+      const int li = t / nb, p = t - (t / nb) * nb;
+      Vs[li][p] = Ab[(long long)(i0 + li) * lda + k0 + p];
+    }
+  } else {                    // rows at or below the panel: A[k0 + p][i], contiguous in i
+    for (int t = tid; t < kSwRows * nb; t += blockDim.x) {
+      const int li = t % kSwRows, p = t / kSwRows, i = i0 + li;
+      double v = 0.0;
+      if (i < n) {
+        if (i < k0) v = Ab[(long long)i * lda + k0 + p];
+        else if (i >= k0 + nb) v = Ab[(long long)(k0 + p) * lda + i];
+      }
+      Vs[li][p] = v;
     }
   }
+  __syncthreads();
+  // W_i = V_i A_PP^{-1} = -V_i S; written with V (layout [b][i][p], p fastest)
+  double* Vb = V + b * (long long)n * kSwNb;
+  double* Wb = W + b * (long long)n * kSwNb;
+  for (int t = tid; t < kSwRows * nb; t += blockDim.x) {
+    const int li = t / nb, p = t - (t / nb) * nb, i = i0 + li;
+    if (i >= n) continue;
+    double w = 0.0;
+    for (int q = 0; q < nb; ++q) w = fma(Vs[li][q], S[q][p], w);
+    Vb[(long long)i * kSwNb + p] = Vs[li][p];
+    Wb[(long long)i * kSwNb + p] = -w;
+  }
+  if (rb == 0)
+    for (int t = tid; t < nb * nb; t += blockDim.x)
+      Sinv[b * kSwNb * kSwNb + (t / nb) * kSwNb + t % nb] = -S[t / nb][t % nb];
 }
 
-// One sweep step on the upper triangles; each thread updates 4 consecutive entries of a row.
-__global__ void sweep_step_kernel(double* __restrict__ A, long long stride, int n, int lda, int batch, int k,
-                                  const double* __restrict__ cin, double* __restrict__ cout,
-                                  int* __restrict__ status) {
-  const int nq = (n + 3) / 4;
-  const long long total = (long long)batch * n * nq;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(t / ((long long)n * nq));
-    const int r = (int)(t - (long long)b * n * nq);
-    const int i = r / nq, j0 = 4 * (r - (r / nq) * nq);
-    if (j0 + 3 < i) continue;                       // wholly below the diagonal
-    const double* ci = cin + (long long)b * (n + 1);
-    const double inv = ci[n];
-    const double cii = ci[i] * inv;
-    double* Ar = A + b * stride + (long long)i * lda;
-    double* co = cout + (long long)b * (n + 1);
-    for (int j = j0; j < j0 + 4 && j < n; ++j) {
-      if (j < i) continue;
-      double v;
-      if (i == k) v = (j == k) ? -inv : ci[j] * inv;
-      else if (j == k) v = cii;
-      else v = fma(-cii, ci[j], Ar[j]);
-      Ar[j] = v;
-      if (k + 1 < n) {
-        if (j == k + 1) co[i] = v;                  // entries (i, k+1), i <= k+1
-        if (i == k + 1) {                           // entries (k+1, j), j >= k+1
-          co[j] = v;
-          if (j == k + 1) {
-            if (!(v > 0.0)) atomicExch(status, 1);
-            co[n] = 1.0 / v;
-          }
-        }
-      }
+// Rank-nb update of the upper triangle for panel P, one 64 x 64 tile (I <= J) per block, 256
+// threads of 4 x 4 entries.  grid: upper tiles x batch.
+__global__ void __launch_bounds__(256) sweep_update_kernel(double* __restrict__ A, long long stride, int n, int lda,
+                                                           int k0, int nb, int ntile,
+                                                           const double* __restrict__ V,
+                                                           const double* __restrict__ W,
+                                                           const double* __restrict__ Sinv) {
+  __shared__ double Ws[kSwNb][kSwRows];
+  __shared__ double Vs[kSwNb][kSwRows];
+  const int nup = ntile * (ntile + 1) / 2;
+  const long long b = blockIdx.x / nup;
+  int t = blockIdx.x - (int)(b * nup), I = 0;
+  while (t >= ntile - I) { t -= ntile - I; ++I; }
+  const int J = I + t;
+  const int tid = threadIdx.x;
+  const double* Wb = W + b * (long long)n * kSwNb;
+  const double* Vb = V + b * (long long)n * kSwNb;
+  for (int e = tid; e < kSwRows * kSwNb; e += blockDim.x) {
+    const int l = e / kSwNb, p = e - (e / kSwNb) * kSwNb;
+    const int i = I * kSwRows + l, j = J * kSwRows + l;
+    Ws[p][l] = (i < n && p < nb) ? Wb[(long long)i * kSwNb + p] : 0.0;
+    Vs[p][l] = (j < n && p < nb) ? Vb[(long long)j * kSwNb + p] : 0.0;
+  }
+  __syncthreads();
+  const int ty = tid / 16, tx = tid - (tid / 16) * 16;
+  double acc[4][4] = {};
+  for (int p = 0; p < nb; ++p) {
+    double w[4], v[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) { w[r] = Ws[p][ty * 4 + r]; v[r] = Vs[p][tx * 4 + r]; }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[r][q] = fma(w[r], v[q], acc[r][q]);
+  }
+  double* Ab = A + b * stride;
+  const double* Sb = Sinv + b * kSwNb * kSwNb;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = I * kSwRows + ty * 4 + r;
+    if (i >= n) continue;
+    const bool pi = i >= k0 && i < k0 + nb;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = J * kSwRows + tx * 4 + q;
+      if (j >= n || j < i) continue;
+      const bool pj = j >= k0 && j < k0 + nb;
+      double* a = Ab + (long long)i * lda + j;
+      if (!pi && !pj) *a -= acc[r][q];
+      else if (!pi) *a = Wb[(long long)i * kSwNb + (j - k0)];
+      else if (!pj) *a = Wb[(long long)j * kSwNb + (i - k0)];
+      else *a = -Sb[(i - k0) * kSwNb + (j - k0)];
     }
   }
 }
@@ -482,22 +568,35 @@ fetidp_status k_assemble_principal(Ctx& c, const int* sigma_dev, int nrb, double
   return FETIDP_OK;
 }
 
-fetidp_status k_spd_inverse_batched(Ctx& c, double* A, long long stride, int n, int lda, int batch, double* work,
-                                    int* status) {
-  ProfScope ps(c, FETIDP_K_SETUP, 2.0 * batch * (double)n * n * n / 2.0, 16.0 * batch * (double)n * n * n / 2.0);
-  double* cbuf[2] = {work, work + (size_t)batch * (n + 1)};
-  sweep_init_kernel<<<grid_for((long long)batch * n, 256), 256, 0, c.stream>>>(A, stride, n, lda, batch, cbuf[0],
-                                                                               status);
-  FD_CHECK_LAUNCH();
-  const long long steps_work = (long long)batch * n * ((n + 3) / 4);
-  const int g = grid_for(steps_work, 256);
-  for (int k = 0; k < n; ++k) {
-    sweep_step_kernel<<<g, 256, 0, c.stream>>>(A, stride, n, lda, batch, k, cbuf[k & 1], cbuf[(k + 1) & 1], status);
-    FD_CHECK_LAUNCH();
+fetidp_status k_spd_inverse_batched(Ctx& c, double* A, long long stride, int n, int lda, int batch, int* status) {
+  ProfScope ps(c, FETIDP_K_SWEEP, 2.0 * batch * (double)n * n * n / 2.0, 16.0 * batch * (double)n * n * n / 2.0);
+  if (n <= 0 || batch <= 0) return FETIDP_OK;
+  double* buf = nullptr;
+  const size_t vw = (size_t)batch * n * kSwNb;
+  FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&buf), sizeof(double) * (2 * vw + (size_t)batch * kSwNb * kSwNb)));
+  double *V = buf, *W = buf + vw, *Sinv = buf + 2 * vw;
+  const int nrows = (n + kSwRows - 1) / kSwRows;
+  const long long panel_blocks = (long long)nrows * batch;
+  const long long update_blocks = (long long)nrows * (nrows + 1) / 2 * batch;
+  fetidp_status st = FETIDP_OK;
+  if (panel_blocks > INT_MAX || update_blocks > INT_MAX) st = FETIDP_EINVAL;
+  for (int k0 = 0; k0 < n && st == FETIDP_OK; k0 += kSwNb) {
+    const int nb = n - k0 < kSwNb ? n - k0 : kSwNb;
+    sweep_panel_kernel<<<(int)panel_blocks, 256, 0, c.stream>>>(A, stride, n, lda, k0, nb, nrows, V, W, Sinv, status);
+    count_launch();
+    sweep_update_kernel<<<(int)update_blocks, 256, 0, c.stream>>>(A, stride, n, lda, k0, nb, nrows, V, W, Sinv);
+    count_launch();
+    if (cudaPeekAtLastError() != cudaSuccess) st = FETIDP_ECUDA;
   }
-  sweep_finish_kernel<<<grid_for((long long)batch * n * n, 256), 256, 0, c.stream>>>(A, stride, n, lda, batch);
-  FD_CHECK_LAUNCH();
-  return FETIDP_OK;
+  if (st == FETIDP_OK) {
+    sweep_finish_kernel<<<grid_for((long long)batch * n * n, 256), 256, 0, c.stream>>>(A, stride, n, lda, batch);
+    count_launch();
+    if (cudaPeekAtLastError() != cudaSuccess) st = FETIDP_ECUDA;
+  }
+  tmp_free(c, buf);
+  if (st == FETIDP_ECUDA) set_error(std::string("kernel launch: ") + cudaGetErrorString(cudaGetLastError()));
+  else if (st == FETIDP_EINVAL) set_error("SPD inverse batch too large for one launch");
+  return st;
 }
 
 fetidp_status k_batched_gemm_nn(Ctx& c, const double* A, long long sa, int lda, const double* B, long long sb,
@@ -526,7 +625,7 @@ fetidp_status k_batched_diag_sum(Ctx& c, const double* A, long long stride, int 
 
 fetidp_status k_df_gemm(Ctx& c, const double* A, int lda, int M, int K, const double* X, int x_cs, long long ncols,
                         double* Y, int y_cs) {
-  ProfScope ps(c, FETIDP_K_SETUP, 2.0 * M * (double)K * ncols, 8.0 * ((double)M * K + (double)ncols * (K + M)));
+  ProfScope ps(c, FETIDP_K_TRACES, 2.0 * M * (double)K * ncols, 8.0 * ((double)M * K + (double)ncols * (K + M)));
   const dim3 grid((unsigned)((ncols + DF_T - 1) / DF_T), (unsigned)((M + DF_T - 1) / DF_T));
   df_gemm_kernel<<<grid, 256, 0, c.stream>>>(A, lda, M, K, X, x_cs, ncols, Y, y_cs);
   FD_CHECK_LAUNCH();

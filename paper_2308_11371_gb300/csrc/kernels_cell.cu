@@ -1006,9 +1006,9 @@ fetidp_status k_grouped_gemm(Ctx& c, const double* A, long long a_stride_k, int 
 fetidp_status k_grouped_gemm_n(Ctx& c, const double* A, long long a_stride_k, int lda, int M,
                                int K, int nk, CCellVec X, CellVec Y, const double* coef,
                                double alpha, double beta, long long ncell, int nrhs, bool separate,
-                               long long y_k_stride) {
+                               long long y_k_stride, int prof_class) {
   const long long ncols = ncell * nrhs;
-  ProfScope ps(c, FETIDP_K_GROUPED_GEMM, 2.0 * M * K * nk * (double)ncols,
+  ProfScope ps(c, prof_class, 2.0 * M * K * nk * (double)ncols,
                8.0 * ((double)nk * M * K + (double)ncols * K + (double)ncols * M * (separate ? nk : 1)));
   dim3 grid((unsigned)ceil_div(ncols, GT), (unsigned)ceil_div(M, GT));
   grouped_gemm_kernel<<<grid, 256, 0, c.stream>>>(A, a_stride_k, lda, M, K, nk, X.p, X.rs, X.cs,

@@ -323,6 +323,7 @@ fetidp_status k_row_update(Ctx& c, double* D, const double* beta, const double* 
 
 fetidp_status k_greedy_step(Ctx& c, double* D, const double* zeta, long long rows, long long len, double* beta,
                             double* inf, double* sq, const GreedyState* st, int i) {
+  ProfScope ps(c, FETIDP_K_GREEDY, 4.0 * rows * (double)len, 16.0 * rows * (double)len);
   greedy_step_kernel<<<(unsigned)rows, kThreads, 0, c.stream>>>(D, zeta, len, beta, inf, sq, st, i);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
@@ -330,6 +331,7 @@ fetidp_status k_greedy_step(Ctx& c, double* D, const double* zeta, long long row
 
 fetidp_status k_greedy_select(Ctx& c, const double* inf, long long n, int i, double tol_rb, double tie,
                               GreedyState* st) {
+  ProfScope ps(c, FETIDP_K_GREEDY, 0.0, 8.0 * (double)n);
   greedy_select_kernel<<<1, 1024, 0, c.stream>>>(inf, n, i, tol_rb, tie, st);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
@@ -337,6 +339,7 @@ fetidp_status k_greedy_select(Ctx& c, const double* inf, long long n, int i, dou
 
 fetidp_status k_greedy_zeta(Ctx& c, const double* D, const double* sq, long long len, int i, const GreedyState* st,
                             double* zeta) {
+  ProfScope ps(c, FETIDP_K_GREEDY, 0.0, 16.0 * (double)len);
   greedy_zeta_kernel<<<gridn(len), kThreads, 0, c.stream>>>(D, sq, len, i, st, zeta);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;

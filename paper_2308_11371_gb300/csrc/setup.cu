@@ -499,18 +499,17 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
     FD_TRY(dalloc_t(c, &c.Sdd, (size_t)nrb * nd * nd));
     int* sigma_dev = nullptr;
     int* st_dev = nullptr;
-    double *work = nullptr, *dvec_d = nullptr;
+    double* dvec_d = nullptr;
     FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&sigma_dev), sizeof(int) * nrb));
     FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&st_dev), sizeof(int)));
     FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Krp_d), sizeof(double) * (size_t)nrb * nr * np));
     FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Kpp_d), sizeof(double) * (size_t)nrb * np * np));
-    FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&work), sizeof(double) * 2 * (size_t)nrb * (nr + 1)));
     FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&dvec_d), sizeof(double) * nrb));
     FD_CUDA(cudaMemcpyAsync(sigma_dev, c.sigma.data(), sizeof(int) * nrb, cudaMemcpyHostToDevice, c.stream));
     FD_CUDA(cudaMemsetAsync(st_dev, 0, sizeof(int), c.stream));
     FD_TRY(k_assemble_principal(c, sigma_dev, nrb, c.Kinv, Krp_d, Kpp_d));
     phase("  principal assembly");
-    FD_TRY(k_spd_inverse_batched(c, c.Kinv, (long long)nr * nr, nr, nr, nrb, work, st_dev));
+    FD_TRY(k_spd_inverse_batched(c, c.Kinv, (long long)nr * nr, nr, nr, nrb, st_dev));
     phase("  principal K_rr inverse");
     FD_TRY(k_batched_gemm_nn(c, c.Kinv, (long long)nr * nr, nr, Krp_d, (long long)nr * np, np, c.Urp,
                              (long long)nr * np, np, nr, np, nr, nrb));
@@ -519,12 +518,12 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
     FD_TRY(k_batched_diag_sum(c, c.Kinv, (long long)nr * nr, nr, ni, nd, nrb, dvec_d));
     FD_TRY(k_batched_block_copy(c, c.Kinv, (long long)nr * nr, nr, ni, ni, c.Sdd, (long long)nd * nd, nd, nd, nd,
                                 nrb, false));
-    FD_TRY(k_spd_inverse_batched(c, c.Sdd, (long long)nd * nd, nd, nd, nrb, work, st_dev));
+    FD_TRY(k_spd_inverse_batched(c, c.Sdd, (long long)nd * nd, nd, nd, nrb, st_dev));
     int hst = 0;
     FD_CUDA(cudaMemcpyAsync(dvec.data(), dvec_d, sizeof(double) * nrb, cudaMemcpyDeviceToHost, c.stream));
     FD_CUDA(cudaMemcpyAsync(&hst, st_dev, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     FD_CUDA(cudaStreamSynchronize(c.stream));
-    tmp_free(c, sigma_dev); tmp_free(c, st_dev); tmp_free(c, work); tmp_free(c, dvec_d);
+    tmp_free(c, sigma_dev); tmp_free(c, st_dev); tmp_free(c, dvec_d);
     if (hst != 0) {
       tmp_free(c, Krp_d); tmp_free(c, Kpp_d);
       set_error("principal K_rr is not positive definite");
@@ -572,7 +571,7 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
       FD_TRY(k_df_gemm(c, Tab, (int)c.nsnap, ntab, (int)c.nsnap, c.snap, (int)c.nsnap, c.N, Y, ntab));
     else
       FD_TRY(k_grouped_gemm_n(c, Tab, 0, (int)c.nsnap, ntab, (int)c.nsnap, 1, CCellVec{c.snap, 0, (int)c.nsnap},
-                              CellVec{Y, 0, ntab}, nullptr, 1.0, 0.0, c.N, 1, false, 0));
+                              CellVec{Y, 0, ntab}, nullptr, 1.0, 0.0, c.N, 1, false, 0, FETIDP_K_TRACES));
     phase("  trace contraction");
     // the two Gram systems of every cell, solved on the device (one warp per system)
     double* dvec_d = nullptr;

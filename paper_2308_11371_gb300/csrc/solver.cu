@@ -138,6 +138,53 @@ static void ensure_pool(int dev) {
   g_pool_ready[dev] = true;
 }
 
+// Timing events outlive contexts, per device: a profiled context borrows them and gives them
+// back when it is destroyed, so profiling a new context costs no event creation.
+static std::vector<cudaEvent_t> g_events[64];
+cudaEvent_t event_take(int dev) {
+  {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (dev >= 0 && dev < 64 && !g_events[dev].empty()) {
+      cudaEvent_t e = g_events[dev].back();
+      g_events[dev].pop_back();
+      return e;
+    }
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+void event_give(int dev, cudaEvent_t e) {
+  if (!e) return;
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (dev >= 0 && dev < 64) g_events[dev].push_back(e);
+  else cudaEventDestroy(e);
+}
+
+// 256 more event pairs for profiled launches, up to 16384 pairs per context (later launches of a
+// profiled class are counted but not timed).
+bool prof_grow(Ctx& c) {
+  Prof& P = c.prof;
+  if (P.capacity >= 16384) return false;
+  for (int i = 0; i < 256; ++i) {
+    cudaEvent_t a = event_take(c.device), b = event_take(c.device);
+    if (!a || !b) {
+      event_give(c.device, a);
+      event_give(c.device, b);
+      break;
+    }
+    P.ev.push_back(a);
+    P.ev.push_back(b);
+    P.cls.push_back(0);
+    ++P.capacity;
+  }
+  return P.used < P.capacity;
+}
+
 fetidp_status tmp_alloc(Ctx& c, void** p, size_t bytes) {
   if (bytes == 0) bytes = 8;
   ensure_pool(c.device);
@@ -304,11 +351,12 @@ fetidp_status pcg_solve(Ctx& c, const double* b, long long b_rs, double* x, long
   }
   const int max_it = c.opt.fixed_inner > 0 ? c.opt.fixed_inner : c.opt.max_inner;
   int cur = S_RZ0, it = 0;
-  // Graph path (no fixed iteration count, no profiling): two iterations (one per rho slot) are
-  // captured once per context and replayed; the convergence test runs on the device and the host
-  // reads the flags once per replay.  A replay may run one iteration past convergence: the
-  // converged right-hand sides are frozen (their x, r, p do not change), only time is spent.
-  const bool graph_ok = nact > 0 && c.opt.fixed_inner <= 0 && c.prof.mask == 0 && !c.pcg_graph_failed;
+  // Graph path (no fixed iteration count): two iterations (one per rho slot) are captured once
+  // per context and replayed; the convergence test runs on the device and the host reads the
+  // flags once per replay.  A replay may run one iteration past convergence: the converged
+  // right-hand sides are frozen (their x, r, p do not change), only time is spent.  Profiled
+  // launches keep their event pairs as event nodes of the graph, read after every replay.
+  const bool graph_ok = nact > 0 && c.opt.fixed_inner <= 0 && !c.pcg_graph_failed;
   // The graph runs on the context's own non-blocking stream (capture is not possible on the
   // legacy default stream), ordered after and before the caller's stream by events.
   struct StreamSwap {
@@ -335,9 +383,23 @@ fetidp_status pcg_solve(Ctx& c, const double* b, long long b_rs, double* x, long
   }
   if (graph_ok) {
     const double tol = c.mixed ? c.opt.tol_inner_mixed : c.opt.tol_inner;
+    Prof& pf = c.prof;
+    if (c.pcg_graph && c.pcg_graph_mask != pf.mask) {   // profiled classes changed: capture again
+      FD_CUDA(cudaGraphExecDestroy(c.pcg_graph));
+      c.pcg_graph = nullptr;
+    }
     if (!c.pcg_graph) {
       const long long l0 = g_launches.load();
+      pf.captured.clear();
+      if (pf.mask != 0 && pf.gev.empty())
+        for (int i = 0; i < 512; ++i) {
+          cudaEvent_t e = event_take(c.device);
+          if (!e) break;
+          pf.gev.push_back(e);
+        }
+      c.pcg_graph_mask = pf.mask;
       FD_CUDA(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
+      pf.capturing = true;
       fetidp_status cap = FETIDP_OK;
       for (int half = 0; half < 2 && cap == FETIDP_OK; ++half) {
         const int rz = half == 0 ? S_RZ0 : S_RZ1, rzn = half == 0 ? S_RZ1 : S_RZ0;
@@ -361,6 +423,7 @@ fetidp_status pcg_solve(Ctx& c, const double* b, long long b_rs, double* x, long
       }
       cudaGraph_t graph = nullptr;
       const cudaError_t ce = cudaStreamEndCapture(c.stream, &graph);
+      pf.capturing = false;
       // captured kernels have not run: they are counted when the graph is replayed
       c.pcg_graph_kernels = g_launches.load() - l0;
       g_launches.fetch_sub(c.pcg_graph_kernels);
@@ -371,6 +434,7 @@ fetidp_status pcg_solve(Ctx& c, const double* b, long long b_rs, double* x, long
         cudaGetLastError();
         c.pcg_graph = nullptr;
         c.pcg_graph_failed = true;
+        pf.captured.clear();
       }
     }
   }
@@ -382,6 +446,14 @@ fetidp_status pcg_solve(Ctx& c, const double* b, long long b_rs, double* x, long
       g_launches.fetch_add(c.pcg_graph_kernels);
       FD_CUDA(cudaMemcpyAsync(hs, sc, sizeof(double) * S_NSLOT * m, cudaMemcpyDeviceToHost, c.stream));
       FD_CUDA(cudaStreamSynchronize(c.stream));
+      for (const Prof::Captured& g : c.prof.captured) {
+        c.prof.launches[g.cls] += 1;
+        float v = 0.f;
+        if (cudaEventElapsedTime(&v, g.e0, g.e1) != cudaSuccess) { cudaGetLastError(); continue; }
+        c.prof.ms[g.cls] += v;
+        c.prof.flops[g.cls] += g.flops;
+        c.prof.bytes[g.cls] += g.bytes;
+      }
       nact = 0;
       it = 0;
       for (int r = 0; r < m; ++r) {
@@ -682,6 +754,7 @@ void fetidp_default_options(fetidp_options* o) {
   o->tc_split = 3;
   o->tol_inner_mixed = 1e-6;
   o->gram_drop_mixed = 1e-9;
+  o->profile_mask = 0;
 }
 
 const char* fetidp_status_string(fetidp_status s) {
@@ -761,21 +834,18 @@ fetidp_status fetidp_tc_selfcheck_static(int M, int K, int N, double* rel_err, v
   return tc_selfcheck_static(c, M, K, N, rel_err);
 }
 
-fetidp_status fetidp_profile_enable(fetidp_ctx* ctx, unsigned mask) {
-  FD_TRY(enter(ctx));
-  Prof& P = ctx->c.prof;
-  FD_CUDA(cudaStreamSynchronize(ctx->c.stream));
-  if (mask != 0 && P.capacity == 0) {
-    const int cap = 16384;
-    P.ev.resize(2 * cap);
-    for (auto& e : P.ev) FD_CUDA(cudaEventCreate(&e));
-    P.cls.assign(cap, 0);
-    P.capacity = cap;
-  }
+static fetidp_status profile_enable(Ctx& c, unsigned mask) {
+  Prof& P = c.prof;
   P.mask = mask;
   P.used = 0;
-  for (int k = 0; k < FETIDP_K_NCLASS; ++k) { P.flops[k] = 0; P.bytes[k] = 0; P.launches[k] = 0; }
+  for (int k = 0; k < FETIDP_K_NCLASS; ++k) { P.flops[k] = 0; P.bytes[k] = 0; P.launches[k] = 0; P.ms[k] = 0; }
   return FETIDP_OK;
+}
+
+fetidp_status fetidp_profile_enable(fetidp_ctx* ctx, unsigned mask) {
+  FD_TRY(enter(ctx));
+  FD_CUDA(cudaStreamSynchronize(ctx->c.stream));
+  return profile_enable(ctx->c, mask);
 }
 
 fetidp_status fetidp_profile_read(fetidp_ctx* ctx, double* ms, long long* launches, double* flops,
@@ -784,6 +854,7 @@ fetidp_status fetidp_profile_read(fetidp_ctx* ctx, double* ms, long long* launch
   Prof& P = ctx->c.prof;
   FD_CUDA(cudaStreamSynchronize(ctx->c.stream));
   double t[FETIDP_K_NCLASS] = {};
+  for (int k = 0; k < FETIDP_K_NCLASS; ++k) t[k] = P.ms[k];
   for (int i = 0; i < P.used; ++i) {
     float v = 0.f;
     FD_CUDA(cudaEventElapsedTime(&v, P.ev[2 * i], P.ev[2 * i + 1]));
@@ -794,7 +865,7 @@ fetidp_status fetidp_profile_read(fetidp_ctx* ctx, double* ms, long long* launch
     if (launches) launches[k] = P.launches[k];
     if (flops) flops[k] = P.flops[k];
     if (bytes) bytes[k] = P.bytes[k];
-    P.flops[k] = 0; P.bytes[k] = 0; P.launches[k] = 0;
+    P.flops[k] = 0; P.bytes[k] = 0; P.launches[k] = 0; P.ms[k] = 0;
   }
   P.used = 0;
   return FETIDP_OK;
@@ -804,8 +875,9 @@ void fetidp_destroy(fetidp_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->c.device);
   cudaStreamSynchronize(ctx->c.stream);
-  for (auto& e : ctx->c.prof.ev) cudaEventDestroy(e);
   if (ctx->c.pcg_graph) cudaGraphExecDestroy(ctx->c.pcg_graph);
+  for (auto& e : ctx->c.prof.ev) event_give(ctx->c.device, e);
+  for (auto& e : ctx->c.prof.gev) event_give(ctx->c.device, e);
   if (ctx->c.ws) {
     cudaStreamSynchronize(ctx->c.ws);
     cudaStreamDestroy(ctx->c.ws);
@@ -836,7 +908,8 @@ fetidp_status fetidp_setup(const fetidp_problem* probs, int n_problems, const fe
   fetidp_ctx* ctx = new fetidp_ctx();
   cudaGetDevice(&ctx->c.device);
   ctx->c.stream = reinterpret_cast<cudaStream_t>(cuda_stream);
-  fetidp_status s = setup_context(ctx->c, probs, n_problems, o);
+  fetidp_status s = o.profile_mask ? profile_enable(ctx->c, o.profile_mask) : FETIDP_OK;
+  if (s == FETIDP_OK) s = setup_context(ctx->c, probs, n_problems, o);
   if (s != FETIDP_OK) {
     fetidp_destroy(ctx);
     return s;

@@ -42,8 +42,19 @@ def test_default_options_and_status_strings(lib):
     o = binding.default_options()
     assert o.tol_outer == 1e-8 and o.tol_inner == 1e-11 and o.precision == binding.FETIDP_FP64
     assert o.tol_inner_mixed == 1e-6 and o.gram_drop_mixed == 1e-9 and o.tc_split == 3
+    assert o.profile_mask == 0
     assert lib.fetidp_status_string(-4) == b"not converged"
     assert lib.fetidp_status_string(0) == b"ok"
+
+
+def test_kernel_classes_match_the_header():
+    with open(os.path.join(ROOT, "include", "fetidp.h")) as f:
+        hdr = f.read()
+    enum = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"FETIDP_K_(\w+)\s*=\s*(\d+)", hdr)}
+    enum.pop("nclass")
+    assert enum == {k.lower(): v for k, v in binding.KCLASS.items()}
+    assert binding.class_mask(["sweep", "tc_gemm"]) == (1 << 9) | (1 << 7)
+    assert binding.default_options(profile=["greedy"]).profile_mask == 1 << 11
 
 
 def test_problem_struct_marshalling():
