@@ -36,9 +36,9 @@ UNIT = "DOF/s"
 # FMA-chain probe) -> 152 SMs x 2 x 2 flop x 2.07 GHz max clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# One double-float multiply-add term of the mixed Eq. 42 trace GEMM issues 13 FP32 instructions
+# One double-float multiply-add term of the mixed Eq. 42 trace GEMM issues 12 FP32 instructions
 # (exact product by FMA residual, two cross products, TwoSum, low-part accumulation).
-DF_OPS_PER_TERM = 13
+DF_OPS_PER_TERM = 12
 
 
 def measured_peaks():
@@ -172,7 +172,7 @@ def kernel_source_hash(files=None):
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_class):
+def ncu_traffic(kernel_class, precision):
     """DRAM bytes per launch from the committed ncu summary, if taken on the current sources."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
@@ -180,7 +180,7 @@ def ncu_traffic(kernel_class):
             data = json.load(f)
     except OSError:
         return None
-    ent = data.get(kernel_class)
+    ent = data.get(f"{kernel_class}:{precision}")
     if not ent or ent.get("source_hash") != kernel_source_hash(CLASS_SOURCES.get(kernel_class)):
         return None
     return ent.get("dram_bytes_per_launch")
@@ -225,6 +225,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="best", choices=["fp64", "mixed", "best"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-ref", action="store_true",
+                    help="skip the one FP64-path step timed for the mixed-vs-FP64 comparison")
     ap.add_argument("--cpu-sample", type=int, default=16)
     ap.add_argument("--cells", type=int, default=64,
                     help="cells per side (64 = the benchmark workload; smaller for profiling)")
@@ -258,7 +260,7 @@ def main():
 
     # the plain FP64 path on the same workload, for the mixed-vs-FP64 comparison (one step)
     fp64_ref = None
-    if prec_name == "mixed":
+    if prec_name == "mixed" and not args.no_fp64_ref:
         s64 = binding.Solver(prob, precision=binding.FETIDP_FP64)
         s64.close()
         torch.cuda.synchronize()
@@ -343,7 +345,7 @@ def main():
     roof["kernel_class"] = dominant
     roof["launches"] = nl
     roof["avg_launch_ms"] = kms / max(nl, 1)
-    tr = ncu_traffic(dominant)
+    tr = ncu_traffic(dominant, prec_name)
     roof["traffic"] = tr
     roof["share_of_step"] = kms / ms if ms > 0 else None
 

@@ -230,6 +230,8 @@ struct Ctx {
   double* r_dev = nullptr;    // [N]
   // snapshots = C_hat at every Gauss point, [N][nsnap]
   double* snap = nullptr;
+  // mixed path: FP32 element matrices [N][nelem][ND][ND] for the Eq. 46b K_s products
+  float* Ke_all = nullptr;
   // ROM coefficients [N][nrb]
   double* alpha = nullptr;
   double* pi = nullptr;
@@ -280,6 +282,10 @@ struct Ctx {
   TcComb cUrd;                  // U_rd^(k) combined with delta (transpose of Algorithm 3)
   uint8_t* tc_bbuf = nullptr;   // packed B operand staging
   size_t tc_bbuf_bytes = 0;
+  float* tc_xf = nullptr;       // resident-operator combination: x in FP32
+  size_t tc_xf_bytes = 0;
+  float* tc_yp = nullptr;       // resident-operator combination: partial sums per principal group
+  size_t tc_yp_bytes = 0;
   int* tc_err = nullptr;        // device error flag of the bounded waits
 };
 
@@ -350,13 +356,13 @@ struct GreedyState {
   int stop;
   int count;
   int sigma[kMaxRbGreedy];
+  double znrm;   // 2-norm of the residual row selected at the current step
 };
 fetidp_status k_greedy_step(Ctx& c, double* D, const double* zeta, long long rows, long long len, double* beta,
-                            double* inf, double* sq, const GreedyState* st, int i);
-fetidp_status k_greedy_select(Ctx& c, const double* inf, long long n, int i, double tol_rb, double tie,
-                              GreedyState* st);
-fetidp_status k_greedy_zeta(Ctx& c, const double* D, const double* sq, long long len, int i, const GreedyState* st,
-                            double* zeta);
+                            double* inf, const GreedyState* st, int i);
+fetidp_status k_greedy_select(Ctx& c, const double* inf, long long n, const double* D, long long len, int i,
+                              double tol_rb, double tie, GreedyState* st);
+fetidp_status k_greedy_zeta(Ctx& c, const double* D, long long len, int i, const GreedyState* st, double* zeta);
 fetidp_status k_greedy_alpha(Ctx& c, const double* Z, const double* nrm, const double* beta, int nrb,
                              const GreedyState* st, double* T, double* alpha);
 // dense batched setup kernels (principal blocks, SPD inverses by sweeps)
@@ -396,6 +402,7 @@ fetidp_status k_grouped_gemm_n(Ctx& c, const double* A, long long a_stride_k, in
 fetidp_status k_gram_solve(Ctx& c, const double* R, const double* KR, CCellVec v, CellVec x,
                            int nrhs);
 fetidp_status k_grad(Ctx& c, const double* u, const double* w, double* g);
+fetidp_status k_element_matrices_f32(Ctx& c);
 fetidp_status k_apply_K_f32(Ctx& c, const float* u, long long u_rs, int u_cs, float* y, long long y_rs,
                             int y_cs, int nvec, int nrhs, bool idp, bool r_only, long long ext = -1);
 fetidp_status k_gram_solve_f32(Ctx& c, const float* R, const float* KR, CCellVec v, CellVec x,
@@ -418,6 +425,9 @@ fetidp_status tc_comb_pack(Ctx& c, TcComb& op, const double* src0, long long st0
                            int M0, const double* src1, long long st1, int lda1, int r01, int c01, int M1,
                            int K, int nops, int split);
 size_t tc_comb_staging_bytes(const TcComb& op, long long ncols);
+bool tc_comb2_ok(const TcComb& op);
+size_t tc_comb2_xf_bytes(const TcComb& op, long long ncols);
+size_t tc_comb2_yp_bytes(const TcComb& op, long long ncols);
 fetidp_status tc_comb_selfcheck(Ctx& c, int M0, int M1, int K, int N, int nops, double* rel_err);
 fetidp_status tc_comb_apply(Ctx& c, const TcComb& op, CCellVec X, const double* coef0, const double* coef1,
                             void* Y, bool y_f64, long long y_rs, int y_cs, double alpha, double beta, int nrhs,

@@ -120,15 +120,18 @@ __global__ void assemble_principal_kernel(const double* __restrict__ snap, const
 // and W = V A_PP^{-1} for the panel column V = A_:P) and one of sweep_update_kernel (the rank-nb
 // update of the upper triangle, 64 x 64 tiles): 2 launches per 32 pivots instead of 32.
 constexpr int kSwNb = 32;     // panel width
-constexpr int kSwRows = 64;   // rows per panel-kernel block and update tile edge
+constexpr int kSwRows = 64;   // largest rows per panel-kernel block and update tile edge
 
-// grid: (row blocks of 64) x batch; 256 threads.
+// grid: (row blocks of `rows` <= 64) x batch; 256 threads.  The nb x nb sweep runs on the upper
+// triangle (mirrored in shared memory) with one reciprocal per pivot: GB300 issues FP64 at
+// 2 FMA/clk/SM, so every redundant FP64 operation of this sequential part is latency.
 __global__ void __launch_bounds__(256) sweep_panel_kernel(const double* __restrict__ A, long long stride, int n,
-                                                          int lda, int k0, int nb, int nrb_rows,
+                                                          int lda, int k0, int nb, int rows, int nrb_rows,
                                                           double* __restrict__ V, double* __restrict__ W,
                                                           double* __restrict__ Sinv, int* __restrict__ status) {
   __shared__ double S[kSwNb][kSwNb + 1];
   __shared__ double Vs[kSwRows][kSwNb + 1];
+  __shared__ double sinv;
   const int rb = blockIdx.x % nrb_rows;
   const long long b = blockIdx.x / nrb_rows;
   const int tid = threadIdx.x;
@@ -138,40 +141,59 @@ __global__ void __launch_bounds__(256) sweep_panel_kernel(const double* __restri
     const int r = t / nb, q = t - (t / nb) * nb;
     S[r][q] = r <= q ? Ab[(long long)(k0 + r) * lda + k0 + q] : Ab[(long long)(k0 + q) * lda + k0 + r];
   }
+  // this thread's upper-triangle entries (r <= q), at most 3 of the 528
+  constexpr int kMaxE = (kSwNb * (kSwNb + 1) / 2 + 255) / 256;
+  int er[kMaxE], eq[kMaxE], ne = 0;
+  for (int t = tid; t < nb * (nb + 1) / 2 && ne < kMaxE; t += blockDim.x) {
+    int r = 0, u = t;
+    while (u >= nb - r) { u -= nb - r; ++r; }
+    er[ne] = r;
+    eq[ne] = r + u;
+    ++ne;
+  }
   __syncthreads();
   // sweep of the nb x nb block: S <- -A_PP^{-1}
   bool bad = false;
   for (int p = 0; p < nb; ++p) {
-    const double a = S[p][p];
-    bad |= !(a > 0.0);
-    const double inv = 1.0 / a;
-    double nv[(kSwNb * kSwNb + 255) / 256];
-    int cnt = 0;
-    for (int t = tid; t < nb * nb; t += blockDim.x, ++cnt) {
-      const int r = t / nb, q = t - (t / nb) * nb;
+    if (tid == 0) {
+      const double a = S[p][p];
+      bad |= !(a > 0.0);
+      sinv = 1.0 / a;
+    }
+    __syncthreads();
+    const double inv = sinv;
+    double nv[kMaxE];
+#pragma unroll
+    for (int e = 0; e < kMaxE; ++e) {
+      if (e >= ne) break;
+      const int r = er[e], q = eq[e];
       double v;
       if (r == p && q == p) v = -inv;
       else if (r == p) v = S[p][q] * inv;
       else if (q == p) v = S[r][p] * inv;
       else v = fma(-S[r][p] * inv, S[p][q], S[r][q]);
-      nv[cnt] = v;
+      nv[e] = v;
     }
     __syncthreads();
-    cnt = 0;
-    for (int t = tid; t < nb * nb; t += blockDim.x, ++cnt) S[t / nb][t - (t / nb) * nb] = nv[cnt];
+#pragma unroll
+    for (int e = 0; e < kMaxE; ++e) {
+      if (e >= ne) break;
+      S[er[e]][eq[e]] = nv[e];
+      S[eq[e]][er[e]] = nv[e];
+    }
     __syncthreads();
   }
-  if (bad && rb == 0 && tid == 0) atomicExch(status, 1);
+  if (bad && rb == 0) atomicExch(status, 1);
   // V rows of this block: V_i = A_iP (zero for i in P, unused there)
-  const int i0 = rb * kSwRows;
-  if (i0 + kSwRows <= k0) {   // rows above the panel: A[i][k0 + p], contiguous in p
-    for (int t = tid; t < kSwRows * nb; t += blockDim.x) {
+  const int i0 = rb * rows;
+  if (i0 + rows <= k0) {   // rows above the panel: A[i][k0 + p], contiguous in p
+    for (int t = tid; t < rows * nb; t += blockDim.x) {
       const int li = t / nb, p = t - (t / nb) * nb;
       Vs[li][p] = Ab[(long long)(i0 + li) * lda + k0 + p];
     }
-  } else {                    // rows at or below the panel: A[k0 + p][i], contiguous in i
-    for (int t = tid; t < kSwRows * nb; t += blockDim.x) {
-      const int li = t % kSwRows, p = t / kSwRows, i = i0 + li;
+  } else {                 // rows at or below the panel: A[k0 + p][i], contiguous in i
+    for (int t = tid; t < rows * nb; t += blockDim.x) {
+      const int li = t % rows, p = t / rows, i = i0 + li;
       double v = 0.0;
       if (i < n) {
         if (i < k0) v = Ab[(long long)i * lda + k0 + p];
@@ -184,7 +206,7 @@ __global__ void __launch_bounds__(256) sweep_panel_kernel(const double* __restri
   // W_i = V_i A_PP^{-1} = -V_i S; written with V (layout [b][i][p], p fastest)
   double* Vb = V + b * (long long)n * kSwNb;
   double* Wb = W + b * (long long)n * kSwNb;
-  for (int t = tid; t < kSwRows * nb; t += blockDim.x) {
+  for (int t = tid; t < rows * nb; t += blockDim.x) {
     const int li = t / nb, p = t - (t / nb) * nb, i = i0 + li;
     if (i >= n) continue;
     double w = 0.0;
@@ -197,15 +219,17 @@ __global__ void __launch_bounds__(256) sweep_panel_kernel(const double* __restri
       Sinv[b * kSwNb * kSwNb + (t / nb) * kSwNb + t % nb] = -S[t / nb][t % nb];
 }
 
-// Rank-nb update of the upper triangle for panel P, one 64 x 64 tile (I <= J) per block, 256
-// threads of 4 x 4 entries.  grid: upper tiles x batch.
+// Rank-nb update of the upper triangle for panel P, one TS x TS tile (I <= J) per block, 256
+// threads of (TS/16) x (TS/16) entries.  grid: upper tiles x batch.
+template <int TS>
 __global__ void __launch_bounds__(256) sweep_update_kernel(double* __restrict__ A, long long stride, int n, int lda,
                                                            int k0, int nb, int ntile,
                                                            const double* __restrict__ V,
                                                            const double* __restrict__ W,
                                                            const double* __restrict__ Sinv) {
-  __shared__ double Ws[kSwNb][kSwRows];
-  __shared__ double Vs[kSwNb][kSwRows];
+  constexpr int E = TS / 16;
+  __shared__ double Ws[kSwNb][TS];
+  __shared__ double Vs[kSwNb][TS];
   const int nup = ntile * (ntile + 1) / 2;
   const long long b = blockIdx.x / nup;
   int t = blockIdx.x - (int)(b * nup), I = 0;
@@ -214,34 +238,34 @@ __global__ void __launch_bounds__(256) sweep_update_kernel(double* __restrict__ 
   const int tid = threadIdx.x;
   const double* Wb = W + b * (long long)n * kSwNb;
   const double* Vb = V + b * (long long)n * kSwNb;
-  for (int e = tid; e < kSwRows * kSwNb; e += blockDim.x) {
+  for (int e = tid; e < TS * kSwNb; e += blockDim.x) {
     const int l = e / kSwNb, p = e - (e / kSwNb) * kSwNb;
-    const int i = I * kSwRows + l, j = J * kSwRows + l;
+    const int i = I * TS + l, j = J * TS + l;
     Ws[p][l] = (i < n && p < nb) ? Wb[(long long)i * kSwNb + p] : 0.0;
     Vs[p][l] = (j < n && p < nb) ? Vb[(long long)j * kSwNb + p] : 0.0;
   }
   __syncthreads();
   const int ty = tid / 16, tx = tid - (tid / 16) * 16;
-  double acc[4][4] = {};
+  double acc[E][E] = {};
   for (int p = 0; p < nb; ++p) {
-    double w[4], v[4];
+    double w[E], v[E];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) { w[r] = Ws[p][ty * 4 + r]; v[r] = Vs[p][tx * 4 + r]; }
+    for (int r = 0; r < E; ++r) { w[r] = Ws[p][ty * E + r]; v[r] = Vs[p][tx * E + r]; }
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < E; ++r)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[r][q] = fma(w[r], v[q], acc[r][q]);
+      for (int q = 0; q < E; ++q) acc[r][q] = fma(w[r], v[q], acc[r][q]);
   }
   double* Ab = A + b * stride;
   const double* Sb = Sinv + b * kSwNb * kSwNb;
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int i = I * kSwRows + ty * 4 + r;
+  for (int r = 0; r < E; ++r) {
+    const int i = I * TS + ty * E + r;
     if (i >= n) continue;
     const bool pi = i >= k0 && i < k0 + nb;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int j = J * kSwRows + tx * 4 + q;
+    for (int q = 0; q < E; ++q) {
+      const int j = J * TS + tx * E + q;
       if (j >= n || j < i) continue;
       const bool pj = j >= k0 && j < k0 + nb;
       double* a = Ab + (long long)i * lda + j;
@@ -477,59 +501,104 @@ __global__ void coarse_assemble_kernel(const double* __restrict__ Spp, long long
 }
 
 // Y[cell][m] = sum_k A[m][k] X[cell][k] in double-float arithmetic on the FP32 pipe (GB300
-// issues FP32 at ~60x its FP64 rate).  Each FP64 operand is split into hi + lo floats (48
-// significant bits); a product is hi*hi, made exact by an FMA residual, plus the cross terms;
-// the sum is kept as an unevaluated pair (s, c) with TwoSum on the leading part.  Relative error
-// ~K * 2^-46 of the largest term, against K * 2^-53 for FP64.  64 x 64 output tile per block,
-// 4 x 4 per thread, K chunks of 16.
-constexpr int DF_T = 64, DF_K = 16;
-__global__ void __launch_bounds__(256) df_gemm_kernel(const double* __restrict__ A, int lda, int M, int K,
-                                                      const double* __restrict__ X, int x_cs, long long ncols,
+// issues FP32 at ~60x its FP64 rate).  Each FP64 operand is split once (df_split_kernel) into
+// float planes hi = fl(v), lo = fl(v - hi) (48 significant bits), zero-padded to whole tiles.  A
+// term is hi*hi, made exact by an FMA residual, plus the two cross products; the sum is kept as
+// an unevaluated pair (s, c) with TwoSum on the leading part: 12 FP32 instructions per term.
+// Relative error ~K * 2^-46 of the largest term, against K * 2^-53 for FP64.  64 x 64 output
+// tile per block, 4 x 4 per thread, K chunks of 16 staged by cp.async in two buffers.
+constexpr int DF_T = 64, DF_K = 16, DF_LD = 20;   // smem rows of 16 floats + 4 pad (16-byte aligned)
+
+__global__ void df_split_kernel(const double* __restrict__ src, long long rows, int cols, long long src_ld,
+                                long long rows_p, int ld_p, float* __restrict__ hi, float* __restrict__ lo) {
+  const long long total = rows_p * ld_p;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long r = t / ld_p;
+    const int q = (int)(t - r * ld_p);
+    const double v = (r < rows && q < cols) ? src[r * src_ld + q] : 0.0;
+    const float h = (float)v;
+    hi[t] = h;
+    lo[t] = (float)(v - (double)h);
+  }
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+__global__ void __launch_bounds__(256, 2) df_gemm_kernel(const float* __restrict__ Ah, const float* __restrict__ Al,
+                                                      const float* __restrict__ Xh, const float* __restrict__ Xl,
+                                                      int ldk, int nkc, int M, long long ncols,
                                                       double* __restrict__ Y, int y_cs) {
-  __shared__ float Ah[DF_K][DF_T + 1], Al[DF_K][DF_T + 1];
-  __shared__ float Xh[DF_K][DF_T + 1], Xl[DF_K][DF_T + 1];
-  const long long col0 = (long long)blockIdx.x * DF_T;
-  const int m0 = blockIdx.y * DF_T;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  float sh[4][4], sl[4][4];
+  __shared__ __align__(16) float sA[2][2][DF_T][DF_LD];   // [buffer][hi, lo][row m][k]
+  __shared__ __align__(16) float sX[2][2][DF_T][DF_LD];   // [buffer][hi, lo][column][k]
+  // row tiles fastest: the blocks resident together share their X (snapshot) tiles, which are
+  // then read from DRAM about once, while the table planes stay in L2
+  const long long m0 = (long long)blockIdx.x * DF_T;
+  const long long col0 = (long long)blockIdx.y * DF_T;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  // one chunk: 4 planes x 64 rows x 4 quads of 16 bytes = 1024 copies, 4 per thread
+  auto load = [&](int buf, int kc) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + 256 * u, plane = e >> 8, row = (e >> 2) & 63, quad = e & 3;
+      const long long off = (long long)kc * DF_K + quad * 4;
+      switch (plane) {
+        case 0: cp_async16(&sA[buf][0][row][quad * 4], Ah + (m0 + row) * ldk + off); break;
+        case 1: cp_async16(&sA[buf][1][row][quad * 4], Al + (m0 + row) * ldk + off); break;
+        case 2: cp_async16(&sX[buf][0][row][quad * 4], Xh + (col0 + row) * ldk + off); break;
+        default: cp_async16(&sX[buf][1][row][quad * 4], Xl + (col0 + row) * ldk + off); break;
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  float s[4][4], cl[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) { sh[i][j] = 0.f; sl[i][j] = 0.f; }
-  for (int k0 = 0; k0 < K; k0 += DF_K) {
-    for (int t = threadIdx.x; t < DF_K * DF_T; t += 256) {
-      const int r = t / DF_K, q = t - r * DF_K;   // q fastest: coalesced rows of A and X
-      const int gm = m0 + r, gk = k0 + q;
-      const double av = (gm < M && gk < K) ? A[(size_t)gm * lda + gk] : 0.0;
-      const float ah = (float)av;
-      Ah[q][r] = ah;
-      Al[q][r] = (float)(av - (double)ah);
-      const long long gc = col0 + r;
-      const double xv = (gc < ncols && gk < K) ? X[gc * x_cs + gk] : 0.0;
-      const float xh = (float)xv;
-      Xh[q][r] = xh;
-      Xl[q][r] = (float)(xv - (double)xh);
+    for (int j = 0; j < 4; ++j) { s[i][j] = 0.f; cl[i][j] = 0.f; }
+  load(0, 0);
+  for (int kc = 0; kc < nkc; ++kc) {
+    const int buf = kc & 1;
+    if (kc + 1 < nkc) {
+      load(buf ^ 1, kc + 1);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     }
     __syncthreads();
-#pragma unroll 4
-    for (int q = 0; q < DF_K; ++q) {
-      float ah[4], al[4], bh[4], bl[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) { ah[i] = Ah[q][ty + 16 * i]; al[i] = Al[q][ty + 16 * i]; }
+    for (int q4 = 0; q4 < DF_K; q4 += 4) {
+      float4 bh[4], bl[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) { bh[j] = Xh[q][tx + 16 * j]; bl[j] = Xl[q][tx + 16 * j]; }
+      for (int j = 0; j < 4; ++j) {
+        bh[j] = *reinterpret_cast<const float4*>(&sX[buf][0][tx + 16 * j][q4]);
+        bl[j] = *reinterpret_cast<const float4*>(&sX[buf][1][tx + 16 * j][q4]);
+      }
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < 4; ++i) {
+        const float4 ah4 = *reinterpret_cast<const float4*>(&sA[buf][0][ty + 16 * i][q4]);
+        const float4 al4 = *reinterpret_cast<const float4*>(&sA[buf][1][ty + 16 * i][q4]);
+        const float ah[4] = {ah4.x, ah4.y, ah4.z, ah4.w}, al[4] = {al4.x, al4.y, al4.z, al4.w};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const float p = ah[i] * bh[j];
-          const float e = fmaf(ah[i], bh[j], -p) + fmaf(ah[i], bl[j], al[i] * bh[j]);
-          const float t = sh[i][j] + p;            // TwoSum(sh, p)
-          const float bv = t - sh[i][j];
-          const float err = (sh[i][j] - (t - bv)) + (p - bv);
-          sh[i][j] = t;
-          sl[i][j] += err + e;
+          const float xh[4] = {bh[j].x, bh[j].y, bh[j].z, bh[j].w}, xl[4] = {bl[j].x, bl[j].y, bl[j].z, bl[j].w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float p = ah[q] * xh[q];
+            const float e = fmaf(ah[q], xh[q], -p);     // exact: p + e = ah * xh
+            float c = fmaf(ah[q], xl[q], cl[i][j]);
+            c = fmaf(al[q], xh[q], c);
+            const float t = s[i][j] + p;                // TwoSum(s, p)
+            const float bv = t - s[i][j];
+            const float err = (s[i][j] - (t - bv)) + (p - bv);
+            s[i][j] = t;
+            cl[i][j] = c + (err + e);
+          }
         }
+      }
     }
     __syncthreads();
   }
@@ -539,8 +608,8 @@ __global__ void __launch_bounds__(256) df_gemm_kernel(const double* __restrict__
     if (gc >= ncols) continue;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int gm = m0 + ty + 16 * i;
-      if (gm < M) Y[gc * y_cs + gm] = (double)sh[i][j] + (double)sl[i][j];
+      const long long gm = m0 + ty + 16 * i;
+      if (gm < M) Y[gc * y_cs + gm] = (double)s[i][j] + (double)cl[i][j];
     }
   }
 }
@@ -575,16 +644,24 @@ fetidp_status k_spd_inverse_batched(Ctx& c, double* A, long long stride, int n, 
   const size_t vw = (size_t)batch * n * kSwNb;
   FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&buf), sizeof(double) * (2 * vw + (size_t)batch * kSwNb * kSwNb)));
   double *V = buf, *W = buf + vw, *Sinv = buf + 2 * vw;
-  const int nrows = (n + kSwRows - 1) / kSwRows;
+  // 64-row blocks and tiles while they fill the GPU, else 32 (small batches of the coarse levels)
+  const int n64 = (n + 63) / 64;
+  const bool wide = (long long)n64 * (n64 + 1) / 2 * batch >= 2 * 152;
+  const int ts = wide ? 64 : 32;
+  const int nrows = (n + ts - 1) / ts;
   const long long panel_blocks = (long long)nrows * batch;
   const long long update_blocks = (long long)nrows * (nrows + 1) / 2 * batch;
   fetidp_status st = FETIDP_OK;
   if (panel_blocks > INT_MAX || update_blocks > INT_MAX) st = FETIDP_EINVAL;
   for (int k0 = 0; k0 < n && st == FETIDP_OK; k0 += kSwNb) {
     const int nb = n - k0 < kSwNb ? n - k0 : kSwNb;
-    sweep_panel_kernel<<<(int)panel_blocks, 256, 0, c.stream>>>(A, stride, n, lda, k0, nb, nrows, V, W, Sinv, status);
+    sweep_panel_kernel<<<(int)panel_blocks, 256, 0, c.stream>>>(A, stride, n, lda, k0, nb, ts, nrows, V, W, Sinv,
+                                                                status);
     count_launch();
-    sweep_update_kernel<<<(int)update_blocks, 256, 0, c.stream>>>(A, stride, n, lda, k0, nb, nrows, V, W, Sinv);
+    if (wide)
+      sweep_update_kernel<64><<<(int)update_blocks, 256, 0, c.stream>>>(A, stride, n, lda, k0, nb, nrows, V, W, Sinv);
+    else
+      sweep_update_kernel<32><<<(int)update_blocks, 256, 0, c.stream>>>(A, stride, n, lda, k0, nb, nrows, V, W, Sinv);
     count_launch();
     if (cudaPeekAtLastError() != cudaSuccess) st = FETIDP_ECUDA;
   }
@@ -625,11 +702,37 @@ fetidp_status k_batched_diag_sum(Ctx& c, const double* A, long long stride, int 
 
 fetidp_status k_df_gemm(Ctx& c, const double* A, int lda, int M, int K, const double* X, int x_cs, long long ncols,
                         double* Y, int y_cs) {
-  ProfScope ps(c, FETIDP_K_TRACES, 2.0 * M * (double)K * ncols, 8.0 * ((double)M * K + (double)ncols * (K + M)));
-  const dim3 grid((unsigned)((ncols + DF_T - 1) / DF_T), (unsigned)((M + DF_T - 1) / DF_T));
-  df_gemm_kernel<<<grid, 256, 0, c.stream>>>(A, lda, M, K, X, x_cs, ncols, Y, y_cs);
-  FD_CHECK_LAUNCH();
-  return FETIDP_OK;
+  if (M <= 0 || ncols <= 0) return FETIDP_OK;
+  const int Kp = (K + DF_K - 1) / DF_K * DF_K;
+  const long long Mp = (M + DF_T - 1) / DF_T * DF_T, Np = (ncols + DF_T - 1) / DF_T * DF_T;
+  float* buf = nullptr;
+  FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&buf), sizeof(float) * 2 * (size_t)(Mp + Np) * Kp));
+  float *Ah = buf, *Al = buf + (size_t)Mp * Kp, *Xh = Al + (size_t)Mp * Kp, *Xl = Xh + (size_t)Np * Kp;
+  fetidp_status st = FETIDP_OK;
+  {
+    ProfScope ps(c, FETIDP_K_SETUP, 0.0, 16.0 * ((double)M * K + (double)ncols * K));
+    df_split_kernel<<<grid_for(Mp * Kp, 256), 256, 0, c.stream>>>(A, M, K, lda, Mp, Kp, Ah, Al);
+    count_launch();
+    df_split_kernel<<<grid_for(Np * Kp, 256), 256, 0, c.stream>>>(X, ncols, K, x_cs, Np, Kp, Xh, Xl);
+    count_launch();
+  }
+  {
+    ProfScope ps(c, FETIDP_K_TRACES, 2.0 * M * (double)K * ncols, 8.0 * ((double)M * K + (double)ncols * (K + M)));
+    if (Np / DF_T > 65535) {
+      tmp_free(c, buf);
+      set_error("trace contraction: too many cells for one launch");
+      return FETIDP_EINVAL;
+    }
+    const dim3 grid((unsigned)(Mp / DF_T), (unsigned)(Np / DF_T));
+    df_gemm_kernel<<<grid, 256, 0, c.stream>>>(Ah, Al, Xh, Xl, Kp, Kp / DF_K, M, ncols, Y, y_cs);
+    count_launch();
+  }
+  if (cudaPeekAtLastError() != cudaSuccess) {
+    set_error(std::string("kernel launch: ") + cudaGetErrorString(cudaGetLastError()));
+    st = FETIDP_ECUDA;
+  }
+  tmp_free(c, buf);
+  return st;
 }
 
 fetidp_status k_batched_gemm(Ctx& c, bool ta, bool tb, int M, int N, int K, double alpha, const double* A,

@@ -176,60 +176,107 @@ __device__ __forceinline__ int sym_index(int I, int J, int NI) {
   return I * NI - I * (I - 1) / 2 + (J - I);
 }
 
-// Multi-vector K_s application in FP32 (the Eq. 46b products K_s R of the mixed path).  One
-// block per (rhs, cell); for each colour group (elements that share no node) the Gauss-point
-// C_hat of its elements is staged in shared memory (coalesced), every element matrix
-// K_e = sum_gp w B^T C_hat B is formed once (one thread per element row) and applied to all
-// vectors of the chunk, one thread per (element, vector).  Vectors are stored dof-major with a
-// padded stride, so the threads of an element read consecutive words and every K_e entry is a
-// broadcast.  Global vectors are read and written in local order through the staged
-// permutation, so no load depends on another.
+// Element matrices K_e = sum_gp w B^T C_hat B of every element of every cell in FP32 (C_hat
+// rounded to FP32 first), row-major ND x ND, for the Eq. 46b products of the mixed path.  They
+// depend on the cell's C_hat only, so they are formed once per setup instead of in every local
+// ROM solve.  One thread per (cell, element, row (A, i)).
 constexpr int kMultiThreads = 512;
-// padded strides (in floats) of the staged element data: odd / 4-mod-32 so that the threads of
-// neighbouring elements hit different banks; K_e rows stay 16-byte aligned
-__host__ __device__ constexpr int multi_ke_stride(int D) { return (D == 2 ? 64 : 576) + 4; }
-__host__ __device__ constexpr int multi_c_stride(int D) { return (D == 2 ? 4 * 16 : 8 * 81) + 1; }
 template <int D>
-__global__ void __launch_bounds__(kMultiThreads) apply_K_multi_kernel(
-    int e, long long ncell, int n, int len, const int* __restrict__ perm, bool idp,
-    const float* __restrict__ u, long long u_rs, int u_cs, float* __restrict__ y, long long y_rs, int y_cs,
-    int nvec, int VB, const double* __restrict__ chat, int nc, float wq, float inv_h, int nelc_max,
-    long long u_ext, long long y_ext) {
+__global__ void element_matrices_f32_kernel(const double* __restrict__ chat, long long ncell, int e, int nc,
+                                            float wq, float inv_h, float* __restrict__ Kall) {
   constexpr int NA = 1 << D;
   constexpr int ND = NA * D;
   constexpr int NI = D * D;
+  const int nel = e * e * (D == 3 ? e : 1);
+  const int cpe = NA * nc;
+  const long long total = ncell * nel * ND;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int row = (int)(t % ND);
+    const long long ce = t / ND;                    // cell * nel + el
+    const int A = row / D, i = row - A * D;
+    const double* Ce = chat + ce * cpe;
+    float krow[ND];
+#pragma unroll
+    for (int k = 0; k < ND; ++k) krow[k] = 0.f;
+    for (int gp = 0; gp < NA; ++gp) {
+      float dn[NA * D];                             // shape-function gradients at this Gauss point
+#pragma unroll
+      for (int B = 0; B < NA; ++B)
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          float v = inv_h;
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            const int off = (B >> k) & 1;
+            const float tk = (float)gauss_t((gp >> k) & 1);
+            if (k == a) v *= off ? 1.f : -1.f;
+            else v *= off ? tk : 1.f - tk;
+          }
+          dn[B * D + a] = v;
+        }
+      float w[D][D];   // w[j][b] = sum_a dN_A[a] C[(i,a),(j,b)]
+#pragma unroll
+      for (int j = 0; j < D; ++j)
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+          float sacc = 0.f;
+#pragma unroll
+          for (int a = 0; a < D; ++a)
+            sacc += dn[A * D + a] * (float)Ce[gp * nc + sym_index(i * D + a, j * D + b, NI)];
+          w[j][b] = sacc;
+        }
+#pragma unroll
+      for (int B = 0; B < NA; ++B)
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          float sacc = 0.f;
+#pragma unroll
+          for (int b = 0; b < D; ++b) sacc += w[j][b] * dn[B * D + b];
+          krow[B * D + j] += wq * sacc;
+        }
+    }
+    float* kr = Kall + t * ND;
+#pragma unroll
+    for (int k = 0; k < ND; k += 4)
+      *reinterpret_cast<float4*>(kr + k) = make_float4(krow[k], krow[k + 1], krow[k + 2], krow[k + 3]);
+  }
+}
+
+// Multi-vector K_s application in FP32 (the Eq. 46b products K_s R of the mixed path).  One
+// block per (rhs, cell); for each colour group (elements that share no node) the precomputed
+// element matrices of its elements are staged in shared memory (contiguous, coalesced) and
+// applied to all vectors of the chunk, one thread per (element, vector).  Vectors are stored
+// dof-major with a padded stride, so the threads of an element read consecutive words and every
+// K_e entry is a broadcast.  Global vectors are read and written in local order through the
+// staged permutation, so no load depends on another.
+// padded K_e row stride (in floats): 4 mod 32 so that neighbouring elements hit different banks;
+// rows stay 16-byte aligned
+__host__ __device__ constexpr int multi_ke_stride(int D) { return (D == 2 ? 64 : 576) + 4; }
+template <int D>
+__global__ void __launch_bounds__(kMultiThreads, 2) apply_K_multi_kernel(
+    int e, long long ncell, int n, int len, const int* __restrict__ perm, bool idp,
+    const float* __restrict__ u, long long u_rs, int u_cs, float* __restrict__ y, long long y_rs, int y_cs,
+    int nvec, int VB, const float* __restrict__ Kall, int nelc_max, long long u_ext, long long y_ext) {
+  constexpr int NA = 1 << D;
+  constexpr int ND = NA * D;
   constexpr int KES = multi_ke_stride(D);
-  constexpr int CS = multi_c_stride(D);
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int VBp = VB + 1;
   float* us = reinterpret_cast<float*>(sm_raw);        // [n][VBp]
   float* ys = us + (size_t)n * VBp;                     // [n][VBp]
   float* Ke = ys + (size_t)n * VBp;                     // [nelc_max][KES], rows of ND
   Ke = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(Ke) + 15) & ~uintptr_t(15));
-  float* Cs = Ke + (size_t)nelc_max * KES;              // [nelc_max][CS]: per gp the full NI x NI C_hat
-  float* dNs = Cs + (size_t)nelc_max * CS;              // [NA gp][NA][D] shape-function gradients
-  int* perm_s = reinterpret_cast<int*>(dNs + NA * NA * D);   // [n] local -> natural
+  int* perm_s = reinterpret_cast<int*>(Ke + (size_t)nelc_max * KES);   // [n] local -> natural
   const long long col = blockIdx.x;
   const int rhs = (int)(col / ncell);
   const long long cell = col - (long long)rhs * ncell;
   const float* uc = u + rhs * u_rs + cell * u_cs;
   float* yc = y + rhs * y_rs + cell * y_cs;
   const int nel = e * e * (D == 3 ? e : 1);
-  const int cpe = NA * nc;                              // C_hat values per element (upper triangles)
-  const double* chat_cell = chat + cell * (long long)cpe * nel;
+  const float* Kcell = Kall + cell * (long long)nel * ND * ND;
   const int ecount[3] = {e, e, D == 3 ? e : 1};
   for (int li = threadIdx.x; li < n; li += blockDim.x) perm_s[li] = idp ? perm[li] : li;
-  for (int t = threadIdx.x; t < NA * NA * D; t += blockDim.x) {
-    const int gp = t / (NA * D), B = (t / D) % NA, a = t % D;
-    float v = inv_h;
-    for (int k = 0; k < D; ++k) {
-      const int off = (B >> k) & 1;
-      const float tk = (float)gauss_t((gp >> k) & 1);
-      if (k == a) v *= off ? 1.f : -1.f;
-      else v *= off ? tk : 1.f - tk;
-    }
-    dNs[t] = v;
-  }
   __syncthreads();
   for (int v0 = 0; v0 < nvec; v0 += VB) {
     const int vb = min(VB, nvec - v0);
@@ -255,51 +302,15 @@ __global__ void __launch_bounds__(kMultiThreads) apply_K_multi_kernel(
         cnt[k] = (k < D) ? (ecount[k] - par[k] + 1) / 2 : 1;
         nelc *= cnt[k];
       }
-      __syncthreads();   // previous colour's K_e and C_hat no longer read
-      // C_hat of the colour's elements, unpacked to the full symmetric NI x NI matrix per gp
-      for (int t = threadIdx.x; t < nelc * NA * NI * NI; t += blockDim.x) {
-        const int q = t / (NA * NI * NI), r = t - q * (NA * NI * NI);
-        const int gp = r / (NI * NI), I = (r / NI) % NI, J = r % NI;
+      __syncthreads();   // previous colour's K_e no longer read
+      // the colour's element matrices, 16-byte loads
+      for (int t = threadIdx.x; t < nelc * ND * (ND / 4); t += blockDim.x) {
+        const int q = t / (ND * ND / 4), r = t - q * (ND * ND / 4);
         const int qx = q % cnt[0], qy = (q / cnt[0]) % cnt[1], qz = q / (cnt[0] * cnt[1]);
         const int el = (par[0] + 2 * qx) + e * ((par[1] + 2 * qy) + e * (par[2] + 2 * qz));
-        Cs[(size_t)q * CS + r] = (float)chat_cell[(size_t)el * cpe + gp * nc + sym_index(I, J, NI)];
-      }
-      __syncthreads();
-      // element matrices of this colour, one row (A, i) per thread
-      for (int t = threadIdx.x; t < nelc * ND; t += blockDim.x) {
-        const int q = t / ND, row = t - q * ND;
-        const int A = row / D, i = row - A * D;
-        const float* Cq = Cs + (size_t)q * CS;
-        float krow[ND];
-#pragma unroll
-        for (int k = 0; k < ND; ++k) krow[k] = 0.f;
-        for (int gp = 0; gp < NA; ++gp) {
-          const float* dn = dNs + gp * NA * D;
-          const float* Cg = Cq + gp * NI * NI + i * D * NI;   // rows (i, a)
-          float w[D][D];   // w[j][b] = sum_a dN_A[a] C[(i,a),(j,b)]
-#pragma unroll
-          for (int j = 0; j < D; ++j)
-#pragma unroll
-            for (int b = 0; b < D; ++b) {
-              float sacc = 0.f;
-#pragma unroll
-              for (int a = 0; a < D; ++a) sacc += dn[A * D + a] * Cg[a * NI + j * D + b];
-              w[j][b] = sacc;
-            }
-#pragma unroll
-          for (int B = 0; B < NA; ++B)
-#pragma unroll
-            for (int j = 0; j < D; ++j) {
-              float sacc = 0.f;
-#pragma unroll
-              for (int b = 0; b < D; ++b) sacc += w[j][b] * dn[B * D + b];
-              krow[B * D + j] += wq * sacc;
-            }
-        }
-        float* kr = Ke + (size_t)q * KES + row * ND;
-#pragma unroll
-        for (int k = 0; k < ND; k += 4)
-          *reinterpret_cast<float4*>(kr + k) = make_float4(krow[k], krow[k + 1], krow[k + 2], krow[k + 3]);
+        const int row = (4 * r) / ND, k = 4 * r - row * ND;
+        *reinterpret_cast<float4*>(Ke + (size_t)q * KES + row * ND + k) =
+            *reinterpret_cast<const float4*>(Kcell + ((size_t)el * ND + row) * ND + k);
       }
       __syncthreads();
       // apply to every vector of the chunk
@@ -546,20 +557,33 @@ __global__ void __launch_bounds__(256) grouped_gemm_kernel(
 //     matrix columns, so the row-major updates are conflict-free).
 //  3. L y = h(piv), L^T c(piv) = y (column-oriented, lane-parallel), c = 0 off the pivots,
 //     and x = R c.
-// Scratch per warp (doubles): S and L (nrb x (nrb + 1) each), h, y, c, pivot column (nrb
-// each), nrb pivot ints (in nrb doubles), 2 scalars, the v chunk (32), then the two staging
-// tiles (32 x 33 and 32 x 36 values of the basis type), padded to an even count.
+// Scratch per warp (doubles): S (nrb x (nrb + 1)), h, y, c, pivot column (nrb each), nrb pivot
+// ints (in nrb doubles), 2 scalars, two v chunks (2 x 32), then one region shared by the two
+// buffers of the two staging tiles (32 rows x kGramLd values of the basis type each; phase 1)
+// and L (nrb x (nrb + 1); phase 2), padded to an even count.
 constexpr int kMaxRb = 64;
 constexpr int kGramQ = 32;     // basis-vector entries per staged chunk
-constexpr int kGramRld = 33;   // row stride of the staged R rows
-constexpr int kGramKld = 36;   // row stride of the staged, transposed K R chunk (16-byte rows)
+constexpr int kGramLd = 36;    // row stride of a staged tile (16-byte rows, 4-bank row offset)
+__host__ __device__ inline int gram_warp_head(int nrb) {
+  const int fixed = nrb * (nrb + 1) + 5 * nrb + 2 + 2 * kGramQ;
+  return fixed + (fixed & 1);   // the shared region starts 16-byte aligned
+}
 __host__ __device__ inline int gram_warp_doubles(int nrb, int tb_bytes) {
-  const int ld = nrb + 1;
-  const int fixed = 2 * nrb * ld + 5 * nrb + 2 + kGramQ;
-  const int head = fixed + (fixed & 1);   // the staging tiles start 16-byte aligned
-  const int tiles = (kGramQ * (kGramRld + kGramKld) * tb_bytes + 7) / 8;
-  const int tot = head + tiles;
+  const int tiles = (2 * 2 * kGramQ * kGramLd * tb_bytes + 7) / 8;
+  const int lmat = nrb * (nrb + 1);
+  const int tot = gram_warp_head(nrb) + (tiles > lmat ? tiles : lmat);
   return tot + (tot & 1);
+}
+
+// One element (4 or 8 bytes) global -> shared without waiting; zero-filled when !valid.
+template <typename TB>
+__device__ __forceinline__ void cp_async_elem(TB* dst, const TB* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = valid ? (int)sizeof(TB) : 0;
+  if (sizeof(TB) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
 }
 
 __device__ __forceinline__ void load4(const float* p, float (&o)[4]) {
@@ -609,6 +633,7 @@ __device__ void warp_pivoted_gram_solve(double* S, double* Lc, const double* hs,
     }
     __syncwarp();
     for (int i = 0; i < nrb; ++i) {                    // lanes own columns j
+      if ((used >> i) & 1ull) continue;                // pivoted rows are not read again
       const double ci = colv[i];
       for (int j = lane; j < nrb; j += 32) S[i * ld + j] -= ci * colv[j];
     }
@@ -659,24 +684,28 @@ __global__ void gram_warp_kernel(const TB* __restrict__ R, const TB* __restrict_
   if (col >= ncell * nrhs) return;                  // the whole warp leaves together
   const int ld = nrb + 1;
   double* S = gwsm + (size_t)wib * gram_warp_doubles(nrb, (int)sizeof(TB));
-  double* Lc = S + nrb * ld;                        // column a of L at Lc[a * ld + i]
-  double* hs = Lc + nrb * ld;
+  double* hs = S + nrb * ld;
   double* ys = hs + nrb;
   double* cs = ys + nrb;
   double* colv = cs + nrb;
   int* piv = reinterpret_cast<int*>(colv + nrb);
   double* sc = colv + 2 * nrb;
-  double* vq = sc + 2;
-  const int fixed = 2 * nrb * ld + 5 * nrb + 2 + kGramQ;
-  TB* Rt = reinterpret_cast<TB*>(S + fixed + (fixed & 1));   // [32][kGramRld]
-  TB* Kt = Rt + kGramQ * kGramRld;                            // [32 q][kGramKld]
+  double* vq = sc + 2;                              // [2][32]: v chunks
+  double* region = S + gram_warp_head(nrb);
+  TB* Rs = reinterpret_cast<TB*>(region);           // phase 1: [2][32 rows][kGramLd]
+  TB* Ks = Rs + 2 * kGramQ * kGramLd;               // phase 1: [2][32 rows][kGramLd]
+  double* Lc = region;                              // phase 2: column a of L at Lc[a * ld + i]
   const int rhs = (int)(col / ncell);
   const long long cell = col - (long long)rhs * ncell;
   const TB* Rc = R + col * (long long)nrb * nr;
   const TB* KRc = KR + col * (long long)nrb * nr;
   const double* vc = v + rhs * v_rs + cell * v_cs;
+  const int nchunk = (nr + kGramQ - 1) / kGramQ;
 
-  // ---- 1. G (upper blocks) and h
+  // ---- 1. G (upper blocks) and h.  Rows of R and K R are staged chunk by chunk (row-major,
+  // lane = entry q, one async copy per element), the next chunk in flight while this one is
+  // used.  Lane j accumulates column j of the block: per row i and 4 entries one broadcast
+  // 16-byte read of R and 4 FMAs against the lane's own K R values.
   for (int ib = 0; ib < nrb; ib += 32) {
     const int ni = min(32, nrb - ib);
     for (int jb = ib; jb < nrb; jb += 32) {
@@ -686,49 +715,67 @@ __global__ void gram_warp_kernel(const TB* __restrict__ R, const TB* __restrict_
       // accurate as FP64 chunk sums, with no FP64 pipe work in the FP32 path)
       TB gacc[32], gcmp[32];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) { gacc[j] = TB(0); gcmp[j] = TB(0); }
+      for (int i = 0; i < 32; ++i) { gacc[i] = TB(0); gcmp[i] = TB(0); }
       TB hacc = TB(0), hcmp = TB(0);
-      for (int q0 = 0; q0 < nr; q0 += kGramQ) {
-        const int qn = min(kGramQ, nr - q0);
+      auto stage = [&](int buf, int ch) {
+        const int q = ch * kGramQ + lane;
+        const bool in = q < nr;
+        TB* rs = Rs + buf * kGramQ * kGramLd;
+        TB* ks = Ks + buf * kGramQ * kGramLd;
+        for (int r = 0; r < 32; ++r) {
+          cp_async_elem(rs + r * kGramLd + lane, Rc + (size_t)(ib + (r < ni ? r : 0)) * nr + (in ? q : 0),
+                        in && r < ni);
+          cp_async_elem(ks + r * kGramLd + lane, KRc + (size_t)(jb + (r < nj ? r : 0)) * nr + (in ? q : 0),
+                        in && r < nj);
+        }
+        if (diag) vq[buf * kGramQ + lane] = in ? vc[q] : 0.0;
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+      };
+      __syncwarp();
+      stage(0, 0);
+      for (int ch = 0; ch < nchunk; ++ch) {
+        const int buf = ch & 1;
+        if (ch + 1 < nchunk) {
+          stage(buf ^ 1, ch + 1);
+          asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+          asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        }
         __syncwarp();
-        for (int r = 0; r < ni; ++r)
-          Rt[r * kGramRld + lane] = lane < qn ? Rc[(size_t)(ib + r) * nr + q0 + lane] : TB(0);
-        for (int r = 0; r < 32; ++r)
-          Kt[lane * kGramKld + r] = (lane < qn && r < nj) ? KRc[(size_t)(jb + r) * nr + q0 + lane] : TB(0);
-        if (diag) vq[lane] = lane < qn ? vc[q0 + lane] : 0.0;
-        __syncwarp();
-        if (lane < ni) {
-          TB acc[32];
+        const TB* rs = Rs + buf * kGramQ * kGramLd;
+        const TB* ks = Ks + buf * kGramQ * kGramLd;
+        TB acc[32];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) acc[j] = TB(0);
-#pragma unroll 2
-          for (int q = 0; q < kGramQ; ++q) {
-            const TB rq = Rt[lane * kGramRld + q];
+        for (int i = 0; i < 32; ++i) acc[i] = TB(0);
 #pragma unroll
-            for (int j = 0; j < 32; j += 4) {
-              TB k4[4];
-              load4(Kt + q * kGramKld + j, k4);
-              acc[j] += rq * k4[0];
-              acc[j + 1] += rq * k4[1];
-              acc[j + 2] += rq * k4[2];
-              acc[j + 3] += rq * k4[3];
-            }
-          }
+        for (int q = 0; q < kGramQ; q += 4) {
+          TB k4[4];
+          load4(ks + lane * kGramLd + q, k4);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) neumaier_add(gacc[j], gcmp[j], acc[j]);
-          if (diag) {
-            TB hsum = TB(0);
-            for (int q = 0; q < kGramQ; ++q) hsum += Rt[lane * kGramRld + q] * (TB)vq[q];
-            neumaier_add(hacc, hcmp, hsum);
+          for (int i = 0; i < 32; ++i) {
+            TB r4[4];
+            load4(rs + i * kGramLd + q, r4);   // broadcast
+            acc[i] = fma(r4[0], k4[0], acc[i]);
+            acc[i] = fma(r4[1], k4[1], acc[i]);
+            acc[i] = fma(r4[2], k4[2], acc[i]);
+            acc[i] = fma(r4[3], k4[3], acc[i]);
           }
         }
-      }
-      if (lane < ni) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (j < nj && (!diag || j >= lane)) S[(ib + lane) * ld + jb + j] = (double)gacc[j] + (double)gcmp[j];
-        if (diag) hs[ib + lane] = (double)hacc + (double)hcmp;
+        for (int i = 0; i < 32; ++i) neumaier_add(gacc[i], gcmp[i], acc[i]);
+        if (diag) {   // h_i, lane i
+          TB hsum = TB(0);
+          for (int q = 0; q < kGramQ; ++q) hsum += rs[lane * kGramLd + q] * (TB)vq[buf * kGramQ + q];
+          neumaier_add(hacc, hcmp, hsum);
+        }
+        __syncwarp();   // this buffer is refilled by the next stage call
       }
+      if (lane < nj) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if (i < ni && (!diag || i <= lane)) S[(ib + i) * ld + jb + lane] = (double)gacc[i] + (double)gcmp[i];
+      }
+      if (diag && lane < ni) hs[ib + lane] = (double)hacc + (double)hcmp;
     }
   }
   __syncwarp();
@@ -910,50 +957,71 @@ fetidp_status k_apply_K(Ctx& c, CCellVec u, CellVec y, int nvec, int nrhs, bool 
   return FETIDP_OK;
 }
 
+// FP32 element matrices of every cell (mixed path), formed once per setup.
+fetidp_status k_element_matrices_f32(Ctx& c) {
+  const int NA = 1 << c.d, ND = NA * c.d;
+  FD_TRY(dalloc_t(c, &c.Ke_all, (size_t)c.N * c.nelem * ND * ND));
+  ProfScope ps(c, FETIDP_K_SETUP, 0.0, (double)c.N * (c.nsnap * 8.0 + (double)c.nelem * ND * ND * 4.0));
+  const float h = 1.0f / c.e;
+  const float wq = (float)pow(0.5 / c.e, c.d);
+  const long long work = c.N * c.nelem * ND;
+  const int grid = (int)std::min<long long>((work + 255) / 256, 152LL * 64);
+  if (c.d == 2)
+    element_matrices_f32_kernel<2><<<grid, 256, 0, c.stream>>>(c.snap, c.N, c.e, c.nc, wq, 1.0f / h, c.Ke_all);
+  else
+    element_matrices_f32_kernel<3><<<grid, 256, 0, c.stream>>>(c.snap, c.N, c.e, c.nc, wq, 1.0f / h, c.Ke_all);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
 // FP32 variant (local ROM bases of the mixed path): u, y float with the same view strides.
 fetidp_status k_apply_K_f32(Ctx& c, const float* u, long long u_rs, int u_cs, float* y, long long y_rs,
                             int y_cs, int nvec, int nrhs, bool idp, bool r_only, long long ext) {
+  if (!c.Ke_all) {
+    set_error("multi-vector K_s: element matrices not formed");
+    return FETIDP_EINVAL;
+  }
   const int len = r_only ? c.nr : c.n;
   const int NA = 1 << c.d, ND = NA * c.d;
   const int half = (c.e + 1) / 2;
   const int nelc_max = half * half * (c.d == 3 ? half : 1);
   const int kes = c.d == 2 ? multi_ke_stride(2) : multi_ke_stride(3);
-  const int cst = c.d == 2 ? multi_c_stride(2) : multi_c_stride(3);
-  const size_t fixed = (size_t)nelc_max * (kes + cst) * sizeof(float) + 16 + (size_t)NA * NA * c.d * sizeof(float) +
-                       (size_t)c.n * sizeof(int);
-  // vectors per chunk: as many as fit beside one colour's element data (<= 32)
+  const size_t fixed = (size_t)nelc_max * kes * sizeof(float) + 16 + (size_t)c.n * sizeof(int);
+  // vectors per chunk: as many as fit beside one colour's element matrices (<= 16) with two
+  // blocks per SM (one block's global loads and stores overlap the other's arithmetic), else
+  // as many as fit with one
   auto bytes = [&](int vb) { return fixed + 2 * (size_t)c.n * (vb + 1) * sizeof(float); };
-  const size_t budget = 220 * 1024;
-  int VB = (int)std::min<long long>(32, nvec);
+  size_t budget = 110 * 1024;
+  int VB = (int)std::min<long long>(16, nvec);
   while (VB > 1 && bytes(VB) > budget) --VB;
+  if (bytes(VB) > budget) {
+    budget = 220 * 1024;
+    VB = (int)std::min<long long>(32, nvec);
+    while (VB > 1 && bytes(VB) > budget) --VB;
+  }
   if (bytes(VB) > budget) {
     set_error("multi-vector K_s: cell too large for shared memory");
     return FETIDP_EINVAL;
   }
   {
-    // algorithmic work: every element matrix once per chunk (ND rows x NA Gauss points x
-    // (D^3 + ND D) FMA) plus one K_e product (ND^2 FMA) per element and vector
+    // algorithmic work: one K_e product (ND^2 FMA) per element and vector; bytes: the element
+    // matrices once per chunk, the vectors in and out
     const double cols = (double)c.N * nrhs;
     const double chunks = (double)((nvec + VB - 1) / VB);
-    const double form = (double)ND * NA * (c.d * c.d * c.d + ND * c.d);
-    c.prof_pending_flops = 2.0 * cols * c.nelem * (chunks * form + (double)nvec * ND * ND);
-    c.prof_pending_bytes = cols * (chunks * c.nsnap * 8.0 + 2.0 * nvec * len * 4.0);
+    c.prof_pending_flops = 2.0 * cols * c.nelem * (double)nvec * ND * ND;
+    c.prof_pending_bytes = cols * (chunks * c.nelem * (double)ND * ND * 4.0 + 2.0 * nvec * len * 4.0);
   }
   ProfScope ps(c, FETIDP_K_APPLY_K, c.prof_pending_flops, c.prof_pending_bytes);
   const size_t smem = bytes(VB);
-  const float h = 1.0f / c.e;
-  const float wq = (float)pow(0.5 / c.e, c.d);
   const dim3 grid((unsigned)(c.N * nrhs));
   if (c.d == 2) {
     cudaFuncSetAttribute(apply_K_multi_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     apply_K_multi_kernel<2><<<grid, kMultiThreads, smem, c.stream>>>(
-        c.e, c.N, c.n, len, c.perm, idp, u, u_rs, u_cs, y, y_rs, y_cs, nvec, VB, c.snap, c.nc, wq, 1.0f / h,
-        nelc_max, ext, ext);
+        c.e, c.N, c.n, len, c.perm, idp, u, u_rs, u_cs, y, y_rs, y_cs, nvec, VB, c.Ke_all, nelc_max, ext, ext);
   } else {
     cudaFuncSetAttribute(apply_K_multi_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     apply_K_multi_kernel<3><<<grid, kMultiThreads, smem, c.stream>>>(
-        c.e, c.N, c.n, len, c.perm, idp, u, u_rs, u_cs, y, y_rs, y_cs, nvec, VB, c.snap, c.nc, wq, 1.0f / h,
-        nelc_max, ext, ext);
+        c.e, c.N, c.n, len, c.perm, idp, u, u_rs, u_cs, y, y_rs, y_cs, nvec, VB, c.Ke_all, nelc_max, ext, ext);
   }
   FD_CHECK_LAUNCH();
   return FETIDP_OK;

@@ -75,14 +75,15 @@ __global__ void row_update_kernel(double* __restrict__ D, const double* __restri
 }
 
 // Selection of step i of Algorithm 4 (one block): the largest infinity norm of the current
-// residual snapshots; the selected cell is the lowest index within relative `tie` of it.  Stops
-// (and every later kernel of the loop returns at once) when the maximum is not above tol_rb
-// (from the second step on) or is zero.
-__global__ void greedy_select_kernel(const double* __restrict__ inf, long long n, int i, double tol_rb, double tie,
-                                     GreedyState* __restrict__ st) {
+// residual snapshots; the selected cell is the lowest index within relative `tie` of it, and the
+// 2-norm of its residual row is kept for the normalisation.  Stops (and every later kernel of the
+// loop returns at once) when the maximum is not above tol_rb (from the second step on) or is zero.
+__global__ void greedy_select_kernel(const double* __restrict__ inf, long long n, const double* __restrict__ D,
+                                     long long len, int i, double tol_rb, double tie, GreedyState* __restrict__ st) {
   __shared__ double sh[32];
   __shared__ double smx;
   __shared__ long long sidx[32];
+  __shared__ long long sbest;
   if (st->stop) return;                             // uniform across the block
   double mx = 0.0;
   for (long long t = threadIdx.x; t < n; t += blockDim.x) mx = fmax(mx, inf[t]);
@@ -106,19 +107,25 @@ __global__ void greedy_select_kernel(const double* __restrict__ inf, long long n
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) best = sidx[k] < best ? sidx[k] : best;
+    sbest = best;
     st->sigma[i] = (int)best;
     st->count = i + 1;
   }
+  __syncthreads();
+  const double* x = D + sbest * len;
+  double acc = 0.0;
+  for (long long t = threadIdx.x; t < len; t += blockDim.x) acc = fma(x[t], x[t], acc);
+  const double q = bsum(acc, sh);
+  if (threadIdx.x == 0) st->znrm = sqrt(q);
 }
 
-// zeta_i = Delta[sigma_i] / ||Delta[sigma_i]||_2, the squared norm taken from the previous step
-// (grid-stride over the row).
-__global__ void greedy_zeta_kernel(const double* __restrict__ D, const double* __restrict__ sq, long long len, int i,
+// zeta_i = Delta[sigma_i] / ||Delta[sigma_i]||_2 (grid-stride over the row).
+__global__ void greedy_zeta_kernel(const double* __restrict__ D, long long len, int i,
                                    const GreedyState* __restrict__ st, double* __restrict__ zeta) {
   if (st->count <= i) return;
   const int sig = st->sigma[i];
   const double* x = D + (long long)sig * len;
-  const double nrm = sqrt(sq[sig]);
+  const double nrm = st->znrm;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len; t += (long long)gridDim.x * blockDim.x)
     zeta[t] = x[t] / nrm;
 }
@@ -153,35 +160,56 @@ __global__ void greedy_alpha_kernel(const double* __restrict__ T, const double* 
 
 // One greedy step of Algorithm 4 for every row, fused: beta = Delta[row] . zeta,
 // Delta[row] -= beta zeta, and the infinity norm of the updated row (the next step's
-// selection).  One block per row; the second pass re-reads the row from L2.
+// selection).  Two FP64 FMAs per entry: at GB300's FP64 rate (2 FMA/clk/SM) they, not the
+// 16 B of HBM traffic, bound the kernel, so the maximum of |v| runs on the integer pipe (the bit
+// patterns of non-negative doubles order like the values).  One block per row; the second pass
+// re-reads the row from L2.
+__device__ __forceinline__ unsigned long long bmax_u64(unsigned long long v, unsigned long long* sh) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long u = __shfl_down_sync(0xffffffffu, v, o);
+    v = u > v ? u : v;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  unsigned long long r = 0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r = sh[k] > r ? sh[k] : r;
+  __syncthreads();
+  return r;
+}
+
 __global__ void greedy_step_kernel(double* __restrict__ D, const double* __restrict__ zeta, long long len,
                                    double* __restrict__ beta_out, double* __restrict__ inf_out,
-                                   double* __restrict__ sq_out, const GreedyState* __restrict__ st, int i) {
+                                   const GreedyState* __restrict__ st, int i) {
   __shared__ double sh[32];
+  __shared__ unsigned long long shu[32];
   __shared__ double sbeta;
   if (st->count <= i) return;                       // the greedy stopped before step i
   double* x = D + blockIdx.x * len;
-  double acc = 0.0;
-#pragma unroll 4
-  for (long long t = threadIdx.x; t < len; t += blockDim.x) acc += x[t] * zeta[t];
-  const double beta = bsum(acc, sh);
+  const long long stride = blockDim.x;
+  double a0 = 0.0, a1 = 0.0;
+  long long t = threadIdx.x;
+  for (; t + stride < len; t += 2 * stride) {
+    a0 = fma(x[t], zeta[t], a0);
+    a1 = fma(x[t + stride], zeta[t + stride], a1);
+  }
+  if (t < len) a0 = fma(x[t], zeta[t], a0);
+  const double beta = bsum(a0 + a1, sh);
   if (threadIdx.x == 0) sbeta = beta;
   __syncthreads();
   const double bt = sbeta;
-  double mx = 0.0, sq = 0.0;
-#pragma unroll 4
-  for (long long t = threadIdx.x; t < len; t += blockDim.x) {
-    const double v = x[t] - bt * zeta[t];
+  unsigned long long mx = 0;
+  for (t = threadIdx.x; t < len; t += stride) {
+    const double v = fma(-bt, zeta[t], x[t]);
     x[t] = v;
-    mx = fmax(mx, fabs(v));
-    sq += v * v;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+    mx = b > mx ? b : mx;
   }
-  const double m = bmax(mx, sh);
-  const double q = bsum(sq, sh);
+  const unsigned long long m = bmax_u64(mx, shu);
   if (threadIdx.x == 0) {
     beta_out[blockIdx.x] = bt;
-    inf_out[blockIdx.x] = m;
-    sq_out[blockIdx.x] = q;
+    inf_out[blockIdx.x] = __longlong_as_double((long long)m);
   }
 }
 
@@ -322,25 +350,24 @@ fetidp_status k_row_update(Ctx& c, double* D, const double* beta, const double* 
 }
 
 fetidp_status k_greedy_step(Ctx& c, double* D, const double* zeta, long long rows, long long len, double* beta,
-                            double* inf, double* sq, const GreedyState* st, int i) {
+                            double* inf, const GreedyState* st, int i) {
   ProfScope ps(c, FETIDP_K_GREEDY, 4.0 * rows * (double)len, 16.0 * rows * (double)len);
-  greedy_step_kernel<<<(unsigned)rows, kThreads, 0, c.stream>>>(D, zeta, len, beta, inf, sq, st, i);
+  greedy_step_kernel<<<(unsigned)rows, kThreads, 0, c.stream>>>(D, zeta, len, beta, inf, st, i);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }
 
-fetidp_status k_greedy_select(Ctx& c, const double* inf, long long n, int i, double tol_rb, double tie,
-                              GreedyState* st) {
-  ProfScope ps(c, FETIDP_K_GREEDY, 0.0, 8.0 * (double)n);
-  greedy_select_kernel<<<1, 1024, 0, c.stream>>>(inf, n, i, tol_rb, tie, st);
+fetidp_status k_greedy_select(Ctx& c, const double* inf, long long n, const double* D, long long len, int i,
+                              double tol_rb, double tie, GreedyState* st) {
+  ProfScope ps(c, FETIDP_K_GREEDY, 0.0, 8.0 * (double)(n + len));
+  greedy_select_kernel<<<1, 1024, 0, c.stream>>>(inf, n, D, len, i, tol_rb, tie, st);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }
 
-fetidp_status k_greedy_zeta(Ctx& c, const double* D, const double* sq, long long len, int i, const GreedyState* st,
-                            double* zeta) {
+fetidp_status k_greedy_zeta(Ctx& c, const double* D, long long len, int i, const GreedyState* st, double* zeta) {
   ProfScope ps(c, FETIDP_K_GREEDY, 0.0, 16.0 * (double)len);
-  greedy_zeta_kernel<<<gridn(len), kThreads, 0, c.stream>>>(D, sq, len, i, st, zeta);
+  greedy_zeta_kernel<<<gridn(len), kThreads, 0, c.stream>>>(D, len, i, st, zeta);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }

@@ -448,30 +448,27 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
   const int nrb_req = p.n_rb;
   if (nrb_req > kMaxRbGreedy) { set_error("n_rb above 64 is not supported"); return FETIDP_EINVAL; }
   double *Delta = nullptr, *nrm = nullptr, *vals = nullptr, *beta_d = nullptr, *Z = nullptr, *T = nullptr;
-  double* sq = nullptr;   // squared 2-norms of the residual rows
   GreedyState* gst = nullptr;
   FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Delta), sizeof(double) * c.N * c.nsnap));
   FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&nrm), sizeof(double) * c.N));
   FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&vals), sizeof(double) * c.N));
-  FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&sq), sizeof(double) * c.N));
   FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&beta_d), sizeof(double) * c.N * nrb_req));
   FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Z), sizeof(double) * c.nsnap * nrb_req));
   FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&T), sizeof(double) * nrb_req * nrb_req));
   FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&gst), sizeof(GreedyState)));
   auto free_greedy = [&]() {
-    tmp_free(c, Delta); tmp_free(c, nrm); tmp_free(c, vals); tmp_free(c, sq); tmp_free(c, beta_d); tmp_free(c, Z); tmp_free(c, T); tmp_free(c, gst);
+    tmp_free(c, Delta); tmp_free(c, nrm); tmp_free(c, vals); tmp_free(c, beta_d); tmp_free(c, Z); tmp_free(c, T); tmp_free(c, gst);
   };
   FD_CUDA(cudaMemsetAsync(gst, 0, sizeof(GreedyState), c.stream));
   FD_TRY(k_row_reduce(c, c.snap, c.N, c.nsnap, nullptr, 0, nrm));
   FD_TRY(k_row_normalise(c, c.snap, nrm, Delta, c.N, c.nsnap));
   FD_TRY(k_row_reduce(c, Delta, c.N, c.nsnap, nullptr, 1, vals));
-  FD_TRY(k_row_reduce(c, Delta, c.N, c.nsnap, nullptr, 3, sq));   // squared 2-norms
   for (int i = 0; i < nrb_req; ++i) {
     double* zeta = Z + (size_t)i * c.nsnap;
-    FD_TRY(k_greedy_select(c, vals, c.N, i, p.tol_rb, kTieRel, gst));
-    FD_TRY(k_greedy_zeta(c, Delta, sq, c.nsnap, i, gst, zeta));
-    // beta_i = Delta . zeta_i, Delta -= beta_i zeta_i, the next infinity and squared 2-norms, one pass
-    FD_TRY(k_greedy_step(c, Delta, zeta, c.N, c.nsnap, beta_d + (size_t)i * c.N, vals, sq, gst, i));
+    FD_TRY(k_greedy_select(c, vals, c.N, Delta, c.nsnap, i, p.tol_rb, kTieRel, gst));
+    FD_TRY(k_greedy_zeta(c, Delta, c.nsnap, i, gst, zeta));
+    // beta_i = Delta . zeta_i, Delta -= beta_i zeta_i and the next infinity norms, one pass
+    FD_TRY(k_greedy_step(c, Delta, zeta, c.N, c.nsnap, beta_d + (size_t)i * c.N, vals, gst, i));
   }
   GreedyState hst{};
   FD_CUDA(cudaMemcpyAsync(&hst, gst, sizeof(GreedyState), cudaMemcpyDeviceToHost, c.stream));
@@ -592,6 +589,7 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
     FD_TRY(k_rom_combine(c, c.Kinv, (long long)nr * nr, nr, ni, ni, nd, nd, c.delta, c.Fdd_c, false));
     FD_TRY(k_rom_combine(c, c.Sdd, (long long)nd * nd, nd, 0, 0, nd, nd, c.alpha, c.Sdd_c, false));
   } else {          // mixed path: principal operators packed for the tensor cores
+    FD_TRY(k_element_matrices_f32(c));
     const int split = o.tc_split == 3 ? 3 : 1;
     const long long ncols = c.N * c.m;
     FD_TRY(tc_pack_operator(c, c.opKinv, c.Kinv, (long long)nr * nr, nr, 0, 0, nr, nr, nrb, true, split));
@@ -618,6 +616,20 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
       mx = std::max(mx, tc_comb_staging_bytes(*cb, ncols));
     c.tc_bbuf_bytes = mx;
     FD_TRY(dalloc(c, reinterpret_cast<void**>(&c.tc_bbuf), mx));
+    // resident-operator combination (every combined operator with one row tile and K <= 128:
+    // F_dd, S_dd of the inner PCG, and U_rd for small cells): FP32 x and group partials
+    size_t xf = 0, yp = 0;
+    for (const TcComb* cb : {&c.cFdd, &c.cSdd, &c.cUrdT, &c.cUrd})
+      if (tc_comb2_ok(*cb)) {
+        xf = std::max(xf, tc_comb2_xf_bytes(*cb, ncols));
+        yp = std::max(yp, tc_comb2_yp_bytes(*cb, ncols));
+      }
+    if (xf > 0) {
+      c.tc_xf_bytes = xf;
+      c.tc_yp_bytes = yp;
+      FD_TRY(dalloc(c, reinterpret_cast<void**>(&c.tc_xf), xf));
+      FD_TRY(dalloc(c, reinterpret_cast<void**>(&c.tc_yp), yp));
+    }
     if (!c.tc_err) FD_TRY(dalloc(c, reinterpret_cast<void**>(&c.tc_err), sizeof(int)));
     FD_CUDA(cudaMemsetAsync(c.tc_err, 0, sizeof(int), c.stream));
   }

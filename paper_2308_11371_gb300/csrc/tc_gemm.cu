@@ -1024,10 +1024,16 @@ static fetidp_status comb_launch(Ctx& c, const TcComb& op, const TcCombParams& P
   return FETIDP_OK;
 }
 
+static fetidp_status comb2_apply(Ctx& c, const TcComb& op, CCellVec X, const double* coef, void* Y, bool y_f64,
+                                 long long y_rs, int y_cs, double alpha, double beta, long long ncols,
+                                 long long ncell);
+
 fetidp_status tc_comb_apply(Ctx& c, const TcComb& op, CCellVec X, const double* coef0, const double* coef1,
                             void* Y, bool y_f64, long long y_rs, int y_cs, double alpha, double beta, int nrhs,
                             long long ncell) {
   const long long ncols = ncell * nrhs;
+  if (tc_comb2_ok(op) && c.tc_xf && c.tc_yp)
+    return comb2_apply(c, op, X, coef0, Y, y_f64, y_rs, y_cs, alpha, beta, ncols, ncell);
   TcCombParams P{};
   P.A = op.tiles;
   P.B = c.tc_bbuf;
@@ -1053,6 +1059,336 @@ fetidp_status tc_comb_apply(Ctx& c, const TcComb& op, CCellVec X, const double* 
   if (bn == 128) return comb_launch<128>(c, op, P, X, ncols, ncell);
   if (bn == 64) return comb_launch<64>(c, op, P, X, ncols, ncell);
   return comb_launch<32>(c, op, P, X, ncols, ncell);
+}
+
+// ---------------------------------------------------------------- resident-operator combination
+// y_c = sum_k coef_k(c) A_k x_c for operators of one row tile (M <= 128, K <= 128): the Eq. 48 / 49
+// combinations F_dd, S_dd of every inner PCG iteration.  Streaming all N_rb operators through
+// every column tile (tc_comb_kernel) makes each CTA read the whole operator set; here a CTA keeps
+// the operators of kG2 principals resident in shared memory and runs over a range of 64-column
+// tiles instead.  Four warps form the scaled operand z = coef_k(c) x_c (FP32 product, split into
+// BF16 hi + lo) in the SW128 layout, one thread issues the MMAs of all the CTA's principals into
+// one TMEM accumulator per tile, and four warps move each accumulator to an FP32 partial sum of
+// the principal group.  comb2_reduce_kernel adds the groups in a fixed order (deterministic).
+constexpr int kG2 = 2;                       // principals per CTA
+constexpr int kBN2 = 64;                     // columns per tile (MMA N)
+constexpr int Z_TILE2 = kBN2 * TC_BK * 2;    // 8 KB
+constexpr int kComb2Threads = 288;           // epilogue warps 0-3, operand warps 4-7, MMA warp 8
+struct TcComb2Params {
+  const uint8_t* A;       // operator tiles (tc_comb_pack layout, one row tile)
+  const float* xf;        // [ncols][KP] x in FP32, zero past K
+  const double* coef;     // [ncell][nops]
+  float* yp;              // [ngroups][ncols][M] partial sums
+  int nops, kto, nA, nZ, M, KP, n_tiles, tiles_per_cta;
+  long long ncols, ncell;
+  int* err;
+};
+
+__global__ void __launch_bounds__(kComb2Threads, 1) tc_comb2_kernel(TcComb2Params P) {
+  constexpr uint32_t IDESC = make_idesc(TC_BM, kBN2, true);
+  constexpr uint32_t TMEM_COLS = 2 * kBN2;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int g = blockIdx.y;
+  const int k0 = g * kG2, ng = min(kG2, P.nops - k0);
+  const int t_begin = blockIdx.x * P.tiles_per_cta;
+  const int t_end = min(P.n_tiles, t_begin + P.tiles_per_cta);
+  if (t_begin >= t_end || ng <= 0) return;          // uniform: before any barrier or TMEM use
+  const int ntile = t_end - t_begin;
+  const int per_op = P.kto * P.nA;
+  const size_t zslot = (size_t)P.kto * P.nZ * Z_TILE2;
+  uint8_t* sA = smem;                               // [kG2][kto][nA] operator tiles
+  uint8_t* sZ = sA + (size_t)kG2 * per_op * A_TILE; // [2 slots][kto][nZ] operand tiles
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sZ + 2 * zslot);
+  // opFull, zFull[2], zEmpty[2], accFull[2], accEmpty[2], done
+  const uint32_t opFull = smem_u32(bars), zFull = smem_u32(bars + 1), zEmpty = smem_u32(bars + 3);
+  const uint32_t accFull = smem_u32(bars + 5), accEmpty = smem_u32(bars + 7), done = smem_u32(bars + 9);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 10);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    mbar_init(opFull, 1);
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(zFull + 8 * s, 128);
+      mbar_init(zEmpty + 8 * s, 1);
+      mbar_init(accFull + 8 * s, 1);
+      mbar_init(accEmpty + 8 * s, 128);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  if (warp == 8) {
+    if (lane == 0) {
+      mbar_expect_tx(opFull, (uint32_t)(ng * per_op * A_TILE));
+      for (int kk = 0; kk < ng; ++kk)
+        bulk_g2s(smem_u32(sA + (size_t)kk * per_op * A_TILE), P.A + (long long)(k0 + kk) * per_op * A_TILE,
+                 (uint32_t)(per_op * A_TILE), opFull);
+      bool ok = mbar_wait(opFull, 0u, abort_flag);
+      if (!ok) { *abort_flag = 1; atomicExch(P.err, 21); }
+      for (int t = 0; ok && t < ntile; ++t) {
+        const int b = t & 1, use = t >> 1;
+        if (use >= 1 && !mbar_wait(accEmpty + 8 * b, (uint32_t)((use - 1) & 1), abort_flag)) {
+          *abort_flag = 1;
+          atomicExch(P.err, 22);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dst = tmem + (uint32_t)(b * kBN2);
+        bool first = true;
+        for (int kk = 0; ok && kk < ng; ++kk) {
+          const int z = t * ng + kk, s = z & 1, n = z >> 1;
+          if (!mbar_wait(zFull + 8 * s, (uint32_t)(n & 1), abort_flag)) {
+            *abort_flag = 1;
+            atomicExch(P.err, 23);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          for (int kt = 0; kt < P.kto; ++kt)
+            for (int part = 0; part < P.nA; ++part) {
+              const uint64_t ad = sw128_desc(smem_u32(sA + ((size_t)(kk * P.kto + kt) * P.nA + part) * A_TILE));
+              // A hi pairs with z hi (and z lo when split); A lo pairs with z hi
+              const int nzp = (part == 0) ? P.nZ : 1;
+              for (int zp = 0; zp < nzp; ++zp) {
+                const uint64_t bd = sw128_desc(smem_u32(sZ + s * zslot + (size_t)(kt * P.nZ + zp) * Z_TILE2));
+#pragma unroll
+                for (int j = 0; j < TC_BK / 16; ++j) {
+                  tc_mma(dst, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), IDESC, first ? 0u : 1u);
+                  first = false;
+                }
+              }
+            }
+          tc_commit(zEmpty + 8 * s);
+        }
+        if (ok) tc_commit(accFull + 8 * b);
+      }
+      // every MMA issued has completed, and the operator copies have landed, before TMEM and
+      // shared memory are released
+      tc_commit(done);
+      unsigned long long t0 = gtime();
+      while (!mbar_try(done, 0u) && gtime() - t0 < kWaitNs) {
+      }
+      t0 = gtime();
+      while (!mbar_try(opFull, 0u) && gtime() - t0 < kWaitNs) {
+      }
+    }
+  } else if (warp >= 4) {
+    // ---------------- operand warps: thread (column c, k tile kt) forms 64 entries of z
+    const int tt = threadIdx.x - 128, c = tt & 63, kt = tt >> 6;
+    bool ok = true;
+    for (int t = 0; ok && t < ntile; ++t) {
+      const long long col = (long long)(t_begin + t) * kBN2 + c;
+      const bool live = col < P.ncols && kt < P.kto;
+      float xv[TC_BK];
+      if (live) {
+        const float4* src = reinterpret_cast<const float4*>(P.xf + col * P.KP + kt * TC_BK);
+#pragma unroll
+        for (int e4 = 0; e4 < TC_BK / 4; ++e4) {
+          const float4 v = src[e4];
+          xv[4 * e4] = v.x; xv[4 * e4 + 1] = v.y; xv[4 * e4 + 2] = v.z; xv[4 * e4 + 3] = v.w;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < TC_BK; ++e) xv[e] = 0.f;
+      }
+      const long long cell = live ? col % P.ncell : 0;
+      for (int kk = 0; kk < ng; ++kk) {
+        const int z = t * ng + kk, s = z & 1, n = z >> 1;
+        if (n >= 1 && !mbar_wait(zEmpty + 8 * s, (uint32_t)((n - 1) & 1), abort_flag)) {
+          *abort_flag = 1;
+          atomicExch(P.err, 24);
+          ok = false;
+          break;
+        }
+        if (kt < P.kto) {
+          const float cf = live ? (float)P.coef[cell * P.nops + k0 + kk] : 0.f;
+          uint8_t* zh = sZ + s * zslot + (size_t)(kt * P.nZ) * Z_TILE2;
+#pragma unroll
+          for (int ch = 0; ch < TC_BK / 8; ++ch) {
+            alignas(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const float zv = cf * xv[ch * 8 + e];
+              h[e] = __float2bfloat16_rn(zv);
+              l[e] = __float2bfloat16_rn(zv - __bfloat162float(h[e]));
+            }
+            *reinterpret_cast<uint4*>(zh + sw128_offset(c, ch * 8)) = *reinterpret_cast<const uint4*>(h);
+            if (P.nZ > 1)
+              *reinterpret_cast<uint4*>(zh + Z_TILE2 + sw128_offset(c, ch * 8)) = *reinterpret_cast<const uint4*>(l);
+          }
+        }
+        // generic-proxy writes made visible to the tensor core before the slot is signalled
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(zFull + 8 * s);
+      }
+    }
+  } else {
+    // ---------------- epilogue warps 0-3: one row per thread, FP32 partial of the group
+    const int m = warp * 32 + lane;
+    for (int t = 0; t < ntile; ++t) {
+      const int b = t & 1, use = t >> 1;
+      if (!mbar_wait(accFull + 8 * b, (uint32_t)(use & 1), abort_flag)) {
+        *abort_flag = 1;
+        atomicExch(P.err, 25);
+        break;
+      }
+      tc_fence_after();
+#pragma unroll
+      for (int ch = 0; ch < kBN2 / 32; ++ch) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * kBN2 + ch * 32), r);
+        tmem_ld_wait();
+        if (m < P.M) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const long long col = (long long)(t_begin + t) * kBN2 + ch * 32 + j;
+            if (col < P.ncols) P.yp[((long long)g * P.ncols + col) * P.M + m] = __uint_as_float(r[j]);
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(accEmpty + 8 * b);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// x (FP64, view strides) -> [ncols][KP] FP32, zero past K
+__global__ void pack_xf_kernel(const double* __restrict__ X, long long x_rs, int x_cs, int K, int KP,
+                               long long ncols, long long ncell, float* __restrict__ xf) {
+  const long long total = ncols * KP;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long col = t / KP;
+    const int k = (int)(t - col * KP);
+    const int rhs = (int)(col / ncell);
+    const long long cell = col - (long long)rhs * ncell;
+    xf[t] = k < K ? (float)X[rhs * x_rs + cell * x_cs + k] : 0.f;
+  }
+}
+
+// y = alpha * sum_g yp[g] + beta * y, groups added in order
+__global__ void comb2_reduce_kernel(const float* __restrict__ yp, int ngroups, long long ncols, int M,
+                                    long long ncell, void* __restrict__ Y, int y_f64, long long y_rs, int y_cs,
+                                    double alpha, double beta) {
+  const long long total = ncols * M;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int gi = 0; gi < ngroups; ++gi) acc += yp[gi * total + t];
+    const long long col = t / M;
+    const int m = (int)(t - col * M);
+    const int rhs = (int)(col / ncell);
+    const long long off = rhs * y_rs + (col - (long long)rhs * ncell) * y_cs + m;
+    const double v = alpha * (double)acc;
+    if (y_f64) {
+      double* y = reinterpret_cast<double*>(Y) + off;
+      *y = (beta == 0.0) ? v : v + beta * (*y);
+    } else {
+      float* y = reinterpret_cast<float*>(Y) + off;
+      *y = (beta == 0.0) ? (float)v : (float)(v + beta * (double)(*y));
+    }
+  }
+}
+
+bool tc_comb2_ok(const TcComb& op) { return op.m_tiles == 1 && op.kto <= 2 && op.msplit == op.M; }
+
+static size_t comb2_smem_bytes(const TcComb& op) {
+  return (size_t)kG2 * op.kto * op.nA * A_TILE + 2 * (size_t)op.kto * op.nX * Z_TILE2 + 128 + 1024;
+}
+
+size_t tc_comb2_xf_bytes(const TcComb& op, long long ncols) { return (size_t)ncols * op.kto * TC_BK * sizeof(float); }
+size_t tc_comb2_yp_bytes(const TcComb& op, long long ncols) {
+  return (size_t)((op.nops + kG2 - 1) / kG2) * ncols * op.M * sizeof(float);
+}
+
+static fetidp_status comb2_apply(Ctx& c, const TcComb& op, CCellVec X, const double* coef, void* Y, bool y_f64,
+                                 long long y_rs, int y_cs, double alpha, double beta, long long ncols,
+                                 long long ncell) {
+  const int KP = op.kto * TC_BK;
+  if (tc_comb2_xf_bytes(op, ncols) > c.tc_xf_bytes || tc_comb2_yp_bytes(op, ncols) > c.tc_yp_bytes) {
+    set_error("resident-operator combination: staging buffers too small");
+    return FETIDP_EINVAL;
+  }
+  const int ngroups = (op.nops + kG2 - 1) / kG2;
+  const int n_tiles = (int)((ncols + kBN2 - 1) / kBN2);
+  int nchunk = std::max(1, std::min(n_tiles, 148 / ngroups));
+  const int tpc = (n_tiles + nchunk - 1) / nchunk;
+  nchunk = (n_tiles + tpc - 1) / tpc;
+  if (ngroups > 65535) {
+    set_error("resident-operator combination: too many principal groups");
+    return FETIDP_EINVAL;
+  }
+  {
+    ProfScope ps(c, FETIDP_K_MAPS, 0.0, (double)ncols * op.K * 8.0 + (double)ncols * KP * 4.0);
+    pack_xf_kernel<<<gridn(ncols * KP), 256, 0, c.stream>>>(X.p, X.rs, X.cs, op.K, KP, ncols, ncell, c.tc_xf);
+    FD_CHECK_LAUNCH();
+  }
+  {
+    const double flops = 2.0 * op.M * (double)op.K * op.nops * (double)ncols;
+    ProfScope ps(c, FETIDP_K_TC_GEMM, flops,
+                 (double)op.bytes + (double)ncols * KP * 4.0 + (double)ngroups * ncols * op.M * 4.0);
+    TcComb2Params P{};
+    P.A = op.tiles;
+    P.xf = c.tc_xf;
+    P.coef = coef;
+    P.yp = c.tc_yp;
+    P.nops = op.nops;
+    P.kto = op.kto;
+    P.nA = op.nA;
+    P.nZ = op.nX;
+    P.M = op.M;
+    P.KP = KP;
+    P.n_tiles = n_tiles;
+    P.tiles_per_cta = tpc;
+    P.ncols = ncols;
+    P.ncell = ncell;
+    P.err = c.tc_err;
+    const size_t smem = comb2_smem_bytes(op);
+    cudaFuncSetAttribute(tc_comb2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    tc_comb2_kernel<<<dim3((unsigned)nchunk, (unsigned)ngroups, 1), kComb2Threads, smem, c.stream>>>(P);
+    FD_CHECK_LAUNCH();
+  }
+  {
+    ProfScope ps(c, FETIDP_K_MAPS, 0.0, (double)ngroups * ncols * op.M * 4.0 + (double)ncols * op.M * 8.0);
+    comb2_reduce_kernel<<<gridn(ncols * op.M), 256, 0, c.stream>>>(c.tc_yp, ngroups, ncols, op.M, ncell, Y,
+                                                                  y_f64 ? 1 : 0, y_rs, y_cs, alpha, beta);
+    FD_CHECK_LAUNCH();
+  }
+  return FETIDP_OK;
+}
+
+// Reference for the resident-operator kernel: Y[c][m] = sum_k sum_kk bf16(A_k[m][kk]) bf16(f32(coef[c][k]) f32(X[c][kk]))
+__global__ void ref_comb2_kernel(const double* A, const double* X, const double* coef, int M, int K, int N,
+                                 int nops, double* Y) {
+  const long long total = (long long)M * N;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int cidx = (int)(t / M), m = (int)(t - (long long)cidx * M);
+    double acc = 0.0;
+    for (int k = 0; k < nops; ++k) {
+      const float cf = (float)coef[(long long)cidx * nops + k];
+      for (int kk = 0; kk < K; ++kk) {
+        const double a = (double)__bfloat162float(__double2bfloat16(A[((long long)k * M + m) * K + kk]));
+        const float zv = cf * (float)X[(long long)cidx * K + kk];
+        acc += a * (double)__bfloat162float(__float2bfloat16_rn(zv));
+      }
+    }
+    Y[(long long)cidx * M + m] = acc;
+  }
 }
 
 // Reference for the combine self-check: Y[c][m] = sum_k coef_sel[c][k] sum_kk bf16(A_k[m][kk]) bf16(X[c][kk])
@@ -1113,6 +1449,43 @@ fetidp_status tc_comb_selfcheck(Ctx& c, int M0, int M1, int K, int N, int nops, 
     ref = std::max(ref, std::fabs(hr[i]));
   }
   *rel_err = mx / (ref > 0 ? ref : 1.0);
+  if (!tc_comb2_ok(op)) return FETIDP_OK;
+  // one row tile, K <= 128: the resident-operator kernel too, against its own reference (the
+  // scaled operand is rounded to BF16 after the FP32 product)
+  c.tc_xf_bytes = tc_comb2_xf_bytes(op, N);
+  c.tc_yp_bytes = tc_comb2_yp_bytes(op, N);
+  FD_TRY(dalloc(c, reinterpret_cast<void**>(&c.tc_xf), c.tc_xf_bytes));
+  FD_TRY(dalloc(c, reinterpret_cast<void**>(&c.tc_yp), c.tc_yp_bytes));
+  FD_CUDA(cudaMalloc(&A, sizeof(double) * (size_t)nops * M * K));
+  FD_CUDA(cudaMalloc(&X, sizeof(double) * (size_t)N * K));
+  FD_CUDA(cudaMalloc(&C0, sizeof(double) * (size_t)N * nops));
+  FD_CUDA(cudaMalloc(&Yt, sizeof(double) * (size_t)N * M));
+  FD_CUDA(cudaMalloc(&Yr, sizeof(double) * (size_t)N * M));
+  fill_random_kernel<<<gridn((long long)nops * M * K), 256, 0, c.stream>>>(A, (long long)nops * M * K, 21);
+  fill_random_kernel<<<gridn((long long)N * K), 256, 0, c.stream>>>(X, (long long)N * K, 22);
+  fill_random_kernel<<<gridn((long long)N * nops), 256, 0, c.stream>>>(C0, (long long)N * nops, 23);
+  FD_CHECK_LAUNCH();
+  TcComb op2;
+  FD_TRY(tc_comb_pack(c, op2, A, (long long)M * K, K, 0, 0, M, nullptr, 0, 0, 0, 0, 0, K, nops, 1));
+  FD_TRY(tc_comb_apply(c, op2, CCellVec{X, 0, K}, C0, C0, Yt, true, 0, M, 1.0, 0.0, 1, N));
+  ref_comb2_kernel<<<gridn((long long)M * N), 256, 0, c.stream>>>(A, X, C0, M, K, N, nops, Yr);
+  FD_CHECK_LAUNCH();
+  FD_CUDA(cudaMemcpyAsync(ht.data(), Yt, sizeof(double) * ht.size(), cudaMemcpyDeviceToHost, c.stream));
+  FD_CUDA(cudaMemcpyAsync(hr.data(), Yr, sizeof(double) * hr.size(), cudaMemcpyDeviceToHost, c.stream));
+  FD_CUDA(cudaMemcpyAsync(&herr, c.tc_err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  FD_CUDA(cudaStreamSynchronize(c.stream));
+  cudaFree(A); cudaFree(X); cudaFree(C0); cudaFree(Yt); cudaFree(Yr);
+  if (herr != 0) {
+    set_error("resident-operator combine kernel wait timed out (code " + std::to_string(herr) + ")");
+    return FETIDP_ETIMEOUT;
+  }
+  mx = 0.0;
+  ref = 0.0;
+  for (size_t i = 0; i < ht.size(); ++i) {
+    mx = std::max(mx, std::fabs(ht[i] - hr[i]));
+    ref = std::max(ref, std::fabs(hr[i]));
+  }
+  *rel_err = std::max(*rel_err, mx / (ref > 0 ? ref : 1.0));
   return FETIDP_OK;
 }
 

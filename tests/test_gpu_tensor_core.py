@@ -26,6 +26,9 @@ def test_tc_gemm_matches_fp64_on_bf16_inputs(M, K, N):
     (56, 8, 56, 16, 2),         # tiny ragged case
     (570, 0, 120, 4096, 8),     # U_rd: 5 row tiles, 128-wide column tiles
     (120, 8, 570, 300, 5),      # long K resident in shared memory, ragged columns
+    (120, 0, 120, 4096, 32),    # F_dd alone: also the resident-operator kernel (16 groups)
+    (56, 0, 56, 16, 3),         # resident-operator kernel, tiny, a one-principal last group
+    (100, 0, 64, 1000, 5),      # resident-operator kernel, one k tile, ragged columns
 ])
 def test_tc_combine_matches_fp64_on_bf16_inputs(M0, M1, K, N, nops):
     import torch
