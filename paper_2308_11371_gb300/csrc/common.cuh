@@ -51,6 +51,13 @@ struct TraceTableSpec {
   const double* Gj;
   int ncol;
 };
+struct TraceTableSpecDF {   // the same rows from gradient float planes (double-float path)
+  const float* Gih;
+  const float* Gil;
+  const float* Gjh;
+  const float* Gjl;
+  int ncol;
+};
 
 // ---------------------------------------------------------------- debug bounds checks
 // Built with -DFETIDP_BOUNDS_CHECK, the kernels of the mixed local-ROM chain compare their
@@ -362,6 +369,14 @@ fetidp_status k_greedy_step(Ctx& c, double* D, const double* zeta, long long row
                             double* inf, const GreedyState* st, int i);
 fetidp_status k_greedy_select(Ctx& c, const double* inf, long long n, const double* D, long long len, int i,
                               double tol_rb, double tie, GreedyState* st);
+fetidp_status k_greedy_init_df(Ctx& c, const double* A, const double* nrm, long long rows, long long len, float* Dh,
+                               float* Dl, double* inf);
+fetidp_status k_greedy_select_df(Ctx& c, const double* inf, long long n, const float* Dh, const float* Dl,
+                                 long long len, int i, double tol_rb, double tie, GreedyState* st);
+fetidp_status k_greedy_zeta_df(Ctx& c, const float* Dh, const float* Dl, long long len, int i, const GreedyState* st,
+                               float* zh, float* zl, double* zeta);
+fetidp_status k_greedy_step_df(Ctx& c, float* Dh, float* Dl, const float* zh, const float* zl, long long rows,
+                               long long len, double* beta, double* inf, const GreedyState* st, int i);
 fetidp_status k_greedy_zeta(Ctx& c, const double* D, long long len, int i, const GreedyState* st, double* zeta);
 fetidp_status k_greedy_alpha(Ctx& c, const double* Z, const double* nrm, const double* beta, int nrb,
                              const GreedyState* st, double* T, double* alpha);
@@ -372,6 +387,10 @@ fetidp_status k_batched_gemm_nn(Ctx& c, const double* A, long long sa, int lda, 
                                 int ldb, double* C, long long sc, int ldc, int M, int N, int K, int batch);
 fetidp_status k_batched_block_copy(Ctx& c, const double* in, long long si, int ldi, int r0, int c0, double* out,
                                    long long so, int ldo, int M, int N, int batch, bool transpose);
+fetidp_status k_df_gemm_planes(Ctx& c, const float* Ah, const float* Al, int M, int K, const double* X, int x_cs,
+                               long long ncols, double* Y, int y_cs);
+int df_pad_rows(long long rows);
+int df_pad_k(int K);
 fetidp_status k_df_gemm(Ctx& c, const double* A, int lda, int M, int K, const double* X, int x_cs, long long ncols,
                         double* Y, int y_cs);
 fetidp_status k_batched_gemm(Ctx& c, bool ta, bool tb, int M, int N, int K, double alpha, const double* A,

@@ -700,29 +700,30 @@ fetidp_status k_batched_diag_sum(Ctx& c, const double* A, long long stride, int 
   return FETIDP_OK;
 }
 
-fetidp_status k_df_gemm(Ctx& c, const double* A, int lda, int M, int K, const double* X, int x_cs, long long ncols,
-                        double* Y, int y_cs) {
+int df_pad_rows(long long rows) { return (int)((rows + DF_T - 1) / DF_T * DF_T); }
+int df_pad_k(int K) { return (K + DF_K - 1) / DF_K * DF_K; }
+
+// A given as padded planes [df_pad_rows(M)][df_pad_k(K)]; X split here.
+fetidp_status k_df_gemm_planes(Ctx& c, const float* Ah, const float* Al, int M, int K, const double* X, int x_cs,
+                               long long ncols, double* Y, int y_cs) {
   if (M <= 0 || ncols <= 0) return FETIDP_OK;
-  const int Kp = (K + DF_K - 1) / DF_K * DF_K;
-  const long long Mp = (M + DF_T - 1) / DF_T * DF_T, Np = (ncols + DF_T - 1) / DF_T * DF_T;
+  const int Kp = df_pad_k(K);
+  const long long Mp = df_pad_rows(M), Np = (ncols + DF_T - 1) / DF_T * DF_T;
+  if (Np / DF_T > 65535) {
+    set_error("trace contraction: too many cells for one launch");
+    return FETIDP_EINVAL;
+  }
   float* buf = nullptr;
-  FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&buf), sizeof(float) * 2 * (size_t)(Mp + Np) * Kp));
-  float *Ah = buf, *Al = buf + (size_t)Mp * Kp, *Xh = Al + (size_t)Mp * Kp, *Xl = Xh + (size_t)Np * Kp;
+  FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&buf), sizeof(float) * 2 * (size_t)Np * Kp));
+  float *Xh = buf, *Xl = buf + (size_t)Np * Kp;
   fetidp_status st = FETIDP_OK;
   {
-    ProfScope ps(c, FETIDP_K_SETUP, 0.0, 16.0 * ((double)M * K + (double)ncols * K));
-    df_split_kernel<<<grid_for(Mp * Kp, 256), 256, 0, c.stream>>>(A, M, K, lda, Mp, Kp, Ah, Al);
-    count_launch();
+    ProfScope ps(c, FETIDP_K_SETUP, 0.0, 16.0 * (double)ncols * K);
     df_split_kernel<<<grid_for(Np * Kp, 256), 256, 0, c.stream>>>(X, ncols, K, x_cs, Np, Kp, Xh, Xl);
     count_launch();
   }
   {
     ProfScope ps(c, FETIDP_K_TRACES, 2.0 * M * (double)K * ncols, 8.0 * ((double)M * K + (double)ncols * (K + M)));
-    if (Np / DF_T > 65535) {
-      tmp_free(c, buf);
-      set_error("trace contraction: too many cells for one launch");
-      return FETIDP_EINVAL;
-    }
     const dim3 grid((unsigned)(Mp / DF_T), (unsigned)(Np / DF_T));
     df_gemm_kernel<<<grid, 256, 0, c.stream>>>(Ah, Al, Xh, Xl, Kp, Kp / DF_K, M, ncols, Y, y_cs);
     count_launch();
@@ -731,6 +732,23 @@ fetidp_status k_df_gemm(Ctx& c, const double* A, int lda, int M, int K, const do
     set_error(std::string("kernel launch: ") + cudaGetErrorString(cudaGetLastError()));
     st = FETIDP_ECUDA;
   }
+  tmp_free(c, buf);
+  return st;
+}
+
+fetidp_status k_df_gemm(Ctx& c, const double* A, int lda, int M, int K, const double* X, int x_cs, long long ncols,
+                        double* Y, int y_cs) {
+  if (M <= 0 || ncols <= 0) return FETIDP_OK;
+  const int Kp = df_pad_k(K);
+  const long long Mp = df_pad_rows(M);
+  float* buf = nullptr;
+  FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&buf), sizeof(float) * 2 * (size_t)Mp * Kp));
+  {
+    ProfScope ps(c, FETIDP_K_SETUP, 0.0, 16.0 * (double)M * K);
+    df_split_kernel<<<grid_for(Mp * Kp, 256), 256, 0, c.stream>>>(A, M, K, lda, Mp, Kp, buf, buf + (size_t)Mp * Kp);
+    count_launch();
+  }
+  const fetidp_status st = k_df_gemm_planes(c, buf, buf + (size_t)Mp * Kp, M, K, X, x_cs, ncols, Y, y_cs);
   tmp_free(c, buf);
   return st;
 }

@@ -213,6 +213,159 @@ __global__ void greedy_step_kernel(double* __restrict__ D, const double* __restr
   }
 }
 
+// ---------------------------------------------------------------- double-float greedy (mixed path)
+// The residual snapshots Delta are kept as float planes (hi, lo) with |lo| <= ulp(hi) / 2, so a
+// greedy step runs on the FP32 pipe (dot product and update in double-float, ~2^-46 relative)
+// and is bound by its 16 B per entry of HBM traffic instead of GB300's FP64 rate.  |hi + lo|
+// orders like the 64-bit key (bits of |hi|, order-preserving bits of sign(hi) lo), so the
+// infinity norm is an integer maximum.
+__device__ __forceinline__ unsigned long long df_abs_key(float h, float l) {
+  const unsigned hb = __float_as_uint(h);
+  const float ls = (hb >> 31) ? -l : l;                   // lo in the direction of |hi|
+  const unsigned lb = __float_as_uint(ls);
+  const unsigned lkey = (lb >> 31) ? ~lb : (lb | 0x80000000u);
+  return ((unsigned long long)(hb & 0x7fffffffu) << 32) | lkey;
+}
+__device__ __forceinline__ double df_key_value(unsigned long long key) {
+  const float ah = __uint_as_float((unsigned)(key >> 32));
+  const unsigned lkey = (unsigned)key;
+  const unsigned lb = (lkey >> 31) ? (lkey & 0x7fffffffu) : ~lkey;
+  return (double)ah + (double)__uint_as_float(lb);
+}
+__device__ __forceinline__ void df_fma_acc(float ah, float al, float bh, float bl, float& s, float& c) {
+  const float p = ah * bh;
+  const float e = fmaf(ah, bh, -p);
+  c = fmaf(ah, bl, c);
+  c = fmaf(al, bh, c);
+  const float t = s + p;
+  const float bv = t - s;
+  const float err = (s - (t - bv)) + (p - bv);
+  s = t;
+  c = c + (err + e);
+}
+
+// Delta[row] = A[row] / ||A[row]|| as planes, and its infinity norm; one block per row.
+__global__ void greedy_init_df_kernel(const double* __restrict__ A, const double* __restrict__ nrm, long long len,
+                                      float* __restrict__ Dh, float* __restrict__ Dl, double* __restrict__ inf_out) {
+  __shared__ double sinv;
+  __shared__ unsigned long long shu[32];
+  if (threadIdx.x == 0) sinv = 1.0 / nrm[blockIdx.x];
+  __syncthreads();
+  const double inv = sinv;
+  const long long o = (long long)blockIdx.x * len;
+  unsigned long long mx = 0;
+  for (long long t = threadIdx.x; t < len; t += blockDim.x) {
+    const double v = A[o + t] * inv;
+    const float h = (float)v, l = (float)(v - (double)h);
+    Dh[o + t] = h;
+    Dl[o + t] = l;
+    const unsigned long long k = df_abs_key(h, l);
+    mx = k > mx ? k : mx;
+  }
+  const unsigned long long m = bmax_u64(mx, shu);
+  if (threadIdx.x == 0) inf_out[blockIdx.x] = df_key_value(m);
+}
+
+// Selection (as greedy_select_kernel) with the selected row's 2-norm from the planes.
+__global__ void greedy_select_df_kernel(const double* __restrict__ inf, long long n, const float* __restrict__ Dh,
+                                        const float* __restrict__ Dl, long long len, int i, double tol_rb,
+                                        double tie, GreedyState* __restrict__ st) {
+  __shared__ double sh[32];
+  __shared__ double smx;
+  __shared__ long long sidx[32];
+  __shared__ long long sbest;
+  if (st->stop) return;
+  double mx = 0.0;
+  for (long long t = threadIdx.x; t < n; t += blockDim.x) mx = fmax(mx, inf[t]);
+  const double m = bmax(mx, sh);
+  if (threadIdx.x == 0) smx = m;
+  __syncthreads();
+  const double M = smx;
+  if ((i > 0 && M <= tol_rb) || M == 0.0) {
+    if (threadIdx.x == 0) st->stop = 1;
+    return;
+  }
+  long long best = n;
+  for (long long t = threadIdx.x; t < n; t += blockDim.x)
+    if (inf[t] >= M * (1.0 - tie)) { best = t; break; }
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long ob = __shfl_down_sync(0xffffffffu, best, o);
+    best = ob < best ? ob : best;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sidx[w] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) best = sidx[k] < best ? sidx[k] : best;
+    sbest = best;
+    st->sigma[i] = (int)best;
+    st->count = i + 1;
+  }
+  __syncthreads();
+  const long long o = sbest * len;
+  float s = 0.f, c = 0.f;
+  for (long long t = threadIdx.x; t < len; t += blockDim.x) df_fma_acc(Dh[o + t], Dl[o + t], Dh[o + t], Dl[o + t], s, c);
+  const double q = bsum((double)s + (double)c, sh);
+  if (threadIdx.x == 0) st->znrm = sqrt(q);
+}
+
+// zeta_i = Delta[sigma_i] / ||Delta[sigma_i]||_2 as planes and in FP64 (for Eq. 56).
+__global__ void greedy_zeta_df_kernel(const float* __restrict__ Dh, const float* __restrict__ Dl, long long len, int i,
+                                      const GreedyState* __restrict__ st, float* __restrict__ zh,
+                                      float* __restrict__ zl, double* __restrict__ zeta) {
+  if (st->count <= i) return;
+  const long long o = (long long)st->sigma[i] * len;
+  const double nrm = st->znrm;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len; t += (long long)gridDim.x * blockDim.x) {
+    const double v = ((double)Dh[o + t] + (double)Dl[o + t]) / nrm;
+    const float h = (float)v;
+    zh[t] = h;
+    zl[t] = (float)(v - (double)h);
+    zeta[t] = v;
+  }
+}
+
+// One greedy step in double-float: beta = Delta[row] . zeta (per-thread pairs summed in FP64),
+// Delta[row] -= beta zeta (TwoSum on the leading parts, renormalised), next infinity norm.
+__global__ void greedy_step_df_kernel(float* __restrict__ Dh, float* __restrict__ Dl, const float* __restrict__ zh,
+                                      const float* __restrict__ zl, long long len, double* __restrict__ beta_out,
+                                      double* __restrict__ inf_out, const GreedyState* __restrict__ st, int i) {
+  __shared__ double sh[32];
+  __shared__ unsigned long long shu[32];
+  __shared__ double sbeta;
+  if (st->count <= i) return;
+  const long long o = (long long)blockIdx.x * len;
+  float s = 0.f, c = 0.f;
+  for (long long t = threadIdx.x; t < len; t += blockDim.x) df_fma_acc(Dh[o + t], Dl[o + t], zh[t], zl[t], s, c);
+  const double beta = bsum((double)s + (double)c, sh);
+  if (threadIdx.x == 0) sbeta = beta;
+  __syncthreads();
+  const double bt = sbeta;
+  const float bh = (float)bt, bl = (float)(bt - (double)bh);
+  unsigned long long mx = 0;
+  for (long long t = threadIdx.x; t < len; t += blockDim.x) {
+    const float xh = Dh[o + t], xl = Dl[o + t], qh = zh[t], ql = zl[t];
+    const float p = bh * qh;
+    const float e = fmaf(bh, qh, -p);
+    const float cr = fmaf(bh, ql, bl * qh);
+    const float t1 = xh - p;                             // TwoSum(xh, -p)
+    const float bv = t1 - xh;
+    const float err = (xh - (t1 - bv)) + (-p - bv);
+    const float low = (xl - (e + cr)) + err;
+    const float vh = t1 + low;                           // renormalise
+    const float vl = low - (vh - t1);
+    Dh[o + t] = vh;
+    Dl[o + t] = vl;
+    const unsigned long long k = df_abs_key(vh, vl);
+    mx = k > mx ? k : mx;
+  }
+  const unsigned long long m = bmax_u64(mx, shu);
+  if (threadIdx.x == 0) {
+    beta_out[blockIdx.x] = bt;
+    inf_out[blockIdx.x] = df_key_value(m);
+  }
+}
+
 __global__ void scale_copy_kernel(const double* __restrict__ x, const double* __restrict__ s,
                                   double* __restrict__ y, long long len) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len;
@@ -301,6 +454,69 @@ __global__ void trace_tables_kernel(const TraceTableSpec* __restrict__ specs, in
   }
 }
 
+// Double-float variant for the mixed path: the same table rows from gradients kept as float
+// planes (hi = fl(g), lo = fl(g - hi)), every product made exact by an FMA residual plus the two
+// cross products, sums kept as (s, c) pairs with TwoSum (~2^-46 relative per term, all on the
+// FP32 pipe).  Rows are written scaled by wq and split into the padded float planes that the
+// double-float trace GEMM reads: Th/Tl[row * ldt + gp * nc + comp].
+__device__ __forceinline__ void df_acc_prod(float ah, float al, float bh, float bl, float& s, float& c) {
+  const float p = ah * bh;
+  const float e = fmaf(ah, bh, -p);
+  c = fmaf(ah, bl, c);
+  c = fmaf(al, bh, c);
+  const float t = s + p;
+  const float bv = t - s;
+  const float err = (s - (t - bv)) + (p - bv);
+  s = t;
+  c = c + (err + e);
+}
+
+template <int D>
+__global__ void trace_tables_df_kernel(const TraceTableSpecDF* __restrict__ specs, int nqp, double wq,
+                                       float* __restrict__ Th, float* __restrict__ Tl, long long ldt) {
+  constexpr int DD = D * D;
+  constexpr int NC = DD * (DD + 1) / 2;
+  const TraceTableSpecDF sp = specs[blockIdx.y];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nqp; t += gridDim.x * blockDim.x) {
+    float s[NC], cc[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) { s[k] = 0.f; cc[k] = 0.f; }
+    for (int l = 0; l < sp.ncol; ++l) {
+      const long long o = ((long long)l * nqp + t) * DD;
+      float ah[DD], al[DD], bh[DD], bl[DD];
+#pragma unroll
+      for (int I = 0; I < DD; ++I) { ah[I] = sp.Gih[o + I]; al[I] = sp.Gil[o + I]; bh[I] = sp.Gjh[o + I]; bl[I] = sp.Gjl[o + I]; }
+      int k = 0;
+#pragma unroll
+      for (int I = 0; I < DD; ++I)
+#pragma unroll
+        for (int J = I; J < DD; ++J, ++k) {
+          df_acc_prod(ah[I], al[I], bh[J], bl[J], s[k], cc[k]);
+          if (J != I) df_acc_prod(ah[J], al[J], bh[I], bl[I], s[k], cc[k]);
+        }
+    }
+    const long long row = (long long)blockIdx.y * ldt + (long long)t * NC;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      const double v = ((double)s[k] + (double)cc[k]) * wq;
+      const float h = (float)v;
+      Th[row + k] = h;
+      Tl[row + k] = (float)(v - (double)h);
+    }
+  }
+}
+
+// hi / lo float planes of n doubles
+__global__ void split_planes_kernel(const double* __restrict__ x, long long n, float* __restrict__ hi,
+                                    float* __restrict__ lo) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const double v = x[t];
+    const float h = (float)v;
+    hi[t] = h;
+    lo[t] = (float)(v - (double)h);
+  }
+}
+
 // out[cell][r][c] = sum_k coef[cell][k] src[k*kstride + (r0 + r)*ld + c0 + c]
 __global__ void rom_combine_kernel(const double* __restrict__ src, long long kstride, int ld,
                                    int r0, int c0, int rows, int cols,
@@ -357,6 +573,38 @@ fetidp_status k_greedy_step(Ctx& c, double* D, const double* zeta, long long row
   return FETIDP_OK;
 }
 
+fetidp_status k_greedy_init_df(Ctx& c, const double* A, const double* nrm, long long rows, long long len, float* Dh,
+                               float* Dl, double* inf) {
+  ProfScope ps(c, FETIDP_K_GREEDY, 0.0, 16.0 * rows * (double)len);
+  greedy_init_df_kernel<<<(unsigned)rows, kThreads, 0, c.stream>>>(A, nrm, len, Dh, Dl, inf);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_greedy_select_df(Ctx& c, const double* inf, long long n, const float* Dh, const float* Dl,
+                                 long long len, int i, double tol_rb, double tie, GreedyState* st) {
+  ProfScope ps(c, FETIDP_K_GREEDY, 0.0, 8.0 * (double)(n + len));
+  greedy_select_df_kernel<<<1, 1024, 0, c.stream>>>(inf, n, Dh, Dl, len, i, tol_rb, tie, st);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_greedy_zeta_df(Ctx& c, const float* Dh, const float* Dl, long long len, int i, const GreedyState* st,
+                               float* zh, float* zl, double* zeta) {
+  ProfScope ps(c, FETIDP_K_GREEDY, 0.0, 24.0 * (double)len);
+  greedy_zeta_df_kernel<<<gridn(len), kThreads, 0, c.stream>>>(Dh, Dl, len, i, st, zh, zl, zeta);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_greedy_step_df(Ctx& c, float* Dh, float* Dl, const float* zh, const float* zl, long long rows,
+                               long long len, double* beta, double* inf, const GreedyState* st, int i) {
+  ProfScope ps(c, FETIDP_K_GREEDY, 4.0 * rows * (double)len, 16.0 * rows * (double)len);
+  greedy_step_df_kernel<<<(unsigned)rows, kThreads, 0, c.stream>>>(Dh, Dl, zh, zl, len, beta, inf, st, i);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
 fetidp_status k_greedy_select(Ctx& c, const double* inf, long long n, const double* D, long long len, int i,
                               double tol_rb, double tie, GreedyState* st) {
   ProfScope ps(c, FETIDP_K_GREEDY, 0.0, 8.0 * (double)(n + len));
@@ -398,6 +646,27 @@ fetidp_status k_column_gradients(Ctx& c, const double* src, long long kstride, l
   else
     column_gradients_kernel<3><<<gridn(work), kThreads, 0, c.stream>>>(
         c.e, c.n, c.perm + c.n, src, kstride, lstride, len_in, mode, unit_base, nk, ncol, inv_h, out);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_split_planes(Ctx& c, const double* x, long long n, float* hi, float* lo) {
+  ProfScope ps(c, FETIDP_K_SETUP, 0.0, 16.0 * (double)n);
+  split_planes_kernel<<<gridn(n), kThreads, 0, c.stream>>>(x, n, hi, lo);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_trace_tables_df(Ctx& c, const TraceTableSpecDF* specs_dev, int ntab, float* Th, float* Tl,
+                                long long ldt) {
+  const int nqp = c.nelem * c.ngp;
+  const double wq = pow(0.5 / c.e, c.d);
+  ProfScope ps(c, FETIDP_K_SETUP, 0.0, 0.0);
+  dim3 grid((unsigned)((nqp + 127) / 128), (unsigned)ntab);
+  if (c.d == 2)
+    trace_tables_df_kernel<2><<<grid, 128, 0, c.stream>>>(specs_dev, nqp, wq, Th, Tl, ldt);
+  else
+    trace_tables_df_kernel<3><<<grid, 128, 0, c.stream>>>(specs_dev, nqp, wq, Th, Tl, ldt);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }

@@ -27,6 +27,9 @@ fetidp_status k_column_gradients(Ctx& c, const double* src, long long kstride, l
                                  int len_in, int mode, int unit_base, int nk, int ncol, double* out);
 fetidp_status k_trace_tables(Ctx& c, const TraceTableSpec* specs_dev, int ntab, double* T,
                              long long tstride);
+fetidp_status k_split_planes(Ctx& c, const double* x, long long n, float* hi, float* lo);
+fetidp_status k_trace_tables_df(Ctx& c, const TraceTableSpecDF* specs_dev, int ntab, float* Th, float* Tl,
+                                long long ldt);
 fetidp_status k_rom_combine(Ctx& c, const double* src, long long kstride, int ld, int r0, int c0,
                             int rows, int cols, const double* coef, double* out, bool transpose);
 
@@ -461,14 +464,31 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
   };
   FD_CUDA(cudaMemsetAsync(gst, 0, sizeof(GreedyState), c.stream));
   FD_TRY(k_row_reduce(c, c.snap, c.N, c.nsnap, nullptr, 0, nrm));
-  FD_TRY(k_row_normalise(c, c.snap, nrm, Delta, c.N, c.nsnap));
-  FD_TRY(k_row_reduce(c, Delta, c.N, c.nsnap, nullptr, 1, vals));
-  for (int i = 0; i < nrb_req; ++i) {
-    double* zeta = Z + (size_t)i * c.nsnap;
-    FD_TRY(k_greedy_select(c, vals, c.N, Delta, c.nsnap, i, p.tol_rb, kTieRel, gst));
-    FD_TRY(k_greedy_zeta(c, Delta, c.nsnap, i, gst, zeta));
-    // beta_i = Delta . zeta_i, Delta -= beta_i zeta_i and the next infinity norms, one pass
-    FD_TRY(k_greedy_step(c, Delta, zeta, c.N, c.nsnap, beta_d + (size_t)i * c.N, vals, gst, i));
+  if (c.mixed) {
+    // mixed path: Delta as double-float planes (the Delta buffer holds them), steps on the FP32
+    // pipe; zeta also as planes (zp) beside its FP64 row in Z
+    float* Dh = reinterpret_cast<float*>(Delta);
+    float* Dl = Dh + (size_t)c.N * c.nsnap;
+    float* zp = nullptr;
+    FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&zp), sizeof(float) * 2 * (size_t)c.nsnap));
+    FD_TRY(k_greedy_init_df(c, c.snap, nrm, c.N, c.nsnap, Dh, Dl, vals));
+    for (int i = 0; i < nrb_req; ++i) {
+      double* zeta = Z + (size_t)i * c.nsnap;
+      FD_TRY(k_greedy_select_df(c, vals, c.N, Dh, Dl, c.nsnap, i, p.tol_rb, kTieRel, gst));
+      FD_TRY(k_greedy_zeta_df(c, Dh, Dl, c.nsnap, i, gst, zp, zp + c.nsnap, zeta));
+      FD_TRY(k_greedy_step_df(c, Dh, Dl, zp, zp + c.nsnap, c.N, c.nsnap, beta_d + (size_t)i * c.N, vals, gst, i));
+    }
+    tmp_free(c, zp);
+  } else {
+    FD_TRY(k_row_normalise(c, c.snap, nrm, Delta, c.N, c.nsnap));
+    FD_TRY(k_row_reduce(c, Delta, c.N, c.nsnap, nullptr, 1, vals));
+    for (int i = 0; i < nrb_req; ++i) {
+      double* zeta = Z + (size_t)i * c.nsnap;
+      FD_TRY(k_greedy_select(c, vals, c.N, Delta, c.nsnap, i, p.tol_rb, kTieRel, gst));
+      FD_TRY(k_greedy_zeta(c, Delta, c.nsnap, i, gst, zeta));
+      // beta_i = Delta . zeta_i, Delta -= beta_i zeta_i and the next infinity norms, one pass
+      FD_TRY(k_greedy_step(c, Delta, zeta, c.N, c.nsnap, beta_d + (size_t)i * c.N, vals, gst, i));
+    }
   }
   GreedyState hst{};
   FD_CUDA(cudaMemcpyAsync(&hst, gst, sizeof(GreedyState), cudaMemcpyDeviceToHost, c.stream));
@@ -538,7 +558,6 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
     FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Gd), sizeof(double) * (size_t)nrb * nd * nqp * dd));
     FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Gp), sizeof(double) * (size_t)nrb * np * nqp * dd));
     FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Ge), sizeof(double) * (size_t)np * nqp * dd));
-    FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Tab), sizeof(double) * (size_t)ntab * c.nsnap));
     FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Y), sizeof(double) * (size_t)c.N * ntab));
     // columns of U_rd^(k) = K_rr^{-1} T_rd: rows ni+l of the symmetric inverse
     FD_TRY(k_column_gradients(c, c.Kinv + (size_t)ni * nr, (long long)nr * nr, nr, nr, 0, 0, nrb, nd, Gd));
@@ -547,28 +566,55 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
     // unit corner vectors e_p (columns of K_rp)
     FD_TRY(k_column_gradients(c, nullptr, 0, 0, 0, 1, nr, 1, np, Ge));
     const size_t gstride_d = (size_t)nd * nqp * dd, gstride_p = (size_t)np * nqp * dd;
-    std::vector<TraceTableSpec> specs;
-    for (int i = 0; i < nrb; ++i)
-      for (int j = i; j < nrb; ++j) specs.push_back({Gp + i * gstride_p, Gp + j * gstride_p, np});
-    for (int i = 0; i < nrb; ++i) specs.push_back({Gp + i * gstride_p, Ge, np});
-    for (int i = 0; i < nrb; ++i)
-      for (int j = i; j < nrb; ++j) specs.push_back({Gd + i * gstride_d, Gd + j * gstride_d, nd});
-    TraceTableSpec* specs_dev = nullptr;
-    FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&specs_dev), sizeof(TraceTableSpec) * specs.size()));
-    FD_CUDA(cudaMemcpyAsync(specs_dev, specs.data(), sizeof(TraceTableSpec) * specs.size(),
-                            cudaMemcpyHostToDevice, c.stream));
-    FD_TRY(k_trace_tables(c, specs_dev, (int)specs.size(), Tab, c.nsnap));
-    phase("  gradients + trace tables");
     // Both trace systems of Eq. 42 are Gram matrices of nearly dependent principal fields; their
     // pivoted solves decide which directions to drop at 1e-12 of the largest pivot and amplify
     // trace errors by ~1e5, so a BF16-split contraction is far too coarse.  The FP64 path takes
-    // the traces in FP64; the mixed path (whose operators carry ~1e-5 BF16 error) in double-float
-    // arithmetic on the FP32 pipe (~1e-13).
-    if (c.mixed)
-      FD_TRY(k_df_gemm(c, Tab, (int)c.nsnap, ntab, (int)c.nsnap, c.snap, (int)c.nsnap, c.N, Y, ntab));
-    else
+    // the tables and traces in FP64; the mixed path (whose operators carry ~1e-5 BF16 error) in
+    // double-float arithmetic on the FP32 pipe (~1e-13), the tables written straight into the
+    // padded float planes of the trace GEMM.
+    void* specs_dev = nullptr;
+    float* planes = nullptr;
+    if (c.mixed) {
+      const size_t nGd = (size_t)nrb * gstride_d, nGp = (size_t)nrb * gstride_p, nGe = gstride_p;
+      const int Mp = df_pad_rows(ntab), Kp = df_pad_k((int)c.nsnap);
+      const size_t nT = (size_t)Mp * Kp;
+      FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&planes), sizeof(float) * 2 * (nGd + nGp + nGe + nT)));
+      float *Gdh = planes, *Gdl = Gdh + nGd, *Gph = Gdl + nGd, *Gpl = Gph + nGp, *Geh = Gpl + nGp, *Gel = Geh + nGe;
+      float *Th = Gel + nGe, *Tl = Th + nT;
+      FD_TRY(k_split_planes(c, Gd, (long long)nGd, Gdh, Gdl));
+      FD_TRY(k_split_planes(c, Gp, (long long)nGp, Gph, Gpl));
+      FD_TRY(k_split_planes(c, Ge, (long long)nGe, Geh, Gel));
+      std::vector<TraceTableSpecDF> specs;
+      for (int i = 0; i < nrb; ++i)
+        for (int j = i; j < nrb; ++j)
+          specs.push_back({Gph + i * gstride_p, Gpl + i * gstride_p, Gph + j * gstride_p, Gpl + j * gstride_p, np});
+      for (int i = 0; i < nrb; ++i) specs.push_back({Gph + i * gstride_p, Gpl + i * gstride_p, Geh, Gel, np});
+      for (int i = 0; i < nrb; ++i)
+        for (int j = i; j < nrb; ++j)
+          specs.push_back({Gdh + i * gstride_d, Gdl + i * gstride_d, Gdh + j * gstride_d, Gdl + j * gstride_d, nd});
+      FD_TRY(tmp_alloc(c, &specs_dev, sizeof(TraceTableSpecDF) * specs.size()));
+      FD_CUDA(cudaMemcpyAsync(specs_dev, specs.data(), sizeof(TraceTableSpecDF) * specs.size(),
+                              cudaMemcpyHostToDevice, c.stream));
+      FD_CUDA(cudaMemsetAsync(Th, 0, sizeof(float) * 2 * nT, c.stream));   // zero padding
+      FD_TRY(k_trace_tables_df(c, static_cast<const TraceTableSpecDF*>(specs_dev), (int)specs.size(), Th, Tl, Kp));
+      phase("  gradients + trace tables");
+      FD_TRY(k_df_gemm_planes(c, Th, Tl, ntab, (int)c.nsnap, c.snap, (int)c.nsnap, c.N, Y, ntab));
+    } else {
+      FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Tab), sizeof(double) * (size_t)ntab * c.nsnap));
+      std::vector<TraceTableSpec> specs;
+      for (int i = 0; i < nrb; ++i)
+        for (int j = i; j < nrb; ++j) specs.push_back({Gp + i * gstride_p, Gp + j * gstride_p, np});
+      for (int i = 0; i < nrb; ++i) specs.push_back({Gp + i * gstride_p, Ge, np});
+      for (int i = 0; i < nrb; ++i)
+        for (int j = i; j < nrb; ++j) specs.push_back({Gd + i * gstride_d, Gd + j * gstride_d, nd});
+      FD_TRY(tmp_alloc(c, &specs_dev, sizeof(TraceTableSpec) * specs.size()));
+      FD_CUDA(cudaMemcpyAsync(specs_dev, specs.data(), sizeof(TraceTableSpec) * specs.size(),
+                              cudaMemcpyHostToDevice, c.stream));
+      FD_TRY(k_trace_tables(c, static_cast<const TraceTableSpec*>(specs_dev), (int)specs.size(), Tab, c.nsnap));
+      phase("  gradients + trace tables");
       FD_TRY(k_grouped_gemm_n(c, Tab, 0, (int)c.nsnap, ntab, (int)c.nsnap, 1, CCellVec{c.snap, 0, (int)c.nsnap},
                               CellVec{Y, 0, ntab}, nullptr, 1.0, 0.0, c.N, 1, false, 0, FETIDP_K_TRACES));
+    }
     phase("  trace contraction");
     // the two Gram systems of every cell, solved on the device (one warp per system)
     double* dvec_d = nullptr;
@@ -578,7 +624,7 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
     FD_CUDA(cudaMemcpyAsync(dvec_d, dvec.data(), sizeof(double) * nrb, cudaMemcpyHostToDevice, c.stream));
     FD_TRY(k_gram_direct(c, Y, ntab, dvec_d, c.pi, c.delta, kDropRel));
     FD_CUDA(cudaStreamSynchronize(c.stream));
-    tmp_free(c, Gd); tmp_free(c, Gp); tmp_free(c, Ge); tmp_free(c, Tab); tmp_free(c, Y); tmp_free(c, specs_dev); tmp_free(c, dvec_d);
+    tmp_free(c, Gd); tmp_free(c, Gp); tmp_free(c, Ge); tmp_free(c, Tab); tmp_free(c, Y); tmp_free(c, specs_dev); tmp_free(c, planes); tmp_free(c, dvec_d);
   }
   phase("projections pi, delta");
 

@@ -1097,13 +1097,16 @@ __global__ void __launch_bounds__(kComb2Threads, 1) tc_comb2_kernel(TcComb2Param
   const int ntile = t_end - t_begin;
   const int per_op = P.kto * P.nA;
   const size_t zslot = (size_t)P.kto * P.nZ * Z_TILE2;
+  const int xld = P.KP + 4;                         // staged x row stride (floats): 16-byte rows, 4-bank offset
   uint8_t* sA = smem;                               // [kG2][kto][nA] operator tiles
   uint8_t* sZ = sA + (size_t)kG2 * per_op * A_TILE; // [2 slots][kto][nZ] operand tiles
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sZ + 2 * zslot);
-  // opFull, zFull[2], zEmpty[2], accFull[2], accEmpty[2], done
+  float* sX = reinterpret_cast<float*>(sZ + 2 * zslot);   // [kBN2][xld] x of the next tile
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sX + (size_t)kBN2 * xld);
+  // opFull, zFull[2], zEmpty[2], accFull[2], accEmpty[2], done, xsync (operand warps)
   const uint32_t opFull = smem_u32(bars), zFull = smem_u32(bars + 1), zEmpty = smem_u32(bars + 3);
   const uint32_t accFull = smem_u32(bars + 5), accEmpty = smem_u32(bars + 7), done = smem_u32(bars + 9);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 10);
+  const uint32_t xsync = smem_u32(bars + 10);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 11);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -1115,6 +1118,7 @@ __global__ void __launch_bounds__(kComb2Threads, 1) tc_comb2_kernel(TcComb2Param
       mbar_init(accEmpty + 8 * s, 128);
     }
     mbar_init(done, 1);
+    mbar_init(xsync, 128);
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -1183,25 +1187,69 @@ __global__ void __launch_bounds__(kComb2Threads, 1) tc_comb2_kernel(TcComb2Param
       }
     }
   } else if (warp >= 4) {
-    // ---------------- operand warps: thread (column c, k tile kt) forms 64 entries of z
+    // ---------------- operand warps: thread (column c, k tile kt) forms 64 entries of z.  The x of
+    // a tile arrives in shared memory by cp.async while the previous tile is formed; the four
+    // operand warps meet on the xsync mbarrier (bounded waits, so an abort never strands them).
     const int tt = threadIdx.x - 128, c = tt & 63, kt = tt >> 6;
-    bool ok = true;
-    for (int t = 0; ok && t < ntile; ++t) {
+    const int xchunks = kBN2 * P.KP / 4;           // 16-byte chunks of one tile's x
+    auto prefetch = [&](int t) {
+      const long long col0 = (long long)(t_begin + t) * kBN2;
+      for (int q = tt; q < xchunks; q += 128) {
+        const int cc = q / (P.KP / 4), k4 = q - cc * (P.KP / 4);
+        const long long col = col0 + cc;
+        const bool in = col < P.ncols;
+        const float* src = P.xf + (in ? col : 0) * P.KP + 4 * k4;
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(sX + (size_t)cc * xld + 4 * k4);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(in ? 16 : 0)
+                     : "memory");
+      }
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    auto coefs = [&](int t, float (&cf)[kG2]) {
       const long long col = (long long)(t_begin + t) * kBN2 + c;
       const bool live = col < P.ncols && kt < P.kto;
+      const long long cell = live ? col % P.ncell : 0;
+#pragma unroll
+      for (int kk = 0; kk < kG2; ++kk) cf[kk] = (live && kk < ng) ? (float)P.coef[cell * P.nops + k0 + kk] : 0.f;
+    };
+    int nsync = 0;
+    auto osync = [&]() -> bool {                   // all 128 operand threads, bounded
+      mbar_arrive(xsync);
+      const bool r = mbar_wait(xsync, (uint32_t)(nsync & 1), abort_flag);
+      ++nsync;
+      return r;
+    };
+    prefetch(0);
+    float cfs[kG2];
+    coefs(0, cfs);
+    bool ok = true;
+    for (int t = 0; ok && t < ntile; ++t) {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      if (!osync()) {                                       // tile t's x is in shared memory
+        *abort_flag = 1;
+        atomicExch(P.err, 26);
+        break;
+      }
       float xv[TC_BK];
-      if (live) {
-        const float4* src = reinterpret_cast<const float4*>(P.xf + col * P.KP + kt * TC_BK);
+      if (kt < P.kto) {
 #pragma unroll
         for (int e4 = 0; e4 < TC_BK / 4; ++e4) {
-          const float4 v = src[e4];
+          const float4 v = *reinterpret_cast<const float4*>(sX + (size_t)c * xld + kt * TC_BK + 4 * e4);
           xv[4 * e4] = v.x; xv[4 * e4 + 1] = v.y; xv[4 * e4 + 2] = v.z; xv[4 * e4 + 3] = v.w;
         }
-      } else {
-#pragma unroll
-        for (int e = 0; e < TC_BK; ++e) xv[e] = 0.f;
       }
-      const long long cell = live ? col % P.ncell : 0;
+      if (!osync()) {                                       // every thread holds its x
+        *abort_flag = 1;
+        atomicExch(P.err, 26);
+        break;
+      }
+      float cf[kG2];
+#pragma unroll
+      for (int kk = 0; kk < kG2; ++kk) cf[kk] = cfs[kk];
+      if (t + 1 < ntile) {
+        prefetch(t + 1);
+        coefs(t + 1, cfs);
+      }
       for (int kk = 0; kk < ng; ++kk) {
         const int z = t * ng + kk, s = z & 1, n = z >> 1;
         if (n >= 1 && !mbar_wait(zEmpty + 8 * s, (uint32_t)((n - 1) & 1), abort_flag)) {
@@ -1211,14 +1259,13 @@ __global__ void __launch_bounds__(kComb2Threads, 1) tc_comb2_kernel(TcComb2Param
           break;
         }
         if (kt < P.kto) {
-          const float cf = live ? (float)P.coef[cell * P.nops + k0 + kk] : 0.f;
           uint8_t* zh = sZ + s * zslot + (size_t)(kt * P.nZ) * Z_TILE2;
 #pragma unroll
           for (int ch = 0; ch < TC_BK / 8; ++ch) {
             alignas(16) __nv_bfloat16 h[8], l[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
-              const float zv = cf * xv[ch * 8 + e];
+              const float zv = cf[kk] * xv[ch * 8 + e];
               h[e] = __float2bfloat16_rn(zv);
               l[e] = __float2bfloat16_rn(zv - __bfloat162float(h[e]));
             }
@@ -1232,6 +1279,7 @@ __global__ void __launch_bounds__(kComb2Threads, 1) tc_comb2_kernel(TcComb2Param
         mbar_arrive(zFull + 8 * s);
       }
     }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // no copy in flight at exit
   } else {
     // ---------------- epilogue warps 0-3: one row per thread, FP32 partial of the group
     const int m = warp * 32 + lane;
@@ -1304,11 +1352,15 @@ __global__ void comb2_reduce_kernel(const float* __restrict__ yp, int ngroups, l
   }
 }
 
-bool tc_comb2_ok(const TcComb& op) { return op.m_tiles == 1 && op.kto <= 2 && op.msplit == op.M; }
-
 static size_t comb2_smem_bytes(const TcComb& op) {
-  return (size_t)kG2 * op.kto * op.nA * A_TILE + 2 * (size_t)op.kto * op.nX * Z_TILE2 + 128 + 1024;
+  return (size_t)kG2 * op.kto * op.nA * A_TILE + 2 * (size_t)op.kto * op.nX * Z_TILE2 +
+         (size_t)kBN2 * (op.kto * TC_BK + 4) * sizeof(float) + 128 + 1024;
 }
+
+bool tc_comb2_ok(const TcComb& op) {
+  return op.m_tiles == 1 && op.kto <= 2 && op.msplit == op.M && comb2_smem_bytes(op) <= 227 * 1024;
+}
+
 
 size_t tc_comb2_xf_bytes(const TcComb& op, long long ncols) { return (size_t)ncols * op.kto * TC_BK * sizeof(float); }
 size_t tc_comb2_yp_bytes(const TcComb& op, long long ncols) {
