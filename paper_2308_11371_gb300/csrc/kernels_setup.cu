@@ -327,6 +327,25 @@ __global__ void greedy_zeta_df_kernel(const float* __restrict__ Dh, const float*
 
 // One greedy step in double-float: beta = Delta[row] . zeta (per-thread pairs summed in FP64),
 // Delta[row] -= beta zeta (TwoSum on the leading parts, renormalised), next infinity norm.
+// 16-byte loads and stores (4 entries per thread and pass; len is a multiple of 4: 2^d Gauss
+// points per element), so enough bytes are in flight to approach the HBM rate.
+__device__ __forceinline__ void df_axpy_entry(float bh, float bl, float qh, float ql, float& xh, float& xl,
+                                              unsigned long long& mx) {
+  const float p = bh * qh;
+  const float e = fmaf(bh, qh, -p);
+  const float cr = fmaf(bh, ql, bl * qh);
+  const float t1 = xh - p;                             // TwoSum(xh, -p)
+  const float bv = t1 - xh;
+  const float err = (xh - (t1 - bv)) + (-p - bv);
+  const float low = (xl - (e + cr)) + err;
+  const float vh = t1 + low;                           // renormalise
+  const float vl = low - (vh - t1);
+  xh = vh;
+  xl = vl;
+  const unsigned long long k = df_abs_key(vh, vl);
+  mx = k > mx ? k : mx;
+}
+
 __global__ void greedy_step_df_kernel(float* __restrict__ Dh, float* __restrict__ Dl, const float* __restrict__ zh,
                                       const float* __restrict__ zl, long long len, double* __restrict__ beta_out,
                                       double* __restrict__ inf_out, const GreedyState* __restrict__ st, int i) {
@@ -335,29 +354,36 @@ __global__ void greedy_step_df_kernel(float* __restrict__ Dh, float* __restrict_
   __shared__ double sbeta;
   if (st->count <= i) return;
   const long long o = (long long)blockIdx.x * len;
+  const long long n4 = len / 4;
+  const float4* xh4 = reinterpret_cast<const float4*>(Dh + o);
+  const float4* xl4 = reinterpret_cast<const float4*>(Dl + o);
+  const float4* zh4 = reinterpret_cast<const float4*>(zh);
+  const float4* zl4 = reinterpret_cast<const float4*>(zl);
   float s = 0.f, c = 0.f;
-  for (long long t = threadIdx.x; t < len; t += blockDim.x) df_fma_acc(Dh[o + t], Dl[o + t], zh[t], zl[t], s, c);
+  for (long long q = threadIdx.x; q < n4; q += blockDim.x) {
+    const float4 a = xh4[q], b = xl4[q], u = zh4[q], w = zl4[q];
+    df_fma_acc(a.x, b.x, u.x, w.x, s, c);
+    df_fma_acc(a.y, b.y, u.y, w.y, s, c);
+    df_fma_acc(a.z, b.z, u.z, w.z, s, c);
+    df_fma_acc(a.w, b.w, u.w, w.w, s, c);
+  }
   const double beta = bsum((double)s + (double)c, sh);
   if (threadIdx.x == 0) sbeta = beta;
   __syncthreads();
   const double bt = sbeta;
   const float bh = (float)bt, bl = (float)(bt - (double)bh);
   unsigned long long mx = 0;
-  for (long long t = threadIdx.x; t < len; t += blockDim.x) {
-    const float xh = Dh[o + t], xl = Dl[o + t], qh = zh[t], ql = zl[t];
-    const float p = bh * qh;
-    const float e = fmaf(bh, qh, -p);
-    const float cr = fmaf(bh, ql, bl * qh);
-    const float t1 = xh - p;                             // TwoSum(xh, -p)
-    const float bv = t1 - xh;
-    const float err = (xh - (t1 - bv)) + (-p - bv);
-    const float low = (xl - (e + cr)) + err;
-    const float vh = t1 + low;                           // renormalise
-    const float vl = low - (vh - t1);
-    Dh[o + t] = vh;
-    Dl[o + t] = vl;
-    const unsigned long long k = df_abs_key(vh, vl);
-    mx = k > mx ? k : mx;
+  float4* wh4 = reinterpret_cast<float4*>(Dh + o);
+  float4* wl4 = reinterpret_cast<float4*>(Dl + o);
+  for (long long q = threadIdx.x; q < n4; q += blockDim.x) {
+    float4 a = wh4[q], b = wl4[q];
+    const float4 u = zh4[q], w = zl4[q];
+    df_axpy_entry(bh, bl, u.x, w.x, a.x, b.x, mx);
+    df_axpy_entry(bh, bl, u.y, w.y, a.y, b.y, mx);
+    df_axpy_entry(bh, bl, u.z, w.z, a.z, b.z, mx);
+    df_axpy_entry(bh, bl, u.w, w.w, a.w, b.w, mx);
+    wh4[q] = a;
+    wl4[q] = b;
   }
   const unsigned long long m = bmax_u64(mx, shu);
   if (threadIdx.x == 0) {
@@ -599,6 +625,10 @@ fetidp_status k_greedy_zeta_df(Ctx& c, const float* Dh, const float* Dl, long lo
 
 fetidp_status k_greedy_step_df(Ctx& c, float* Dh, float* Dl, const float* zh, const float* zl, long long rows,
                                long long len, double* beta, double* inf, const GreedyState* st, int i) {
+  if (len % 4 != 0) {
+    set_error("double-float greedy: snapshot length not a multiple of 4");
+    return FETIDP_EINVAL;
+  }
   ProfScope ps(c, FETIDP_K_GREEDY, 4.0 * rows * (double)len, 16.0 * rows * (double)len);
   greedy_step_df_kernel<<<(unsigned)rows, kThreads, 0, c.stream>>>(Dh, Dl, zh, zl, len, beta, inf, st, i);
   FD_CHECK_LAUNCH();
