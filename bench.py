@@ -8,7 +8,7 @@ The roofline line is that of the kernel class with the most device time in the s
 (setup included), timed by CUDA events inside the timed steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--precision fp64|mixed|best] [--no-cpu-baseline]
+                  [--precision fp64|mixed|best] [--no-cpu-baseline] [--no-fp64-ref] [--cells C]
 
 N > 1 runs N independent replicas (one per GPU; the solve has no cross-GPU exchange
 on one lattice), value = DOF of all replicas / max-over-ranks time.
