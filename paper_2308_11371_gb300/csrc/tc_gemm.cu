@@ -280,19 +280,29 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(TcParams P) {
   if (!ok) atomicExch(P.err, 3);
   if (ok && !*abort_flag) {
     const int m = mt * TC_BM + warp * 32 + lane;
+    // plain store (alpha = 1, beta = 0): no FP64 arithmetic in the epilogue
+    const bool plain = P.alpha == 1.0 && P.beta == 0.0;
     for (int ch = 0; ch < BN / 32; ++ch) {
       uint32_t r[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 32), r);
       tmem_ld_wait();
       if (m < P.M) {
-        for (int j = 0; j < 32; ++j) {
-          const long long cidx = (long long)nt * BN + ch * 32 + j;
-          if (cidx >= P.ncols) break;
-          const int rhs = (int)(cidx / P.ncell);
-          const long long cell = cidx - (long long)rhs * P.ncell;
+        // (rhs, cell) of the chunk's first column once, then stepped: no division per entry
+        const long long c0 = (long long)nt * BN + ch * 32;
+        int rhs = (int)(c0 / P.ncell);
+        long long cell = c0 - (long long)rhs * P.ncell;
+        for (int j = 0; j < 32; ++j, ++cell) {
+          if (cell == P.ncell) { cell = 0; ++rhs; }
+          if (c0 + j >= P.ncols) break;
           const long long off = bz * P.y_b_stride + rhs * P.y_rs + cell * P.y_cs + m;
           if (!FD_INB(off, P.y_ext, 103)) continue;
-          const double v = P.alpha * (double)__uint_as_float(r[j]);
+          const float a = __uint_as_float(r[j]);
+          if (plain) {
+            if (P.y_f64) reinterpret_cast<double*>(P.Y)[off] = (double)a;
+            else reinterpret_cast<float*>(P.Y)[off] = a;
+            continue;
+          }
+          const double v = P.alpha * (double)a;
           if (P.y_f64) {
             double* y = reinterpret_cast<double*>(P.Y) + off;
             *y = (P.beta == 0.0) ? v : v + P.beta * (*y);
@@ -658,12 +668,15 @@ __global__ void __launch_bounds__(192, 1) tc_comb_kernel(TcCombParams P) {
       mbar_arrive(accEmpty + 8 * b);
     }
     if (ok && !*abort_flag && m < P.M) {
+      // (rhs, cell) of the tile's first column once, then stepped: no division per entry
+      const long long c0 = (long long)nt * BN;
+      int rhs = (int)(c0 / P.ncell);
+      long long cell = c0 - (long long)rhs * P.ncell;
 #pragma unroll
-      for (int j = 0; j < BN; ++j) {
-        const long long cidx = (long long)nt * BN + j;
+      for (int j = 0; j < BN; ++j, ++cell) {
+        if (cell == P.ncell) { cell = 0; ++rhs; }
+        const long long cidx = c0 + j;
         if (cidx < P.ncols) {
-          const int rhs = (int)(cidx / P.ncell);
-          const long long cell = cidx - (long long)rhs * P.ncell;
           const long long off = rhs * P.y_rs + cell * P.y_cs + m;
           const double v = P.alpha * (double)acc[j];
           if (P.y_f64) {
@@ -1333,14 +1346,26 @@ __global__ void comb2_reduce_kernel(const float* __restrict__ yp, int ngroups, l
                                     long long ncell, void* __restrict__ Y, int y_f64, long long y_rs, int y_cs,
                                     double alpha, double beta) {
   const long long total = ncols * M;
+  const bool narrow = total < (1ll << 31) && ncell < (1ll << 31);   // 32-bit index arithmetic
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     float acc = 0.f;
     for (int gi = 0; gi < ngroups; ++gi) acc += yp[gi * total + t];
-    const long long col = t / M;
-    const int m = (int)(t - col * M);
-    const int rhs = (int)(col / ncell);
-    const long long off = rhs * y_rs + (col - (long long)rhs * ncell) * y_cs + m;
+    long long col, cell;
+    int m, rhs;
+    if (narrow) {
+      const unsigned tu = (unsigned)t, cu = tu / (unsigned)M;
+      m = (int)(tu - cu * (unsigned)M);
+      rhs = (int)(cu / (unsigned)ncell);
+      col = cu;
+      cell = (long long)(cu - (unsigned)rhs * (unsigned)ncell);
+    } else {
+      col = t / M;
+      m = (int)(t - col * M);
+      rhs = (int)(col / ncell);
+      cell = col - (long long)rhs * ncell;
+    }
+    const long long off = rhs * y_rs + cell * y_cs + m;
     const double v = alpha * (double)acc;
     if (y_f64) {
       double* y = reinterpret_cast<double*>(Y) + off;
