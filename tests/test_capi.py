@@ -76,3 +76,45 @@ def test_setup_rejects_bad_input_without_gpu(lib):
     h = ctypes.c_void_p()
     st = lib.fetidp_setup(ctypes.byref(s), 2, None, None, ctypes.byref(h))
     assert st == -1 and not h.value
+
+
+@pytest.mark.parametrize("case", ["batch_elems", "batch_loads", "tc_split", "gram_drop", "clamp_axis", "nu",
+                                  "iterations"])
+def test_setup_validation_without_gpu(lib, case):
+    """Every argument and batch-compatibility check of fetidp_setup runs before any CUDA call and
+    answers FETIDP_EINVAL (-1) with no context."""
+    import ctypes
+    from paper_2308_11371_gb300 import workloads as W
+    a = W.config1()
+    probs = [a]
+    opts = {}
+    if case == "batch_elems":
+        probs = [a, W.lattice_2d(3, 3, 6, n_rb=2)]             # 8 vs 6 elements per cell edge
+    elif case == "batch_loads":
+        b = W.config1()
+        b.loads = b.loads + b.loads                              # 1 vs 2 load cases
+        probs = [a, b]
+    elif case == "tc_split":
+        opts = {"precision": binding.FETIDP_MIXED_BF16, "tc_split": 2}
+    elif case == "gram_drop":
+        opts = {"precision": binding.FETIDP_MIXED_BF16, "gram_drop_mixed": 1.5}
+    elif case == "clamp_axis":
+        a.clamp_axis = 2                                         # 2D lattice
+    elif case == "nu":
+        a.nu = 0.5
+    elif case == "iterations":
+        opts = {"max_outer": 0}
+    arr = (binding.Problem * len(probs))()
+    keep = []
+    for i, q in enumerate(probs):
+        s, k = binding.make_problem_struct(q)
+        arr[i] = s
+        keep.append(k)
+    o = binding.default_options(**opts)
+    h = ctypes.c_void_p()
+    st = lib.fetidp_setup(arr, len(probs), ctypes.byref(o), None, ctypes.byref(h))
+    assert st == -1 and not h.value
+    expect = {"batch_elems": "must share", "batch_loads": "must share", "tc_split": "tc_split",
+              "gram_drop": "gram_drop_mixed", "clamp_axis": "clamp axis", "nu": "nu out of range",
+              "iterations": "iteration limits"}[case]
+    assert expect in lib.fetidp_last_error().decode()
