@@ -118,3 +118,43 @@ def test_setup_validation_without_gpu(lib, case):
               "gram_drop": "gram_drop_mixed", "clamp_axis": "clamp axis", "nu": "nu out of range",
               "iterations": "iteration limits"}[case]
     assert expect in lib.fetidp_last_error().decode()
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <string.h>
+#include "fetidp.h"
+int main(void) {
+  fetidp_options o;
+  fetidp_ctx *h = 0;
+  fetidp_default_options(&o);
+  if (o.tol_outer != 1e-8 || o.tc_split != 3 || o.profile_mask != 0u) return 1;
+  if (strcmp(fetidp_status_string(FETIDP_ENOTCONV), "not converged") != 0) return 2;
+  /* no lattice: EINVAL before any CUDA call, no context */
+  if (fetidp_setup(0, 0, &o, 0, &h) != FETIDP_EINVAL || h) return 3;
+  printf("%s\n", fetidp_last_error());
+  return 0;
+}
+"""
+
+
+def test_c_program_links_the_library(lib, tmp_path):
+    """The boundary is a plain C ABI: a C99 program compiled against include/fetidp.h links the
+    library and calls the entry points that need no GPU."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "abi"
+    libdir = os.path.dirname(build.LIB)
+    libname = os.path.basename(build.LIB)[3:-3]          # libfetidp.so -> fetidp
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                        "-L", libdir, f"-l{libname}", f"-Wl,-rpath,{libdir}", "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert run.returncode == 0, (run.returncode, run.stderr)
+    assert "problem" in run.stdout
