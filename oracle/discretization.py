@@ -15,9 +15,13 @@ Readings of silent points (the same ones the CUDA path takes):
   cells s_1 < ... < s_m, rows u(s_j) - u(s_{j+1}); every cell copy of a
   clamped node gets its own row u(s) = 0 and no inter-cell rows.
 * Clamped corner DOF are removed from the global primal vector.
-* Scaling D = 1/m on inter-cell rows (m = cells sharing the node), 1 on
-  Dirichlet rows (Eq. 30 asks for sum_s B_d D B_d^T = I, which chain rows
-  cannot meet exactly at 3D edges).
+* Scaling D of the Dirichlet preconditioner (Eq. 30): the one matrix common
+  to all cells that meets the condition sum_s B_d^(s) B_d^(s)T D = I_L, i.e.
+  D = (B B^T)^{-1}.  B B^T is block diagonal over the rows of one node and
+  component: 1 on a Dirichlet row, 2 on the single row of a node shared by two
+  cells (so D = 1/2 there: every 2D row), and the tridiagonal (2, -1) matrix
+  of the m - 1 chain rows of a node shared by m = 4 cells (3D cell edges),
+  whose inverse is not diagonal.
 """
 from __future__ import annotations
 
@@ -345,7 +349,7 @@ class Lattice:
             for ln in ref.dual_nodes:
                 owners.setdefault(int(self.cell_global_nodes[s, ln]), []).append((s, int(ln)))
         rows = []          # list of [(cell, local dual dof index, sign)]
-        row_m = []         # multiplicity of the node of each row
+        row_block = []     # (global node, component) of each row: the blocks of B B^T
         row_dirichlet = []
         for gn in sorted(owners):
             lst = sorted(owners[gn])
@@ -356,24 +360,35 @@ class Lattice:
                 for (s, ln) in lst:
                     for c in range(d):
                         rows.append([(s, dual_local_index[ln] * d + c, 1.0)])
-                        row_m.append(m); row_dirichlet.append(True)
+                        row_block.append((gn, s, c)); row_dirichlet.append(True)
             else:
                 for j in range(m - 1):
                     (s1, l1), (s2, l2) = lst[j], lst[j + 1]
                     for c in range(d):
                         rows.append([(s1, dual_local_index[l1] * d + c, 1.0),
                                      (s2, dual_local_index[l2] * d + c, -1.0)])
-                        row_m.append(m); row_dirichlet.append(False)
+                        row_block.append((gn, -1, c)); row_dirichlet.append(False)
         self.rows = rows
         self.L = len(rows)
         self.row_dirichlet = np.array(row_dirichlet, bool)
-        self.D = np.where(self.row_dirichlet, 1.0, 1.0 / np.maximum(np.array(row_m, float), 1.0))
         # B_d^(s) as one sparse (L x N*n_d) matrix over the concatenated dual vectors
         ri, ci, vi = [], [], []
         for l, row in enumerate(rows):
             for (s, j, sg) in row:
                 ri.append(l); ci.append(s * ref.n_d + j); vi.append(sg)
         self.Bd = sp.csr_matrix((vi, (ri, ci)), shape=(self.L, self.N * ref.n_d))
+        # D = (sum_s B_d^(s) B_d^(s)T)^{-1} (Eq. 30), inverted block by block
+        BBt = (self.Bd @ self.Bd.T).tocsr()
+        blocks = {}
+        for l, key in enumerate(row_block):
+            blocks.setdefault(key, []).append(l)
+        ri, ci, vi = [], [], []
+        for idx in blocks.values():
+            inv = np.linalg.inv(BBt[idx][:, idx].toarray())
+            for a, la in enumerate(idx):
+                for b, lb in enumerate(idx):
+                    ri.append(la); ci.append(lb); vi.append(inv[a, b])
+        self.Dmat = sp.csr_matrix((vi, (ri, ci)), shape=(self.L, self.L))
         # --- primal DOF (Eq. 18): free lattice vertices, lexicographic, x fastest
         vdims = nc + 1
         vstr = np.cumprod(np.concatenate([[1], vdims[:-1]]))
@@ -396,6 +411,10 @@ class Lattice:
                     ri.append(v * d + c); ci.append(s * ref.n_p + k * d + c)
         # A_p as one (n_P x N*n_p) Boolean matrix over the concatenated corner vectors
         self.Ap = sp.csr_matrix((np.ones(len(ri)), (ri, ci)), shape=(self.n_P, self.N * ref.n_p))
+
+    def apply_D(self, r: np.ndarray) -> np.ndarray:
+        """D r with the Eq. 30 scaling D = (B B^T)^{-1}; r of shape (L,) or (L, k)."""
+        return self.Dmat @ r
 
     # ---- convenience
     def loads_idp(self, s: int) -> np.ndarray:

@@ -140,9 +140,9 @@ class StandardFETIDP:
     def apply_MD(self, r):
         """Dirichlet preconditioner of Eq. 30."""
         lat = self.lat
-        g = (lat.Bd.T @ (lat.D * r)).reshape(lat.N, -1)
+        g = (lat.Bd.T @ lat.apply_D(r)).reshape(lat.N, -1)
         y = np.stack([self.Sdd[s] @ g[s] for s in range(lat.N)])
-        return lat.D * (lat.Bd @ y.ravel())
+        return lat.apply_D(lat.Bd @ y.ravel())
 
     def solve(self, rhs=0, tol=1e-13, max_it=1000, record=None):
         """Eqs. 23-25 by PCG, then Eqs. 21 and 20. Returns (u_R, u_P, lambda, its)."""

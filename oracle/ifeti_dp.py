@@ -68,10 +68,9 @@ class InexactFETIDP:
         return self.scatter(y)
 
     def apply_MD(self, r):
-        """Eq. 49: M_D_ring^{-1} r with D = diag scaling."""
-        D = self.lat.D
-        g = self.gather(D * r)
-        return D * self.scatter(self.rom.Sdd_ring(g))
+        """Eq. 49: M_D_ring^{-1} r with the Eq. 30 scaling D = (B B^T)^{-1}."""
+        g = self.gather(self.lat.apply_D(r))
+        return self.lat.apply_D(self.scatter(self.rom.Sdd_ring(g)))
 
     def U_apply(self, vR, vP):
         """Algorithm 3: U_ring v.  Returns (z, z_P)."""

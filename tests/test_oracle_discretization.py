@@ -203,8 +203,45 @@ def test_jump_operator_brute_force(prob):
                 assert np.array_equal(up[s, k * d:(k + 1) * d], uc[s, ref.dof_p[k * d:(k + 1) * d]])
 
 
-def test_dirichlet_scaling_partition_of_unity_2d():
-    """In 2D every interface row couples exactly two copies, so sum_s B_d D B_d^T = I (Eq. 30)."""
+def test_dirichlet_scaling_2d_is_one_half():
+    """In 2D every inter-cell row couples exactly two copies: D = 1/2 there, 1 on Dirichlet
+    rows, and nothing off the diagonal (Eq. 30)."""
     lat = Lattice(W.config1())
-    M = (lat.Bd @ lat.Bd.T).toarray() @ np.diag(lat.D)
-    assert np.allclose(M, np.eye(lat.L))
+    D = lat.Dmat.toarray()
+    assert np.array_equal(D, np.diag(np.diag(D)))
+    assert np.all(np.diag(D)[lat.row_dirichlet] == 1.0)
+    assert np.all(np.diag(D)[~lat.row_dirichlet] == 0.5)
+
+
+def test_dirichlet_scaling_3d_edge_block():
+    """A node on a cell edge shared by four cells has three chain rows per component; the
+    scaling block there is the inverse of tridiag(-1, 2, -1), [[3,2,1],[2,4,2],[1,2,3]]/4
+    (hand computed), and a face node shared by two cells gets 1/2."""
+    lat = Lattice(W.lattice_3d(2, 2, 2, e=2))
+    d = lat.dim
+    D = lat.Dmat.toarray()
+    # find a four-cell edge node: rows whose D block has three entries per row
+    nnz = (np.abs(D) > 0).sum(1)
+    rows3 = np.nonzero(nnz == 3)[0]
+    assert len(rows3) > 0
+    l0 = rows3[0]
+    blk = np.nonzero(D[l0])[0]
+    assert len(blk) == 3 and np.all(np.diff(blk) == d)     # rows of one node, same component
+    assert np.allclose(D[np.ix_(blk, blk)], np.array([[3, 2, 1], [2, 4, 2], [1, 2, 3]]) / 4.0,
+                       rtol=0, atol=1e-15)
+    rows1 = np.nonzero((nnz == 1) & ~lat.row_dirichlet)[0]
+    assert len(rows1) > 0 and np.all(np.diag(D)[rows1] == 0.5)
+
+
+@pytest.mark.parametrize("prob", [W.config1(), W.lattice_3d(2, 2, 2, e=2, r=0.25)])
+def test_dirichlet_scaling_meets_eq30_and_projects(prob):
+    """sum_s B_d^(s) B_d^(s)T D = I_L (Eq. 30), and P_D = B^T D B is an orthogonal projection
+    (P_D^2 = P_D, symmetric) that leaves every jump B w unchanged."""
+    lat = Lattice(prob)
+    B = lat.Bd.toarray()
+    D = lat.Dmat.toarray()
+    assert np.allclose(B @ B.T @ D, np.eye(lat.L), atol=1e-13)
+    P = B.T @ D @ B
+    assert np.allclose(P @ P, P, atol=1e-13) and np.allclose(P, P.T, atol=1e-15)
+    w = np.random.default_rng(2).standard_normal(B.shape[1])
+    assert np.allclose(B @ (P @ w), B @ w, atol=1e-12)

@@ -216,3 +216,22 @@ def test_hard_mask_gradient_vanishes():
     lat = Lattice(W.config1())
     u = _mono_cells(lat)
     assert np.all(adjoint.gradient(lat, u) == 0.0)
+
+
+@pytest.mark.parametrize("prob", [
+    W.config1(),
+    W.lattice_3d(2, 2, 2, e=2, r=0.25, r_spread=0.05, seed=2),
+    W.lattice_3d(2, 2, 3, e=3, r=0.2, r_spread=0.05, seed=2, mask_kind=W.MASK_BCC_SIGMOID),
+], ids=["cfg1", "bcc_2x2x2_e2", "bcc_sigmoid_2x2x3_e3"])
+def test_dirichlet_preconditioned_spectrum_lower_bound(prob):
+    """FETI-DP theory (Mandel-Tezaur; Klawonn-Widlund): when B_D^T B is a projection, every
+    eigenvalue of M_D^{-1} F is >= 1 (Eqs. 26, 30).  A scaling that violates Eq. 30's condition
+    (e.g. 1/m on the chain rows of a 3D edge) gives eigenvalues near 0.01 on these lattices."""
+    lat = Lattice(prob)
+    fd = feti_dp.StandardFETIDP(lat)
+    F = np.stack([fd.apply_F(e) for e in np.eye(lat.L)], axis=1)
+    MF = np.stack([fd.apply_MD(F[:, j]) for j in range(lat.L)], axis=1)
+    ev = np.linalg.eigvals(MF).real
+    assert ev.min() >= 1.0 - 1e-8
+    if prob.dim == 3:
+        assert ev.max() / ev.min() < 1e3
