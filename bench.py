@@ -1,17 +1,27 @@
 """Benchmark: ROM-based inexact FETI-DP time-to-solution on GB300.
 
-One step = one full time-to-solution of the 64x64-cell 2D lattice (16x16 Q1 cells,
-2.37M DOF, 32 principal cells): fetidp_setup (maps, snapshots, greedy, principal
-factorisations, projections, coarse factorisation) + fetidp_solve to outer relative
-residual 1e-8, through the C ABI.  value = DOF / second (cells x DOF per cell x RHS).
-The roofline line is that of the kernel class with the most device time in the step
-(setup included), timed by CUDA events inside the timed steps.
+One step = one full time-to-solution through the C ABI: fetidp_setup (maps, snapshots, greedy,
+principal factorisations, projections, coarse factorisation) + fetidp_solve to outer relative
+residual 1e-8.  The default workload is the largest single-GPU configuration, the 3D lattice of
+32 x 32 x 16 body-centred-cubic cells (6^3 Q1 elements per cell, 16.86M DOF, 6 load cases) in the
+mixed precision.  value = DOF / second with the paper's convention (cells x DOF per cell x RHS).
+
+Around the timed steps, outside the timed region:
+  * one FP64-path solve of the same workload (the metric's "mixed vs FP64") and the relative
+    displacement difference between the two solutions;
+  * the 64 x 64 2D lattice (config2) as a secondary line;
+  * end to end through fetidp_solve_host (host output buffers, D2H inside the timed region);
+  * the CPU oracle on a bounded sample of the workload (rank 0, N = 1).
+Every kernel class is timed by CUDA events on the context stream inside the timed steps; each
+class's roofline (HBM, tensor or FP32/FP64 pipe) is in "rooflines", the class with the most
+device time in "roofline".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--precision fp64|mixed|best] [--no-cpu-baseline] [--no-fp64-ref] [--cells C]
+                  [--workload cfg5|cfg2|cfg4] [--precision mixed|fp64]
+                  [--no-cpu-baseline] [--no-fp64-ref] [--no-secondary] [--e2e-steps E]
 
-N > 1 runs N independent replicas (one per GPU; the solve has no cross-GPU exchange
-on one lattice), value = DOF of all replicas / max-over-ranks time.
+N > 1 runs N independent replicas (one per GPU; one lattice has no cross-GPU exchange here),
+value = DOF of all replicas / max-over-ranks time.
 """
 from __future__ import annotations
 
@@ -23,7 +33,6 @@ import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -32,13 +41,21 @@ sys.path.insert(0, ROOT)
 METRIC = ("FETI-DP time-to-solution (rel. residual 1e-8) & DOF/s, mixed vs FP64 GPU; "
           "HBM/tensor %")
 UNIT = "DOF/s"
-# FP64 FMA issue: 2 DFMA / clk / SM on GB300 (measured 1.21 TFLOP/s at 2.0 GHz with an
-# FMA-chain probe) -> 152 SMs x 2 x 2 flop x 2.07 GHz max clock.
+# Derived pipe peaks (no measured FP64/FP32 figure in MEASURED_PEAKS.json): GB300 issues 2 DFMA and
+# 128 FFMA per clock per SM; 152 SMs at the 2.07 GHz maximum clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# One double-float multiply-add term of the mixed Eq. 42 trace GEMM issues 12 FP32 instructions
-# (exact product by FMA residual, two cross products, TwoSum, low-part accumulation).
+# One double-float multiply-add term of the mixed Eq. 42 trace GEMM issues 12 FP32 instructions.
 DF_OPS_PER_TERM = 12
+
+# Principal cells: the hard strut mask with a graded radius needs more principal cells than the
+# configured ones for the outer solver to converge (the paper advises growing the reduced basis
+# until the outer iterations are few, Sec. 5.1.2): 8 -> 32 in 2D, 16 -> 64 in 3D.
+WORKLOADS = {
+    "cfg5": {"label": "3d_32x32x16_bcc_e6_6rhs", "n_rb": 64, "opts": {"restart": 10, "max_outer": 60}},
+    "cfg2": {"label": "2d_64x64_e16", "n_rb": 32, "opts": {}},
+    "cfg4": {"label": "3d_24x24x12_bcc_sigmoid_e6", "n_rb": 16, "opts": {"restart": 10, "max_outer": 60}},
+}
 
 
 def measured_peaks():
@@ -50,28 +67,47 @@ def measured_peaks():
                 "_fallback": True}
 
 
-def sample_problem(nx):
-    """nx x nx sub-lattice of the 64x64 workload: same cell, mask, radius law and bend."""
-    import numpy as np
+def workload_problem(name):
     from paper_2308_11371_gb300 import workloads as W
-    full = W.config2(n_rb=W.CONFIG2_SOLVE_N_RB)
-    q = W.lattice_2d(nx, nx, 16, a=full.map_params[0], r=0.1, n_rb=full.n_rb, r_grade=0.05,
-                     name=f"2d_{nx}x{nx}_e16_sample")
-    q.map_params = (full.map_params[0], 64.0)
-    xc = np.arange(nx) + 0.5
-    q.r_cell = np.tile(0.1 + 0.05 * np.sin(2 * np.pi * xc / 64.0), nx)
+    w = WORKLOADS[name]
+    prob = {"cfg5": W.config5, "cfg2": W.config2, "cfg4": W.config4}[name]()
+    prob.n_rb = w["n_rb"]
+    return prob
+
+
+def sample_problem(name, cells):
+    """The cells [0, cells) of the workload lattice (same cell, mask, radii, macro map and load
+    kinds): a bounded sample for the CPU oracle."""
+    import numpy as np
+    full = workload_problem(name)
+    nx, ny, nz = cells
+    fx, fy, fz = full.cells
+    idx = np.arange(fz)[:nz, None, None] * fy * fx + np.arange(fy)[None, :ny, None] * fx + \
+        np.arange(fx)[None, None, :nx]
+    q = type(full)(**{k: getattr(full, k) for k in full.__dataclass_fields__})
+    q.cells = (nx, ny, nz)
+    q.r_cell = np.asarray(full.r_cell)[idx.ravel()]
+    q.n_rb = min(full.n_rb, nx * ny * nz)
+    q.name = f"{full.name}_sample_{nx}x{ny}x{nz}"
+    q.extra = {}
     return q
 
 
-def oracle_time_to_solution(nx):
-    """Oracle (plain numpy/scipy FP64) inexact FETI-DP on a sub-lattice; returns (DOF/s, s, dof)."""
+SAMPLES = {"cfg5": {"cpu": (4, 4, 2), "reference": (2, 2, 2)},
+           "cfg4": {"cpu": (4, 4, 2), "reference": (2, 2, 2)},
+           "cfg2": {"cpu": (16, 16, 1), "reference": (12, 12, 1)}}
+
+
+def oracle_time_to_solution(name, cells):
+    """Oracle (plain numpy/scipy FP64) inexact FETI-DP on a sample; returns (DOF/s, s, dof)."""
     from oracle import ifeti_dp
     from oracle.discretization import Lattice
-    q = sample_problem(nx)
+    q = sample_problem(name, cells)
     t0 = time.perf_counter()
     lat = Lattice(q)
     s = ifeti_dp.InexactFETIDP(lat)
-    s.solve(tol=1e-8)
+    for r in range(q.n_rhs):
+        s.solve(rhs=r, tol=1e-8)
     dt = time.perf_counter() - t0
     dof = q.n_cells * lat.ref.n_dof * q.n_rhs
     return dof / dt, dt, dof
@@ -159,7 +195,9 @@ def barrier(world):
 # Source files that hold the kernels (and their launch code) of each class: a committed ncu
 # traffic figure stays valid while these files are unchanged.
 CLASS_SOURCES = {"tc_gemm": ["tc_gemm.cu"], "sweep": ["dense.cu"], "traces": ["dense.cu"],
-                 "greedy": ["kernels_setup.cu"]}
+                 "greedy": ["kernels_setup.cu"], "cell_gemv": ["kernels_cell.cu"],
+                 "apply_K": ["kernels_cell.cu"], "maps": ["kernels_maps.cu"], "coarse": ["coarse.cu"],
+                 "gram": ["kernels_cell.cu"], "vector": ["kernels_maps.cu"]}
 
 
 def kernel_source_hash(files=None):
@@ -172,7 +210,7 @@ def kernel_source_hash(files=None):
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_class, precision):
+def ncu_traffic(kernel_class, precision, workload=None):
     """DRAM bytes per launch from the committed ncu summary, if taken on the current sources."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
@@ -180,37 +218,78 @@ def ncu_traffic(kernel_class, precision):
             data = json.load(f)
     except OSError:
         return None
-    ent = data.get(f"{kernel_class}:{precision}")
+    ent = data.get(f"{kernel_class}:{precision}" + (f":{workload}" if workload else ""))
+    if ent is None and workload:
+        ent = data.get(f"{kernel_class}:{precision}")
     if not ent or ent.get("source_hash") != kernel_source_hash(CLASS_SOURCES.get(kernel_class)):
         return None
     return ent.get("dram_bytes_per_launch")
 
 
+# The bound of each kernel class in each precision: "hbm" (algorithmic bytes / time against the
+# measured copy bandwidth), "tensor" (algorithmic flops against the measured BF16 peak), "fp32" /
+# "fp64" (algorithmic flops against the derived pipe peak), "df" (double-float FP64-equivalent
+# flops against the FP32 issue rate / 12).
+CLASS_BOUND = {
+    "mixed": {"maps": "hbm", "vector": "hbm", "cell_gemv": "hbm", "coarse": "hbm", "apply_K": "fp32",
+              "tc_gemm": "tensor", "gram": "fp32", "grouped_gemm": "fp64", "sweep": "fp64",
+              "traces": "df", "greedy": "hbm", "setup": "hbm"},
+    "fp64": {"maps": "hbm", "vector": "hbm", "cell_gemv": "hbm", "coarse": "hbm", "apply_K": "fp64",
+             "tc_gemm": "tensor", "gram": "fp64", "grouped_gemm": "fp64", "sweep": "fp64",
+             "traces": "fp64", "greedy": "fp64", "setup": "hbm"},
+}
+
+
+def class_roofline(name, p, prec, peaks, step_ms=None):
+    """Roofline entry of one kernel class from its summed event time, flops and bytes."""
+    bound = CLASS_BOUND[prec].get(name, "hbm")
+    s = p["ms"] / 1e3
+    if s <= 0 or p["launches"] == 0:
+        return None
+    if bound == "hbm":
+        ach, peak, unit, src = p["bytes"] / s / 1e9, peaks["hbm_gbs"], "GB/s", "measured HBM copy"
+    elif bound == "tensor":
+        ach, peak, unit, src = (p["flops"] / s / 1e12, peaks["bf16_tflops_sustained"], "TFLOP/s",
+                                "measured BF16 sustained (cuBLAS)")
+    elif bound == "fp32":
+        ach, peak, unit, src = p["flops"] / s / 1e12, FP32_PEAK_TFLOPS, "TFLOP/s", "derived FP32 FFMA rate"
+    elif bound == "df":
+        ach, peak, unit, src = (p["flops"] / s / 1e12, FP32_PEAK_TFLOPS / DF_OPS_PER_TERM,
+                                "TFLOP/s (FP64-equivalent)", "derived FP32 issue rate / 12 per term")
+    else:
+        ach, peak, unit, src = p["flops"] / s / 1e12, FP64_PEAK_TFLOPS, "TFLOP/s", "derived FP64 DFMA rate"
+    e = {"bound": "alu" if bound in ("fp32", "fp64", "df") else bound, "achieved": ach, "peak": peak,
+         "unit": unit, "frac": ach / peak, "peak_source": src, "launches": p["launches"],
+         "avg_launch_ms": p["ms"] / p["launches"], "total_ms": p["ms"]}
+    if step_ms:
+        e["share_of_step"] = p["ms"] / step_ms
+    return e
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    import os as _os
-    nx = 12
+    cells = SAMPLES[args.workload]["reference"]
     for _ in range(args.warmup):
-        oracle_time_to_solution(nx)
-    vals, times = [], []
+        oracle_time_to_solution(args.workload, cells)
+    times = []
+    dof = 0
     for _ in range(args.steps):
-        v, dt, dof = oracle_time_to_solution(nx)
-        vals.append(v)
+        v, dt, dof = oracle_time_to_solution(args.workload, cells)
         times.append(dt)
     total = sum(times)
     value = args.steps * dof / total
-    cores = _os.cpu_count()
+    cores = os.cpu_count()
+    sample = (f"{cells[0]}x{cells[1]}x{cells[2]}-cell corner of the {WORKLOADS[args.workload]['label']} "
+              "lattice (same cell, mask, radii, macro map, load kinds), oracle inexact FETI-DP setup + "
+              "solve to 1e-8 for every load case")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "2d_64x64_e16", "sample": f"{nx}x{nx}-cell sub-lattice of the "
-                   "64x64 workload (same cell, mask, radius law, bend), oracle inexact FETI-DP "
-                   "setup + solve to 1e-8", "dof_per_step": dof},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{nx}x{nx} cells x 578 DOF"},
+        "config": {"workload": WORKLOADS[args.workload]["label"], "sample": sample, "dof_per_step": dof},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -223,13 +302,14 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="best", choices=["fp64", "mixed", "best"])
+    ap.add_argument("--workload", default="cfg5", choices=list(WORKLOADS))
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-ref", action="store_true",
-                    help="skip the one FP64-path step timed for the mixed-vs-FP64 comparison")
-    ap.add_argument("--cpu-sample", type=int, default=16)
-    ap.add_argument("--cells", type=int, default=64,
-                    help="cells per side (64 = the benchmark workload; smaller for profiling)")
+                    help="skip the FP64-path solve of the mixed-vs-FP64 comparison")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the 2D config2 secondary line")
+    ap.add_argument("--e2e-steps", type=int, default=3,
+                    help="end-to-end steps through fetidp_solve_host (each one time-to-solution)")
     args = ap.parse_args()
     rank, world, local = dist_init()
     if args.impl == "reference":
@@ -237,49 +317,40 @@ def main():
 
     import numpy as np
     import torch
-    from paper_2308_11371_gb300 import binding, workloads as W
+    from paper_2308_11371_gb300 import binding
 
     torch.cuda.set_device(local)
     binding.load()
-    prob = W.config2(n_rb=W.CONFIG2_SOLVE_N_RB)
-    if args.cells != 64:   # same cell / mask / radius law / bend, fewer cells (profiling runs)
-        prob = sample_problem(args.cells)
-    prec_name = {"fp64": "fp64", "mixed": "mixed", "best": "mixed"}[args.precision]
-    precision = binding.FETIDP_FP64 if prec_name == "fp64" else binding.FETIDP_MIXED_BF16
+    wl = WORKLOADS[args.workload]
+    prob = workload_problem(args.workload)
+    opts = dict(wl["opts"])
+    prec = args.precision
+    precision = binding.FETIDP_FP64 if prec == "fp64" else binding.FETIDP_MIXED_BF16
     stream = torch.cuda.current_stream()
-    dof = prob.n_cells * 578 * prob.n_rhs
+    n_dof = (prob.elems + 1) ** prob.dim * prob.dim
+    dof = prob.n_cells * n_dof * prob.n_rhs
+    peaks = measured_peaks()
 
-    def one_step(profile=None):
-        # profile: kernel classes timed from the start of setup (None: no events)
-        opts = {"profile": profile} if profile is not None else {}
-        s = binding.Solver(prob, precision=precision, **opts)
+    def one_step(precision=precision, keep=False, profile=True):
+        s = binding.Solver(prob, precision=precision, profile=list(binding.KCLASS) if profile else None, **opts)
         u, lam, info = s.solve()
-        prof = s.profile_read() if profile is not None else None
+        prof = s.profile_read() if profile else None
+        if keep:
+            return s, u, info, prof
         s.close()
-        return info, prof
+        del u, lam
+        return None, None, info, prof
 
-    # the plain FP64 path on the same workload, for the mixed-vs-FP64 comparison (one step)
-    fp64_ref = None
-    if prec_name == "mixed" and not args.no_fp64_ref:
-        s64 = binding.Solver(prob, precision=binding.FETIDP_FP64)
-        s64.close()
-        torch.cuda.synchronize()
-        f0 = time.perf_counter()
-        s64 = binding.Solver(prob, precision=binding.FETIDP_FP64)
-        _, _, info64 = s64.solve()
-        s64.close()
-        torch.cuda.synchronize()
-        fp64_ref = {"ms": 1e3 * (time.perf_counter() - f0), "outer_its": info64["outer_its"],
-                    "inner_its_total": info64["inner_its_total"],
-                    "t_setup_ms": 1e3 * info64["t_setup_s"], "t_solve_ms": 1e3 * info64["t_solve_s"]}
-
-    # warm-up; the first step also profiles every kernel class to find the dominant one
-    info0, prof0 = one_step(profile=list(binding.KCLASS))
+    # warm-up (the first step also yields a mixed solution kept for the FP64 comparison)
+    s_keep, u_keep, info0, _ = one_step(keep=True)
+    u_mixed_host = u_keep.cpu() if prec == "mixed" and not args.no_fp64_ref else None
+    s_keep.close()
+    del u_keep
     for _ in range(max(0, args.warmup - 1)):
-        one_step()
-    dominant = max(prof0, key=lambda k: prof0[k]["ms"])
+        one_step(profile=False)
+    torch.cuda.empty_cache()
 
-    # timed region: K steps, device-resident inputs (problem description) and outputs
+    # timed region: K steps of setup + solve; every kernel class timed by CUDA events
     clocks = ClockSampler(local)
     barrier(world)
     torch.cuda.synchronize()
@@ -289,9 +360,9 @@ def main():
     e0.record(stream)
     infos, profs = [], []
     for _ in range(args.steps):
-        info, prof = one_step(profile=[dominant])
+        _, _, info, prof = one_step()
         infos.append(info)
-        profs.append(prof[dominant])
+        profs.append(prof)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
@@ -300,93 +371,107 @@ def main():
     ms = e0.elapsed_time(e1)
     ms_max = max_over_ranks(ms, world, device="cuda")
     value = world * args.steps * dof / (ms_max / 1e3)
+    step_ms = ms_max / args.steps
 
-    # adjoint of the solved state (compliance and its gradient in the per-cell radii), outside the
-    # timed region: CUDA events around the calls on the solver's stream
-    adjoint = None
-    try:
-        s = binding.Solver(prob, precision=precision)
-        u, _, _ = s.solve()
-        g = s.grad(u)                     # warm
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        reps = 5
-        for _ in range(reps):
-            g = s.grad(u, out=g)
-        a1.record(stream)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        c = s.compliance(u)
-        t_c = time.perf_counter() - t0
-        adjoint = {"grad_ms": a0.elapsed_time(a1) / reps, "compliance_ms_host_clock": 1e3 * t_c,
-                   "compliance": [float(x) for x in c], "grad_abs_max": float(g.abs().max()),
-                   "note": "this workload's hard strut mask has no derivative in r, so the gradient "
-                           "is zero; nonzero gradients are exercised on sigmoid-mask lattices"}
-        s.close()
-    except Exception as exc:   # reported, never fatal for the benchmark line
-        adjoint = {"error": str(exc)[:200]}
+    # per-class rooflines over the timed steps
+    tot = {}
+    for p in profs:
+        for k, v in p.items():
+            a = tot.setdefault(k, {"ms": 0.0, "launches": 0, "flops": 0.0, "bytes": 0.0})
+            for f in a:
+                a[f] += v[f]
+    rooflines = {}
+    for k, v in tot.items():
+        e = class_roofline(k, v, prec, peaks, step_ms * args.steps)
+        if e:
+            rooflines[k] = e
+    dominant = max(rooflines, key=lambda k: rooflines[k]["total_ms"])
+    roof = dict(rooflines[dominant])
+    roof["kernel_class"] = dominant
+    roof["traffic"] = ncu_traffic(dominant, prec, args.workload)   # DRAM bytes per launch (ncu)
+    hot_path = {k: rooflines[k] for k in ("maps", "cell_gemv", "apply_K", "tc_gemm", "coarse", "gram", "vector")
+                if k in rooflines}
 
-    # end-to-end through the public API with HOST output buffers (pinned)
-    u_host = torch.empty((prob.n_rhs, prob.n_cells, 578), dtype=torch.float64).pin_memory().numpy()
+    # the FP64 path on the same workload (one solve, outside the timed region) and the
+    # displacement difference between the two solutions
+    fp64_ref = None
+    if prec == "mixed" and not args.no_fp64_ref:
+        try:
+            torch.cuda.synchronize()
+            f0 = time.perf_counter()
+            s64 = binding.Solver(prob, precision=binding.FETIDP_FP64, **opts)
+            u64, _, info64 = s64.solve()
+            torch.cuda.synchronize()
+            f_ms = 1e3 * (time.perf_counter() - f0)
+            um = u_mixed_host.to(u64.device)
+            err = float((um - u64).abs().max() / u64.abs().max())
+            fp64_ref = {"ms": f_ms, "outer_its": info64["outer_its"], "inner_its_total": info64["inner_its_total"],
+                        "rel_residual": info64["rel_residual"], "t_setup_ms": 1e3 * info64["t_setup_s"],
+                        "t_solve_ms": 1e3 * info64["t_solve_s"], "device_bytes": info64["device_bytes"],
+                        "disp_err_mixed_vs_fp64": err,
+                        "disp_err_note": "max |u_mixed - u_fp64| / max |u_fp64|, both at outer residual <= 1e-8"}
+            s64.close()
+            del u64, um
+        except Exception as exc:   # reported, never fatal for the benchmark line
+            fp64_ref = {"error": str(exc)[:300]}
+        torch.cuda.empty_cache()
+
+    # end to end through the public API with HOST output buffers (pinned)
+    u_host = torch.empty((prob.n_rhs, prob.n_cells, n_dof), dtype=torch.float64).pin_memory().numpy()
+    ne = max(1, args.e2e_steps)
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        s = binding.Solver(prob, precision=precision)
+    for _ in range(ne):
+        s = binding.Solver(prob, precision=precision, **opts)
         s.solve_host(u_host)
         s.close()
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, device="cuda")
-    e2e_value = world * args.steps * dof / e2e_s
+    e2e_value = world * ne * dof / e2e_s
     h2d = prob.n_cells * 8 + len(prob.loads) * (3 * 4 + prob.dim * 8)
     d2h = u_host.nbytes
+    del u_host
+    torch.cuda.empty_cache()
 
-    # roofline of the dominant kernel class, from its CUDA-event time inside the timed region
-    peaks = measured_peaks()
-    fl = sum(p["flops"] for p in profs)
-    by = sum(p["bytes"] for p in profs)
-    kms = sum(p["ms"] for p in profs)
-    nl = sum(p["launches"] for p in profs)
-    fp64_alu = ("sweep",) + (("grouped_gemm", "gram", "apply_K", "traces") if prec_name == "fp64" else ())
-    if dominant in fp64_alu:
-        achieved = fl / (kms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "peak_source": "derived FP64 DFMA rate (152 SMs x 2 DFMA/clk x 2.07 GHz)"}
-    elif dominant == "tc_gemm":
-        achieved = fl / (kms / 1e3) / 1e12
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops_sustained"],
-                "unit": "TFLOP/s", "peak_source": "measured bf16 sustained"}
-    elif dominant == "traces":
-        achieved = fl / (kms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS / DF_OPS_PER_TERM,
-                "unit": "TFLOP/s (FP64-equivalent)",
-                "peak_source": f"derived FP32 issue rate (152 SMs x 128 x 2.07 GHz) / {DF_OPS_PER_TERM} "
-                               "FP32 instructions per double-float term"}
-    else:
-        achieved = by / (kms / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "peak_source": "measured HBM copy"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["kernel_class"] = dominant
-    roof["launches"] = nl
-    roof["avg_launch_ms"] = kms / max(nl, 1)
-    tr = ncu_traffic(dominant, prec_name)
-    roof["traffic"] = tr
-    roof["share_of_step"] = kms / ms if ms > 0 else None
+    # secondary line: the 2D 64x64 lattice (config2), a few steps, same step definition
+    secondary = None
+    if not args.no_secondary and args.workload != "cfg2":
+        try:
+            p2 = workload_problem("cfg2")
+            for _ in range(2):
+                binding.Solver(p2, precision=precision).close()
+            torch.cuda.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            n2 = 5
+            for _ in range(n2):
+                s2 = binding.Solver(p2, precision=precision)
+                _, _, i2 = s2.solve()
+                s2.close()
+            a1.record(stream)
+            torch.cuda.synchronize()
+            ms2 = a0.elapsed_time(a1) / n2
+            dof2 = p2.n_cells * 578 * p2.n_rhs
+            secondary = {"workload": WORKLOADS["cfg2"]["label"], "n_rb": i2["n_rb"], "ms_per_step": ms2,
+                         "value": dof2 / (ms2 / 1e3), "unit": UNIT, "outer_its": i2["outer_its"],
+                         "inner_its_total": i2["inner_its_total"], "rel_residual": i2["rel_residual"]}
+        except Exception as exc:
+            secondary = {"error": str(exc)[:300]}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if prec_name == "fp64" else "bf16-tc/f32/f64",
+        "dtype": "f64" if prec == "fp64" else "bf16-tc/f32/f64",
         "data": "synthetic",
         "config": {
-            "workload": "2d_64x64_e16" if args.cells == 64 else f"2d_{args.cells}x{args.cells}_e16",
-            "cells": [args.cells, args.cells], "q1_per_cell": [16, 16],
-            "dof": dof, "rhs": prob.n_rhs, "n_rb": info0["n_rb"], "precision": prec_name,
-            "n_rb_note": "8 principal cells stagnate on this hard-mask lattice; 32 used",
-            "step": "fetidp_setup + fetidp_solve to outer rel. residual 1e-8",
-            "l2": "inputs larger than L2 (C_hat snapshots 335 MB, ROM operators ~1 GB per step)",
+            "workload": wl["label"], "cells": list(prob.cells), "q1_per_cell": [prob.elems] * prob.dim,
+            "dof": dof, "rhs": prob.n_rhs, "n_rb": info0["n_rb"], "precision": prec,
+            "n_rb_note": "the configured principal-cell count does not converge on this hard-mask, "
+                         "graded-radius lattice; the reduced basis is grown as the paper advises",
+            "step": "fetidp_setup + fetidp_solve to outer rel. residual 1e-8 (all load cases)",
+            "l2": "inputs larger than L2 (snapshots, element matrices, assembled operators)",
             "outer_its": infos[-1]["outer_its"], "inner_its_total": infos[-1]["inner_its_total"],
             "rel_residual": infos[-1]["rel_residual"],
             "t_setup_ms": 1e3 * statistics.median(i["t_setup_s"] for i in infos),
@@ -394,22 +479,24 @@ def main():
             "device_bytes": infos[-1]["device_bytes"],
             "parallelism": f"replicas x{world}",
             "fp64_path": fp64_ref,
-            "adjoint": adjoint,
-            "speedup_vs_fp64": (fp64_ref["ms"] / (ms_max / args.steps)) if fp64_ref else None,
+            "speedup_vs_fp64": (fp64_ref["ms"] / step_ms) if fp64_ref and "ms" in fp64_ref else None,
+            "secondary": secondary,
+            "e2e_steps": ne,
         },
         "roofline": roof,
+        "rooflines": hot_path,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,
-        "class_profile_ms": {k: round(v["ms"], 3) for k, v in prof0.items() if v["launches"]},
+        "class_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in tot.items() if v["launches"]},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, dt, d = oracle_time_to_solution(args.cpu_sample)
+        cells = SAMPLES[args.workload]["cpu"]
+        v, dt, d = oracle_time_to_solution(args.workload, cells)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                                "sample": f"{args.cpu_sample}x{args.cpu_sample}-cell sub-lattice "
-                                          f"of the 64x64 workload ({d} DOF), setup + solve, "
-                                          f"{dt:.1f} s"}
+                                "sample": f"{cells[0]}x{cells[1]}x{cells[2]}-cell corner of the workload "
+                                          f"lattice ({d} DOF over all load cases), setup + solve, {dt:.1f} s"}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

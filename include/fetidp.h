@@ -17,8 +17,11 @@
  *             host-visible results (fetidp_solve's info, fetidp_rom_data)
  *             synchronise that stream; the others are asynchronous.
  * Errors      Every call returns a fetidp_status and never aborts the process.
- *             A CUDA error is reported as FETIDP_ECUDA; a non-finite value in
- *             an input vector is not checked on the hot path.
+ *             A CUDA error is reported as FETIDP_ECUDA.  Non-finite host data
+ *             given to fetidp_setup (radii, loads, map parameters, material)
+ *             give FETIDP_EINVAL; so do non-finite input vectors when the
+ *             context's check_inputs option is set (the default).  A device
+ *             wait that exceeds wait_budget_ns gives FETIDP_ETIMEOUT.
  * Layouts     n_rhs load cases ("RHS") are stored RHS-major:
  *               multiplier vectors   lambda[rhs][L]
  *               cell vectors         u[rhs][cell][n_dof]  (cell-duplicated,
@@ -55,7 +58,9 @@ typedef enum {
   FETIDP_FP64 = 0,         /* every step in FP64 */
   FETIDP_MIXED_BF16 = 1    /* grouped principal contractions on tcgen05 in BF16 with FP32
                               accumulation; Krylov recurrences, reductions, coarse solve,
-                              outer operator in FP64 */
+                              outer operator in FP64.  There is no TF32 precision: one TF32
+                              product keeps 11 significand bits, fewer than the 16 of the
+                              three-product BF16 split used here, at half its MMA rate */
 } fetidp_precision;
 
 /* One lattice problem (Sec. 2.1-2.2.1, Eqs. 1-6).  Host memory; copied at setup.
@@ -107,9 +112,7 @@ typedef struct {
 typedef struct {
   double tol_outer;         /* stop when the TRUE ||b - A x|| / ||b|| <= tol_outer (1e-8) */
   double tol_inner;         /* inner PCG stop: ||r_k|| / ||r_0|| <= tol_inner (1e-11; P. 579) */
-  int max_outer;            /* FGMRES iterations per cycle (50); sizes the Krylov storage.
-                               A cycle restarts from the current iterate while the true
-                               residual is above tol_outer (at most 8 cycles)            */
+  int max_outer;            /* FGMRES iterations in total, over all restart cycles (100)    */
   int max_inner;            /* PCG iterations per preconditioner application (1000) */
   int precision;            /* fetidp_precision (FETIDP_FP64) */
   int fixed_outer;          /* > 0: run exactly this many outer iterations (iterate-locked) */
@@ -126,6 +129,26 @@ typedef struct {
   unsigned profile_mask;    /* kernel classes (bit k = fetidp_kernel_class k) timed from the
                                start of fetidp_setup, as fetidp_profile_enable does from the
                                call on; read with fetidp_profile_read (0)                     */
+  int restart;              /* FGMRES cycle length: the Krylov storage holds restart + 1 basis
+                               vectors and restart preconditioned ones per RHS (2 x restart x
+                               n_tot x n_rhs x 8 bytes).  After a cycle the true residual is
+                               recomputed and a new cycle starts from the current iterate.
+                               0 = min(max_outer, 30) (0); fixed_outer > restart raises it    */
+  long long wait_budget_ns; /* bound of every device-side wait of the tensor-core kernels, in
+                               ns of the GPU's global timer (1e9).  On expiry the kernel stops,
+                               lets its own copies and MMAs finish (a separate fixed 1 s bound),
+                               frees its tensor memory and returns; the call reports
+                               FETIDP_ETIMEOUT and the context stays usable.  Must be > 0     */
+  int check_inputs;         /* 1: entry points that take input vectors (all but fetidp_solve)
+                               check them for NaN/Inf first (FETIDP_EINVAL) and, in the mixed
+                               precision, report an expired device wait (FETIDP_ETIMEOUT);
+                               both synchronise the stream.  0: no check, fully asynchronous
+                               calls (1)                                                     */
+  int mixed_assembled;      /* mixed path, operators of the inner PCG (Eqs. 48, 49): 1 = each
+                               cell's F_dd_ring and S_dd_ring assembled once in FP32 and streamed
+                               (4 n_d^2 bytes per cell per application, shared by the RHS);
+                               0 = principal form on the tensor cores (2 N_rb n_d^2 flops per
+                               column); -1 = assembled when n_d > 128, i.e. for 3D cells (-1)  */
 } fetidp_options;
 
 typedef struct {
@@ -317,7 +340,17 @@ fetidp_status fetidp_tc_comb_selfcheck(int M0, int M1, int K, int N, int nops, d
  * Errors: EINVAL (sizes, or scratch too small), ECUDA, ETIMEOUT (a bounded device wait expired). */
 fetidp_status fetidp_tc_selfcheck_static(int M, int K, int N, double *rel_err, void *stream);
 
-/* Number of kernels this library has launched in the calling process. */
+/* Probe of the bounded device waits (the paper has no counterpart): one thread of a one-block
+ * kernel waits, through the same bounded wait the tensor-core kernels use, on an mbarrier phase
+ * that nothing completes.  The wait expires after wait_budget_ns (0 < budget <= 1e10 ns) and the
+ * call returns FETIDP_ETIMEOUT -- the status a solve or an entry point returns when one of its
+ * kernels' waits expires -- with the device and every context still usable.  FETIDP_OK would mean
+ * the wait completed, which it cannot.  stream: cudaStream_t or NULL; the call synchronises it.
+ * waited_s (host, may be NULL): wall time of the call.  The flag it uses is one static device int
+ * of this library, so calls that overlap in time race on it.  EINVAL for a budget out of range. */
+fetidp_status fetidp_wait_selfcheck(long long wait_budget_ns, void *stream, double *waited_s);
+
+/* Number of kernels this library has launched in the calling process. *//* Number of kernels this library has launched in the calling process. */
 long long fetidp_kernel_launches(void);
 
 void fetidp_destroy(fetidp_ctx *ctx);

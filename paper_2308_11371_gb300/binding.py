@@ -30,7 +30,7 @@ SYMBOLS = ["fetidp_sizes", "fetidp_default_options", "fetidp_setup", "fetidp_app
            "fetidp_status_string", "fetidp_last_error", "fetidp_profile_enable",
            "fetidp_profile_read", "fetidp_kernel_launches", "fetidp_tc_selfcheck",
            "fetidp_tc_comb_selfcheck", "fetidp_tc_selfcheck_static",
-           "fetidp_compliance", "fetidp_batch_layout"]
+           "fetidp_compliance", "fetidp_batch_layout", "fetidp_wait_selfcheck"]
 
 KCLASS = {"grouped_gemm": 0, "apply_K": 1, "maps": 2, "coarse": 3, "cell_gemv": 4, "vector": 5,
           "gram": 6, "tc_gemm": 7, "setup": 8, "sweep": 9, "traces": 10, "greedy": 11}
@@ -63,7 +63,9 @@ class Options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("fixed_outer", ctypes.c_int),
                 ("fixed_inner", ctypes.c_int), ("tc_split", ctypes.c_int),
                 ("tol_inner_mixed", ctypes.c_double), ("gram_drop_mixed", ctypes.c_double),
-                ("profile_mask", ctypes.c_uint)]
+                ("profile_mask", ctypes.c_uint), ("restart", ctypes.c_int),
+                ("wait_budget_ns", ctypes.c_longlong), ("check_inputs", ctypes.c_int),
+                ("mixed_assembled", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -135,6 +137,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.fetidp_tc_selfcheck.argtypes = [I, I, I, ctypes.POINTER(ctypes.c_double)]
     lib.fetidp_tc_selfcheck_static.restype = I
     lib.fetidp_tc_selfcheck_static.argtypes = [I, I, I, ctypes.POINTER(ctypes.c_double), V]
+    lib.fetidp_wait_selfcheck.restype = I
+    lib.fetidp_wait_selfcheck.argtypes = [ctypes.c_longlong, V, ctypes.POINTER(ctypes.c_double)]
     lib.fetidp_kernel_launches.restype = ctypes.c_longlong
     lib.fetidp_kernel_launches.argtypes = []
     _LIB = lib
@@ -387,3 +391,11 @@ def tc_selfcheck_static(M: int, K: int, N: int, stream: int = 0) -> float:
     err = ctypes.c_double()
     _check(load().fetidp_tc_selfcheck_static(M, K, N, ctypes.byref(err), ctypes.c_void_p(stream or None)))
     return err.value
+
+
+def wait_selfcheck(wait_budget_ns: int, stream: int = 0):
+    """Run the bounded-wait probe; returns (status, seconds waited).  The expected status is
+    FETIDP_ETIMEOUT (-5): the probe waits on a barrier nothing completes."""
+    waited = ctypes.c_double()
+    st = load().fetidp_wait_selfcheck(int(wait_budget_ns), ctypes.c_void_p(stream or None), ctypes.byref(waited))
+    return int(st), waited.value

@@ -206,6 +206,7 @@ struct Ctx {
   long long nsnap = 0;
   long long N = 0, L = 0, nP = 0, ntot = 0;
   int m = 0;        // RHS
+  int kry = 0;      // FGMRES cycle length (Krylov storage)
   int nrb = 0;      // principal cells selected
   int nV = 0;       // free lattice vertices (all lattices)
   int clamp_axis = 0, clamp_side = 0;
@@ -231,7 +232,7 @@ struct Ctx {
   // lattice maps
   int* gath = nullptr;        // [N*nd*2] signed (row+1) codes, 0 = none (B_d^T)
   int* scat = nullptr;        // [L*2] signed (cell*nd + j + 1) codes, 0 = none (B_d)
-  double* Dw = nullptr;       // [L] scaling D
+  int* dinfo = nullptr;       // [L] (n << 8) | q: chain row q of n at the row's node (Eq. 30 D)
   int* corner_v = nullptr;    // [N*ncorner] free vertex index or -1 (A_p)
   int* vert_cells = nullptr;  // [nV*ncorner] (cell*ncorner + k) or -1 (A_p^T gather)
   double* r_dev = nullptr;    // [N]
@@ -251,6 +252,11 @@ struct Ctx {
   // ROM per-cell operators (assembled, Eq. 43)
   double* Fdd_c = nullptr;    // [N][nd][nd]
   double* Sdd_c = nullptr;    // [N][nd][nd]
+  // mixed path, large cells: the same operators assembled in FP32, rows padded to ld_f (16 bytes)
+  float* Fdd_f = nullptr;     // [N][nd][ld_f]
+  float* Sdd_f = nullptr;     // [N][nd][ld_f]
+  int ld_f = 0;
+  bool asm_f32 = false;
   double* Urp_c = nullptr;    // [N][nr][np]
   double* UrpT_c = nullptr;   // [N][np][nr]
   // coarse solve
@@ -294,6 +300,8 @@ struct Ctx {
   float* tc_yp = nullptr;       // resident-operator combination: partial sums per principal group
   size_t tc_yp_bytes = 0;
   int* tc_err = nullptr;        // device error flag of the bounded waits
+  unsigned long long wait_ns = 1000000000ull;   // budget of every device-side wait
+  int* chk = nullptr;           // device flag of the input checks
 };
 
 // RAII timing of one launch (or one multi-kernel step) of a kernel class.
@@ -337,9 +345,11 @@ fetidp_status dalloc_t(Ctx& c, T** p, size_t count) {
 }
 
 // ---------------------------------------------------------------- kernels (maps, vectors)
-fetidp_status k_gather_BT(Ctx& c, const double* lam, long long lam_rs, const double* scale,
+fetidp_status k_gather_BT(Ctx& c, const double* lam, long long lam_rs, const int* dinfo,
                           CellVec out_d, int nrhs, double beta);
-fetidp_status k_scatter_B(Ctx& c, CCellVec yd, double* out, long long out_rs, const double* scale,
+fetidp_status k_nonfinite(Ctx& c, const double* x, long long n, int* flag);
+fetidp_status wait_selfcheck(unsigned long long wait_ns, cudaStream_t stream);
+fetidp_status k_scatter_B(Ctx& c, CCellVec yd, double* out, long long out_rs, const int* dinfo,
                           double alpha, double beta, int nrhs);
 fetidp_status k_primal_assemble(Ctx& c, CCellVec cp, double* out, long long out_rs, double alpha,
                                 double beta, int nrhs);
@@ -408,6 +418,10 @@ fetidp_status k_batched_diag_sum(Ctx& c, const double* A, long long stride, int 
                                  double* out);
 fetidp_status k_apply_K(Ctx& c, CCellVec u, CellVec y, int nvec_per_col, int ncols, bool idp,
                         bool r_only, const double* chat, double chat_scale_dr);
+fetidp_status k_rom_combine_f32(Ctx& c, const double* src, long long kstride, int ld, int r0, int c0, int rows,
+                                int cols, const double* coef, float* out, int ldo);
+fetidp_status k_cell_gemm_f32(Ctx& c, const float* mats, int ldm, int rows, int cols, CCellVec x, CellVec y,
+                              double alpha, double beta, int nrhs);
 fetidp_status k_cell_gemv_strided(Ctx& c, const double* mats, long long mstride, int ld, int mrows,
                                   int mcols, CCellVec x, CellVec y, double alpha, double beta,
                                   int nrhs);

@@ -244,7 +244,8 @@ __global__ void element_matrices_f32_kernel(const double* __restrict__ chat, lon
 }
 
 // Multi-vector K_s application in FP32 (the Eq. 46b products K_s R of the mixed path).  One
-// block per (rhs, cell); for each colour group (elements that share no node) the precomputed
+// block per (cell, rhs, chunk of VB vectors), the cell slowest: the blocks of one cell run side
+// by side and read its element matrices from L2, not once per chunk from HBM.  For each colour group (elements that share no node) the precomputed
 // element matrices of its elements are staged in shared memory (contiguous, coalesced) and
 // applied to all vectors of the chunk, one thread per (element, vector).  Vectors are stored
 // dof-major with a padded stride, so the threads of an element read consecutive words and every
@@ -257,7 +258,8 @@ template <int D>
 __global__ void __launch_bounds__(kMultiThreads, 2) apply_K_multi_kernel(
     int e, long long ncell, int n, int len, const int* __restrict__ perm, bool idp,
     const float* __restrict__ u, long long u_rs, int u_cs, float* __restrict__ y, long long y_rs, int y_cs,
-    int nvec, int VB, const float* __restrict__ Kall, int nelc_max, long long u_ext, long long y_ext) {
+    int nvec, int VB, int nchunk, int nrhs, const float* __restrict__ Kall, int nelc_max, long long u_ext,
+    long long y_ext) {
   constexpr int NA = 1 << D;
   constexpr int ND = NA * D;
   constexpr int KES = multi_ke_stride(D);
@@ -268,9 +270,10 @@ __global__ void __launch_bounds__(kMultiThreads, 2) apply_K_multi_kernel(
   float* Ke = ys + (size_t)n * VBp;                     // [nelc_max][KES], rows of ND
   Ke = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(Ke) + 15) & ~uintptr_t(15));
   int* perm_s = reinterpret_cast<int*>(Ke + (size_t)nelc_max * KES);   // [n] local -> natural
-  const long long col = blockIdx.x;
-  const int rhs = (int)(col / ncell);
-  const long long cell = col - (long long)rhs * ncell;
+  const int chunk = (int)(blockIdx.x % nchunk);
+  const long long rest = blockIdx.x / nchunk;
+  const int rhs = (int)(rest % nrhs);
+  const long long cell = rest / nrhs;
   const float* uc = u + rhs * u_rs + cell * u_cs;
   float* yc = y + rhs * y_rs + cell * y_cs;
   const int nel = e * e * (D == 3 ? e : 1);
@@ -278,7 +281,8 @@ __global__ void __launch_bounds__(kMultiThreads, 2) apply_K_multi_kernel(
   const int ecount[3] = {e, e, D == 3 ? e : 1};
   for (int li = threadIdx.x; li < n; li += blockDim.x) perm_s[li] = idp ? perm[li] : li;
   __syncthreads();
-  for (int v0 = 0; v0 < nvec; v0 += VB) {
+  {
+    const int v0 = chunk * VB;
     const int vb = min(VB, nvec - v0);
 #pragma unroll 4
     for (int t = threadIdx.x; t < vb * len; t += blockDim.x) {
@@ -454,6 +458,99 @@ __global__ void cell_gemv_narrow_kernel(const double* __restrict__ mats, long lo
         if (r < rb) {
           double* dst = y + (r0 + r) * y_rs + cell * y_cs + row;
           *dst = (beta == 0.0) ? alpha * acc[r] : alpha * acc[r] + beta * (*dst);
+        }
+      }
+    }
+  }
+}
+
+// ---- assembled per-cell ROM operators in FP32 (mixed path, large cells)
+// F_dd_ring^(s) = sum_k delta_k F_dd^(sigma_k) and S_dd_ring^(s) = sum_k alpha_k S_dd^(sigma_k)
+// (Eqs. 43, 48, 49) formed once per setup.  Applying the principal form costs 2 N_rb n_d^2 flops
+// per column (three BF16 products with the hi/lo split); the assembled operator costs 4 n_d^2
+// bytes per cell, shared by the cell's m columns.  At n_d = 630 the streamed operator is the
+// cheaper of the two on GB300, and it is HBM-bound.
+
+// out[cell][r][c] (row stride ldo, FP32) = sum_k coef[cell][k] src[k][(r0 + r) * ld + c0 + c].
+// A thread owns one entry (r, c): its NRBM principal values sit in registers and are reused for
+// kCombCells cells, whose coefficients are staged in shared memory (FP32 arithmetic).
+constexpr int kCombCells = 32;
+template <int NRBM>
+__global__ void __launch_bounds__(256) rom_combine_f32_kernel(const double* __restrict__ src, long long kstride,
+                                                              int ld, int r0, int c0, int rows, int cols,
+                                                              const double* __restrict__ coef, int nrb,
+                                                              long long ncell, float* __restrict__ out, int ldo) {
+  __shared__ float cs[kCombCells][NRBM];
+  const long long per = (long long)rows * cols;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const bool live = t < per;
+  const int r = live ? (int)(t / cols) : 0, cc = live ? (int)(t - (long long)r * cols) : 0;
+  float p[NRBM];
+#pragma unroll
+  for (int k = 0; k < NRBM; ++k)
+    p[k] = (live && k < nrb) ? (float)src[k * kstride + (long long)(r0 + r) * ld + c0 + cc] : 0.f;
+  for (long long cell0 = (long long)blockIdx.y * kCombCells; cell0 < ncell; cell0 += (long long)gridDim.y * kCombCells) {
+    const int nc = (int)min((long long)kCombCells, ncell - cell0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < kCombCells * NRBM; q += blockDim.x) {
+      const int ci = q / NRBM, k = q - ci * NRBM;
+      cs[ci][k] = (ci < nc && k < nrb) ? (float)coef[(cell0 + ci) * nrb + k] : 0.f;
+    }
+    __syncthreads();
+    if (!live) continue;
+    for (int ci = 0; ci < nc; ++ci) {
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k < NRBM; ++k) acc = fmaf(cs[ci][k], p[k], acc);
+      out[(cell0 + ci) * (long long)rows * ldo + (long long)r * ldo + cc] = acc;
+    }
+  }
+}
+
+// y[rhs][cell][0..rows) = alpha M_f32[cell] x[rhs][cell][0..cols) + beta y: one CTA per cell,
+// x converted to FP32 in shared memory, one warp per row with 16-byte loads of the row (ldm a
+// multiple of 4, 16-byte aligned matrices), FP32 accumulation for up to kMaxRhsF32 columns.
+constexpr int kMaxRhsF32 = 8;
+__global__ void __launch_bounds__(256) cell_gemm_f32_kernel(const float* __restrict__ mats, int ldm, int rows,
+                                                            int cols, const double* __restrict__ x, long long x_rs,
+                                                            int x_cs, double* __restrict__ y, long long y_rs,
+                                                            int y_cs, double alpha, double beta, int nrhs) {
+  extern __shared__ float xsf[];   // [nrhs][ldm]
+  const long long cell = blockIdx.x;
+  for (int t = threadIdx.x; t < nrhs * ldm; t += blockDim.x) {
+    const int rr = t / ldm, q = t - rr * ldm;
+    xsf[t] = q < cols ? (float)x[rr * x_rs + cell * x_cs + q] : 0.f;
+  }
+  __syncthreads();
+  const float4* M = reinterpret_cast<const float4*>(mats + cell * (long long)rows * ldm);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int n4 = ldm >> 2;
+  for (int row = warp; row < rows; row += nw) {
+    const float4* Mr = M + (long long)row * n4;
+    for (int rb0 = 0; rb0 < nrhs; rb0 += kMaxRhsF32) {
+      const int rb = min(kMaxRhsF32, nrhs - rb0);
+      float acc[kMaxRhsF32];
+#pragma unroll
+      for (int q = 0; q < kMaxRhsF32; ++q) acc[q] = 0.f;
+      for (int j = lane; j < n4; j += 32) {
+        const float4 m4 = __ldcs(Mr + j);   // streamed once per apply: keep it out of L2's way
+#pragma unroll
+        for (int q = 0; q < kMaxRhsF32; ++q) {
+          if (q < rb) {
+            const float4 x4 = reinterpret_cast<const float4*>(xsf + (rb0 + q) * ldm)[j];
+            acc[q] = fmaf(m4.x, x4.x, fmaf(m4.y, x4.y, fmaf(m4.z, x4.z, fmaf(m4.w, x4.w, acc[q]))));
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kMaxRhsF32; ++q) {
+        if (q < rb) {
+          float sv = acc[q];
+          for (int o = 16; o > 0; o >>= 1) sv += __shfl_down_sync(0xffffffffu, sv, o);
+          if (lane == 0) {
+            double* dst = y + (rb0 + q) * y_rs + cell * y_cs + row;
+            *dst = (beta == 0.0) ? alpha * (double)sv : alpha * (double)sv + beta * (*dst);
+          }
         }
       }
     }
@@ -1005,24 +1102,61 @@ fetidp_status k_apply_K_f32(Ctx& c, const float* u, long long u_rs, int u_cs, fl
   }
   {
     // algorithmic work: one K_e product (ND^2 FMA) per element and vector; bytes: the element
-    // matrices once per chunk, the vectors in and out
+    // matrices once per cell, the vectors in and out
     const double cols = (double)c.N * nrhs;
-    const double chunks = (double)((nvec + VB - 1) / VB);
     c.prof_pending_flops = 2.0 * cols * c.nelem * (double)nvec * ND * ND;
-    c.prof_pending_bytes = cols * (chunks * c.nelem * (double)ND * ND * 4.0 + 2.0 * nvec * len * 4.0);
+    c.prof_pending_bytes = (double)c.N * c.nelem * (double)ND * ND * 4.0 + cols * 2.0 * nvec * len * 4.0;
   }
   ProfScope ps(c, FETIDP_K_APPLY_K, c.prof_pending_flops, c.prof_pending_bytes);
   const size_t smem = bytes(VB);
-  const dim3 grid((unsigned)(c.N * nrhs));
+  const int nchunk = (nvec + VB - 1) / VB;
+  const dim3 grid((unsigned)(c.N * nrhs * nchunk));
   if (c.d == 2) {
     cudaFuncSetAttribute(apply_K_multi_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     apply_K_multi_kernel<2><<<grid, kMultiThreads, smem, c.stream>>>(
-        c.e, c.N, c.n, len, c.perm, idp, u, u_rs, u_cs, y, y_rs, y_cs, nvec, VB, c.Ke_all, nelc_max, ext, ext);
+        c.e, c.N, c.n, len, c.perm, idp, u, u_rs, u_cs, y, y_rs, y_cs, nvec, VB, nchunk, nrhs, c.Ke_all, nelc_max,
+        ext, ext);
   } else {
     cudaFuncSetAttribute(apply_K_multi_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     apply_K_multi_kernel<3><<<grid, kMultiThreads, smem, c.stream>>>(
-        c.e, c.N, c.n, len, c.perm, idp, u, u_rs, u_cs, y, y_rs, y_cs, nvec, VB, c.Ke_all, nelc_max, ext, ext);
+        c.e, c.N, c.n, len, c.perm, idp, u, u_rs, u_cs, y, y_rs, y_cs, nvec, VB, nchunk, nrhs, c.Ke_all, nelc_max,
+        ext, ext);
   }
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_rom_combine_f32(Ctx& c, const double* src, long long kstride, int ld, int r0, int c0, int rows,
+                                int cols, const double* coef, float* out, int ldo) {
+  if (c.nrb > 64) { set_error("n_rb above 64"); return FETIDP_EINVAL; }
+  const long long per = (long long)rows * cols;
+  long long gy = (c.N + kCombCells - 1) / kCombCells;
+  if (gy > 64) gy = 64;
+  const dim3 grid((unsigned)((per + 255) / 256), (unsigned)gy);
+  ProfScope ps(c, FETIDP_K_SETUP, 2.0 * c.nrb * per * (double)c.N, 4.0 * per * (double)c.N);
+  if (c.nrb <= 16)
+    rom_combine_f32_kernel<16><<<grid, 256, 0, c.stream>>>(src, kstride, ld, r0, c0, rows, cols, coef, c.nrb, c.N, out, ldo);
+  else if (c.nrb <= 32)
+    rom_combine_f32_kernel<32><<<grid, 256, 0, c.stream>>>(src, kstride, ld, r0, c0, rows, cols, coef, c.nrb, c.N, out, ldo);
+  else
+    rom_combine_f32_kernel<64><<<grid, 256, 0, c.stream>>>(src, kstride, ld, r0, c0, rows, cols, coef, c.nrb, c.N, out, ldo);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_cell_gemm_f32(Ctx& c, const float* mats, int ldm, int rows, int cols, CCellVec x, CellVec y,
+                              double alpha, double beta, int nrhs) {
+  if (ldm % 4 != 0 || (reinterpret_cast<uintptr_t>(mats) & 15) != 0) {
+    set_error("FP32 cell operators need 16-byte aligned rows");
+    return FETIDP_EINVAL;
+  }
+  // algorithmic bytes: the operators once, the FP64 vectors in and out
+  ProfScope ps(c, FETIDP_K_CELL_GEMV, 2.0 * rows * cols * (double)c.N * nrhs,
+               4.0 * c.N * (double)rows * ldm + 8.0 * c.N * (double)nrhs * (rows + cols));
+  const size_t smem = (size_t)nrhs * ldm * sizeof(float);
+  cudaFuncSetAttribute(cell_gemm_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cell_gemm_f32_kernel<<<(unsigned)c.N, 256, smem, c.stream>>>(mats, ldm, rows, cols, x.p, x.rs, x.cs, y.p, y.rs,
+                                                               y.cs, alpha, beta, nrhs);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }

@@ -16,61 +16,99 @@ namespace {
 constexpr int kRedBlocks = kReductionBlocks;
 constexpr int kRedThreads = 256;
 
+// Dirichlet-preconditioner scaling D = (B B^T)^{-1} (Eq. 30: sum_s B_d B_d^T D = I_L).
+// B B^T is block diagonal over the rows of one node and component.  dinfo[row] = (n << 8) | q:
+// the row is chain row q of the n chain rows of its node (rows of one node and component lie d
+// apart), n = 0 for a Dirichlet row (block 1).  The block is the inverse of the n x n matrix
+// tridiag(-1, 2, -1), (T^{-1})_ab = (min(a, b) + 1)(n - max(a, b)) / (n + 1): 1/2 for n = 1
+// (every 2D row, 3D face rows), quarters for the n = 3 rows of a 3D cell edge (exact in binary).
+__device__ __forceinline__ double tinv(int a, int b, int n) {
+  const int lo = a < b ? a : b, hi = a < b ? b : a;
+  return (double)((lo + 1) * (n - hi)) / (double)(n + 1);
+}
+
+__device__ __forceinline__ double d_scaled(const double* __restrict__ l, const int* __restrict__ dinfo,
+                                           int row, int d) {
+  const int code = dinfo[row];
+  const int n = code >> 8, q = code & 0xff;
+  if (n == 0) return l[row];
+  double v = 0.0;
+  for (int b = 0; b < n; ++b) v += tinv(q, b, n) * l[row + (b - q) * d];
+  return v;
+}
+
+// x_d = B_d^T lambda, or B_d^T D lambda when dinfo is given.  One thread per (cell, dual DOF)
+// for every RHS: the index codes are read once and reused for all load cases.
 __global__ void gather_BT_kernel(const int* __restrict__ gath, const double* __restrict__ lam,
-                                 long long lam_rs, const double* __restrict__ scale,
+                                 long long lam_rs, const int* __restrict__ dinfo, int d,
                                  double* __restrict__ out, long long out_rs, int out_cs, int nd,
                                  long long ncell, int nrhs, double beta) {
   const long long total = ncell * nd;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total * nrhs;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int rhs = (int)(t / total);
-    const long long cj = t - rhs * total;
+  for (long long cj = blockIdx.x * (long long)blockDim.x + threadIdx.x; cj < total;
+       cj += (long long)gridDim.x * blockDim.x) {
     const long long cell = cj / nd;
     const int j = (int)(cj - cell * nd);
-    const int c0 = gath[2 * cj], c1 = gath[2 * cj + 1];
-    const double* l = lam + rhs * lam_rs;
-    double v = 0.0;
-    if (c0 != 0) {
-      const int row = (c0 > 0 ? c0 : -c0) - 1;
-      const double x = scale ? scale[row] * l[row] : l[row];
-      v = c0 > 0 ? x : -x;
+    const int2 cc = reinterpret_cast<const int2*>(gath)[cj];
+    const int row0 = (cc.x > 0 ? cc.x : -cc.x) - 1, row1 = (cc.y > 0 ? cc.y : -cc.y) - 1;
+    for (int rhs = 0; rhs < nrhs; ++rhs) {
+      const double* l = lam + rhs * lam_rs;
+      double v = 0.0;
+      if (cc.x != 0) {
+        const double x = dinfo ? d_scaled(l, dinfo, row0, d) : l[row0];
+        v = cc.x > 0 ? x : -x;
+      }
+      if (cc.y != 0) {
+        const double x = dinfo ? d_scaled(l, dinfo, row1, d) : l[row1];
+        v += cc.y > 0 ? x : -x;
+      }
+      double* o = out + rhs * out_rs + cell * out_cs + j;
+      *o = (beta == 0.0) ? v : v + beta * (*o);
     }
-    if (c1 != 0) {
-      const int row = (c1 > 0 ? c1 : -c1) - 1;
-      const double x = scale ? scale[row] * l[row] : l[row];
-      v += c1 > 0 ? x : -x;
-    }
-    double* o = out + rhs * out_rs + cell * out_cs + j;
-    *o = (beta == 0.0) ? v : v + beta * (*o);
   }
 }
 
+// (B y)_row: the two signed terms of one multiplier row.
+__device__ __forceinline__ double b_row(const int* __restrict__ scat, const double* __restrict__ y,
+                                        int y_cs, int nd, long long row) {
+  double v = 0.0;
+  const int c0 = scat[2 * row], c1 = scat[2 * row + 1];
+  if (c0 != 0) {
+    const long long idx = (c0 > 0 ? c0 : -c0) - 1;
+    const long long cell = idx / nd;
+    const double x = y[cell * y_cs + (idx - cell * nd)];
+    v = c0 > 0 ? x : -x;
+  }
+  if (c1 != 0) {
+    const long long idx = (c1 > 0 ? c1 : -c1) - 1;
+    const long long cell = idx / nd;
+    const double x = y[cell * y_cs + (idx - cell * nd)];
+    v += c1 > 0 ? x : -x;
+  }
+  return v;
+}
+
+// z = alpha B y + beta z, or alpha D B y + beta z when dinfo is given.  One thread per row for
+// every RHS: the row's codes are read once.
 __global__ void scatter_B_kernel(const int* __restrict__ scat, const double* __restrict__ yd,
-                                 long long y_rs, int y_cs, int nd, const double* __restrict__ scale,
-                                 double* __restrict__ out, long long out_rs, long long L,
+                                 long long y_rs, int y_cs, int nd, const int* __restrict__ dinfo,
+                                 int d, double* __restrict__ out, long long out_rs, long long L,
                                  double alpha, double beta, int nrhs) {
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < L * nrhs;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int rhs = (int)(t / L);
-    const long long row = t - rhs * L;
-    const double* y = yd + rhs * y_rs;
-    double v = 0.0;
-    const int c0 = scat[2 * row], c1 = scat[2 * row + 1];
-    if (c0 != 0) {
-      const long long idx = (c0 > 0 ? c0 : -c0) - 1;
-      const long long cell = idx / nd;
-      const double x = y[cell * y_cs + (idx - cell * nd)];
-      v = c0 > 0 ? x : -x;
+  for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < L;
+       row += (long long)gridDim.x * blockDim.x) {
+    const int code = dinfo ? dinfo[row] : 0;
+    const int n = code >> 8, q = code & 0xff;
+    for (int rhs = 0; rhs < nrhs; ++rhs) {
+      const double* y = yd + rhs * y_rs;
+      double v;
+      if (n == 0) {
+        v = b_row(scat, y, y_cs, nd, row);
+      } else {
+        v = 0.0;
+        for (int b = 0; b < n; ++b) v += tinv(q, b, n) * b_row(scat, y, y_cs, nd, row + (long long)(b - q) * d);
+      }
+      double* o = out + rhs * out_rs + row;
+      *o = (beta == 0.0) ? alpha * v : alpha * v + beta * (*o);
     }
-    if (c1 != 0) {
-      const long long idx = (c1 > 0 ? c1 : -c1) - 1;
-      const long long cell = idx / nd;
-      const double x = y[cell * y_cs + (idx - cell * nd)];
-      v += c1 > 0 ? x : -x;
-    }
-    if (scale) v *= scale[row];
-    double* o = out + rhs * out_rs + row;
-    *o = (beta == 0.0) ? alpha * v : alpha * v + beta * (*o);
   }
 }
 
@@ -215,6 +253,15 @@ __global__ void copy_scale_kernel(const double* __restrict__ x, double* __restri
   }
 }
 
+// flag |= 1 if any x[i] is NaN or +-Inf (input validation of the C entry points)
+__global__ void nonfinite_kernel(const double* __restrict__ x, long long n, int* __restrict__ flag) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    if (!isfinite(x[i])) {
+      atomicOr(flag, 1);
+      return;
+    }
+}
+
 inline int grid_for(long long work, int threads = 256) {
   long long g = (work + threads - 1) / threads;
   if (g > 152LL * 16) g = 152LL * 16;
@@ -224,21 +271,21 @@ inline int grid_for(long long work, int threads = 256) {
 
 }  // namespace
 
-fetidp_status k_gather_BT(Ctx& c, const double* lam, long long lam_rs, const double* scale,
+fetidp_status k_gather_BT(Ctx& c, const double* lam, long long lam_rs, const int* dinfo,
                           CellVec out, int nrhs, double beta) {
-  const long long work = c.N * c.nd * nrhs;
+  const long long work = c.N * c.nd;
   ProfScope ps(c, FETIDP_K_MAPS, 0.0, (double)nrhs * (c.L * 8.0 + c.N * c.nd * 8.0) + c.N * c.nd * 8.0);
-  gather_BT_kernel<<<grid_for(work), 256, 0, c.stream>>>(c.gath, lam, lam_rs, scale, out.p, out.rs,
+  gather_BT_kernel<<<grid_for(work), 256, 0, c.stream>>>(c.gath, lam, lam_rs, dinfo, c.d, out.p, out.rs,
                                                           out.cs, c.nd, c.N, nrhs, beta);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }
 
-fetidp_status k_scatter_B(Ctx& c, CCellVec yd, double* out, long long out_rs, const double* scale,
+fetidp_status k_scatter_B(Ctx& c, CCellVec yd, double* out, long long out_rs, const int* dinfo,
                           double alpha, double beta, int nrhs) {
   ProfScope ps(c, FETIDP_K_MAPS, 0.0, (double)nrhs * (c.L * 8.0 + c.N * c.nd * 8.0) + c.L * 8.0);
-  scatter_B_kernel<<<grid_for(c.L * nrhs), 256, 0, c.stream>>>(
-      c.scat, yd.p, yd.rs, yd.cs, c.nd, scale, out, out_rs, c.L, alpha, beta, nrhs);
+  scatter_B_kernel<<<grid_for(c.L), 256, 0, c.stream>>>(
+      c.scat, yd.p, yd.rs, yd.cs, c.nd, dinfo, c.d, out, out_rs, c.L, alpha, beta, nrhs);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }
@@ -307,6 +354,17 @@ fetidp_status k_copy_scale(Ctx& c, const double* x, double* y, long long len, in
   ProfScope ps(c, FETIDP_K_VECTOR, (double)len * nrhs, 16.0 * len * nrhs);
   copy_scale_kernel<<<grid_for(len * nrhs), 256, 0, c.stream>>>(x, y, len, nrhs, xs, ys, s_dev,
                                                                  s_host);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+}  // namespace fetidp
+
+namespace fetidp {
+
+fetidp_status k_nonfinite(Ctx& c, const double* x, long long n, int* flag) {
+  if (n <= 0) return FETIDP_OK;
+  nonfinite_kernel<<<grid_for(n), 256, 0, c.stream>>>(x, n, flag);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }

@@ -6,6 +6,7 @@
 // traces of Eq. 42 (one GEMM against the snapshot matrix) and the ROM local
 // operators of Eq. 43.
 #include <chrono>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -194,6 +195,21 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
       set_error("missing loads or radii"); return FETIDP_EINVAL;
     }
     if (q.n_rb < 1 || q.n_rb > 64) { set_error("n_rb must be in [1, 64]"); return FETIDP_EINVAL; }
+    if (q.E_solid < 0.0 || q.E_void < 0.0) { set_error("negative Young's modulus"); return FETIDP_EINVAL; }
+    if (q.E_solid == 0.0 && q.E_void == 0.0) {
+      set_error("E_solid = E_void = 0: every cell stiffness is zero");
+      return FETIDP_ESINGULAR;
+    }
+    {
+      // non-finite host data would propagate silently into every operator
+      bool fin = std::isfinite(q.nu) && std::isfinite(q.E_solid) && std::isfinite(q.E_void) &&
+                 std::isfinite(q.mask_width) && std::isfinite(q.tol_rb);
+      for (int k = 0; k < 8; ++k) fin = fin && std::isfinite(q.map_params[k]);
+      const long long nq = (long long)q.cells[0] * q.cells[1] * q.cells[2];
+      for (long long k = 0; k < nq && fin; ++k) fin = std::isfinite(q.r_cell[k]);
+      for (int k = 0; k < q.n_loads * q.dim && fin; ++k) fin = std::isfinite(q.load_dir[k]);
+      if (!fin) { set_error("non-finite value in the problem data"); return FETIDP_EINVAL; }
+    }
     if (q.clamp_axis < 0 || q.clamp_axis >= q.dim) { set_error("bad clamp axis"); return FETIDP_EINVAL; }
     if (!(q.nu > -1.0 && q.nu < 0.5)) { set_error("nu out of range"); return FETIDP_EINVAL; }
     if (q.mask_kind < 0 || q.mask_kind > 2 || (q.dim == 2) != (q.mask_kind == 0)) {
@@ -206,8 +222,21 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
       return FETIDP_EINVAL;
     }
   }
-  if (o.max_outer < 1 || o.max_inner < 1) { set_error("bad iteration limits"); return FETIDP_EINVAL; }
+  if (o.max_outer < 1 || o.max_inner < 1 || o.restart < 0 || o.fixed_outer < 0 || o.fixed_inner < 0) {
+    set_error("bad iteration limits");
+    return FETIDP_EINVAL;
+  }
+  if (o.wait_budget_ns <= 0) { set_error("wait_budget_ns must be > 0"); return FETIDP_EINVAL; }
+  if (o.mixed_assembled < -1 || o.mixed_assembled > 1) { set_error("mixed_assembled must be -1, 0 or 1"); return FETIDP_EINVAL; }
+  if (!(std::isfinite(o.tol_outer) && std::isfinite(o.tol_inner) && std::isfinite(o.tol_inner_mixed) &&
+        o.tol_outer >= 0.0 && o.tol_inner >= 0.0 && o.tol_inner_mixed >= 0.0)) {
+    set_error("tolerances must be finite and >= 0");
+    return FETIDP_EINVAL;
+  }
   c.opt = o;
+  c.kry = o.restart > 0 ? o.restart : std::min(o.max_outer, 30);
+  if (o.fixed_outer > c.kry) c.kry = o.fixed_outer;
+  c.wait_ns = (unsigned long long)o.wait_budget_ns;
   c.mixed = o.precision == FETIDP_MIXED_BF16;
   if (c.mixed && o.tc_split != 1 && o.tc_split != 3) { set_error("tc_split must be 1 or 3"); return FETIDP_EINVAL; }
   if (!(o.gram_drop_mixed >= 0.0 && o.gram_drop_mixed < 1.0)) {
@@ -258,17 +287,17 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
   const int nn1 = e + 1;
   std::vector<int> gath((size_t)c.N * c.nd * 2, 0);
   std::vector<int> scat;
-  std::vector<double> Dw;
+  std::vector<int> dinfo;   // per row: (chain rows n of its node << 8) | chain position q
   {
     // about one multiplier per dual DOF of every cell and component (upper bound for reserve)
     const size_t est = (size_t)c.N * c.nd;
     scat.reserve(2 * est);
-    Dw.reserve(est);
+    dinfo.reserve(est);
   }
   for (int bl = 0; bl < nprob; ++bl) {
   const fetidp_problem& pl = probs[bl];
   const long long cell0 = c.lat[bl].cell0;
-  c.lat[bl].L0 = (long long)Dw.size();
+  c.lat[bl].L0 = (long long)dinfo.size();
   const int nx = pl.cells[0], ny = pl.cells[1], nz = pl.cells[2];
   const long long gd[3] = {(long long)nx * e + 1, (long long)ny * e + 1, d == 3 ? (long long)nz * e + 1 : 1};
   const long long clamp_coord = pl.clamp_side ? (long long)pl.cells[pl.clamp_axis] * e : 0;
@@ -318,32 +347,32 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
           for (int q = 0; q < mult; ++q)
             for (int comp = 0; comp < d; ++comp) {
               const auto& ow = own[q];
-              const long long row = (long long)Dw.size();
+              const long long row = (long long)dinfo.size();
               const int j = ow.second * d + comp;
               scat.push_back((int)(ow.first * c.nd + j + 1));
               scat.push_back(0);
-              Dw.push_back(1.0);
+              dinfo.push_back(0);
               add_gath(ow.first, j, (int)(row + 1));
             }
         } else {
           for (int q = 0; q + 1 < mult; ++q)
             for (int comp = 0; comp < d; ++comp) {
-              const long long row = (long long)Dw.size();
+              const long long row = (long long)dinfo.size();
               const int j1 = own[q].second * d + comp, j2 = own[q + 1].second * d + comp;
               scat.push_back((int)(own[q].first * c.nd + j1 + 1));
               scat.push_back(-(int)(own[q + 1].first * c.nd + j2 + 1));
-              Dw.push_back(1.0 / mult);
+              dinfo.push_back(((mult - 1) << 8) | q);
               add_gath(own[q].first, j1, (int)(row + 1));
               add_gath(own[q + 1].first, j2, -(int)(row + 1));
             }
         }
       }
-  c.lat[bl].nL = (long long)Dw.size() - c.lat[bl].L0;
+  c.lat[bl].nL = (long long)dinfo.size() - c.lat[bl].L0;
   }
-  c.L = (long long)Dw.size();
+  c.L = (long long)dinfo.size();
   FD_TRY(upload(c, &c.gath, gath));
   FD_TRY(upload(c, &c.scat, scat));
-  FD_TRY(upload(c, &c.Dw, Dw));
+  FD_TRY(upload(c, &c.dinfo, dinfo));
   phase("multiplier maps");
 
   // ---------------------------------------------------------------- primal DOF (Eq. 18)
@@ -639,6 +668,19 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
     const int split = o.tc_split == 3 ? 3 : 1;
     const long long ncols = c.N * c.m;
     FD_TRY(tc_pack_operator(c, c.opKinv, c.Kinv, (long long)nr * nr, nr, 0, 0, nr, nr, nrb, true, split));
+    // F_dd_ring and S_dd_ring of the inner PCG: assembled per cell in FP32 for large cells (streamed,
+    // HBM-bound), principal form on the tensor cores otherwise
+    c.asm_f32 = o.mixed_assembled > 0 || (o.mixed_assembled < 0 && nd > 128);
+    if (c.asm_f32) {
+      c.ld_f = (nd + 3) & ~3;
+      const size_t fbytes = sizeof(float) * (size_t)c.N * nd * c.ld_f;
+      FD_TRY(dalloc(c, reinterpret_cast<void**>(&c.Fdd_f), fbytes));
+      FD_TRY(dalloc(c, reinterpret_cast<void**>(&c.Sdd_f), fbytes));
+      FD_CUDA(cudaMemsetAsync(c.Fdd_f, 0, fbytes, c.stream));   // row padding stays zero
+      FD_CUDA(cudaMemsetAsync(c.Sdd_f, 0, fbytes, c.stream));
+      FD_TRY(k_rom_combine_f32(c, c.Kinv, (long long)nr * nr, nr, ni, ni, nd, nd, c.delta, c.Fdd_f, c.ld_f));
+      FD_TRY(k_rom_combine_f32(c, c.Sdd, (long long)nd * nd, nd, 0, 0, nd, nd, c.alpha, c.Sdd_f, c.ld_f));
+    }
     FD_TRY(tc_comb_pack(c, c.cFdd, c.Kinv, (long long)nr * nr, nr, ni, ni, nd, nullptr, 0, 0, 0, 0, 0, nd, nrb,
                         split));
     FD_TRY(tc_comb_pack(c, c.cSdd, c.Sdd, (long long)nd * nd, nd, 0, 0, nd, nullptr, 0, 0, 0, 0, 0, nd, nrb, split));
@@ -715,15 +757,19 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
   FD_TRY(dalloc_t(c, &c.w_P2, m * c.nP + 1));
   FD_TRY(dalloc_t(c, &c.w_zP, m * c.nP + 1));
   FD_TRY(dalloc_t(c, &c.w_L1, m * c.L + 1));
-  FD_TRY(dalloc_t(c, &c.w_R, m * c.N * nrb * nr));
-  FD_TRY(dalloc_t(c, &c.w_KR, m * c.N * nrb * nr));
+  // local ROM bases R and K_s R (Eq. 46): FP64 in the FP64 path, FP32 in the mixed path
+  const size_t rom_elems = m * c.N * nrb * nr;
+  FD_TRY(dalloc_t(c, &c.w_R, c.mixed ? (rom_elems + 1) / 2 : rom_elems));
+  FD_TRY(dalloc_t(c, &c.w_KR, c.mixed ? (rom_elems + 1) / 2 : rom_elems));
   FD_TRY(dalloc_t(c, &c.w_tot, 3 * m * c.ntot));
-  FD_TRY(dalloc_t(c, &c.V, (size_t)(o.max_outer + 1) * m * c.ntot));
-  FD_TRY(dalloc_t(c, &c.Z, (size_t)o.max_outer * m * c.ntot));
+  // Krylov storage: one restart cycle (c.kry basis vectors and preconditioned vectors per RHS)
+  FD_TRY(dalloc_t(c, &c.V, (size_t)(c.kry + 1) * m * c.ntot));
+  FD_TRY(dalloc_t(c, &c.Z, (size_t)c.kry * m * c.ntot));
   FD_TRY(dalloc_t(c, &c.pcg, 6 * m * c.L + 1));
-  FD_TRY(dalloc_t(c, &c.red, (size_t)m * (o.max_outer + 2) * 304));
-  FD_TRY(dalloc_t(c, &c.scal, 64 * m + (size_t)m * (o.max_outer + 2) * 2));
-  FD_CUDA(cudaMallocHost(&c.h_scal, sizeof(double) * (64 * m + (size_t)m * (o.max_outer + 2) * 2)));
+  FD_TRY(dalloc(c, reinterpret_cast<void**>(&c.chk), sizeof(int)));
+  FD_TRY(dalloc_t(c, &c.red, (size_t)m * (c.kry + 2) * 304));
+  FD_TRY(dalloc_t(c, &c.scal, 64 * m + (size_t)m * (c.kry + 2) * 2));
+  FD_CUDA(cudaMallocHost(&c.h_scal, sizeof(double) * (64 * m + (size_t)m * (c.kry + 2) * 2)));
   FD_CUDA(cudaStreamSynchronize(c.stream));
   phase("workspace");
   c.t_setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -18,6 +18,8 @@
 #include <mutex>
 #include <string>
 
+#include <initializer_list>
+
 #include "common.cuh"
 
 namespace fetidp {
@@ -246,7 +248,9 @@ fetidp_status op_apply_F(Ctx& c, const double* lam, long long lam_rs, double* y,
   const int m = c.m, nd = c.nd, np = c.np, nr = c.nr, ni = c.ni;
   CellVec g{c.w_d1, c.N * nd, nd}, yd{c.w_d2, c.N * nd, nd}, cp{c.w_p1, c.N * np, np};
   FD_TRY(k_gather_BT(c, lam, lam_rs, nullptr, g, m, 0.0));
-  if (c.mixed)
+  if (c.asm_f32)
+    FD_TRY(k_cell_gemm_f32(c, c.Fdd_f, c.ld_f, nd, nd, cview(g), yd, 1.0, 0.0, m));
+  else if (c.mixed)
     FD_TRY(tc_comb_apply(c, c.cFdd, cview(g), c.delta, c.delta, yd.p, true, yd.rs, yd.cs, 1.0, 0.0, m, c.N));
   else
     FD_TRY(cell_op(c, c.Fdd_c, (long long)nd * nd, nd, nd, nd, cview(g), yd, 1.0, 0.0));
@@ -264,12 +268,14 @@ fetidp_status op_apply_F(Ctx& c, const double* lam, long long lam_rs, double* y,
 fetidp_status op_apply_MD(Ctx& c, const double* r, long long r_rs, double* z, long long z_rs) {
   const int m = c.m, nd = c.nd;
   CellVec g{c.w_d1, c.N * nd, nd}, yd{c.w_d2, c.N * nd, nd};
-  FD_TRY(k_gather_BT(c, r, r_rs, c.Dw, g, m, 0.0));
-  if (c.mixed)
+  FD_TRY(k_gather_BT(c, r, r_rs, c.dinfo, g, m, 0.0));
+  if (c.asm_f32)
+    FD_TRY(k_cell_gemm_f32(c, c.Sdd_f, c.ld_f, nd, nd, cview(g), yd, 1.0, 0.0, m));
+  else if (c.mixed)
     FD_TRY(tc_comb_apply(c, c.cSdd, cview(g), c.alpha, c.alpha, yd.p, true, yd.rs, yd.cs, 1.0, 0.0, m, c.N));
   else
     FD_TRY(cell_op(c, c.Sdd_c, (long long)nd * nd, nd, nd, nd, cview(g), yd, 1.0, 0.0));
-  FD_TRY(k_scatter_B(c, cview(yd), z, z_rs, c.Dw, 1.0, 0.0, m));
+  FD_TRY(k_scatter_B(c, cview(yd), z, z_rs, c.dinfo, 1.0, 0.0, m));
   return FETIDP_OK;
 }
 
@@ -303,7 +309,7 @@ fetidp_status local_rom(Ctx& c, CCellVec vR, CellVec xR) {
     float* Rf = reinterpret_cast<float*>(c.w_R);
     float* KRf = reinterpret_cast<float*>(c.w_KR);
     const long long rs = c.N * nrb * nr;
-    const long long rext = 2 * (long long)m * rs;   // float capacity of the double-sized buffers
+    const long long rext = (long long)m * rs;       // floats held by each buffer
     FD_TRY(tc_apply(c, c.opKinv, vR, nullptr, Rf, false, rs, nrb * nr, nr, 1.0, 0.0, m, c.N, rext));
     FD_TRY(fd_check_tc("local ROM basis (tensor cores)"));
     FD_TRY(k_apply_K_f32(c, Rf, rs, nrb * nr, KRf, rs, nrb * nr, nrb, m, true, true, rext));
@@ -573,10 +579,10 @@ struct OuterResult {
 // while it is above tol_outer (the least-squares estimate and the true residual drift
 // apart when the preconditioner changes between applications).
 fetidp_status fgmres(Ctx& c, double* xout, OuterResult& res) {
-  const int m = c.m, mo = c.opt.max_outer;
+  const int m = c.m, mo = c.kry;      // cycle length = Krylov storage
   const long long nt = c.ntot, mnt = (long long)m * nt;
   const bool fixed = c.opt.fixed_outer > 0;
-  const int max_cycles = fixed ? 1 : 8;
+  const int max_total = fixed ? c.opt.fixed_outer : c.opt.max_outer;
   double* dots1 = c.scal + 64 * m;
   double* dots2 = dots1 + (size_t)m * (mo + 2);
   double* rcur = c.w_tot + mnt;        // residual of the current cycle
@@ -596,7 +602,7 @@ fetidp_status fgmres(Ctx& c, double* xout, OuterResult& res) {
   std::vector<std::vector<double>> g(m, std::vector<double>(mo + 1, 0.0)), cs(m, std::vector<double>(mo)),
       sn(m, std::vector<double>(mo));
   auto Hij = [&](int r, int i, int j) -> double& { return H[r][(size_t)i * mo + j]; };
-  for (int cycle = 0; cycle < max_cycles; ++cycle) {
+  while (total_its < max_total) {
     std::vector<char> active(m, 0);
     std::vector<double> target(m, 0.0);
     int nact = 0;
@@ -619,7 +625,7 @@ fetidp_status fgmres(Ctx& c, double* xout, OuterResult& res) {
     std::vector<int> k_used(m, 0);
     std::vector<char> live = active;
     int j = 0;
-    for (j = 0; j < mo && nact > 0; ++j) {
+    for (j = 0; j < mo && nact > 0 && total_its < max_total; ++j) {
       double* Vj = c.V + (size_t)j * mnt;
       double* Zj = c.Z + (size_t)j * mnt;
       double* w = c.V + (size_t)(j + 1) * mnt;
@@ -740,13 +746,47 @@ static fetidp_status enter(fetidp_ctx* ctx) {
   return FETIDP_OK;
 }
 
+// Input validation of the vector entry points (option check_inputs): null pointers, then NaN/Inf
+// in each input of n doubles.  Synchronises the stream.
+struct InVec { const double* p; long long n; const char* name; };
+static fetidp_status check_inputs(Ctx& c, std::initializer_list<InVec> ins, const void* out) {
+  for (const InVec& v : ins)
+    if (!v.p) { set_error(std::string("null input ") + v.name); return FETIDP_EINVAL; }
+  if (!out) { set_error("null output"); return FETIDP_EINVAL; }
+  if (!c.opt.check_inputs) return FETIDP_OK;
+  for (const InVec& v : ins) {
+    FD_CUDA(cudaMemsetAsync(c.chk, 0, sizeof(int), c.stream));
+    FD_TRY(k_nonfinite(c, v.p, v.n, c.chk));
+    int h = 0;
+    FD_CUDA(cudaMemcpyAsync(&h, c.chk, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    FD_CUDA(cudaStreamSynchronize(c.stream));
+    if (h) { set_error(std::string("non-finite value in ") + v.name); return FETIDP_EINVAL; }
+  }
+  return FETIDP_OK;
+}
+
+// After a call that ran tensor-core kernels: an expired device wait gives ETIMEOUT (the flag is
+// cleared, so the context stays usable).  Only with check_inputs, which already synchronises.
+static fetidp_status check_waits(Ctx& c, fetidp_status st) {
+  if (!c.mixed || !c.tc_err || !c.opt.check_inputs) return st;
+  int h = 0;
+  FD_CUDA(cudaMemcpyAsync(&h, c.tc_err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  FD_CUDA(cudaStreamSynchronize(c.stream));
+  if (h) {
+    FD_CUDA(cudaMemsetAsync(c.tc_err, 0, sizeof(int), c.stream));
+    set_error("a tensor-core kernel's device wait exceeded wait_budget_ns (code " + std::to_string(h) + ")");
+    return FETIDP_ETIMEOUT;
+  }
+  return st;
+}
+
 extern "C" {
 
 void fetidp_default_options(fetidp_options* o) {
   if (!o) return;
   o->tol_outer = 1e-8;
   o->tol_inner = 1e-11;
-  o->max_outer = 50;
+  o->max_outer = 100;
   o->max_inner = 1000;
   o->precision = FETIDP_FP64;
   o->fixed_outer = 0;
@@ -755,6 +795,10 @@ void fetidp_default_options(fetidp_options* o) {
   o->tol_inner_mixed = 1e-6;
   o->gram_drop_mixed = 1e-9;
   o->profile_mask = 0;
+  o->restart = 0;
+  o->wait_budget_ns = 1000000000LL;
+  o->check_inputs = 1;
+  o->mixed_assembled = -1;
 }
 
 const char* fetidp_status_string(fetidp_status s) {
@@ -832,6 +876,17 @@ fetidp_status fetidp_tc_selfcheck_static(int M, int K, int N, double* rel_err, v
   FD_CUDA(cudaGetDevice(&c.device));
   c.stream = static_cast<cudaStream_t>(stream);
   return tc_selfcheck_static(c, M, K, N, rel_err);
+}
+
+fetidp_status fetidp_wait_selfcheck(long long wait_budget_ns, void* stream, double* waited_s) {
+  if (wait_budget_ns <= 0 || wait_budget_ns > 10000000000LL) {
+    set_error("wait_budget_ns must lie in (0, 1e10]");
+    return FETIDP_EINVAL;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  const fetidp_status st = wait_selfcheck((unsigned long long)wait_budget_ns, static_cast<cudaStream_t>(stream));
+  if (waited_s) *waited_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return st;
 }
 
 static fetidp_status profile_enable(Ctx& c, unsigned mask) {
@@ -941,29 +996,36 @@ fetidp_status fetidp_sizes(const fetidp_ctx* ctx, long long o[12]) {
 
 fetidp_status fetidp_apply_F(fetidp_ctx* ctx, const double* lambda, double* y) {
   FD_TRY(enter(ctx));
-  return op_apply_F(ctx->c, lambda, ctx->c.L, y, ctx->c.L);
+  Ctx& c = ctx->c;
+  FD_TRY(check_inputs(c, {{lambda, (long long)c.m * c.L, "lambda"}}, y));
+  return check_waits(c, op_apply_F(c, lambda, c.L, y, c.L));
 }
 
 fetidp_status fetidp_precond(fetidp_ctx* ctx, const double* r, double* z) {
   FD_TRY(enter(ctx));
-  return op_apply_MD(ctx->c, r, ctx->c.L, z, ctx->c.L);
+  Ctx& c = ctx->c;
+  FD_TRY(check_inputs(c, {{r, (long long)c.m * c.L, "r"}}, z));
+  return check_waits(c, op_apply_MD(c, r, c.L, z, c.L));
 }
 
 fetidp_status fetidp_gather_BT(fetidp_ctx* ctx, const double* lambda, double* x_d) {
   FD_TRY(enter(ctx));
   Ctx& c = ctx->c;
+  FD_TRY(check_inputs(c, {{lambda, (long long)c.m * c.L, "lambda"}}, x_d));
   return k_gather_BT(c, lambda, c.L, nullptr, CellVec{x_d, c.N * c.nd, c.nd}, c.m, 0.0);
 }
 
 fetidp_status fetidp_scatter_B(fetidp_ctx* ctx, const double* y_d, double* z) {
   FD_TRY(enter(ctx));
   Ctx& c = ctx->c;
+  FD_TRY(check_inputs(c, {{y_d, (long long)c.m * c.N * c.nd, "y_d"}}, z));
   return k_scatter_B(c, CCellVec{y_d, c.N * c.nd, c.nd}, z, c.L, nullptr, 1.0, 0.0, c.m);
 }
 
 fetidp_status fetidp_apply_K(fetidp_ctx* ctx, const double* u, double* y) {
   FD_TRY(enter(ctx));
   Ctx& c = ctx->c;
+  FD_TRY(check_inputs(c, {{u, (long long)c.m * c.N * c.n, "u"}}, y));
   return k_apply_K(c, CCellVec{u, c.N * c.n, c.n}, CellVec{y, c.N * c.n, c.n}, 1, c.m, false, false,
                    c.snap, 0.0);
 }
@@ -971,6 +1033,7 @@ fetidp_status fetidp_apply_K(fetidp_ctx* ctx, const double* u, double* y) {
 fetidp_status fetidp_coarse_solve(fetidp_ctx* ctx, const double* b, double* x) {
   FD_TRY(enter(ctx));
   Ctx& c = ctx->c;
+  FD_TRY(check_inputs(c, {{b, (long long)c.m * c.nP, "b"}}, x));
   return coarse_solve(c, b, c.nP, x, c.nP, c.m);
 }
 
@@ -978,17 +1041,22 @@ fetidp_status fetidp_local_rom_solve(fetidp_ctx* ctx, const double* v, double* x
   FD_TRY(enter(ctx));
   Ctx& c = ctx->c;
   const long long ext = (long long)c.m * c.N * c.nr;
-  return local_rom(c, CCellVec{v, c.N * c.nr, c.nr, ext}, CellVec{x, c.N * c.nr, c.nr, ext});
+  FD_TRY(check_inputs(c, {{v, ext, "v"}}, x));
+  return check_waits(c, local_rom(c, CCellVec{v, c.N * c.nr, c.nr, ext}, CellVec{x, c.N * c.nr, c.nr, ext}));
 }
 
 fetidp_status fetidp_apply_A(fetidp_ctx* ctx, const double* x, double* y) {
   FD_TRY(enter(ctx));
-  return op_apply_A(ctx->c, x, y);
+  Ctx& c = ctx->c;
+  FD_TRY(check_inputs(c, {{x, (long long)c.m * c.ntot, "x"}}, y));
+  return op_apply_A(c, x, y);
 }
 
 fetidp_status fetidp_apply_P(fetidp_ctx* ctx, const double* x, double* y) {
   FD_TRY(enter(ctx));
-  return op_precondition(ctx->c, x, y);
+  Ctx& c = ctx->c;
+  FD_TRY(check_inputs(c, {{x, (long long)c.m * c.ntot, "x"}}, y));
+  return check_waits(c, op_precondition(c, x, y));
 }
 
 fetidp_status fetidp_rom_data(fetidp_ctx* ctx, int* sigma, double* alpha, double* pi, double* delta) {
@@ -1007,16 +1075,22 @@ static fetidp_status solve_common(fetidp_ctx* ctx, fetidp_info* info, OuterResul
   Ctx& c = ctx->c;
   auto t0 = std::chrono::steady_clock::now();
   c.inner_total = 0;
-  FD_TRY(fgmres(c, c.w_tot, r));
+  if (c.mixed) FD_CUDA(cudaMemsetAsync(c.tc_err, 0, sizeof(int), c.stream));
+  const fetidp_status st = fgmres(c, c.w_tot, r);
   FD_CUDA(cudaStreamSynchronize(c.stream));
   if (c.mixed) {
+    // an expired device wait explains whatever else went wrong (e.g. a breakdown on the garbage it
+    // left behind), so it is reported first; the flag is cleared for the next call
     int herr = 0;
     FD_CUDA(cudaMemcpy(&herr, c.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (herr != 0) {
-      set_error("tensor-core GEMM wait timed out (code " + std::to_string(herr) + ")");
+      FD_CUDA(cudaMemsetAsync(c.tc_err, 0, sizeof(int), c.stream));
+      FD_CUDA(cudaStreamSynchronize(c.stream));
+      set_error("a tensor-core kernel's device wait exceeded wait_budget_ns (code " + std::to_string(herr) + ")");
       return FETIDP_ETIMEOUT;
     }
   }
+  FD_TRY(st);
   if (info) {
     info->outer_its = r.its;
     info->inner_its_total = c.inner_total;
@@ -1063,7 +1137,7 @@ fetidp_status fetidp_solve_host(fetidp_ctx* ctx, double* u_host, double* lambda_
 fetidp_status fetidp_compliance(fetidp_ctx* ctx, const double* u, double* c_out) {
   FD_TRY(enter(ctx));
   Ctx& c = ctx->c;
-  if (!u || !c_out) { set_error("null pointer"); return FETIDP_EINVAL; }
+  FD_TRY(check_inputs(c, {{u, (long long)c.m * c.N * c.n, "u"}}, c_out));
   // scratch: the partial sums and the results live in the reduction workspace
   FD_TRY(k_compliance(c, u, c.red + (size_t)c.m * kReductionBlocks, c.red));
   FD_CUDA(cudaMemcpyAsync(c_out, c.red + (size_t)c.m * kReductionBlocks, sizeof(double) * c.m, cudaMemcpyDefault,
@@ -1075,6 +1149,8 @@ fetidp_status fetidp_compliance(fetidp_ctx* ctx, const double* u, double* c_out)
 fetidp_status fetidp_grad(fetidp_ctx* ctx, const double* u, const double* w, double* g) {
   FD_TRY(enter(ctx));
   Ctx& c = ctx->c;
+  const long long nu = (long long)c.m * c.N * c.n;
+  FD_TRY(check_inputs(c, {{u, nu, "u"}, {w ? w : u, nu, "w"}}, g));
   return k_grad(c, u, w ? w : u, g);
 }
 

@@ -16,12 +16,17 @@
 // back to the producer; all four warps drain the accumulator with tcgen05.ld.
 // Operands are pre-packed in global memory in the canonical 128-byte-swizzled
 // K-major layout, so a linear bulk copy lands the exact shared-memory image.
-// Every mbarrier wait is bounded (1 s of globaltimer): on expiry the CTA sets
-// an error flag, drains its own copies (bounded), frees TMEM and returns.
+// Every mbarrier wait is bounded by the caller's budget (wait_ns of globaltimer,
+// 1 s by default): on expiry the CTA sets an error flag and every role stops.
+// Before TMEM is freed and the CTA exits, the copy issuer waits for each of its
+// bulk copies to land and the MMA issuer commits a final barrier and waits for
+// it (every MMA issued has completed, every earlier commit has arrived).  Those
+// drain waits have their own fixed 1 s bound, independent of the budget, so even
+// a budget of 1 ns leaves no asynchronous write aimed at a CTA that has exited.
 #include <cuda_bf16.h>
 
 #include <cstdint>
-#include <mutex>
+#include <cmath>
 
 #include "common.cuh"
 
@@ -32,7 +37,7 @@ namespace {
 constexpr int TC_BM = 128;
 constexpr int TC_BK = 64;                     // bf16 elements per 128-byte row
 constexpr int A_TILE = TC_BM * TC_BK * 2;     // 16 KB
-constexpr unsigned long long kWaitNs = 1000000000ull;   // 1 s bound on every wait
+constexpr unsigned long long kDrainNs = 1000000000ull;   // fixed bound of the exit drains
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -62,15 +67,23 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait: false on timeout or when another role has aborted
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+// bounded wait: false after wait_ns of globaltimer or when another role has aborted
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          unsigned long long wait_ns) {
   const unsigned long long t0 = gtime();
   for (unsigned it = 0;; ++it) {
     if (mbar_try(bar, parity)) return true;
     if ((it & 63u) == 63u) {
       if (*abort_flag) return false;
-      if (gtime() - t0 > kWaitNs) return false;
+      if (gtime() - t0 > wait_ns) return false;
     }
+  }
+}
+// exit drain: wait for a phase that is certain to complete (an issued copy, a committed MMA
+// batch), ignoring the abort flag, bounded by kDrainNs
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
+  const unsigned long long t0 = gtime();
+  while (!mbar_try(bar, parity) && gtime() - t0 < kDrainNs) {
   }
 }
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
@@ -164,6 +177,7 @@ struct TcParams {
   long long y_b_stride;
   double alpha, beta;
   int* err;
+  unsigned long long wait_ns;          // bound of every pipeline wait
   long long a_bytes, b_bytes, y_ext;   // extents for checked builds
 };
 
@@ -210,7 +224,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(TcParams P) {
     int issued = 0;
     for (int kt = 0; kt < KT; ++kt) {
       const int s = kt % STAGES, n = kt / STAGES;
-      if (kt >= STAGES && !mbar_wait(empty0 + 8 * s, (uint32_t)((n - 1) & 1), abort_flag)) {
+      if (kt >= STAGES && !mbar_wait(empty0 + 8 * s, (uint32_t)((n - 1) & 1), abort_flag, P.wait_ns)) {
         *abort_flag = 1;
         atomicExch(P.err, 1);
         break;
@@ -230,35 +244,19 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(TcParams P) {
       bulk_g2s(smem_u32(sB + s * B_TILE), Bb + (long long)kr * B_TILE, B_TILE, full0 + 8 * s);
       ++issued;
     }
-    if (*abort_flag) {
-      // drain our own copies in flight and the MMA thread's releases (both bounded) before
-      // the CTA may exit
-      for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued; ++kt) {
-        const int s = kt % STAGES, n = kt / STAGES;
-        unsigned long long t0 = gtime();
-        while (!mbar_try(full0 + 8 * s, (uint32_t)(n & 1)) && gtime() - t0 < kWaitNs) {
-        }
-        t0 = gtime();
-        while (!mbar_try(empty0 + 8 * s, (uint32_t)(n & 1)) && gtime() - t0 < kWaitNs / 8) {
-        }
-      }
-    } else {
-      // pipeline tail: wait until the MMA thread has released the last stages.  The arrivals of
-      // tcgen05.commit on the empty barriers are asynchronous; a CTA that exits before they land
-      // would let them write into shared memory that the next kernel's CTAs already own.
-      for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued; ++kt) {
-        const int s = kt % STAGES, n = kt / STAGES;
-        if (!mbar_wait(empty0 + 8 * s, (uint32_t)(n & 1), abort_flag)) {
-          atomicExch(P.err, 5);
-          break;
-        }
-      }
-    }
+    // exit drain: every copy issued has landed (earlier stages were seen released before their
+    // slot was reused).  The MMA thread drains its own commits; without an abort the last stages'
+    // releases are also awaited here.
+    for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued; ++kt)
+      mbar_drain(full0 + 8 * (kt % STAGES), (uint32_t)((kt / STAGES) & 1));
+    for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued && !*abort_flag; ++kt)
+      if (!mbar_wait(empty0 + 8 * (kt % STAGES), (uint32_t)((kt / STAGES) & 1), abort_flag, P.wait_ns))
+        atomicExch(P.err, 5);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     for (int kt = 0; kt < KT; ++kt) {
       const int s = kt % STAGES, n = kt / STAGES;
-      if (!mbar_wait(full0 + 8 * s, (uint32_t)(n & 1), abort_flag)) {
+      if (!mbar_wait(full0 + 8 * s, (uint32_t)(n & 1), abort_flag, P.wait_ns)) {
         *abort_flag = 1;
         atomicExch(P.err, 2);
         break;
@@ -271,11 +269,14 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(TcParams P) {
         tc_mma(tmem, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), IDESC, (kt > 0 || j > 0) ? 1u : 0u);
       tc_commit(empty0 + 8 * s);
     }
+    // every MMA issued has completed and every commit above has arrived before TMEM and shared
+    // memory are released (the epilogue below may stop waiting early on an abort)
     tc_commit(done);
+    mbar_drain(done, 0u);
   }
   __syncwarp();
   // ---------------- epilogue: TMEM -> registers -> global (rows = TMEM lanes)
-  const bool ok = mbar_wait(done, 0u, abort_flag);
+  const bool ok = mbar_wait(done, 0u, abort_flag, P.wait_ns);
   tc_fence_after();
   if (!ok) atomicExch(P.err, 3);
   if (ok && !*abort_flag) {
@@ -479,6 +480,7 @@ struct TcCombParams {
   int y_cs;
   double alpha, beta;
   int* err;
+  unsigned long long wait_ns;
 };
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -497,13 +499,15 @@ __global__ void __launch_bounds__(192, 1) tc_comb_kernel(TcCombParams P) {
   uint8_t* sB = smem;
   uint8_t* sA = sB + (size_t)KX * B_TILE;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sA + (size_t)S * P.tps * A_TILE);
-  // bars: aFull[kCombStages], aEmpty[kCombStages], bFull, accFull[2], accEmpty[2]
+  // bars: aFull[kCombStages], aEmpty[kCombStages], bFull, accFull[2], accEmpty[2], (TMEM slot and
+  // abort flag), done
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kCombStages + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* sCoef = reinterpret_cast<float*>(bars + kCombBars);   // [set][op][column], FP32
   const uint32_t aFull = smem_u32(bars), aEmpty = smem_u32(bars + kCombStages);
   const uint32_t bFull = smem_u32(bars + 2 * kCombStages);
   const uint32_t accFull = smem_u32(bars + 2 * kCombStages + 1), accEmpty = smem_u32(bars + 2 * kCombStages + 3);
+  const uint32_t done = smem_u32(bars + 2 * kCombStages + 6);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nt = blockIdx.x, mt = blockIdx.y;
   // the tile's combination coefficients, once: 1 without coefficients, 0 past the last column
@@ -528,6 +532,7 @@ __global__ void __launch_bounds__(192, 1) tc_comb_kernel(TcCombParams P) {
       mbar_init(accFull + 8 * b, 1);
       mbar_init(accEmpty + 8 * b, 128);
     }
+    mbar_init(done, 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -557,7 +562,7 @@ __global__ void __launch_bounds__(192, 1) tc_comb_kernel(TcCombParams P) {
       int issued = 0;
       for (int c = 0; c < nchunk; ++c) {
         const int s = c % S, n = c / S;
-        if (c >= S && !mbar_wait(aEmpty + 8 * s, (uint32_t)((n - 1) & 1), abort_flag)) {
+        if (c >= S && !mbar_wait(aEmpty + 8 * s, (uint32_t)((n - 1) & 1), abort_flag, P.wait_ns)) {
           *abort_flag = 1;
           atomicExch(P.err, 11);
           break;
@@ -570,30 +575,23 @@ __global__ void __launch_bounds__(192, 1) tc_comb_kernel(TcCombParams P) {
         bulk_g2s(smem_u32(sA + (size_t)s * stage_bytes), src, (uint32_t)(ntl * A_TILE), aFull + 8 * s);
         ++issued;
       }
-      // tail: every stage released (and, on abort, every copy landed) before the CTA may exit
-      for (int c = (issued > S ? issued - S : 0); c < issued; ++c) {
-        const int s = c % S, n = c / S;
-        unsigned long long t0 = gtime();
-        while (!mbar_try(aFull + 8 * s, (uint32_t)(n & 1)) && gtime() - t0 < kWaitNs) {
-        }
-        t0 = gtime();
-        while (!mbar_try(aEmpty + 8 * s, (uint32_t)(n & 1)) && gtime() - t0 < kWaitNs) {
-        }
-      }
-      {
-        const unsigned long long t0 = gtime();
-        while (!mbar_try(bFull, 0u) && gtime() - t0 < kWaitNs) {
-        }
-      }
+      // exit drain: every copy issued has landed (the MMA thread drains its own commits; without
+      // an abort the last stages' releases are also awaited here)
+      for (int c = (issued > S ? issued - S : 0); c < issued; ++c)
+        mbar_drain(aFull + 8 * (c % S), (uint32_t)((c / S) & 1));
+      mbar_drain(bFull, 0u);
+      for (int c = (issued > S ? issued - S : 0); c < issued && !*abort_flag; ++c)
+        if (!mbar_wait(aEmpty + 8 * (c % S), (uint32_t)((c / S) & 1), abort_flag, P.wait_ns))
+          atomicExch(P.err, 16);
     }
   } else if (warp == 5) {
     if (lane == 0) {
-      bool ok = mbar_wait(bFull, 0u, abort_flag);
+      bool ok = mbar_wait(bFull, 0u, abort_flag, P.wait_ns);
       if (!ok) { *abort_flag = 1; atomicExch(P.err, 12); }
       int c = 0;
       for (int k = 0; ok && k < P.nops; ++k) {
         const int b = k & 1;
-        if (k >= 2 && !mbar_wait(accEmpty + 8 * b, (uint32_t)(((k >> 1) - 1) & 1), abort_flag)) {
+        if (k >= 2 && !mbar_wait(accEmpty + 8 * b, (uint32_t)(((k >> 1) - 1) & 1), abort_flag, P.wait_ns)) {
           *abort_flag = 1;
           atomicExch(P.err, 13);
           ok = false;
@@ -604,7 +602,7 @@ __global__ void __launch_bounds__(192, 1) tc_comb_kernel(TcCombParams P) {
         const uint32_t dst = tmem + (uint32_t)(b * BN);
         for (int cc = 0; ok && cc < cpo; ++cc, ++c) {
           const int s = c % S, n = c / S;
-          if (!mbar_wait(aFull + 8 * s, (uint32_t)(n & 1), abort_flag)) {
+          if (!mbar_wait(aFull + 8 * s, (uint32_t)(n & 1), abort_flag, P.wait_ns)) {
             *abort_flag = 1;
             atomicExch(P.err, 14);
             ok = false;
@@ -630,6 +628,10 @@ __global__ void __launch_bounds__(192, 1) tc_comb_kernel(TcCombParams P) {
         }
         if (ok) tc_commit(accFull + 8 * b);
       }
+      // every MMA issued has completed and every commit above has arrived before TMEM and
+      // shared memory are released
+      tc_commit(done);
+      mbar_drain(done, 0u);
     }
   } else {
     // ---------------- epilogue warps 0-3: one row per thread
@@ -642,7 +644,7 @@ __global__ void __launch_bounds__(192, 1) tc_comb_kernel(TcCombParams P) {
     for (int kk = 0; kk < P.nops; ++kk) {
       const int b = kk & 1;
       const int k = (kk + rot) % P.nops;
-      if (!mbar_wait(accFull + 8 * b, (uint32_t)((kk >> 1) & 1), abort_flag)) {
+      if (!mbar_wait(accFull + 8 * b, (uint32_t)((kk >> 1) & 1), abort_flag, P.wait_ns)) {
         *abort_flag = 1;
         atomicExch(P.err, 15);
         ok = false;
@@ -878,6 +880,7 @@ fetidp_status tc_apply(Ctx& c, const TcOperator& op, CCellVec X, const double* c
   P.alpha = alpha;
   P.beta = beta;
   P.err = c.tc_err;
+  P.wait_ns = c.wait_ns;
   P.a_bytes = (long long)batch * op.batch_bytes;
   P.b_bytes = (long long)c.tc_bbuf_bytes;
   P.y_ext = y_ext;
@@ -893,11 +896,16 @@ fetidp_status tc_apply(Ctx& c, const TcOperator& op, CCellVec X, const double* c
 // Self-check of the tensor-core path: random A (M x K), X (N columns), compare with an FP64
 // GEMM of the same bf16-rounded inputs.  Returns the max relative error in *rel_err.
 fetidp_status tc_selfcheck(Ctx& c, int M, int K, int N, double* rel_err) {
-  double *A = nullptr, *X = nullptr, *Yt = nullptr, *Yr = nullptr;
-  FD_CUDA(cudaMalloc(&A, sizeof(double) * M * K));
-  FD_CUDA(cudaMalloc(&X, sizeof(double) * (size_t)N * K));
-  FD_CUDA(cudaMalloc(&Yt, sizeof(double) * (size_t)N * M));
-  FD_CUDA(cudaMalloc(&Yr, sizeof(double) * (size_t)N * M));
+  // the four buffers are freed on every return path
+  struct Bufs {
+    double *A = nullptr, *X = nullptr, *Yt = nullptr, *Yr = nullptr;
+    ~Bufs() { cudaFree(A); cudaFree(X); cudaFree(Yt); cudaFree(Yr); }
+  } b;
+  FD_CUDA(cudaMalloc(&b.A, sizeof(double) * M * K));
+  FD_CUDA(cudaMalloc(&b.X, sizeof(double) * (size_t)N * K));
+  FD_CUDA(cudaMalloc(&b.Yt, sizeof(double) * (size_t)N * M));
+  FD_CUDA(cudaMalloc(&b.Yr, sizeof(double) * (size_t)N * M));
+  double *A = b.A, *X = b.X, *Yt = b.Yt, *Yr = b.Yr;
   fill_random_kernel<<<gridn((long long)M * K), 256, 0, c.stream>>>(A, (long long)M * K, 1234);
   fill_random_kernel<<<gridn((long long)N * K), 256, 0, c.stream>>>(X, (long long)N * K, 5678);
   FD_CHECK_LAUNCH();
@@ -912,14 +920,15 @@ fetidp_status tc_selfcheck(Ctx& c, int M, int K, int N, double* rel_err) {
   int herr = 0;
   FD_CUDA(cudaMemcpyAsync(&herr, c.tc_err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
   FD_CUDA(cudaStreamSynchronize(c.stream));
-  cudaFree(A); cudaFree(X); cudaFree(Yt); cudaFree(Yr);
   if (herr != 0) {
     set_error("tensor-core GEMM wait timed out (code " + std::to_string(herr) + ")");
     return FETIDP_ETIMEOUT;
   }
+  // a non-finite difference counts as an infinite error (the rule of absmax_pair_kernel)
   double mx = 0.0, ref = 0.0;
   for (size_t i = 0; i < ht.size(); ++i) {
-    mx = std::max(mx, std::fabs(ht[i] - hr[i]));
+    const double dv = std::fabs(ht[i] - hr[i]);
+    mx = std::isfinite(dv) ? std::max(mx, dv) : INFINITY;
     ref = std::max(ref, std::fabs(hr[i]));
   }
   *rel_err = mx / (ref > 0 ? ref : 1.0);
@@ -1068,6 +1077,7 @@ fetidp_status tc_comb_apply(Ctx& c, const TcComb& op, CCellVec X, const double* 
   P.alpha = alpha;
   P.beta = beta;
   P.err = c.tc_err;
+  P.wait_ns = c.wait_ns;
   const int bn = tc_comb_bn(ncols, op.m_tiles, op.kto, op.nX, op.nops, op.msplit < op.M);
   if (bn == 128) return comb_launch<128>(c, op, P, X, ncols, ncell);
   if (bn == 64) return comb_launch<64>(c, op, P, X, ncols, ncell);
@@ -1095,6 +1105,7 @@ struct TcComb2Params {
   int nops, kto, nA, nZ, M, KP, n_tiles, tiles_per_cta;
   long long ncols, ncell;
   int* err;
+  unsigned long long wait_ns;
 };
 
 __global__ void __launch_bounds__(kComb2Threads, 1) tc_comb2_kernel(TcComb2Params P) {
@@ -1149,11 +1160,11 @@ __global__ void __launch_bounds__(kComb2Threads, 1) tc_comb2_kernel(TcComb2Param
       for (int kk = 0; kk < ng; ++kk)
         bulk_g2s(smem_u32(sA + (size_t)kk * per_op * A_TILE), P.A + (long long)(k0 + kk) * per_op * A_TILE,
                  (uint32_t)(per_op * A_TILE), opFull);
-      bool ok = mbar_wait(opFull, 0u, abort_flag);
+      bool ok = mbar_wait(opFull, 0u, abort_flag, P.wait_ns);
       if (!ok) { *abort_flag = 1; atomicExch(P.err, 21); }
       for (int t = 0; ok && t < ntile; ++t) {
         const int b = t & 1, use = t >> 1;
-        if (use >= 1 && !mbar_wait(accEmpty + 8 * b, (uint32_t)((use - 1) & 1), abort_flag)) {
+        if (use >= 1 && !mbar_wait(accEmpty + 8 * b, (uint32_t)((use - 1) & 1), abort_flag, P.wait_ns)) {
           *abort_flag = 1;
           atomicExch(P.err, 22);
           ok = false;
@@ -1164,7 +1175,7 @@ __global__ void __launch_bounds__(kComb2Threads, 1) tc_comb2_kernel(TcComb2Param
         bool first = true;
         for (int kk = 0; ok && kk < ng; ++kk) {
           const int z = t * ng + kk, s = z & 1, n = z >> 1;
-          if (!mbar_wait(zFull + 8 * s, (uint32_t)(n & 1), abort_flag)) {
+          if (!mbar_wait(zFull + 8 * s, (uint32_t)(n & 1), abort_flag, P.wait_ns)) {
             *abort_flag = 1;
             atomicExch(P.err, 23);
             ok = false;
@@ -1192,12 +1203,8 @@ __global__ void __launch_bounds__(kComb2Threads, 1) tc_comb2_kernel(TcComb2Param
       // every MMA issued has completed, and the operator copies have landed, before TMEM and
       // shared memory are released
       tc_commit(done);
-      unsigned long long t0 = gtime();
-      while (!mbar_try(done, 0u) && gtime() - t0 < kWaitNs) {
-      }
-      t0 = gtime();
-      while (!mbar_try(opFull, 0u) && gtime() - t0 < kWaitNs) {
-      }
+      mbar_drain(done, 0u);
+      mbar_drain(opFull, 0u);
     }
   } else if (warp >= 4) {
     // ---------------- operand warps: thread (column c, k tile kt) forms 64 entries of z.  The x of
@@ -1228,7 +1235,7 @@ __global__ void __launch_bounds__(kComb2Threads, 1) tc_comb2_kernel(TcComb2Param
     int nsync = 0;
     auto osync = [&]() -> bool {                   // all 128 operand threads, bounded
       mbar_arrive(xsync);
-      const bool r = mbar_wait(xsync, (uint32_t)(nsync & 1), abort_flag);
+      const bool r = mbar_wait(xsync, (uint32_t)(nsync & 1), abort_flag, P.wait_ns);
       ++nsync;
       return r;
     };
@@ -1265,7 +1272,7 @@ __global__ void __launch_bounds__(kComb2Threads, 1) tc_comb2_kernel(TcComb2Param
       }
       for (int kk = 0; kk < ng; ++kk) {
         const int z = t * ng + kk, s = z & 1, n = z >> 1;
-        if (n >= 1 && !mbar_wait(zEmpty + 8 * s, (uint32_t)((n - 1) & 1), abort_flag)) {
+        if (n >= 1 && !mbar_wait(zEmpty + 8 * s, (uint32_t)((n - 1) & 1), abort_flag, P.wait_ns)) {
           *abort_flag = 1;
           atomicExch(P.err, 24);
           ok = false;
@@ -1298,7 +1305,7 @@ __global__ void __launch_bounds__(kComb2Threads, 1) tc_comb2_kernel(TcComb2Param
     const int m = warp * 32 + lane;
     for (int t = 0; t < ntile; ++t) {
       const int b = t & 1, use = t >> 1;
-      if (!mbar_wait(accFull + 8 * b, (uint32_t)(use & 1), abort_flag)) {
+      if (!mbar_wait(accFull + 8 * b, (uint32_t)(use & 1), abort_flag, P.wait_ns)) {
         *abort_flag = 1;
         atomicExch(P.err, 25);
         break;
@@ -1434,6 +1441,7 @@ static fetidp_status comb2_apply(Ctx& c, const TcComb& op, CCellVec X, const dou
     P.ncols = ncols;
     P.ncell = ncell;
     P.err = c.tc_err;
+  P.wait_ns = c.wait_ns;
     const size_t smem = comb2_smem_bytes(op);
     cudaFuncSetAttribute(tc_comb2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     tc_comb2_kernel<<<dim3((unsigned)nchunk, (unsigned)ngroups, 1), kComb2Threads, smem, c.stream>>>(P);
@@ -1520,9 +1528,11 @@ fetidp_status tc_comb_selfcheck(Ctx& c, int M0, int M1, int K, int N, int nops, 
     set_error("combine kernel wait timed out (code " + std::to_string(herr) + ")");
     return FETIDP_ETIMEOUT;
   }
+  // a non-finite difference counts as an infinite error (the rule of absmax_pair_kernel)
   double mx = 0.0, ref = 0.0;
   for (size_t i = 0; i < ht.size(); ++i) {
-    mx = std::max(mx, std::fabs(ht[i] - hr[i]));
+    const double dv = std::fabs(ht[i] - hr[i]);
+    mx = std::isfinite(dv) ? std::max(mx, dv) : INFINITY;
     ref = std::max(ref, std::fabs(hr[i]));
   }
   *rel_err = mx / (ref > 0 ? ref : 1.0);
@@ -1579,10 +1589,6 @@ struct TcCheckSlot {   // results of one probe, written on the device
   int err;             // tensor-core wait / bounds status: must be zero before the GEMM runs
   int pad;
 };
-
-constexpr int kStaticMaxDevices = 64;
-std::mutex g_static_mu;
-void* g_static_addr[kStaticMaxDevices] = {};
 
 size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -1648,21 +1654,12 @@ __global__ void __launch_bounds__(1024) absmax_pair_kernel(const double* a, cons
 
 size_t tc_selfcheck_static_bytes(int M, int K, int N) { return static_layout(M, K, N).total; }
 
-// Address of the static scratch on the current device; the first call on a device looks it up.
+// Address of the static scratch on the current device, looked up on every call: a cached address
+// would go stale if the device's primary context were reset and the module loaded again.
 fetidp_status tc_static_scratch(uint8_t** p) {
-  int dev = 0;
-  FD_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kStaticMaxDevices) {
-    set_error("device ordinal beyond the static-scratch table");
-    return FETIDP_EINVAL;
-  }
-  std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_addr[dev]) {
-    void* a = nullptr;
-    FD_CUDA(cudaGetSymbolAddress(&a, g_tc_static_scratch));
-    g_static_addr[dev] = a;
-  }
-  *p = static_cast<uint8_t*>(g_static_addr[dev]);
+  void* a = nullptr;
+  FD_CUDA(cudaGetSymbolAddress(&a, g_tc_static_scratch));
+  *p = static_cast<uint8_t*>(a);
   return FETIDP_OK;
 }
 
@@ -1715,6 +1712,44 @@ fetidp_status tc_selfcheck_static(Ctx& c, int M, int K, int N, double* rel_err) 
     return FETIDP_ETIMEOUT;
   }
   *rel_err = h.diff / (h.ref > 0 ? h.ref : 1.0);
+  return FETIDP_OK;
+}
+
+// ---------------------------------------------------------------- bounded-wait probe
+// One thread waits, through the pipeline's own bounded wait, on phase 0 of an mbarrier that
+// expects one arrival nobody makes: the wait must expire after wait_ns and set the error flag,
+// exactly as an expired wait does in the tensor-core kernels.  Nothing asynchronous is in flight.
+namespace {
+__device__ int g_wait_probe_flag;
+
+__global__ void wait_probe_kernel(unsigned long long wait_ns, int* flag) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    *flag = mbar_wait(smem_u32(&bar), 0u, reinterpret_cast<volatile int*>(&abort_flag), wait_ns) ? 0 : 31;
+}
+}  // namespace
+
+fetidp_status wait_selfcheck(unsigned long long wait_ns, cudaStream_t stream) {
+  void* a = nullptr;
+  FD_CUDA(cudaGetSymbolAddress(&a, g_wait_probe_flag));
+  int* flag = static_cast<int*>(a);
+  FD_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), stream));
+  wait_probe_kernel<<<1, 32, 0, stream>>>(wait_ns, flag);
+  FD_CHECK_LAUNCH();
+  int h = 0;
+  FD_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  FD_CUDA(cudaStreamSynchronize(stream));
+  if (h != 0) {
+    set_error("device wait expired after its budget (code " + std::to_string(h) + ")");
+    return FETIDP_ETIMEOUT;
+  }
   return FETIDP_OK;
 }
 

@@ -180,6 +180,24 @@ def config3(seed: int = 3) -> List[LatticeProblem]:
     return out
 
 
+def config3_sample(seed: int = 3, n_lattices: int = 4, max_xy: int = 4, max_z: int = 2,
+                   n_rb: int = 64) -> List[LatticeProblem]:
+    """Lattices drawn with config3's recipe (6^3 BCC cells, per-cell radii ~ U[0.15, 0.3], shear +
+    bend map, three top tractions) at sizes small enough for the oracle's monolithic solve:
+    nx, ny ~ U{2..max_xy}, nz ~ U{1..max_z}."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(n_lattices):
+        nx, ny = (int(v) for v in rng.integers(2, max_xy + 1, size=2))
+        nz = int(rng.integers(1, max_z + 1))
+        r_cell = rng.uniform(0.15, 0.3, size=nx * ny * nz)
+        g1, g2 = rng.uniform(-0.2, 0.2, size=2)
+        a = rng.uniform(0.0, nx / 8.0)
+        out.append(_bcc((nx, ny, nz), 6, r_cell, MASK_BCC_HARD, MAP_SHEAR_BEND_3D,
+                        (a, float(nx), g1, g2), _top_tractions(), n_rb, f"batch3d_sample_{b}"))
+    return out
+
+
 def config4(seed: int = 4) -> LatticeProblem:
     """3D 24x24x12 BCC with sigmoid density, identity map, unit downward top traction."""
     rng = np.random.default_rng(seed)

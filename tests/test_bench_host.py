@@ -42,14 +42,34 @@ def test_max_over_ranks_gloo_world2():
 
 
 def test_cpu_sample_is_a_sub_lattice_of_the_workload():
+    """The oracle's bounded sample is the corner of the benchmark lattice: same cell, mask, macro
+    map and loads, and each sampled cell keeps its radius."""
     import numpy as np
     import bench
-    from paper_2308_11371_gb300 import workloads as W
-    full = W.config2(n_rb=W.CONFIG2_SOLVE_N_RB)
-    q = bench.sample_problem(8)
-    assert q.cells == (8, 8, 1) and q.elems == full.elems and q.n_rb == full.n_rb
-    assert q.map_params == (full.map_params[0], 64.0)
-    assert np.allclose(q.r_cell.reshape(8, 8), full.r_cell.reshape(64, 64)[:8, :8])
+    full = bench.workload_problem("cfg5")
+    q = bench.sample_problem("cfg5", (4, 3, 2))
+    assert q.cells == (4, 3, 2) and q.elems == full.elems and q.dim == 3
+    assert q.map_kind == full.map_kind and q.map_params == full.map_params
+    assert q.mask_kind == full.mask_kind and len(q.loads) == len(full.loads) == 6
+    fr = np.asarray(full.r_cell).reshape(16, 32, 32)
+    assert np.array_equal(q.r_cell.reshape(2, 3, 4), fr[:2, :3, :4])
+    q2 = bench.sample_problem("cfg2", (8, 8, 1))
+    f2 = bench.workload_problem("cfg2")
+    assert q2.cells == (8, 8, 1) and q2.map_params == f2.map_params
+    assert np.allclose(q2.r_cell.reshape(8, 8), np.asarray(f2.r_cell).reshape(64, 64)[:8, :8])
+
+
+def test_class_roofline_uses_the_bound_of_each_class():
+    import bench
+    peaks = {"hbm_gbs": 6000.0, "bf16_tflops_sustained": 1500.0}
+    p = {"ms": 2.0, "launches": 4, "flops": 3e12, "bytes": 6e9}
+    e = bench.class_roofline("maps", p, "mixed", peaks)
+    assert e["bound"] == "hbm" and abs(e["achieved"] - 3000.0) < 1e-9 and abs(e["frac"] - 0.5) < 1e-12
+    t = bench.class_roofline("tc_gemm", p, "mixed", peaks)
+    assert t["bound"] == "tensor" and abs(t["achieved"] - 1500.0) < 1e-9 and abs(t["frac"] - 1.0) < 1e-12
+    f = bench.class_roofline("apply_K", p, "fp64", peaks)
+    assert f["bound"] == "alu" and f["peak"] == bench.FP64_PEAK_TFLOPS
+    assert bench.class_roofline("maps", {"ms": 0.0, "launches": 0, "flops": 0, "bytes": 0}, "mixed", peaks) is None
 
 
 def test_ncu_traffic_lookup_follows_class_precision_and_sources(tmp_path, monkeypatch):

@@ -43,6 +43,7 @@ def test_default_options_and_status_strings(lib):
     assert o.tol_outer == 1e-8 and o.tol_inner == 1e-11 and o.precision == binding.FETIDP_FP64
     assert o.tol_inner_mixed == 1e-6 and o.gram_drop_mixed == 1e-9 and o.tc_split == 3
     assert o.profile_mask == 0
+    assert o.max_outer == 100 and o.restart == 0 and o.wait_budget_ns == 10 ** 9 and o.check_inputs == 1
     assert lib.fetidp_status_string(-4) == b"not converged"
     assert lib.fetidp_status_string(0) == b"ok"
 
@@ -79,7 +80,8 @@ def test_setup_rejects_bad_input_without_gpu(lib):
 
 
 @pytest.mark.parametrize("case", ["batch_elems", "batch_loads", "tc_split", "gram_drop", "clamp_axis", "nu",
-                                  "iterations"])
+                                  "iterations", "restart", "wait_budget", "nan_radius", "inf_load", "nan_map",
+                                  "nan_tol", "negative_E"])
 def test_setup_validation_without_gpu(lib, case):
     """Every argument and batch-compatibility check of fetidp_setup runs before any CUDA call and
     answers FETIDP_EINVAL (-1) with no context."""
@@ -104,6 +106,20 @@ def test_setup_validation_without_gpu(lib, case):
         a.nu = 0.5
     elif case == "iterations":
         opts = {"max_outer": 0}
+    elif case == "restart":
+        opts = {"restart": -1}
+    elif case == "wait_budget":
+        opts = {"wait_budget_ns": 0}
+    elif case == "nan_radius":
+        a.r_cell = a.r_cell.copy(); a.r_cell[5] = float("nan")
+    elif case == "inf_load":
+        a.loads = [W.Load(W.LOAD_TRACTION, (0.0, float("inf")), axis=0, side=1)]
+    elif case == "nan_map":
+        a.map_params = (float("nan"), 4.0)
+    elif case == "nan_tol":
+        opts = {"tol_outer": float("nan")}
+    elif case == "negative_E":
+        a.E_void = -1e-3
     arr = (binding.Problem * len(probs))()
     keep = []
     for i, q in enumerate(probs):
@@ -116,8 +132,24 @@ def test_setup_validation_without_gpu(lib, case):
     assert st == -1 and not h.value
     expect = {"batch_elems": "must share", "batch_loads": "must share", "tc_split": "tc_split",
               "gram_drop": "gram_drop_mixed", "clamp_axis": "clamp axis", "nu": "nu out of range",
-              "iterations": "iteration limits"}[case]
+              "iterations": "iteration limits", "restart": "iteration limits",
+              "wait_budget": "wait_budget_ns", "nan_radius": "non-finite", "inf_load": "non-finite",
+              "nan_map": "non-finite", "nan_tol": "tolerances", "negative_E": "negative"}[case]
     assert expect in lib.fetidp_last_error().decode()
+
+
+def test_zero_material_is_singular_without_gpu(lib):
+    """E_solid = E_void = 0 leaves every cell stiffness zero: FETIDP_ESINGULAR (-6), no context."""
+    import ctypes
+    from paper_2308_11371_gb300 import workloads as W
+    a = W.config1()
+    a.E_solid = 0.0
+    a.E_void = 0.0
+    s, keep = binding.make_problem_struct(a)
+    h = ctypes.c_void_p()
+    st = lib.fetidp_setup(ctypes.byref(s), 1, None, None, ctypes.byref(h))
+    assert st == -6 and not h.value
+    assert "zero" in lib.fetidp_last_error().decode()
 
 
 C_PROGRAM = r"""

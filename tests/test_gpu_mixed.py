@@ -43,26 +43,33 @@ def oracle(name):
         prob = {"cfg1": W.config1(),
                 "ragged2d": W.lattice_2d(12, 7, 6, a=0.9, r=0.12, r_grade=0.04, n_rb=5),
                 "bcc3d": W.lattice_3d(2, 2, 2, e=3, r=0.2, r_spread=0.06, seed=7, n_rb=4,
-                                      map_kind=W.MAP_SHEAR_BEND_3D, map_params=(0.3, 2.0, 0.1, -0.15))}[name]
+                                      map_kind=W.MAP_SHEAR_BEND_3D, map_params=(0.3, 2.0, 0.1, -0.15)),
+                # the benchmark's 3D cell (6^3 Q1 elements) with three load cases
+                "bcc6": W.lattice_3d(2, 2, 2, e=6, r=0.2, r_spread=0.06, seed=8, n_rb=4, mask_kind=W.MASK_BCC_SIGMOID,
+                                     map_kind=W.MAP_SHEAR_BEND_3D, map_params=(0.3, 2.0, 0.1, -0.15),
+                                     loads=[W.Load(W.LOAD_TRACTION, (1.0, 0.0, 0.0), axis=2, side=1),
+                                            W.Load(W.LOAD_TRACTION, (0.0, 0.0, -1.0), axis=2, side=1),
+                                            W.Load(W.LOAD_BODY, (0.0, 1.0, 0.0))])}[name]
         lat = Lattice(prob)
         _OC[name] = (prob, lat, ifeti_dp.InexactFETIDP(lat))
     return _OC[name]
 
 
 @pytest.mark.parametrize("split,tol", [(1, 3e-2), (3, 3e-4)])
-@pytest.mark.parametrize("name", ["cfg1", "ragged2d", "bcc3d"])
+@pytest.mark.parametrize("name", ["cfg1", "ragged2d", "bcc3d", "bcc6"])
 def test_mixed_interface_operators(name, split, tol):
     prob, lat, fe = oracle(name)
     s = _mixed(prob, tc_split=split)
     rng = np.random.default_rng(31)
     lam = rng.standard_normal((s.n_rhs, s.L))
-    y = _host(s.apply_F(_dev(lam)))[0]
-    z = _host(s.precond(_dev(lam)))[0]
-    assert _rel(y, fe.apply_F(lam[0])) < tol
-    assert _rel(z, fe.apply_MD(lam[0])) < tol
+    y = _host(s.apply_F(_dev(lam)))
+    z = _host(s.precond(_dev(lam)))
+    for r in range(s.n_rhs):
+        assert _rel(y[r], fe.apply_F(lam[r])) < tol
+        assert _rel(z[r], fe.apply_MD(lam[r])) < tol
 
 
-@pytest.mark.parametrize("name", ["cfg1", "ragged2d", "bcc3d"])
+@pytest.mark.parametrize("name", ["cfg1", "ragged2d", "bcc3d", "bcc6"])
 def test_mixed_local_rom_solve(name):
     """Eq. 46 with an FP32 basis from the tensor cores: the Galerkin projection with the exact
     K_s keeps the solve a near-best approximation, so it matches the FP64 one closely."""
@@ -70,11 +77,12 @@ def test_mixed_local_rom_solve(name):
     s = _mixed(prob)
     rng = np.random.default_rng(33)
     v = rng.standard_normal((s.n_rhs, s.N, s.n_r))
-    x = _host(s.local_rom_solve(_dev(v)))[0]
-    assert _rel(x, fe.rom.local_rom_solve(v[0])) < 1e-3
+    x = _host(s.local_rom_solve(_dev(v)))
+    for r in range(s.n_rhs):
+        assert _rel(x[r], fe.rom.local_rom_solve(v[r])) < 1e-3
 
 
-@pytest.mark.parametrize("name", ["cfg1", "ragged2d", "bcc3d"])
+@pytest.mark.parametrize("name", ["cfg1", "ragged2d", "bcc3d", "bcc6"])
 def test_mixed_rom_data_matches_oracle(name):
     """The mixed setup's double-float greedy (Algorithm 4) and Eq. 42 traces select the oracle's
     principal cells and reproduce its FP64 alpha (Eq. 56) to 1e-10; pi and delta come from pivoted
@@ -88,16 +96,25 @@ def test_mixed_rom_data_matches_oracle(name):
     assert _rel(delta, fe.rom.delta) < 1e-7
 
 
+_MONO = {}
+
+
 @pytest.mark.parametrize("split", [1, 3])
-@pytest.mark.parametrize("name", ["cfg1", "ragged2d", "bcc3d"])
+@pytest.mark.parametrize("name", ["cfg1", "ragged2d", "bcc3d", "bcc6"])
 def test_mixed_solve_matches_monolithic(name, split):
+    """Mixed precision at the FP64 outer residual 1e-8: displacement within 1e-7 of the oracle's
+    monolithic solution, for every load case."""
     from oracle import monolithic
     prob, lat, fe = oracle(name)
     s = _mixed(prob, tc_split=split)
     u, lam, info = s.solve()
     assert info["rel_residual"] <= 1e-8
-    ref = monolithic.to_cells(lat, monolithic.solve(lat))
-    assert _rel(_host(u)[0], ref[0]) < 1e-7
+    if name not in _MONO:
+        _MONO[name] = monolithic.to_cells(lat, monolithic.solve(lat))
+    ref = _MONO[name]
+    uh = _host(u)
+    for r in range(s.n_rhs):
+        assert _rel(uh[r], ref[r]) < 1e-7
 
 
 def test_mixed_config2_converges():
