@@ -15,6 +15,10 @@ U_ring^T = K_ring^{-ROM} B^T "using the ROM dual solutions"):
     out  = ( U_RD B_R^T y - U_RP z_P ,  z_P ).
 The outer solver is flexible GMRES because the inner PCG makes the
 preconditioner vary between applications (the paper uses GMRES, Sec. 2.3).
+
+interface="md_rom" takes the other sub-preconditioner of Sec. 3.2.3 (Eq. 47):
+F_ring^{-1} ~ M_D^{-ROM}, one application of the Dirichlet preconditioner whose
+interior solves K_ii^{-1} are ROM approximations, instead of the PCG on Eq. 48.
 """
 from __future__ import annotations
 
@@ -27,7 +31,10 @@ from .rom import ROM
 
 
 class InexactFETIDP:
-    def __init__(self, lat: Lattice, rom: ROM = None, blocks=None, n_rb=None):
+    def __init__(self, lat: Lattice, rom: ROM = None, blocks=None, n_rb=None, interface: str = "pcg"):
+        if interface not in ("pcg", "md_rom"):
+            raise ValueError(interface)
+        self.interface = interface
         self.lat = lat
         self.blocks = blocks or [CellBlocks(lat, s) for s in range(lat.N)]
         self.rom = rom or ROM(lat, n_rb=n_rb, blocks=self.blocks)
@@ -72,6 +79,11 @@ class InexactFETIDP:
         g = self.gather(self.lat.apply_D(r))
         return self.lat.apply_D(self.scatter(self.rom.Sdd_ring(g)))
 
+    def apply_MD_rom(self, r):
+        """Eq. 47: M_D^{-ROM} r, the Dirichlet preconditioner of Eq. 30 with ROM interior solves."""
+        g = self.gather(self.lat.apply_D(r))
+        return self.lat.apply_D(self.scatter(self.rom.Sdd_rom(g)))
+
     def U_apply(self, vR, vP):
         """Algorithm 3: U_ring v.  Returns (z, z_P)."""
         rom = self.rom
@@ -103,7 +115,10 @@ class InexactFETIDP:
         Uv, zP = self.U_apply(vR, vP)
         wbar = w - Uv
         rec = []
-        ysol, its = pcg(self.apply_F, self.apply_MD, wbar, tol_inner, max_inner, record=rec)
+        if self.interface == "md_rom":
+            ysol, its = self.apply_MD_rom(wbar), 0
+        else:
+            ysol, its = pcg(self.apply_F, self.apply_MD, wbar, tol_inner, max_inner, record=rec)
         y = -ysol
         self.inner_its.append(its)
         self.inner_records.append(rec)

@@ -8,6 +8,8 @@
   S_dd = F_dd^{-1}, from exact factorisations of the principal K_rr.
 * Projections pi, delta (Eqs. 40-42) with each cell's exact K_rr^(s).
 * ROM local operators (Eq. 43) and the assembled coarse S_PP (Sec. 3.2.1).
+* The ROM-based Dirichlet solve of Eq. 47: K_ii^(s)^{-1} approximated like the K_rr solves of
+  Eq. 46, from the principal cells' K_ii^{-1}.
 
 Readings: ties in the greedy argmax go to the lowest cell index among cells
 within relative 1e-12 of the maximum; the greedy stops at the requested
@@ -120,6 +122,7 @@ class ROM:
         T_rd = np.zeros((nr, nd)); T_rd[ni:, :] = np.eye(nd)
         self.Kp = []          # full principal K (dense, idp order)
         self.Krr_inv, self.Urp, self.Spp, self.Urd, self.Fdd, self.Sdd = [], [], [], [], [], []
+        self.Kii_inv = []     # principal K_ii^{-1} (Eq. 47's ROM Dirichlet solves)
         for s in self.sigma:
             K = Ks[s].toarray()
             self.Kp.append(K)
@@ -134,6 +137,7 @@ class ROM:
             self.Urd.append(Urd)
             self.Fdd.append(Fdd)
             self.Sdd.append(np.linalg.inv(Fdd))            # S_dd = F_dd^{-1} (Sec. 3.1.1)
+            self.Kii_inv.append(sla.cho_solve(sla.cho_factor(Krr[:ni, :ni], lower=True), np.eye(ni)))
         # -- projections pi, delta (Eqs. 41-42)
         k = self.n_rb
         self.pi = np.zeros((N, k))
@@ -191,3 +195,26 @@ class ROM:
             c = gram_solve(G, R.T @ v[s])
             x[s] = R @ c
         return x
+
+    # ---- Eq. 47: Dirichlet Schur complements with ROM-approximated interior solves
+    def dirichlet_rom_solve(self, s: int, v_i: np.ndarray) -> np.ndarray:
+        """x_i ~ K_ii^(s)^{-1} v_i in the span of R = [K_ii^(sigma_k)^{-1} v_i]_k, K_ii^(s)-orthogonally
+        (the construction of Eq. 46 applied to the interior block)."""
+        ni = self.lat.ref.n_i
+        Kii = self.K[s][:ni, :ni]
+        R = np.stack([Kinv @ v_i for Kinv in self.Kii_inv], axis=1)
+        G = R.T @ (Kii @ R)
+        c = gram_solve(G, R.T @ v_i)
+        return R @ c
+
+    def Sdd_rom(self, g):
+        """S_dd^(s) g = K_dd g - K_di K_ii^{-1} K_id g per cell, K_ii^{-1} by dirichlet_rom_solve."""
+        ref = self.lat.ref
+        ni, nr = ref.n_i, ref.n_r
+        y = np.zeros_like(g)
+        for s in range(self.lat.N):
+            K = self.K[s]
+            Kid = K[:ni, ni:nr]
+            x_i = self.dirichlet_rom_solve(s, Kid @ g[s])
+            y[s] = K[ni:nr, ni:nr] @ g[s] - K[ni:nr, :ni] @ x_i
+        return y

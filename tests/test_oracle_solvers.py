@@ -235,3 +235,48 @@ def test_dirichlet_preconditioned_spectrum_lower_bound(prob):
     assert ev.min() >= 1.0 - 1e-8
     if prob.dim == 3:
         assert ev.max() / ev.min() < 1e3
+
+
+def test_dirichlet_rom_solve_is_exact_on_principal_cells():
+    """Eq. 47's ROM interior solve keeps K_ii^(sigma)^{-1} v_i in its basis, so the K_ii-orthogonal
+    projection returns it exactly on every principal cell."""
+    lat = Lattice(W.lattice_2d(4, 3, 6, a=0.6, r=0.12, r_grade=0.04, n_rb=3))
+    R = rom.ROM(lat)
+    ni = lat.ref.n_i
+    v = np.random.default_rng(4).standard_normal(ni)
+    for k, s in enumerate(R.sigma):
+        Kii = R.K[s][:ni, :ni].toarray()
+        assert np.allclose(R.dirichlet_rom_solve(s, v), np.linalg.solve(Kii, v), rtol=0, atol=1e-10 * np.abs(
+            np.linalg.solve(Kii, v)).max())
+
+
+@pytest.mark.parametrize("prob", [W.lattice_2d(3, 2, 4, a=0.5, r=0.12, n_rb=6),
+                                  W.lattice_3d(2, 1, 2, e=2, r=0.22, r_spread=0.04, seed=3, n_rb=4)],
+                         ids=["2d_all_principal", "3d_all_principal"])
+def test_md_rom_equals_exact_dirichlet_preconditioner_when_all_cells_are_principal(prob):
+    """With every cell principal (or a copy of one: the 2D lattice's columns repeat), M_D^{-ROM}
+    (Eq. 47) is the Dirichlet preconditioner of standard FETI-DP (Eq. 30) exactly."""
+    lat = Lattice(prob)
+    fd = feti_dp.StandardFETIDP(lat)
+    it = ifeti_dp.InexactFETIDP(lat, blocks=fd.blocks, interface="md_rom")
+    # the greedy stopped on an exhausted residual: every snapshot lies in the principal span
+    assert it.rom.n_rb < prob.n_rb or it.rom.n_rb == lat.N
+    r = np.random.default_rng(6).standard_normal(lat.L)
+    a, b = it.apply_MD_rom(r), fd.apply_MD(r)
+    assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max()
+
+
+def test_md_rom_interface_solver_converges_to_monolithic():
+    """Algorithm 1 with F_ring^{-1} ~ M_D^{-ROM} (Eq. 47) in place of the inner PCG: FGMRES still
+    reaches the monolithic solution, with more outer and no inner iterations."""
+    prob = W.lattice_2d(4, 3, 6, a=0.6, r=0.12, r_grade=0.04, n_rb=3)
+    lat = Lattice(prob)
+    it = ifeti_dp.InexactFETIDP(lat, interface="md_rom")
+    uR, uP, lam, res = it.solve(tol=1e-10, max_outer=200)
+    assert res <= 1e-10 and sum(it.inner_its) == 0
+    u = feti_dp.cell_vectors(lat, uR, uP)
+    ref = _mono_cells(lat)[0]
+    assert np.abs(u - ref).max() <= 1e-8 * np.abs(ref).max()
+    pc = ifeti_dp.InexactFETIDP(lat)
+    pc.solve(tol=1e-10)
+    assert it.outer_its > pc.outer_its
