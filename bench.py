@@ -19,6 +19,7 @@ device time in "roofline".
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload cfg5|cfg2|cfg4] [--precision mixed|fp64]
                   [--no-cpu-baseline] [--no-fp64-ref] [--no-secondary] [--e2e-steps E]
+                  [--sample NX,NY,NZ]
 
 N > 1 runs N independent replicas (one per GPU; one lattice has no cross-GPU exchange here),
 value = DOF of all replicas / max-over-ranks time.
@@ -197,7 +198,8 @@ def barrier(world):
 CLASS_SOURCES = {"tc_gemm": ["tc_gemm.cu"], "sweep": ["dense.cu"], "traces": ["dense.cu"],
                  "greedy": ["kernels_setup.cu"], "cell_gemv": ["kernels_cell.cu"],
                  "apply_K": ["kernels_cell.cu"], "maps": ["kernels_maps.cu"], "coarse": ["coarse.cu"],
-                 "gram": ["kernels_cell.cu"], "vector": ["kernels_maps.cu"]}
+                 "gram": ["kernels_cell.cu"], "vector": ["kernels_maps.cu"], "asm_op": ["kernels_cell.cu"],
+                 "multi_K": ["kernels_cell.cu"]}
 
 
 def kernel_source_hash(files=None):
@@ -231,9 +233,9 @@ def ncu_traffic(kernel_class, precision, workload=None):
 # "fp64" (algorithmic flops against the derived pipe peak), "df" (double-float FP64-equivalent
 # flops against the FP32 issue rate / 12).
 CLASS_BOUND = {
-    "mixed": {"maps": "hbm", "vector": "hbm", "cell_gemv": "hbm", "coarse": "hbm", "apply_K": "fp32",
-              "tc_gemm": "tensor", "gram": "fp32", "grouped_gemm": "fp64", "sweep": "fp64",
-              "traces": "df", "greedy": "hbm", "setup": "hbm"},
+    "mixed": {"maps": "hbm", "vector": "hbm", "cell_gemv": "hbm", "asm_op": "hbm", "coarse": "hbm",
+              "apply_K": "fp64", "multi_K": "fp32", "tc_gemm": "tensor", "gram": "fp32",
+              "grouped_gemm": "fp64", "sweep": "fp64", "traces": "df", "greedy": "hbm", "setup": "hbm"},
     "fp64": {"maps": "hbm", "vector": "hbm", "cell_gemv": "hbm", "coarse": "hbm", "apply_K": "fp64",
              "tc_gemm": "tensor", "gram": "fp64", "grouped_gemm": "fp64", "sweep": "fp64",
              "traces": "fp64", "greedy": "fp64", "setup": "hbm"},
@@ -310,6 +312,8 @@ def main():
     ap.add_argument("--no-secondary", action="store_true", help="skip the 2D config2 secondary line")
     ap.add_argument("--e2e-steps", type=int, default=3,
                     help="end-to-end steps through fetidp_solve_host (each one time-to-solution)")
+    ap.add_argument("--sample", default=None,
+                    help="NX,NY,NZ: run the workload's corner sub-lattice of that size (profiling runs)")
     args = ap.parse_args()
     rank, world, local = dist_init()
     if args.impl == "reference":
@@ -321,8 +325,12 @@ def main():
 
     torch.cuda.set_device(local)
     binding.load()
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
     prob = workload_problem(args.workload)
+    if args.sample:
+        cells = tuple(int(v) for v in args.sample.split(","))
+        prob = sample_problem(args.workload, cells)
+        wl["label"] = "%s_sample_%dx%dx%d" % (wl["label"], cells[0], cells[1], cells[2])
     opts = dict(wl["opts"])
     prec = args.precision
     precision = binding.FETIDP_FP64 if prec == "fp64" else binding.FETIDP_MIXED_BF16
@@ -389,8 +397,8 @@ def main():
     roof = dict(rooflines[dominant])
     roof["kernel_class"] = dominant
     roof["traffic"] = ncu_traffic(dominant, prec, args.workload)   # DRAM bytes per launch (ncu)
-    hot_path = {k: rooflines[k] for k in ("maps", "cell_gemv", "apply_K", "tc_gemm", "coarse", "gram", "vector")
-                if k in rooflines}
+    hot_path = {k: rooflines[k] for k in ("maps", "asm_op", "cell_gemv", "apply_K", "multi_K", "tc_gemm",
+                                          "coarse", "gram", "vector", "grouped_gemm") if k in rooflines}
 
     # the FP64 path on the same workload (one solve, outside the timed region) and the
     # displacement difference between the two solutions

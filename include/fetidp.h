@@ -149,6 +149,12 @@ typedef struct {
                                (4 n_d^2 bytes per cell per application, shared by the RHS);
                                0 = principal form on the tensor cores (2 N_rb n_d^2 flops per
                                column); -1 = assembled when n_d > 128, i.e. for 3D cells (-1)  */
+  int interface;            /* interface sub-preconditioner of Algorithm 1 (Sec. 3.2.3): 0 = PCG on
+                               F_ring (Eq. 48) preconditioned by M_D_ring (Eq. 49); 1 = one
+                               application of M_D^{-ROM} (Eq. 47), the Dirichlet preconditioner
+                               whose interior solves K_ii^(s)^{-1} are ROM approximations built
+                               from the principal K_ii^{-1} as Eq. 46 builds the K_rr solves;
+                               FP64 arithmetic in both precisions (0)                         */
 } fetidp_options;
 
 typedef struct {
@@ -199,6 +205,12 @@ fetidp_status fetidp_apply_F(fetidp_ctx *ctx, const double *lambda, double *y);
 /* z = M_D_ring^{-1} r (Eq. 49): D-scaled gather, alpha-combined principal
  * Dirichlet Schur complements, D-scaled scatter.  r, z: device [n_rhs][L].  */
 fetidp_status fetidp_precond(fetidp_ctx *ctx, const double *r, double *z);
+
+/* z = M_D^{-ROM} r (Eq. 47): D-scaled gather, per cell K_dd g - K_di x_i with x_i the ROM
+ * approximation of K_ii^(s)^{-1} K_id g (basis [K_ii^(sigma_k)^{-1} K_id g]_k, K_ii^(s)-orthogonal
+ * projection), D-scaled scatter; K_s matrix-free (Eq. 52), FP64.  The context must have been set
+ * up with the option interface = 1 (EINVAL otherwise).  r, z: device [n_rhs][L].            */
+fetidp_status fetidp_precond_rom(fetidp_ctx *ctx, const double *r, double *z);
 
 /* Solve the saddle-point system of Eq. 16 by right-preconditioned flexible
  * GMRES with the block preconditioner of Eq. 44 (Algorithms 1-3), x_0 = 0,
@@ -276,6 +288,8 @@ enum {
   FETIDP_K_SWEEP = 9,         /* setup: blocked sweep SPD inverses (K_rr, S_dd, coarse blocks) */
   FETIDP_K_TRACES = 10,       /* setup: Eq. 42 snapshot traces (FP64 or double-float GEMM) */
   FETIDP_K_GREEDY = 11,       /* setup: Algorithm 4 greedy steps */
+  FETIDP_K_MULTI_K = 12,      /* mixed: K_rr^(s) times the N_rb local ROM basis vectors (Eq. 46b) */
+  FETIDP_K_ASM_OP = 13,       /* mixed: assembled FP32 F_dd_ring / S_dd_ring of the inner PCG */
   FETIDP_K_NCLASS = 16
 };
 

@@ -30,10 +30,12 @@ SYMBOLS = ["fetidp_sizes", "fetidp_default_options", "fetidp_setup", "fetidp_app
            "fetidp_status_string", "fetidp_last_error", "fetidp_profile_enable",
            "fetidp_profile_read", "fetidp_kernel_launches", "fetidp_tc_selfcheck",
            "fetidp_tc_comb_selfcheck", "fetidp_tc_selfcheck_static",
-           "fetidp_compliance", "fetidp_batch_layout", "fetidp_wait_selfcheck"]
+           "fetidp_compliance", "fetidp_batch_layout", "fetidp_wait_selfcheck",
+           "fetidp_precond_rom"]
 
 KCLASS = {"grouped_gemm": 0, "apply_K": 1, "maps": 2, "coarse": 3, "cell_gemv": 4, "vector": 5,
-          "gram": 6, "tc_gemm": 7, "setup": 8, "sweep": 9, "traces": 10, "greedy": 11}
+          "gram": 6, "tc_gemm": 7, "setup": 8, "sweep": 9, "traces": 10, "greedy": 11, "multi_K": 12,
+          "asm_op": 13}
 
 
 class FetidpError(RuntimeError):
@@ -65,7 +67,7 @@ class Options(ctypes.Structure):
                 ("tol_inner_mixed", ctypes.c_double), ("gram_drop_mixed", ctypes.c_double),
                 ("profile_mask", ctypes.c_uint), ("restart", ctypes.c_int),
                 ("wait_budget_ns", ctypes.c_longlong), ("check_inputs", ctypes.c_int),
-                ("mixed_assembled", ctypes.c_int)]
+                ("mixed_assembled", ctypes.c_int), ("interface", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -107,7 +109,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
                                  ctypes.POINTER(P)]
     lib.fetidp_sizes.restype = I
     lib.fetidp_sizes.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
-    for name in ("fetidp_apply_F", "fetidp_precond", "fetidp_gather_BT", "fetidp_scatter_B",
+    for name in ("fetidp_apply_F", "fetidp_precond", "fetidp_precond_rom", "fetidp_gather_BT", "fetidp_scatter_B",
                  "fetidp_apply_K", "fetidp_coarse_solve", "fetidp_local_rom_solve",
                  "fetidp_apply_A", "fetidp_apply_P"):
         f = getattr(lib, name)
@@ -252,6 +254,10 @@ class Solver:
 
     def precond(self, r, out=None):
         return self._call2("fetidp_precond", r, out if out is not None else self._empty(self.n_rhs, self.L))
+
+    def precond_rom(self, r, out=None):
+        """M_D^{-ROM} r (Eq. 47); needs a context set up with interface=1."""
+        return self._call2("fetidp_precond_rom", r, out if out is not None else self._empty(self.n_rhs, self.L))
 
     def gather_BT(self, lam, out=None):
         o = out if out is not None else self._empty(self.n_rhs, self.N, self.n_d)

@@ -240,6 +240,14 @@ struct Ctx {
   double* snap = nullptr;
   // mixed path: FP32 element matrices [N][nelem][ND][ND] for the Eq. 46b K_s products
   float* Ke_all = nullptr;
+  // sparse K_rr of every cell in ELL form (mixed path, Eq. 46b): columns [nnz][nr] shared by all
+  // cells, FP32 values [N][nnz][nr]
+  int* krr_col = nullptr;
+  float* krr_val = nullptr;
+  int krr_nnz = 0;
+  // Eq. 47 interface option: principal K_ii^{-1} [nrb][ni][ni] and the interior work vector
+  double* Kii_inv = nullptr;
+  double* w_i = nullptr;        // [m][N][ni]
   // ROM coefficients [N][nrb]
   double* alpha = nullptr;
   double* pi = nullptr;
@@ -417,7 +425,7 @@ fetidp_status k_gram_direct(Ctx& c, const double* Y, int ntab, const double* dve
 fetidp_status k_batched_diag_sum(Ctx& c, const double* A, long long stride, int lda, int r0, int m, int batch,
                                  double* out);
 fetidp_status k_apply_K(Ctx& c, CCellVec u, CellVec y, int nvec_per_col, int ncols, bool idp,
-                        bool r_only, const double* chat, double chat_scale_dr);
+                        bool r_only, const double* chat, double chat_scale_dr, int len_override = 0);
 fetidp_status k_rom_combine_f32(Ctx& c, const double* src, long long kstride, int ld, int r0, int c0, int rows,
                                 int cols, const double* coef, float* out, int ldo);
 fetidp_status k_cell_gemm_f32(Ctx& c, const float* mats, int ldm, int rows, int cols, CCellVec x, CellVec y,
@@ -433,9 +441,10 @@ fetidp_status k_grouped_gemm_n(Ctx& c, const double* A, long long a_stride_k, in
                                double alpha, double beta, long long ncell, int nrhs, bool separate,
                                long long y_k_stride, int prof_class = FETIDP_K_GROUPED_GEMM);
 fetidp_status k_gram_solve(Ctx& c, const double* R, const double* KR, CCellVec v, CellVec x,
-                           int nrhs);
+                           int nrhs, int len = -1);
 fetidp_status k_grad(Ctx& c, const double* u, const double* w, double* g);
 fetidp_status k_element_matrices_f32(Ctx& c);
+fetidp_status k_krr_ell_assemble(Ctx& c, const int* cnt, const int* idx, int cmax);
 fetidp_status k_apply_K_f32(Ctx& c, const float* u, long long u_rs, int u_cs, float* y, long long y_rs,
                             int y_cs, int nvec, int nrhs, bool idp, bool r_only, long long ext = -1);
 fetidp_status k_gram_solve_f32(Ctx& c, const float* R, const float* KR, CCellVec v, CellVec x,

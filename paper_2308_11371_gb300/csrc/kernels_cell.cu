@@ -44,56 +44,52 @@ __global__ void snapshot_kernel(Geo g, const double* __restrict__ r_cell, long l
   }
 }
 
-// Element contribution f_e = sum_gp w dN^T C_hat dN u_e for one element and one vector.
+// Contribution of one Gauss point gp of one element: f = w dN^T C_hat(gp) dN u_e (Eq. 52).
 template <int D, typename T>
-__device__ __forceinline__ void element_apply(const double* __restrict__ chat_el, int nc,
-                                              T wq, T inv_h, const T* ue, T* fe) {
+__device__ __forceinline__ void gp_apply(const double* __restrict__ chat_gp, int gp, T wq, T inv_h, const T* ue,
+                                         T* fe) {
   constexpr int NA = 1 << D;
   constexpr int NI = D * D;
-  for (int k = 0; k < NA * D; ++k) fe[k] = T(0);
-  for (int gp = 0; gp < NA; ++gp) {
-    T t[D];
-    for (int k = 0; k < D; ++k) t[k] = (T)gauss_t((gp >> k) & 1);
-    // dN_A / dxi_a
-    T dN[NA][D];
-    for (int A = 0; A < NA; ++A) {
-      for (int a = 0; a < D; ++a) {
-        T v = inv_h;
-        for (int k = 0; k < D; ++k) {
-          const int off = (A >> k) & 1;
-          if (k == a) v *= off ? T(1) : T(-1);
-          else v *= off ? t[k] : T(1) - t[k];
-        }
-        dN[A][a] = v;
+  T t[D];
+  for (int k = 0; k < D; ++k) t[k] = (T)gauss_t((gp >> k) & 1);
+  T dN[NA][D];
+  for (int A = 0; A < NA; ++A)
+    for (int a = 0; a < D; ++a) {
+      T v = inv_h;
+      for (int k = 0; k < D; ++k) {
+        const int off = (A >> k) & 1;
+        if (k == a) v *= off ? T(1) : T(-1);
+        else v *= off ? t[k] : T(1) - t[k];
       }
+      dN[A][a] = v;
     }
-    T G[NI];
-    for (int I = 0; I < NI; ++I) G[I] = T(0);
-    for (int A = 0; A < NA; ++A)
-      for (int i = 0; i < D; ++i)
-        for (int a = 0; a < D; ++a) G[i * D + a] += ue[A * D + i] * dN[A][a];
-    T S[NI];
-    for (int I = 0; I < NI; ++I) S[I] = T(0);
-    const double* C = chat_el + gp * nc;
-    int q = 0;
-    for (int I = 0; I < NI; ++I) {
-      for (int J = I; J < NI; ++J) {
-        const T cij = (T)C[q++];
-        S[I] += cij * G[J];
-        if (J != I) S[J] += cij * G[I];
-      }
+  T G[NI];
+  for (int I = 0; I < NI; ++I) G[I] = T(0);
+  for (int A = 0; A < NA; ++A)
+    for (int i = 0; i < D; ++i)
+      for (int a = 0; a < D; ++a) G[i * D + a] += ue[A * D + i] * dN[A][a];
+  T S[NI];
+  for (int I = 0; I < NI; ++I) S[I] = T(0);
+  int q = 0;
+  for (int I = 0; I < NI; ++I)
+    for (int J = I; J < NI; ++J) {
+      const T cij = (T)chat_gp[q++];
+      S[I] += cij * G[J];
+      if (J != I) S[J] += cij * G[I];
     }
-    for (int A = 0; A < NA; ++A)
-      for (int i = 0; i < D; ++i) {
-        T v = T(0);
-        for (int a = 0; a < D; ++a) v += dN[A][a] * S[i * D + a];
-        fe[A * D + i] += wq * v;
-      }
-  }
+  for (int A = 0; A < NA; ++A)
+    for (int i = 0; i < D; ++i) {
+      T v = T(0);
+      for (int a = 0; a < D; ++a) v += dN[A][a] * S[i * D + a];
+      fe[A * D + i] = wq * v;
+    }
 }
 
-// One block per (rhs, cell) column; vectors of the column processed VB at a time.
-// T = double (FP64 path) or float (the Eq. 46b products of the mixed path).
+// One block per (cell, rhs) column, the cell slowest (the RHS of a cell share its C_hat in L2);
+// vectors of the column processed VB at a time.  Within a colour group (elements that share no
+// node) one thread per (vector, element, Gauss point); the 2^D threads of an element are adjacent
+// lanes and sum their contributions with a fixed butterfly before one of them adds the element
+// into the column's shared accumulator.  T = double (FP64 path) or float.
 template <int D, typename T>
 __global__ void apply_K_kernel(int e, long long ncell, int n, int len, const int* __restrict__ perm,
                                const int* __restrict__ iperm, bool idp, const T* __restrict__ u,
@@ -103,9 +99,9 @@ __global__ void apply_K_kernel(int e, long long ncell, int n, int len, const int
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sm = reinterpret_cast<T*>(sm_raw);
   constexpr int NA = 1 << D;
-  const long long col = blockIdx.x;
-  const int rhs = (int)(col / ncell);
-  const long long cell = col - (long long)rhs * ncell;
+  const int nrhs = (int)(gridDim.x / ncell);
+  const long long cell = blockIdx.x / nrhs;
+  const int rhs = (int)(blockIdx.x - cell * nrhs);
   const T* uc = u + rhs * u_rs + cell * u_cs;
   T* yc = y + rhs * y_rs + cell * y_cs;
   const double* chat_cell = chat + cell * (long long)nc * NA * (e * e * (D == 3 ? e : 1));
@@ -139,8 +135,14 @@ __global__ void apply_K_kernel(int e, long long ncell, int n, int len, const int
         cnt[k] = (k < D) ? (ecount[k] - par[k] + 1) / 2 : 1;
         nel *= cnt[k];
       }
-      for (int t = threadIdx.x; t < vb * nel; t += blockDim.x) {
-        const int v = t / nel, q = t - v * nel;
+      // uniform trip count (total and blockDim are multiples of NA): every lane reaches the shuffles
+      const int total = vb * nel * NA;
+      for (int t0 = 0; t0 < total; t0 += blockDim.x) {
+        const int t = t0 + threadIdx.x;
+        const bool live = t < total;
+        const int gp = t & (NA - 1);
+        const int vq = live ? t / NA : 0;
+        const int v = vq / nel, q = vq - v * nel;
         const int qx = q % cnt[0], qy = (q / cnt[0]) % cnt[1], qz = q / (cnt[0] * cnt[1]);
         const int ex = par[0] + 2 * qx, ey = par[1] + 2 * qy, ez = par[2] + 2 * qz;
         const int el = ex + e * (ey + e * ez);
@@ -152,11 +154,16 @@ __global__ void apply_K_kernel(int e, long long ncell, int n, int len, const int
         T ue[NA * D], fe[NA * D];
         const T* uv = us + (size_t)v * n;
         for (int A = 0; A < NA; ++A)
-          for (int i = 0; i < D; ++i) ue[A * D + i] = uv[nodes[A] * D + i];
-        element_apply<D, T>(chat_cell + (size_t)el * NA * nc, nc, wq, inv_h, ue, fe);
-        T* yv = ys + (size_t)v * n;
-        for (int A = 0; A < NA; ++A)
-          for (int i = 0; i < D; ++i) yv[nodes[A] * D + i] += fe[A * D + i];
+          for (int i = 0; i < D; ++i) ue[A * D + i] = live ? uv[nodes[A] * D + i] : T(0);
+        gp_apply<D, T>(chat_cell + ((size_t)el * NA + gp) * nc, gp, wq, inv_h, ue, fe);
+#pragma unroll
+        for (int k = 0; k < NA * D; ++k)
+          for (int o = 1; o < NA; o <<= 1) fe[k] += __shfl_xor_sync(0xffffffffu, fe[k], o);
+        if (live && gp == 0) {
+          T* yv = ys + (size_t)v * n;
+          for (int A = 0; A < NA; ++A)
+            for (int i = 0; i < D; ++i) yv[nodes[A] * D + i] += fe[A * D + i];
+        }
       }
       __syncthreads();
     }
@@ -360,6 +367,78 @@ __global__ void __launch_bounds__(kMultiThreads, 2) apply_K_multi_kernel(
   }
 }
 
+// ---- K_rr^(s) R for many vectors as a sparse product (Eq. 46b, mixed path)
+// Every cell has the same sparsity pattern, so K_rr^(s) (remaining DOF, local (i, d) order) is
+// stored in ELL form: one column table [slot][row] shared by all cells and FP32 values
+// [cell][slot][row] (row fastest, so a warp's 32 rows read 128 contiguous bytes per slot).  The
+// values are summed from the element matrices once per setup, in a fixed order.
+
+// val[cell][slot][row] = sum over the entry's contributions of Ke[cell][el][a][b]
+__global__ void krr_ell_assemble_kernel(const float* __restrict__ Ke, long long ke_cell, const int* __restrict__ cnt,
+                                        const int* __restrict__ idx, int cmax, int nnz, int nr, long long ncell,
+                                        float* __restrict__ val) {
+  const long long per = (long long)nnz * nr;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ncell * per;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long cell = t / per;
+    const int e = (int)(t - cell * per);
+    const float* kc = Ke + cell * ke_cell;
+    float v = 0.f;
+    for (int q = 0; q < cnt[e]; ++q) v += kc[idx[(long long)e * cmax + q]];
+    val[t] = v;
+  }
+}
+
+constexpr int kSpVB = 16;   // vectors per block
+constexpr int kSpLd = 20;   // shared row stride (floats): 16 vectors + 4, conflict-free 16-byte reads
+// One block per (cell, rhs, chunk of kSpVB vectors), cell slowest: the vectors of the chunk are
+// staged transposed ([dof][vector]) in shared memory, each thread owns rows and accumulates the
+// chunk's kSpVB products in registers (four 16-byte shared reads per 16 FMAs per slot).
+__global__ void __launch_bounds__(256) krr_spmm_f32_kernel(const int* __restrict__ ecol, const float* __restrict__ eval,
+                                                           int nnz, int nr, int nrhs, int nchunk,
+                                                           const float* __restrict__ u, long long u_rs, int u_cs,
+                                                           float* __restrict__ y, long long y_rs, int y_cs, int nvec,
+                                                           long long ext) {
+  extern __shared__ __align__(16) float uss[];   // [nr][kSpLd]
+  const int chunk = (int)(blockIdx.x % nchunk);
+  const long long rest = blockIdx.x / nchunk;
+  const int rhs = (int)(rest % nrhs);
+  const long long cell = rest / nrhs;
+  const int v0 = chunk * kSpVB, vb = min(kSpVB, nvec - v0);
+  const long long base = rhs * u_rs + cell * u_cs;
+  for (int t = threadIdx.x; t < kSpVB * nr; t += blockDim.x) {
+    const int v = t / nr, q = t - v * nr;
+    float x = 0.f;
+    if (v < vb && FD_INB(base + (long long)(v0 + v) * nr + q, ext, 205)) x = u[base + (long long)(v0 + v) * nr + q];
+    uss[q * kSpLd + v] = x;
+  }
+  __syncthreads();
+  const float* ev = eval + cell * (long long)nnz * nr;
+  const long long ybase = rhs * y_rs + cell * y_cs;
+  for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+    float acc[kSpVB];
+#pragma unroll
+    for (int v = 0; v < kSpVB; ++v) acc[v] = 0.f;
+#pragma unroll 4
+    for (int sl = 0; sl < nnz; ++sl) {
+      const int col = __ldg(ecol + (long long)sl * nr + r);
+      const float a = __ldcs(ev + (long long)sl * nr + r);
+      const float4* xs = reinterpret_cast<const float4*>(uss + col * kSpLd);
+#pragma unroll
+      for (int v4 = 0; v4 < kSpVB / 4; ++v4) {
+        const float4 x = xs[v4];
+        acc[4 * v4] = fmaf(a, x.x, acc[4 * v4]);
+        acc[4 * v4 + 1] = fmaf(a, x.y, acc[4 * v4 + 1]);
+        acc[4 * v4 + 2] = fmaf(a, x.z, acc[4 * v4 + 2]);
+        acc[4 * v4 + 3] = fmaf(a, x.w, acc[4 * v4 + 3]);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < kSpVB; ++v)
+      if (v < vb && FD_INB(ybase + (long long)(v0 + v) * nr + r, ext, 206)) y[ybase + (long long)(v0 + v) * nr + r] = acc[v];
+  }
+}
+
 // Per-cell dense operators: y[rhs,cell] = alpha M_cell x[rhs,cell] + beta y, M_cell at
 // mats + cell*mstride with row stride ld (sub-blocks of the per-cell ROM operators).
 constexpr int kMaxRhsGemv = 8;
@@ -508,9 +587,12 @@ __global__ void __launch_bounds__(256) rom_combine_f32_kernel(const double* __re
 }
 
 // y[rhs][cell][0..rows) = alpha M_f32[cell] x[rhs][cell][0..cols) + beta y: one CTA per cell,
-// x converted to FP32 in shared memory, one warp per row with 16-byte loads of the row (ldm a
-// multiple of 4, 16-byte aligned matrices), FP32 accumulation for up to kMaxRhsF32 columns.
+// x converted to FP32 in shared memory, one warp per pair of rows.  Each lane issues all T 16-byte
+// loads of its share of both rows before any arithmetic (2T loads in flight per lane, streamed
+// past L2), then reads each x chunk once for both rows; FP32 accumulation for up to kMaxRhsF32
+// columns.  ldm is a multiple of 4 and the matrices are 16-byte aligned.
 constexpr int kMaxRhsF32 = 8;
+template <int T>
 __global__ void __launch_bounds__(256) cell_gemm_f32_kernel(const float* __restrict__ mats, int ldm, int rows,
                                                             int cols, const double* __restrict__ x, long long x_rs,
                                                             int x_cs, double* __restrict__ y, long long y_rs,
@@ -525,31 +607,46 @@ __global__ void __launch_bounds__(256) cell_gemm_f32_kernel(const float* __restr
   const float4* M = reinterpret_cast<const float4*>(mats + cell * (long long)rows * ldm);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int n4 = ldm >> 2;
-  for (int row = warp; row < rows; row += nw) {
-    const float4* Mr = M + (long long)row * n4;
+  for (int row = 2 * warp; row < rows; row += 2 * nw) {
+    const bool two = row + 1 < rows;
+    float4 m0[T], m1[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+      const int j = lane + 32 * t;
+      const bool in = j < n4;
+      m0[t] = in ? __ldcs(M + (long long)row * n4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+      m1[t] = (in && two) ? __ldcs(M + (long long)(row + 1) * n4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     for (int rb0 = 0; rb0 < nrhs; rb0 += kMaxRhsF32) {
       const int rb = min(kMaxRhsF32, nrhs - rb0);
-      float acc[kMaxRhsF32];
+      float a0[kMaxRhsF32], a1[kMaxRhsF32];
 #pragma unroll
-      for (int q = 0; q < kMaxRhsF32; ++q) acc[q] = 0.f;
-      for (int j = lane; j < n4; j += 32) {
-        const float4 m4 = __ldcs(Mr + j);   // streamed once per apply: keep it out of L2's way
+      for (int q = 0; q < kMaxRhsF32; ++q) { a0[q] = 0.f; a1[q] = 0.f; }
+#pragma unroll
+      for (int t = 0; t < T; ++t) {
+        const int j = lane + 32 * t;
+        if (j >= n4) break;
 #pragma unroll
         for (int q = 0; q < kMaxRhsF32; ++q) {
           if (q < rb) {
             const float4 x4 = reinterpret_cast<const float4*>(xsf + (rb0 + q) * ldm)[j];
-            acc[q] = fmaf(m4.x, x4.x, fmaf(m4.y, x4.y, fmaf(m4.z, x4.z, fmaf(m4.w, x4.w, acc[q]))));
+            a0[q] = fmaf(m0[t].x, x4.x, fmaf(m0[t].y, x4.y, fmaf(m0[t].z, x4.z, fmaf(m0[t].w, x4.w, a0[q]))));
+            a1[q] = fmaf(m1[t].x, x4.x, fmaf(m1[t].y, x4.y, fmaf(m1[t].z, x4.z, fmaf(m1[t].w, x4.w, a1[q]))));
           }
         }
       }
 #pragma unroll
       for (int q = 0; q < kMaxRhsF32; ++q) {
         if (q < rb) {
-          float sv = acc[q];
-          for (int o = 16; o > 0; o >>= 1) sv += __shfl_down_sync(0xffffffffu, sv, o);
+          float s0 = a0[q], s1 = a1[q];
+          for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_down_sync(0xffffffffu, s0, o);
+            s1 += __shfl_down_sync(0xffffffffu, s1, o);
+          }
           if (lane == 0) {
             double* dst = y + (rb0 + q) * y_rs + cell * y_cs + row;
-            *dst = (beta == 0.0) ? alpha * (double)sv : alpha * (double)sv + beta * (*dst);
+            *dst = (beta == 0.0) ? alpha * (double)s0 : alpha * (double)s0 + beta * (*dst);
+            if (two) dst[1] = (beta == 0.0) ? alpha * (double)s1 : alpha * (double)s1 + beta * dst[1];
           }
         }
       }
@@ -768,6 +865,108 @@ __device__ __forceinline__ void neumaier_add(T& s, T& c, T x) {
   const T t = s + x;
   c += (fabs(s) >= fabs(x)) ? ((s - t) + x) : ((x - t) + s);
   s = t;
+}
+
+// Eq. 46b in FP32 for one (rhs, cell) per block of 256 threads: G = R^T (K R) and h = R^T v from
+// 32-entry chunks of the basis staged in shared memory, each thread a strided 4 x 4 tile of G
+// (rows ti + 16a, columns tj + 16b: a broadcast read of R and a conflict-free read of K R per
+// product), FP32 chunk sums accumulated with Neumaier's compensation; then warp 0 runs the same
+// diagonal-pivoted Cholesky solve as the warp kernel, and all threads form x = R c.
+constexpr int kGbQ = 32;
+constexpr int kGbLd = 33;
+__host__ __device__ inline size_t gram_block_smem(int nrb) {
+  const size_t ld = (size_t)nrb + 1;
+  return sizeof(double) * (2 * nrb * ld + 6 * (size_t)nrb) + sizeof(float) * (2 * (size_t)nrb * kGbLd + kGbQ);
+}
+__global__ void __launch_bounds__(256) gram_block_f32_kernel(const float* __restrict__ R, const float* __restrict__ KR,
+                                                             const double* __restrict__ v, long long v_rs, int v_cs,
+                                                             double* __restrict__ x, long long x_rs, int x_cs, int nr,
+                                                             int nrb, long long ncell, double drop_rel) {
+  extern __shared__ __align__(16) double gbsm[];
+  const int ld = nrb + 1;
+  double* S = gbsm;                                  // [nrb][ld]
+  double* Lc = S + (size_t)nrb * ld;                 // [nrb][ld]
+  double* hs = Lc + (size_t)nrb * ld;
+  double* ys = hs + nrb;
+  double* cs = ys + nrb;
+  double* colv = cs + nrb;
+  int* piv = reinterpret_cast<int*>(colv + nrb);     // nrb ints in 2 nrb doubles of room
+  float* Rs = reinterpret_cast<float*>(colv + 3 * nrb);
+  float* Ks = Rs + (size_t)nrb * kGbLd;
+  float* vs = Ks + (size_t)nrb * kGbLd;
+  const long long col = blockIdx.x;                  // rhs * ncell + cell
+  const int rhs = (int)(col / ncell);
+  const long long cell = col - (long long)rhs * ncell;
+  const float* Rc = R + col * (long long)nrb * nr;
+  const float* KRc = KR + col * (long long)nrb * nr;
+  const double* vc = v + rhs * v_rs + cell * v_cs;
+  const int tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
+  float acc[4][4], cmp[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) { acc[a][b] = 0.f; cmp[a][b] = 0.f; }
+  float hacc = 0.f, hcmp = 0.f;
+  for (int q0 = 0; q0 < nr; q0 += kGbQ) {
+    __syncthreads();                                  // the previous chunk is no longer read
+    for (int t = tid; t < nrb * kGbQ; t += blockDim.x) {
+      const int i = t / kGbQ, qq = t - i * kGbQ, q = q0 + qq;
+      Rs[i * kGbLd + qq] = q < nr ? Rc[(size_t)i * nr + q] : 0.f;
+      Ks[i * kGbLd + qq] = q < nr ? KRc[(size_t)i * nr + q] : 0.f;
+    }
+    if (tid < kGbQ) vs[tid] = q0 + tid < nr ? (float)vc[q0 + tid] : 0.f;
+    __syncthreads();
+    float part[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) part[a][b] = 0.f;
+#pragma unroll 8
+    for (int qq = 0; qq < kGbQ; ++qq) {
+      float rv[4], kv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int i = ti + 16 * a, j = tj + 16 * a;
+        rv[a] = i < nrb ? Rs[i * kGbLd + qq] : 0.f;
+        kv[a] = j < nrb ? Ks[j * kGbLd + qq] : 0.f;
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) part[a][b] = fmaf(rv[a], kv[b], part[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) neumaier_add(acc[a][b], cmp[a][b], part[a][b]);
+    if (tid < nrb) {
+      float hp = 0.f;
+      for (int qq = 0; qq < kGbQ; ++qq) hp = fmaf(Rs[tid * kGbLd + qq], vs[qq], hp);
+      neumaier_add(hacc, hcmp, hp);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = ti + 16 * a, j = tj + 16 * b;
+      if (i < nrb && j < nrb && i <= j) S[i * ld + j] = (double)acc[a][b] + (double)cmp[a][b];
+    }
+  if (tid < nrb) hs[tid] = (double)hacc + (double)hcmp;
+  __syncthreads();
+  for (int t = tid; t < nrb * nrb; t += blockDim.x) {   // the upper triangle, mirrored
+    const int i = t / nrb, j = t - (t / nrb) * nrb;
+    if (i > j) S[i * ld + j] = S[j * ld + i];
+  }
+  __syncthreads();
+  if (tid < 32) warp_pivoted_gram_solve(S, Lc, hs, ys, cs, colv, piv, nrb, ld, drop_rel, tid);
+  __syncthreads();
+  double* xc = x + rhs * x_rs + cell * x_cs;
+  for (int q = tid; q < nr; q += blockDim.x) {
+    float sx = 0.f;
+    for (int i = 0; i < nrb; ++i) sx += (float)cs[i] * Rc[(size_t)i * nr + q];
+    xc[q] = (double)sx;
+  }
 }
 
 template <typename TB>
@@ -1024,8 +1223,8 @@ fetidp_status k_snapshots(Ctx& c) {
 
 // u, y: column (rhs, cell) holds nvec vectors of length len (n, or n_r when r_only).
 fetidp_status k_apply_K(Ctx& c, CCellVec u, CellVec y, int nvec, int nrhs, bool idp, bool r_only,
-                        const double* chat, double /*unused*/) {
-  const int len = r_only ? c.nr : c.n;
+                        const double* chat, double /*unused*/, int len_override) {
+  const int len = len_override > 0 ? len_override : (r_only ? c.nr : c.n);
   const int VB = nvec < 8 ? nvec : 8;
   {
     const double D = c.d, NA = c.ngp;
@@ -1055,6 +1254,18 @@ fetidp_status k_apply_K(Ctx& c, CCellVec u, CellVec y, int nvec, int nrhs, bool 
 }
 
 // FP32 element matrices of every cell (mixed path), formed once per setup.
+fetidp_status k_krr_ell_assemble(Ctx& c, const int* cnt, const int* idx, int cmax) {
+  const int NA = 1 << c.d, ND = NA * c.d;
+  FD_TRY(dalloc_t(c, &c.krr_val, (size_t)c.N * c.krr_nnz * c.nr));
+  ProfScope ps(c, FETIDP_K_SETUP, 0.0, 4.0 * (double)c.N * c.krr_nnz * c.nr * 2.0);
+  const long long work = c.N * (long long)c.krr_nnz * c.nr;
+  const int grid = (int)std::min<long long>((work + 255) / 256, 152LL * 64);
+  krr_ell_assemble_kernel<<<grid, 256, 0, c.stream>>>(c.Ke_all, (long long)c.nelem * ND * ND, cnt, idx, cmax,
+                                                     c.krr_nnz, c.nr, c.N, c.krr_val);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
 fetidp_status k_element_matrices_f32(Ctx& c) {
   const int NA = 1 << c.d, ND = NA * c.d;
   FD_TRY(dalloc_t(c, &c.Ke_all, (size_t)c.N * c.nelem * ND * ND));
@@ -1074,6 +1285,19 @@ fetidp_status k_element_matrices_f32(Ctx& c) {
 // FP32 variant (local ROM bases of the mixed path): u, y float with the same view strides.
 fetidp_status k_apply_K_f32(Ctx& c, const float* u, long long u_rs, int u_cs, float* y, long long y_rs,
                             int y_cs, int nvec, int nrhs, bool idp, bool r_only, long long ext) {
+  if (idp && r_only && c.krr_val) {   // sparse K_rr in ELL form
+    const int nchunk = (nvec + kSpVB - 1) / kSpVB;
+    const size_t smem = (size_t)c.nr * kSpLd * sizeof(float);
+    // algorithmic work: one FMA per stored entry and vector; bytes: the values once per cell, the
+    // vectors in and out
+    ProfScope ps(c, FETIDP_K_MULTI_K, 2.0 * (double)c.N * nrhs * nvec * c.krr_nnz * c.nr,
+                 4.0 * (double)c.N * c.krr_nnz * c.nr + 8.0 * (double)c.N * nrhs * nvec * c.nr);
+    cudaFuncSetAttribute(krr_spmm_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    krr_spmm_f32_kernel<<<(unsigned)(c.N * nrhs * nchunk), 256, smem, c.stream>>>(
+        c.krr_col, c.krr_val, c.krr_nnz, c.nr, nrhs, nchunk, u, u_rs, u_cs, y, y_rs, y_cs, nvec, ext);
+    FD_CHECK_LAUNCH();
+    return FETIDP_OK;
+  }
   if (!c.Ke_all) {
     set_error("multi-vector K_s: element matrices not formed");
     return FETIDP_EINVAL;
@@ -1107,7 +1331,7 @@ fetidp_status k_apply_K_f32(Ctx& c, const float* u, long long u_rs, int u_cs, fl
     c.prof_pending_flops = 2.0 * cols * c.nelem * (double)nvec * ND * ND;
     c.prof_pending_bytes = (double)c.N * c.nelem * (double)ND * ND * 4.0 + cols * 2.0 * nvec * len * 4.0;
   }
-  ProfScope ps(c, FETIDP_K_APPLY_K, c.prof_pending_flops, c.prof_pending_bytes);
+  ProfScope ps(c, FETIDP_K_MULTI_K, c.prof_pending_flops, c.prof_pending_bytes);
   const size_t smem = bytes(VB);
   const int nchunk = (nvec + VB - 1) / VB;
   const dim3 grid((unsigned)(c.N * nrhs * nchunk));
@@ -1151,12 +1375,26 @@ fetidp_status k_cell_gemm_f32(Ctx& c, const float* mats, int ldm, int rows, int 
     return FETIDP_EINVAL;
   }
   // algorithmic bytes: the operators once, the FP64 vectors in and out
-  ProfScope ps(c, FETIDP_K_CELL_GEMV, 2.0 * rows * cols * (double)c.N * nrhs,
+  ProfScope ps(c, FETIDP_K_ASM_OP, 2.0 * rows * cols * (double)c.N * nrhs,
                4.0 * c.N * (double)rows * ldm + 8.0 * c.N * (double)nrhs * (rows + cols));
   const size_t smem = (size_t)nrhs * ldm * sizeof(float);
-  cudaFuncSetAttribute(cell_gemm_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cell_gemm_f32_kernel<<<(unsigned)c.N, 256, smem, c.stream>>>(mats, ldm, rows, cols, x.p, x.rs, x.cs, y.p, y.rs,
-                                                               y.cs, alpha, beta, nrhs);
+  const int T = (ldm / 4 + 31) / 32;
+  if (T > 8) { set_error("FP32 cell operators wider than 1024 columns"); return FETIDP_EINVAL; }
+  auto launch = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<(unsigned)c.N, 256, smem, c.stream>>>(mats, ldm, rows, cols, x.p, x.rs, x.cs, y.p, y.rs, y.cs, alpha,
+                                                 beta, nrhs);
+  };
+  switch (T) {
+    case 1: launch(cell_gemm_f32_kernel<1>); break;
+    case 2: launch(cell_gemm_f32_kernel<2>); break;
+    case 3: launch(cell_gemm_f32_kernel<3>); break;
+    case 4: launch(cell_gemm_f32_kernel<4>); break;
+    case 5: launch(cell_gemm_f32_kernel<5>); break;
+    case 6: launch(cell_gemm_f32_kernel<6>); break;
+    case 7: launch(cell_gemm_f32_kernel<7>); break;
+    default: launch(cell_gemm_f32_kernel<8>); break;
+  }
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }
@@ -1222,34 +1460,47 @@ fetidp_status k_grouped_gemm_n(Ctx& c, const double* A, long long a_stride_k, in
 
 template <typename TB>
 static fetidp_status gram_solve_t(Ctx& c, const TB* R, const TB* KR, CCellVec v, CellVec x, int nrhs,
-                                  double drop_rel) {
+                                  double drop_rel, int len = -1) {
+  if (len < 0) len = c.nr;
   if (c.nrb > kMaxRb) {
     set_error("n_rb above 64 is not supported by the Gram solve");
     return FETIDP_EINVAL;
   }
   const long long cols = c.N * nrhs;
-  ProfScope ps(c, FETIDP_K_GRAM, cols * 2.0 * c.nr * (c.nrb * (c.nrb + 1) / 2.0 + 2.0 * c.nrb),
-               cols * (double)sizeof(TB) * (2.0 * c.nrb * c.nr) + cols * 16.0 * c.nr);
+  ProfScope ps(c, FETIDP_K_GRAM, cols * 2.0 * len * (c.nrb * (c.nrb + 1) / 2.0 + 2.0 * c.nrb),
+               cols * (double)sizeof(TB) * (2.0 * c.nrb * len) + cols * 16.0 * len);
   const size_t per_warp = (size_t)gram_warp_doubles(c.nrb, (int)sizeof(TB)) * sizeof(double);
   int wpb = (int)std::min<size_t>(8, (200 * 1024) / per_warp);
   if (wpb < 1) wpb = 1;
   const size_t smem = per_warp * wpb;
   cudaFuncSetAttribute(gram_warp_kernel<TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   gram_warp_kernel<TB><<<(unsigned)ceil_div(cols, wpb), 32 * wpb, smem, c.stream>>>(
-      R, KR, v.p, v.rs, v.cs, x.p, x.rs, x.cs, c.nr, c.nrb, c.N, nrhs, drop_rel);
+      R, KR, v.p, v.rs, v.cs, x.p, x.rs, x.cs, len, c.nrb, c.N, nrhs, drop_rel);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }
 
 fetidp_status k_gram_solve(Ctx& c, const double* R, const double* KR, CCellVec v, CellVec x,
-                           int nrhs) {
-  return gram_solve_t<double>(c, R, KR, v, x, nrhs, 1e-12);
+                           int nrhs, int len) {
+  return gram_solve_t<double>(c, R, KR, v, x, nrhs, 1e-12, len);
 }
 
 fetidp_status k_gram_solve_f32(Ctx& c, const float* R, const float* KR, CCellVec v, CellVec x,
                                int nrhs, long long r_ext) {
   (void)r_ext;
-  return gram_solve_t<float>(c, R, KR, v, x, nrhs, c.opt.gram_drop_mixed);
+  if (c.nrb > kMaxRb) {
+    set_error("n_rb above 64 is not supported by the Gram solve");
+    return FETIDP_EINVAL;
+  }
+  const long long cols = c.N * nrhs;
+  ProfScope ps(c, FETIDP_K_GRAM, cols * 2.0 * c.nr * ((double)c.nrb * c.nrb + c.nrb) + cols * 2.0 * c.nr * c.nrb,
+               cols * 4.0 * (2.0 * c.nrb * c.nr) + cols * 16.0 * c.nr);
+  const size_t smem = gram_block_smem(c.nrb);
+  cudaFuncSetAttribute(gram_block_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  gram_block_f32_kernel<<<(unsigned)cols, 256, smem, c.stream>>>(R, KR, v.p, v.rs, v.cs, x.p, x.rs, x.cs, c.nr,
+                                                                  c.nrb, c.N, c.opt.gram_drop_mixed);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
 }
 
 fetidp_status k_grad(Ctx& c, const double* u, const double* w, double* g) {

@@ -27,18 +27,10 @@ __device__ __forceinline__ double tinv(int a, int b, int n) {
   return (double)((lo + 1) * (n - hi)) / (double)(n + 1);
 }
 
-__device__ __forceinline__ double d_scaled(const double* __restrict__ l, const int* __restrict__ dinfo,
-                                           int row, int d) {
-  const int code = dinfo[row];
-  const int n = code >> 8, q = code & 0xff;
-  if (n == 0) return l[row];
-  double v = 0.0;
-  for (int b = 0; b < n; ++b) v += tinv(q, b, n) * l[row + (b - q) * d];
-  return v;
-}
 
-// x_d = B_d^T lambda, or B_d^T D lambda when dinfo is given.  One thread per (cell, dual DOF)
-// for every RHS: the index codes are read once and reused for all load cases.
+// x_d = B_d^T lambda, or B_d^T D lambda when dinfo is given.  One thread per (cell, dual DOF):
+// the (multiplier row, weight) terms of the entry -- at most two signed rows, each expanded into
+// at most three rows by the D block -- are decoded once, then applied to every RHS.
 __global__ void gather_BT_kernel(const int* __restrict__ gath, const double* __restrict__ lam,
                                  long long lam_rs, const int* __restrict__ dinfo, int d,
                                  double* __restrict__ out, long long out_rs, int out_cs, int nd,
@@ -49,46 +41,36 @@ __global__ void gather_BT_kernel(const int* __restrict__ gath, const double* __r
     const long long cell = cj / nd;
     const int j = (int)(cj - cell * nd);
     const int2 cc = reinterpret_cast<const int2*>(gath)[cj];
-    const int row0 = (cc.x > 0 ? cc.x : -cc.x) - 1, row1 = (cc.y > 0 ? cc.y : -cc.y) - 1;
+    int idx[6];
+    double w[6];
+    int nt = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int code = h ? cc.y : cc.x;
+      if (code == 0) continue;
+      const int row = (code > 0 ? code : -code) - 1;
+      const double sg = code > 0 ? 1.0 : -1.0;
+      const int dc = dinfo ? dinfo[row] : 0;
+      const int n = dc >> 8, q = dc & 0xff;
+      if (n == 0) {
+        idx[nt] = row; w[nt] = sg; ++nt;
+      } else {
+        for (int b = 0; b < n; ++b) { idx[nt] = row + (b - q) * d; w[nt] = sg * tinv(q, b, n); ++nt; }
+      }
+    }
     for (int rhs = 0; rhs < nrhs; ++rhs) {
       const double* l = lam + rhs * lam_rs;
       double v = 0.0;
-      if (cc.x != 0) {
-        const double x = dinfo ? d_scaled(l, dinfo, row0, d) : l[row0];
-        v = cc.x > 0 ? x : -x;
-      }
-      if (cc.y != 0) {
-        const double x = dinfo ? d_scaled(l, dinfo, row1, d) : l[row1];
-        v += cc.y > 0 ? x : -x;
-      }
+      for (int k = 0; k < nt; ++k) v = fma(w[k], l[idx[k]], v);
       double* o = out + rhs * out_rs + cell * out_cs + j;
       *o = (beta == 0.0) ? v : v + beta * (*o);
     }
   }
 }
 
-// (B y)_row: the two signed terms of one multiplier row.
-__device__ __forceinline__ double b_row(const int* __restrict__ scat, const double* __restrict__ y,
-                                        int y_cs, int nd, long long row) {
-  double v = 0.0;
-  const int c0 = scat[2 * row], c1 = scat[2 * row + 1];
-  if (c0 != 0) {
-    const long long idx = (c0 > 0 ? c0 : -c0) - 1;
-    const long long cell = idx / nd;
-    const double x = y[cell * y_cs + (idx - cell * nd)];
-    v = c0 > 0 ? x : -x;
-  }
-  if (c1 != 0) {
-    const long long idx = (c1 > 0 ? c1 : -c1) - 1;
-    const long long cell = idx / nd;
-    const double x = y[cell * y_cs + (idx - cell * nd)];
-    v += c1 > 0 ? x : -x;
-  }
-  return v;
-}
-
-// z = alpha B y + beta z, or alpha D B y + beta z when dinfo is given.  One thread per row for
-// every RHS: the row's codes are read once.
+// z = alpha B y + beta z, or alpha D B y + beta z when dinfo is given.  One thread per row: the
+// (cell entry, weight) terms -- two signed copies of each of at most three chain rows -- are decoded
+// once, then applied to every RHS.
 __global__ void scatter_B_kernel(const int* __restrict__ scat, const double* __restrict__ yd,
                                  long long y_rs, int y_cs, int nd, const int* __restrict__ dinfo,
                                  int d, double* __restrict__ out, long long out_rs, long long L,
@@ -97,15 +79,29 @@ __global__ void scatter_B_kernel(const int* __restrict__ scat, const double* __r
        row += (long long)gridDim.x * blockDim.x) {
     const int code = dinfo ? dinfo[row] : 0;
     const int n = code >> 8, q = code & 0xff;
+    long long idx[6];
+    double w[6];
+    int nt = 0;
+    const int nb = n == 0 ? 1 : n;
+    for (int b = 0; b < nb; ++b) {
+      const long long r = n == 0 ? row : row + (long long)(b - q) * d;
+      const double wr = n == 0 ? 1.0 : tinv(q, b, n);
+      const int2 sc = reinterpret_cast<const int2*>(scat)[r];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = h ? sc.y : sc.x;
+        if (c == 0) continue;
+        const long long e = (c > 0 ? c : -c) - 1;
+        const long long cell = e / nd;
+        idx[nt] = cell * y_cs + (e - cell * nd);
+        w[nt] = c > 0 ? wr : -wr;
+        ++nt;
+      }
+    }
     for (int rhs = 0; rhs < nrhs; ++rhs) {
       const double* y = yd + rhs * y_rs;
-      double v;
-      if (n == 0) {
-        v = b_row(scat, y, y_cs, nd, row);
-      } else {
-        v = 0.0;
-        for (int b = 0; b < n; ++b) v += tinv(q, b, n) * b_row(scat, y, y_cs, nd, row + (long long)(b - q) * d);
-      }
+      double v = 0.0;
+      for (int k = 0; k < nt; ++k) v = fma(w[k], y[idx[k]], v);
       double* o = out + rhs * out_rs + row;
       *o = (beta == 0.0) ? alpha * v : alpha * v + beta * (*o);
     }

@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <thread>
 
 #include "common.cuh"
 #include "host_linalg.h"
@@ -78,7 +79,7 @@ RefCell build_ref(int d, int e, int& ni, int& nd, int& np) {
 }
 
 // f^(s) of one load case for one cell (natural order), Eq. 5b.
-void cell_load(const Ctx& c, const fetidp_problem& p, int load, int cx, int cy, int cz,
+void cell_load(const Ctx& c, const Geo& g, const fetidp_problem& p, int load, int cx, int cy, int cz,
                std::vector<double>& f) {
   const int d = c.d, e = c.e, NA = 1 << d;
   const double h = 1.0 / e;
@@ -90,8 +91,8 @@ void cell_load(const Ctx& c, const fetidp_problem& p, int load, int cx, int cy, 
       const int ec[3] = {el % e, (el / e) % e, el / (e * e)};
       for (int gp = 0; gp < NA; ++gp) {
         double eta[3], xi[3], J[3][3];
-        gauss_point(c.geo, cx, cy, cz, ec[0], ec[1], ec[2], gp, eta, xi);
-        macro_jacobian(c.geo, xi, J);
+        gauss_point(g, cx, cy, cz, ec[0], ec[1], ec[2], gp, eta, xi);
+        macro_jacobian(g, xi, J);
         double det;
         if (d == 2) det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
         else
@@ -114,7 +115,7 @@ void cell_load(const Ctx& c, const fetidp_problem& p, int load, int cx, int cy, 
     return;
   }
   const int ax = p.load_axis[load], side = p.load_side[load];
-  if (cc[ax] != (side ? c.geo.nc[ax] - 1 : 0)) return;
+  if (cc[ax] != (side ? g.nc[ax] - 1 : 0)) return;
   int tang[2], nt = 0;
   for (int k = 0; k < d; ++k)
     if (k != ax) tang[nt++] = k;
@@ -128,7 +129,7 @@ void cell_load(const Ctx& c, const fetidp_problem& p, int load, int cx, int cy, 
       double xi[3] = {0.0, 0.0, 0.0};
       for (int k = 0; k < d; ++k) xi[k] = cc[k] + (ec[k] + t[k]) * h;
       double J[3][3];
-      macro_jacobian(c.geo, xi, J);
+      macro_jacobian(g, xi, J);
       double meas;
       if (d == 2) {
         meas = std::sqrt(J[0][tang[0]] * J[0][tang[0]] + J[1][tang[0]] * J[1][tang[0]]);
@@ -228,6 +229,7 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
   }
   if (o.wait_budget_ns <= 0) { set_error("wait_budget_ns must be > 0"); return FETIDP_EINVAL; }
   if (o.mixed_assembled < -1 || o.mixed_assembled > 1) { set_error("mixed_assembled must be -1, 0 or 1"); return FETIDP_EINVAL; }
+  if (o.interface < 0 || o.interface > 1) { set_error("interface must be 0 or 1"); return FETIDP_EINVAL; }
   if (!(std::isfinite(o.tol_outer) && std::isfinite(o.tol_inner) && std::isfinite(o.tol_inner_mixed) &&
         o.tol_outer >= 0.0 && o.tol_inner >= 0.0 && o.tol_inner_mixed >= 0.0)) {
     set_error("tolerances must be finite and >= 0");
@@ -422,29 +424,45 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
   // ---------------------------------------------------------------- loads: rhs = (f_R, f_P, 0)
   {
     std::vector<double> rhs((size_t)c.m * c.ntot, 0.0), fpc((size_t)c.m * c.N * c.np, 0.0);
-    std::vector<double> f(c.n);
+    // each cell's loads (Eq. 5b) on the host threads; every cell writes only its own entries
+    auto cells_range = [&](long long s0, long long s1) {
+      std::vector<double> f(c.n);
+      for (int l = 0; l < c.m; ++l) {
+        double* rl = rhs.data() + (size_t)l * c.ntot;
+        for (long long s = s0; s < s1; ++s) {
+          int bl = 0;
+          while (bl + 1 < nprob && s >= c.lat[bl + 1].cell0) ++bl;
+          const fetidp_problem& pl = probs[bl];
+          const long long sl = s - c.lat[bl].cell0;
+          const int nx = pl.cells[0], ny = pl.cells[1];
+          const int cx = (int)(sl % nx), cy = (int)((sl / nx) % ny), cz = (int)(sl / ((long long)nx * ny));
+          cell_load(c, c.lat[bl].geo, pl, l, cx, cy, cz, f);
+          for (int li = 0; li < c.nr; ++li) rl[s * c.nr + li] = f[ref.perm[li]];
+          for (int q = 0; q < c.np; ++q) fpc[((size_t)l * c.N + s) * c.np + q] = f[ref.perm[c.nr + q]];
+        }
+      }
+    };
+    {
+      const long long nthr = std::max(1LL, std::min<long long>(std::thread::hardware_concurrency(), 32));
+      const long long per = (c.N + nthr - 1) / nthr;
+      std::vector<std::thread> pool;
+      for (long long t = 0; t < nthr; ++t) {
+        const long long s0 = t * per, s1 = std::min(c.N, s0 + per);
+        if (s0 < s1) pool.emplace_back(cells_range, s0, s1);
+      }
+      for (auto& th : pool) th.join();
+    }
+    // primal loads f_P = sum_s A_p f_p (Eq. 18), assembled in cell order
     for (int l = 0; l < c.m; ++l) {
       double* rl = rhs.data() + (size_t)l * c.ntot;
-      for (long long s = 0; s < c.N; ++s) {
-        int bl = 0;
-        while (bl + 1 < nprob && s >= c.lat[bl + 1].cell0) ++bl;
-        const fetidp_problem& pl = probs[bl];
-        const long long sl = s - c.lat[bl].cell0;
-        const int nx = pl.cells[0], ny = pl.cells[1];
-        const int cx = (int)(sl % nx), cy = (int)((sl / nx) % ny), cz = (int)(sl / ((long long)nx * ny));
-        c.geo = c.lat[bl].geo;
-        cell_load(c, pl, l, cx, cy, cz, f);
-        for (int li = 0; li < c.nr; ++li) rl[s * c.nr + li] = f[ref.perm[li]];
-        for (int q = 0; q < c.np; ++q) fpc[((size_t)l * c.N + s) * c.np + q] = f[ref.perm[c.nr + q]];
+      for (long long s = 0; s < c.N; ++s)
         for (int k = 0; k < c.ncorner; ++k) {
           const int vn = corner_v[(size_t)s * c.ncorner + k];
           if (vn < 0) continue;
           for (int comp = 0; comp < d; ++comp)
-            rl[c.N * c.nr + (size_t)vn * d + comp] += f[ref.perm[c.nr + k * d + comp]];
+            rl[c.N * c.nr + (size_t)vn * d + comp] += fpc[((size_t)l * c.N + s) * c.np + k * d + comp];
         }
-      }
     }
-    c.geo = c.lat[0].geo;
     FD_TRY(upload(c, &c.rhs, rhs));
     FD_TRY(upload(c, &c.rhs_p_cells, fpc));
     // per RHS: min over lattices of ||f_b|| / ||f|| (f_b: the lattice's remaining and primal loads)
@@ -554,6 +572,12 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
     FD_CUDA(cudaMemcpyAsync(sigma_dev, c.sigma.data(), sizeof(int) * nrb, cudaMemcpyHostToDevice, c.stream));
     FD_CUDA(cudaMemsetAsync(st_dev, 0, sizeof(int), c.stream));
     FD_TRY(k_assemble_principal(c, sigma_dev, nrb, c.Kinv, Krp_d, Kpp_d));
+    if (o.interface == 1) {   // Eq. 47: the principal interior blocks K_ii, inverted below
+      FD_TRY(dalloc_t(c, &c.Kii_inv, (size_t)nrb * ni * ni));
+      FD_TRY(k_batched_block_copy(c, c.Kinv, (long long)nr * nr, nr, 0, 0, c.Kii_inv, (long long)ni * ni, ni, ni,
+                                  ni, nrb, false));
+      FD_TRY(k_spd_inverse_batched(c, c.Kii_inv, (long long)ni * ni, ni, ni, nrb, st_dev));
+    }
     phase("  principal assembly");
     FD_TRY(k_spd_inverse_batched(c, c.Kinv, (long long)nr * nr, nr, nr, nrb, st_dev));
     phase("  principal K_rr inverse");
@@ -665,6 +689,54 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
     FD_TRY(k_rom_combine(c, c.Sdd, (long long)nd * nd, nd, 0, 0, nd, nd, c.alpha, c.Sdd_c, false));
   } else {          // mixed path: principal operators packed for the tensor cores
     FD_TRY(k_element_matrices_f32(c));
+    {
+      // ELL pattern of K_rr on the reference cell (remaining DOF, local order) and, for each
+      // stored entry, the element-matrix entries that sum into it (at most 2^d, fixed order)
+      const int d = c.d, e = c.e, NA = 1 << d, ND = NA * d, nn1 = e + 1;
+      std::vector<std::map<int, std::vector<int>>> rows(nr);
+      for (int el = 0; el < c.nelem; ++el) {
+        const int ex = el % e, ey = (el / e) % e, ez = d == 3 ? el / (e * e) : 0;
+        for (int a = 0; a < ND; ++a) {
+          const int A = a / d, ia = a % d;
+          const int na = (ex + (A & 1)) + nn1 * ((ey + ((A >> 1) & 1)) + nn1 * (d == 3 ? ez + ((A >> 2) & 1) : 0));
+          const int ga = ref.iperm[na * d + ia];
+          if (ga >= nr) continue;
+          for (int b = 0; b < ND; ++b) {
+            const int B = b / d, ib = b % d;
+            const int nb = (ex + (B & 1)) + nn1 * ((ey + ((B >> 1) & 1)) + nn1 * (d == 3 ? ez + ((B >> 2) & 1) : 0));
+            const int gb = ref.iperm[nb * d + ib];
+            if (gb >= nr) continue;
+            rows[ga][gb].push_back(el * ND * ND + a * ND + b);
+          }
+        }
+      }
+      int nnz = 0;
+      for (const auto& r : rows) nnz = std::max(nnz, (int)r.size());
+      const int cmax = NA;
+      std::vector<int> col((size_t)nnz * nr), cnt((size_t)nnz * nr, 0), idx((size_t)nnz * nr * cmax, 0);
+      for (int r = 0; r < nr; ++r) {
+        int sl = 0;
+        for (const auto& kv : rows[r]) {
+          col[(size_t)sl * nr + r] = kv.first;
+          cnt[(size_t)sl * nr + r] = (int)kv.second.size();
+          for (size_t q = 0; q < kv.second.size() && q < (size_t)cmax; ++q)
+            idx[((size_t)sl * nr + r) * cmax + q] = kv.second[q];
+          ++sl;
+        }
+        for (; sl < nnz; ++sl) col[(size_t)sl * nr + r] = r;   // padding: value 0 on the diagonal column
+      }
+      c.krr_nnz = nnz;
+      int *cnt_d = nullptr, *idx_d = nullptr;
+      FD_TRY(upload(c, &c.krr_col, col));
+      FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&cnt_d), sizeof(int) * cnt.size()));
+      FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&idx_d), sizeof(int) * idx.size()));
+      FD_CUDA(cudaMemcpyAsync(cnt_d, cnt.data(), sizeof(int) * cnt.size(), cudaMemcpyHostToDevice, c.stream));
+      FD_CUDA(cudaMemcpyAsync(idx_d, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, c.stream));
+      FD_TRY(k_krr_ell_assemble(c, cnt_d, idx_d, cmax));
+      FD_CUDA(cudaStreamSynchronize(c.stream));
+      tmp_free(c, cnt_d);
+      tmp_free(c, idx_d);
+    }
     const int split = o.tc_split == 3 ? 3 : 1;
     const long long ncols = c.N * c.m;
     FD_TRY(tc_pack_operator(c, c.opKinv, c.Kinv, (long long)nr * nr, nr, 0, 0, nr, nr, nrb, true, split));
@@ -759,14 +831,16 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
   FD_TRY(dalloc_t(c, &c.w_L1, m * c.L + 1));
   // local ROM bases R and K_s R (Eq. 46): FP64 in the FP64 path, FP32 in the mixed path
   const size_t rom_elems = m * c.N * nrb * nr;
-  FD_TRY(dalloc_t(c, &c.w_R, c.mixed ? (rom_elems + 1) / 2 : rom_elems));
-  FD_TRY(dalloc_t(c, &c.w_KR, c.mixed ? (rom_elems + 1) / 2 : rom_elems));
+  const bool rom_f32 = c.mixed && o.interface != 1;   // the Eq. 47 interior bases are FP64
+  FD_TRY(dalloc_t(c, &c.w_R, rom_f32 ? (rom_elems + 1) / 2 : rom_elems));
+  FD_TRY(dalloc_t(c, &c.w_KR, rom_f32 ? (rom_elems + 1) / 2 : rom_elems));
   FD_TRY(dalloc_t(c, &c.w_tot, 3 * m * c.ntot));
   // Krylov storage: one restart cycle (c.kry basis vectors and preconditioned vectors per RHS)
   FD_TRY(dalloc_t(c, &c.V, (size_t)(c.kry + 1) * m * c.ntot));
   FD_TRY(dalloc_t(c, &c.Z, (size_t)c.kry * m * c.ntot));
   FD_TRY(dalloc_t(c, &c.pcg, 6 * m * c.L + 1));
   FD_TRY(dalloc(c, reinterpret_cast<void**>(&c.chk), sizeof(int)));
+  if (o.interface == 1) FD_TRY(dalloc_t(c, &c.w_i, m * c.N * c.ni));
   FD_TRY(dalloc_t(c, &c.red, (size_t)m * (c.kry + 2) * 304));
   FD_TRY(dalloc_t(c, &c.scal, 64 * m + (size_t)m * (c.kry + 2) * 2));
   FD_CUDA(cudaMallocHost(&c.h_scal, sizeof(double) * (64 * m + (size_t)m * (c.kry + 2) * 2)));

@@ -32,7 +32,7 @@ constexpr int S_RZ0 = 0, S_RZ1 = 1, S_PQ = 2, S_RR = 3, S_ACT = 4, S_R0 = 5, S_E
 
 __global__ void copy_cells_kernel(const double* __restrict__ x, long long x_rs, int x_cs,
                                   double* __restrict__ y, long long y_rs, int y_cs, int len,
-                                  long long ncell, int nrhs) {
+                                  long long ncell, int nrhs, double scale) {
   const long long per = ncell * len;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < per * nrhs;
        t += (long long)gridDim.x * blockDim.x) {
@@ -40,7 +40,8 @@ __global__ void copy_cells_kernel(const double* __restrict__ x, long long x_rs, 
     const long long q = t - rhs * per;
     const long long cell = q / len;
     const int i = (int)(q - cell * len);
-    y[rhs * y_rs + cell * y_cs + i] = x[rhs * x_rs + cell * x_cs + i];
+    const double v = x[rhs * x_rs + cell * x_cs + i];
+    y[rhs * y_rs + cell * y_cs + i] = scale == 1.0 ? v : scale * v;
   }
 }
 
@@ -220,9 +221,9 @@ fetidp_status dalloc(Ctx& c, void** p, size_t bytes) {
 
 namespace {
 
-fetidp_status copy_cells(Ctx& c, CCellVec x, CellVec y, int len, int nrhs) {
+fetidp_status copy_cells(Ctx& c, CCellVec x, CellVec y, int len, int nrhs, double scale = 1.0) {
   copy_cells_kernel<<<gridn(c.N * len * nrhs), 256, 0, c.stream>>>(x.p, x.rs, x.cs, y.p, y.rs, y.cs,
-                                                                   len, c.N, nrhs);
+                                                                   len, c.N, nrhs, scale);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }
@@ -276,6 +277,34 @@ fetidp_status op_apply_MD(Ctx& c, const double* r, long long r_rs, double* z, lo
   else
     FD_TRY(cell_op(c, c.Sdd_c, (long long)nd * nd, nd, nd, nd, cview(g), yd, 1.0, 0.0));
   FD_TRY(k_scatter_B(c, cview(yd), z, z_rs, c.dinfo, 1.0, 0.0, m));
+  return FETIDP_OK;
+}
+
+// ------------------------------------------------------------------ Eq. 47
+// z = M_D^{-ROM} r: the Dirichlet preconditioner of Eq. 30 whose interior solves K_ii^(s)^{-1} are
+// approximated like Eq. 46 approximates K_rr^(s)^{-1}: R = [K_ii^(sigma_k)^{-1} v_i]_k and the
+// K_ii^(s)-orthogonal projection x_i = R (R^T K_ii R)^{-1} R^T v_i.  Every product with the cell's
+// own stiffness is the matrix-free K_s of Eq. 52 on full local vectors.
+fetidp_status op_apply_MD_rom(Ctx& c, const double* r, long long r_rs, double* z, long long z_rs) {
+  if (!c.Kii_inv) { set_error("the context was set up without the Eq. 47 interface option"); return FETIDP_EINVAL; }
+  const int m = c.m, nd = c.nd, ni = c.ni, n = c.n, nrb = c.nrb;
+  CellVec g{c.w_d1, c.N * nd, nd};
+  FD_TRY(k_gather_BT(c, r, r_rs, c.dinfo, g, m, 0.0));
+  // K_s (0; g; 0): its interior part is K_id g, its dual part K_dd g
+  CellVec ua{c.w_cell_a, c.N * n, n}, kb{c.w_cell_b, c.N * n, n};
+  FD_CUDA(cudaMemsetAsync(c.w_cell_a, 0, sizeof(double) * (size_t)m * c.N * n, c.stream));
+  FD_TRY(copy_cells(c, cview(g), CellVec{c.w_cell_a + ni, c.N * n, n}, nd, m));
+  FD_TRY(k_apply_K(c, cview(ua), kb, 1, m, true, false, c.snap, 0.0));
+  // x_i ~ K_ii^{-1} K_id g
+  CCellVec vi{c.w_cell_b, c.N * n, n};
+  CellVec R{c.w_R, c.N * nrb * ni, nrb * ni}, KR{c.w_KR, c.N * nrb * ni, nrb * ni}, xi{c.w_i, c.N * ni, ni};
+  FD_TRY(k_grouped_gemm(c, c.Kii_inv, (long long)ni * ni, ni, ni, ni, vi, R, nullptr, 1.0, 0.0, m, true, ni));
+  FD_TRY(k_apply_K(c, cview(R), KR, nrb, m, true, false, c.snap, 0.0, ni));
+  FD_TRY(k_gram_solve(c, c.w_R, c.w_KR, vi, xi, m, ni));
+  // y_d = K_dd g - K_di x_i = [K_s (-x_i; g; 0)]_d
+  FD_TRY(copy_cells(c, cview(xi), ua, ni, m, -1.0));
+  FD_TRY(k_apply_K(c, cview(ua), kb, 1, m, true, false, c.snap, 0.0));
+  FD_TRY(k_scatter_B(c, CCellVec{c.w_cell_b + ni, c.N * n, n}, z, z_rs, c.dinfo, 1.0, 0.0, m));
   return FETIDP_OK;
 }
 
@@ -542,8 +571,11 @@ fetidp_status op_precondition(Ctx& c, const double* x, double* y) {
   // w_bar = w - U_ring v  (Algorithm 3; keeps z_P = x_P of Algorithm 2 in w_zP)
   FD_TRY(U_apply(c, vR, vP, nt, c.w_L1, c.L));
   FD_TRY(axpby(c, w, nt, c.w_L1, c.L, pcg_b, c.L, 1.0, -1.0, c.L, m));
-  // y = -F_ring^{-pcg} w_bar
-  FD_TRY(pcg_solve(c, pcg_b, c.L, yL, nt));
+  // y = -F_ring^{-pcg} w_bar, or y = -M_D^{-ROM} w_bar (Eq. 47)
+  if (c.opt.interface == 1)
+    FD_TRY(op_apply_MD_rom(c, pcg_b, c.L, yL, nt));
+  else
+    FD_TRY(pcg_solve(c, pcg_b, c.L, yL, nt));
   FD_TRY(k_copy_scale(c, yL, yL, c.L, m, nt, nt, nullptr, -1.0));
   // x = K_ring^{-ROM} v - U_ring^T y   (Algorithm 2 with Eq. 46)
   FD_TRY(local_rom(c, vR, yR));
@@ -799,6 +831,7 @@ void fetidp_default_options(fetidp_options* o) {
   o->wait_budget_ns = 1000000000LL;
   o->check_inputs = 1;
   o->mixed_assembled = -1;
+  o->interface = 0;
 }
 
 const char* fetidp_status_string(fetidp_status s) {
@@ -1006,6 +1039,13 @@ fetidp_status fetidp_precond(fetidp_ctx* ctx, const double* r, double* z) {
   Ctx& c = ctx->c;
   FD_TRY(check_inputs(c, {{r, (long long)c.m * c.L, "r"}}, z));
   return check_waits(c, op_apply_MD(c, r, c.L, z, c.L));
+}
+
+fetidp_status fetidp_precond_rom(fetidp_ctx* ctx, const double* r, double* z) {
+  FD_TRY(enter(ctx));
+  Ctx& c = ctx->c;
+  FD_TRY(check_inputs(c, {{r, (long long)c.m * c.L, "r"}}, z));
+  return op_apply_MD_rom(c, r, c.L, z, c.L);
 }
 
 fetidp_status fetidp_gather_BT(fetidp_ctx* ctx, const double* lambda, double* x_d) {
