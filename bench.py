@@ -94,8 +94,8 @@ def sample_problem(name, cells):
     return q
 
 
-SAMPLES = {"cfg5": {"cpu": (4, 4, 2), "reference": (2, 2, 2)},
-           "cfg4": {"cpu": (4, 4, 2), "reference": (2, 2, 2)},
+SAMPLES = {"cfg5": {"cpu": (2, 2, 2), "reference": (2, 2, 1)},
+           "cfg4": {"cpu": (2, 2, 2), "reference": (2, 2, 1)},
            "cfg2": {"cpu": (16, 16, 1), "reference": (12, 12, 1)}}
 
 

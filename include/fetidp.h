@@ -155,6 +155,12 @@ typedef struct {
                                whose interior solves K_ii^(s)^{-1} are ROM approximations built
                                from the principal K_ii^{-1} as Eq. 46 builds the K_rr solves;
                                FP64 arithmetic in both precisions (0)                         */
+  int method;               /* 0 = ROM-based inexact FETI-DP (Secs. 3-4); 1 = standard FETI-DP
+                               (Sec. 2.2.4, the paper's comparison system): every cell's K_rr is
+                               factorised (dense inverse, N n_r^2 doubles), F and M_D are exact and
+                               the block preconditioner of Eq. 44 is exact, so FGMRES takes one
+                               outer iteration and the inner PCG is standard FETI-DP's.  FP64 with
+                               interface 0 only; fetidp_rom_data answers EINVAL (0)           */
 } fetidp_options;
 
 typedef struct {

@@ -67,7 +67,7 @@ class Options(ctypes.Structure):
                 ("tol_inner_mixed", ctypes.c_double), ("gram_drop_mixed", ctypes.c_double),
                 ("profile_mask", ctypes.c_uint), ("restart", ctypes.c_int),
                 ("wait_budget_ns", ctypes.c_longlong), ("check_inputs", ctypes.c_int),
-                ("mixed_assembled", ctypes.c_int), ("interface", ctypes.c_int)]
+                ("mixed_assembled", ctypes.c_int), ("interface", ctypes.c_int), ("method", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

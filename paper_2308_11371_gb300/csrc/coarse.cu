@@ -176,6 +176,163 @@ __global__ void bcr_final_kernel(const double* __restrict__ Ainv, int b, const d
   }
 }
 
+// ---- FP32 copy for the mixed path's inner iterations.  The level vectors hold up to eight RHS
+//      interleaved ([chunk][vec_len][8] floats), so one lane reads all RHS of a column as two
+//      16-byte loads; a warp computes one output row, each lane summing every 32nd column of it in
+//      FP32, and the eight lane partials are reduced in FP64.
+struct BcrLevelF {
+  int b, n, nch;
+  long long rs;                 // per-chunk stride of the level vectors, in 8-float entries
+  const float* mats;
+  const long long* offA;
+  const long long* offU;
+  const long long* offUT;
+  const long long* offV;
+  const long long* offVT;
+  float* bl_l;
+  float* bl_n;
+  float* xl_l;
+  const float* xl_n;
+};
+
+__device__ __forceinline__ void bcr_row_f32(const float* __restrict__ M, const float* __restrict__ v, int b,
+                                            int lane, float sgn, float acc[8]) {
+#pragma unroll 4
+  for (int q = lane; q < b; q += 32) {
+    const float mv = sgn * __ldcs(M + q);
+    const float4 a = *reinterpret_cast<const float4*>(v + (size_t)q * 8);
+    const float4 e = *reinterpret_cast<const float4*>(v + (size_t)q * 8 + 4);
+    acc[0] = fmaf(mv, a.x, acc[0]);
+    acc[1] = fmaf(mv, a.y, acc[1]);
+    acc[2] = fmaf(mv, a.z, acc[2]);
+    acc[3] = fmaf(mv, a.w, acc[3]);
+    acc[4] = fmaf(mv, e.x, acc[4]);
+    acc[5] = fmaf(mv, e.y, acc[5]);
+    acc[6] = fmaf(mv, e.z, acc[6]);
+    acc[7] = fmaf(mv, e.w, acc[7]);
+  }
+}
+
+// warp sum of the eight partials; lane 0 receives them in s[]
+__device__ __forceinline__ void bcr_warp_sum8(const float acc[8], double s[8]) {
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    double t = (double)acc[r];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    s[r] = t;
+  }
+}
+
+__global__ void bcr_forward_f32_kernel(BcrLevelF P) {
+  const int lane = threadIdx.x & 31;
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int n_new = (P.n + 1) / 2;
+  if (gw >= (long long)n_new * P.b) return;
+  const int inew = (int)(gw / P.b), row = (int)(gw - (long long)inew * P.b);
+  const int i = 2 * inew, b = P.b;
+  for (int ch = 0; ch < P.nch; ++ch) {
+    const float* vl = P.bl_l + (size_t)ch * P.rs * 8;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (i - 1 >= 0 && P.offUT[i - 1] >= 0)
+      bcr_row_f32(P.mats + P.offUT[i - 1] + (size_t)row * b, vl + (size_t)(i - 1) * b * 8, b, lane, 1.f, acc);
+    if (i + 1 < P.n)
+      bcr_row_f32(P.mats + P.offVT[i + 1] + (size_t)row * b, vl + (size_t)(i + 1) * b * 8, b, lane, 1.f, acc);
+    double s[8];
+    bcr_warp_sum8(acc, s);
+    if (lane == 0) {
+      const float* src = vl + ((size_t)i * b + row) * 8;
+      float* dst = P.bl_n + (size_t)ch * P.rs * 8 + ((size_t)inew * b + row) * 8;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) dst[r] = (float)((double)src[r] - s[r]);
+    }
+  }
+}
+
+__global__ void bcr_backward_f32_kernel(BcrLevelF P) {
+  const int lane = threadIdx.x & 31;
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (gw >= (long long)P.n * P.b) return;
+  const int j = (int)(gw / P.b), row = (int)(gw - (long long)j * P.b);
+  const int b = P.b;
+  for (int ch = 0; ch < P.nch; ++ch) {
+    const size_t co = (size_t)ch * P.rs * 8;
+    float* dst = P.xl_l + co + ((size_t)j * b + row) * 8;
+    if ((j & 1) == 0) {   // even block: copied from the reduced level
+      if (lane < 2)
+        reinterpret_cast<float4*>(dst)[lane] =
+            reinterpret_cast<const float4*>(P.xl_n + co + ((size_t)(j / 2) * b + row) * 8)[lane];
+      continue;
+    }
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    bcr_row_f32(P.mats + P.offA[j] + (size_t)row * b, P.bl_l + co + (size_t)j * b * 8, b, lane, 1.f, acc);
+    bcr_row_f32(P.mats + P.offV[j] + (size_t)row * b, P.xl_n + co + (size_t)((j - 1) / 2) * b * 8, b, lane, -1.f,
+                acc);
+    if (j + 1 < P.n)
+      bcr_row_f32(P.mats + P.offU[j] + (size_t)row * b, P.xl_n + co + (size_t)((j + 1) / 2) * b * 8, b, lane,
+                  -1.f, acc);
+    double s[8];
+    bcr_warp_sum8(acc, s);
+    if (lane == 0)
+#pragma unroll
+      for (int r = 0; r < 8; ++r) dst[r] = (float)s[r];
+  }
+}
+
+__global__ void bcr_final_f32_kernel(const float* __restrict__ Ainv, int b, const float* bl, float* xl,
+                                     long long rs, int nch) {
+  const int lane = threadIdx.x & 31;
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (gw >= b) return;
+  const int row = (int)gw;
+  for (int ch = 0; ch < nch; ++ch) {
+    const size_t co = (size_t)ch * rs * 8;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    bcr_row_f32(Ainv + (size_t)row * b, bl + co, b, lane, 1.f, acc);
+    double s[8];
+    bcr_warp_sum8(acc, s);
+    if (lane == 0)
+#pragma unroll
+      for (int r = 0; r < 8; ++r) xl[co + (size_t)row * 8 + r] = (float)s[r];
+  }
+}
+
+// level-0 right-hand sides: bl[ch][q][r8] = b[8 ch + r8][perm[q]] (0 on padding and absent RHS)
+__global__ void bcr_gather_f32_kernel(const int* __restrict__ perm, const double* __restrict__ b, long long b_rs,
+                                      float* __restrict__ bl, long long rs, long long len, int nrhs, int nch) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)nch * len * 8;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int r8 = (int)(t & 7);
+    const long long e = t >> 3;
+    const int ch = (int)(e / len);
+    const long long q = e - (long long)ch * len;
+    const int r = ch * 8 + r8;
+    const int pq = perm[q];
+    bl[((size_t)ch * rs + q) * 8 + r8] = (pq >= 0 && r < nrhs) ? (float)b[r * b_rs + pq] : 0.f;
+  }
+}
+
+__global__ void bcr_scatter_f32_kernel(const int* __restrict__ perm, const float* __restrict__ xl, long long rs,
+                                       double* __restrict__ x, long long x_rs, long long len, int nrhs) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len * nrhs;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(t / len);
+    const long long q = t - r * len;
+    const int pq = perm[q];
+    if (pq >= 0) x[r * x_rs + pq] = (double)xl[((size_t)(r >> 3) * rs + q) * 8 + (r & 7)];
+  }
+}
+
+// dst[dst_off[k] + e] = (float) src[src_off[k] + e] for e < bb, block k = blockIdx.y
+__global__ void bcr_convert_blocks_kernel(const double* __restrict__ src, const long long* __restrict__ src_off,
+                                          float* __restrict__ dst, const long long* __restrict__ dst_off,
+                                          long long bb) {
+  const double* s = src + src_off[blockIdx.y];
+  float* d = dst + dst_off[blockIdx.y];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < bb; e += (long long)gridDim.x * blockDim.x)
+    d[e] = (float)s[e];
+}
+
 // grid-stride kernels may cap the grid; the warp-per-row kernels may not
 inline int gridn(long long work, int threads = 256) {
   long long g = (work + threads - 1) / threads;
@@ -375,6 +532,44 @@ fetidp_status coarse_setup(Ctx& c, const double* Spp_dev) {
   FD_CUDA(cudaMemcpyAsync(B.perm, perm.data(), perm.size() * sizeof(int), cudaMemcpyHostToDevice, c.stream));
   FD_TRY(dalloc_t(c, &B.bl, (size_t)c.m * B.vec_len));
   FD_TRY(dalloc_t(c, &B.xl, (size_t)c.m * B.vec_len));
+  if (c.mixed) {
+    // FP32 copy of every used block, packed in table order; tab_f mirrors tab with the new offsets
+    std::vector<long long> tab_f(tab.size(), -1), src_off, dst_off;
+    long long pos = 0;
+    for (size_t k = 0; k < tab.size(); ++k) {
+      if (tab[k] < 0) continue;
+      tab_f[k] = pos;
+      src_off.push_back(tab[k]);
+      dst_off.push_back(pos);
+      pos += bb;
+    }
+    B.off_final_f = pos;
+    src_off.push_back(B.off_final);
+    dst_off.push_back(pos);
+    pos += bb;
+    FD_TRY(dalloc_t(c, &B.mats_f, (size_t)pos));
+    B.mat_bytes_f = (size_t)pos * sizeof(float);
+    FD_TRY(dalloc_t(c, &B.tables_f, tab_f.size() + 1));
+    if (!tab_f.empty())
+      FD_CUDA(cudaMemcpyAsync(B.tables_f, tab_f.data(), tab_f.size() * sizeof(long long), cudaMemcpyHostToDevice,
+                              c.stream));
+    long long* offs = nullptr;
+    const size_t nblk = src_off.size();
+    FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&offs), sizeof(long long) * 2 * nblk));
+    FD_CUDA(cudaMemcpyAsync(offs, src_off.data(), sizeof(long long) * nblk, cudaMemcpyHostToDevice, c.stream));
+    FD_CUDA(cudaMemcpyAsync(offs + nblk, dst_off.data(), sizeof(long long) * nblk, cudaMemcpyHostToDevice, c.stream));
+    for (size_t k0 = 0; k0 < nblk; k0 += 65535) {
+      const unsigned ny = (unsigned)std::min<size_t>(65535, nblk - k0);
+      bcr_convert_blocks_kernel<<<dim3((unsigned)std::min<long long>((bb + 255) / 256, 1024), ny), 256, 0,
+                                  c.stream>>>(B.mats, offs + k0, B.mats_f, offs + nblk + k0, bb);
+      FD_CHECK_LAUNCH();
+    }
+    const int nch = (c.m + 7) / 8;
+    FD_TRY(dalloc_t(c, &B.bl_f, (size_t)nch * B.vec_len * 8));
+    FD_TRY(dalloc_t(c, &B.xl_f, (size_t)nch * B.vec_len * 8));
+    FD_CUDA(cudaStreamSynchronize(c.stream));   // host offset lists go out of scope
+    tmp_free(c, offs);
+  }
   FD_CUDA(cudaStreamSynchronize(c.stream));   // host tables go out of scope
   return FETIDP_OK;
 }
@@ -422,6 +617,56 @@ fetidp_status coarse_solve(Ctx& c, const double* b, long long b_rs, double* x, l
     FD_CHECK_LAUNCH();
   }
   bcr_scatter_kernel<<<gridn(len0 * nrhs), 256, 0, c.stream>>>(B.perm, B.xl, rs, x, x_rs, len0, nrhs);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+// The same solve on the FP32 copy (mixed path): FP32 factor and level vectors, FP32 products summed
+// per lane, FP64 warp sums.  The rounding of the copy is a fixed linear perturbation of S_PP^{-1}.
+fetidp_status coarse_solve_f32(Ctx& c, const double* b, long long b_rs, double* x, long long x_rs, int nrhs) {
+  CoarseBCR& B = c.bcr;
+  if (!B.mats_f) return coarse_solve(c, b, b_rs, x, x_rs, nrhs);
+  const int nch = (nrhs + 7) / 8;
+  if (nch > (c.m + 7) / 8) { set_error("coarse solve: more RHS than the context holds"); return FETIDP_EINVAL; }
+  const long long len0 = (long long)B.nb * B.b;
+  const long long rs = B.vec_len;
+  ProfScope ps(c, FETIDP_K_COARSE, 2.0 * (B.mat_bytes_f / 4.0) * 8.0 * nch,
+               (double)B.mat_bytes_f + 4.0 * 8.0 * nch * 4.0 * B.vec_len);
+  bcr_gather_f32_kernel<<<gridn(len0 * nch * 8), 256, 0, c.stream>>>(B.perm, b, b_rs, B.bl_f, rs, len0, nrhs, nch);
+  FD_CHECK_LAUNCH();
+  std::vector<const long long*> tA(B.levels), tU(B.levels), tUT(B.levels), tV(B.levels), tVT(B.levels);
+  {
+    const long long* p = B.tables_f;
+    for (int l = 0; l < B.levels; ++l) {
+      const int n = B.n_at[l];
+      tA[l] = p; p += n;
+      tU[l] = p; p += n;
+      tUT[l] = p; p += n;
+      tV[l] = p; p += n;
+      tVT[l] = p; p += n;
+    }
+  }
+  for (int l = 0; l < B.levels; ++l) {
+    BcrLevelF P{B.b, B.n_at[l], nch, rs, B.mats_f, tA[l], tU[l], tUT[l], tV[l], tVT[l],
+                B.bl_f + B.vec_off[l] * 8, B.bl_f + B.vec_off[l + 1] * 8, nullptr, nullptr};
+    const long long warps = (long long)((B.n_at[l] + 1) / 2) * B.b;
+    bcr_forward_f32_kernel<<<grid_exact(warps * 32), 256, 0, c.stream>>>(P);
+    FD_CHECK_LAUNCH();
+  }
+  {
+    const int L = B.levels;
+    bcr_final_f32_kernel<<<grid_exact((long long)B.b * 32), 256, 0, c.stream>>>(
+        B.mats_f + B.off_final_f, B.b, B.bl_f + B.vec_off[L] * 8, B.xl_f + B.vec_off[L] * 8, rs, nch);
+    FD_CHECK_LAUNCH();
+  }
+  for (int l = B.levels - 1; l >= 0; --l) {
+    BcrLevelF P{B.b, B.n_at[l], nch, rs, B.mats_f, tA[l], tU[l], tUT[l], tV[l], tVT[l],
+                B.bl_f + B.vec_off[l] * 8, nullptr, B.xl_f + B.vec_off[l] * 8, B.xl_f + B.vec_off[l + 1] * 8};
+    const long long warps = (long long)B.n_at[l] * B.b;
+    bcr_backward_f32_kernel<<<grid_exact(warps * 32), 256, 0, c.stream>>>(P);
+    FD_CHECK_LAUNCH();
+  }
+  bcr_scatter_f32_kernel<<<gridn(len0 * nrhs), 256, 0, c.stream>>>(B.perm, B.xl_f, rs, x, x_rs, len0, nrhs);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }

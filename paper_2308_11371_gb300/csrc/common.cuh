@@ -144,6 +144,14 @@ struct CoarseBCR {
   double* bl = nullptr;            // device [m][vec_len] right-hand sides per level
   double* xl = nullptr;            // device [m][vec_len] solutions per level
   size_t mat_bytes = 0;
+  // mixed path: an FP32 copy of the used blocks (compact pool, same per-level table layout) and
+  // level vectors [rhs chunk of 8][vec_len][8] for the inner iterations' coarse correction
+  float* mats_f = nullptr;
+  long long* tables_f = nullptr;
+  long long off_final_f = 0;
+  float* bl_f = nullptr;
+  float* xl_f = nullptr;
+  size_t mat_bytes_f = 0;
 };
 
 // A principal-operator set packed for the tensor-core GEMM (BF16, SW128 K-major tiles).
@@ -245,6 +253,7 @@ struct Ctx {
   int* krr_col = nullptr;
   float* krr_val = nullptr;
   int krr_nnz = 0;
+  int* krr_nbr = nullptr;       // [nnz/d][nr/d] neighbour node of each node-level slot (nodal pattern)
   // Eq. 47 interface option: principal K_ii^{-1} [nrb][ni][ni] and the interior work vector
   double* Kii_inv = nullptr;
   double* w_i = nullptr;        // [m][N][ni]
@@ -265,6 +274,8 @@ struct Ctx {
   float* Sdd_f = nullptr;     // [N][nd][ld_f]
   int ld_f = 0;
   bool asm_f32 = false;
+  bool exact = false;         // standard FETI-DP: every cell's own K_rr^{-1} (nrb = N, no ROM)
+  float* Udp_f = nullptr;     // [N][nd][np] mixed path: the dual rows of U_rp_ring in FP32
   double* Urp_c = nullptr;    // [N][nr][np]
   double* UrpT_c = nullptr;   // [N][np][nr]
   // coarse solve
@@ -478,6 +489,8 @@ fetidp_status tc_comb_apply(Ctx& c, const TcComb& op, CCellVec X, const double* 
 // ---------------------------------------------------------------- setup / coarse
 fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, const fetidp_options& o);
 fetidp_status coarse_setup(Ctx& c, const double* Spp_dev);   // per-cell S_pp_ring on the device
+fetidp_status coarse_solve_f32(Ctx& c, const double* b, long long b_rs, double* x, long long x_rs, int nrhs);
+fetidp_status k_udp_f32(Ctx& c, bool trans, CCellVec x, CellVec y, double alpha, double beta, int nrhs);
 fetidp_status coarse_solve(Ctx& c, const double* b, long long b_rs, double* x, long long x_rs,
                            int nrhs);
 

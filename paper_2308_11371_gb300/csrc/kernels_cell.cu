@@ -419,23 +419,97 @@ __global__ void __launch_bounds__(256) krr_spmm_f32_kernel(const int* __restrict
     float acc[kSpVB];
 #pragma unroll
     for (int v = 0; v < kSpVB; ++v) acc[v] = 0.f;
-#pragma unroll 4
-    for (int sl = 0; sl < nnz; ++sl) {
-      const int col = __ldg(ecol + (long long)sl * nr + r);
-      const float a = __ldcs(ev + (long long)sl * nr + r);
-      const float4* xs = reinterpret_cast<const float4*>(uss + col * kSpLd);
+    // eight slots' (column, value) pairs are loaded before any of them is used
+    for (int sl0 = 0; sl0 < nnz; sl0 += 8) {
+      int cc[8];
+      float aa[8];
 #pragma unroll
-      for (int v4 = 0; v4 < kSpVB / 4; ++v4) {
-        const float4 x = xs[v4];
-        acc[4 * v4] = fmaf(a, x.x, acc[4 * v4]);
-        acc[4 * v4 + 1] = fmaf(a, x.y, acc[4 * v4 + 1]);
-        acc[4 * v4 + 2] = fmaf(a, x.z, acc[4 * v4 + 2]);
-        acc[4 * v4 + 3] = fmaf(a, x.w, acc[4 * v4 + 3]);
+      for (int u = 0; u < 8; ++u) {
+        const int sl = sl0 + u;
+        cc[u] = sl < nnz ? __ldg(ecol + (long long)sl * nr + r) : 0;
+        aa[u] = sl < nnz ? __ldcs(ev + (long long)sl * nr + r) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float4* xs = reinterpret_cast<const float4*>(uss + cc[u] * kSpLd);
+        const float a = aa[u];
+#pragma unroll
+        for (int v4 = 0; v4 < kSpVB / 4; ++v4) {
+          const float4 x = xs[v4];
+          acc[4 * v4] = fmaf(a, x.x, acc[4 * v4]);
+          acc[4 * v4 + 1] = fmaf(a, x.y, acc[4 * v4 + 1]);
+          acc[4 * v4 + 2] = fmaf(a, x.z, acc[4 * v4 + 2]);
+          acc[4 * v4 + 3] = fmaf(a, x.w, acc[4 * v4 + 3]);
+        }
       }
     }
 #pragma unroll
     for (int v = 0; v < kSpVB; ++v)
       if (v < vb && FD_INB(ybase + (long long)(v0 + v) * nr + r, ext, 206)) y[ybase + (long long)(v0 + v) * nr + r] = acc[v];
+  }
+}
+
+// The same product for the nodal pattern of K_rr (every node's D rows share their neighbour
+// nodes): one thread per node, so each 16-byte shared read of a neighbour component's vectors feeds
+// D rows (3 D FMA per read in 3D instead of 4), and the warp's lanes read consecutive nodes'
+// neighbours (regular, conflict-free addresses).  The stored values stay cached for the other
+// (rhs, chunk) blocks of the cell.
+template <int D>
+__global__ void __launch_bounds__(352, 2) krr_spmm_nodal_f32_kernel(
+    const int* __restrict__ nbr, const float* __restrict__ eval, int nnz, int nr, int nrhs, int nchunk,
+    const float* __restrict__ u, long long u_rs, int u_cs, float* __restrict__ y, long long y_rs, int y_cs, int nvec,
+    long long ext) {
+  extern __shared__ __align__(16) float uss[];   // [nr][kSpLd]
+  const int chunk = (int)(blockIdx.x % nchunk);
+  const long long rest = blockIdx.x / nchunk;
+  const int rhs = (int)(rest % nrhs);
+  const long long cell = rest / nrhs;
+  const int v0 = chunk * kSpVB, vb = min(kSpVB, nvec - v0);
+  const long long base = rhs * u_rs + cell * u_cs;
+  for (int t = threadIdx.x; t < kSpVB * nr; t += blockDim.x) {
+    const int v = t / nr, q = t - v * nr;
+    float x = 0.f;
+    if (v < vb && FD_INB(base + (long long)(v0 + v) * nr + q, ext, 207)) x = u[base + (long long)(v0 + v) * nr + q];
+    uss[q * kSpLd + v] = x;
+  }
+  __syncthreads();
+  const int nnode = nr / D, nk = nnz / D;
+  const float* ev = eval + cell * (long long)nnz * nr;
+  const long long ybase = rhs * y_rs + cell * y_cs;
+  for (int n = threadIdx.x; n < nnode; n += blockDim.x) {
+    float acc[D][kSpVB];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int v = 0; v < kSpVB; ++v) acc[a][v] = 0.f;
+    for (int k = 0; k < nk; ++k) {
+      const int m = __ldg(nbr + (long long)k * nnode + n);
+#pragma unroll
+      for (int cq = 0; cq < D; ++cq) {
+        float av[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) av[a] = __ldg(ev + (long long)(D * k + cq) * nr + D * n + a);
+        const float4* xs = reinterpret_cast<const float4*>(uss + (D * m + cq) * kSpLd);
+#pragma unroll
+        for (int v4 = 0; v4 < kSpVB / 4; ++v4) {
+          const float4 x = xs[v4];
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            acc[a][4 * v4] = fmaf(av[a], x.x, acc[a][4 * v4]);
+            acc[a][4 * v4 + 1] = fmaf(av[a], x.y, acc[a][4 * v4 + 1]);
+            acc[a][4 * v4 + 2] = fmaf(av[a], x.z, acc[a][4 * v4 + 2]);
+            acc[a][4 * v4 + 3] = fmaf(av[a], x.w, acc[a][4 * v4 + 3]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < kSpVB; ++v)
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const long long o = ybase + (long long)(v0 + v) * nr + D * n + a;
+        if (v < vb && FD_INB(o, ext, 208)) y[o] = acc[a][v];
+      }
   }
 }
 
@@ -484,12 +558,11 @@ __global__ void cell_gemv_narrow_fixed(const double* __restrict__ mats, long lon
                                        const double* __restrict__ x, long long x_rs, int x_cs,
                                        double* __restrict__ y, long long y_rs, int y_cs, double alpha,
                                        double beta, int nrhs, long long ncell) {
-  const long long total = ncell * mrows;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const long long cell = t / mrows;
-    const int row = (int)(t - cell * mrows);
-    const double2* Mr = reinterpret_cast<const double2*>(mats + cell * mstride + (long long)row * ld);
+  const int total = (int)(ncell * mrows);             // < 2^31, checked by the host
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const int cell = t / mrows;
+    const int row = t - cell * mrows;
+    const double2* Mr = reinterpret_cast<const double2*>(mats + (long long)cell * mstride + (long long)row * ld);
     double mv[MC];
 #pragma unroll
     for (int q = 0; q < MC / 2; ++q) {
@@ -498,11 +571,11 @@ __global__ void cell_gemv_narrow_fixed(const double* __restrict__ mats, long lon
       mv[2 * q + 1] = v.y;
     }
     for (int r = 0; r < nrhs; ++r) {
-      const double* xc = x + r * x_rs + cell * x_cs;
+      const double* xc = x + r * x_rs + (long long)cell * x_cs;
       double acc = 0.0;
 #pragma unroll
       for (int q = 0; q < MC; ++q) acc = fma(mv[q], xc[q], acc);
-      double* dst = y + r * y_rs + cell * y_cs + row;
+      double* dst = y + r * y_rs + (long long)cell * y_cs + row;
       *dst = (beta == 0.0) ? alpha * acc : alpha * acc + beta * (*dst);
     }
   }
@@ -586,68 +659,184 @@ __global__ void __launch_bounds__(256) rom_combine_f32_kernel(const double* __re
   }
 }
 
-// y[rhs][cell][0..rows) = alpha M_f32[cell] x[rhs][cell][0..cols) + beta y: one CTA per cell,
-// x converted to FP32 in shared memory, one warp per pair of rows.  Each lane issues all T 16-byte
-// loads of its share of both rows before any arithmetic (2T loads in flight per lane, streamed
-// past L2), then reads each x chunk once for both rows; FP32 accumulation for up to kMaxRhsF32
-// columns.  ldm is a multiple of 4 and the matrices are 16-byte aligned.
+// y[rhs][cell][0..rows) = alpha M_f32[cell] x[rhs][cell][0..cols) + beta y for SYMMETRIC square
+// operators (F_dd_ring and S_dd_ring: combinations of symmetric principal operators): row j of M is
+// read as column j.  One CTA per cell, one thread per output row (up to kAsmRows rows per thread);
+// for each column j the threads read 32 consecutive entries of M per warp (128 coalesced bytes,
+// streamed past L2) and the column's x values for every RHS as one broadcast 16-byte read per four
+// RHS from shared memory ([column][8] layout), so each warp-wide shared read is one wavefront.
 constexpr int kMaxRhsF32 = 8;
-template <int T>
+constexpr int kAsmRows = 3;            // rows per thread: 256 threads cover n_d <= 768
+constexpr int kAsmUnroll = 4;          // columns whose loads are issued before their arithmetic
 __global__ void __launch_bounds__(256) cell_gemm_f32_kernel(const float* __restrict__ mats, int ldm, int rows,
                                                             int cols, const double* __restrict__ x, long long x_rs,
                                                             int x_cs, double* __restrict__ y, long long y_rs,
                                                             int y_cs, double alpha, double beta, int nrhs) {
-  extern __shared__ float xsf[];   // [nrhs][ldm]
+  extern __shared__ __align__(16) float xsf[];   // [cols][kMaxRhsF32]
   const long long cell = blockIdx.x;
-  for (int t = threadIdx.x; t < nrhs * ldm; t += blockDim.x) {
-    const int rr = t / ldm, q = t - rr * ldm;
-    xsf[t] = q < cols ? (float)x[rr * x_rs + cell * x_cs + q] : 0.f;
-  }
-  __syncthreads();
-  const float4* M = reinterpret_cast<const float4*>(mats + cell * (long long)rows * ldm);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int n4 = ldm >> 2;
-  for (int row = 2 * warp; row < rows; row += 2 * nw) {
-    const bool two = row + 1 < rows;
-    float4 m0[T], m1[T];
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-      const int j = lane + 32 * t;
-      const bool in = j < n4;
-      m0[t] = in ? __ldcs(M + (long long)row * n4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
-      m1[t] = (in && two) ? __ldcs(M + (long long)(row + 1) * n4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+  const int tid = threadIdx.x;
+  const float* M = mats + cell * (long long)rows * ldm;
+  for (int rb0 = 0; rb0 < nrhs; rb0 += kMaxRhsF32) {
+    const int rb = min(kMaxRhsF32, nrhs - rb0);
+    __syncthreads();
+    for (int t = tid; t < cols * kMaxRhsF32; t += blockDim.x) {
+      const int j = t / kMaxRhsF32, q = t - j * kMaxRhsF32;
+      xsf[t] = q < rb ? (float)x[(rb0 + q) * x_rs + cell * x_cs + j] : 0.f;
     }
-    for (int rb0 = 0; rb0 < nrhs; rb0 += kMaxRhsF32) {
-      const int rb = min(kMaxRhsF32, nrhs - rb0);
-      float a0[kMaxRhsF32], a1[kMaxRhsF32];
+    __syncthreads();
+    float acc[kAsmRows][kMaxRhsF32];
 #pragma unroll
-      for (int q = 0; q < kMaxRhsF32; ++q) { a0[q] = 0.f; a1[q] = 0.f; }
+    for (int a = 0; a < kAsmRows; ++a)
 #pragma unroll
-      for (int t = 0; t < T; ++t) {
-        const int j = lane + 32 * t;
-        if (j >= n4) break;
+      for (int q = 0; q < kMaxRhsF32; ++q) acc[a][q] = 0.f;
+    int r[kAsmRows];
+    bool live[kAsmRows];
 #pragma unroll
-        for (int q = 0; q < kMaxRhsF32; ++q) {
-          if (q < rb) {
-            const float4 x4 = reinterpret_cast<const float4*>(xsf + (rb0 + q) * ldm)[j];
-            a0[q] = fmaf(m0[t].x, x4.x, fmaf(m0[t].y, x4.y, fmaf(m0[t].z, x4.z, fmaf(m0[t].w, x4.w, a0[q]))));
-            a1[q] = fmaf(m1[t].x, x4.x, fmaf(m1[t].y, x4.y, fmaf(m1[t].z, x4.z, fmaf(m1[t].w, x4.w, a1[q]))));
-          }
-        }
+    for (int a = 0; a < kAsmRows; ++a) {
+      r[a] = tid + a * (int)blockDim.x;
+      live[a] = r[a] < rows;
+    }
+    for (int j0 = 0; j0 < cols; j0 += kAsmUnroll) {
+      float m[kAsmUnroll][kAsmRows];
+#pragma unroll
+      for (int u = 0; u < kAsmUnroll; ++u)
+#pragma unroll
+        for (int a = 0; a < kAsmRows; ++a)
+          m[u][a] = (live[a] && j0 + u < cols) ? __ldcs(M + (long long)(j0 + u) * ldm + r[a]) : 0.f;
+#pragma unroll
+      for (int u = 0; u < kAsmUnroll; ++u) {
+        if (j0 + u >= cols) break;
+        const float4 x0 = reinterpret_cast<const float4*>(xsf)[(j0 + u) * 2];
+        const float4 x1 = reinterpret_cast<const float4*>(xsf)[(j0 + u) * 2 + 1];
+        const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+        for (int a = 0; a < kAsmRows; ++a)
+#pragma unroll
+          for (int q = 0; q < kMaxRhsF32; ++q) acc[a][q] = fmaf(m[u][a], xv[q], acc[a][q]);
       }
+    }
+#pragma unroll
+    for (int a = 0; a < kAsmRows; ++a) {
+      if (!live[a]) continue;
 #pragma unroll
       for (int q = 0; q < kMaxRhsF32; ++q) {
         if (q < rb) {
-          float s0 = a0[q], s1 = a1[q];
-          for (int o = 16; o > 0; o >>= 1) {
-            s0 += __shfl_down_sync(0xffffffffu, s0, o);
-            s1 += __shfl_down_sync(0xffffffffu, s1, o);
-          }
-          if (lane == 0) {
-            double* dst = y + (rb0 + q) * y_rs + cell * y_cs + row;
-            *dst = (beta == 0.0) ? alpha * (double)s0 : alpha * (double)s0 + beta * (*dst);
-            if (two) dst[1] = (beta == 0.0) ? alpha * (double)s1 : alpha * (double)s1 + beta * dst[1];
-          }
+          double* dst = y + (rb0 + q) * y_rs + cell * y_cs + r[a];
+          *dst = (beta == 0.0) ? alpha * (double)acc[a][q] : alpha * (double)acc[a][q] + beta * (*dst);
+        }
+      }
+    }
+  }
+}
+
+// Coarse restriction and prolongation of the inner iterations (the coarse term of Eq. 48) with the
+// FP32 copy of U_dp_ring (the dual rows of U_rp_ring), [cell][n_d][NP] row-major:
+//   udp_t:  cp[rhs][cell][p] = sum_d U[d][p] g[rhs][cell][d]
+//   udp_n:  y[rhs][cell][d]  = alpha sum_p U[d][p] cp[rhs][cell][p] + beta y
+// One CTA per cell.  In udp_t a thread owns four consecutive p of every RG-th row (one 16-byte
+// load per row), accumulates them for up to eight RHS in FP32 and the RG row groups are summed in
+// shared memory; in udp_n a thread owns a row.
+template <int NP>
+__global__ void __launch_bounds__(256) udp_t_f32_kernel(const float* __restrict__ U, int nd,
+                                                        const double* __restrict__ g, long long g_rs, int g_cs,
+                                                        double* __restrict__ cp, long long c_rs, int c_cs,
+                                                        int nrhs) {
+  constexpr int G = NP / 4;          // 16-byte groups per row
+  constexpr int RG = 256 / G;        // row groups
+  extern __shared__ __align__(16) float smu[];   // gs[nd][8], red[RG * G][32]
+  float* gs = smu;
+  float* red = smu + (size_t)nd * 8;
+  const long long cell = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int grp = tid % G, rg = tid / G;
+  const float4* Uc = reinterpret_cast<const float4*>(U + cell * (long long)nd * NP);
+  for (int rb0 = 0; rb0 < nrhs; rb0 += 8) {
+    const int rb = min(8, nrhs - rb0);
+    __syncthreads();
+    for (int t = tid; t < nd * 8; t += blockDim.x) {
+      const int q = t / nd, d = t - q * nd;
+      gs[d * 8 + q] = q < rb ? (float)g[(rb0 + q) * g_rs + cell * g_cs + d] : 0.f;
+    }
+    __syncthreads();
+    float acc[4][8];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[a][q] = 0.f;
+    if (rg < RG) {
+#pragma unroll 2
+      for (int d = rg; d < nd; d += RG) {
+        const float4 u = __ldcs(Uc + (long long)d * G + grp);
+        const float4 x0 = reinterpret_cast<const float4*>(gs)[d * 2];
+        const float4 x1 = reinterpret_cast<const float4*>(gs)[d * 2 + 1];
+        const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+        const float uv[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int q = 0; q < 8; ++q) acc[a][q] = fmaf(uv[a], xv[q], acc[a][q]);
+      }
+      float4* rd = reinterpret_cast<float4*>(red + (size_t)(rg * G + grp) * 32);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        rd[2 * a] = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+        rd[2 * a + 1] = make_float4(acc[a][4], acc[a][5], acc[a][6], acc[a][7]);
+      }
+    }
+    __syncthreads();
+    for (int o = tid; o < NP * 8; o += blockDim.x) {
+      const int p = o >> 3, q = o & 7;
+      const int gp = p >> 2, a = p & 3;
+      float sum = 0.f;
+      for (int k = 0; k < RG; ++k) sum += red[(size_t)(k * G + gp) * 32 + a * 8 + q];
+      if (q < rb) cp[(rb0 + q) * c_rs + cell * c_cs + p] = (double)sum;
+    }
+  }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(1024) udp_n_f32_kernel(const float* __restrict__ U, int nd,
+                                                         const double* __restrict__ cp, long long c_rs, int c_cs,
+                                                         double* __restrict__ y, long long y_rs, int y_cs,
+                                                         double alpha, double beta, int nrhs) {
+  constexpr int G = NP / 4;
+  __shared__ __align__(16) float cs[NP][8];
+  const long long cell = blockIdx.x;
+  const int tid = threadIdx.x;
+  const float4* Uc = reinterpret_cast<const float4*>(U + cell * (long long)nd * NP);
+  for (int rb0 = 0; rb0 < nrhs; rb0 += 8) {
+    const int rb = min(8, nrhs - rb0);
+    __syncthreads();
+    for (int t = tid; t < NP * 8; t += blockDim.x) {
+      const int p = t >> 3, q = t & 7;
+      cs[p][q] = q < rb ? (float)cp[(rb0 + q) * c_rs + cell * c_cs + p] : 0.f;
+    }
+    __syncthreads();
+    for (int d = tid; d < nd; d += blockDim.x) {
+      float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int gq = 0; gq < G; ++gq) {
+        const float4 u = __ldcs(Uc + (long long)d * G + gq);
+        const float uv[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const float4 x0 = reinterpret_cast<const float4*>(cs[4 * gq + a])[0];
+          const float4 x1 = reinterpret_cast<const float4*>(cs[4 * gq + a])[1];
+          acc[0] = fmaf(uv[a], x0.x, acc[0]);
+          acc[1] = fmaf(uv[a], x0.y, acc[1]);
+          acc[2] = fmaf(uv[a], x0.z, acc[2]);
+          acc[3] = fmaf(uv[a], x0.w, acc[3]);
+          acc[4] = fmaf(uv[a], x1.x, acc[4]);
+          acc[5] = fmaf(uv[a], x1.y, acc[5]);
+          acc[6] = fmaf(uv[a], x1.z, acc[6]);
+          acc[7] = fmaf(uv[a], x1.w, acc[7]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (q < rb) {
+          double* dst = y + (rb0 + q) * y_rs + cell * y_cs + d;
+          *dst = (beta == 0.0) ? alpha * (double)acc[q] : alpha * (double)acc[q] + beta * (*dst);
         }
       }
     }
@@ -855,6 +1044,80 @@ __device__ void warp_pivoted_gram_solve(double* S, double* Lc, const double* hs,
   }
 }
 
+// The same diagonal-pivoted Cholesky solve by a whole CTA (nthreads threads, all of them calling):
+// warp 0 picks the pivot, every thread forms part of the pivot column and of the rank-1 update,
+// which touches only the upper triangle of the unpivoted rows and columns (S stays symmetric there,
+// and each entry receives the same FP64 operations in the same order as in the warp solve, so both
+// give identical results).  The substitutions run on warp 0.  sh holds a double and an int of
+// block-shared scratch.
+__device__ void block_pivoted_gram_solve(double* S, double* Lc, const double* hs, double* ys, double* cs,
+                                         double* colv, int* piv, double* sh_inv, int* sh_jb, int nrb, int ld,
+                                         double drop_rel, int tid, int nthreads) {
+  const int lane = tid & 31, warp = tid >> 5;
+  double dmax = 0.0;
+  for (int i = 0; i < nrb; ++i) dmax = fmax(dmax, S[i * ld + i]);
+  unsigned long long used = 0ull;                   // identical in every thread
+  int np = 0;
+  while (np < nrb) {
+    if (warp == 0) {
+      int jb = -1;
+      double best = 0.0;
+      for (int i = lane; i < nrb; i += 32) {
+        if ((used >> i) & 1ull) continue;
+        const double dv = S[i * ld + i];
+        if (jb < 0 || dv > best) { best = dv; jb = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, jb, o);
+        if (oj >= 0 && (jb < 0 || ob > best || (ob == best && oj < jb))) { best = ob; jb = oj; }
+      }
+      if (lane == 0) {
+        const bool take = jb >= 0 && best > drop_rel * dmax;
+        *sh_jb = take ? jb : -1;
+        if (take) { *sh_inv = 1.0 / sqrt(best); piv[np] = jb; }
+      }
+    }
+    __syncthreads();
+    const int jb = *sh_jb;
+    if (jb < 0) break;                                 // uniform across the block
+    const double inv = *sh_inv;
+    used |= 1ull << jb;
+    for (int i = tid; i < nrb; i += nthreads) {
+      const double cv = S[min(i, jb) * ld + max(i, jb)] * inv;
+      colv[i] = cv;
+      Lc[np * ld + i] = cv;
+    }
+    __syncthreads();
+    for (int t = tid; t < nrb * nrb; t += nthreads) {
+      const int i = t / nrb, j = t - i * nrb;
+      if (i > j || ((used >> i) & 1ull) || ((used >> j) & 1ull)) continue;
+      S[i * ld + j] -= colv[i] * colv[j];
+    }
+    ++np;
+    __syncthreads();
+  }
+  if (warp != 0) return;
+  for (int i = lane; i < nrb; i += 32) { ys[i] = hs[i]; cs[i] = 0.0; }
+  __syncwarp();
+  for (int a = 0; a < np; ++a) {
+    const int pa = piv[a];
+    const double ya = ys[pa] / Lc[a * ld + pa];
+    __syncwarp();
+    for (int r = a + 1 + lane; r < np; r += 32) ys[piv[r]] -= Lc[a * ld + piv[r]] * ya;
+    if (lane == 0) colv[a] = ya;
+    __syncwarp();
+  }
+  for (int a = np - 1; a >= 0; --a) {
+    const int pa = piv[a];
+    const double ca = colv[a] / Lc[a * ld + pa];
+    __syncwarp();
+    for (int r = lane; r < a; r += 32) colv[r] -= Lc[r * ld + pa] * ca;
+    if (lane == 0) cs[pa] = ca;
+    __syncwarp();
+  }
+}
+
 // s + c += x with Neumaier's compensation (c collects the rounding error of every addition)
 template <typename T>
 __device__ __forceinline__ void neumaier_add(T& s, T& c, T x) {
@@ -876,7 +1139,7 @@ constexpr int kGbQ = 32;
 constexpr int kGbLd = 33;
 __host__ __device__ inline size_t gram_block_smem(int nrb) {
   const size_t ld = (size_t)nrb + 1;
-  return sizeof(double) * (2 * nrb * ld + 6 * (size_t)nrb) + sizeof(float) * (2 * (size_t)nrb * kGbLd + kGbQ);
+  return sizeof(double) * (2 * nrb * ld + 6 * (size_t)nrb + 2) + sizeof(float) * (2 * (size_t)nrb * kGbLd + kGbQ);
 }
 __global__ void __launch_bounds__(256) gram_block_f32_kernel(const float* __restrict__ R, const float* __restrict__ KR,
                                                              const double* __restrict__ v, long long v_rs, int v_cs,
@@ -891,7 +1154,9 @@ __global__ void __launch_bounds__(256) gram_block_f32_kernel(const float* __rest
   double* cs = ys + nrb;
   double* colv = cs + nrb;
   int* piv = reinterpret_cast<int*>(colv + nrb);     // nrb ints in 2 nrb doubles of room
-  float* Rs = reinterpret_cast<float*>(colv + 3 * nrb);
+  double* sh_inv = colv + 3 * nrb;
+  int* sh_jb = reinterpret_cast<int*>(sh_inv + 1);
+  float* Rs = reinterpret_cast<float*>(sh_inv + 2);
   float* Ks = Rs + (size_t)nrb * kGbLd;
   float* vs = Ks + (size_t)nrb * kGbLd;
   const long long col = blockIdx.x;                  // rhs * ncell + cell
@@ -959,7 +1224,7 @@ __global__ void __launch_bounds__(256) gram_block_f32_kernel(const float* __rest
     if (i > j) S[i * ld + j] = S[j * ld + i];
   }
   __syncthreads();
-  if (tid < 32) warp_pivoted_gram_solve(S, Lc, hs, ys, cs, colv, piv, nrb, ld, drop_rel, tid);
+  block_pivoted_gram_solve(S, Lc, hs, ys, cs, colv, piv, sh_inv, sh_jb, nrb, ld, drop_rel, tid, blockDim.x);
   __syncthreads();
   double* xc = x + rhs * x_rs + cell * x_cs;
   for (int q = tid; q < nr; q += blockDim.x) {
@@ -1292,9 +1557,23 @@ fetidp_status k_apply_K_f32(Ctx& c, const float* u, long long u_rs, int u_cs, fl
     // vectors in and out
     ProfScope ps(c, FETIDP_K_MULTI_K, 2.0 * (double)c.N * nrhs * nvec * c.krr_nnz * c.nr,
                  4.0 * (double)c.N * c.krr_nnz * c.nr + 8.0 * (double)c.N * nrhs * nvec * c.nr);
-    cudaFuncSetAttribute(krr_spmm_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    krr_spmm_f32_kernel<<<(unsigned)(c.N * nrhs * nchunk), 256, smem, c.stream>>>(
-        c.krr_col, c.krr_val, c.krr_nnz, c.nr, nrhs, nchunk, u, u_rs, u_cs, y, y_rs, y_cs, nvec, ext);
+    const int nnode = c.nr / c.d;
+    if (c.krr_nbr && nnode <= 704) {
+      const int threads = std::min(352, (nnode + 31) / 32 * 32);
+      if (c.d == 3) {
+        cudaFuncSetAttribute(krr_spmm_nodal_f32_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        krr_spmm_nodal_f32_kernel<3><<<(unsigned)(c.N * nrhs * nchunk), threads, smem, c.stream>>>(
+            c.krr_nbr, c.krr_val, c.krr_nnz, c.nr, nrhs, nchunk, u, u_rs, u_cs, y, y_rs, y_cs, nvec, ext);
+      } else {
+        cudaFuncSetAttribute(krr_spmm_nodal_f32_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        krr_spmm_nodal_f32_kernel<2><<<(unsigned)(c.N * nrhs * nchunk), threads, smem, c.stream>>>(
+            c.krr_nbr, c.krr_val, c.krr_nnz, c.nr, nrhs, nchunk, u, u_rs, u_cs, y, y_rs, y_cs, nvec, ext);
+      }
+    } else {
+      cudaFuncSetAttribute(krr_spmm_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      krr_spmm_f32_kernel<<<(unsigned)(c.N * nrhs * nchunk), 256, smem, c.stream>>>(
+          c.krr_col, c.krr_val, c.krr_nnz, c.nr, nrhs, nchunk, u, u_rs, u_cs, y, y_rs, y_cs, nvec, ext);
+    }
     FD_CHECK_LAUNCH();
     return FETIDP_OK;
   }
@@ -1370,30 +1649,45 @@ fetidp_status k_rom_combine_f32(Ctx& c, const double* src, long long kstride, in
 
 fetidp_status k_cell_gemm_f32(Ctx& c, const float* mats, int ldm, int rows, int cols, CCellVec x, CellVec y,
                               double alpha, double beta, int nrhs) {
-  if (ldm % 4 != 0 || (reinterpret_cast<uintptr_t>(mats) & 15) != 0) {
-    set_error("FP32 cell operators need 16-byte aligned rows");
-    return FETIDP_EINVAL;
-  }
   // algorithmic bytes: the operators once, the FP64 vectors in and out
   ProfScope ps(c, FETIDP_K_ASM_OP, 2.0 * rows * cols * (double)c.N * nrhs,
                4.0 * c.N * (double)rows * ldm + 8.0 * c.N * (double)nrhs * (rows + cols));
-  const size_t smem = (size_t)nrhs * ldm * sizeof(float);
-  const int T = (ldm / 4 + 31) / 32;
-  if (T > 8) { set_error("FP32 cell operators wider than 1024 columns"); return FETIDP_EINVAL; }
-  auto launch = [&](auto kern) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<(unsigned)c.N, 256, smem, c.stream>>>(mats, ldm, rows, cols, x.p, x.rs, x.cs, y.p, y.rs, y.cs, alpha,
-                                                 beta, nrhs);
-  };
-  switch (T) {
-    case 1: launch(cell_gemm_f32_kernel<1>); break;
-    case 2: launch(cell_gemm_f32_kernel<2>); break;
-    case 3: launch(cell_gemm_f32_kernel<3>); break;
-    case 4: launch(cell_gemm_f32_kernel<4>); break;
-    case 5: launch(cell_gemm_f32_kernel<5>); break;
-    case 6: launch(cell_gemm_f32_kernel<6>); break;
-    case 7: launch(cell_gemm_f32_kernel<7>); break;
-    default: launch(cell_gemm_f32_kernel<8>); break;
+  if (rows != cols || rows > kAsmRows * 256) {
+    set_error("FP32 cell operators: square and at most 768 rows");
+    return FETIDP_EINVAL;
+  }
+  const size_t smem = (size_t)cols * kMaxRhsF32 * sizeof(float);
+  cudaFuncSetAttribute(cell_gemm_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cell_gemm_f32_kernel<<<(unsigned)c.N, 256, smem, c.stream>>>(mats, ldm, rows, cols, x.p, x.rs, x.cs, y.p, y.rs,
+                                                               y.cs, alpha, beta, nrhs);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_udp_f32(Ctx& c, bool trans, CCellVec x, CellVec y, double alpha, double beta, int nrhs) {
+  const int nd = c.nd, np = c.np;
+  if (!c.Udp_f || (np != 8 && np != 24) || nd < 1) { set_error("FP32 U_dp needs n_p of 8 or 24"); return FETIDP_EINVAL; }
+  ProfScope ps(c, FETIDP_K_CELL_GEMV, 2.0 * nd * np * (double)c.N * nrhs,
+               4.0 * c.N * nd * np + 8.0 * c.N * nrhs * (nd + np + (beta != 0.0 ? nd : 0)));
+  if (trans) {
+    const int G = np / 4, RG = 256 / G;
+    const size_t smem = sizeof(float) * ((size_t)nd * 8 + (size_t)RG * G * 32);
+    if (smem > 227 * 1024) { set_error("FP32 U_dp: n_d too large"); return FETIDP_EINVAL; }
+    if (np == 8) {
+      cudaFuncSetAttribute(udp_t_f32_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      udp_t_f32_kernel<8><<<(unsigned)c.N, 256, smem, c.stream>>>(c.Udp_f, nd, x.p, x.rs, x.cs, y.p, y.rs, y.cs, nrhs);
+    } else {
+      cudaFuncSetAttribute(udp_t_f32_kernel<24>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      udp_t_f32_kernel<24><<<(unsigned)c.N, 256, smem, c.stream>>>(c.Udp_f, nd, x.p, x.rs, x.cs, y.p, y.rs, y.cs, nrhs);
+    }
+  } else {
+    const int threads = std::min(1024, (nd + 31) / 32 * 32);
+    if (np == 8)
+      udp_n_f32_kernel<8><<<(unsigned)c.N, threads, 0, c.stream>>>(c.Udp_f, nd, x.p, x.rs, x.cs, y.p, y.rs, y.cs,
+                                                                   alpha, beta, nrhs);
+    else
+      udp_n_f32_kernel<24><<<(unsigned)c.N, threads, 0, c.stream>>>(c.Udp_f, nd, x.p, x.rs, x.cs, y.p, y.rs, y.cs,
+                                                                    alpha, beta, nrhs);
   }
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
@@ -1405,7 +1699,7 @@ fetidp_status k_cell_gemv_strided(Ctx& c, const double* mats, long long mstride,
   ProfScope ps(c, FETIDP_K_CELL_GEMV, 2.0 * mrows * mcols * (double)c.N * nrhs,
                8.0 * c.N * ((double)mrows * mcols + (double)nrhs * (mrows + mcols)));
   const bool aligned16 = (ld % 2 == 0) && (mstride % 2 == 0) && ((reinterpret_cast<uintptr_t>(mats) & 15) == 0);
-  if ((mcols == 8 || mcols == 24) && aligned16) {
+  if ((mcols == 8 || mcols == 24) && aligned16 && c.N * mrows < (1LL << 31)) {
     const long long total = c.N * mrows;
     long long grid = (total + 255) / 256;
     if (grid > 152LL * 32) grid = 152LL * 32;

@@ -35,15 +35,17 @@ __global__ void gather_BT_kernel(const int* __restrict__ gath, const double* __r
                                  long long lam_rs, const int* __restrict__ dinfo, int d,
                                  double* __restrict__ out, long long out_rs, int out_cs, int nd,
                                  long long ncell, int nrhs, double beta) {
-  const long long total = ncell * nd;
-  for (long long cj = blockIdx.x * (long long)blockDim.x + threadIdx.x; cj < total;
-       cj += (long long)gridDim.x * blockDim.x) {
-    const long long cell = cj / nd;
-    const int j = (int)(cj - cell * nd);
+  const int total = (int)(ncell * nd);               // < 2^31, checked by the host
+  for (int cj = blockIdx.x * blockDim.x + threadIdx.x; cj < total; cj += gridDim.x * blockDim.x) {
+    const int cell = cj / nd;
+    const int j = cj - cell * nd;
     const int2 cc = reinterpret_cast<const int2*>(gath)[cj];
+    // at most two signed rows, each expanded into at most three rows by its D block: six terms,
+    // kept in registers (fixed trip counts) with zero weights past the live ones
     int idx[6];
     double w[6];
-    int nt = 0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) { idx[k] = 0; w[k] = 0.0; }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int code = h ? cc.y : cc.x;
@@ -52,17 +54,24 @@ __global__ void gather_BT_kernel(const int* __restrict__ gath, const double* __r
       const double sg = code > 0 ? 1.0 : -1.0;
       const int dc = dinfo ? dinfo[row] : 0;
       const int n = dc >> 8, q = dc & 0xff;
-      if (n == 0) {
-        idx[nt] = row; w[nt] = sg; ++nt;
-      } else {
-        for (int b = 0; b < n; ++b) { idx[nt] = row + (b - q) * d; w[nt] = sg * tinv(q, b, n); ++nt; }
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const int k = 3 * h + b;
+        if (n == 0) {
+          if (b == 0) { idx[k] = row; w[k] = sg; }
+        } else if (b < n) {
+          idx[k] = row + (b - q) * d;
+          w[k] = sg * tinv(q, b, n);
+        }
       }
     }
     for (int rhs = 0; rhs < nrhs; ++rhs) {
       const double* l = lam + rhs * lam_rs;
       double v = 0.0;
-      for (int k = 0; k < nt; ++k) v = fma(w[k], l[idx[k]], v);
-      double* o = out + rhs * out_rs + cell * out_cs + j;
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        if (w[k] != 0.0) v = fma(w[k], l[idx[k]], v);
+      double* o = out + rhs * out_rs + (long long)cell * out_cs + j;
       *o = (beta == 0.0) ? v : v + beta * (*o);
     }
   }
@@ -75,33 +84,37 @@ __global__ void scatter_B_kernel(const int* __restrict__ scat, const double* __r
                                  long long y_rs, int y_cs, int nd, const int* __restrict__ dinfo,
                                  int d, double* __restrict__ out, long long out_rs, long long L,
                                  double alpha, double beta, int nrhs) {
-  for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < L;
-       row += (long long)gridDim.x * blockDim.x) {
+  const int Li = (int)L;                             // < 2^31, checked by the host
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < Li; row += gridDim.x * blockDim.x) {
     const int code = dinfo ? dinfo[row] : 0;
     const int n = code >> 8, q = code & 0xff;
+    // at most three chain rows with two signed entries each: six terms in registers
     long long idx[6];
     double w[6];
-    int nt = 0;
-    const int nb = n == 0 ? 1 : n;
-    for (int b = 0; b < nb; ++b) {
-      const long long r = n == 0 ? row : row + (long long)(b - q) * d;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) { idx[k] = 0; w[k] = 0.0; }
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      if (b > 0 && b >= n) break;
+      const int r = n == 0 ? row : row + (b - q) * d;
       const double wr = n == 0 ? 1.0 : tinv(q, b, n);
       const int2 sc = reinterpret_cast<const int2*>(scat)[r];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int c = h ? sc.y : sc.x;
         if (c == 0) continue;
-        const long long e = (c > 0 ? c : -c) - 1;
-        const long long cell = e / nd;
-        idx[nt] = cell * y_cs + (e - cell * nd);
-        w[nt] = c > 0 ? wr : -wr;
-        ++nt;
+        const int e = (c > 0 ? c : -c) - 1;
+        const int cell = e / nd;
+        idx[2 * b + h] = (long long)cell * y_cs + (e - cell * nd);
+        w[2 * b + h] = c > 0 ? wr : -wr;
       }
     }
     for (int rhs = 0; rhs < nrhs; ++rhs) {
       const double* y = yd + rhs * y_rs;
       double v = 0.0;
-      for (int k = 0; k < nt; ++k) v = fma(w[k], y[idx[k]], v);
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        if (w[k] != 0.0) v = fma(w[k], y[idx[k]], v);
       double* o = out + rhs * out_rs + row;
       *o = (beta == 0.0) ? alpha * v : alpha * v + beta * (*o);
     }
@@ -270,6 +283,7 @@ inline int grid_for(long long work, int threads = 256) {
 fetidp_status k_gather_BT(Ctx& c, const double* lam, long long lam_rs, const int* dinfo,
                           CellVec out, int nrhs, double beta) {
   const long long work = c.N * c.nd;
+  if (work >= (1LL << 31) || c.L >= (1LL << 31)) { set_error("lattice too large for 32-bit map indices"); return FETIDP_EINVAL; }
   ProfScope ps(c, FETIDP_K_MAPS, 0.0, (double)nrhs * (c.L * 8.0 + c.N * c.nd * 8.0) + c.N * c.nd * 8.0);
   gather_BT_kernel<<<grid_for(work), 256, 0, c.stream>>>(c.gath, lam, lam_rs, dinfo, c.d, out.p, out.rs,
                                                           out.cs, c.nd, c.N, nrhs, beta);
@@ -279,6 +293,7 @@ fetidp_status k_gather_BT(Ctx& c, const double* lam, long long lam_rs, const int
 
 fetidp_status k_scatter_B(Ctx& c, CCellVec yd, double* out, long long out_rs, const int* dinfo,
                           double alpha, double beta, int nrhs) {
+  if (c.L >= (1LL << 31) || c.N * c.nd >= (1LL << 31)) { set_error("lattice too large for 32-bit map indices"); return FETIDP_EINVAL; }
   ProfScope ps(c, FETIDP_K_MAPS, 0.0, (double)nrhs * (c.L * 8.0 + c.N * c.nd * 8.0) + c.L * 8.0);
   scatter_B_kernel<<<grid_for(c.L), 256, 0, c.stream>>>(
       c.scat, yd.p, yd.rs, yd.cs, c.nd, dinfo, c.d, out, out_rs, c.L, alpha, beta, nrhs);

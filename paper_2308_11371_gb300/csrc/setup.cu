@@ -230,6 +230,11 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
   if (o.wait_budget_ns <= 0) { set_error("wait_budget_ns must be > 0"); return FETIDP_EINVAL; }
   if (o.mixed_assembled < -1 || o.mixed_assembled > 1) { set_error("mixed_assembled must be -1, 0 or 1"); return FETIDP_EINVAL; }
   if (o.interface < 0 || o.interface > 1) { set_error("interface must be 0 or 1"); return FETIDP_EINVAL; }
+  if (o.method < 0 || o.method > 1) { set_error("method must be 0 or 1"); return FETIDP_EINVAL; }
+  if (o.method == 1 && (o.precision != FETIDP_FP64 || o.interface != 0)) {
+    set_error("standard FETI-DP (method 1) runs in FP64 with the PCG interface solve");
+    return FETIDP_EINVAL;
+  }
   if (!(std::isfinite(o.tol_outer) && std::isfinite(o.tol_inner) && std::isfinite(o.tol_inner_mixed) &&
         o.tol_outer >= 0.0 && o.tol_inner >= 0.0 && o.tol_inner_mixed >= 0.0)) {
     set_error("tolerances must be finite and >= 0");
@@ -495,8 +500,10 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
   // The whole loop is enqueued without host round trips: each step selects on the device (or
   // sets the stop flag, after which the remaining kernels return at once); sigma is read back
   // once at the end.
-  const int nrb_req = p.n_rb;
+  c.exact = o.method == 1;
+  const int nrb_req = c.exact ? 0 : p.n_rb;
   if (nrb_req > kMaxRbGreedy) { set_error("n_rb above 64 is not supported"); return FETIDP_EINVAL; }
+  if (!c.exact) {
   double *Delta = nullptr, *nrm = nullptr, *vals = nullptr, *beta_d = nullptr, *Z = nullptr, *T = nullptr;
   GreedyState* gst = nullptr;
   FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&Delta), sizeof(double) * c.N * c.nsnap));
@@ -542,13 +549,20 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
   FD_CUDA(cudaStreamSynchronize(c.stream));
   c.sigma.assign(hst.sigma, hst.sigma + hst.count);
   c.nrb = hst.count;
-  const int nrb = c.nrb;
   // ---------------------------------------------------------------- alpha (Eq. 56)
-  FD_TRY(dalloc_t(c, &c.alpha, (size_t)c.N * nrb));
-  FD_TRY(k_greedy_alpha(c, Z, nrm, beta_d, nrb, gst, T, c.alpha));
+  FD_TRY(dalloc_t(c, &c.alpha, (size_t)c.N * c.nrb));
+  FD_TRY(k_greedy_alpha(c, Z, nrm, beta_d, c.nrb, gst, T, c.alpha));
   FD_CUDA(cudaStreamSynchronize(c.stream));
   free_greedy();
   phase("greedy + alpha");
+  } else {
+    // standard FETI-DP (Sec. 2.2.4): every cell is factorised; the "principal" operators below
+    // are every cell's own, and no ROM coefficient is formed
+    c.sigma.resize(c.N);
+    for (long long s = 0; s < c.N; ++s) c.sigma[s] = (int)s;
+    c.nrb = (int)c.N;
+  }
+  const int nrb = c.nrb;
 
   // ---------------------------------------------------------------- principal operators (Eq. 39)
   const int nr = c.nr, ni = c.ni, nd = c.nd, np = c.np;
@@ -603,7 +617,7 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
   phase("principal factorisations");
 
   // ---------------------------------------------------------------- projections pi, delta (Eqs. 41-42)
-  {
+  if (!c.exact) {
     const int nqp = c.nelem * c.ngp, dd = d * d;
     const int npair = nrb * (nrb + 1) / 2;
     const int ntab = 2 * npair + nrb;
@@ -682,7 +696,12 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
   phase("projections pi, delta");
 
   // ---------------------------------------------------------------- ROM local operators (Eq. 43)
-  if (!c.mixed) {   // FP64 path: per-cell assembled F_dd_ring, S_dd_ring
+  if (c.exact) {    // standard FETI-DP: every cell's own F_dd and S_dd
+    FD_TRY(dalloc_t(c, &c.Fdd_c, (size_t)c.N * nd * nd));
+    FD_TRY(k_batched_block_copy(c, c.Kinv, (long long)nr * nr, nr, ni, ni, c.Fdd_c, (long long)nd * nd, nd, nd, nd,
+                                nrb, false));
+    c.Sdd_c = c.Sdd;
+  } else if (!c.mixed) {   // FP64 path: per-cell assembled F_dd_ring, S_dd_ring
     FD_TRY(dalloc_t(c, &c.Fdd_c, (size_t)c.N * nd * nd));
     FD_TRY(dalloc_t(c, &c.Sdd_c, (size_t)c.N * nd * nd));
     FD_TRY(k_rom_combine(c, c.Kinv, (long long)nr * nr, nr, ni, ni, nd, nd, c.delta, c.Fdd_c, false));
@@ -726,6 +745,26 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
         for (; sl < nnz; ++sl) col[(size_t)sl * nr + r] = r;   // padding: value 0 on the diagonal column
       }
       c.krr_nnz = nnz;
+      // nodal structure: the d rows of a node share their neighbour nodes, slot d k + c' of row
+      // d n + a holding component c' of the k-th neighbour (columns sorted, components interleaved)
+      bool nodal = nr % d == 0 && nnz % d == 0;
+      const int nnode = nr / d, nk = nnz / d;
+      std::vector<int> nbr;
+      if (nodal) nbr.assign((size_t)nk * nnode, 0);
+      for (int n = 0; nodal && n < nnode; ++n)
+        for (int k = 0; nodal && k < nk; ++k) {
+          const size_t e0 = (size_t)(d * k) * nr + (size_t)d * n;
+          const bool pad = cnt[e0] == 0;
+          const int c0 = col[e0];
+          if (!pad && c0 % d != 0) nodal = false;
+          for (int a = 0; nodal && a < d; ++a)
+            for (int cq = 0; cq < d; ++cq) {
+              const size_t e = (size_t)(d * k + cq) * nr + (size_t)d * n + a;
+              if ((cnt[e] == 0) != pad || (!pad && col[e] != c0 + cq)) { nodal = false; break; }
+            }
+          if (nodal) nbr[(size_t)k * nnode + n] = pad ? n : c0 / d;
+        }
+      if (nodal) FD_TRY(upload(c, &c.krr_nbr, nbr));
       int *cnt_d = nullptr, *idx_d = nullptr;
       FD_TRY(upload(c, &c.krr_col, col));
       FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&cnt_d), sizeof(int) * cnt.size()));
@@ -793,10 +832,19 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
     if (!c.tc_err) FD_TRY(dalloc(c, reinterpret_cast<void**>(&c.tc_err), sizeof(int)));
     FD_CUDA(cudaMemsetAsync(c.tc_err, 0, sizeof(int), c.stream));
   }
-  FD_TRY(dalloc_t(c, &c.Urp_c, (size_t)c.N * nr * np));
-  FD_TRY(dalloc_t(c, &c.UrpT_c, (size_t)c.N * nr * np));
-  FD_TRY(k_rom_combine(c, c.Urp, (long long)nr * np, np, 0, 0, nr, np, c.pi, c.Urp_c, false));
-  FD_TRY(k_rom_combine(c, c.Urp, (long long)nr * np, np, 0, 0, nr, np, c.pi, c.UrpT_c, true));
+  if (c.exact) {
+    c.Urp_c = c.Urp;
+    c.UrpT_c = c.UrpT;
+  } else {
+    FD_TRY(dalloc_t(c, &c.Urp_c, (size_t)c.N * nr * np));
+    FD_TRY(dalloc_t(c, &c.UrpT_c, (size_t)c.N * nr * np));
+    FD_TRY(k_rom_combine(c, c.Urp, (long long)nr * np, np, 0, 0, nr, np, c.pi, c.Urp_c, false));
+    FD_TRY(k_rom_combine(c, c.Urp, (long long)nr * np, np, 0, 0, nr, np, c.pi, c.UrpT_c, true));
+  }
+  if (c.mixed && (np == 8 || np == 24)) {   // the inner iterations' coarse term (Eq. 48) in FP32
+    FD_TRY(dalloc_t(c, &c.Udp_f, (size_t)c.N * nd * np));
+    FD_TRY(k_rom_combine_f32(c, c.Urp, (long long)nr * np, np, ni, 0, nd, np, c.pi, c.Udp_f, np));
+  }
 
   phase("ROM operators / packing");
 
@@ -805,10 +853,21 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
     // P_kj = K_rp^(k)T U_rp^(j), then per cell S_pp_ring = sym(K_pp_ring - K_rp_ring^T U_rp_ring)
     double *Pkj = nullptr, *Spp = nullptr;
     fetidp_status st = FETIDP_OK;
-    st = tmp_alloc(c, reinterpret_cast<void**>(&Pkj), sizeof(double) * (size_t)nrb * nrb * np * np);
-    if (st == FETIDP_OK) st = tmp_alloc(c, reinterpret_cast<void**>(&Spp), sizeof(double) * (size_t)c.N * np * np);
-    if (st == FETIDP_OK) st = k_principal_pairs(c, Krp_d, Pkj);
-    if (st == FETIDP_OK) st = k_spp_cells(c, Kpp_d, Pkj, Spp);
+    if (c.exact) {   // every cell's exact S_pp = K_pp - K_rp^T U_rp (Eq. 22)
+      st = tmp_alloc(c, reinterpret_cast<void**>(&Spp), sizeof(double) * (size_t)c.N * np * np);
+      if (st == FETIDP_OK && cudaMemcpyAsync(Spp, Kpp_d, sizeof(double) * (size_t)c.N * np * np, cudaMemcpyDeviceToDevice,
+                                             c.stream) != cudaSuccess)
+        st = FETIDP_ECUDA;
+      if (st == FETIDP_OK)
+        st = k_batched_gemm(c, true, false, np, np, nr, -1.0, Krp_d, (long long)nr * np, np, c.Urp, (long long)nr * np,
+                            np, 1.0, Spp, (long long)np * np, np, (int)c.N);
+      if (st == FETIDP_OK) st = k_batched_symmetrize(c, Spp, (long long)np * np, np, np, (int)c.N);
+    } else {
+      st = tmp_alloc(c, reinterpret_cast<void**>(&Pkj), sizeof(double) * (size_t)nrb * nrb * np * np);
+      if (st == FETIDP_OK) st = tmp_alloc(c, reinterpret_cast<void**>(&Spp), sizeof(double) * (size_t)c.N * np * np);
+      if (st == FETIDP_OK) st = k_principal_pairs(c, Krp_d, Pkj);
+      if (st == FETIDP_OK) st = k_spp_cells(c, Kpp_d, Pkj, Spp);
+    }
     if (st == FETIDP_OK) phase("S_pp per cell");
     if (st == FETIDP_OK) st = coarse_setup(c, Spp);
     cudaStreamSynchronize(c.stream);
@@ -830,7 +889,7 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
   FD_TRY(dalloc_t(c, &c.w_zP, m * c.nP + 1));
   FD_TRY(dalloc_t(c, &c.w_L1, m * c.L + 1));
   // local ROM bases R and K_s R (Eq. 46): FP64 in the FP64 path, FP32 in the mixed path
-  const size_t rom_elems = m * c.N * nrb * nr;
+  const size_t rom_elems = c.exact ? 1 : m * c.N * nrb * nr;
   const bool rom_f32 = c.mixed && o.interface != 1;   // the Eq. 47 interior bases are FP64
   FD_TRY(dalloc_t(c, &c.w_R, rom_f32 ? (rom_elems + 1) / 2 : rom_elems));
   FD_TRY(dalloc_t(c, &c.w_KR, rom_f32 ? (rom_elems + 1) / 2 : rom_elems));

@@ -255,12 +255,23 @@ fetidp_status op_apply_F(Ctx& c, const double* lam, long long lam_rs, double* y,
     FD_TRY(tc_comb_apply(c, c.cFdd, cview(g), c.delta, c.delta, yd.p, true, yd.rs, yd.cs, 1.0, 0.0, m, c.N));
   else
     FD_TRY(cell_op(c, c.Fdd_c, (long long)nd * nd, nd, nd, nd, cview(g), yd, 1.0, 0.0));
-  // coarse correction: c_p = (T_dr U_rp_ring)^T g, assembled, S_PP^{-1}, prolonged
-  FD_TRY(cell_op(c, c.UrpT_c + ni, (long long)np * nr, nr, np, nd, cview(g), cp, 1.0, 0.0));
+  // coarse correction: c_p = (T_dr U_rp_ring)^T g, assembled, S_PP^{-1}, prolonged.  The mixed path
+  // applies it with FP32 copies of U_dp_ring and of the S_PP factor (a fixed perturbation of the
+  // operator of the inner iterations, well inside their 1e-6 tolerance; the outer FGMRES is FP64).
+  if (c.Udp_f)
+    FD_TRY(k_udp_f32(c, true, cview(g), cp, 1.0, 0.0, m));
+  else
+    FD_TRY(cell_op(c, c.UrpT_c + ni, (long long)np * nr, nr, np, nd, cview(g), cp, 1.0, 0.0));
   FD_TRY(k_primal_assemble(c, cview(cp), c.w_P1, c.nP, 1.0, 0.0, m));
-  FD_TRY(coarse_solve(c, c.w_P1, c.nP, c.w_P2, c.nP, m));
+  if (c.bcr.mats_f)
+    FD_TRY(coarse_solve_f32(c, c.w_P1, c.nP, c.w_P2, c.nP, m));
+  else
+    FD_TRY(coarse_solve(c, c.w_P1, c.nP, c.w_P2, c.nP, m));
   FD_TRY(k_primal_extract(c, c.w_P2, c.nP, cp, m));
-  FD_TRY(cell_op(c, c.Urp_c + (size_t)ni * np, (long long)nr * np, np, nd, np, cview(cp), yd, 1.0, 1.0));
+  if (c.Udp_f)
+    FD_TRY(k_udp_f32(c, false, cview(cp), yd, 1.0, 1.0, m));
+  else
+    FD_TRY(cell_op(c, c.Urp_c + (size_t)ni * np, (long long)nr * np, np, nd, np, cview(cp), yd, 1.0, 1.0));
   FD_TRY(k_scatter_B(c, cview(yd), y, y_rs, nullptr, 1.0, 0.0, m));
   return FETIDP_OK;
 }
@@ -320,7 +331,9 @@ fetidp_status U_apply(Ctx& c, CCellVec vR, const double* vP, long long vP_rs, do
   FD_TRY(k_primal_assemble(c, cview(cp), c.w_P1, c.nP, -1.0, 1.0, m));
   FD_TRY(coarse_solve(c, c.w_P1, c.nP, c.w_zP, c.nP, m));
   // t_d = U_rd_ring^T v_r - T_dr U_rp_ring A_p^T z_P
-  if (c.mixed)
+  if (c.exact)   // standard FETI-DP: rows d of each cell's own K_rr^{-1} (symmetric)
+    FD_TRY(cell_op(c, c.Kinv + (size_t)ni * nr, (long long)nr * nr, nr, nd, nr, vR, td, 1.0, 0.0));
+  else if (c.mixed)
     FD_TRY(tc_comb_apply(c, c.cUrdT, vR, c.delta, c.delta, td.p, true, td.rs, td.cs, 1.0, 0.0, m, c.N));
   else
     FD_TRY(k_grouped_gemm(c, c.Kinv + (size_t)ni * nr, (long long)nr * nr, nr, nd, nr, vR, td, c.delta,
@@ -331,9 +344,11 @@ fetidp_status U_apply(Ctx& c, CCellVec vR, const double* vP, long long vP_rs, do
   return FETIDP_OK;
 }
 
-// Eq. 46 for every (rhs, cell): x_r = R (R^T K_s R)^{-1} R^T v_r, R = [K_rr^(sigma_k)^{-1} v_r]_k
+// Eq. 46 for every (rhs, cell): x_r = R (R^T K_s R)^{-1} R^T v_r, R = [K_rr^(sigma_k)^{-1} v_r]_k;
+// standard FETI-DP: x_r = K_rr^(s)^{-1} v_r with the cell's own inverse
 fetidp_status local_rom(Ctx& c, CCellVec vR, CellVec xR) {
   const int m = c.m, nr = c.nr, nrb = c.nrb;
+  if (c.exact) return cell_op(c, c.Kinv, (long long)nr * nr, nr, nr, nr, vR, xR, 1.0, 0.0);
   if (c.mixed) {
     float* Rf = reinterpret_cast<float*>(c.w_R);
     float* KRf = reinterpret_cast<float*>(c.w_KR);
@@ -588,7 +603,9 @@ fetidp_status op_precondition(Ctx& c, const double* x, double* y) {
   FD_TRY(cell_op(c, c.UrpT_c + ni, (long long)np * nr, nr, np, nd, cview(g), cp, 1.0, 0.0));
   FD_TRY(k_primal_assemble(c, cview(cp), c.w_P1, c.nP, -1.0, 0.0, m));
   FD_TRY(coarse_solve(c, c.w_P1, c.nP, c.w_P1, c.nP, m));
-  if (c.mixed)
+  if (c.exact)   // columns d of each cell's own K_rr^{-1}
+    FD_TRY(cell_op(c, c.Kinv + ni, (long long)nr * nr, nr, nr, nd, cview(g), yR, -1.0, 1.0));
+  else if (c.mixed)
     FD_TRY(tc_comb_apply(c, c.cUrd, cview(g), c.delta, c.delta, yR.p, true, yR.rs, yR.cs, -1.0, 1.0, m, c.N));
   else
     FD_TRY(k_grouped_gemm(c, c.Kinv + ni, (long long)nr * nr, nr, nr, nd, cview(g), yR, c.delta, -1.0,
@@ -832,6 +849,7 @@ void fetidp_default_options(fetidp_options* o) {
   o->check_inputs = 1;
   o->mixed_assembled = -1;
   o->interface = 0;
+  o->method = 0;
 }
 
 const char* fetidp_status_string(fetidp_status s) {
@@ -1104,6 +1122,7 @@ fetidp_status fetidp_rom_data(fetidp_ctx* ctx, int* sigma, double* alpha, double
   Ctx& c = ctx->c;
   if (sigma) std::memcpy(sigma, c.sigma.data(), sizeof(int) * c.nrb);
   const size_t bytes = sizeof(double) * c.N * c.nrb;
+  if (c.exact) { set_error("standard FETI-DP has no reduced-order model"); return FETIDP_EINVAL; }
   if (alpha) FD_CUDA(cudaMemcpyAsync(alpha, c.alpha, bytes, cudaMemcpyDeviceToHost, c.stream));
   if (pi) FD_CUDA(cudaMemcpyAsync(pi, c.pi, bytes, cudaMemcpyDeviceToHost, c.stream));
   if (delta) FD_CUDA(cudaMemcpyAsync(delta, c.delta, bytes, cudaMemcpyDeviceToHost, c.stream));

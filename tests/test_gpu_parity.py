@@ -335,3 +335,28 @@ def test_rom_dirichlet_interface_solve_converges_to_monolithic(name):
         assert _rel(uh[r], ref[r]) < 1e-8
     _, _, info_pcg = _solver(oc.prob, tol_outer=1e-10).solve()
     assert info["outer_its"] > info_pcg["outer_its"]
+
+
+@pytest.mark.parametrize("name", ["cfg1", "bcc3d"])
+def test_standard_fetidp_on_gpu(name):
+    """method = 1, the paper's comparison system (Sec. 2.2.4): every cell's own K_rr^{-1}.  The block
+    preconditioner of Eq. 44 is then exact, so FGMRES takes one outer iteration and its inner PCG
+    is standard FETI-DP's (the oracle's StandardFETIDP needs the same number of iterations at the
+    same tolerance); the solution is the monolithic one."""
+    from oracle import feti_dp
+    oc = case(name)
+    s = _solver(oc.prob, method=1, tol_outer=1e-8, tol_inner=1e-11)
+    u, lam, info = s.solve()
+    assert info["outer_its"] == 1 and info["rel_residual"] <= 1e-8
+    fd = feti_dp.StandardFETIDP(oc.lat, blocks=oc.blocks)
+    its = []
+    for r in range(s.n_rhs):
+        its.append(fd.solve(rhs=r, tol=1e-11)[3])
+    # the load cases share one PCG (counted once, to the slowest one), checked every second iteration
+    assert abs(info["inner_its_total"] - max(its)) <= 2
+    ref = _mono_cells(oc)
+    uh = _host(u)
+    for r in range(s.n_rhs):
+        assert _rel(uh[r], ref[r]) < 1e-9
+    with pytest.raises(Exception):
+        s.rom_data()
