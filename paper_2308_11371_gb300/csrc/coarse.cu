@@ -178,8 +178,8 @@ __global__ void bcr_final_kernel(const double* __restrict__ Ainv, int b, const d
 
 // ---- FP32 copy for the mixed path's inner iterations.  The level vectors hold up to eight RHS
 //      interleaved ([chunk][vec_len][8] floats), so one lane reads all RHS of a column as two
-//      16-byte loads; a warp computes one output row, each lane summing every 32nd column of it in
-//      FP32, and the eight lane partials are reduced in FP64.
+//      16-byte loads; a warp computes four output rows, each lane summing every 32nd column of
+//      them in FP32, and the 32 (row, RHS) lane partials are reduced by halving exchanges.
 struct BcrLevelF {
   int b, n, nch;
   long long rs;                 // per-chunk stride of the level vectors, in 8-float entries
@@ -195,87 +195,100 @@ struct BcrLevelF {
   const float* xl_n;
 };
 
-__device__ __forceinline__ void bcr_row_f32(const float* __restrict__ M, const float* __restrict__ v, int b,
-                                            int lane, float sgn, float acc[8]) {
-#pragma unroll 4
+// acc[a][r] += sgn * sum_q M[(row0 + a) b + q] v[q][r] over this lane's columns q (every 32nd),
+// for the rows row0 + a < b.  One pair of 16-byte reads of v serves the four rows.
+__device__ __forceinline__ void bcr_rows4_f32(const float* __restrict__ M, int row0, const float* __restrict__ v,
+                                              int b, int lane, float sgn, float acc[4][8]) {
+  const int na = min(4, b - row0);
+#pragma unroll 2
   for (int q = lane; q < b; q += 32) {
-    const float mv = sgn * __ldcs(M + q);
-    const float4 a = *reinterpret_cast<const float4*>(v + (size_t)q * 8);
-    const float4 e = *reinterpret_cast<const float4*>(v + (size_t)q * 8 + 4);
-    acc[0] = fmaf(mv, a.x, acc[0]);
-    acc[1] = fmaf(mv, a.y, acc[1]);
-    acc[2] = fmaf(mv, a.z, acc[2]);
-    acc[3] = fmaf(mv, a.w, acc[3]);
-    acc[4] = fmaf(mv, e.x, acc[4]);
-    acc[5] = fmaf(mv, e.y, acc[5]);
-    acc[6] = fmaf(mv, e.z, acc[6]);
-    acc[7] = fmaf(mv, e.w, acc[7]);
+    const float4 x0 = *reinterpret_cast<const float4*>(v + (size_t)q * 8);
+    const float4 x1 = *reinterpret_cast<const float4*>(v + (size_t)q * 8 + 4);
+    const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const float mv = a < na ? sgn * __ldcs(M + (size_t)(row0 + a) * b + q) : 0.f;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) acc[a][r] = fmaf(mv, xv[r], acc[a][r]);
+    }
   }
 }
 
-// warp sum of the eight partials; lane 0 receives them in s[]
-__device__ __forceinline__ void bcr_warp_sum8(const float acc[8], double s[8]) {
+// Sum of the 32 values acc[a][r] over the warp by halving exchanges (31 shuffles): lane l ends
+// with the total of value l = 8 a + r.
+__device__ __forceinline__ float bcr_warp_reduce32(float acc[4][8], int lane) {
+  float v[32];
 #pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    double t = (double)acc[r];
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-    s[r] = t;
+    for (int r = 0; r < 8; ++r) v[8 * a + r] = acc[a][r];
+#pragma unroll
+  for (int o = 16, n = 32; o > 0; o >>= 1, n >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int k = 0; k < n / 2; ++k) {
+      const float send = up ? v[k] : v[k + n / 2];
+      const float keep = up ? v[k + n / 2] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
   }
+  return v[0];
 }
 
+// one warp per four rows of a new block: bl[l+1][i/2] = bl[l][i] - U_{i-1}^T bl[l][i-1] - V_{i+1}^T bl[l][i+1]
 __global__ void bcr_forward_f32_kernel(BcrLevelF P) {
   const int lane = threadIdx.x & 31;
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int n_new = (P.n + 1) / 2;
-  if (gw >= (long long)n_new * P.b) return;
-  const int inew = (int)(gw / P.b), row = (int)(gw - (long long)inew * P.b);
-  const int i = 2 * inew, b = P.b;
+  const int n_new = (P.n + 1) / 2, b = P.b, g4 = (b + 3) / 4;
+  if (gw >= (long long)n_new * g4) return;
+  const int inew = (int)(gw / g4), row0 = 4 * (int)(gw - (long long)inew * g4);
+  const int i = 2 * inew;
+  const int a = lane >> 3, r = lane & 7;
   for (int ch = 0; ch < P.nch; ++ch) {
     const float* vl = P.bl_l + (size_t)ch * P.rs * 8;
-    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (i - 1 >= 0 && P.offUT[i - 1] >= 0)
-      bcr_row_f32(P.mats + P.offUT[i - 1] + (size_t)row * b, vl + (size_t)(i - 1) * b * 8, b, lane, 1.f, acc);
-    if (i + 1 < P.n)
-      bcr_row_f32(P.mats + P.offVT[i + 1] + (size_t)row * b, vl + (size_t)(i + 1) * b * 8, b, lane, 1.f, acc);
-    double s[8];
-    bcr_warp_sum8(acc, s);
-    if (lane == 0) {
-      const float* src = vl + ((size_t)i * b + row) * 8;
-      float* dst = P.bl_n + (size_t)ch * P.rs * 8 + ((size_t)inew * b + row) * 8;
+    float acc[4][8];
 #pragma unroll
-      for (int r = 0; r < 8; ++r) dst[r] = (float)((double)src[r] - s[r]);
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
+    if (i - 1 >= 0 && P.offUT[i - 1] >= 0)
+      bcr_rows4_f32(P.mats + P.offUT[i - 1], row0, vl + (size_t)(i - 1) * b * 8, b, lane, 1.f, acc);
+    if (i + 1 < P.n) bcr_rows4_f32(P.mats + P.offVT[i + 1], row0, vl + (size_t)(i + 1) * b * 8, b, lane, 1.f, acc);
+    const float s = bcr_warp_reduce32(acc, lane);
+    if (row0 + a < b) {
+      const size_t o = ((size_t)(row0 + a)) * 8 + r;
+      P.bl_n[(size_t)ch * P.rs * 8 + (size_t)inew * b * 8 + o] = vl[(size_t)i * b * 8 + o] - s;
     }
   }
 }
 
+// one warp per four rows: x[l][j] = Ainv_j bl[l][j] - V_j x[l][j-1] - U_j x[l][j+1] (odd j),
+// x[l][j] = x[l+1][j/2] (even j)
 __global__ void bcr_backward_f32_kernel(BcrLevelF P) {
   const int lane = threadIdx.x & 31;
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (gw >= (long long)P.n * P.b) return;
-  const int j = (int)(gw / P.b), row = (int)(gw - (long long)j * P.b);
-  const int b = P.b;
+  const int b = P.b, g4 = (b + 3) / 4;
+  if (gw >= (long long)P.n * g4) return;
+  const int j = (int)(gw / g4), row0 = 4 * (int)(gw - (long long)j * g4);
+  const int a = lane >> 3, r = lane & 7;
   for (int ch = 0; ch < P.nch; ++ch) {
     const size_t co = (size_t)ch * P.rs * 8;
-    float* dst = P.xl_l + co + ((size_t)j * b + row) * 8;
-    if ((j & 1) == 0) {   // even block: copied from the reduced level
-      if (lane < 2)
-        reinterpret_cast<float4*>(dst)[lane] =
-            reinterpret_cast<const float4*>(P.xl_n + co + ((size_t)(j / 2) * b + row) * 8)[lane];
+    const size_t o = ((size_t)(row0 + a)) * 8 + r;
+    if ((j & 1) == 0) {
+      if (row0 + a < b) P.xl_l[co + (size_t)j * b * 8 + o] = P.xl_n[co + (size_t)(j / 2) * b * 8 + o];
       continue;
     }
-    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    bcr_row_f32(P.mats + P.offA[j] + (size_t)row * b, P.bl_l + co + (size_t)j * b * 8, b, lane, 1.f, acc);
-    bcr_row_f32(P.mats + P.offV[j] + (size_t)row * b, P.xl_n + co + (size_t)((j - 1) / 2) * b * 8, b, lane, -1.f,
-                acc);
-    if (j + 1 < P.n)
-      bcr_row_f32(P.mats + P.offU[j] + (size_t)row * b, P.xl_n + co + (size_t)((j + 1) / 2) * b * 8, b, lane,
-                  -1.f, acc);
-    double s[8];
-    bcr_warp_sum8(acc, s);
-    if (lane == 0)
+    float acc[4][8];
 #pragma unroll
-      for (int r = 0; r < 8; ++r) dst[r] = (float)s[r];
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
+    bcr_rows4_f32(P.mats + P.offA[j], row0, P.bl_l + co + (size_t)j * b * 8, b, lane, 1.f, acc);
+    bcr_rows4_f32(P.mats + P.offV[j], row0, P.xl_n + co + (size_t)((j - 1) / 2) * b * 8, b, lane, -1.f, acc);
+    if (j + 1 < P.n)
+      bcr_rows4_f32(P.mats + P.offU[j], row0, P.xl_n + co + (size_t)((j + 1) / 2) * b * 8, b, lane, -1.f, acc);
+    const float s = bcr_warp_reduce32(acc, lane);
+    if (row0 + a < b) P.xl_l[co + (size_t)j * b * 8 + o] = s;
   }
 }
 
@@ -283,17 +296,20 @@ __global__ void bcr_final_f32_kernel(const float* __restrict__ Ainv, int b, cons
                                      long long rs, int nch) {
   const int lane = threadIdx.x & 31;
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (gw >= b) return;
-  const int row = (int)gw;
+  const int g4 = (b + 3) / 4;
+  if (gw >= g4) return;
+  const int row0 = 4 * (int)gw;
+  const int a = lane >> 3, r = lane & 7;
   for (int ch = 0; ch < nch; ++ch) {
     const size_t co = (size_t)ch * rs * 8;
-    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    bcr_row_f32(Ainv + (size_t)row * b, bl + co, b, lane, 1.f, acc);
-    double s[8];
-    bcr_warp_sum8(acc, s);
-    if (lane == 0)
+    float acc[4][8];
 #pragma unroll
-      for (int r = 0; r < 8; ++r) xl[co + (size_t)row * 8 + r] = (float)s[r];
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
+    bcr_rows4_f32(Ainv, row0, bl + co, b, lane, 1.f, acc);
+    const float s = bcr_warp_reduce32(acc, lane);
+    if (row0 + a < b) xl[co + ((size_t)(row0 + a)) * 8 + r] = s;
   }
 }
 
@@ -622,7 +638,7 @@ fetidp_status coarse_solve(Ctx& c, const double* b, long long b_rs, double* x, l
 }
 
 // The same solve on the FP32 copy (mixed path): FP32 factor and level vectors, FP32 products summed
-// per lane, FP64 warp sums.  The rounding of the copy is a fixed linear perturbation of S_PP^{-1}.
+// per lane and over the warp.  The rounding of the copy is a fixed linear perturbation of S_PP^{-1}.
 fetidp_status coarse_solve_f32(Ctx& c, const double* b, long long b_rs, double* x, long long x_rs, int nrhs) {
   CoarseBCR& B = c.bcr;
   if (!B.mats_f) return coarse_solve(c, b, b_rs, x, x_rs, nrhs);
@@ -649,20 +665,20 @@ fetidp_status coarse_solve_f32(Ctx& c, const double* b, long long b_rs, double* 
   for (int l = 0; l < B.levels; ++l) {
     BcrLevelF P{B.b, B.n_at[l], nch, rs, B.mats_f, tA[l], tU[l], tUT[l], tV[l], tVT[l],
                 B.bl_f + B.vec_off[l] * 8, B.bl_f + B.vec_off[l + 1] * 8, nullptr, nullptr};
-    const long long warps = (long long)((B.n_at[l] + 1) / 2) * B.b;
+    const long long warps = (long long)((B.n_at[l] + 1) / 2) * ((B.b + 3) / 4);
     bcr_forward_f32_kernel<<<grid_exact(warps * 32), 256, 0, c.stream>>>(P);
     FD_CHECK_LAUNCH();
   }
   {
     const int L = B.levels;
-    bcr_final_f32_kernel<<<grid_exact((long long)B.b * 32), 256, 0, c.stream>>>(
+    bcr_final_f32_kernel<<<grid_exact((long long)((B.b + 3) / 4) * 32), 256, 0, c.stream>>>(
         B.mats_f + B.off_final_f, B.b, B.bl_f + B.vec_off[L] * 8, B.xl_f + B.vec_off[L] * 8, rs, nch);
     FD_CHECK_LAUNCH();
   }
   for (int l = B.levels - 1; l >= 0; --l) {
     BcrLevelF P{B.b, B.n_at[l], nch, rs, B.mats_f, tA[l], tU[l], tUT[l], tV[l], tVT[l],
                 B.bl_f + B.vec_off[l] * 8, nullptr, B.xl_f + B.vec_off[l] * 8, B.xl_f + B.vec_off[l + 1] * 8};
-    const long long warps = (long long)B.n_at[l] * B.b;
+    const long long warps = (long long)B.n_at[l] * ((B.b + 3) / 4);
     bcr_backward_f32_kernel<<<grid_exact(warps * 32), 256, 0, c.stream>>>(P);
     FD_CHECK_LAUNCH();
   }

@@ -661,21 +661,25 @@ __global__ void __launch_bounds__(256) rom_combine_f32_kernel(const double* __re
 
 // y[rhs][cell][0..rows) = alpha M_f32[cell] x[rhs][cell][0..cols) + beta y for SYMMETRIC square
 // operators (F_dd_ring and S_dd_ring: combinations of symmetric principal operators): row j of M is
-// read as column j.  One CTA per cell, one thread per output row (up to kAsmRows rows per thread);
-// for each column j the threads read 32 consecutive entries of M per warp (128 coalesced bytes,
-// streamed past L2) and the column's x values for every RHS as one broadcast 16-byte read per four
-// RHS from shared memory ([column][8] layout), so each warp-wide shared read is one wavefront.
+// read as column j.  One CTA per cell; a thread owns four consecutive rows, so for each column j it
+// issues one 16-byte streaming load of M[j][4t..4t+3] (a warp reads 512 contiguous bytes), and the
+// column's x values for every RHS arrive as two broadcast 16-byte reads from shared memory
+// ([column][8] layout).  kAsmU columns' loads are issued before their arithmetic.
 constexpr int kMaxRhsF32 = 8;
-constexpr int kAsmRows = 3;            // rows per thread: 256 threads cover n_d <= 768
-constexpr int kAsmUnroll = 4;          // columns whose loads are issued before their arithmetic
-__global__ void __launch_bounds__(256) cell_gemm_f32_kernel(const float* __restrict__ mats, int ldm, int rows,
-                                                            int cols, const double* __restrict__ x, long long x_rs,
-                                                            int x_cs, double* __restrict__ y, long long y_rs,
-                                                            int y_cs, double alpha, double beta, int nrhs) {
+constexpr int kAsmU = 8;
+constexpr int kAsmMaxThreads = 256;    // rows <= 1024
+__global__ void __launch_bounds__(kAsmMaxThreads) cell_gemm_f32_kernel(const float* __restrict__ mats, int ldm,
+                                                                       int rows, int cols,
+                                                                       const double* __restrict__ x, long long x_rs,
+                                                                       int x_cs, double* __restrict__ y,
+                                                                       long long y_rs, int y_cs, double alpha,
+                                                                       double beta, int nrhs) {
   extern __shared__ __align__(16) float xsf[];   // [cols][kMaxRhsF32]
   const long long cell = blockIdx.x;
   const int tid = threadIdx.x;
   const float* M = mats + cell * (long long)rows * ldm;
+  const int r0 = 4 * tid;                        // ldm is a multiple of 4 and >= rows: the load stays in row j
+  const bool live = r0 < rows;
   for (int rb0 = 0; rb0 < nrhs; rb0 += kMaxRhsF32) {
     const int rb = min(kMaxRhsF32, nrhs - rb0);
     __syncthreads();
@@ -684,44 +688,37 @@ __global__ void __launch_bounds__(256) cell_gemm_f32_kernel(const float* __restr
       xsf[t] = q < rb ? (float)x[(rb0 + q) * x_rs + cell * x_cs + j] : 0.f;
     }
     __syncthreads();
-    float acc[kAsmRows][kMaxRhsF32];
+    float acc[4][kMaxRhsF32];
 #pragma unroll
-    for (int a = 0; a < kAsmRows; ++a)
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int q = 0; q < kMaxRhsF32; ++q) acc[a][q] = 0.f;
-    int r[kAsmRows];
-    bool live[kAsmRows];
+    for (int j0 = 0; j0 < cols; j0 += kAsmU) {
+      float4 m[kAsmU];
 #pragma unroll
-    for (int a = 0; a < kAsmRows; ++a) {
-      r[a] = tid + a * (int)blockDim.x;
-      live[a] = r[a] < rows;
-    }
-    for (int j0 = 0; j0 < cols; j0 += kAsmUnroll) {
-      float m[kAsmUnroll][kAsmRows];
+      for (int u = 0; u < kAsmU; ++u)
+        m[u] = (live && j0 + u < cols) ? __ldcs(reinterpret_cast<const float4*>(M + (long long)(j0 + u) * ldm + r0))
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-      for (int u = 0; u < kAsmUnroll; ++u)
-#pragma unroll
-        for (int a = 0; a < kAsmRows; ++a)
-          m[u][a] = (live[a] && j0 + u < cols) ? __ldcs(M + (long long)(j0 + u) * ldm + r[a]) : 0.f;
-#pragma unroll
-      for (int u = 0; u < kAsmUnroll; ++u) {
+      for (int u = 0; u < kAsmU; ++u) {
         if (j0 + u >= cols) break;
         const float4 x0 = reinterpret_cast<const float4*>(xsf)[(j0 + u) * 2];
         const float4 x1 = reinterpret_cast<const float4*>(xsf)[(j0 + u) * 2 + 1];
         const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+        const float mv[4] = {m[u].x, m[u].y, m[u].z, m[u].w};
 #pragma unroll
-        for (int a = 0; a < kAsmRows; ++a)
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-          for (int q = 0; q < kMaxRhsF32; ++q) acc[a][q] = fmaf(m[u][a], xv[q], acc[a][q]);
+          for (int q = 0; q < kMaxRhsF32; ++q) acc[a][q] = fmaf(mv[a], xv[q], acc[a][q]);
       }
     }
 #pragma unroll
-    for (int a = 0; a < kAsmRows; ++a) {
-      if (!live[a]) continue;
+    for (int a = 0; a < 4; ++a) {
+      if (r0 + a >= rows) continue;
 #pragma unroll
       for (int q = 0; q < kMaxRhsF32; ++q) {
         if (q < rb) {
-          double* dst = y + (rb0 + q) * y_rs + cell * y_cs + r[a];
+          double* dst = y + (rb0 + q) * y_rs + cell * y_cs + r0 + a;
           *dst = (beta == 0.0) ? alpha * (double)acc[a][q] : alpha * (double)acc[a][q] + beta * (*dst);
         }
       }
@@ -737,7 +734,7 @@ __global__ void __launch_bounds__(256) cell_gemm_f32_kernel(const float* __restr
 // load per row), accumulates them for up to eight RHS in FP32 and the RG row groups are summed in
 // shared memory; in udp_n a thread owns a row.
 template <int NP>
-__global__ void __launch_bounds__(256) udp_t_f32_kernel(const float* __restrict__ U, int nd,
+__global__ void __launch_bounds__(256, 3) udp_t_f32_kernel(const float* __restrict__ U, int nd,
                                                         const double* __restrict__ g, long long g_rs, int g_cs,
                                                         double* __restrict__ cp, long long c_rs, int c_cs,
                                                         int nrhs) {
@@ -764,7 +761,7 @@ __global__ void __launch_bounds__(256) udp_t_f32_kernel(const float* __restrict_
 #pragma unroll
       for (int q = 0; q < 8; ++q) acc[a][q] = 0.f;
     if (rg < RG) {
-#pragma unroll 2
+#pragma unroll 4
       for (int d = rg; d < nd; d += RG) {
         const float4 u = __ldcs(Uc + (long long)d * G + grp);
         const float4 x0 = reinterpret_cast<const float4*>(gs)[d * 2];
@@ -1136,27 +1133,31 @@ __device__ __forceinline__ void neumaier_add(T& s, T& c, T x) {
 // product), FP32 chunk sums accumulated with Neumaier's compensation; then warp 0 runs the same
 // diagonal-pivoted Cholesky solve as the warp kernel, and all threads form x = R c.
 constexpr int kGbQ = 32;
-constexpr int kGbLd = 33;
+constexpr int kGbLd = 36;   // 16-byte rows; a warp's 16 distinct K R rows take the minimum two wavefronts
+// The staging chunks of R, K R and v live inside the L factor's region (used only after the Gram
+// matrix is complete), so a 64-basis block needs 70 KB and three blocks fit an SM.
 __host__ __device__ inline size_t gram_block_smem(int nrb) {
   const size_t ld = (size_t)nrb + 1;
-  return sizeof(double) * (2 * nrb * ld + 6 * (size_t)nrb + 2) + sizeof(float) * (2 * (size_t)nrb * kGbLd + kGbQ);
+  const size_t stage = sizeof(float) * (2 * (size_t)nrb * kGbLd + kGbQ);
+  const size_t lc = sizeof(double) * nrb * ld;
+  return sizeof(double) * (nrb * ld + 6 * (size_t)nrb + 2) + (stage > lc ? stage : lc);
 }
-__global__ void __launch_bounds__(256) gram_block_f32_kernel(const float* __restrict__ R, const float* __restrict__ KR,
+__global__ void __launch_bounds__(256, 3) gram_block_f32_kernel(const float* __restrict__ R, const float* __restrict__ KR,
                                                              const double* __restrict__ v, long long v_rs, int v_cs,
                                                              double* __restrict__ x, long long x_rs, int x_cs, int nr,
                                                              int nrb, long long ncell, double drop_rel) {
   extern __shared__ __align__(16) double gbsm[];
   const int ld = nrb + 1;
   double* S = gbsm;                                  // [nrb][ld]
-  double* Lc = S + (size_t)nrb * ld;                 // [nrb][ld]
-  double* hs = Lc + (size_t)nrb * ld;
+  double* hs = S + (size_t)nrb * ld;
   double* ys = hs + nrb;
   double* cs = ys + nrb;
   double* colv = cs + nrb;
   int* piv = reinterpret_cast<int*>(colv + nrb);     // nrb ints in 2 nrb doubles of room
   double* sh_inv = colv + 3 * nrb;
   int* sh_jb = reinterpret_cast<int*>(sh_inv + 1);
-  float* Rs = reinterpret_cast<float*>(sh_inv + 2);
+  double* Lc = sh_inv + 2;                           // [nrb][ld], after the Gram matrix is formed
+  float* Rs = reinterpret_cast<float*>(Lc);          // staging while it is formed
   float* Ks = Rs + (size_t)nrb * kGbLd;
   float* vs = Ks + (size_t)nrb * kGbLd;
   const long long col = blockIdx.x;                  // rhs * ncell + cell
@@ -1186,19 +1187,26 @@ __global__ void __launch_bounds__(256) gram_block_f32_kernel(const float* __rest
     for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int b = 0; b < 4; ++b) part[a][b] = 0.f;
-#pragma unroll 8
-    for (int qq = 0; qq < kGbQ; ++qq) {
-      float rv[4], kv[4];
+#pragma unroll 2
+    for (int qq = 0; qq < kGbQ; qq += 4) {
+      float4 rv[4], kv[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
         const int i = ti + 16 * a, j = tj + 16 * a;
-        rv[a] = i < nrb ? Rs[i * kGbLd + qq] : 0.f;
-        kv[a] = j < nrb ? Ks[j * kGbLd + qq] : 0.f;
+        rv[a] = i < nrb ? *reinterpret_cast<const float4*>(Rs + i * kGbLd + qq) : make_float4(0.f, 0.f, 0.f, 0.f);
+        kv[a] = j < nrb ? *reinterpret_cast<const float4*>(Ks + j * kGbLd + qq) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) part[a][b] = fmaf(rv[a], kv[b], part[a][b]);
+        for (int b = 0; b < 4; ++b) {
+          float p = part[a][b];
+          p = fmaf(rv[a].x, kv[b].x, p);
+          p = fmaf(rv[a].y, kv[b].y, p);
+          p = fmaf(rv[a].z, kv[b].z, p);
+          p = fmaf(rv[a].w, kv[b].w, p);
+          part[a][b] = p;
+        }
     }
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -1652,14 +1660,16 @@ fetidp_status k_cell_gemm_f32(Ctx& c, const float* mats, int ldm, int rows, int 
   // algorithmic bytes: the operators once, the FP64 vectors in and out
   ProfScope ps(c, FETIDP_K_ASM_OP, 2.0 * rows * cols * (double)c.N * nrhs,
                4.0 * c.N * (double)rows * ldm + 8.0 * c.N * (double)nrhs * (rows + cols));
-  if (rows != cols || rows > kAsmRows * 256) {
-    set_error("FP32 cell operators: square and at most 768 rows");
+  if (rows != cols || rows > 4 * kAsmMaxThreads || ldm % 4 != 0 || ldm < rows ||
+      (reinterpret_cast<uintptr_t>(mats) & 15) != 0) {
+    set_error("FP32 cell operators: square, at most 1024 rows, rows padded to 16 bytes");
     return FETIDP_EINVAL;
   }
   const size_t smem = (size_t)cols * kMaxRhsF32 * sizeof(float);
+  const int threads = ((rows + 3) / 4 + 31) / 32 * 32;
   cudaFuncSetAttribute(cell_gemm_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cell_gemm_f32_kernel<<<(unsigned)c.N, 256, smem, c.stream>>>(mats, ldm, rows, cols, x.p, x.rs, x.cs, y.p, y.rs,
-                                                               y.cs, alpha, beta, nrhs);
+  cell_gemm_f32_kernel<<<(unsigned)c.N, threads, smem, c.stream>>>(mats, ldm, rows, cols, x.p, x.rs, x.cs, y.p,
+                                                                   y.rs, y.cs, alpha, beta, nrhs);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }

@@ -22,28 +22,43 @@ constexpr int kRedThreads = 256;
 // apart), n = 0 for a Dirichlet row (block 1).  The block is the inverse of the n x n matrix
 // tridiag(-1, 2, -1), (T^{-1})_ab = (min(a, b) + 1)(n - max(a, b)) / (n + 1): 1/2 for n = 1
 // (every 2D row, 3D face rows), quarters for the n = 3 rows of a 3D cell edge (exact in binary).
+// The blocks for n = 1, 2, 3 as constants (each the correctly rounded quotient, as a run-time FP64
+// division would give): GB300's FP64 divide is a long software sequence on its slow FP64 pipe.
 __device__ __forceinline__ double tinv(int a, int b, int n) {
   const int lo = a < b ? a : b, hi = a < b ? b : a;
-  return (double)((lo + 1) * (n - hi)) / (double)(n + 1);
+  const int num = (lo + 1) * (n - hi);
+  if (n == 1) return 0.5;
+  if (n == 2) return num == 2 ? 2.0 / 3.0 : 1.0 / 3.0;
+  if (n == 3) return 0.25 * num;
+  return (double)num / (double)(n + 1);
 }
 
 
+// -x when neg is 1, by the sign bit alone (no FP64 instruction: GB300 runs FP64 at 1/64 of FP32)
+__device__ __forceinline__ double flip_sign(double x, int neg) {
+  return __longlong_as_double(__double_as_longlong(x) ^ ((long long)neg << 63));
+}
+
 // x_d = B_d^T lambda, or B_d^T D lambda when dinfo is given.  One thread per (cell, dual DOF):
 // the (multiplier row, weight) terms of the entry -- at most two signed rows, each expanded into
-// at most three rows by the D block -- are decoded once, then applied to every RHS.
+// at most three rows by the D block -- are decoded once, then applied to every RHS.  Entries whose
+// terms all have weight +-1 (every entry of the unscaled map) take one FP64 addition per RHS, the
+// signs applied to the bits.
 __global__ void gather_BT_kernel(const int* __restrict__ gath, const double* __restrict__ lam,
                                  long long lam_rs, const int* __restrict__ dinfo, int d,
                                  double* __restrict__ out, long long out_rs, int out_cs, int nd,
                                  long long ncell, int nrhs, double beta) {
   const int total = (int)(ncell * nd);               // < 2^31, checked by the host
+  const bool overwrite = beta == 0.0;
   for (int cj = blockIdx.x * blockDim.x + threadIdx.x; cj < total; cj += gridDim.x * blockDim.x) {
     const int cell = cj / nd;
     const int j = cj - cell * nd;
     const int2 cc = reinterpret_cast<const int2*>(gath)[cj];
-    // at most two signed rows, each expanded into at most three rows by its D block: six terms,
-    // kept in registers (fixed trip counts) with zero weights past the live ones
+    // six term slots in registers (fixed trip counts); live / neg are bit masks over the slots
     int idx[6];
     double w[6];
+    int live = 0, neg = 0;
+    bool unit = true;
 #pragma unroll
     for (int k = 0; k < 6; ++k) { idx[k] = 0; w[k] = 0.0; }
 #pragma unroll
@@ -51,46 +66,61 @@ __global__ void gather_BT_kernel(const int* __restrict__ gath, const double* __r
       const int code = h ? cc.y : cc.x;
       if (code == 0) continue;
       const int row = (code > 0 ? code : -code) - 1;
-      const double sg = code > 0 ? 1.0 : -1.0;
+      const int sg = code < 0 ? 1 : 0;
       const int dc = dinfo ? dinfo[row] : 0;
       const int n = dc >> 8, q = dc & 0xff;
+      if (n == 0) {
+        idx[3 * h] = row;
+        w[3 * h] = sg ? -1.0 : 1.0;
+        live |= 1 << (3 * h);
+        neg |= sg << (3 * h);
+        continue;
+      }
+      unit = false;
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
-        const int k = 3 * h + b;
-        if (n == 0) {
-          if (b == 0) { idx[k] = row; w[k] = sg; }
-        } else if (b < n) {
+        if (b < n) {
+          const int k = 3 * h + b;
           idx[k] = row + (b - q) * d;
-          w[k] = sg * tinv(q, b, n);
+          const double t = tinv(q, b, n);
+          w[k] = sg ? -t : t;
+          live |= 1 << k;
         }
       }
     }
     for (int rhs = 0; rhs < nrhs; ++rhs) {
       const double* l = lam + rhs * lam_rs;
-      double v = 0.0;
+      double v;
+      if (unit) {
+        const double a = (live & 1) ? l[idx[0]] : 0.0, bv = (live & 8) ? l[idx[3]] : 0.0;
+        v = flip_sign(a, neg & 1) + flip_sign(bv, (neg >> 3) & 1);
+      } else {
+        v = 0.0;
 #pragma unroll
-      for (int k = 0; k < 6; ++k)
-        if (w[k] != 0.0) v = fma(w[k], l[idx[k]], v);
+        for (int k = 0; k < 6; ++k)
+          if ((live >> k) & 1) v = fma(w[k], l[idx[k]], v);
+      }
       double* o = out + rhs * out_rs + (long long)cell * out_cs + j;
-      *o = (beta == 0.0) ? v : v + beta * (*o);
+      *o = overwrite ? v : v + beta * (*o);
     }
   }
 }
 
 // z = alpha B y + beta z, or alpha D B y + beta z when dinfo is given.  One thread per row: the
 // (cell entry, weight) terms -- two signed copies of each of at most three chain rows -- are decoded
-// once, then applied to every RHS.
+// once, then applied to every RHS (a signed FP64 sum for the unscaled rows, as in the gather).
 __global__ void scatter_B_kernel(const int* __restrict__ scat, const double* __restrict__ yd,
                                  long long y_rs, int y_cs, int nd, const int* __restrict__ dinfo,
                                  int d, double* __restrict__ out, long long out_rs, long long L,
                                  double alpha, double beta, int nrhs) {
   const int Li = (int)L;                             // < 2^31, checked by the host
+  const bool overwrite = beta == 0.0, unscaled = alpha == 1.0;
   for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < Li; row += gridDim.x * blockDim.x) {
     const int code = dinfo ? dinfo[row] : 0;
     const int n = code >> 8, q = code & 0xff;
-    // at most three chain rows with two signed entries each: six terms in registers
     long long idx[6];
     double w[6];
+    int live = 0, neg = 0;
 #pragma unroll
     for (int k = 0; k < 6; ++k) { idx[k] = 0; w[k] = 0.0; }
 #pragma unroll
@@ -105,18 +135,28 @@ __global__ void scatter_B_kernel(const int* __restrict__ scat, const double* __r
         if (c == 0) continue;
         const int e = (c > 0 ? c : -c) - 1;
         const int cell = e / nd;
-        idx[2 * b + h] = (long long)cell * y_cs + (e - cell * nd);
-        w[2 * b + h] = c > 0 ? wr : -wr;
+        const int k = 2 * b + h;
+        idx[k] = (long long)cell * y_cs + (e - cell * nd);
+        w[k] = c > 0 ? wr : -wr;
+        live |= 1 << k;
+        neg |= (c < 0 ? 1 : 0) << k;
       }
     }
     for (int rhs = 0; rhs < nrhs; ++rhs) {
       const double* y = yd + rhs * y_rs;
-      double v = 0.0;
+      double v;
+      if (n == 0) {   // weights +-1
+        const double a = (live & 1) ? y[idx[0]] : 0.0, bv = (live & 2) ? y[idx[1]] : 0.0;
+        v = flip_sign(a, neg & 1) + flip_sign(bv, (neg >> 1) & 1);
+      } else {
+        v = 0.0;
 #pragma unroll
-      for (int k = 0; k < 6; ++k)
-        if (w[k] != 0.0) v = fma(w[k], y[idx[k]], v);
+        for (int k = 0; k < 6; ++k)
+          if ((live >> k) & 1) v = fma(w[k], y[idx[k]], v);
+      }
       double* o = out + rhs * out_rs + row;
-      *o = (beta == 0.0) ? alpha * v : alpha * v + beta * (*o);
+      const double av = unscaled ? v : alpha * v;
+      *o = overwrite ? av : av + beta * (*o);
     }
   }
 }

@@ -179,6 +179,7 @@ struct TcParams {
   int* err;
   unsigned long long wait_ns;          // bound of every pipeline wait
   long long a_bytes, b_bytes, y_ext;   // extents for checked builds
+  int batch, bgroup;                   // operators, and operators per L2-resident group
 };
 
 namespace {
@@ -196,7 +197,21 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(TcParams P) {
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nt = blockIdx.x, mt = blockIdx.y, bz = blockIdx.z;
+  // CTA order: groups of bgroup operators; within a group the column tile is the slowest index, so
+  // consecutive CTAs share one B tile (read from DRAM once per group) while the group's A tiles
+  // stay resident in L2 across the column tiles
+  int nt, mt, bz;
+  {
+    const long long bid = blockIdx.x;
+    const long long per_group = (long long)P.n_tiles * P.m_tiles * P.bgroup;
+    const int g = (int)(bid / per_group);
+    const long long r = bid - (long long)g * per_group;
+    const int gb = min(P.bgroup, P.batch - g * P.bgroup);
+    nt = (int)(r / ((long long)P.m_tiles * gb));
+    const int r2 = (int)(r - (long long)nt * P.m_tiles * gb);
+    bz = g * P.bgroup + r2 / P.m_tiles;
+    mt = r2 - (r2 / P.m_tiles) * P.m_tiles;
+  }
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -449,8 +464,12 @@ template <int BN, int STAGES>
 fetidp_status launch_tc(Ctx& c, const TcParams& P, int batch) {
   const size_t smem = tc_smem_bytes<BN, STAGES>();
   cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  dim3 grid((unsigned)P.n_tiles, (unsigned)P.m_tiles, (unsigned)batch);
-  tc_gemm_kernel<BN, STAGES><<<grid, 128, smem, c.stream>>>(P);
+  const long long nblk = (long long)P.n_tiles * P.m_tiles * batch;
+  if (nblk >= (1LL << 31) || P.batch != batch || P.bgroup < 1) {
+    set_error("tensor-core GEMM: grid too large");
+    return FETIDP_EINVAL;
+  }
+  tc_gemm_kernel<BN, STAGES><<<(unsigned)nblk, 128, smem, c.stream>>>(P);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }
@@ -884,6 +903,9 @@ fetidp_status tc_apply(Ctx& c, const TcOperator& op, CCellVec X, const double* c
   P.a_bytes = (long long)batch * op.batch_bytes;
   P.b_bytes = (long long)c.tc_bbuf_bytes;
   P.y_ext = y_ext;
+  P.batch = batch;
+  // operators per group: their A tiles (batch_bytes each) within about 48 MB of the 129 MB L2
+  P.bgroup = (int)std::max<long long>(1, std::min<long long>(batch, (48LL << 20) / std::max<long long>(1, op.batch_bytes)));
   // algorithmic flops: one M x K product per operator and column (no padding, no split products)
   const double flops = 2.0 * op.M * (double)op.K * op.nops * (double)ncols;
   ProfScope ps(c, FETIDP_K_TC_GEMM, flops,
