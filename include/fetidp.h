@@ -148,7 +148,10 @@ typedef struct {
                                cell's F_dd_ring and S_dd_ring assembled once in FP32 and streamed
                                (4 n_d^2 bytes per cell per application, shared by the RHS);
                                0 = principal form on the tensor cores (2 N_rb n_d^2 flops per
-                               column); -1 = assembled when n_d > 128, i.e. for 3D cells (-1)  */
+                               column); 2 = assembled in FP32 as packed upper-triangle 32 x 32
+                               tiles, each read once and used for both triangles (about half
+                               the memory of 1; n_d <= 640); -1 = 1 when n_d > 128, i.e. for 3D
+                               cells, else 0 (-1)                                              */
   int interface;            /* interface sub-preconditioner of Algorithm 1 (Sec. 3.2.3): 0 = PCG on
                                F_ring (Eq. 48) preconditioned by M_D_ring (Eq. 49); 1 = one
                                application of M_D^{-ROM} (Eq. 47), the Dirichlet preconditioner

@@ -272,7 +272,8 @@ struct Ctx {
   // mixed path, large cells: the same operators assembled in FP32, rows padded to ld_f (16 bytes)
   float* Fdd_f = nullptr;     // [N][nd][ld_f]
   float* Sdd_f = nullptr;     // [N][nd][ld_f]
-  int ld_f = 0;
+  int ld_f = 0;                // 0: packed symmetric tiles (sym_T tile rows of 32), else dense row stride
+  int sym_T = 0;
   bool asm_f32 = false;
   bool exact = false;         // standard FETI-DP: every cell's own K_rr^{-1} (nrb = N, no ROM)
   float* Udp_f = nullptr;     // [N][nd][np] mixed path: the dual rows of U_rp_ring in FP32
@@ -438,7 +439,8 @@ fetidp_status k_batched_diag_sum(Ctx& c, const double* A, long long stride, int 
 fetidp_status k_apply_K(Ctx& c, CCellVec u, CellVec y, int nvec_per_col, int ncols, bool idp,
                         bool r_only, const double* chat, double chat_scale_dr, int len_override = 0);
 fetidp_status k_rom_combine_f32(Ctx& c, const double* src, long long kstride, int ld, int r0, int c0, int rows,
-                                int cols, const double* coef, float* out, int ldo);
+                                int cols, const double* coef, float* out, int ldo, int symT = 0);
+fetidp_status k_cell_symv_f32(Ctx& c, const float* mats, CCellVec x, CellVec y, double alpha, double beta, int nrhs);
 fetidp_status k_cell_gemm_f32(Ctx& c, const float* mats, int ldm, int rows, int cols, CCellVec x, CellVec y,
                               double alpha, double beta, int nrhs);
 fetidp_status k_cell_gemv_strided(Ctx& c, const double* mats, long long mstride, int ld, int mrows,

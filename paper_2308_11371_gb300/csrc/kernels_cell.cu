@@ -451,44 +451,63 @@ __global__ void __launch_bounds__(256) krr_spmm_f32_kernel(const int* __restrict
 
 // The same product for the nodal pattern of K_rr (every node's D rows share their neighbour
 // nodes): one thread per node, so each 16-byte shared read of a neighbour component's vectors feeds
-// D rows (3 D FMA per read in 3D instead of 4), and the warp's lanes read consecutive nodes'
-// neighbours (regular, conflict-free addresses).  The stored values stay cached for the other
-// (rhs, chunk) blocks of the cell.
+// D rows, and the warp's lanes read consecutive nodes' neighbours (regular, conflict-free
+// addresses).  The D slots of neighbour k (D * n_r values, shared by the cell's (rhs, chunk)
+// blocks through L2) are staged in shared memory by cp.async one neighbour ahead.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
 template <int D>
 __global__ void __launch_bounds__(352, 2) krr_spmm_nodal_f32_kernel(
     const int* __restrict__ nbr, const float* __restrict__ eval, int nnz, int nr, int nrhs, int nchunk,
     const float* __restrict__ u, long long u_rs, int u_cs, float* __restrict__ y, long long y_rs, int y_cs, int nvec,
     long long ext) {
-  extern __shared__ __align__(16) float uss[];   // [nr][kSpLd]
+  extern __shared__ __align__(16) float uss[];   // [nr][kSpLd], then two slot buffers [D * nr]
+  float* evs = uss + (size_t)nr * kSpLd;
   const int chunk = (int)(blockIdx.x % nchunk);
   const long long rest = blockIdx.x / nchunk;
   const int rhs = (int)(rest % nrhs);
   const long long cell = rest / nrhs;
   const int v0 = chunk * kSpVB, vb = min(kSpVB, nvec - v0);
   const long long base = rhs * u_rs + cell * u_cs;
+  const int nnode = nr / D, nk = nnz / D, sl = D * nr;
+  const float* ev = eval + cell * (long long)nnz * nr;
+  for (int t = threadIdx.x; t < sl; t += blockDim.x) cp_async4(evs + t, ev + t);   // neighbour 0
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
   for (int t = threadIdx.x; t < kSpVB * nr; t += blockDim.x) {
     const int v = t / nr, q = t - v * nr;
     float x = 0.f;
     if (v < vb && FD_INB(base + (long long)(v0 + v) * nr + q, ext, 207)) x = u[base + (long long)(v0 + v) * nr + q];
     uss[q * kSpLd + v] = x;
   }
-  __syncthreads();
-  const int nnode = nr / D, nk = nnz / D;
-  const float* ev = eval + cell * (long long)nnz * nr;
   const long long ybase = rhs * y_rs + cell * y_cs;
-  for (int n = threadIdx.x; n < nnode; n += blockDim.x) {
-    float acc[D][kSpVB];
+  const int n = threadIdx.x;                      // one node per thread (the host launches >= nnode threads)
+  const bool live = n < nnode;
+  float acc[D][kSpVB];
 #pragma unroll
-    for (int a = 0; a < D; ++a)
+  for (int a = 0; a < D; ++a)
 #pragma unroll
-      for (int v = 0; v < kSpVB; ++v) acc[a][v] = 0.f;
-    for (int k = 0; k < nk; ++k) {
-      const int m = __ldg(nbr + (long long)k * nnode + n);
+    for (int v = 0; v < kSpVB; ++v) acc[a][v] = 0.f;
+  int m_next = live ? __ldg(nbr + n) : 0;
+  for (int k = 0; k < nk; ++k) {
+    if (k + 1 < nk) {
+      const float* src = ev + (long long)(k + 1) * sl;
+      float* dst = evs + ((k + 1) & 1) * sl;
+      for (int t = threadIdx.x; t < sl; t += blockDim.x) cp_async4(dst + t, src + t);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    __syncthreads();                              // neighbour k's slots (and the vectors) are in place
+    const int m = m_next;
+    if (live && k + 1 < nk) m_next = __ldg(nbr + (long long)(k + 1) * nnode + n);
+    if (live) {
+      const float* e = evs + (k & 1) * sl;
 #pragma unroll
       for (int cq = 0; cq < D; ++cq) {
         float av[D];
 #pragma unroll
-        for (int a = 0; a < D; ++a) av[a] = __ldg(ev + (long long)(D * k + cq) * nr + D * n + a);
+        for (int a = 0; a < D; ++a) av[a] = e[cq * nr + D * n + a];
         const float4* xs = reinterpret_cast<const float4*>(uss + (D * m + cq) * kSpLd);
 #pragma unroll
         for (int v4 = 0; v4 < kSpVB / 4; ++v4) {
@@ -503,14 +522,16 @@ __global__ void __launch_bounds__(352, 2) krr_spmm_nodal_f32_kernel(
         }
       }
     }
-#pragma unroll
-    for (int v = 0; v < kSpVB; ++v)
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        const long long o = ybase + (long long)(v0 + v) * nr + D * n + a;
-        if (v < vb && FD_INB(o, ext, 208)) y[o] = acc[a][v];
-      }
+    __syncthreads();                              // buffer k & 1 is refilled at step k + 1
   }
+  if (!live) return;
+#pragma unroll
+  for (int v = 0; v < kSpVB; ++v)
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const long long o = ybase + (long long)(v0 + v) * nr + D * n + a;
+      if (v < vb && FD_INB(o, ext, 208)) y[o] = acc[a][v];
+    }
 }
 
 // Per-cell dense operators: y[rhs,cell] = alpha M_cell x[rhs,cell] + beta y, M_cell at
@@ -627,16 +648,29 @@ __global__ void cell_gemv_narrow_kernel(const double* __restrict__ mats, long lo
 // A thread owns one entry (r, c): its NRBM principal values sit in registers and are reused for
 // kCombCells cells, whose coefficients are staged in shared memory (FP32 arithmetic).
 constexpr int kCombCells = 32;
+// symT > 0: the output is the packed symmetric tile form (upper-triangle 32 x 32 tiles of a
+// symT x symT tile grid, sym_tile_offset) and entries below the diagonal tiles are not written.
+__host__ __device__ inline long long sym_tile_index(int I, int J, int T) {
+  return (long long)I * T - (long long)I * (I - 1) / 2 + (J - I);
+}
+// element (r, c) of a 32 x 32 tile: quad c / 4 of row r at float4 slot 32 (c / 4) + r, so a warp
+// whose lane r loads quad k reads 512 contiguous bytes
+__host__ __device__ inline int sym_in_tile(int r, int c) { return (((c >> 2) * 32 + r) << 2) + (c & 3); }
 template <int NRBM>
 __global__ void __launch_bounds__(256) rom_combine_f32_kernel(const double* __restrict__ src, long long kstride,
                                                               int ld, int r0, int c0, int rows, int cols,
                                                               const double* __restrict__ coef, int nrb,
-                                                              long long ncell, float* __restrict__ out, int ldo) {
+                                                              long long ncell, float* __restrict__ out, int ldo,
+                                                              int symT) {
   __shared__ float cs[kCombCells][NRBM];
   const long long per = (long long)rows * cols;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const bool live = t < per;
-  const int r = live ? (int)(t / cols) : 0, cc = live ? (int)(t - (long long)r * cols) : 0;
+  const int r_ = t < per ? (int)(t / cols) : 0, c_ = t < per ? (int)(t - (long long)r_ * cols) : 0;
+  const bool live = t < per && (symT == 0 || (r_ >> 5) <= (c_ >> 5));
+  const int r = r_, cc = c_;
+  const long long cell_stride = symT ? 1024LL * symT * (symT + 1) / 2 : (long long)rows * ldo;
+  const long long eoff = symT ? 1024LL * sym_tile_index(r >> 5, cc >> 5, symT) + sym_in_tile(r & 31, cc & 31)
+                              : (long long)r * ldo + cc;
   float p[NRBM];
 #pragma unroll
   for (int k = 0; k < NRBM; ++k)
@@ -654,7 +688,7 @@ __global__ void __launch_bounds__(256) rom_combine_f32_kernel(const double* __re
       float acc = 0.f;
 #pragma unroll
       for (int k = 0; k < NRBM; ++k) acc = fmaf(cs[ci][k], p[k], acc);
-      out[(cell0 + ci) * (long long)rows * ldo + (long long)r * ldo + cc] = acc;
+      out[(cell0 + ci) * cell_stride + eoff] = acc;
     }
   }
 }
@@ -722,6 +756,145 @@ __global__ void __launch_bounds__(kAsmMaxThreads) cell_gemm_f32_kernel(const flo
           *dst = (beta == 0.0) ? alpha * (double)acc[a][q] : alpha * (double)acc[a][q] + beta * (*dst);
         }
       }
+    }
+  }
+}
+
+// y = alpha M x + beta y for the SYMMETRIC per-cell operators stored as packed upper-triangle tiles
+// (32 x 32, T tile rows, sym_in_tile layout): every stored tile (I, J), I < J, is read from memory
+// once and used twice, y_I += M_IJ x_J and y_J += M_IJ^T x_I; a diagonal tile gives y_I += M_II x_I.
+// One CTA per cell with T'/2 warps (T' = T rounded up to even).  The off-diagonal tiles are visited
+// in the T' - 1 rounds of the circle schedule -- in each round the warps hold disjoint block pairs,
+// so every y block has one writer per round and the summation order is fixed (deterministic, no
+// atomics) -- then the diagonal tiles.  A warp loads its tile with lane r owning row r (eight
+// 16-byte loads of 512 contiguous bytes) and the next round's tile while it computes; the column
+// products read the tile transposed through a 32 x 33 shared buffer.  x and y are staged in
+// shared memory in FP32 ([row][8] and [row][9]), up to eight RHS at a time.
+__device__ __forceinline__ bool sym_round_pair(int round, int w, int Tp, int T, int& I, int& J) {
+  int a, b;
+  if (w == 0) {
+    a = round;
+    b = Tp - 1;
+  } else {
+    a = (round + w) % (Tp - 1);
+    b = (round - w + (Tp - 1)) % (Tp - 1);
+  }
+  I = min(a, b);
+  J = max(a, b);
+  return J < T;                                   // block T of an odd T is the empty pad block
+}
+__global__ void __launch_bounds__(320, 2) cell_symv_f32_kernel(const float* __restrict__ mats, int T, int n,
+                                                               const double* __restrict__ x, long long x_rs,
+                                                               int x_cs, double* __restrict__ y, long long y_rs,
+                                                               int y_cs, double alpha, double beta, int nrhs) {
+  extern __shared__ __align__(16) float symsm[];
+  const int NP = T * 32;
+  float* xs = symsm;                              // [NP][8]
+  float* ys = xs + (size_t)NP * 8;                // [NP][9]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  float* tb = ys + (size_t)NP * 9 + (size_t)warp * 32 * 33;
+  const int Tp = (T + 1) & ~1;
+  const long long cell = blockIdx.x;
+  const float4* Mc = reinterpret_cast<const float4*>(mats + cell * 1024LL * T * (T + 1) / 2);
+  const int nrounds = Tp - 1;
+  for (int rb0 = 0; rb0 < nrhs; rb0 += 8) {
+    const int rb = min(8, nrhs - rb0);
+    __syncthreads();
+    for (int t = tid; t < NP * 8; t += blockDim.x) {
+      const int q = t / NP, j = t - q * NP;
+      xs[j * 8 + q] = (q < rb && j < n) ? (float)x[(rb0 + q) * x_rs + cell * x_cs + j] : 0.f;
+    }
+    for (int t = tid; t < NP * 9; t += blockDim.x) ys[t] = 0.f;
+    __syncthreads();
+    // rounds 0 .. nrounds-1: off-diagonal pairs; round nrounds + s: diagonal tiles w + s * nw
+    int I, J;
+    bool have = nrounds > 0 ? sym_round_pair(0, warp, Tp, T, I, J) : false;
+    float4 m[8];
+    if (have)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) m[k] = __ldcs(Mc + sym_tile_index(I, J, T) * 256 + k * 32 + lane);
+    const int ndiag_steps = (T + nw - 1) / nw;
+    for (int step = 0; step < nrounds + ndiag_steps; ++step) {
+      // the next step's tile, loaded before this one is used
+      int In = 0, Jn = 0;
+      bool have_n = false;
+      if (step + 1 < nrounds) have_n = sym_round_pair(step + 1, warp, Tp, T, In, Jn);
+      else if (step + 1 < nrounds + ndiag_steps) {
+        In = Jn = warp + (step + 1 - nrounds) * nw;
+        have_n = In < T;
+      }
+      float4 mn[8];
+      if (have_n)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) mn[k] = __ldcs(Mc + sym_tile_index(In, Jn, T) * 256 + k * 32 + lane);
+      if (have) {
+        // y_I[lane] += sum_c M[lane][c] x_J[c]
+        float ar[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const float4* xJ = reinterpret_cast<const float4*>(xs + (size_t)J * 32 * 8);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const float mv[4] = {m[k].x, m[k].y, m[k].z, m[k].w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float4 x0 = xJ[(4 * k + e) * 2], x1 = xJ[(4 * k + e) * 2 + 1];
+            ar[0] = fmaf(mv[e], x0.x, ar[0]);
+            ar[1] = fmaf(mv[e], x0.y, ar[1]);
+            ar[2] = fmaf(mv[e], x0.z, ar[2]);
+            ar[3] = fmaf(mv[e], x0.w, ar[3]);
+            ar[4] = fmaf(mv[e], x1.x, ar[4]);
+            ar[5] = fmaf(mv[e], x1.y, ar[5]);
+            ar[6] = fmaf(mv[e], x1.z, ar[6]);
+            ar[7] = fmaf(mv[e], x1.w, ar[7]);
+          }
+        }
+        float* yI = ys + (size_t)(I * 32 + lane) * 9;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) yI[q] += ar[q];
+        if (I != J) {
+          // y_J[lane] += sum_r M[r][lane] x_I[r], column lane of the tile through the buffer
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            tb[lane * 33 + 4 * k] = m[k].x;
+            tb[lane * 33 + 4 * k + 1] = m[k].y;
+            tb[lane * 33 + 4 * k + 2] = m[k].z;
+            tb[lane * 33 + 4 * k + 3] = m[k].w;
+          }
+          __syncwarp();
+          float ac[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          const float4* xI = reinterpret_cast<const float4*>(xs + (size_t)I * 32 * 8);
+#pragma unroll 8
+          for (int r = 0; r < 32; ++r) {
+            const float tv = tb[r * 33 + lane];
+            const float4 x0 = xI[r * 2], x1 = xI[r * 2 + 1];
+            ac[0] = fmaf(tv, x0.x, ac[0]);
+            ac[1] = fmaf(tv, x0.y, ac[1]);
+            ac[2] = fmaf(tv, x0.z, ac[2]);
+            ac[3] = fmaf(tv, x0.w, ac[3]);
+            ac[4] = fmaf(tv, x1.x, ac[4]);
+            ac[5] = fmaf(tv, x1.y, ac[5]);
+            ac[6] = fmaf(tv, x1.z, ac[6]);
+            ac[7] = fmaf(tv, x1.w, ac[7]);
+          }
+          __syncwarp();                           // the buffer is rewritten by the next tile
+          float* yJ = ys + (size_t)(J * 32 + lane) * 9;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) yJ[q] += ac[q];
+        }
+      }
+      __syncthreads();                            // this round's y blocks are complete
+      have = have_n;
+      I = In;
+      J = Jn;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) m[k] = mn[k];
+    }
+    const bool plain = alpha == 1.0, overwrite = beta == 0.0;
+    for (int t = tid; t < n * 8; t += blockDim.x) {
+      const int q = t / n, r = t - q * n;
+      if (q >= rb) continue;
+      double* dst = y + (rb0 + q) * y_rs + cell * y_cs + r;
+      const double v = plain ? (double)ys[r * 9 + q] : alpha * (double)ys[r * 9 + q];
+      *dst = overwrite ? v : v + beta * (*dst);
     }
   }
 }
@@ -1051,8 +1224,11 @@ __device__ void block_pivoted_gram_solve(double* S, double* Lc, const double* hs
                                          double* colv, int* piv, double* sh_inv, int* sh_jb, int nrb, int ld,
                                          double drop_rel, int tid, int nthreads) {
   const int lane = tid & 31, warp = tid >> 5;
-  double dmax = 0.0;
-  for (int i = 0; i < nrb; ++i) dmax = fmax(dmax, S[i * ld + i]);
+  double dmax = 0.0;                                 // needed by warp 0 only
+  if (warp == 0) {
+    for (int i = lane; i < nrb; i += 32) dmax = fmax(dmax, S[i * ld + i]);
+    for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+  }
   unsigned long long used = 0ull;                   // identical in every thread
   int np = 0;
   while (np < nrb) {
@@ -1086,9 +1262,9 @@ __device__ void block_pivoted_gram_solve(double* S, double* Lc, const double* hs
       Lc[np * ld + i] = cv;
     }
     __syncthreads();
-    for (int t = tid; t < nrb * nrb; t += nthreads) {
-      const int i = t / nrb, j = t - i * nrb;
-      if (i > j || ((used >> i) & 1ull) || ((used >> j) & 1ull)) continue;
+    for (int t = tid; t < 64 * 64; t += nthreads) {   // nrb <= 64
+      const int i = t >> 6, j = t & 63;
+      if (j >= nrb || i > j || ((used >> i) & 1ull) || ((used >> j) & 1ull)) continue;
       S[i * ld + j] -= colv[i] * colv[j];
     }
     ++np;
@@ -1234,10 +1410,14 @@ __global__ void __launch_bounds__(256, 3) gram_block_f32_kernel(const float* __r
   __syncthreads();
   block_pivoted_gram_solve(S, Lc, hs, ys, cs, colv, piv, sh_inv, sh_jb, nrb, ld, drop_rel, tid, blockDim.x);
   __syncthreads();
+  float* csf = reinterpret_cast<float*>(ys);         // the coefficients in FP32, converted once
+  if (tid < nrb) csf[tid] = (float)cs[tid];
+  __syncthreads();
   double* xc = x + rhs * x_rs + cell * x_cs;
   for (int q = tid; q < nr; q += blockDim.x) {
     float sx = 0.f;
-    for (int i = 0; i < nrb; ++i) sx += (float)cs[i] * Rc[(size_t)i * nr + q];
+#pragma unroll 8
+    for (int i = 0; i < nrb; ++i) sx = fmaf(csf[i], Rc[(size_t)i * nr + q], sx);
     xc[q] = (double)sx;
   }
 }
@@ -1566,15 +1746,16 @@ fetidp_status k_apply_K_f32(Ctx& c, const float* u, long long u_rs, int u_cs, fl
     ProfScope ps(c, FETIDP_K_MULTI_K, 2.0 * (double)c.N * nrhs * nvec * c.krr_nnz * c.nr,
                  4.0 * (double)c.N * c.krr_nnz * c.nr + 8.0 * (double)c.N * nrhs * nvec * c.nr);
     const int nnode = c.nr / c.d;
-    if (c.krr_nbr && nnode <= 704) {
-      const int threads = std::min(352, (nnode + 31) / 32 * 32);
+    const size_t smem_n = smem + sizeof(float) * 2 * (size_t)c.d * c.nr;
+    if (c.krr_nbr && nnode <= 352 && smem_n <= 113 * 1024) {
+      const int threads = (nnode + 31) / 32 * 32;
       if (c.d == 3) {
-        cudaFuncSetAttribute(krr_spmm_nodal_f32_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        krr_spmm_nodal_f32_kernel<3><<<(unsigned)(c.N * nrhs * nchunk), threads, smem, c.stream>>>(
+        cudaFuncSetAttribute(krr_spmm_nodal_f32_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_n);
+        krr_spmm_nodal_f32_kernel<3><<<(unsigned)(c.N * nrhs * nchunk), threads, smem_n, c.stream>>>(
             c.krr_nbr, c.krr_val, c.krr_nnz, c.nr, nrhs, nchunk, u, u_rs, u_cs, y, y_rs, y_cs, nvec, ext);
       } else {
-        cudaFuncSetAttribute(krr_spmm_nodal_f32_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        krr_spmm_nodal_f32_kernel<2><<<(unsigned)(c.N * nrhs * nchunk), threads, smem, c.stream>>>(
+        cudaFuncSetAttribute(krr_spmm_nodal_f32_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_n);
+        krr_spmm_nodal_f32_kernel<2><<<(unsigned)(c.N * nrhs * nchunk), threads, smem_n, c.stream>>>(
             c.krr_nbr, c.krr_val, c.krr_nnz, c.nr, nrhs, nchunk, u, u_rs, u_cs, y, y_rs, y_cs, nvec, ext);
       }
     } else {
@@ -1638,7 +1819,7 @@ fetidp_status k_apply_K_f32(Ctx& c, const float* u, long long u_rs, int u_cs, fl
 }
 
 fetidp_status k_rom_combine_f32(Ctx& c, const double* src, long long kstride, int ld, int r0, int c0, int rows,
-                                int cols, const double* coef, float* out, int ldo) {
+                                int cols, const double* coef, float* out, int ldo, int symT) {
   if (c.nrb > 64) { set_error("n_rb above 64"); return FETIDP_EINVAL; }
   const long long per = (long long)rows * cols;
   long long gy = (c.N + kCombCells - 1) / kCombCells;
@@ -1646,11 +1827,14 @@ fetidp_status k_rom_combine_f32(Ctx& c, const double* src, long long kstride, in
   const dim3 grid((unsigned)((per + 255) / 256), (unsigned)gy);
   ProfScope ps(c, FETIDP_K_SETUP, 2.0 * c.nrb * per * (double)c.N, 4.0 * per * (double)c.N);
   if (c.nrb <= 16)
-    rom_combine_f32_kernel<16><<<grid, 256, 0, c.stream>>>(src, kstride, ld, r0, c0, rows, cols, coef, c.nrb, c.N, out, ldo);
+    rom_combine_f32_kernel<16><<<grid, 256, 0, c.stream>>>(src, kstride, ld, r0, c0, rows, cols, coef, c.nrb, c.N, out, ldo,
+                                                             symT);
   else if (c.nrb <= 32)
-    rom_combine_f32_kernel<32><<<grid, 256, 0, c.stream>>>(src, kstride, ld, r0, c0, rows, cols, coef, c.nrb, c.N, out, ldo);
+    rom_combine_f32_kernel<32><<<grid, 256, 0, c.stream>>>(src, kstride, ld, r0, c0, rows, cols, coef, c.nrb, c.N, out, ldo,
+                                                             symT);
   else
-    rom_combine_f32_kernel<64><<<grid, 256, 0, c.stream>>>(src, kstride, ld, r0, c0, rows, cols, coef, c.nrb, c.N, out, ldo);
+    rom_combine_f32_kernel<64><<<grid, 256, 0, c.stream>>>(src, kstride, ld, r0, c0, rows, cols, coef, c.nrb, c.N, out, ldo,
+                                                             symT);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }
@@ -1670,6 +1854,26 @@ fetidp_status k_cell_gemm_f32(Ctx& c, const float* mats, int ldm, int rows, int 
   cudaFuncSetAttribute(cell_gemm_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cell_gemm_f32_kernel<<<(unsigned)c.N, threads, smem, c.stream>>>(mats, ldm, rows, cols, x.p, x.rs, x.cs, y.p,
                                                                    y.rs, y.cs, alpha, beta, nrhs);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_cell_symv_f32(Ctx& c, const float* mats, CCellVec x, CellVec y, double alpha, double beta,
+                              int nrhs) {
+  const int T = c.sym_T, n = c.nd;
+  const long long ntile = (long long)T * (T + 1) / 2;
+  // algorithmic bytes: the packed operator once, the FP64 vectors in and out
+  ProfScope ps(c, FETIDP_K_ASM_OP, 2.0 * n * n * (double)c.N * nrhs,
+               4096.0 * ntile * c.N + 8.0 * c.N * (double)nrhs * 2.0 * n);
+  const int nw = (T + 1) / 2;
+  if (T < 1 || n > 32 * T || nw > 10 || (reinterpret_cast<uintptr_t>(mats) & 15) != 0) {
+    set_error("packed FP32 cell operators: at most 20 tile rows");
+    return FETIDP_EINVAL;
+  }
+  const size_t smem = sizeof(float) * ((size_t)T * 32 * 17 + (size_t)nw * 32 * 33);
+  cudaFuncSetAttribute(cell_symv_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cell_symv_f32_kernel<<<(unsigned)c.N, 32 * nw, smem, c.stream>>>(mats, T, n, x.p, x.rs, x.cs, y.p, y.rs, y.cs,
+                                                                   alpha, beta, nrhs);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }

@@ -228,7 +228,7 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
     return FETIDP_EINVAL;
   }
   if (o.wait_budget_ns <= 0) { set_error("wait_budget_ns must be > 0"); return FETIDP_EINVAL; }
-  if (o.mixed_assembled < -1 || o.mixed_assembled > 1) { set_error("mixed_assembled must be -1, 0 or 1"); return FETIDP_EINVAL; }
+  if (o.mixed_assembled < -1 || o.mixed_assembled > 2) { set_error("mixed_assembled must be -1, 0, 1 or 2"); return FETIDP_EINVAL; }
   if (o.interface < 0 || o.interface > 1) { set_error("interface must be 0 or 1"); return FETIDP_EINVAL; }
   if (o.method < 0 || o.method > 1) { set_error("method must be 0 or 1"); return FETIDP_EINVAL; }
   if (o.method == 1 && (o.precision != FETIDP_FP64 || o.interface != 0)) {
@@ -783,14 +783,20 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
     // HBM-bound), principal form on the tensor cores otherwise
     c.asm_f32 = o.mixed_assembled > 0 || (o.mixed_assembled < 0 && nd > 128);
     if (c.asm_f32) {
-      c.ld_f = (nd + 3) & ~3;
-      const size_t fbytes = sizeof(float) * (size_t)c.N * nd * c.ld_f;
+      // dense rows padded to 16 bytes (streamed at the HBM rate), or with mixed_assembled = 2 the
+      // packed upper-triangle 32 x 32 tiles of these symmetric operators (about half the bytes, up to
+      // 20 tile rows; on GB300 that kernel is bound by its shared-memory traffic and is not faster)
+      const int T = (nd + 31) / 32;
+      c.sym_T = (o.mixed_assembled == 2 && T <= 20) ? T : 0;
+      c.ld_f = c.sym_T ? 0 : (nd + 3) & ~3;
+      const size_t fbytes = c.sym_T ? sizeof(float) * (size_t)c.N * 1024 * T * (T + 1) / 2
+                                    : sizeof(float) * (size_t)c.N * nd * c.ld_f;
       FD_TRY(dalloc(c, reinterpret_cast<void**>(&c.Fdd_f), fbytes));
       FD_TRY(dalloc(c, reinterpret_cast<void**>(&c.Sdd_f), fbytes));
-      FD_CUDA(cudaMemsetAsync(c.Fdd_f, 0, fbytes, c.stream));   // row padding stays zero
+      FD_CUDA(cudaMemsetAsync(c.Fdd_f, 0, fbytes, c.stream));   // padding stays zero
       FD_CUDA(cudaMemsetAsync(c.Sdd_f, 0, fbytes, c.stream));
-      FD_TRY(k_rom_combine_f32(c, c.Kinv, (long long)nr * nr, nr, ni, ni, nd, nd, c.delta, c.Fdd_f, c.ld_f));
-      FD_TRY(k_rom_combine_f32(c, c.Sdd, (long long)nd * nd, nd, 0, 0, nd, nd, c.alpha, c.Sdd_f, c.ld_f));
+      FD_TRY(k_rom_combine_f32(c, c.Kinv, (long long)nr * nr, nr, ni, ni, nd, nd, c.delta, c.Fdd_f, c.ld_f, c.sym_T));
+      FD_TRY(k_rom_combine_f32(c, c.Sdd, (long long)nd * nd, nd, 0, 0, nd, nd, c.alpha, c.Sdd_f, c.ld_f, c.sym_T));
     }
     FD_TRY(tc_comb_pack(c, c.cFdd, c.Kinv, (long long)nr * nr, nr, ni, ni, nd, nullptr, 0, 0, 0, 0, 0, nd, nrb,
                         split));

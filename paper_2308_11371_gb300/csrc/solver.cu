@@ -249,7 +249,9 @@ fetidp_status op_apply_F(Ctx& c, const double* lam, long long lam_rs, double* y,
   const int m = c.m, nd = c.nd, np = c.np, nr = c.nr, ni = c.ni;
   CellVec g{c.w_d1, c.N * nd, nd}, yd{c.w_d2, c.N * nd, nd}, cp{c.w_p1, c.N * np, np};
   FD_TRY(k_gather_BT(c, lam, lam_rs, nullptr, g, m, 0.0));
-  if (c.asm_f32)
+  if (c.asm_f32 && c.sym_T)
+    FD_TRY(k_cell_symv_f32(c, c.Fdd_f, cview(g), yd, 1.0, 0.0, m));
+  else if (c.asm_f32)
     FD_TRY(k_cell_gemm_f32(c, c.Fdd_f, c.ld_f, nd, nd, cview(g), yd, 1.0, 0.0, m));
   else if (c.mixed)
     FD_TRY(tc_comb_apply(c, c.cFdd, cview(g), c.delta, c.delta, yd.p, true, yd.rs, yd.cs, 1.0, 0.0, m, c.N));
@@ -281,7 +283,9 @@ fetidp_status op_apply_MD(Ctx& c, const double* r, long long r_rs, double* z, lo
   const int m = c.m, nd = c.nd;
   CellVec g{c.w_d1, c.N * nd, nd}, yd{c.w_d2, c.N * nd, nd};
   FD_TRY(k_gather_BT(c, r, r_rs, c.dinfo, g, m, 0.0));
-  if (c.asm_f32)
+  if (c.asm_f32 && c.sym_T)
+    FD_TRY(k_cell_symv_f32(c, c.Sdd_f, cview(g), yd, 1.0, 0.0, m));
+  else if (c.asm_f32)
     FD_TRY(k_cell_gemm_f32(c, c.Sdd_f, c.ld_f, nd, nd, cview(g), yd, 1.0, 0.0, m));
   else if (c.mixed)
     FD_TRY(tc_comb_apply(c, c.cSdd, cview(g), c.alpha, c.alpha, yd.p, true, yd.rs, yd.cs, 1.0, 0.0, m, c.N));

@@ -145,3 +145,29 @@ def test_mixed_config2_matches_monolithic_full_size():
         assert np.abs(res - f).max() < 1e-6 * np.abs(Kc @ uloc).max()
     ref = monolithic.to_cells(lat, monolithic.solve(lat))[0]
     assert _rel(uh, ref) < 1e-7
+
+
+@pytest.mark.parametrize("name", ["cfg1", "ragged2d", "bcc3d"])
+def test_mixed_assembled_and_principal_forms(name):
+    """F_dd_ring and S_dd_ring applied in every mixed form -- the principal form on the tensor cores
+    (three BF16 products), assembled per cell in FP32 with dense rows, and assembled as packed
+    symmetric tiles read once per application -- agree with the FP64 oracle within the split's
+    bound on 2D cells (one or two tile rows), on 3^3 cells (five tile rows, an odd count) and with
+    each other."""
+    prob, lat, fe = oracle(name)
+    rng = np.random.default_rng(37)
+    out = {}
+    for form in (0, 1, 2):
+        s = _mixed(prob, tc_split=3, mixed_assembled=form)
+        lam = rng.standard_normal((s.n_rhs, s.L)) if not out else out["lam"]
+        out["lam"] = lam
+        out[form] = (_host(s.apply_F(_dev(lam))), _host(s.precond(_dev(lam))))
+        s.close()
+    lam = out["lam"]
+    for r in range(prob.n_rhs):
+        yF, yM = fe.apply_F(lam[r]), fe.apply_MD(lam[r])
+        for form in (0, 1, 2):
+            assert _rel(out[form][0][r], yF) < 3e-4
+            assert _rel(out[form][1][r], yM) < 3e-4
+        assert _rel(out[1][0][r], out[0][0][r]) < 3e-4
+        assert _rel(out[2][0][r], out[1][0][r]) < 1e-5 and _rel(out[2][1][r], out[1][1][r]) < 1e-5
