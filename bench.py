@@ -463,7 +463,9 @@ def main():
             dof2 = p2.n_cells * 578 * p2.n_rhs
             secondary = {"workload": WORKLOADS["cfg2"]["label"], "n_rb": i2["n_rb"], "ms_per_step": ms2,
                          "value": dof2 / (ms2 / 1e3), "unit": UNIT, "outer_its": i2["outer_its"],
-                         "inner_its_total": i2["inner_its_total"], "rel_residual": i2["rel_residual"]}
+                         "inner_its_total": i2["inner_its_total"], "rel_residual": i2["rel_residual"],
+                         "solve_kernel_launches": i2["kernel_launches"], "solve_host_launches": i2["host_launches"],
+                         "inner_pcg_graph": bool(i2["inner_graph"])}
         except Exception as exc:
             secondary = {"error": str(exc)[:300]}
 
@@ -485,6 +487,9 @@ def main():
             "t_setup_ms": 1e3 * statistics.median(i["t_setup_s"] for i in infos),
             "t_solve_ms": 1e3 * statistics.median(i["t_solve_s"] for i in infos),
             "device_bytes": infos[-1]["device_bytes"],
+            "solve_kernel_launches": infos[-1]["kernel_launches"],
+            "solve_host_launches": infos[-1]["host_launches"],
+            "inner_pcg_graph": bool(infos[-1]["inner_graph"]),
             "parallelism": f"replicas x{world}",
             "fp64_path": fp64_ref,
             "speedup_vs_fp64": (fp64_ref["ms"] / step_ms) if fp64_ref and "ms" in fp64_ref else None,

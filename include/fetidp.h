@@ -134,10 +134,12 @@ typedef struct {
                                n_tot x n_rhs x 8 bytes).  After a cycle the true residual is
                                recomputed and a new cycle starts from the current iterate.
                                0 = min(max_outer, 30) (0); fixed_outer > restart raises it    */
-  long long wait_budget_ns; /* bound of every device-side wait of the tensor-core kernels, in
-                               ns of the GPU's global timer (1e9).  On expiry the kernel stops,
-                               lets its own copies and MMAs finish (a separate fixed 1 s bound),
-                               frees its tensor memory and returns; the call reports
+  long long wait_budget_ns; /* bound of every device-side wait of the tensor-core kernels and
+                               of the grid barriers of the mixed path's one-launch coarse solve,
+                               in ns of the GPU's global timer (1e9).  On expiry a tensor-core
+                               kernel stops, lets its own copies and MMAs finish (a separate
+                               fixed 1 s bound), frees its tensor memory and returns; a coarse
+                               solve runs its remaining levels without waiting; the call reports
                                FETIDP_ETIMEOUT and the context stays usable.  Must be > 0     */
   int check_inputs;         /* 1: entry points that take input vectors (all but fetidp_solve)
                                check them for NaN/Inf first (FETIDP_EINVAL) and, in the mixed
@@ -174,6 +176,11 @@ typedef struct {
                                min over lattices of ||b_lattice||, which bounds the worst lattice) */
   double t_setup_s, t_solve_s;
   size_t device_bytes;      /* device workspace held by the context */
+  long long kernel_launches;   /* kernels of this library run by the solve (graph replays included;
+                                  a process-wide counter, so concurrent calls on other contexts
+                                  are counted too) */
+  long long host_launches;     /* launch calls the host issued for them (a graph replay is one) */
+  int inner_graph;             /* 1: the inner PCG iterations ran as a captured CUDA graph */
 } fetidp_info;
 
 /* Sizes of a context: out[0..11] = N cells, n_dof, n_i, n_d, n_p, n_r per cell,

@@ -74,7 +74,8 @@ class Info(ctypes.Structure):
     _fields_ = [("outer_its", ctypes.c_int), ("inner_its_total", ctypes.c_int),
                 ("n_rb", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("t_setup_s", ctypes.c_double), ("t_solve_s", ctypes.c_double),
-                ("device_bytes", ctypes.c_size_t)]
+                ("device_bytes", ctypes.c_size_t), ("kernel_launches", ctypes.c_longlong),
+                ("host_launches", ctypes.c_longlong), ("inner_graph", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

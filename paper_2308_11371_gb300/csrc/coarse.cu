@@ -176,24 +176,67 @@ __global__ void bcr_final_kernel(const double* __restrict__ Ainv, int b, const d
   }
 }
 
-// ---- FP32 copy for the mixed path's inner iterations.  The level vectors hold up to eight RHS
-//      interleaved ([chunk][vec_len][8] floats), so one lane reads all RHS of a column as two
-//      16-byte loads; a warp computes four output rows, each lane summing every 32nd column of
-//      them in FP32, and the 32 (row, RHS) lane partials are reduced by halving exchanges.
-struct BcrLevelF {
-  int b, n, nch;
-  long long rs;                 // per-chunk stride of the level vectors, in 8-float entries
+// ---- FP32 copy for the mixed path's inner iterations: the whole solve is one cooperative launch.
+//      The level vectors hold up to eight RHS interleaved ([chunk][vec_len][8] floats), so one lane
+//      reads all RHS of a column as two 16-byte loads; a warp forms four output rows, each lane
+//      summing every 32nd column of them in FP32, and the 32 (row, RHS) lane partials are summed by
+//      halving exchanges.  The levels are separated by grid-wide barriers whose waits are bounded.
+constexpr int kBcrMaxLevels = 24;
+struct BcrCoopF {
+  int b, L, nch, nrhs;
+  long long rs;                         // per-chunk stride of the level vectors, in 8-float entries
+  long long len0;                       // nb * b
   const float* mats;
-  const long long* offA;
-  const long long* offU;
-  const long long* offUT;
-  const long long* offV;
-  const long long* offVT;
-  float* bl_l;
-  float* bl_n;
-  float* xl_l;
-  const float* xl_n;
+  const long long* tables;              // per level: A, U, UT, V, VT offset arrays of n_at[l] entries
+  long long off_final;
+  int n_at[kBcrMaxLevels + 1];
+  long long vec_off[kBcrMaxLevels + 1];
+  long long tab_off[kBcrMaxLevels];
+  float* bl;
+  float* xl;
+  const int* perm;
+  const double* bin;
+  long long b_rs;
+  double* xout;
+  long long x_rs;
+  unsigned* bar;                        // [0] arrivals, [1] generation (arrivals zeroed before launch)
+  int* err;
+  unsigned long long wait_ns;
 };
+
+__device__ __forceinline__ unsigned long long bcr_gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier for a cooperative launch.  The last block to arrive resets the arrival count
+// and advances the generation; the others spin on the generation until the kernel's deadline, after
+// which they record error 7 and go on (every later wait then ends at once, so the kernel finishes).
+__device__ __forceinline__ void bcr_grid_sync(unsigned* bar, unsigned nblocks, unsigned long long deadline,
+                                              int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      while (*gen == g) {
+        if (bcr_gtime() > deadline) {
+          atomicExch(err, 7);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
 
 // acc[a][r] += sgn * sum_q M[(row0 + a) b + q] v[q][r] over this lane's columns q (every 32nd),
 // for the rows row0 + a < b.  One pair of 16-byte reads of v serves the four rows.
@@ -235,107 +278,100 @@ __device__ __forceinline__ float bcr_warp_reduce32(float acc[4][8], int lane) {
   return v[0];
 }
 
-// one warp per four rows of a new block: bl[l+1][i/2] = bl[l][i] - U_{i-1}^T bl[l][i-1] - V_{i+1}^T bl[l][i+1]
-__global__ void bcr_forward_f32_kernel(BcrLevelF P) {
-  const int lane = threadIdx.x & 31;
-  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int n_new = (P.n + 1) / 2, b = P.b, g4 = (b + 3) / 4;
-  if (gw >= (long long)n_new * g4) return;
-  const int inew = (int)(gw / g4), row0 = 4 * (int)(gw - (long long)inew * g4);
-  const int i = 2 * inew;
-  const int a = lane >> 3, r = lane & 7;
-  for (int ch = 0; ch < P.nch; ++ch) {
-    const float* vl = P.bl_l + (size_t)ch * P.rs * 8;
-    float acc[4][8];
+__device__ __forceinline__ void bcr_zero(float acc[4][8]) {
 #pragma unroll
-    for (int x = 0; x < 4; ++x)
+  for (int x = 0; x < 4; ++x)
 #pragma unroll
-      for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
-    if (i - 1 >= 0 && P.offUT[i - 1] >= 0)
-      bcr_rows4_f32(P.mats + P.offUT[i - 1], row0, vl + (size_t)(i - 1) * b * 8, b, lane, 1.f, acc);
-    if (i + 1 < P.n) bcr_rows4_f32(P.mats + P.offVT[i + 1], row0, vl + (size_t)(i + 1) * b * 8, b, lane, 1.f, acc);
-    const float s = bcr_warp_reduce32(acc, lane);
-    if (row0 + a < b) {
-      const size_t o = ((size_t)(row0 + a)) * 8 + r;
-      P.bl_n[(size_t)ch * P.rs * 8 + (size_t)inew * b * 8 + o] = vl[(size_t)i * b * 8 + o] - s;
-    }
-  }
+    for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
 }
 
-// one warp per four rows: x[l][j] = Ainv_j bl[l][j] - V_j x[l][j-1] - U_j x[l][j+1] (odd j),
-// x[l][j] = x[l+1][j/2] (even j)
-__global__ void bcr_backward_f32_kernel(BcrLevelF P) {
+__global__ void __launch_bounds__(256) bcr_coop_f32_kernel(BcrCoopF P) {
+  const unsigned long long deadline = bcr_gtime() + P.wait_ns;
+  const unsigned nblocks = gridDim.x;
   const int lane = threadIdx.x & 31;
-  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long gthreads = (long long)gridDim.x * blockDim.x;
+  const long long gt0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nwarps = gthreads >> 5, gw0 = gt0 >> 5;
   const int b = P.b, g4 = (b + 3) / 4;
-  if (gw >= (long long)P.n * g4) return;
-  const int j = (int)(gw / g4), row0 = 4 * (int)(gw - (long long)j * g4);
   const int a = lane >> 3, r = lane & 7;
-  for (int ch = 0; ch < P.nch; ++ch) {
-    const size_t co = (size_t)ch * P.rs * 8;
-    const size_t o = ((size_t)(row0 + a)) * 8 + r;
-    if ((j & 1) == 0) {
-      if (row0 + a < b) P.xl_l[co + (size_t)j * b * 8 + o] = P.xl_n[co + (size_t)(j / 2) * b * 8 + o];
-      continue;
-    }
-    float acc[4][8];
-#pragma unroll
-    for (int x = 0; x < 4; ++x)
-#pragma unroll
-      for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
-    bcr_rows4_f32(P.mats + P.offA[j], row0, P.bl_l + co + (size_t)j * b * 8, b, lane, 1.f, acc);
-    bcr_rows4_f32(P.mats + P.offV[j], row0, P.xl_n + co + (size_t)((j - 1) / 2) * b * 8, b, lane, -1.f, acc);
-    if (j + 1 < P.n)
-      bcr_rows4_f32(P.mats + P.offU[j], row0, P.xl_n + co + (size_t)((j + 1) / 2) * b * 8, b, lane, -1.f, acc);
-    const float s = bcr_warp_reduce32(acc, lane);
-    if (row0 + a < b) P.xl_l[co + (size_t)j * b * 8 + o] = s;
-  }
-}
-
-__global__ void bcr_final_f32_kernel(const float* __restrict__ Ainv, int b, const float* bl, float* xl,
-                                     long long rs, int nch) {
-  const int lane = threadIdx.x & 31;
-  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int g4 = (b + 3) / 4;
-  if (gw >= g4) return;
-  const int row0 = 4 * (int)gw;
-  const int a = lane >> 3, r = lane & 7;
-  for (int ch = 0; ch < nch; ++ch) {
-    const size_t co = (size_t)ch * rs * 8;
-    float acc[4][8];
-#pragma unroll
-    for (int x = 0; x < 4; ++x)
-#pragma unroll
-      for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
-    bcr_rows4_f32(Ainv, row0, bl + co, b, lane, 1.f, acc);
-    const float s = bcr_warp_reduce32(acc, lane);
-    if (row0 + a < b) xl[co + ((size_t)(row0 + a)) * 8 + r] = s;
-  }
-}
-
-// level-0 right-hand sides: bl[ch][q][r8] = b[8 ch + r8][perm[q]] (0 on padding and absent RHS)
-__global__ void bcr_gather_f32_kernel(const int* __restrict__ perm, const double* __restrict__ b, long long b_rs,
-                                      float* __restrict__ bl, long long rs, long long len, int nrhs, int nch) {
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)nch * len * 8;
-       t += (long long)gridDim.x * blockDim.x) {
+  // level-0 right-hand sides: bl[ch][q][r8] = b[8 ch + r8][perm[q]] (0 on padding and absent RHS)
+  for (long long t = gt0; t < (long long)P.nch * P.len0 * 8; t += gthreads) {
     const int r8 = (int)(t & 7);
     const long long e = t >> 3;
-    const int ch = (int)(e / len);
-    const long long q = e - (long long)ch * len;
-    const int r = ch * 8 + r8;
-    const int pq = perm[q];
-    bl[((size_t)ch * rs + q) * 8 + r8] = (pq >= 0 && r < nrhs) ? (float)b[r * b_rs + pq] : 0.f;
+    const int ch = (int)(e / P.len0);
+    const long long q = e - (long long)ch * P.len0;
+    const int rr = ch * 8 + r8;
+    const int pq = P.perm[q];
+    P.bl[((size_t)ch * P.rs + q) * 8 + r8] = (pq >= 0 && rr < P.nrhs) ? (float)P.bin[rr * P.b_rs + pq] : 0.f;
   }
-}
-
-__global__ void bcr_scatter_f32_kernel(const int* __restrict__ perm, const float* __restrict__ xl, long long rs,
-                                       double* __restrict__ x, long long x_rs, long long len, int nrhs) {
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len * nrhs;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(t / len);
-    const long long q = t - r * len;
-    const int pq = perm[q];
-    if (pq >= 0) x[r * x_rs + pq] = (double)xl[((size_t)(r >> 3) * rs + q) * 8 + (r & 7)];
+  bcr_grid_sync(P.bar, nblocks, deadline, P.err);
+  // forward: bl[l+1][i/2] = bl[l][i] - U_{i-1}^T bl[l][i-1] - V_{i+1}^T bl[l][i+1]
+  for (int l = 0; l < P.L; ++l) {
+    const int n = P.n_at[l], n_new = (n + 1) / 2;
+    const long long* tUT = P.tables + P.tab_off[l] + 2LL * n;
+    const long long* tVT = P.tables + P.tab_off[l] + 4LL * n;
+    for (long long task = gw0; task < (long long)n_new * g4 * P.nch; task += nwarps) {
+      const int ch = (int)(task / ((long long)n_new * g4));
+      const long long tr = task - (long long)ch * n_new * g4;
+      const int inew = (int)(tr / g4), row0 = 4 * (int)(tr - (long long)inew * g4);
+      const int i = 2 * inew;
+      const float* vl = P.bl + ((size_t)ch * P.rs + P.vec_off[l]) * 8;
+      float acc[4][8];
+      bcr_zero(acc);
+      if (i - 1 >= 0 && tUT[i - 1] >= 0)
+        bcr_rows4_f32(P.mats + tUT[i - 1], row0, vl + (size_t)(i - 1) * b * 8, b, lane, 1.f, acc);
+      if (i + 1 < n) bcr_rows4_f32(P.mats + tVT[i + 1], row0, vl + (size_t)(i + 1) * b * 8, b, lane, 1.f, acc);
+      const float s = bcr_warp_reduce32(acc, lane);
+      if (row0 + a < b) {
+        const size_t o = (size_t)(row0 + a) * 8 + r;
+        P.bl[((size_t)ch * P.rs + P.vec_off[l + 1]) * 8 + (size_t)inew * b * 8 + o] = vl[(size_t)i * b * 8 + o] - s;
+      }
+    }
+    bcr_grid_sync(P.bar, nblocks, deadline, P.err);
+  }
+  // the last remaining block: x = A^{-1} bl
+  for (long long task = gw0; task < (long long)g4 * P.nch; task += nwarps) {
+    const int ch = (int)(task / g4), row0 = 4 * (int)(task - (long long)ch * g4);
+    float acc[4][8];
+    bcr_zero(acc);
+    bcr_rows4_f32(P.mats + P.off_final, row0, P.bl + ((size_t)ch * P.rs + P.vec_off[P.L]) * 8, b, lane, 1.f, acc);
+    const float s = bcr_warp_reduce32(acc, lane);
+    if (row0 + a < b) P.xl[((size_t)ch * P.rs + P.vec_off[P.L]) * 8 + (size_t)(row0 + a) * 8 + r] = s;
+  }
+  bcr_grid_sync(P.bar, nblocks, deadline, P.err);
+  // backward: x[l][j] = Ainv_j bl[l][j] - V_j x[l][j-1] - U_j x[l][j+1] (odd j), x[l][j] = x[l+1][j/2]
+  for (int l = P.L - 1; l >= 0; --l) {
+    const int n = P.n_at[l];
+    const long long* tA = P.tables + P.tab_off[l];
+    const long long* tU = tA + n;
+    const long long* tV = tA + 3LL * n;
+    for (long long task = gw0; task < (long long)n * g4 * P.nch; task += nwarps) {
+      const int ch = (int)(task / ((long long)n * g4));
+      const long long tr = task - (long long)ch * n * g4;
+      const int j = (int)(tr / g4), row0 = 4 * (int)(tr - (long long)j * g4);
+      const size_t cl = ((size_t)ch * P.rs + P.vec_off[l]) * 8, cn = ((size_t)ch * P.rs + P.vec_off[l + 1]) * 8;
+      const size_t o = (size_t)(row0 + a) * 8 + r;
+      if ((j & 1) == 0) {
+        if (row0 + a < b) P.xl[cl + (size_t)j * b * 8 + o] = P.xl[cn + (size_t)(j / 2) * b * 8 + o];
+        continue;
+      }
+      float acc[4][8];
+      bcr_zero(acc);
+      bcr_rows4_f32(P.mats + tA[j], row0, P.bl + cl + (size_t)j * b * 8, b, lane, 1.f, acc);
+      bcr_rows4_f32(P.mats + tV[j], row0, P.xl + cn + (size_t)((j - 1) / 2) * b * 8, b, lane, -1.f, acc);
+      if (j + 1 < n)
+        bcr_rows4_f32(P.mats + tU[j], row0, P.xl + cn + (size_t)((j + 1) / 2) * b * 8, b, lane, -1.f, acc);
+      const float s = bcr_warp_reduce32(acc, lane);
+      if (row0 + a < b) P.xl[cl + (size_t)j * b * 8 + o] = s;
+    }
+    bcr_grid_sync(P.bar, nblocks, deadline, P.err);
+  }
+  // scatter of level 0 back to the primal DOF
+  for (long long t = gt0; t < P.len0 * P.nrhs; t += gthreads) {
+    const int rr = (int)(t / P.len0);
+    const long long q = t - rr * P.len0;
+    const int pq = P.perm[q];
+    if (pq >= 0) P.xout[rr * P.x_rs + pq] = (double)P.xl[((size_t)(rr >> 3) * P.rs + q) * 8 + (rr & 7)];
   }
 }
 
@@ -583,6 +619,22 @@ fetidp_status coarse_setup(Ctx& c, const double* Spp_dev) {
     const int nch = (c.m + 7) / 8;
     FD_TRY(dalloc_t(c, &B.bl_f, (size_t)nch * B.vec_len * 8));
     FD_TRY(dalloc_t(c, &B.xl_f, (size_t)nch * B.vec_len * 8));
+    // cooperative grid: every block resident (occupancy x SMs), no more than the widest level needs
+    int dev = 0, nsm = 0, per_sm = 0;
+    FD_CUDA(cudaGetDevice(&dev));
+    FD_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    FD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bcr_coop_f32_kernel, 256, 0));
+    int coop_ok = 0;
+    FD_CUDA(cudaDeviceGetAttribute(&coop_ok, cudaDevAttrCooperativeLaunch, dev));
+    if (coop_ok && per_sm > 0) {
+      // up to two CTAs per SM (measured faster than one at both the 2D and the 3D benchmark sizes),
+      // no more than one warp per task of the widest level
+      const long long widest = (long long)std::max(nb, 1) * ((b + 3) / 4) * nch;   // warp tasks
+      const long long want = (widest * 32 + 255) / 256;
+      B.coop_grid = (int)std::max<long long>(1, std::min<long long>((long long)std::min(per_sm, 2) * nsm, want));
+      FD_TRY(dalloc_t(c, &B.coop_bar, 2));
+      FD_CUDA(cudaMemsetAsync(B.coop_bar, 0, 2 * sizeof(unsigned), c.stream));
+    }
     FD_CUDA(cudaStreamSynchronize(c.stream));   // host offset lists go out of scope
     tmp_free(c, offs);
   }
@@ -638,52 +690,52 @@ fetidp_status coarse_solve(Ctx& c, const double* b, long long b_rs, double* x, l
 }
 
 // The same solve on the FP32 copy (mixed path): FP32 factor and level vectors, FP32 products summed
-// per lane and over the warp.  The rounding of the copy is a fixed linear perturbation of S_PP^{-1}.
+// per lane and over the warp, one cooperative launch for the whole solve (gather, levels, scatter).
+// The rounding of the copy is a fixed linear perturbation of S_PP^{-1}.
 fetidp_status coarse_solve_f32(Ctx& c, const double* b, long long b_rs, double* x, long long x_rs, int nrhs) {
   CoarseBCR& B = c.bcr;
-  if (!B.mats_f) return coarse_solve(c, b, b_rs, x, x_rs, nrhs);
+  if (!B.mats_f || !B.coop_bar || !c.tc_err) return coarse_solve(c, b, b_rs, x, x_rs, nrhs);
   const int nch = (nrhs + 7) / 8;
-  if (nch > (c.m + 7) / 8) { set_error("coarse solve: more RHS than the context holds"); return FETIDP_EINVAL; }
-  const long long len0 = (long long)B.nb * B.b;
-  const long long rs = B.vec_len;
+  if (nch > (c.m + 7) / 8 || B.levels > kBcrMaxLevels) {
+    set_error("coarse solve: more RHS or levels than the FP32 copy holds");
+    return FETIDP_EINVAL;
+  }
   ProfScope ps(c, FETIDP_K_COARSE, 2.0 * (B.mat_bytes_f / 4.0) * 8.0 * nch,
                (double)B.mat_bytes_f + 4.0 * 8.0 * nch * 4.0 * B.vec_len);
-  bcr_gather_f32_kernel<<<gridn(len0 * nch * 8), 256, 0, c.stream>>>(B.perm, b, b_rs, B.bl_f, rs, len0, nrhs, nch);
-  FD_CHECK_LAUNCH();
-  std::vector<const long long*> tA(B.levels), tU(B.levels), tUT(B.levels), tV(B.levels), tVT(B.levels);
-  {
-    const long long* p = B.tables_f;
-    for (int l = 0; l < B.levels; ++l) {
-      const int n = B.n_at[l];
-      tA[l] = p; p += n;
-      tU[l] = p; p += n;
-      tUT[l] = p; p += n;
-      tV[l] = p; p += n;
-      tVT[l] = p; p += n;
+  BcrCoopF P;
+  P.b = B.b;
+  P.L = B.levels;
+  P.nch = nch;
+  P.nrhs = nrhs;
+  P.rs = B.vec_len;
+  P.len0 = (long long)B.nb * B.b;
+  P.mats = B.mats_f;
+  P.tables = B.tables_f;
+  P.off_final = B.off_final_f;
+  long long toff = 0;
+  for (int l = 0; l <= B.levels; ++l) {
+    P.n_at[l] = B.n_at[l];
+    P.vec_off[l] = B.vec_off[l];
+    if (l < B.levels) {
+      P.tab_off[l] = toff;
+      toff += 5LL * B.n_at[l];
     }
   }
-  for (int l = 0; l < B.levels; ++l) {
-    BcrLevelF P{B.b, B.n_at[l], nch, rs, B.mats_f, tA[l], tU[l], tUT[l], tV[l], tVT[l],
-                B.bl_f + B.vec_off[l] * 8, B.bl_f + B.vec_off[l + 1] * 8, nullptr, nullptr};
-    const long long warps = (long long)((B.n_at[l] + 1) / 2) * ((B.b + 3) / 4);
-    bcr_forward_f32_kernel<<<grid_exact(warps * 32), 256, 0, c.stream>>>(P);
-    FD_CHECK_LAUNCH();
-  }
-  {
-    const int L = B.levels;
-    bcr_final_f32_kernel<<<grid_exact((long long)((B.b + 3) / 4) * 32), 256, 0, c.stream>>>(
-        B.mats_f + B.off_final_f, B.b, B.bl_f + B.vec_off[L] * 8, B.xl_f + B.vec_off[L] * 8, rs, nch);
-    FD_CHECK_LAUNCH();
-  }
-  for (int l = B.levels - 1; l >= 0; --l) {
-    BcrLevelF P{B.b, B.n_at[l], nch, rs, B.mats_f, tA[l], tU[l], tUT[l], tV[l], tVT[l],
-                B.bl_f + B.vec_off[l] * 8, nullptr, B.xl_f + B.vec_off[l] * 8, B.xl_f + B.vec_off[l + 1] * 8};
-    const long long warps = (long long)B.n_at[l] * ((B.b + 3) / 4);
-    bcr_backward_f32_kernel<<<grid_exact(warps * 32), 256, 0, c.stream>>>(P);
-    FD_CHECK_LAUNCH();
-  }
-  bcr_scatter_f32_kernel<<<gridn(len0 * nrhs), 256, 0, c.stream>>>(B.perm, B.xl_f, rs, x, x_rs, len0, nrhs);
-  FD_CHECK_LAUNCH();
+  P.bl = B.bl_f;
+  P.xl = B.xl_f;
+  P.perm = B.perm;
+  P.bin = b;
+  P.b_rs = b_rs;
+  P.xout = x;
+  P.x_rs = x_rs;
+  P.bar = B.coop_bar;
+  P.err = c.tc_err;
+  P.wait_ns = c.wait_ns;
+  FD_CUDA(cudaMemsetAsync(B.coop_bar, 0, sizeof(unsigned), c.stream));   // arrivals (the generation runs on)
+  void* args[] = {&P};
+  FD_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(bcr_coop_f32_kernel), dim3((unsigned)B.coop_grid),
+                                      dim3(256), args, 0, c.stream));
+  count_launch();
   return FETIDP_OK;
 }
 

@@ -152,6 +152,8 @@ struct CoarseBCR {
   float* bl_f = nullptr;
   float* xl_f = nullptr;
   size_t mat_bytes_f = 0;
+  unsigned* coop_bar = nullptr;    // grid barrier of the cooperative FP32 solve (arrivals, generation)
+  int coop_grid = 0;
 };
 
 // A principal-operator set packed for the tensor-core GEMM (BF16, SW128 K-major tiles).
@@ -222,6 +224,8 @@ struct Ctx {
   cudaGraphExec_t pcg_graph = nullptr;   // two inner PCG iterations, captured on first use
   long long pcg_graph_kernels = 0;       // kernels in that graph
   bool pcg_graph_failed = false;         // capture not possible: iterations run one by one
+  long long graph_replays = 0;           // graph launches issued by the host
+  long long graph_kernels_run = 0;       // kernels run inside those replays
   unsigned pcg_graph_mask = 0;           // profiled kernel classes when the graph was captured
   cudaStream_t ws = nullptr;             // the context's own stream for graph capture and replay
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;

@@ -498,6 +498,8 @@ fetidp_status pcg_solve(Ctx& c, const double* b, long long b_rs, double* x, long
     while (true) {
       FD_CUDA(cudaGraphLaunch(c.pcg_graph, c.stream));
       g_launches.fetch_add(c.pcg_graph_kernels);
+      c.graph_kernels_run += c.pcg_graph_kernels;
+      ++c.graph_replays;
       FD_CUDA(cudaMemcpyAsync(hs, sc, sizeof(double) * S_NSLOT * m, cudaMemcpyDeviceToHost, c.stream));
       FD_CUDA(cudaStreamSynchronize(c.stream));
       for (const Prof::Captured& g : c.prof.captured) {
@@ -827,7 +829,7 @@ static fetidp_status check_waits(Ctx& c, fetidp_status st) {
   FD_CUDA(cudaStreamSynchronize(c.stream));
   if (h) {
     FD_CUDA(cudaMemsetAsync(c.tc_err, 0, sizeof(int), c.stream));
-    set_error("a tensor-core kernel's device wait exceeded wait_budget_ns (code " + std::to_string(h) + ")");
+    set_error("a device wait (tensor-core pipeline or coarse-solve barrier) exceeded wait_budget_ns (code " + std::to_string(h) + ")");
     return FETIDP_ETIMEOUT;
   }
   return st;
@@ -1138,6 +1140,7 @@ static fetidp_status solve_common(fetidp_ctx* ctx, fetidp_info* info, OuterResul
   Ctx& c = ctx->c;
   auto t0 = std::chrono::steady_clock::now();
   c.inner_total = 0;
+  const long long l0 = g_launches.load(), gk0 = c.graph_kernels_run, gr0 = c.graph_replays;
   if (c.mixed) FD_CUDA(cudaMemsetAsync(c.tc_err, 0, sizeof(int), c.stream));
   const fetidp_status st = fgmres(c, c.w_tot, r);
   FD_CUDA(cudaStreamSynchronize(c.stream));
@@ -1149,7 +1152,7 @@ static fetidp_status solve_common(fetidp_ctx* ctx, fetidp_info* info, OuterResul
     if (herr != 0) {
       FD_CUDA(cudaMemsetAsync(c.tc_err, 0, sizeof(int), c.stream));
       FD_CUDA(cudaStreamSynchronize(c.stream));
-      set_error("a tensor-core kernel's device wait exceeded wait_budget_ns (code " + std::to_string(herr) + ")");
+      set_error("a device wait (tensor-core pipeline or coarse-solve barrier) exceeded wait_budget_ns (code " + std::to_string(herr) + ")");
       return FETIDP_ETIMEOUT;
     }
   }
@@ -1162,6 +1165,10 @@ static fetidp_status solve_common(fetidp_ctx* ctx, fetidp_info* info, OuterResul
     info->t_setup_s = c.t_setup_s;
     info->t_solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     info->device_bytes = c.device_bytes;
+    const long long kl = g_launches.load() - l0;
+    info->kernel_launches = kl;
+    info->host_launches = kl - (c.graph_kernels_run - gk0) + (c.graph_replays - gr0);
+    info->inner_graph = c.pcg_graph != nullptr && !c.pcg_graph_failed ? 1 : 0;
   }
   return FETIDP_OK;
 }

@@ -171,3 +171,16 @@ def test_mixed_assembled_and_principal_forms(name):
             assert _rel(out[form][1][r], yM) < 3e-4
         assert _rel(out[1][0][r], out[0][0][r]) < 3e-4
         assert _rel(out[2][0][r], out[1][0][r]) < 1e-5 and _rel(out[2][1][r], out[1][1][r]) < 1e-5
+
+
+@pytest.mark.parametrize("name", ["cfg1", "bcc3d"])
+def test_mixed_inner_pcg_runs_as_one_graph(name):
+    """The inner PCG iterations of the mixed path (with the one-launch cooperative coarse solve of
+    their coarse term) are captured and replayed as a CUDA graph: the solve reports it, and the host
+    issues fewer launch calls than kernels run."""
+    prob, lat, fe = oracle(name)
+    s = _mixed(prob)
+    _, _, info = s.solve()
+    assert info["rel_residual"] <= 1e-8
+    assert info["inner_graph"] == 1
+    assert 0 < info["host_launches"] < info["kernel_launches"]
