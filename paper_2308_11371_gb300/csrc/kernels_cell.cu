@@ -473,14 +473,16 @@ __global__ void __launch_bounds__(352, 2) krr_spmm_nodal_f32_kernel(
   const long long base = rhs * u_rs + cell * u_cs;
   const int nnode = nr / D, nk = nnz / D, sl = D * nr;
   const float* ev = eval + cell * (long long)nnz * nr;
-  for (int t = threadIdx.x; t < sl; t += blockDim.x) cp_async4(evs + t, ev + t);   // neighbour 0
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  // the chunk's vectors, transposed into [dof][vector], and neighbour 0's slots: asynchronous copies
   for (int t = threadIdx.x; t < kSpVB * nr; t += blockDim.x) {
     const int v = t / nr, q = t - v * nr;
-    float x = 0.f;
-    if (v < vb && FD_INB(base + (long long)(v0 + v) * nr + q, ext, 207)) x = u[base + (long long)(v0 + v) * nr + q];
-    uss[q * kSpLd + v] = x;
+    if (v < vb && FD_INB(base + (long long)(v0 + v) * nr + q, ext, 207))
+      cp_async4(uss + q * kSpLd + v, u + base + (long long)(v0 + v) * nr + q);
+    else
+      uss[q * kSpLd + v] = 0.f;
   }
+  for (int t = threadIdx.x; t < sl; t += blockDim.x) cp_async4(evs + t, ev + t);   // neighbour 0
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
   const long long ybase = rhs * y_rs + cell * y_cs;
   const int n = threadIdx.x;                      // one node per thread (the host launches >= nnode threads)
   const bool live = n < nnode;
@@ -1216,10 +1218,11 @@ __device__ void warp_pivoted_gram_solve(double* S, double* Lc, const double* hs,
 
 // The same diagonal-pivoted Cholesky solve by a whole CTA (nthreads threads, all of them calling):
 // warp 0 picks the pivot, every thread forms part of the pivot column and of the rank-1 update,
-// which touches only the upper triangle of the unpivoted rows and columns (S stays symmetric there,
-// and each entry receives the same FP64 operations in the same order as in the warp solve, so both
-// give identical results).  The substitutions run on warp 0.  sh holds a double and an int of
-// block-shared scratch.
+// which touches only the upper triangle of the unpivoted rows and columns (S stays symmetric there;
+// each entry receives the same FP64 operations in the same order as in the warp solve, and the
+// pivot's scale is one rsqrt instead of a square root and a division, the step's latency on
+// GB300's FP64 unit).  The substitutions run on warp 0.  sh holds a double and an int of
+// block-shared scratch.  nthreads is a multiple of 64 and nrb <= 64.
 __device__ void block_pivoted_gram_solve(double* S, double* Lc, const double* hs, double* ys, double* cs,
                                          double* colv, int* piv, double* sh_inv, int* sh_jb, int nrb, int ld,
                                          double drop_rel, int tid, int nthreads) {
@@ -1248,7 +1251,7 @@ __device__ void block_pivoted_gram_solve(double* S, double* Lc, const double* hs
       if (lane == 0) {
         const bool take = jb >= 0 && best > drop_rel * dmax;
         *sh_jb = take ? jb : -1;
-        if (take) { *sh_inv = 1.0 / sqrt(best); piv[np] = jb; }
+        if (take) { *sh_inv = rsqrt(best); piv[np] = jb; }   // one call on the pivot chain
       }
     }
     __syncthreads();
@@ -1262,10 +1265,15 @@ __device__ void block_pivoted_gram_solve(double* S, double* Lc, const double* hs
       Lc[np * ld + i] = cv;
     }
     __syncthreads();
-    for (int t = tid; t < 64 * 64; t += nthreads) {   // nrb <= 64
-      const int i = t >> 6, j = t & 63;
-      if (j >= nrb || i > j || ((used >> i) & 1ull) || ((used >> j) & 1ull)) continue;
-      S[i * ld + j] -= colv[i] * colv[j];
+    // nrb <= 64 and nthreads a multiple of 64: the thread's column j is fixed, its rows step by
+    // nthreads / 64 up to the diagonal
+    {
+      const int j = tid & 63, rs = nthreads >> 6;
+      if (j < nrb && !((used >> j) & 1ull)) {
+        const double cj = colv[j];
+        for (int i = tid >> 6; i <= j; i += rs)
+          if (!((used >> i) & 1ull)) S[i * ld + j] -= colv[i] * cj;
+      }
     }
     ++np;
     __syncthreads();
@@ -1310,11 +1318,13 @@ __device__ __forceinline__ void neumaier_add(T& s, T& c, T x) {
 // diagonal-pivoted Cholesky solve as the warp kernel, and all threads form x = R c.
 constexpr int kGbQ = 32;
 constexpr int kGbLd = 36;   // 16-byte rows; a warp's 16 distinct K R rows take the minimum two wavefronts
-// The staging chunks of R, K R and v live inside the L factor's region (used only after the Gram
-// matrix is complete), so a 64-basis block needs 70 KB and three blocks fit an SM.
+// The two staging stages of R, K R and v (filled by cp.async one chunk ahead) live inside the L
+// factor's region, used only after the Gram matrix is complete: a 64-basis block needs 74 KB and
+// three blocks fit an SM.
+__host__ __device__ inline size_t gram_block_stage_floats(int nrb) { return 2 * (size_t)nrb * kGbLd + kGbQ; }
 __host__ __device__ inline size_t gram_block_smem(int nrb) {
   const size_t ld = (size_t)nrb + 1;
-  const size_t stage = sizeof(float) * (2 * (size_t)nrb * kGbLd + kGbQ);
+  const size_t stage = 2 * sizeof(float) * gram_block_stage_floats(nrb);
   const size_t lc = sizeof(double) * nrb * ld;
   return sizeof(double) * (nrb * ld + 6 * (size_t)nrb + 2) + (stage > lc ? stage : lc);
 }
@@ -1333,9 +1343,8 @@ __global__ void __launch_bounds__(256, 3) gram_block_f32_kernel(const float* __r
   double* sh_inv = colv + 3 * nrb;
   int* sh_jb = reinterpret_cast<int*>(sh_inv + 1);
   double* Lc = sh_inv + 2;                           // [nrb][ld], after the Gram matrix is formed
-  float* Rs = reinterpret_cast<float*>(Lc);          // staging while it is formed
-  float* Ks = Rs + (size_t)nrb * kGbLd;
-  float* vs = Ks + (size_t)nrb * kGbLd;
+  float* stage0 = reinterpret_cast<float*>(Lc);      // two staging stages while it is formed
+  const size_t stage_f = gram_block_stage_floats(nrb);
   const long long col = blockIdx.x;                  // rhs * ncell + cell
   const int rhs = (int)(col / ncell);
   const long long cell = col - (long long)rhs * ncell;
@@ -1349,20 +1358,39 @@ __global__ void __launch_bounds__(256, 3) gram_block_f32_kernel(const float* __r
 #pragma unroll
     for (int b = 0; b < 4; ++b) { acc[a][b] = 0.f; cmp[a][b] = 0.f; }
   float hacc = 0.f, hcmp = 0.f;
-  for (int q0 = 0; q0 < nr; q0 += kGbQ) {
-    __syncthreads();                                  // the previous chunk is no longer read
+  // chunk k of R and K R goes to stage k & 1 by cp.async (zero-filled past n_r), one chunk ahead
+  auto issue = [&](int q0, float* st) {
+    float* Rs_ = st;
+    float* Ks_ = st + (size_t)nrb * kGbLd;
     for (int t = tid; t < nrb * kGbQ; t += blockDim.x) {
       const int i = t / kGbQ, qq = t - i * kGbQ, q = q0 + qq;
-      Rs[i * kGbLd + qq] = q < nr ? Rc[(size_t)i * nr + q] : 0.f;
-      Ks[i * kGbLd + qq] = q < nr ? KRc[(size_t)i * nr + q] : 0.f;
+      const bool in = q < nr;
+      cp_async_elem(Rs_ + i * kGbLd + qq, Rc + (size_t)i * nr + (in ? q : 0), in);
+      cp_async_elem(Ks_ + i * kGbLd + qq, KRc + (size_t)i * nr + (in ? q : 0), in);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  const int nchunk = (nr + kGbQ - 1) / kGbQ;
+  issue(0, stage0);
+  float part[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) part[a][b] = 0.f;
+  float hp = 0.f;
+  for (int ck = 0; ck < nchunk; ++ck) {
+    const int q0 = ck * kGbQ;
+    float* Rs = stage0 + (ck & 1) * stage_f;
+    float* Ks = Rs + (size_t)nrb * kGbLd;
+    float* vs = Ks + (size_t)nrb * kGbLd;
+    if (ck + 1 < nchunk) {
+      issue(q0 + kGbQ, stage0 + ((ck + 1) & 1) * stage_f);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     }
     if (tid < kGbQ) vs[tid] = q0 + tid < nr ? (float)vc[q0 + tid] : 0.f;
-    __syncthreads();
-    float part[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) part[a][b] = 0.f;
+    __syncthreads();                                  // chunk ck (and its v) is in place
 #pragma unroll 2
     for (int qq = 0; qq < kGbQ; qq += 4) {
       float4 rv[4], kv[4];
@@ -1384,15 +1412,21 @@ __global__ void __launch_bounds__(256, 3) gram_block_f32_kernel(const float* __r
           part[a][b] = p;
         }
     }
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) neumaier_add(acc[a][b], cmp[a][b], part[a][b]);
-    if (tid < nrb) {
-      float hp = 0.f;
+    if (tid < nrb)
       for (int qq = 0; qq < kGbQ; ++qq) hp = fmaf(Rs[tid * kGbLd + qq], vs[qq], hp);
-      neumaier_add(hacc, hcmp, hp);
+    // the partial sums of two chunks (64 terms) are added with Neumaier's compensation
+    if ((ck & 1) || ck + 1 == nchunk) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          neumaier_add(acc[a][b], cmp[a][b], part[a][b]);
+          part[a][b] = 0.f;
+        }
+      if (tid < nrb) neumaier_add(hacc, hcmp, hp);
+      hp = 0.f;
     }
+    __syncthreads();                                  // stage ck & 1 is refilled at chunk ck + 2
   }
 #pragma unroll
   for (int a = 0; a < 4; ++a)
