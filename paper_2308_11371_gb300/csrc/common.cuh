@@ -276,6 +276,11 @@ struct Ctx {
   // mixed path, large cells: the same operators assembled in FP32, rows padded to ld_f (16 bytes)
   float* Fdd_f = nullptr;     // [N][nd][ld_f]
   float* Sdd_f = nullptr;     // [N][nd][ld_f]
+  // mixed path, large cells: U_id_ring = the (i, d) block of the delta-combined K_rr^{-1} (Algorithm
+  // 3), in FP32 in both orientations, [N][n_i][ld_id] and [N][n_d][ld_di]
+  float* Uid_f = nullptr;
+  float* Udi_f = nullptr;
+  int ld_id = 0, ld_di = 0;
   int ld_f = 0;                // 0: packed symmetric tiles (sym_T tile rows of 32), else dense row stride
   int sym_T = 0;
   bool asm_f32 = false;
@@ -445,7 +450,7 @@ fetidp_status k_apply_K(Ctx& c, CCellVec u, CellVec y, int nvec_per_col, int nco
 fetidp_status k_rom_combine_f32(Ctx& c, const double* src, long long kstride, int ld, int r0, int c0, int rows,
                                 int cols, const double* coef, float* out, int ldo, int symT = 0);
 fetidp_status k_cell_symv_f32(Ctx& c, const float* mats, CCellVec x, CellVec y, double alpha, double beta, int nrhs);
-fetidp_status k_cell_gemm_f32(Ctx& c, const float* mats, int ldm, int rows, int cols, CCellVec x, CellVec y,
+fetidp_status k_cell_gemm_f32(Ctx& c, const float* mats, int ldm, int nout, int nin, CCellVec x, CellVec y,
                               double alpha, double beta, int nrhs);
 fetidp_status k_cell_gemv_strided(Ctx& c, const double* mats, long long mstride, int ld, int mrows,
                                   int mcols, CCellVec x, CellVec y, double alpha, double beta,

@@ -695,26 +695,28 @@ __global__ void __launch_bounds__(256) rom_combine_f32_kernel(const double* __re
   }
 }
 
-// y[rhs][cell][0..rows) = alpha M_f32[cell] x[rhs][cell][0..cols) + beta y for SYMMETRIC square
-// operators (F_dd_ring and S_dd_ring: combinations of symmetric principal operators): row j of M is
-// read as column j.  One CTA per cell; a thread owns four consecutive rows, so for each column j it
-// issues one 16-byte streaming load of M[j][4t..4t+3] (a warp reads 512 contiguous bytes), and the
-// column's x values for every RHS arrive as two broadcast 16-byte reads from shared memory
-// ([column][8] layout).  kAsmU columns' loads are issued before their arithmetic.
+// y[rhs][cell][0..nout) = alpha M[cell]^T x[rhs][cell][0..nin) + beta y for per-cell FP32 matrices
+// M[cell] of nin stored rows of nout entries (row stride ldm, a multiple of 4, >= nout): row j of M
+// multiplies x_j.  For the symmetric F_dd_ring and S_dd_ring (combinations of symmetric principal
+// operators) this is M x.  One CTA per cell; a thread owns four consecutive outputs, so for each
+// stored row j it issues one 16-byte streaming load of M[j][4t..4t+3] (a warp reads 512 contiguous
+// bytes), and the row's x values for every RHS arrive as two broadcast 16-byte reads from shared
+// memory ([row][8] layout).  kAsmU rows' loads are issued before their arithmetic.
 constexpr int kMaxRhsF32 = 8;
 constexpr int kAsmU = 8;
 constexpr int kAsmMaxThreads = 256;    // rows <= 1024
 __global__ void __launch_bounds__(kAsmMaxThreads) cell_gemm_f32_kernel(const float* __restrict__ mats, int ldm,
-                                                                       int rows, int cols,
+                                                                       int nout, int nin,
                                                                        const double* __restrict__ x, long long x_rs,
                                                                        int x_cs, double* __restrict__ y,
                                                                        long long y_rs, int y_cs, double alpha,
                                                                        double beta, int nrhs) {
-  extern __shared__ __align__(16) float xsf[];   // [cols][kMaxRhsF32]
+  extern __shared__ __align__(16) float xsf[];   // [nin][kMaxRhsF32]
   const long long cell = blockIdx.x;
   const int tid = threadIdx.x;
-  const float* M = mats + cell * (long long)rows * ldm;
-  const int r0 = 4 * tid;                        // ldm is a multiple of 4 and >= rows: the load stays in row j
+  const int rows = nout, cols = nin;             // outputs, stored rows
+  const float* M = mats + cell * (long long)nin * ldm;
+  const int r0 = 4 * tid;                        // ldm is a multiple of 4 and >= nout: the load stays in row j
   const bool live = r0 < rows;
   for (int rb0 = 0; rb0 < nrhs; rb0 += kMaxRhsF32) {
     const int rb = min(kMaxRhsF32, nrhs - rb0);
@@ -1873,20 +1875,20 @@ fetidp_status k_rom_combine_f32(Ctx& c, const double* src, long long kstride, in
   return FETIDP_OK;
 }
 
-fetidp_status k_cell_gemm_f32(Ctx& c, const float* mats, int ldm, int rows, int cols, CCellVec x, CellVec y,
+fetidp_status k_cell_gemm_f32(Ctx& c, const float* mats, int ldm, int nout, int nin, CCellVec x, CellVec y,
                               double alpha, double beta, int nrhs) {
-  // algorithmic bytes: the operators once, the FP64 vectors in and out
-  ProfScope ps(c, FETIDP_K_ASM_OP, 2.0 * rows * cols * (double)c.N * nrhs,
-               4.0 * c.N * (double)rows * ldm + 8.0 * c.N * (double)nrhs * (rows + cols));
-  if (rows != cols || rows > 4 * kAsmMaxThreads || ldm % 4 != 0 || ldm < rows ||
-      (reinterpret_cast<uintptr_t>(mats) & 15) != 0) {
-    set_error("FP32 cell operators: square, at most 1024 rows, rows padded to 16 bytes");
+  // algorithmic bytes: the operators once (padded rows as stored), the FP64 vectors in and out
+  ProfScope ps(c, FETIDP_K_ASM_OP, 2.0 * nout * nin * (double)c.N * nrhs,
+               4.0 * c.N * (double)nin * ldm + 8.0 * c.N * (double)nrhs * (nout + nin));
+  if (nout < 1 || nin < 1 || nout > 4 * kAsmMaxThreads || ldm % 4 != 0 || ldm < nout ||
+      (size_t)nin * kMaxRhsF32 * sizeof(float) > 200 * 1024 || (reinterpret_cast<uintptr_t>(mats) & 15) != 0) {
+    set_error("FP32 cell operators: at most 1024 outputs, rows padded to 16 bytes");
     return FETIDP_EINVAL;
   }
-  const size_t smem = (size_t)cols * kMaxRhsF32 * sizeof(float);
-  const int threads = ((rows + 3) / 4 + 31) / 32 * 32;
+  const size_t smem = (size_t)nin * kMaxRhsF32 * sizeof(float);
+  const int threads = ((nout + 3) / 4 + 31) / 32 * 32;
   cudaFuncSetAttribute(cell_gemm_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cell_gemm_f32_kernel<<<(unsigned)c.N, threads, smem, c.stream>>>(mats, ldm, rows, cols, x.p, x.rs, x.cs, y.p,
+  cell_gemm_f32_kernel<<<(unsigned)c.N, threads, smem, c.stream>>>(mats, ldm, nout, nin, x.p, x.rs, x.cs, y.p,
                                                                    y.rs, y.cs, alpha, beta, nrhs);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;

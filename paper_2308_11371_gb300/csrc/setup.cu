@@ -797,6 +797,17 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
       FD_CUDA(cudaMemsetAsync(c.Sdd_f, 0, fbytes, c.stream));
       FD_TRY(k_rom_combine_f32(c, c.Kinv, (long long)nr * nr, nr, ni, ni, nd, nd, c.delta, c.Fdd_f, c.ld_f, c.sym_T));
       FD_TRY(k_rom_combine_f32(c, c.Sdd, (long long)nd * nd, nd, 0, 0, nd, nd, c.alpha, c.Sdd_f, c.ld_f, c.sym_T));
+      // Algorithm 3's U_rd_ring = [U_id_ring; F_dd_ring]: the (i, d) block in FP32, stored once per
+      // orientation so that both of its products stream rows (K_rr^{-1} is symmetric, so the (d, i)
+      // block is its transpose)
+      c.ld_id = (nd + 3) & ~3;
+      c.ld_di = (ni + 3) & ~3;
+      FD_TRY(dalloc_t(c, &c.Uid_f, (size_t)c.N * ni * c.ld_id));
+      FD_TRY(dalloc_t(c, &c.Udi_f, (size_t)c.N * nd * c.ld_di));
+      FD_CUDA(cudaMemsetAsync(c.Uid_f, 0, sizeof(float) * (size_t)c.N * ni * c.ld_id, c.stream));
+      FD_CUDA(cudaMemsetAsync(c.Udi_f, 0, sizeof(float) * (size_t)c.N * nd * c.ld_di, c.stream));
+      FD_TRY(k_rom_combine_f32(c, c.Kinv, (long long)nr * nr, nr, 0, ni, ni, nd, c.delta, c.Uid_f, c.ld_id));
+      FD_TRY(k_rom_combine_f32(c, c.Kinv, (long long)nr * nr, nr, ni, 0, nd, ni, c.delta, c.Udi_f, c.ld_di));
     }
     FD_TRY(tc_comb_pack(c, c.cFdd, c.Kinv, (long long)nr * nr, nr, ni, ni, nd, nullptr, 0, 0, 0, 0, 0, nd, nrb,
                         split));

@@ -337,7 +337,14 @@ fetidp_status U_apply(Ctx& c, CCellVec vR, const double* vP, long long vP_rs, do
   // t_d = U_rd_ring^T v_r - T_dr U_rp_ring A_p^T z_P
   if (c.exact)   // standard FETI-DP: rows d of each cell's own K_rr^{-1} (symmetric)
     FD_TRY(cell_op(c, c.Kinv + (size_t)ni * nr, (long long)nr * nr, nr, nd, nr, vR, td, 1.0, 0.0));
-  else if (c.mixed)
+  else if (c.Uid_f) {   // assembled FP32 blocks: U_id^T v_i + F_dd v_d
+    FD_TRY(k_cell_gemm_f32(c, c.Uid_f, c.ld_id, nd, ni, vR, td, 1.0, 0.0, m));
+    const CCellVec vd{vR.p + ni, vR.rs, vR.cs};
+    if (c.sym_T)
+      FD_TRY(k_cell_symv_f32(c, c.Fdd_f, vd, td, 1.0, 1.0, m));
+    else
+      FD_TRY(k_cell_gemm_f32(c, c.Fdd_f, c.ld_f, nd, nd, vd, td, 1.0, 1.0, m));
+  } else if (c.mixed)
     FD_TRY(tc_comb_apply(c, c.cUrdT, vR, c.delta, c.delta, td.p, true, td.rs, td.cs, 1.0, 0.0, m, c.N));
   else
     FD_TRY(k_grouped_gemm(c, c.Kinv + (size_t)ni * nr, (long long)nr * nr, nr, nd, nr, vR, td, c.delta,
@@ -611,7 +618,14 @@ fetidp_status op_precondition(Ctx& c, const double* x, double* y) {
   FD_TRY(coarse_solve(c, c.w_P1, c.nP, c.w_P1, c.nP, m));
   if (c.exact)   // columns d of each cell's own K_rr^{-1}
     FD_TRY(cell_op(c, c.Kinv + ni, (long long)nr * nr, nr, nr, nd, cview(g), yR, -1.0, 1.0));
-  else if (c.mixed)
+  else if (c.Uid_f) {   // assembled FP32 blocks: y_i -= U_id g, y_d -= F_dd g
+    FD_TRY(k_cell_gemm_f32(c, c.Udi_f, c.ld_di, ni, nd, cview(g), yR, -1.0, 1.0, m));
+    const CellVec yd{yR.p + ni, yR.rs, yR.cs};
+    if (c.sym_T)
+      FD_TRY(k_cell_symv_f32(c, c.Fdd_f, cview(g), yd, -1.0, 1.0, m));
+    else
+      FD_TRY(k_cell_gemm_f32(c, c.Fdd_f, c.ld_f, nd, nd, cview(g), yd, -1.0, 1.0, m));
+  } else if (c.mixed)
     FD_TRY(tc_comb_apply(c, c.cUrd, cview(g), c.delta, c.delta, yR.p, true, yR.rs, yR.cs, -1.0, 1.0, m, c.N));
   else
     FD_TRY(k_grouped_gemm(c, c.Kinv + ni, (long long)nr * nr, nr, nr, nd, cview(g), yR, c.delta, -1.0,
