@@ -9,7 +9,7 @@ mixed precision.  value = DOF / second with the paper's convention (cells x DOF 
 Around the timed steps, outside the timed region:
   * one FP64-path solve of the same workload (the metric's "mixed vs FP64") and the relative
     displacement difference between the two solutions;
-  * the 64 x 64 2D lattice (config2) as a secondary line;
+  * the 64 x 64 2D lattice (frame_2d_64x64) as a secondary line;
   * end to end through fetidp_solve_host (host output buffers, D2H inside the timed region);
   * the CPU oracle on a bounded sample of the workload (rank 0, N = 1).
 Every kernel class is timed by CUDA events on the context stream inside the timed steps; each
@@ -17,7 +17,7 @@ class's roofline (HBM, tensor or FP32/FP64 pipe) is in "rooflines", the class wi
 device time in "roofline".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload cfg5|cfg2|cfg4] [--precision mixed|fp64]
+                  [--workload bcc_3d_32x32x16|frame_2d_64x64|bcc_adjoint_24x24x12] [--precision mixed|fp64]
                   [--no-cpu-baseline] [--no-fp64-ref] [--no-secondary] [--e2e-steps E]
                   [--sample NX,NY,NZ]
 
@@ -53,9 +53,9 @@ DF_OPS_PER_TERM = 12
 # configured ones for the outer solver to converge (the paper advises growing the reduced basis
 # until the outer iterations are few, Sec. 5.1.2): 8 -> 32 in 2D, 16 -> 64 in 3D.
 WORKLOADS = {
-    "cfg5": {"label": "3d_32x32x16_bcc_e6_6rhs", "n_rb": 64, "opts": {"restart": 10, "max_outer": 60}},
-    "cfg2": {"label": "2d_64x64_e16", "n_rb": 32, "opts": {}},
-    "cfg4": {"label": "3d_24x24x12_bcc_sigmoid_e6", "n_rb": 16, "opts": {"restart": 10, "max_outer": 60}},
+    "bcc_3d_32x32x16": {"label": "3d_32x32x16_bcc_e6_6rhs", "n_rb": 64, "opts": {"restart": 10, "max_outer": 60}},
+    "frame_2d_64x64": {"label": "2d_64x64_e16", "n_rb": 32, "opts": {}},
+    "bcc_adjoint_24x24x12": {"label": "3d_24x24x12_bcc_sigmoid_e6", "n_rb": 16, "opts": {"restart": 10, "max_outer": 60}},
 }
 
 
@@ -71,7 +71,7 @@ def measured_peaks():
 def workload_problem(name):
     from paper_2308_11371_gb300 import workloads as W
     w = WORKLOADS[name]
-    prob = {"cfg5": W.config5, "cfg2": W.config2, "cfg4": W.config4}[name]()
+    prob = {"bcc_3d_32x32x16": W.bcc_3d_32x32x16, "frame_2d_64x64": W.frame_2d_64x64, "bcc_adjoint_24x24x12": W.bcc_adjoint_24x24x12}[name]()
     prob.n_rb = w["n_rb"]
     return prob
 
@@ -94,9 +94,9 @@ def sample_problem(name, cells):
     return q
 
 
-SAMPLES = {"cfg5": {"cpu": (2, 2, 2), "reference": (2, 2, 1)},
-           "cfg4": {"cpu": (2, 2, 2), "reference": (2, 2, 1)},
-           "cfg2": {"cpu": (16, 16, 1), "reference": (12, 12, 1)}}
+SAMPLES = {"bcc_3d_32x32x16": {"cpu": (2, 2, 2), "reference": (2, 2, 1)},
+           "bcc_adjoint_24x24x12": {"cpu": (2, 2, 2), "reference": (2, 2, 1)},
+           "frame_2d_64x64": {"cpu": (16, 16, 1), "reference": (12, 12, 1)}}
 
 
 def oracle_time_to_solution(name, cells):
@@ -304,12 +304,12 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cfg5", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="bcc_3d_32x32x16", choices=list(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-ref", action="store_true",
                     help="skip the FP64-path solve of the mixed-vs-FP64 comparison")
-    ap.add_argument("--no-secondary", action="store_true", help="skip the 2D config2 secondary line")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the 2D frame_2d_64x64 secondary line")
     ap.add_argument("--e2e-steps", type=int, default=3,
                     help="end-to-end steps through fetidp_solve_host (each one time-to-solution)")
     ap.add_argument("--sample", default=None,
@@ -442,11 +442,11 @@ def main():
     del u_host
     torch.cuda.empty_cache()
 
-    # secondary line: the 2D 64x64 lattice (config2), a few steps, same step definition
+    # secondary line: the 2D 64x64 lattice (frame_2d_64x64), a few steps, same step definition
     secondary = None
-    if not args.no_secondary and args.workload != "cfg2":
+    if not args.no_secondary and args.workload != "frame_2d_64x64":
         try:
-            p2 = workload_problem("cfg2")
+            p2 = workload_problem("frame_2d_64x64")
             for _ in range(2):
                 binding.Solver(p2, precision=precision).close()
             torch.cuda.synchronize()
@@ -461,7 +461,7 @@ def main():
             torch.cuda.synchronize()
             ms2 = a0.elapsed_time(a1) / n2
             dof2 = p2.n_cells * 578 * p2.n_rhs
-            secondary = {"workload": WORKLOADS["cfg2"]["label"], "n_rb": i2["n_rb"], "ms_per_step": ms2,
+            secondary = {"workload": WORKLOADS["frame_2d_64x64"]["label"], "n_rb": i2["n_rb"], "ms_per_step": ms2,
                          "value": dof2 / (ms2 / 1e3), "unit": UNIT, "outer_its": i2["outer_its"],
                          "inner_its_total": i2["inner_its_total"], "rel_residual": i2["rel_residual"],
                          "solve_kernel_launches": i2["kernel_launches"], "solve_host_launches": i2["host_launches"],

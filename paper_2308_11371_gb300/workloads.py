@@ -117,7 +117,7 @@ def lattice_2d(nx=4, ny=4, e=8, a=0.0, r=0.12, n_rb=2, r_grade=0.0,
     return _frame_problem(nx, ny, e, r_cell, a, n_rb, name)
 
 
-def config1(seed: int = 1) -> LatticeProblem:
+def frame_2d_4x4(seed: int = 1) -> LatticeProblem:
     """2D plane strain, 4x4 cells of 8x8 Q1, r = 0.12, a ~ U[0, 0.5], 2 principal cells."""
     rng = np.random.default_rng(seed)
     a = rng.uniform(0.0, 0.5)
@@ -130,10 +130,10 @@ def config1(seed: int = 1) -> LatticeProblem:
 # the outer solver stagnates (measured on the oracle and on the GPU).  32 principal cells
 # converge in a few outer iterations, following the paper's advice to grow the reduced
 # basis until the global iterations are few (Sec. 5.1.2, Fig. 9).
-CONFIG2_SOLVE_N_RB = 32
+FRAME_64X64_SOLVE_N_RB = 32
 
 
-def config2(seed: int = 2, n_rb: int = 8) -> LatticeProblem:
+def frame_2d_64x64(seed: int = 2, n_rb: int = 8) -> LatticeProblem:
     """2D plane strain, 64x64 cells of 16x16 Q1, graded r_s, a ~ U[0, 4], n_rb principal cells."""
     rng = np.random.default_rng(seed)
     a = rng.uniform(0.0, 4.0)
@@ -165,7 +165,7 @@ def lattice_3d(nx=2, ny=2, nz=2, e=3, r=0.2, r_spread=0.0, map_kind=MAP_IDENTITY
     return _bcc((nx, ny, nz), e, r_cell, mask_kind, map_kind, map_params, loads, n_rb, name)
 
 
-def config3(seed: int = 3) -> List[LatticeProblem]:
+def bcc_batch_32(seed: int = 3) -> List[LatticeProblem]:
     """32 independent 3D BCC lattices of uneven size, 3 top tractions each."""
     rng = np.random.default_rng(seed)
     out = []
@@ -180,9 +180,9 @@ def config3(seed: int = 3) -> List[LatticeProblem]:
     return out
 
 
-def config3_sample(seed: int = 3, n_lattices: int = 4, max_xy: int = 4, max_z: int = 2,
+def bcc_batch_sample(seed: int = 3, n_lattices: int = 4, max_xy: int = 4, max_z: int = 2,
                    n_rb: int = 64) -> List[LatticeProblem]:
-    """Lattices drawn with config3's recipe (6^3 BCC cells, per-cell radii ~ U[0.15, 0.3], shear +
+    """Lattices drawn with bcc_batch_32's recipe (6^3 BCC cells, per-cell radii ~ U[0.15, 0.3], shear +
     bend map, three top tractions) at sizes small enough for the oracle's monolithic solve:
     nx, ny ~ U{2..max_xy}, nz ~ U{1..max_z}."""
     rng = np.random.default_rng(seed)
@@ -198,7 +198,7 @@ def config3_sample(seed: int = 3, n_lattices: int = 4, max_xy: int = 4, max_z: i
     return out
 
 
-def config4(seed: int = 4) -> LatticeProblem:
+def bcc_adjoint_24x24x12(seed: int = 4) -> LatticeProblem:
     """3D 24x24x12 BCC with sigmoid density, identity map, unit downward top traction."""
     rng = np.random.default_rng(seed)
     cells = (24, 24, 12)
@@ -210,7 +210,7 @@ def config4(seed: int = 4) -> LatticeProblem:
     return p
 
 
-def config5(seed: int = 5) -> LatticeProblem:
+def bcc_3d_32x32x16(seed: int = 5) -> LatticeProblem:
     """3D 32x32x16 BCC, radius graded along x, bend+twist map, 6 load cases."""
     rng = np.random.default_rng(seed)
     nx, ny, nz = 32, 32, 16
@@ -225,4 +225,4 @@ def config5(seed: int = 5) -> LatticeProblem:
                 (a, float(nx), tau, ny / 2.0, nz / 2.0), loads, 16, "3d_32x32x16")
 
 
-CONFIGS = {1: config1, 2: config2, 3: config3, 4: config4, 5: config5}
+WORKLOAD_FNS = {1: frame_2d_4x4, 2: frame_2d_64x64, 3: bcc_batch_32, 4: bcc_adjoint_24x24x12, 5: bcc_3d_32x32x16}

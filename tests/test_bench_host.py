@@ -46,15 +46,15 @@ def test_cpu_sample_is_a_sub_lattice_of_the_workload():
     map and loads, and each sampled cell keeps its radius."""
     import numpy as np
     import bench
-    full = bench.workload_problem("cfg5")
-    q = bench.sample_problem("cfg5", (4, 3, 2))
+    full = bench.workload_problem("bcc_3d_32x32x16")
+    q = bench.sample_problem("bcc_3d_32x32x16", (4, 3, 2))
     assert q.cells == (4, 3, 2) and q.elems == full.elems and q.dim == 3
     assert q.map_kind == full.map_kind and q.map_params == full.map_params
     assert q.mask_kind == full.mask_kind and len(q.loads) == len(full.loads) == 6
     fr = np.asarray(full.r_cell).reshape(16, 32, 32)
     assert np.array_equal(q.r_cell.reshape(2, 3, 4), fr[:2, :3, :4])
-    q2 = bench.sample_problem("cfg2", (8, 8, 1))
-    f2 = bench.workload_problem("cfg2")
+    q2 = bench.sample_problem("frame_2d_64x64", (8, 8, 1))
+    f2 = bench.workload_problem("frame_2d_64x64")
     assert q2.cells == (8, 8, 1) and q2.map_params == f2.map_params
     assert np.allclose(q2.r_cell.reshape(8, 8), np.asarray(f2.r_cell).reshape(64, 64)[:8, :8])
 

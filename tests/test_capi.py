@@ -60,7 +60,7 @@ def test_kernel_classes_match_the_header():
 
 def test_problem_struct_marshalling():
     from paper_2308_11371_gb300 import workloads as W
-    p = W.config5()
+    p = W.bcc_3d_32x32x16()
     s, keep = binding.make_problem_struct(p)
     assert (s.dim, list(s.cells), s.elems, s.n_loads, s.n_rb) == (3, [32, 32, 16], 6, 6, 16)
     assert s.load_kind[3] == W.LOAD_BODY and s.load_dir[3 * 3 + 0] == 1.0
@@ -71,7 +71,7 @@ def test_setup_rejects_bad_input_without_gpu(lib):
     """Argument checks run before any CUDA call."""
     import ctypes
     from paper_2308_11371_gb300 import workloads as W
-    p = W.config1()
+    p = W.frame_2d_4x4()
     p.n_rb = 0
     s, keep = binding.make_problem_struct(p)
     h = ctypes.c_void_p()
@@ -87,13 +87,13 @@ def test_setup_validation_without_gpu(lib, case):
     answers FETIDP_EINVAL (-1) with no context."""
     import ctypes
     from paper_2308_11371_gb300 import workloads as W
-    a = W.config1()
+    a = W.frame_2d_4x4()
     probs = [a]
     opts = {}
     if case == "batch_elems":
         probs = [a, W.lattice_2d(3, 3, 6, n_rb=2)]             # 8 vs 6 elements per cell edge
     elif case == "batch_loads":
-        b = W.config1()
+        b = W.frame_2d_4x4()
         b.loads = b.loads + b.loads                              # 1 vs 2 load cases
         probs = [a, b]
     elif case == "tc_split":
@@ -142,7 +142,7 @@ def test_zero_material_is_singular_without_gpu(lib):
     """E_solid = E_void = 0 leaves every cell stiffness zero: FETIDP_ESINGULAR (-6), no context."""
     import ctypes
     from paper_2308_11371_gb300 import workloads as W
-    a = W.config1()
+    a = W.frame_2d_4x4()
     a.E_solid = 0.0
     a.E_void = 0.0
     s, keep = binding.make_problem_struct(a)

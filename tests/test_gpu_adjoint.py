@@ -76,13 +76,13 @@ def test_mixed_precision_gradient():
     assert np.abs(gmx - g64).max() / np.abs(g64).max() < 1e-6
 
 
-def test_config4_full_size_gradient_against_finite_differences():
+def test_bcc_adjoint_24x24x12_full_size_gradient_against_finite_differences():
     """The 24x24x12 sigmoid-mask lattice (6,912 cells of 6^3 Q1, 7.1M DOF): dc/dr over every cell,
     mixed forward and adjoint, against the FP64 gradient (<= 1e-6 relative), and the FP64
     gradient against central differences (h = 1e-5, FP64 solves to 1e-12) on the 16 cells the
     workload draws for that check."""
     from paper_2308_11371_gb300 import autograd, binding
-    prob = W.config4()
+    prob = W.bcc_adjoint_24x24x12()
     r0 = np.array(prob.r_cell, dtype=np.float64)
     fd_cells = prob.extra["fd_cells"]
     opts64 = {"tol_outer": 1e-12, "restart": 10, "max_outer": 100}

@@ -83,11 +83,11 @@ def test_batch_of_one_is_the_single_lattice_solve():
     assert torch.equal(u1, u2) and i1["outer_its"] == i2["outer_its"]
 
 
-def test_batch_of_config3_recipe_lattices_matches_each_lattice():
+def test_batch_of_bcc_batch_32_recipe_lattices_matches_each_lattice():
     """Four lattices of uneven size drawn with the 32-lattice workload's recipe (6^3 BCC cells with
     per-cell random radii, shear + bend, three load cases), solved as one mixed-precision batch:
     each lattice's displacement within 1e-6 of its own monolithic solution at residual 1e-8."""
     from paper_2308_11371_gb300 import binding
-    probs = W.config3_sample()
+    probs = W.bcc_batch_sample()
     assert len({q.cells for q in probs}) > 1 and all(q.elems == 6 and q.n_rhs == 3 for q in probs)
     _check_against_monolithic(probs, binding.FETIDP_MIXED_BF16, 1e-8, 1e-6)

@@ -35,7 +35,7 @@ def _status(fn, *a):
 
 @pytest.mark.parametrize("bad", [float("nan"), float("inf")])
 def test_non_finite_inputs_are_rejected(bad):
-    s = _solver(W.config1())
+    s = _solver(W.frame_2d_4x4())
     lam = torch.zeros(s.n_rhs, s.L, dtype=torch.float64, device="cuda")
     lam[0, s.L // 3] = bad
     assert _status(s.apply_F, lam) == EINVAL
@@ -59,7 +59,7 @@ def test_non_finite_inputs_are_rejected(bad):
 def test_void_without_stiffness_is_singular():
     """E_void = 0 leaves the nodes inside the voids without stiffness: the principal K_rr has
     zero pivots and setup answers FETIDP_ESINGULAR."""
-    p = W.config1()
+    p = W.frame_2d_4x4()
     p.E_void = 0.0
     p.r_cell = np.full(p.n_cells, 0.03)        # thin struts: 8 nodes per cell touch only void
     from paper_2308_11371_gb300 import binding
@@ -69,7 +69,7 @@ def test_void_without_stiffness_is_singular():
 
 
 def test_iteration_limit_reports_not_converged_with_info():
-    s = _solver(W.config1(), max_outer=1, tol_outer=1e-14)
+    s = _solver(W.frame_2d_4x4(), max_outer=1, tol_outer=1e-14)
     u, lam, info = s.solve(allow_notconv=True)
     assert info["status"] == ENOTCONV
     assert info["outer_its"] == 1 and info["inner_its_total"] > 0
@@ -102,7 +102,7 @@ def test_expired_device_wait_reports_timeout_and_the_process_recovers():
     st, waited = binding.wait_selfcheck(1)                     # expires at its first check
     assert st == ETIMEOUT and waited < 2.0
     assert binding.wait_selfcheck(0)[0] == EINVAL
-    p = W.config1()
+    p = W.frame_2d_4x4()
     ok = _solver(p, precision=binding.FETIDP_MIXED_BF16)
     u, _, info = ok.solve()
     assert info["rel_residual"] <= 1e-8
@@ -112,7 +112,7 @@ def test_expired_device_wait_reports_timeout_and_the_process_recovers():
 def test_wait_budget_option_reaches_the_kernels():
     """A context's wait_budget_ns bounds its tensor-core waits; a generous budget changes nothing."""
     from paper_2308_11371_gb300 import binding
-    p = W.config1()
+    p = W.frame_2d_4x4()
     a = _solver(p, precision=binding.FETIDP_MIXED_BF16, wait_budget_ns=5_000_000_000)
     ua, _, ia = a.solve()
     b = _solver(p, precision=binding.FETIDP_MIXED_BF16)

@@ -40,7 +40,7 @@ def oracle(name):
     if name not in _OC:
         from oracle.discretization import Lattice
         from oracle import ifeti_dp
-        prob = {"cfg1": W.config1(),
+        prob = {"frame4x4": W.frame_2d_4x4(),
                 "ragged2d": W.lattice_2d(12, 7, 6, a=0.9, r=0.12, r_grade=0.04, n_rb=5),
                 "bcc3d": W.lattice_3d(2, 2, 2, e=3, r=0.2, r_spread=0.06, seed=7, n_rb=4,
                                       map_kind=W.MAP_SHEAR_BEND_3D, map_params=(0.3, 2.0, 0.1, -0.15)),
@@ -56,7 +56,7 @@ def oracle(name):
 
 
 @pytest.mark.parametrize("split,tol", [(1, 3e-2), (3, 3e-4)])
-@pytest.mark.parametrize("name", ["cfg1", "ragged2d", "bcc3d", "bcc6"])
+@pytest.mark.parametrize("name", ["frame4x4", "ragged2d", "bcc3d", "bcc6"])
 def test_mixed_interface_operators(name, split, tol):
     prob, lat, fe = oracle(name)
     s = _mixed(prob, tc_split=split)
@@ -69,7 +69,7 @@ def test_mixed_interface_operators(name, split, tol):
         assert _rel(z[r], fe.apply_MD(lam[r])) < tol
 
 
-@pytest.mark.parametrize("name", ["cfg1", "ragged2d", "bcc3d", "bcc6"])
+@pytest.mark.parametrize("name", ["frame4x4", "ragged2d", "bcc3d", "bcc6"])
 def test_mixed_local_rom_solve(name):
     """Eq. 46 with an FP32 basis from the tensor cores: the Galerkin projection with the exact
     K_s keeps the solve a near-best approximation, so it matches the FP64 one closely."""
@@ -82,7 +82,7 @@ def test_mixed_local_rom_solve(name):
         assert _rel(x[r], fe.rom.local_rom_solve(v[r])) < 1e-3
 
 
-@pytest.mark.parametrize("name", ["cfg1", "ragged2d", "bcc3d", "bcc6"])
+@pytest.mark.parametrize("name", ["frame4x4", "ragged2d", "bcc3d", "bcc6"])
 def test_mixed_rom_data_matches_oracle(name):
     """The mixed setup's double-float greedy (Algorithm 4) and Eq. 42 traces select the oracle's
     principal cells and reproduce its FP64 alpha (Eq. 56) to 1e-10; pi and delta come from pivoted
@@ -100,7 +100,7 @@ _MONO = {}
 
 
 @pytest.mark.parametrize("split", [1, 3])
-@pytest.mark.parametrize("name", ["cfg1", "ragged2d", "bcc3d", "bcc6"])
+@pytest.mark.parametrize("name", ["frame4x4", "ragged2d", "bcc3d", "bcc6"])
 def test_mixed_solve_matches_monolithic(name, split):
     """Mixed precision at the FP64 outer residual 1e-8: displacement within 1e-7 of the oracle's
     monolithic solution, for every load case."""
@@ -117,14 +117,14 @@ def test_mixed_solve_matches_monolithic(name, split):
         assert _rel(uh[r], ref[r]) < 1e-7
 
 
-def test_mixed_config2_matches_monolithic_full_size():
+def test_mixed_frame_2d_64x64_matches_monolithic_full_size():
     """The 64x64 workload (32 principal cells, 2.37M cell-duplicated DOF) in mixed precision at
     outer residual 1e-8: its solution is continuous across every inter-cell row, satisfies local
     equilibrium on sampled cells (oracle stiffness and loads), and matches the oracle's monolithic
     solution (a sparse direct solve of all 2.10M unique DOF) element by element to 1e-7."""
     from oracle import monolithic
     from oracle.discretization import Lattice
-    prob = W.config2(n_rb=W.CONFIG2_SOLVE_N_RB)
+    prob = W.frame_2d_64x64(n_rb=W.FRAME_64X64_SOLVE_N_RB)
     s = _mixed(prob)
     u, lam, info = s.solve()
     assert info["rel_residual"] <= 1e-8 and info["outer_its"] <= 12
@@ -147,7 +147,7 @@ def test_mixed_config2_matches_monolithic_full_size():
     assert _rel(uh, ref) < 1e-7
 
 
-@pytest.mark.parametrize("name", ["cfg1", "ragged2d", "bcc3d"])
+@pytest.mark.parametrize("name", ["frame4x4", "ragged2d", "bcc3d"])
 def test_mixed_assembled_and_principal_forms(name):
     """F_dd_ring and S_dd_ring applied in every mixed form -- the principal form on the tensor cores
     (three BF16 products), assembled per cell in FP32 with dense rows, and assembled as packed
@@ -173,7 +173,7 @@ def test_mixed_assembled_and_principal_forms(name):
         assert _rel(out[2][0][r], out[1][0][r]) < 1e-5 and _rel(out[2][1][r], out[1][1][r]) < 1e-5
 
 
-@pytest.mark.parametrize("name", ["cfg1", "bcc3d"])
+@pytest.mark.parametrize("name", ["frame4x4", "bcc3d"])
 def test_mixed_inner_pcg_runs_as_one_graph(name):
     """The inner PCG iterations of the mixed path (with the one-launch cooperative coarse solve of
     their coarse term) are captured and replayed as a CUDA graph: the solve reports it, and the host

@@ -63,7 +63,7 @@ BCC6 = W.lattice_3d(2, 2, 2, e=6, r=0.2, r_spread=0.06, seed=8, n_rb=4, mask_kin
 def case(name):
     if name not in _CASES:
         probs = {
-            "cfg1": W.config1(),
+            "frame4x4": W.frame_2d_4x4(),
             "ragged2d": W.lattice_2d(12, 7, 6, a=0.9, r=0.12, r_grade=0.04, n_rb=5),
             "bcc3d": W.lattice_3d(2, 2, 2, e=3, r=0.2, r_spread=0.06, seed=7, n_rb=4,
                                   map_kind=W.MAP_SHEAR_BEND_3D, map_params=(0.3, 2.0, 0.1, -0.15),
@@ -78,7 +78,7 @@ def case(name):
     return _CASES[name]
 
 
-@pytest.mark.parametrize("name", ["cfg1", "ragged2d", "bcc3d", "bcc6"])
+@pytest.mark.parametrize("name", ["frame4x4", "ragged2d", "bcc3d", "bcc6"])
 def test_sizes_and_rom_selection(name):
     oc = case(name)
     s = _solver(oc.prob)
@@ -92,7 +92,7 @@ def test_sizes_and_rom_selection(name):
     assert _rel(delta, oc.rom.delta) < 1e-9
 
 
-@pytest.mark.parametrize("name", ["cfg1", "bcc3d"])
+@pytest.mark.parametrize("name", ["frame4x4", "bcc3d"])
 def test_gather_scatter_bit_exact(name):
     oc = case(name)
     s = _solver(oc.prob)
@@ -108,7 +108,7 @@ def test_gather_scatter_bit_exact(name):
         assert np.array_equal(z[r], oc.lat.Bd @ yd[r].ravel())
 
 
-@pytest.mark.parametrize("name", ["cfg1", "ragged2d", "bcc3d"])
+@pytest.mark.parametrize("name", ["frame4x4", "ragged2d", "bcc3d"])
 def test_apply_K_matches_assembled_stiffness(name):
     oc = case(name)
     s = _solver(oc.prob)
@@ -121,7 +121,7 @@ def test_apply_K_matches_assembled_stiffness(name):
             assert _rel(y[r, c], ref) < 1e-12
 
 
-@pytest.mark.parametrize("name", ["cfg1", "ragged2d", "bcc3d", "bcc6"])
+@pytest.mark.parametrize("name", ["frame4x4", "ragged2d", "bcc3d", "bcc6"])
 def test_coarse_solve_matches_oracle(name):
     oc = case(name)
     s = _solver(oc.prob)
@@ -132,7 +132,7 @@ def test_coarse_solve_matches_oracle(name):
         assert _rel(x[r], oc.rom.coarse_solve(b[r])) < 1e-9
 
 
-@pytest.mark.parametrize("name", ["cfg1", "ragged2d", "bcc3d", "bcc6"])
+@pytest.mark.parametrize("name", ["frame4x4", "ragged2d", "bcc3d", "bcc6"])
 def test_interface_operator_and_dirichlet_preconditioner(name):
     oc = case(name)
     s = _solver(oc.prob)
@@ -145,7 +145,7 @@ def test_interface_operator_and_dirichlet_preconditioner(name):
         assert _rel(z[r], oc.ifeti.apply_MD(lam[r])) < 1e-11
 
 
-@pytest.mark.parametrize("name", ["cfg1", "ragged2d", "bcc3d", "bcc6"])
+@pytest.mark.parametrize("name", ["frame4x4", "ragged2d", "bcc3d", "bcc6"])
 def test_local_rom_solve_matches_oracle(name):
     oc = case(name)
     s = _solver(oc.prob)
@@ -156,7 +156,7 @@ def test_local_rom_solve_matches_oracle(name):
         assert _rel(x[r], oc.rom.local_rom_solve(v[r])) < 1e-9
 
 
-@pytest.mark.parametrize("name", ["cfg1", "bcc3d", "bcc6"])
+@pytest.mark.parametrize("name", ["frame4x4", "bcc3d", "bcc6"])
 def test_saddle_operator_matches_oracle(name):
     oc = case(name)
     s = _solver(oc.prob)
@@ -167,7 +167,7 @@ def test_saddle_operator_matches_oracle(name):
         assert _rel(y[r], oc.ifeti.A(x[r])) < 1e-12
 
 
-@pytest.mark.parametrize("name", ["cfg1", "bcc3d"])
+@pytest.mark.parametrize("name", ["frame4x4", "bcc3d"])
 def test_block_preconditioner_iterate_locked(name):
     """Algorithm 1 with the same fixed number of inner PCG iterations on both sides."""
     oc = case(name)
@@ -186,7 +186,7 @@ def _mono_cells(oc):
     return monolithic.to_cells(oc.lat, monolithic.solve(oc.lat))
 
 
-@pytest.mark.parametrize("name,J,K", [("cfg1", 4, 30), ("ragged2d", 4, 30), ("bcc3d", 2, 80),
+@pytest.mark.parametrize("name,J,K", [("frame4x4", 4, 30), ("ragged2d", 4, 30), ("bcc3d", 2, 80),
                                      ("bcc6", 2, BCC6_K)])
 def test_solve_iterate_locked_matches_oracle(name, J, K):
     """Same fixed outer/inner iteration counts: the FP64 GPU iterate equals the oracle's.
@@ -208,7 +208,7 @@ def test_solve_iterate_locked_matches_oracle(name, J, K):
         assert _rel(u[r], ref) < 1e-10
 
 
-@pytest.mark.parametrize("name", ["cfg1", "ragged2d", "bcc3d", "bcc6"])
+@pytest.mark.parametrize("name", ["frame4x4", "ragged2d", "bcc3d", "bcc6"])
 def test_solve_converges_to_monolithic(name):
     oc = case(name)
     s = _solver(oc.prob, tol_outer=1e-11)
@@ -223,13 +223,13 @@ def test_solve_converges_to_monolithic(name):
     assert abs(info["outer_its"] - oc.ifeti.outer_its) <= 2
 
 
-def test_config2_with_8_principal_cells_stagnates_like_the_oracle():
+def test_frame_2d_64x64_with_8_principal_cells_stagnates_like_the_oracle():
     """The 64x64 lattice's 8-principal-cell ROM cannot represent the hard-mask radius grading:
     on a 64x2 strip of the same cells, 30 outer iterations leave the residual above 0.3 on the
     GPU and on the oracle alike."""
     from oracle.discretization import Lattice
     from oracle import ifeti_dp
-    p = W.lattice_2d(64, 2, 16, a=W.config2().map_params[0], r=0.1, n_rb=8, r_grade=0.05)
+    p = W.lattice_2d(64, 2, 16, a=W.frame_2d_64x64().map_params[0], r=0.1, n_rb=8, r_grade=0.05)
     s = _solver(p, max_outer=30, restart=30)
     u, lam, info = s.solve(allow_notconv=True)
     assert info["status"] == -4 and info["rel_residual"] > 0.3
@@ -249,7 +249,7 @@ def test_identical_cells_single_outer_iteration():
 
 
 def test_solve_host_matches_device():
-    oc = case("cfg1")
+    oc = case("frame4x4")
     s = _solver(oc.prob)
     u, lam, info = s.solve()
     uh = np.empty((s.n_rhs, s.N, s.n_dof))
@@ -275,11 +275,11 @@ def test_gradient_matches_oracle():
     assert _rel(g, adjoint.gradient(lat, uo)) < 1e-6
 
 
-def test_config2_full_size_properties():
+def test_frame_2d_64x64_full_size_properties():
     """64x64 cells of 16x16 Q1 (2.37M DOF): exact maps on the full lattice, K_s on sampled cells,
     and a converged solve that satisfies sampled equilibrium and continuity rows."""
     from oracle.discretization import Lattice
-    prob = W.config2(n_rb=W.CONFIG2_SOLVE_N_RB)
+    prob = W.frame_2d_64x64(n_rb=W.FRAME_64X64_SOLVE_N_RB)
     lat = Lattice(prob)
     s = _solver(prob)
     assert (s.N, s.L, s.n_P) == (4096, lat.L, lat.n_P) == (4096, 243840, 8320)
@@ -308,7 +308,7 @@ def test_config2_full_size_properties():
         assert np.abs(res - f).max() < 1e-6 * fscale
 
 
-@pytest.mark.parametrize("name", ["cfg1", "ragged2d", "bcc3d"])
+@pytest.mark.parametrize("name", ["frame4x4", "ragged2d", "bcc3d"])
 def test_rom_dirichlet_preconditioner_matches_oracle(name):
     """M_D^{-ROM} (Eq. 47): ROM interior solves from the principal K_ii^{-1}; the pivoted Gram
     solve sits behind it, hence the 1e-9 bound of the factorised quantities."""
@@ -321,7 +321,7 @@ def test_rom_dirichlet_preconditioner_matches_oracle(name):
         assert _rel(z[k], oc.ifeti.apply_MD_rom(r[k])) < 1e-9
 
 
-@pytest.mark.parametrize("name", ["cfg1", "bcc3d"])
+@pytest.mark.parametrize("name", ["frame4x4", "bcc3d"])
 def test_rom_dirichlet_interface_solve_converges_to_monolithic(name):
     """Algorithm 1 with F_ring^{-1} ~ M_D^{-ROM} instead of the inner PCG still reaches the
     monolithic solution; it needs more outer iterations and no inner ones."""
@@ -337,7 +337,7 @@ def test_rom_dirichlet_interface_solve_converges_to_monolithic(name):
     assert info["outer_its"] > info_pcg["outer_its"]
 
 
-@pytest.mark.parametrize("name", ["cfg1", "bcc3d"])
+@pytest.mark.parametrize("name", ["frame4x4", "bcc3d"])
 def test_standard_fetidp_on_gpu(name):
     """method = 1, the paper's comparison system (Sec. 2.2.4): every cell's own K_rr^{-1}.  The block
     preconditioner of Eq. 44 is then exact, so FGMRES takes one outer iteration and its inner PCG

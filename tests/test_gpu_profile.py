@@ -29,7 +29,7 @@ def _solve(prob, precision, classes=None, **opts):
 def test_profiling_keeps_the_solution_and_times_every_class(prec):
     from paper_2308_11371_gb300 import binding
     precision = binding.FETIDP_FP64 if prec == "fp64" else binding.FETIDP_MIXED_BF16
-    prob = W.config1()
+    prob = W.frame_2d_4x4()
     u0, i0, _ = _solve(prob, precision, tol_outer=1e-8)
     u1, i1, prof = _solve(prob, precision, classes=list(binding.KCLASS), tol_outer=1e-8)
     assert torch.equal(u0, u1)
@@ -48,7 +48,7 @@ def test_profiling_keeps_the_solution_and_times_every_class(prec):
 def test_profile_of_one_class_matches_the_all_class_profile():
     """Profiling one class only (another graph capture) counts the same launches and flops."""
     from paper_2308_11371_gb300 import binding
-    prob = W.config1()
+    prob = W.frame_2d_4x4()
     _, _, pall = _solve(prob, binding.FETIDP_MIXED_BF16, classes=list(binding.KCLASS), tol_outer=1e-8)
     _, _, pone = _solve(prob, binding.FETIDP_MIXED_BF16, classes=["tc_gemm"], tol_outer=1e-8)
     assert pone["tc_gemm"]["launches"] == pall["tc_gemm"]["launches"]
@@ -58,7 +58,7 @@ def test_profile_of_one_class_matches_the_all_class_profile():
 
 def test_fixed_inner_count_runs_eagerly_and_profiles():
     from paper_2308_11371_gb300 import binding
-    prob = W.config1()
+    prob = W.frame_2d_4x4()
     _, info, prof = _solve(prob, binding.FETIDP_FP64, classes=["vector"], fixed_inner=20, tol_outer=1e-8)
     assert info["inner_its_total"] > 0 and info["inner_its_total"] % 20 == 0
     assert prof["vector"]["launches"] > 0 and prof["vector"]["ms"] > 0.0

@@ -22,8 +22,8 @@ def test_reference_cell_counts(dim, e, n, ni, nd, npp):
     assert ref.n_p == dim * 2 ** dim
 
 
-def test_config1_sizes():
-    lat = Lattice(W.config1())
+def test_frame_2d_4x4_sizes():
+    lat = Lattice(W.frame_2d_4x4())
     assert (lat.N, lat.L, lat.n_P) == (16, 392, 40)
     # 2D: interior vertical edges 3*4*7 nodes, horizontal 4*3*7, clamped face 4 cells*7 nodes
     assert lat.L == 2 * (3 * 4 * 7 + 4 * 3 * 7 + 4 * 7)
@@ -162,7 +162,7 @@ def test_load_resultants():
     assert np.allclose(F4, [0.0, 0.0, 6.0], atol=1e-13)
 
 
-@pytest.mark.parametrize("prob", [W.config1(), W.lattice_3d(2, 2, 2, e=2)])
+@pytest.mark.parametrize("prob", [W.frame_2d_4x4(), W.lattice_3d(2, 2, 2, e=2)])
 def test_jump_operator_brute_force(prob):
     """Every B row couples copies of ONE physical node (or clamps a node); B kills continuous
     fields off the Dirichlet rows; B has full row rank; A_p^T reproduces corner values."""
@@ -206,7 +206,7 @@ def test_jump_operator_brute_force(prob):
 def test_dirichlet_scaling_2d_is_one_half():
     """In 2D every inter-cell row couples exactly two copies: D = 1/2 there, 1 on Dirichlet
     rows, and nothing off the diagonal (Eq. 30)."""
-    lat = Lattice(W.config1())
+    lat = Lattice(W.frame_2d_4x4())
     D = lat.Dmat.toarray()
     assert np.array_equal(D, np.diag(np.diag(D)))
     assert np.all(np.diag(D)[lat.row_dirichlet] == 1.0)
@@ -233,7 +233,7 @@ def test_dirichlet_scaling_3d_edge_block():
     assert len(rows1) > 0 and np.all(np.diag(D)[rows1] == 0.5)
 
 
-@pytest.mark.parametrize("prob", [W.config1(), W.lattice_3d(2, 2, 2, e=2, r=0.25)])
+@pytest.mark.parametrize("prob", [W.frame_2d_4x4(), W.lattice_3d(2, 2, 2, e=2, r=0.25)])
 def test_dirichlet_scaling_meets_eq30_and_projects(prob):
     """sum_s B_d^(s) B_d^(s)T D = I_L (Eq. 30), and P_D = B^T D B is an orthogonal projection
     (P_D^2 = P_D, symmetric) that leaves every jump B w unchanged."""

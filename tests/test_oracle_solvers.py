@@ -14,12 +14,12 @@ def _mono_cells(lat):
 
 
 @pytest.fixture(scope="module")
-def cfg1():
-    lat = Lattice(W.config1())
+def frame4x4():
+    lat = Lattice(W.frame_2d_4x4())
     return lat, feti_dp.StandardFETIDP(lat)
 
 
-@pytest.mark.parametrize("prob", [W.config1(),
+@pytest.mark.parametrize("prob", [W.frame_2d_4x4(),
                                   W.lattice_3d(2, 2, 2, e=3, r=0.2, r_spread=0.05, seed=3,
                                                map_kind=W.MAP_SHEAR_BEND_3D,
                                                map_params=(0.2, 2.0, 0.1, -0.1))])
@@ -32,16 +32,16 @@ def test_standard_fetidp_equals_monolithic(prob):
     assert np.abs(u - ref).max() <= 1e-11 * np.abs(ref).max()
 
 
-def test_interface_operator_spd(cfg1):
+def test_interface_operator_spd(frame4x4):
     """F = B K^{-1} B^T (Eq. 26) is symmetric positive definite (B full rank, K SPD)."""
-    lat, fd = cfg1
+    lat, fd = frame4x4
     F = np.stack([fd.apply_F(e) for e in np.eye(lat.L)], axis=1)
     assert np.abs(F - F.T).max() < 1e-12 * np.abs(F).max()
     assert np.linalg.eigvalsh(0.5 * (F + F.T)).min() > 0.0
 
 
-def test_saddle_point_residual_of_fetidp_solution(cfg1):
-    lat, fd = cfg1
+def test_saddle_point_residual_of_fetidp_solution(frame4x4):
+    lat, fd = frame4x4
     uR, uP, lam, _ = fd.solve(tol=1e-13)
     A = feti_dp.saddle_operator(lat, fd.blocks)
     b = feti_dp.saddle_rhs(lat, fd.blocks, 0)
@@ -49,9 +49,9 @@ def test_saddle_point_residual_of_fetidp_solution(cfg1):
     assert np.linalg.norm(A(x) - b) < 1e-10 * np.linalg.norm(b)
 
 
-def test_dirichlet_schur_is_inverse_neumann_schur(cfg1):
+def test_dirichlet_schur_is_inverse_neumann_schur(frame4x4):
     """S_dd = F_dd^{-1} (Sec. 3.1.1): Dirichlet Schur from K_ii^{-1}, F_dd from K_rr^{-1}."""
-    lat, fd = cfg1
+    lat, fd = frame4x4
     R = rom.ROM(lat, blocks=fd.blocks)
     for k, s in enumerate(R.sigma):
         assert np.allclose(fd.Sdd[s] @ R.Fdd[k], np.eye(lat.ref.n_d), atol=1e-9)
@@ -72,15 +72,15 @@ def test_greedy_on_hand_made_snapshots():
 
 
 @pytest.fixture(scope="module")
-def cfg1_rom():
-    lat = Lattice(W.config1())
+def frame4x4_rom():
+    lat = Lattice(W.frame_2d_4x4())
     blocks = [feti_dp.CellBlocks(lat, s) for s in range(lat.N)]
     return lat, blocks, rom.ROM(lat, blocks=blocks)
 
 
-def test_greedy_interpolation_and_orthonormality(cfg1_rom):
+def test_greedy_interpolation_and_orthonormality(frame4x4_rom):
     """Eq. 55 (interpolation at principal cells) and Z^T Z = I."""
-    lat, _, R = cfg1_rom
+    lat, _, R = frame4x4_rom
     assert np.allclose(R.Z.T @ R.Z, np.eye(R.n_rb), atol=1e-13)
     for k, s in enumerate(R.sigma):
         ring = R.norms[s] * R.Z @ R.beta[s]
@@ -88,17 +88,17 @@ def test_greedy_interpolation_and_orthonormality(cfg1_rom):
         assert np.allclose(R.alpha[s], np.eye(R.n_rb)[k], atol=1e-12)
 
 
-def test_projection_coefficients_on_principal_cells(cfg1_rom):
+def test_projection_coefficients_on_principal_cells(frame4x4_rom):
     """Eqs. 41-42 on a principal cell reproduce its own operators: pi = delta = e_k."""
-    lat, _, R = cfg1_rom
+    lat, _, R = frame4x4_rom
     for k, s in enumerate(R.sigma):
         assert np.allclose(R.pi[s], np.eye(R.n_rb)[k], atol=1e-9)
         assert np.allclose(R.delta[s], np.eye(R.n_rb)[k], atol=1e-9)
 
 
-def test_rom_local_solve_exact_on_principal_cells(cfg1_rom):
+def test_rom_local_solve_exact_on_principal_cells(frame4x4_rom):
     """Eq. 46b: K_rr^(s)^{-1} v lies in span(R) when s is principal, so the ROM solve is exact."""
-    lat, blocks, R = cfg1_rom
+    lat, blocks, R = frame4x4_rom
     rng = np.random.default_rng(2)
     v = rng.standard_normal((lat.N, lat.ref.n_r))
     x = R.local_rom_solve(v)
@@ -107,9 +107,9 @@ def test_rom_local_solve_exact_on_principal_cells(cfg1_rom):
         assert np.allclose(x[s], exact, rtol=1e-8, atol=1e-10 * np.abs(exact).max())
 
 
-def test_rom_local_solve_is_energy_projection(cfg1_rom):
+def test_rom_local_solve_is_energy_projection(frame4x4_rom):
     """Eq. 46b for a non-principal cell: the error is K_rr-orthogonal to span(R)."""
-    lat, blocks, R = cfg1_rom
+    lat, blocks, R = frame4x4_rom
     s = [c for c in range(lat.N) if c not in set(R.sigma)][0]
     rng = np.random.default_rng(3)
     v = rng.standard_normal((lat.N, lat.ref.n_r))
@@ -159,7 +159,7 @@ def test_all_cells_principal_is_exact():
 
 
 def test_inexact_fetidp_converges_to_monolithic():
-    lat = Lattice(W.config1())
+    lat = Lattice(W.frame_2d_4x4())
     s = ifeti_dp.InexactFETIDP(lat)
     uR, uP, lam, res = s.solve(tol=1e-10)
     assert res < 1e-10 and s.outer_its > 1
@@ -205,7 +205,7 @@ def test_adjoint_gradient_matches_central_differences():
 
 def test_compliance_equals_strain_energy_twice():
     """At equilibrium f^T u = u^T K u."""
-    lat = Lattice(W.config1())
+    lat = Lattice(W.frame_2d_4x4())
     u = _mono_cells(lat)
     c = adjoint.compliance(lat, u)[0]
     e = sum(u[0, s] @ (lat.stiffness(s) @ u[0, s]) for s in range(lat.N))
@@ -213,16 +213,16 @@ def test_compliance_equals_strain_energy_twice():
 
 
 def test_hard_mask_gradient_vanishes():
-    lat = Lattice(W.config1())
+    lat = Lattice(W.frame_2d_4x4())
     u = _mono_cells(lat)
     assert np.all(adjoint.gradient(lat, u) == 0.0)
 
 
 @pytest.mark.parametrize("prob", [
-    W.config1(),
+    W.frame_2d_4x4(),
     W.lattice_3d(2, 2, 2, e=2, r=0.25, r_spread=0.05, seed=2),
     W.lattice_3d(2, 2, 3, e=3, r=0.2, r_spread=0.05, seed=2, mask_kind=W.MASK_BCC_SIGMOID),
-], ids=["cfg1", "bcc_2x2x2_e2", "bcc_sigmoid_2x2x3_e3"])
+], ids=["frame4x4", "bcc_2x2x2_e2", "bcc_sigmoid_2x2x3_e3"])
 def test_dirichlet_preconditioned_spectrum_lower_bound(prob):
     """FETI-DP theory (Mandel-Tezaur; Klawonn-Widlund): when B_D^T B is a projection, every
     eigenvalue of M_D^{-1} F is >= 1 (Eqs. 26, 30).  A scaling that violates Eq. 30's condition
