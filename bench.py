@@ -78,23 +78,12 @@ def workload_problem(name):
 
 def sample_problem(name, cells):
     """The cells [0, cells) of the workload lattice (same cell, mask, radii, macro map and load
-    kinds): a bounded sample for the CPU oracle."""
-    import numpy as np
-    full = workload_problem(name)
-    nx, ny, nz = cells
-    fx, fy, fz = full.cells
-    idx = np.arange(fz)[:nz, None, None] * fy * fx + np.arange(fy)[None, :ny, None] * fx + \
-        np.arange(fx)[None, None, :nx]
-    q = type(full)(**{k: getattr(full, k) for k in full.__dataclass_fields__})
-    q.cells = (nx, ny, nz)
-    q.r_cell = np.asarray(full.r_cell)[idx.ravel()]
-    q.n_rb = min(full.n_rb, nx * ny * nz)
-    q.name = f"{full.name}_sample_{nx}x{ny}x{nz}"
-    q.extra = {}
-    return q
+    kinds): a bounded sample for the CPU oracle and for profiling runs."""
+    from paper_2308_11371_gb300 import workloads as W
+    return W.corner(workload_problem(name), cells)
 
 
-SAMPLES = {"bcc_3d_32x32x16": {"cpu": (2, 2, 2), "reference": (2, 2, 1)},
+SAMPLES = {"bcc_3d_32x32x16": {"cpu": (4, 4, 2), "reference": (2, 2, 1)},
            "bcc_adjoint_24x24x12": {"cpu": (2, 2, 2), "reference": (2, 2, 1)},
            "frame_2d_64x64": {"cpu": (16, 16, 1), "reference": (12, 12, 1)}}
 

@@ -166,6 +166,10 @@ typedef struct {
                                the block preconditioner of Eq. 44 is exact, so FGMRES takes one
                                outer iteration and the inner PCG is standard FETI-DP's.  FP64 with
                                interface 0 only; fetidp_rom_data answers EINVAL (0)           */
+  int tc_bn;                /* mixed path: column-tile width of the Eq. 46a tensor-core GEMM, 64,
+                               128 or 256; 0 = the library's rule (the widest tile that still
+                               gives a wave of CTAs).  fetidp_tc_time measures the candidates and
+                               the Python tuner stores the best per problem shape (0)          */
 } fetidp_options;
 
 typedef struct {
@@ -378,6 +382,13 @@ fetidp_status fetidp_tc_selfcheck_static(int M, int K, int N, double *rel_err, v
  * the wait completed, which it cannot.  stream: cudaStream_t or NULL; the call synchronises it.
  * waited_s (host, may be NULL): wall time of the call.  The flag it uses is one static device int
  * of this library, so calls that overlap in time race on it.  EINVAL for a budget out of range. */
+/* Mean device time (ms, CUDA events on the context's stream) of `reps` launches of the context's
+ * Eq. 46a tensor-core GEMM (all principal inverses against every cell's column, into the local
+ * bases' buffer) with column-tile width bn (64, 128 or 256), after one untimed launch.  Mixed
+ * contexts only (EINVAL otherwise); the inputs are the context's workspace, so the call changes no
+ * solver state that a later solve reads.  Synchronises the stream.                               */
+fetidp_status fetidp_tc_time(fetidp_ctx *ctx, int bn, int reps, double *ms);
+
 fetidp_status fetidp_wait_selfcheck(long long wait_budget_ns, void *stream, double *waited_s);
 
 /* Number of kernels this library has launched in the calling process. *//* Number of kernels this library has launched in the calling process. */

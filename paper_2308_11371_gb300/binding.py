@@ -31,7 +31,7 @@ SYMBOLS = ["fetidp_sizes", "fetidp_default_options", "fetidp_setup", "fetidp_app
            "fetidp_profile_read", "fetidp_kernel_launches", "fetidp_tc_selfcheck",
            "fetidp_tc_comb_selfcheck", "fetidp_tc_selfcheck_static",
            "fetidp_compliance", "fetidp_batch_layout", "fetidp_wait_selfcheck",
-           "fetidp_precond_rom"]
+           "fetidp_precond_rom", "fetidp_tc_time"]
 
 KCLASS = {"grouped_gemm": 0, "apply_K": 1, "maps": 2, "coarse": 3, "cell_gemv": 4, "vector": 5,
           "gram": 6, "tc_gemm": 7, "setup": 8, "sweep": 9, "traces": 10, "greedy": 11, "multi_K": 12,
@@ -67,7 +67,8 @@ class Options(ctypes.Structure):
                 ("tol_inner_mixed", ctypes.c_double), ("gram_drop_mixed", ctypes.c_double),
                 ("profile_mask", ctypes.c_uint), ("restart", ctypes.c_int),
                 ("wait_budget_ns", ctypes.c_longlong), ("check_inputs", ctypes.c_int),
-                ("mixed_assembled", ctypes.c_int), ("interface", ctypes.c_int), ("method", ctypes.c_int)]
+                ("mixed_assembled", ctypes.c_int), ("interface", ctypes.c_int), ("method", ctypes.c_int),
+                ("tc_bn", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -142,6 +143,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.fetidp_tc_selfcheck_static.argtypes = [I, I, I, ctypes.POINTER(ctypes.c_double), V]
     lib.fetidp_wait_selfcheck.restype = I
     lib.fetidp_wait_selfcheck.argtypes = [ctypes.c_longlong, V, ctypes.POINTER(ctypes.c_double)]
+    lib.fetidp_tc_time.restype = I
+    lib.fetidp_tc_time.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     lib.fetidp_kernel_launches.restype = ctypes.c_longlong
     lib.fetidp_kernel_launches.argtypes = []
     _LIB = lib
@@ -222,6 +225,9 @@ class Solver:
         probs = list(problem) if isinstance(problem, (list, tuple)) else [problem]
         self.problem = problem
         self.n_lattices = len(probs)
+        if precision == FETIDP_MIXED_BF16 and "tc_bn" not in opts:
+            from . import tune   # the measured tile width of this problem shape, if tabulated
+            opts = dict(opts, tc_bn=tune.table_choice(probs))
         self.options = default_options(precision=precision, **opts)
         st = stream if stream is not None else torch.cuda.current_stream()
         self.stream = st
@@ -255,6 +261,12 @@ class Solver:
 
     def precond(self, r, out=None):
         return self._call2("fetidp_precond", r, out if out is not None else self._empty(self.n_rhs, self.L))
+
+    def tc_time(self, bn: int, reps: int = 3) -> float:
+        """Mean device time (ms) of this context's Eq. 46a tensor-core GEMM at column-tile width bn."""
+        ms = ctypes.c_double(0.0)
+        _check(load().fetidp_tc_time(self._h, int(bn), int(reps), ctypes.byref(ms)))
+        return ms.value
 
     def precond_rom(self, r, out=None):
         """M_D^{-ROM} r (Eq. 47); needs a context set up with interface=1."""

@@ -231,6 +231,10 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
   if (o.mixed_assembled < -1 || o.mixed_assembled > 2) { set_error("mixed_assembled must be -1, 0, 1 or 2"); return FETIDP_EINVAL; }
   if (o.interface < 0 || o.interface > 1) { set_error("interface must be 0 or 1"); return FETIDP_EINVAL; }
   if (o.method < 0 || o.method > 1) { set_error("method must be 0 or 1"); return FETIDP_EINVAL; }
+  if (o.tc_bn != 0 && o.tc_bn != 64 && o.tc_bn != 128 && o.tc_bn != 256) {
+    set_error("tc_bn must be 0, 64, 128 or 256");
+    return FETIDP_EINVAL;
+  }
   if (o.method == 1 && (o.precision != FETIDP_FP64 || o.interface != 0)) {
     set_error("standard FETI-DP (method 1) runs in FP64 with the PCG interface solve");
     return FETIDP_EINVAL;
@@ -822,11 +826,10 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
         return FETIDP_EINVAL;
       }
     size_t mx = 0;
-    {
+    for (int bn : {64, 128, 256}) {   // room for every tile width (fetidp_tc_time, option tc_bn)
       const TcOperator* op = &c.opKinv;
-      const int bn = tc_bn_for(ncols, op->m_tiles, op->nops);
       const long long n_tiles = (ncols + bn - 1) / bn;
-      mx = (size_t)n_tiles * op->k_tiles * bn * 64 * 2;
+      mx = std::max(mx, (size_t)n_tiles * op->k_tiles * bn * 64 * 2);
     }
     for (const TcComb* cb : {&c.cFdd, &c.cSdd, &c.cUrdT, &c.cUrd})
       mx = std::max(mx, tc_comb_staging_bytes(*cb, ncols));

@@ -870,6 +870,7 @@ void fetidp_default_options(fetidp_options* o) {
   o->mixed_assembled = -1;
   o->interface = 0;
   o->method = 0;
+  o->tc_bn = 0;
 }
 
 const char* fetidp_status_string(fetidp_status s) {
@@ -947,6 +948,48 @@ fetidp_status fetidp_tc_selfcheck_static(int M, int K, int N, double* rel_err, v
   FD_CUDA(cudaGetDevice(&c.device));
   c.stream = static_cast<cudaStream_t>(stream);
   return tc_selfcheck_static(c, M, K, N, rel_err);
+}
+
+fetidp_status fetidp_tc_time(fetidp_ctx* ctx, int bn, int reps, double* ms) {
+  FD_TRY(enter(ctx));
+  Ctx& c = ctx->c;
+  if (!ms || reps < 1 || (bn != 64 && bn != 128 && bn != 256)) {
+    set_error("fetidp_tc_time: bn must be 64, 128 or 256, reps >= 1, ms non-null");
+    return FETIDP_EINVAL;
+  }
+  if (!c.mixed || c.exact || !c.opKinv.tiles) {
+    set_error("fetidp_tc_time: a mixed-precision ROM context is required");
+    return FETIDP_EINVAL;
+  }
+  // the Eq. 46a GEMM of the local ROM solve, on zeroed workspace columns, into the bases' buffer
+  const int m = c.m, nr = c.nr, nrb = c.nrb;
+  const long long rs = c.N * nrb * nr;
+  float* Rf = reinterpret_cast<float*>(c.w_R);
+  FD_CUDA(cudaMemsetAsync(c.w_cell_a, 0, sizeof(double) * (size_t)m * c.N * nr, c.stream));
+  const CCellVec vR{c.w_cell_a, c.N * nr, nr};
+  const int saved = c.opt.tc_bn;
+  c.opt.tc_bn = bn;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  fetidp_status st = FETIDP_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    set_error("fetidp_tc_time: event creation failed");
+    st = FETIDP_ECUDA;
+  }
+  if (st == FETIDP_OK) st = tc_apply(c, c.opKinv, vR, nullptr, Rf, false, rs, nrb * nr, nr, 1.0, 0.0, m, c.N, m * rs);
+  if (st == FETIDP_OK && cudaEventRecord(e0, c.stream) != cudaSuccess) st = FETIDP_ECUDA;
+  for (int r = 0; r < reps && st == FETIDP_OK; ++r)
+    st = tc_apply(c, c.opKinv, vR, nullptr, Rf, false, rs, nrb * nr, nr, 1.0, 0.0, m, c.N, m * rs);
+  if (st == FETIDP_OK && cudaEventRecord(e1, c.stream) != cudaSuccess) st = FETIDP_ECUDA;
+  c.opt.tc_bn = saved;
+  if (st == FETIDP_OK && cudaEventSynchronize(e1) != cudaSuccess) st = FETIDP_ECUDA;
+  float t = 0.f;
+  if (st == FETIDP_OK && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) st = FETIDP_ECUDA;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st == FETIDP_ECUDA) set_error("fetidp_tc_time: CUDA event failure");
+  FD_TRY(st);
+  *ms = t / reps;
+  return check_waits(c, FETIDP_OK);
 }
 
 fetidp_status fetidp_wait_selfcheck(long long wait_budget_ns, void* stream, double* waited_s) {

@@ -854,7 +854,7 @@ fetidp_status tc_apply(Ctx& c, const TcOperator& op, CCellVec X, const double* c
                        double beta, int nrhs, long long ncell, long long y_ext) {
   const long long ncols = ncell * nrhs;
   const int batch = op.separate ? op.nops : 1;
-  const int BN = tc_bn_for(ncols, op.m_tiles, batch);
+  const int BN = c.opt.tc_bn > 0 ? c.opt.tc_bn : tc_bn_for(ncols, op.m_tiles, batch);
   const int n_tiles = (int)((ncols + BN - 1) / BN);
   const int nops_b = op.separate ? 1 : op.nops;
   const int k_tiles = nops_b * op.nterm * op.k_tiles_op;

@@ -225,4 +225,21 @@ def bcc_3d_32x32x16(seed: int = 5) -> LatticeProblem:
                 (a, float(nx), tau, ny / 2.0, nz / 2.0), loads, 16, "3d_32x32x16")
 
 
-WORKLOAD_FNS = {1: frame_2d_4x4, 2: frame_2d_64x64, 3: bcc_batch_32, 4: bcc_adjoint_24x24x12, 5: bcc_3d_32x32x16}
+WORKLOAD_FNS = {"frame_2d_4x4": frame_2d_4x4, "frame_2d_64x64": frame_2d_64x64,
+                "bcc_adjoint_24x24x12": bcc_adjoint_24x24x12, "bcc_3d_32x32x16": bcc_3d_32x32x16}
+
+
+def corner(full: LatticeProblem, cells) -> LatticeProblem:
+    """The cells [0, nx) x [0, ny) x [0, nz) of a lattice: the same cell, mask, radii, macro map
+    and load kinds on a corner sub-lattice (n_rb capped at its cell count)."""
+    nx, ny, nz = cells
+    fx, fy, fz = full.cells
+    idx = np.arange(fz)[:nz, None, None] * fy * fx + np.arange(fy)[None, :ny, None] * fx + \
+        np.arange(fx)[None, None, :nx]
+    q = LatticeProblem(**{k: getattr(full, k) for k in full.__dataclass_fields__})
+    q.cells = (nx, ny, nz)
+    q.r_cell = np.asarray(full.r_cell)[idx.ravel()]
+    q.n_rb = min(full.n_rb, nx * ny * nz)
+    q.name = f"{full.name}_sample_{nx}x{ny}x{nz}"
+    q.extra = {}
+    return q

@@ -44,6 +44,7 @@ def test_default_options_and_status_strings(lib):
     assert o.tol_inner_mixed == 1e-6 and o.gram_drop_mixed == 1e-9 and o.tc_split == 3
     assert o.profile_mask == 0
     assert o.max_outer == 100 and o.restart == 0 and o.wait_budget_ns == 10 ** 9 and o.check_inputs == 1
+    assert o.tc_bn == 0
     assert lib.fetidp_status_string(-4) == b"not converged"
     assert lib.fetidp_status_string(0) == b"ok"
 
@@ -81,7 +82,7 @@ def test_setup_rejects_bad_input_without_gpu(lib):
 
 @pytest.mark.parametrize("case", ["batch_elems", "batch_loads", "tc_split", "gram_drop", "clamp_axis", "nu",
                                   "iterations", "restart", "wait_budget", "nan_radius", "inf_load", "nan_map",
-                                  "nan_tol", "negative_E"])
+                                  "nan_tol", "negative_E", "tc_bn"])
 def test_setup_validation_without_gpu(lib, case):
     """Every argument and batch-compatibility check of fetidp_setup runs before any CUDA call and
     answers FETIDP_EINVAL (-1) with no context."""
@@ -120,6 +121,8 @@ def test_setup_validation_without_gpu(lib, case):
         opts = {"tol_outer": float("nan")}
     elif case == "negative_E":
         a.E_void = -1e-3
+    elif case == "tc_bn":
+        opts = {"precision": binding.FETIDP_MIXED_BF16, "tc_bn": 96}
     arr = (binding.Problem * len(probs))()
     keep = []
     for i, q in enumerate(probs):
@@ -134,7 +137,8 @@ def test_setup_validation_without_gpu(lib, case):
               "gram_drop": "gram_drop_mixed", "clamp_axis": "clamp axis", "nu": "nu out of range",
               "iterations": "iteration limits", "restart": "iteration limits",
               "wait_budget": "wait_budget_ns", "nan_radius": "non-finite", "inf_load": "non-finite",
-              "nan_map": "non-finite", "nan_tol": "tolerances", "negative_E": "negative"}[case]
+              "nan_map": "non-finite", "nan_tol": "tolerances", "negative_E": "negative",
+              "tc_bn": "tc_bn"}[case]
     assert expect in lib.fetidp_last_error().decode()
 
 

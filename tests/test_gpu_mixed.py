@@ -184,3 +184,26 @@ def test_mixed_inner_pcg_runs_as_one_graph(name):
     assert info["rel_residual"] <= 1e-8
     assert info["inner_graph"] == 1
     assert 0 < info["host_launches"] < info["kernel_launches"]
+
+
+def test_tc_tile_widths_time_and_agree():
+    """fetidp_tc_time measures the Eq. 46a tensor-core GEMM at every column-tile width, and solves
+    forced to each width reach the tolerance with the same solution (the widths change only the
+    rounding order of the K loop)."""
+    from paper_2308_11371_gb300 import binding
+    prob, lat, fe = oracle("bcc6")
+    s = _mixed(prob, tc_bn=0)
+    ms = {bn: s.tc_time(bn, 2) for bn in (64, 128, 256)}
+    s.close()
+    assert all(v > 0 for v in ms.values())
+    sols = []
+    for bn in (64, 128, 256):
+        s = _mixed(prob, tc_bn=bn)
+        u, _, info = s.solve()
+        assert info["rel_residual"] <= 1e-8
+        sols.append(_host(u))
+        s.close()
+    for u in sols[1:]:
+        assert _rel(u, sols[0]) < 1e-6
+    with pytest.raises(Exception):
+        binding.Solver(prob, precision=binding.FETIDP_FP64).tc_time(128)
