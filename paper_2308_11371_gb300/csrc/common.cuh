@@ -394,6 +394,8 @@ fetidp_status k_copy_scale(Ctx& c, const double* x, double* y, long long len, in
 
 // ---------------------------------------------------------------- kernels (cell-level compute)
 fetidp_status k_snapshots(Ctx& c);
+fetidp_status k_body_loads(Ctx& c, const Geo& g, const int* perm_dev, const double* dirs_dev, const int* body_dev,
+                           double* rhs, long long rhs_rs, double* fpc);
 // c[l] = sum_s f_l^(s) . u_l^(s) (u natural cell order); partial: [m][kRedBlocks] scratch
 fetidp_status k_compliance(Ctx& c, const double* u, double* out, double* partial);
 // Device state of the greedy loop (Algorithm 4): selected cells and a stop flag.

@@ -568,6 +568,69 @@ inline int gridn(long long work) {
   return (int)(g < 1 ? 1 : g);
 }
 
+
+// Body-force loads (Eq. 5b) of every cell for the body-force load cases: f_a = sum over the elements
+// and Gauss points of w detJ N_a(gp) times the load's direction.  One CTA per cell: the w detJ of
+// every (element, Gauss point) in shared memory, then each node's sum of w detJ N_a over its
+// elements, then every local DOF (natural index perm[li]) of every body load written into the
+// remaining-DOF right-hand side (li < nr) or the cell's corner loads (li >= nr).
+__global__ void body_loads_kernel(Geo g, int nelem, const int* __restrict__ perm, int n, int nr, int np,
+                                  const double* __restrict__ dirs, const int* __restrict__ body, int m,
+                                  double* __restrict__ rhs, long long rhs_rs, double* __restrict__ fpc,
+                                  long long ncell) {
+  extern __shared__ double blsm[];
+  const int d = g.dim, e = g.e, NA = 1 << d, nn1 = e + 1;
+  double* wq = blsm;                                  // [nelem][NA]
+  double* mn = blsm + (size_t)nelem * NA;             // [(e+1)^d]
+  const long long s = blockIdx.x;
+  const int nx = g.nc[0], ny = g.nc[1];
+  const int cx = (int)(s % nx), cy = (int)((s / nx) % ny), cz = (int)(s / ((long long)nx * ny));
+  const double h = 1.0 / e;
+  double hw = 1.0;
+  for (int k = 0; k < d; ++k) hw *= 0.5 * h;
+  for (int t = threadIdx.x; t < nelem * NA; t += blockDim.x) {
+    const int el = t / NA, gp = t - el * NA;
+    const int ex = el % e, ey = (el / e) % e, ez = el / (e * e);
+    double eta[3], xi[3], J[3][3];
+    gauss_point(g, cx, cy, cz, ex, ey, ez, gp, eta, xi);
+    macro_jacobian(g, xi, J);
+    const double det = d == 2 ? J[0][0] * J[1][1] - J[0][1] * J[1][0]
+                              : J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                                    J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                                    J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    wq[t] = hw * det;
+  }
+  __syncthreads();
+  const int nnode = d == 2 ? nn1 * nn1 : nn1 * nn1 * nn1;
+  for (int node = threadIdx.x; node < nnode; node += blockDim.x) {
+    const int ix = node % nn1, iy = (node / nn1) % nn1, iz = d == 3 ? node / (nn1 * nn1) : 0;
+    double acc = 0.0;
+    for (int A = 0; A < NA; ++A) {                    // the element in which this node is local node A
+      const int ex = ix - (A & 1), ey = iy - ((A >> 1) & 1), ez = d == 3 ? iz - ((A >> 2) & 1) : 0;
+      if (ex < 0 || ex >= e || ey < 0 || ey >= e || ez < 0 || (d == 3 && ez >= e)) continue;
+      const int el = ex + e * (ey + e * ez);
+      for (int gp = 0; gp < NA; ++gp) {
+        double Nv = 1.0;
+        for (int k = 0; k < d; ++k) {
+          const double tk = gauss_t((gp >> k) & 1);
+          Nv *= ((A >> k) & 1) ? tk : 1.0 - tk;
+        }
+        acc += wq[el * NA + gp] * Nv;
+      }
+    }
+    mn[node] = acc;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < m * n; t += blockDim.x) {
+    const int l = t / n, li = t - l * n;
+    if (!body[l]) continue;
+    const int nat = perm[li];
+    const double v = mn[nat / d] * dirs[l * d + nat % d];
+    if (li < nr) rhs[l * rhs_rs + s * nr + li] += v;
+    else fpc[((long long)l * ncell + s) * np + (li - nr)] += v;
+  }
+}
+
 }  // namespace
 
 fetidp_status k_row_reduce(Ctx& c, const double* X, long long rows, long long len, const double* z,
@@ -716,6 +779,19 @@ fetidp_status k_rom_combine(Ctx& c, const double* src, long long kstride, int ld
                             int rows, int cols, const double* coef, double* out, bool transpose) {
   rom_combine_kernel<<<gridn(c.N * rows * cols), kThreads, 0, c.stream>>>(
       src, kstride, ld, r0, c0, rows, cols, coef, c.nrb, c.N, out, transpose);
+  FD_CHECK_LAUNCH();
+  return FETIDP_OK;
+}
+
+fetidp_status k_body_loads(Ctx& c, const Geo& g, const int* perm_dev, const double* dirs_dev, const int* body_dev,
+                           double* rhs, long long rhs_rs, double* fpc) {
+  const int NA = 1 << c.d;
+  const int nnode = c.d == 2 ? (c.e + 1) * (c.e + 1) : (c.e + 1) * (c.e + 1) * (c.e + 1);
+  const size_t smem = sizeof(double) * ((size_t)c.nelem * NA + nnode);
+  ProfScope ps(c, FETIDP_K_SETUP, 0.0, 8.0 * (double)c.N * c.m * c.n);
+  cudaFuncSetAttribute(body_loads_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  body_loads_kernel<<<(unsigned)c.N, 256, smem, c.stream>>>(g, c.nelem, perm_dev, c.n, c.nr, c.np, dirs_dev,
+                                                             body_dev, c.m, rhs, rhs_rs, fpc, c.N);
   FD_CHECK_LAUNCH();
   return FETIDP_OK;
 }

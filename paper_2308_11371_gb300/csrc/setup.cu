@@ -433,10 +433,16 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
   // ---------------------------------------------------------------- loads: rhs = (f_R, f_P, 0)
   {
     std::vector<double> rhs((size_t)c.m * c.ntot, 0.0), fpc((size_t)c.m * c.N * c.np, 0.0);
+    // a single lattice's body-force loads are integrated on the GPU (every cell's Gauss points);
+    // tractions (face cells only) and batches stay on the host threads
+    bool any_body = false;
+    for (int l = 0; l < c.m; ++l) any_body = any_body || probs[0].load_kind[l] == 1;
+    const bool gpu_body = nprob == 1 && any_body;
     // each cell's loads (Eq. 5b) on the host threads; every cell writes only its own entries
     auto cells_range = [&](long long s0, long long s1) {
       std::vector<double> f(c.n);
       for (int l = 0; l < c.m; ++l) {
+        if (gpu_body && probs[0].load_kind[l] == 1) continue;
         double* rl = rhs.data() + (size_t)l * c.ntot;
         for (long long s = s0; s < s1; ++s) {
           int bl = 0;
@@ -461,8 +467,9 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
       }
       for (auto& th : pool) th.join();
     }
-    // primal loads f_P = sum_s A_p f_p (Eq. 18), assembled in cell order
-    for (int l = 0; l < c.m; ++l) {
+    // primal loads f_P = sum_s A_p f_p (Eq. 18), assembled in cell order (on the GPU below when the
+    // body forces are integrated there)
+    for (int l = 0; l < c.m && !gpu_body; ++l) {
       double* rl = rhs.data() + (size_t)l * c.ntot;
       for (long long s = 0; s < c.N; ++s)
         for (int k = 0; k < c.ncorner; ++k) {
@@ -474,6 +481,30 @@ fetidp_status setup_context(Ctx& c, const fetidp_problem* probs, int nprob, cons
     }
     FD_TRY(upload(c, &c.rhs, rhs));
     FD_TRY(upload(c, &c.rhs_p_cells, fpc));
+    if (gpu_body) {
+      std::vector<int> body(c.m);
+      std::vector<double> dirs((size_t)c.m * d);
+      for (int l = 0; l < c.m; ++l) {
+        body[l] = probs[0].load_kind[l] == 1 ? 1 : 0;
+        for (int i = 0; i < d; ++i) dirs[(size_t)l * d + i] = probs[0].load_dir[(size_t)l * d + i];
+      }
+      int *perm_d = nullptr, *body_d = nullptr;
+      double* dirs_d = nullptr;
+      FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&perm_d), sizeof(int) * c.n));
+      FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&body_d), sizeof(int) * c.m));
+      FD_TRY(tmp_alloc(c, reinterpret_cast<void**>(&dirs_d), sizeof(double) * dirs.size()));
+      FD_CUDA(cudaMemcpyAsync(perm_d, ref.perm.data(), sizeof(int) * c.n, cudaMemcpyHostToDevice, c.stream));
+      FD_CUDA(cudaMemcpyAsync(body_d, body.data(), sizeof(int) * c.m, cudaMemcpyHostToDevice, c.stream));
+      FD_CUDA(cudaMemcpyAsync(dirs_d, dirs.data(), sizeof(double) * dirs.size(), cudaMemcpyHostToDevice, c.stream));
+      FD_TRY(k_body_loads(c, c.lat[0].geo, perm_d, dirs_d, body_d, c.rhs, c.ntot, c.rhs_p_cells));
+      // f_P from every cell's corner loads (tractions and body forces)
+      FD_TRY(k_primal_assemble(c, CCellVec{c.rhs_p_cells, c.N * c.np, c.np}, c.rhs + c.N * c.nr, c.ntot, 1.0,
+                               1.0, c.m));
+      FD_CUDA(cudaStreamSynchronize(c.stream));   // host vectors go out of scope
+      tmp_free(c, perm_d);
+      tmp_free(c, body_d);
+      tmp_free(c, dirs_d);
+    }
     // per RHS: min over lattices of ||f_b|| / ||f|| (f_b: the lattice's remaining and primal loads)
     c.tol_scale.assign(c.m, 1.0);
     if (nprob > 1)
